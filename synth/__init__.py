@@ -1,0 +1,61 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests/bench and the oracle.
+
+Holds workload definitions (sizes, degrees, seeds) and random draws only; none
+of the method's arithmetic lives here. Knot vectors are inputs of the setup
+call: open, uniform, interior multiplicity p - alpha with alpha = p - 1.
+"""
+import numpy as np
+
+# Named workloads. "n_el" is per direction; p = pressure degree.
+WORKLOADS = {
+    # 2D unit square, Taylor-Hood, p=2, 16x16 elements, FP64 FD, MINRES 1e-8, seed 1
+    "square_th_p2_16": dict(dim=2, disc="TH", p=2, n_el=(16, 16), seeds=[1]),
+    # 3D unit cube, Taylor-Hood, p=3, 64^3 elements, 16 right-hand sides, seeds 200..215
+    "cube_th_p3_64": dict(dim=3, disc="TH", p=3, n_el=(64, 64, 64), seeds=list(range(200, 216))),
+    # 3D mapped cube (sine bump map, variable viscosity), p=3, 32^3 elements, seeds 300..303
+    "mapped_th_p3_32": dict(dim=3, disc="TH", p=3, n_el=(32, 32, 32), seeds=list(range(300, 304)),
+                            geometry="sine_bump"),
+}
+
+
+def open_uniform_knots(n_el, p, alpha=None):
+    """[0]*(p+1), interior j/n_el repeated (p - alpha) times, [1]*(p+1)."""
+    alpha = p - 1 if alpha is None else alpha
+    mult = p - alpha
+    knots = [0.0] * (p + 1)
+    for j in range(1, n_el):
+        knots += [j / n_el] * mult
+    knots += [1.0] * (p + 1)
+    return np.array(knots, dtype=np.float64)
+
+
+def knots_for(workload):
+    w = WORKLOADS[workload] if isinstance(workload, str) else workload
+    return [open_uniform_knots(n, w["p"]) for n in w["n_el"]]
+
+
+def rhs(seed, block_sizes):
+    """Right-hand side i.i.d. N(0,1) from numpy.random.default_rng(seed); the
+    last (pressure) block has its arithmetic mean removed so that the
+    right-hand side is orthogonal to the constant-pressure kernel."""
+    rng = np.random.default_rng(seed)
+    b = rng.standard_normal(int(sum(block_sizes)))
+    npres = block_sizes[-1]
+    b[-npres:] -= b[-npres:].mean()
+    return b
+
+
+def random_vector(seed, n):
+    return np.random.default_rng(seed).standard_normal(n)
+
+
+def batched_instances(seed=400, count=64, p_range=(2, 6), nel_range=(16, 96)):
+    """Independent unit-cube Taylor-Hood instances: p ~ U{2..6}, elements per
+    direction ~ U{16..96} independently per direction."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        p = int(rng.integers(p_range[0], p_range[1] + 1))
+        n_el = tuple(int(v) for v in rng.integers(nel_range[0], nel_range[1] + 1, size=3))
+        out.append(dict(dim=3, disc="TH", p=p, n_el=n_el))
+    return out

@@ -1,0 +1,60 @@
+"""Pins for oracle.stokes (paper Sec. 3 forms, Sec. 5 P_V / P_Q, Sec. 7 A_kk = P_V,k)."""
+import numpy as np
+import pytest
+
+from oracle import kron, stokes
+
+
+@pytest.mark.parametrize("dim,p,n_el", [(2, 1, 2), (2, 2, 2), (3, 1, 2)])
+def test_kronecker_blocks_vs_brute_force_quadrature(dim, p, n_el):
+    S = stokes.build_uniform(n_el, p, dim)
+    A_bf, B_bf = stokes.brute_force_TH(S)
+    A = stokes.assembled(S)
+    nv = S.block_sizes[0] * dim
+    np.testing.assert_allclose(A[:nv, :nv], A_bf, atol=1e-12 * np.abs(A_bf).max())
+    np.testing.assert_allclose(A[nv:, :nv], B_bf, atol=1e-12 * np.abs(B_bf).max())
+    np.testing.assert_allclose(A[:nv, nv:], B_bf.T, atol=1e-12 * np.abs(B_bf).max())
+    assert np.all(A[nv:, nv:] == 0)
+
+
+@pytest.mark.parametrize("dim,disc", [(2, "TH"), (3, "TH"), (2, "RT")])
+def test_symmetry_nullspace_and_matvec(dim, disc):
+    S = stokes.build_uniform(3 if dim == 3 else 4, 2, dim, disc)
+    A = stokes.assembled(S)
+    np.testing.assert_allclose(A, A.T, atol=1e-12 * np.abs(A).max())
+    # constant pressure is in the kernel: B^T 1 = 0 (partition of unity + v = 0 on the boundary)
+    x = np.zeros(S.n_total)
+    x[-S.block_sizes[-1]:] = 1.0
+    assert np.abs(A @ x).max() < 1e-12
+    rng = np.random.default_rng(2)
+    y = rng.standard_normal(S.n_total)
+    np.testing.assert_allclose(stokes.matvec(S, y), A @ y, atol=1e-11 * np.abs(A @ y).max())
+    # A_kk equals P_{V,k} on the identity map
+    off = np.concatenate([[0], np.cumsum(S.block_sizes)])
+    for k in range(dim):
+        np.testing.assert_allclose(A[off[k]:off[k + 1], off[k]:off[k + 1]], stokes.pv_matrix(S, k), atol=0)
+
+
+@pytest.mark.parametrize("disc", ["TH", "RT"])
+def test_preconditioner_blocks_spd(disc):
+    S = stokes.build_uniform(3, 2, 2, disc)
+    for k in range(2):
+        assert np.linalg.eigvalsh(stokes.pv_matrix(S, k)).min() > 0
+    assert np.linalg.eigvalsh(kron.kron_matrix(stokes.pq_factors(S))).min() > 0
+
+
+def test_rt_divergence_lands_in_pressure_space():
+    """RT (Sec. 2.2.2): d/d eta_k of the direction-k factor space is the pressure
+    space, so the velocity-pressure coupling is B = -P_Q D with D the exact
+    discrete divergence; hence P_Q^{-1} B has integer-free entries that
+    reproduce the divergence of a field exactly."""
+    S = stokes.build_uniform(4, 2, 2, "RT")
+    A = stokes.assembled(S)
+    nv = sum(S.block_sizes[:2])
+    B = A[nv:, :nv]
+    D = -np.linalg.solve(kron.kron_matrix(stokes.pq_factors(S)), B)
+    # a velocity field with zero discrete divergence has B v = 0 and D v = 0 simultaneously
+    ns = np.linalg.svd(B)[2][np.linalg.matrix_rank(B):]
+    assert np.abs(D @ ns.T).max() < 1e-9
+    # rank of B: all pressures except the constant
+    assert np.linalg.matrix_rank(B) == S.block_sizes[-1] - 1
