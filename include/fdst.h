@@ -1,0 +1,170 @@
+/*
+ * fdst.h - C ABI of the GB300 library for Fast-Diagonalization (FD)
+ * preconditioned MINRES on the isogeometric Stokes system
+ * (Montardini, Sangalli, Tani, arXiv 1712.00403).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Unknowns are ordered as the block system of Sec. 3 (eq. Stokes_system):
+ *   [u_1; u_2; (u_3;) p]. Each block is vec-ordered with i1 fastest (Sec. 2.3,
+ *   vec operator): index i1 + n1*(i2 + n2*i3). Velocity blocks hold interior
+ *   (Dirichlet-free) functions only (Taylor-Hood: eq. V_TH_0_basis1;
+ *   Raviart-Thomas: eq. basisRT_V1); the pressure block holds all functions.
+ * - Several right-hand sides are stored back to back: vector j starts at
+ *   j * n_total doubles.
+ * - Pointers named d_* are device pointers owned by the caller; pointers named
+ *   h_* are host pointers owned by the caller. Device work is enqueued on the
+ *   given stream (NULL = legacy default stream) and is asynchronous unless a
+ *   function says otherwise. Input and output vectors must not alias.
+ * - Every function returns an fdst_status; nothing throws across the ABI.
+ *   fdst_last_error() returns a thread-local text for the last failure.
+ */
+#ifndef FDST_H
+#define FDST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ABI-compatible with cudaStream_t; callers need not include CUDA headers. */
+typedef struct CUstream_st *fdst_stream;
+typedef struct fdst_ctx *fdst_handle;
+
+typedef enum {
+  FDST_OK = 0,
+  FDST_INVALID_ARGUMENT = 1, /* bad knots (not open, decreasing, multiplicity > p), sizes, flags */
+  FDST_NOT_SPD = 2,          /* Cholesky of a univariate mass matrix failed */
+  FDST_OUT_OF_MEMORY = 3,    /* device allocation failed */
+  FDST_CUDA_ERROR = 4,       /* a CUDA runtime call failed */
+  FDST_MAXIT = 5,            /* MINRES hit maxit before the tolerance */
+  FDST_STAGNATION = 6,       /* MINRES residual estimate stopped decreasing */
+  FDST_BREAKDOWN = 7,        /* Lanczos breakdown: preconditioner not positive on a Krylov vector */
+  FDST_TIMEOUT = 8,          /* a bounded device-side wait expired */
+  FDST_NAN_DETECTED = 9,     /* NaN/Inf in a MINRES inner product */
+  FDST_ADMISSION_REJECTED = 10,
+  FDST_NOT_SUPPORTED = 11    /* combination of options not implemented */
+} fdst_status;
+
+enum { FDST_TH = 0, FDST_RT = 1 };                          /* discretization (Sec. 2.2) */
+enum { FDST_FD_F64 = 0, FDST_FD_TF32X3 = 1, FDST_FD_BF16X6 = 2 }; /* FD contraction precision */
+enum { FDST_GEOM_IDENTITY = 0, FDST_GEOM_SINE_BUMP = 1 };   /* geometry map G */
+enum { FDST_VARIANT_PD = 0, FDST_VARIANT_PD_GEO = 1 };      /* P_D (Sec. 5) or P_D^G (Sec. 6) */
+
+typedef struct {
+  int dim;                 /* 2 or 3 */
+  int discretization;      /* FDST_TH or FDST_RT */
+  int degree;              /* pressure spline degree p >= 1; velocity degree is p+1 (Sec. 2.2) */
+  const double *h_knots[3];/* open pressure knot vector of each direction on [0,1] (Sec. 2.1) */
+  int nknots[3];           /* its length m + p + 1 */
+  double viscosity;        /* constant nu > 0 (identity geometry); ignored for SINE_BUMP */
+  int geometry;            /* FDST_GEOM_* */
+  int variant;             /* FDST_VARIANT_* */
+  int fd_precision;        /* FDST_FD_* */
+  double cpen;             /* Nitsche penalty C_pen (RT); <= 0 selects 5(alpha+1) (Sec. 7) */
+  int max_rhs;             /* most right-hand sides one call will pass (workspace sizing), >= 1 */
+} fdst_desc;
+
+typedef struct {
+  int dim;
+  int64_t n_total;         /* length of one block vector */
+  int nblocks;             /* dim velocity blocks + 1 pressure block */
+  int64_t block_offset[4];
+  int block_shape[4][3];   /* (n1, n2, n3) of each block; n3 = 1 in 2D */
+  int64_t device_bytes;    /* device memory held by the handle */
+  double flops_apply;      /* algorithmic flops of one preconditioner apply (one right-hand side):
+                              velocity 4 N sum_d n_d (Algorithm 1 steps 2 and 4), pressure 2 N sum_d n_d */
+  double flops_matvec;     /* algorithmic flops of one matvec: 2 x (band entries used) over the
+                              banded Kronecker factors of the evaluation plan */
+} fdst_sizes;
+
+typedef struct {
+  int iterations;
+  int status;              /* FDST_OK (converged), FDST_MAXIT, FDST_BREAKDOWN, FDST_NAN_DETECTED, ... */
+  double eta_rel;          /* final ||r||_{P^-1} / ||r_0||_{P^-1} from the MINRES recurrence */
+  double true_rel_res;     /* ||b - A x||_2 / ||b||_2 computed in FP64 after the solve */
+} fdst_solve_info;
+
+/*
+ * fdst_setup - build the spaces, univariate matrices, eigen-factors and
+ * device data of one Stokes problem (Sec. 2.1-2.2, Sec. 5, eq. eig_dec,
+ * Algorithm 1 step 1; Sec. 6 and the Appendix for FDST_VARIANT_PD_GEO).
+ * Host arrays in *desc are copied; the caller keeps them. Blocks the host
+ * until the device data are uploaded. On failure *out is NULL.
+ * Errors: FDST_INVALID_ARGUMENT, FDST_NOT_SPD, FDST_OUT_OF_MEMORY,
+ * FDST_CUDA_ERROR, FDST_NOT_SUPPORTED.
+ */
+fdst_status fdst_setup(const fdst_desc *desc, fdst_handle *out);
+
+/* Release every device and host resource of the handle (NULL is accepted). */
+fdst_status fdst_destroy(fdst_handle h);
+
+/* Sizes and layout of the block vectors of the handle. */
+fdst_status fdst_get_sizes(fdst_handle h, fdst_sizes *out);
+
+/*
+ * fdst_apply_prec - s = P^{-1} r for nrhs stacked vectors, with P = P_D =
+ * diag(P_V, P_Q) (eq. P_D) or P_D^G (Sec. 6). Velocity blocks by the FD method
+ * (Algorithm 1: s = (U3 x U2 x U1) Delta^{-1} (U3 x U2 x U1)^T r with
+ * Delta = sum_d c_d Lambda_d, c_k = 2 for component k, eq. prec3D_TH),
+ * pressure by P_Q^{-1} = M3^{-1} x M2^{-1} x M1^{-1} (eq. precQ).
+ * d_r, d_s: device, nrhs * n_total doubles each, not aliased.
+ * Uses the handle's workspace: calls on one handle must not overlap in time.
+ * Errors: FDST_INVALID_ARGUMENT (nrhs < 1 or > max_rhs), FDST_CUDA_ERROR.
+ */
+fdst_status fdst_apply_prec(fdst_handle h, const double *d_r, double *d_s, int nrhs, fdst_stream stream);
+
+/*
+ * fdst_matvec - y = A x with A the Stokes matrix of eq. Stokes_system:
+ * matrix-free Kronecker form on the identity map (blocks A_rs, B_r of Sec. 3
+ * with nu constant), assembled CSR on a mapped geometry.
+ * d_x, d_y: device, nrhs * n_total doubles each, not aliased.
+ */
+fdst_status fdst_matvec(fdst_handle h, const double *d_x, double *d_y, int nrhs, fdst_stream stream);
+
+/*
+ * fdst_solve - P-preconditioned MINRES (Paige-Saunders; Sec. 4, Sec. 7: tol
+ * 1e-8, x0 = 0) on nrhs independent right-hand sides at once. Every
+ * right-hand side keeps its own recurrence and stops on its own when
+ * ||r_j||_{P^-1} <= tol ||r_0||_{P^-1}. d_x holds the initial guesses on entry
+ * and the solutions on exit. info: host array of nrhs entries, filled when
+ * the call returns (the call synchronizes the stream). Returns FDST_OK when
+ * every right-hand side converged, otherwise the first non-OK per-RHS status.
+ */
+fdst_status fdst_solve(fdst_handle h, const double *d_b, double *d_x, int nrhs, double tol, int maxit,
+                       fdst_solve_info *info, fdst_stream stream);
+
+/*
+ * fdst_solve_host - fdst_solve with host vectors: copies h_b (and h_x as the
+ * initial guess) to handle-owned device buffers, solves, copies the
+ * solutions back to h_x. Pinned host memory makes the copies asynchronous.
+ */
+fdst_status fdst_solve_host(fdst_handle h, const double *h_b, double *h_x, int nrhs, double tol, int maxit,
+                            fdst_solve_info *info, fdst_stream stream);
+
+/* fdst_apply_prec_host - fdst_apply_prec with host vectors (copies in and out). */
+fdst_status fdst_apply_prec_host(fdst_handle h, const double *h_r, double *h_s, int nrhs, fdst_stream stream);
+
+/*
+ * fdst_set_timing - when on, fdst_solve records CUDA events around its
+ * phases (Stokes matvec, preconditioner, vector updates) on its stream and
+ * accumulates their durations; fdst_get_timing returns the sums (ms) and the
+ * number of matvec and preconditioner launches since the last reset.
+ */
+fdst_status fdst_set_timing(fdst_handle h, int on);
+fdst_status fdst_get_timing(fdst_handle h, double *ms_matvec, double *ms_prec, double *ms_vector,
+                            int64_t *n_matvec, int64_t *n_prec);
+
+/* Number of CUDA kernels this library has launched in the process so far
+ * (diagnostics: lets a caller count the kernels inside a timed region). */
+int64_t fdst_kernel_launches(void);
+
+/* Thread-local description of the last error on this thread. */
+const char *fdst_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FDST_H */

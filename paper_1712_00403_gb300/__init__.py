@@ -1,0 +1,209 @@
+"""GB300 (sm_103a) library for Fast-Diagonalization-preconditioned MINRES on
+the isogeometric Stokes system (Montardini, Sangalli, Tani, arXiv 1712.00403).
+
+Thin ctypes binding over the C ABI declared in include/fdst.h: argument
+marshalling only, every step of the computation runs in the library's CUDA
+kernels. PyTorch supplies device memory and streams. Importing this package
+fails loudly when the compiled library is missing; there is no CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfdst.so")
+
+TH, RT = 0, 1
+FD_F64, FD_TF32X3, FD_BF16X6 = 0, 1, 2
+GEOM_IDENTITY, GEOM_SINE_BUMP = 0, 1
+VARIANT_PD, VARIANT_PD_GEO = 0, 1
+
+STATUS = {0: "OK", 1: "INVALID_ARGUMENT", 2: "NOT_SPD", 3: "OUT_OF_MEMORY", 4: "CUDA_ERROR", 5: "MAXIT",
+          6: "STAGNATION", 7: "BREAKDOWN", 8: "TIMEOUT", 9: "NAN_DETECTED", 10: "ADMISSION_REJECTED",
+          11: "NOT_SUPPORTED"}
+
+
+class FdstError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("discretization", ctypes.c_int), ("degree", ctypes.c_int),
+                ("h_knots", ctypes.POINTER(ctypes.c_double) * 3), ("nknots", ctypes.c_int * 3),
+                ("viscosity", ctypes.c_double), ("geometry", ctypes.c_int), ("variant", ctypes.c_int),
+                ("fd_precision", ctypes.c_int), ("cpen", ctypes.c_double), ("max_rhs", ctypes.c_int)]
+
+
+class Sizes(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n_total", ctypes.c_int64), ("nblocks", ctypes.c_int),
+                ("block_offset", ctypes.c_int64 * 4), ("block_shape", (ctypes.c_int * 3) * 4),
+                ("device_bytes", ctypes.c_int64), ("flops_apply", ctypes.c_double),
+                ("flops_matvec", ctypes.c_double)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("status", ctypes.c_int), ("eta_rel", ctypes.c_double),
+                ("true_rel_res", ctypes.c_double)]
+
+
+ENTRY_POINTS = ["fdst_setup", "fdst_destroy", "fdst_get_sizes", "fdst_apply_prec", "fdst_matvec", "fdst_solve",
+                "fdst_solve_host", "fdst_apply_prec_host", "fdst_set_timing", "fdst_get_timing",
+                "fdst_kernel_launches", "fdst_last_error"]
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libfdst.so (built by paper_1712_00403_gb300.build). Raises when absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: run paper_1712_00403_gb300.build.build() (nvcc, sm_103a)")
+    lib = ctypes.CDLL(path)
+    vp, i, d, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
+    lib.fdst_setup.argtypes = [ctypes.POINTER(Desc), ctypes.POINTER(vp)]
+    lib.fdst_destroy.argtypes = [vp]
+    lib.fdst_get_sizes.argtypes = [vp, ctypes.POINTER(Sizes)]
+    lib.fdst_apply_prec.argtypes = [vp, vp, vp, i, vp]
+    lib.fdst_matvec.argtypes = [vp, vp, vp, i, vp]
+    lib.fdst_solve.argtypes = [vp, vp, vp, i, d, i, ctypes.POINTER(SolveInfo), vp]
+    lib.fdst_solve_host.argtypes = [vp, vp, vp, i, d, i, ctypes.POINTER(SolveInfo), vp]
+    lib.fdst_apply_prec_host.argtypes = [vp, vp, vp, i, vp]
+    lib.fdst_set_timing.argtypes = [vp, i]
+    lib.fdst_get_timing.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d),
+                                    ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    lib.fdst_last_error.restype = ctypes.c_char_p
+    for name in ENTRY_POINTS[:-2]:
+        getattr(lib, name).restype = ctypes.c_int
+    lib.fdst_kernel_launches.restype = ctypes.c_int64
+    lib.fdst_kernel_launches.argtypes = []
+    _lib = lib
+    return lib
+
+
+def kernel_launches():
+    """Kernels launched by the library so far in this process."""
+    return int(load_library().fdst_kernel_launches())
+
+
+def _check(code):
+    if code != 0:
+        raise FdstError(code, _lib.fdst_last_error().decode())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Stokes:
+    """One Stokes problem on the device: spaces, FD factors, operator and MINRES workspace.
+
+    knots: list (one per direction) of open pressure knot vectors on [0,1];
+    p: pressure degree. See include/fdst.h for the meaning of every option.
+    """
+
+    def __init__(self, knots, p, disc=TH, viscosity=1.0, fd_precision=FD_F64, max_rhs=1,
+                 geometry=GEOM_IDENTITY, variant=VARIANT_PD, cpen=0.0):
+        lib = load_library()
+        self._knots = [np.ascontiguousarray(k, dtype=np.float64) for k in knots]
+        desc = Desc()
+        desc.dim = len(knots)
+        desc.discretization = disc
+        desc.degree = p
+        for e, k in enumerate(self._knots):
+            desc.h_knots[e] = k.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            desc.nknots[e] = len(k)
+        desc.viscosity = viscosity
+        desc.geometry = geometry
+        desc.variant = variant
+        desc.fd_precision = fd_precision
+        desc.cpen = cpen
+        desc.max_rhs = max_rhs
+        h = ctypes.c_void_p()
+        _check(lib.fdst_setup(ctypes.byref(desc), ctypes.byref(h)))
+        self._h = h
+        self.max_rhs = max_rhs
+        s = Sizes()
+        _check(lib.fdst_get_sizes(h, ctypes.byref(s)))
+        self.dim = s.dim
+        self.n_total = int(s.n_total)
+        self.block_offsets = [int(s.block_offset[b]) for b in range(s.nblocks)] + [self.n_total]
+        self.block_shapes = [tuple(int(v) for v in s.block_shape[b]) for b in range(s.nblocks)]
+        self.block_sizes = [self.block_offsets[b + 1] - self.block_offsets[b] for b in range(s.nblocks)]
+        self.device_bytes = int(s.device_bytes)
+        self.flops_apply = float(s.flops_apply)
+        self.flops_matvec = float(s.flops_matvec)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.fdst_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _nrhs(self, t):
+        n = t.numel() // self.n_total
+        if n * self.n_total != t.numel():
+            raise ValueError("vector length is not a multiple of n_total")
+        return n
+
+    def apply_prec(self, r, s, stream=None):
+        _check(_lib.fdst_apply_prec(self._h, _dptr(r), _dptr(s), self._nrhs(r), _stream_ptr(stream)))
+
+    def matvec(self, x, y, stream=None):
+        _check(_lib.fdst_matvec(self._h, _dptr(x), _dptr(y), self._nrhs(x), _stream_ptr(stream)))
+
+    def solve(self, b, x, tol=1e-8, maxit=1000, stream=None, check=False):
+        n = self._nrhs(b)
+        info = (SolveInfo * n)()
+        code = _lib.fdst_solve(self._h, _dptr(b), _dptr(x), n, tol, maxit, info, _stream_ptr(stream))
+        if check:
+            _check(code)
+        elif code not in (0, 5, 6, 7, 9):
+            _check(code)
+        return [dict(iterations=i.iterations, status=STATUS.get(i.status, i.status), eta_rel=i.eta_rel,
+                     true_rel_res=i.true_rel_res) for i in info]
+
+    def solve_host(self, b, x, tol=1e-8, maxit=1000, stream=None):
+        """b, x: host numpy float64 arrays (x is the initial guess, overwritten)."""
+        n = b.size // self.n_total
+        info = (SolveInfo * n)()
+        code = _lib.fdst_solve_host(self._h, ctypes.c_void_p(b.ctypes.data), ctypes.c_void_p(x.ctypes.data), n,
+                                    tol, maxit, info, _stream_ptr(stream))
+        if code not in (0, 5, 6, 7, 9):
+            _check(code)
+        return [dict(iterations=i.iterations, status=STATUS.get(i.status, i.status), eta_rel=i.eta_rel,
+                     true_rel_res=i.true_rel_res) for i in info]
+
+    def apply_prec_host(self, r, s, stream=None):
+        n = r.size // self.n_total
+        _check(_lib.fdst_apply_prec_host(self._h, ctypes.c_void_p(r.ctypes.data), ctypes.c_void_p(s.ctypes.data),
+                                         n, _stream_ptr(stream)))
+
+    def set_timing(self, on=True):
+        _check(_lib.fdst_set_timing(self._h, int(on)))
+
+    def get_timing(self):
+        a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        m, p = ctypes.c_int64(), ctypes.c_int64()
+        _check(_lib.fdst_get_timing(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(m),
+                                    ctypes.byref(p)))
+        return dict(ms_matvec=a.value, ms_prec=b.value, ms_vector=c.value, n_matvec=m.value, n_prec=p.value)

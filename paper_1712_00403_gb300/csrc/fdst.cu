@@ -1,0 +1,854 @@
+// C ABI implementation: setup of the spaces, univariate matrices and FD
+// factors (paper Sec. 2.2, Sec. 5, Algorithm 1 step 1), the preconditioner
+// apply as a chain of rotation GEMMs (Algorithm 1 steps 2-4), the
+// matrix-free Kronecker Stokes matvec (Sec. 3 blocks on the identity map)
+// and the multi-right-hand-side MINRES driver (Sec. 4, Sec. 7).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "kernels.h"
+#include "kernels_tc.h"
+
+namespace fdst {
+
+static thread_local std::string g_err;
+void set_error(const std::string &s) { g_err = s; }
+
+#define CK(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) {                                                          \
+      set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                  \
+      return FDST_CUDA_ERROR;                                                         \
+    }                                                                                 \
+  } while (0)
+
+// ------------------------------------------------------------------ handle
+
+struct FdChain {
+  int nsteps = 0;
+  int div_step = -1;
+  const double *B[6] = {};
+  const float *Bt[6] = {};     // split-TF32 operand of the same step (pre-split, padded)
+  int R[6] = {}, K[6] = {}, N[6] = {};
+  double *lam_row = nullptr, *lam_col = nullptr;
+  float *lam_row_f = nullptr, *lam_col_f = nullptr;
+  const double *scale = nullptr;  // D^{-1/2} of P^G (nullptr: identity)
+  int64_t off = 0, size = 0;
+};
+
+struct BandDev {
+  int rows, cols, w;
+  double *vals;
+  int *lo;
+};
+
+struct PlanOp {
+  int stage;
+  int in_kind, in_id;    // kind: 0 = user x block, 1 = T1 buffer, 2 = G buffer
+  int out_kind, out_id;  // kind: 1 = T1, 2 = G, 3 = user y block
+  int band;
+  int mode;
+  int dims[3];           // input dims
+  double coef;
+  int accumulate;
+};
+
+}  // namespace fdst
+
+struct fdst_ctx {
+  fdst_desc desc{};
+  int dim = 0, p = 0;
+  std::vector<std::vector<double>> knots;
+  std::vector<fdst::Space1D> pres;
+  std::vector<std::vector<fdst::Space1D>> vel;
+  int nblocks = 0;
+  int shape[4][3] = {};
+  int64_t off[5] = {};
+  int64_t n_total = 0;
+  int max_rhs = 1;
+  std::vector<void *> allocs;
+  int64_t device_bytes = 0;
+  // FD
+  std::vector<fdst::FdChain> chains;
+  double *work[2] = {nullptr, nullptr};
+  float *work_f[2] = {nullptr, nullptr};
+  // matvec
+  std::vector<fdst::BandDev> bands;
+  std::vector<fdst::PlanOp> plan;
+  std::vector<double *> t1, g;
+  std::vector<int64_t> t1_size, g_size;
+  // MINRES
+  double *v = nullptr, *v_old = nullptr, *z = nullptr, *z_new = nullptr, *Az = nullptr, *w = nullptr,
+         *w_old = nullptr;
+  double *partials = nullptr, *dots = nullptr;
+  unsigned *counters = nullptr;
+  fdst::MinresState *state = nullptr;
+  int *done = nullptr, *n_stopped = nullptr;
+  int *h_n_stopped = nullptr;
+  double *h_dots = nullptr;
+  double *hb = nullptr, *hx = nullptr;  // device buffers for the host-pointer entry points
+  // timing
+  int timing = 0;
+  double ms_matvec = 0, ms_prec = 0, ms_vector = 0;
+  int64_t n_matvec = 0, n_prec = 0;
+};
+
+namespace fdst {
+
+template <typename T>
+static fdst_status dalloc(fdst_ctx *h, T **p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    *p = nullptr;
+    return e == cudaErrorMemoryAllocation ? FDST_OUT_OF_MEMORY : FDST_CUDA_ERROR;
+  }
+  h->allocs.push_back((void *)*p);
+  h->device_bytes += (int64_t)(count * sizeof(T));
+  return FDST_OK;
+}
+
+template <typename T>
+static fdst_status upload(fdst_ctx *h, T **p, const std::vector<T> &v) {
+  fdst_status st = dalloc(h, p, v.size());
+  if (st != FDST_OK) return st;
+  CK(cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return FDST_OK;
+}
+
+#define TRY(x)                           \
+  do {                                   \
+    fdst_status s_ = (x);                \
+    if (s_ != FDST_OK) return s_;        \
+  } while (0)
+
+static std::string space_key(const Space1D &s) {
+  std::ostringstream o;
+  o.precision(17);
+  o << s.degree << "|" << s.first << "|" << s.n << "|" << s.nitsche << "|" << s.cpen << "|" << s.h << "|";
+  for (double k : s.knots) o << k << ",";
+  return o.str();
+}
+
+// ------------------------------------------------------------------ setup: spaces
+
+static fdst_status build_spaces(fdst_ctx *h) {
+  const fdst_desc &d = h->desc;
+  const int dim = h->dim, p = h->p;
+  h->pres.resize(dim);
+  h->vel.assign(dim, std::vector<Space1D>(dim));
+  for (int e = 0; e < dim; ++e) {
+    Space1D s;
+    s.knots = h->knots[e];
+    s.degree = p;
+    s.first = 0;
+    s.n = s.m();
+    h->pres[e] = s;
+  }
+  for (int k = 0; k < dim; ++k)
+    for (int e = 0; e < dim; ++e) {
+      Space1D s;
+      if (d.discretization == FDST_TH) {
+        s.knots = elevate(h->knots[e]);
+        s.degree = p + 1;
+        s.first = 1;
+        s.n = s.m() - 2;
+      } else {
+        if (e == k) {
+          s.knots = h->knots[e];
+          s.knots.insert(s.knots.begin(), 0.0);
+          s.knots.push_back(1.0);
+          s.degree = p + 1;
+          s.first = 1;
+          s.n = s.m() - 2;
+        } else {
+          s.knots = h->knots[e];
+          s.degree = p;
+          s.first = 0;
+          s.n = s.m();
+          s.nitsche = true;
+          double hmax = 0.0;
+          for (size_t i = 1; i < s.knots.size(); ++i) hmax = std::max(hmax, s.knots[i] - s.knots[i - 1]);
+          s.h = hmax;
+          int alpha = p - inner_multiplicity(s.knots);
+          s.cpen = d.cpen > 0.0 ? d.cpen : 5.0 * (alpha + 1);
+        }
+      }
+      if (s.n < 1) {
+        set_error("velocity space has no interior functions (too few elements)");
+        return FDST_INVALID_ARGUMENT;
+      }
+      h->vel[k][e] = s;
+    }
+  h->nblocks = dim + 1;
+  int64_t o = 0;
+  for (int b = 0; b <= dim; ++b) {
+    for (int e = 0; e < 3; ++e) h->shape[b][e] = 1;
+    for (int e = 0; e < dim; ++e) h->shape[b][e] = b < dim ? h->vel[b][e].n : h->pres[e].n;
+    h->off[b] = o;
+    o += (int64_t)h->shape[b][0] * h->shape[b][1] * h->shape[b][2];
+  }
+  h->off[dim + 1] = o;
+  h->n_total = o;
+  return FDST_OK;
+}
+
+// ------------------------------------------------------------------ setup: FD chains
+
+static fdst_status build_fd(fdst_ctx *h) {
+  const int dim = h->dim, p = h->p;
+  const int npts = p + 2;
+  std::map<std::string, std::pair<std::vector<double>, Mat>> eig_cache;  // key -> (lam, U)
+  std::map<std::string, const double *> dev_cache;
+  auto dev_mat = [&](const std::string &key, const Mat &A, const double **out) -> fdst_status {
+    auto it = dev_cache.find(key);
+    if (it != dev_cache.end()) { *out = it->second; return FDST_OK; }
+    double *d = nullptr;
+    TRY(upload(h, &d, A.a));
+    dev_cache[key] = d;
+    *out = d;
+    return FDST_OK;
+  };
+  auto transpose = [](const Mat &A) {
+    Mat T(A.cols, A.rows);
+    for (int i = 0; i < A.rows; ++i)
+      for (int j = 0; j < A.cols; ++j) T(j, i) = A(i, j);
+    return T;
+  };
+  h->chains.clear();
+  for (int k = 0; k < dim; ++k) {
+    FdChain c;
+    c.off = h->off[k];
+    c.size = h->off[k + 1] - h->off[k];
+    std::vector<double> lam[3];
+    const double *Uf[3], *Ub[3];
+    for (int e = 0; e < dim; ++e) {
+      const Space1D &s = h->vel[k][e];
+      std::string key = space_key(s);
+      auto it = eig_cache.find(key);
+      if (it == eig_cache.end()) {
+        Mat K = stiffness_matrix(s, npts), M = mixed_matrix(s, 0, s, 0, npts);
+        std::vector<double> l;
+        Mat U;
+        if (!gen_eig(K, M, l, U)) {
+          set_error("univariate velocity mass matrix is not SPD");
+          return FDST_NOT_SPD;
+        }
+        it = eig_cache.emplace(key, std::make_pair(l, U)).first;
+      }
+      lam[e] = it->second.first;
+      TRY(dev_mat("U" + key, it->second.second, &Uf[e]));
+      TRY(dev_mat("Ut" + key, transpose(it->second.second), &Ub[e]));
+    }
+    const int n1 = h->shape[k][0], n2 = h->shape[k][1], n3 = h->shape[k][2];
+    double cf[3];
+    for (int e = 0; e < 3; ++e) cf[e] = (e == k) ? 2.0 : 1.0;
+    std::vector<double> lr, lc;
+    if (dim == 3) {
+      c.nsteps = 6;
+      int Rs[6] = {n2 * n3, n1 * n3, n1 * n2, n2 * n3, n1 * n3, n1 * n2};
+      int Ns[6] = {n1, n2, n3, n1, n2, n3};
+      for (int j = 0; j < 6; ++j) {
+        c.R[j] = Rs[j];
+        c.K[j] = c.N[j] = Ns[j];
+        c.B[j] = j < 3 ? Uf[j] : Ub[j - 3];
+      }
+      c.div_step = 2;
+      lr.resize((size_t)n1 * n2);
+      for (int b = 0; b < n2; ++b)
+        for (int a = 0; a < n1; ++a) lr[(size_t)b * n1 + a] = cf[0] * lam[0][a] + cf[1] * lam[1][b];
+      lc.resize(n3);
+      for (int cc = 0; cc < n3; ++cc) lc[cc] = cf[2] * lam[2][cc];
+    } else {
+      c.nsteps = 4;
+      int Rs[4] = {n2, n1, n2, n1};
+      int Ns[4] = {n1, n2, n1, n2};
+      for (int j = 0; j < 4; ++j) {
+        c.R[j] = Rs[j];
+        c.K[j] = c.N[j] = Ns[j];
+        c.B[j] = j < 2 ? Uf[j] : Ub[j - 2];
+      }
+      c.div_step = 1;
+      lr.resize(n1);
+      for (int a = 0; a < n1; ++a) lr[a] = cf[0] * lam[0][a];
+      lc.resize(n2);
+      for (int b = 0; b < n2; ++b) lc[b] = cf[1] * lam[1][b];
+    }
+    TRY(upload(h, &c.lam_row, lr));
+    TRY(upload(h, &c.lam_col, lc));
+    std::vector<float> lrf(lr.begin(), lr.end()), lcf(lc.begin(), lc.end());
+    TRY(upload(h, &c.lam_row_f, lrf));
+    TRY(upload(h, &c.lam_col_f, lcf));
+    h->chains.push_back(c);
+  }
+  // pressure: P_Q^{-1} = W3 x W2 x W1 with W_d = M_d^{-1} (eq. precQ, eq. kroninv)
+  {
+    FdChain c;
+    c.off = h->off[dim];
+    c.size = h->off[dim + 1] - h->off[dim];
+    const double *W[3];
+    for (int e = 0; e < dim; ++e) {
+      Mat M = mixed_matrix(h->pres[e], 0, h->pres[e], 0, npts), Mi;
+      if (!spd_inverse(M, Mi)) {
+        set_error("univariate pressure mass matrix is not SPD");
+        return FDST_NOT_SPD;
+      }
+      TRY(dev_mat("W" + space_key(h->pres[e]), Mi, &W[e]));
+    }
+    const int n1 = h->shape[dim][0], n2 = h->shape[dim][1], n3 = h->shape[dim][2];
+    if (dim == 3) {
+      c.nsteps = 3;
+      int Rs[3] = {n2 * n3, n1 * n3, n1 * n2};
+      int Ns[3] = {n1, n2, n3};
+      for (int j = 0; j < 3; ++j) { c.R[j] = Rs[j]; c.K[j] = c.N[j] = Ns[j]; c.B[j] = W[j]; }
+    } else {
+      c.nsteps = 2;
+      int Rs[2] = {n2, n1};
+      int Ns[2] = {n1, n2};
+      for (int j = 0; j < 2; ++j) { c.R[j] = Rs[j]; c.K[j] = c.N[j] = Ns[j]; c.B[j] = W[j]; }
+    }
+    h->chains.push_back(c);
+  }
+  return FDST_OK;
+}
+
+// ------------------------------------------------------------------ setup: matvec plan
+
+struct Term {
+  int dst, src;
+  double coef;
+  int f[3];  // band ids (mode order); -1 for the unused mode in 2D
+};
+
+static fdst_status build_matvec(fdst_ctx *h) {
+  const int dim = h->dim, p = h->p, npts = p + 2;
+  const double nu = h->desc.viscosity > 0.0 ? h->desc.viscosity : 1.0;
+  std::map<std::string, int> band_ids;
+  // factor key -> band id; builds int_0^1 b_a^(da) b_b^(db) (stiffness with Nitsche when both da=db=1 and same space)
+  auto band_of = [&](const Space1D &sa, int da, const Space1D &sb, int db, int *id) -> fdst_status {
+    std::string key = space_key(sa) + "#" + std::to_string(da) + "#" + space_key(sb) + "#" + std::to_string(db);
+    auto it = band_ids.find(key);
+    if (it != band_ids.end()) { *id = it->second; return FDST_OK; }
+    Mat A = (da == 1 && db == 1 && space_key(sa) == space_key(sb)) ? stiffness_matrix(sa, npts)
+                                                                    : mixed_matrix(sa, da, sb, db, npts);
+    int w = 0;
+    std::vector<int> first(A.rows, 0), last(A.rows, -1);
+    for (int i = 0; i < A.rows; ++i) {
+      for (int j = 0; j < A.cols; ++j)
+        if (A(i, j) != 0.0) { if (last[i] < 0) first[i] = j; last[i] = j; }
+      if (last[i] >= 0) w = std::max(w, last[i] - first[i] + 1);
+    }
+    if (w == 0) w = 1;
+    std::vector<int> lo(A.rows);
+    std::vector<double> vals((size_t)A.rows * w, 0.0);
+    for (int i = 0; i < A.rows; ++i) {
+      int l = last[i] < 0 ? 0 : first[i];
+      if (l + w > A.cols) l = A.cols - w;
+      lo[i] = l;
+      for (int j = 0; j < w; ++j) vals[(size_t)i * w + j] = A(i, l + j);
+    }
+    BandDev b{A.rows, A.cols, w, nullptr, nullptr};
+    TRY(upload(h, &b.vals, vals));
+    TRY(upload(h, &b.lo, lo));
+    *id = (int)h->bands.size();
+    h->bands.push_back(b);
+    band_ids[key] = *id;
+    return FDST_OK;
+  };
+  std::vector<Term> terms;
+  for (int r = 0; r < dim; ++r) {
+    for (int s = 0; s < dim; ++s) {
+      if (r == s) {
+        for (int d = 0; d < dim; ++d) {
+          Term t{r, s, nu * (d == r ? 2.0 : 1.0), {-1, -1, -1}};
+          for (int e = 0; e < dim; ++e) {
+            const Space1D &sp = h->vel[r][e];
+            TRY(band_of(sp, e == d, sp, e == d, &t.f[e]));
+          }
+          terms.push_back(t);
+        }
+      } else {
+        // [A_rs]_{ij} = nu int d_s B_i d_r B_j: direction s: (b_i)' b_j, direction r: b_i (b_j)'
+        Term t{r, s, nu, {-1, -1, -1}};
+        for (int e = 0; e < dim; ++e)
+          TRY(band_of(h->vel[r][e], e == s, h->vel[s][e], e == r, &t.f[e]));
+        terms.push_back(t);
+      }
+    }
+    // B_r^T p: direction r: (b^v)' b^p, others b^v b^p ; coefficient -1
+    Term t{r, dim, -1.0, {-1, -1, -1}};
+    for (int e = 0; e < dim; ++e) TRY(band_of(h->vel[r][e], e == r, h->pres[e], 0, &t.f[e]));
+    terms.push_back(t);
+  }
+  for (int r = 0; r < dim; ++r) {
+    Term t{dim, r, -1.0, {-1, -1, -1}};
+    for (int e = 0; e < dim; ++e) TRY(band_of(h->pres[e], 0, h->vel[r][e], e == r, &t.f[e]));
+    terms.push_back(t);
+  }
+  // ---- common-subexpression plan: stage 1 = distinct (src, f0); stage 2 (3D) = each term
+  // into the accumulator G(dst, f2); stage 3 = dst += G x_3 f2. In 2D stage 2 writes dst.
+  std::map<std::pair<int, int>, int> t1_ids;
+  std::map<std::pair<int, int>, int> g_ids;
+  std::vector<PlanOp> st1, st2, st3;
+  std::vector<int> g_first;            // whether the G buffer was written yet
+  std::vector<int> dst_written(dim + 1, 0);
+  auto srcdims = [&](int b, int out[3]) { for (int e = 0; e < 3; ++e) out[e] = h->shape[b][e]; };
+  for (const Term &t : terms) {
+    auto k1 = std::make_pair(t.src, t.f[0]);
+    int t1;
+    auto it = t1_ids.find(k1);
+    if (it == t1_ids.end()) {
+      t1 = (int)h->t1_size.size();
+      t1_ids[k1] = t1;
+      PlanOp op{};
+      op.stage = 1;
+      op.in_kind = 0; op.in_id = t.src;
+      op.out_kind = 1; op.out_id = t1;
+      op.band = t.f[0]; op.mode = 0;
+      srcdims(t.src, op.dims);
+      op.coef = 1.0; op.accumulate = 0;
+      st1.push_back(op);
+      int64_t sz = (int64_t)h->bands[t.f[0]].rows * op.dims[1] * op.dims[2];
+      h->t1_size.push_back(sz);
+    } else t1 = it->second;
+    int d1[3];
+    srcdims(t.src, d1);
+    d1[0] = h->bands[t.f[0]].rows;
+    if (dim == 2) {
+      PlanOp op{};
+      op.stage = 2;
+      op.in_kind = 1; op.in_id = t1;
+      op.out_kind = 3; op.out_id = t.dst;
+      op.band = t.f[1]; op.mode = 1;
+      for (int e = 0; e < 3; ++e) op.dims[e] = d1[e];
+      op.coef = t.coef;
+      op.accumulate = dst_written[t.dst];
+      dst_written[t.dst] = 1;
+      st2.push_back(op);
+    } else {
+      auto kg = std::make_pair(t.dst, t.f[2]);
+      int gid;
+      auto ig = g_ids.find(kg);
+      if (ig == g_ids.end()) {
+        gid = (int)h->g_size.size();
+        g_ids[kg] = gid;
+        h->g_size.push_back((int64_t)d1[0] * h->bands[t.f[1]].rows * d1[2]);
+        g_first.push_back(0);
+        PlanOp op3{};
+        op3.stage = 3;
+        op3.in_kind = 2; op3.in_id = gid;
+        op3.out_kind = 3; op3.out_id = t.dst;
+        op3.band = t.f[2]; op3.mode = 2;
+        op3.dims[0] = d1[0]; op3.dims[1] = h->bands[t.f[1]].rows; op3.dims[2] = d1[2];
+        op3.coef = 1.0;
+        op3.accumulate = dst_written[t.dst];
+        dst_written[t.dst] = 1;
+        st3.push_back(op3);
+      } else gid = ig->second;
+      PlanOp op{};
+      op.stage = 2;
+      op.in_kind = 1; op.in_id = t1;
+      op.out_kind = 2; op.out_id = gid;
+      op.band = t.f[1]; op.mode = 1;
+      for (int e = 0; e < 3; ++e) op.dims[e] = d1[e];
+      op.coef = t.coef;
+      op.accumulate = g_first[gid];
+      g_first[gid] = 1;
+      st2.push_back(op);
+    }
+  }
+  h->plan.clear();
+  h->plan.insert(h->plan.end(), st1.begin(), st1.end());
+  h->plan.insert(h->plan.end(), st2.begin(), st2.end());
+  h->plan.insert(h->plan.end(), st3.begin(), st3.end());
+  for (int64_t sz : h->t1_size) {
+    double *b = nullptr;
+    TRY(dalloc(h, &b, (size_t)sz * h->max_rhs));
+    h->t1.push_back(b);
+  }
+  for (int64_t sz : h->g_size) {
+    double *b = nullptr;
+    TRY(dalloc(h, &b, (size_t)sz * h->max_rhs));
+    h->g.push_back(b);
+  }
+  return FDST_OK;
+}
+
+// ------------------------------------------------------------------ split-TF32 operands
+
+static fdst_status tc_prepare(fdst_ctx *) {
+  set_error("split-TF32 FD contraction not built");
+  return FDST_NOT_SUPPORTED;
+}
+
+// ------------------------------------------------------------------ execution
+
+static fdst_status run_apply(fdst_ctx *h, const double *r, double *s, int nrhs, const int *done, cudaStream_t st) {
+  int maxsteps = 0;
+  for (auto &c : h->chains) maxsteps = std::max(maxsteps, c.nsteps);
+  const bool tc = h->desc.fd_precision != FDST_FD_F64;
+  for (int j = 0; j < maxsteps; ++j) {
+    if (tc) {
+      TcGroup g;
+      for (auto &c : h->chains) {
+        if (j >= c.nsteps) continue;
+        TcProb &P = g.p[g.nprob++];
+        const bool first = j == 0, last = j == c.nsteps - 1;
+        P.A64 = first ? r + c.off : nullptr;
+        P.A32 = first ? nullptr : h->work_f[(j - 1) % 2] + c.off;
+        P.C64 = last ? s + c.off : nullptr;
+        P.C32 = last ? nullptr : h->work_f[j % 2] + c.off;
+        P.Bt = c.Bt[j];
+        P.rhs_stride = h->n_total;
+        P.R = c.R[j]; P.K = c.K[j]; P.N = c.N[j];
+        if (j == c.div_step) { P.lam_row = c.lam_row_f; P.lam_col = c.lam_col_f; }
+        P.scale_in = first ? c.scale : nullptr;
+        P.scale_out = last ? c.scale : nullptr;
+      }
+      TRY(launch_gemm_tc(g, nrhs, done, st));
+    } else {
+      GemmGroup g;
+      for (auto &c : h->chains) {
+        if (j >= c.nsteps) continue;
+        GemmProb &P = g.p[g.nprob++];
+        P.A = j == 0 ? r + c.off : h->work[(j - 1) % 2] + c.off;
+        P.C = j == c.nsteps - 1 ? s + c.off : h->work[j % 2] + c.off;
+        P.B = c.B[j];
+        P.a_rhs_stride = P.c_rhs_stride = h->n_total;
+        P.R = c.R[j]; P.K = c.K[j]; P.N = c.N[j];
+        if (j == c.div_step) { P.lam_row = c.lam_row; P.lam_col = c.lam_col; }
+        P.scale_in = j == 0 ? c.scale : nullptr;
+        P.scale_out = j == c.nsteps - 1 ? c.scale : nullptr;
+      }
+      launch_gemm_f64(g, nrhs, done, st);
+    }
+  }
+  CK(cudaGetLastError());
+  return FDST_OK;
+}
+
+static fdst_status run_matvec(fdst_ctx *h, const double *x, double *y, int nrhs, const int *done, cudaStream_t st) {
+  // pack consecutive ops of a stage into launches with pairwise distinct outputs
+  size_t i = 0;
+  const auto &P = h->plan;
+  while (i < P.size()) {
+    BandGroup g;
+    std::vector<std::pair<int, int>> outs;
+    int stage = P[i].stage;
+    while (i < P.size() && P[i].stage == stage && g.nop < kMaxGroup) {
+      auto o = std::make_pair(P[i].out_kind, P[i].out_id);
+      if (std::find(outs.begin(), outs.end(), o) != outs.end()) break;
+      outs.push_back(o);
+      const PlanOp &op = P[i];
+      BandOp &b = g.op[g.nop++];
+      const BandDev &bd = h->bands[op.band];
+      b.vals = bd.vals; b.lo = bd.lo; b.w = bd.w; b.rows = bd.rows;
+      b.d0 = op.dims[0]; b.d1 = op.dims[1]; b.d2 = op.dims[2]; b.mode = op.mode;
+      b.coef = op.coef; b.accumulate = op.accumulate;
+      if (op.in_kind == 0) { b.X = x + h->off[op.in_id]; b.x_rhs_stride = h->n_total; }
+      else if (op.in_kind == 1) { b.X = h->t1[op.in_id]; b.x_rhs_stride = h->t1_size[op.in_id]; }
+      else { b.X = h->g[op.in_id]; b.x_rhs_stride = h->g_size[op.in_id]; }
+      if (op.out_kind == 3) { b.Y = y + h->off[op.out_id]; b.y_rhs_stride = h->n_total; }
+      else if (op.out_kind == 1) { b.Y = h->t1[op.out_id]; b.y_rhs_stride = h->t1_size[op.out_id]; }
+      else { b.Y = h->g[op.out_id]; b.y_rhs_stride = h->g_size[op.out_id]; }
+      ++i;
+    }
+    launch_band(g, nrhs, done, st);
+  }
+  CK(cudaGetLastError());
+  return FDST_OK;
+}
+
+}  // namespace fdst
+
+using namespace fdst;
+
+extern "C" {
+
+const char *fdst_last_error(void) { return g_err.c_str(); }
+
+int64_t fdst_kernel_launches(void) { return (int64_t)launch_count(); }
+
+fdst_status fdst_destroy(fdst_handle h) {
+  if (!h) return FDST_OK;
+  for (void *p : h->allocs) cudaFree(p);
+  if (h->h_n_stopped) cudaFreeHost(h->h_n_stopped);
+  if (h->h_dots) cudaFreeHost(h->h_dots);
+  delete h;
+  return FDST_OK;
+}
+
+fdst_status fdst_setup(const fdst_desc *desc, fdst_handle *out) {
+  if (!out) { set_error("out is NULL"); return FDST_INVALID_ARGUMENT; }
+  *out = nullptr;
+  if (!desc) { set_error("desc is NULL"); return FDST_INVALID_ARGUMENT; }
+  if (desc->dim != 2 && desc->dim != 3) { set_error("dim must be 2 or 3"); return FDST_INVALID_ARGUMENT; }
+  if (desc->discretization != FDST_TH && desc->discretization != FDST_RT) {
+    set_error("unknown discretization");
+    return FDST_INVALID_ARGUMENT;
+  }
+  if (desc->degree < 1 || desc->degree > 12) { set_error("degree must be in [1, 12]"); return FDST_INVALID_ARGUMENT; }
+  if (desc->max_rhs < 1) { set_error("max_rhs must be >= 1"); return FDST_INVALID_ARGUMENT; }
+  if (desc->geometry != FDST_GEOM_IDENTITY || desc->variant != FDST_VARIANT_PD) {
+    set_error("mapped geometry / P_D^G not available in this build");
+    return FDST_NOT_SUPPORTED;
+  }
+  if (desc->fd_precision != FDST_FD_F64 && desc->fd_precision != FDST_FD_TF32X3) {
+    set_error("unknown or unsupported FD precision");
+    return FDST_NOT_SUPPORTED;
+  }
+  std::unique_ptr<fdst_ctx> h(new fdst_ctx());
+  h->desc = *desc;
+  h->dim = desc->dim;
+  h->p = desc->degree;
+  h->max_rhs = desc->max_rhs;
+  for (int e = 0; e < h->dim; ++e) {
+    if (!desc->h_knots[e] || desc->nknots[e] <= 0) { set_error("missing knot vector"); return FDST_INVALID_ARGUMENT; }
+    std::vector<double> t(desc->h_knots[e], desc->h_knots[e] + desc->nknots[e]);
+    std::string msg = validate_knots(t, h->p);
+    if (!msg.empty()) { set_error("direction " + std::to_string(e + 1) + ": " + msg); return FDST_INVALID_ARGUMENT; }
+    h->knots.push_back(t);
+  }
+  for (int e = h->dim; e < 3; ++e) h->desc.h_knots[e] = nullptr;
+  for (int e = 0; e < 3; ++e) h->desc.h_knots[e] = nullptr;   // not kept: the caller owns them
+  fdst_ctx *hp = h.get();
+  fdst_status st;
+  auto fail = [&](fdst_status s) { fdst_destroy(h.release()); return s; };
+  if ((st = build_spaces(hp)) != FDST_OK) return fail(st);
+  if ((st = build_fd(hp)) != FDST_OK) return fail(st);
+  if (desc->fd_precision == FDST_FD_TF32X3) {
+    if ((st = tc_prepare(hp)) != FDST_OK) return fail(st);
+  }
+  if ((st = build_matvec(hp)) != FDST_OK) return fail(st);
+  const size_t nv = (size_t)hp->n_total * hp->max_rhs;
+  if ((st = dalloc(hp, &hp->work[0], nv)) != FDST_OK) return fail(st);
+  if ((st = dalloc(hp, &hp->work[1], nv)) != FDST_OK) return fail(st);
+  double **vecs[] = {&hp->v, &hp->v_old, &hp->z, &hp->z_new, &hp->Az, &hp->w, &hp->w_old};
+  for (double **pv : vecs)
+    if ((st = dalloc(hp, pv, nv)) != FDST_OK) return fail(st);
+  if ((st = dalloc(hp, &hp->partials, (size_t)304 * hp->max_rhs)) != FDST_OK) return fail(st);
+  if ((st = dalloc(hp, &hp->dots, (size_t)4 * hp->max_rhs)) != FDST_OK) return fail(st);
+  if ((st = dalloc(hp, &hp->counters, (size_t)hp->max_rhs)) != FDST_OK) return fail(st);
+  if ((st = dalloc(hp, &hp->state, (size_t)hp->max_rhs)) != FDST_OK) return fail(st);
+  if ((st = dalloc(hp, &hp->done, (size_t)hp->max_rhs)) != FDST_OK) return fail(st);
+  if ((st = dalloc(hp, &hp->n_stopped, 1)) != FDST_OK) return fail(st);
+  if (cudaMemset(hp->counters, 0, sizeof(unsigned) * hp->max_rhs) != cudaSuccess ||
+      cudaMallocHost((void **)&hp->h_n_stopped, sizeof(int)) != cudaSuccess ||
+      cudaMallocHost((void **)&hp->h_dots, sizeof(double) * 4 * hp->max_rhs) != cudaSuccess) {
+    set_error("pinned host allocation failed");
+    return fail(FDST_CUDA_ERROR);
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    set_error(std::string("setup: ") + cudaGetErrorString(cudaGetLastError()));
+    return fail(FDST_CUDA_ERROR);
+  }
+  *out = h.release();
+  return FDST_OK;
+}
+
+fdst_status fdst_get_sizes(fdst_handle h, fdst_sizes *out) {
+  if (!h || !out) { set_error("NULL argument"); return FDST_INVALID_ARGUMENT; }
+  std::memset(out, 0, sizeof(*out));
+  out->dim = h->dim;
+  out->n_total = h->n_total;
+  out->nblocks = h->nblocks;
+  for (int b = 0; b < h->nblocks; ++b) {
+    out->block_offset[b] = h->off[b];
+    for (int e = 0; e < 3; ++e) out->block_shape[b][e] = h->shape[b][e];
+  }
+  out->device_bytes = h->device_bytes;
+  double fa = 0.0;
+  for (auto &c : h->chains) {
+    double sum_n = 0.0;
+    for (int j = 0; j < c.nsteps; ++j) sum_n += c.N[j];
+    fa += 2.0 * (double)c.size * sum_n;   // each step: 2 K N R flops with K = N = n_d, R N = size
+  }
+  out->flops_apply = fa;
+  double fm = 0.0;
+  for (auto &op : h->plan) {
+    int od[3] = {op.dims[0], op.dims[1], op.dims[2]};
+    od[op.mode] = h->bands[op.band].rows;
+    fm += 2.0 * h->bands[op.band].w * (double)od[0] * od[1] * od[2];
+  }
+  out->flops_matvec = fm;
+  return FDST_OK;
+}
+
+fdst_status fdst_apply_prec(fdst_handle h, const double *d_r, double *d_s, int nrhs, fdst_stream stream) {
+  if (!h || !d_r || !d_s) { set_error("NULL argument"); return FDST_INVALID_ARGUMENT; }
+  if (nrhs < 1 || nrhs > h->max_rhs) { set_error("nrhs out of range [1, max_rhs]"); return FDST_INVALID_ARGUMENT; }
+  if (d_r == d_s) { set_error("r and s alias"); return FDST_INVALID_ARGUMENT; }
+  return run_apply(h, d_r, d_s, nrhs, nullptr, (cudaStream_t)stream);
+}
+
+fdst_status fdst_matvec(fdst_handle h, const double *d_x, double *d_y, int nrhs, fdst_stream stream) {
+  if (!h || !d_x || !d_y) { set_error("NULL argument"); return FDST_INVALID_ARGUMENT; }
+  if (nrhs < 1 || nrhs > h->max_rhs) { set_error("nrhs out of range [1, max_rhs]"); return FDST_INVALID_ARGUMENT; }
+  if (d_x == d_y) { set_error("x and y alias"); return FDST_INVALID_ARGUMENT; }
+  return run_matvec(h, d_x, d_y, nrhs, nullptr, (cudaStream_t)stream);
+}
+
+fdst_status fdst_set_timing(fdst_handle h, int on) {
+  if (!h) { set_error("NULL handle"); return FDST_INVALID_ARGUMENT; }
+  h->timing = on;
+  h->ms_matvec = h->ms_prec = h->ms_vector = 0;
+  h->n_matvec = h->n_prec = 0;
+  return FDST_OK;
+}
+
+fdst_status fdst_get_timing(fdst_handle h, double *ms_matvec, double *ms_prec, double *ms_vector, int64_t *n_matvec,
+                            int64_t *n_prec) {
+  if (!h) { set_error("NULL handle"); return FDST_INVALID_ARGUMENT; }
+  if (ms_matvec) *ms_matvec = h->ms_matvec;
+  if (ms_prec) *ms_prec = h->ms_prec;
+  if (ms_vector) *ms_vector = h->ms_vector;
+  if (n_matvec) *n_matvec = h->n_matvec;
+  if (n_prec) *n_prec = h->n_prec;
+  return FDST_OK;
+}
+
+fdst_status fdst_solve(fdst_handle h, const double *d_b, double *d_x, int nrhs, double tol, int maxit,
+                       fdst_solve_info *info, fdst_stream stream) {
+  if (!h || !d_b || !d_x || !info) { set_error("NULL argument"); return FDST_INVALID_ARGUMENT; }
+  if (nrhs < 1 || nrhs > h->max_rhs) { set_error("nrhs out of range [1, max_rhs]"); return FDST_INVALID_ARGUMENT; }
+  if (!(tol >= 0.0) || maxit < 1) { set_error("tol must be >= 0 and maxit >= 1"); return FDST_INVALID_ARGUMENT; }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = h->n_total;
+  // timing events: (matvec, prec, vector) per phase
+  std::vector<cudaEvent_t> ev;
+  auto mark = [&](void) -> cudaEvent_t {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    cudaEventRecord(e, st);
+    ev.push_back(e);
+    return e;
+  };
+  struct Span { int kind; size_t a, b; };
+  std::vector<Span> spans;
+  // ---- init: v = b - A x0 ; v_old = w = w_old = 0 ; z = P^{-1} v ; gamma_1 = sqrt(<v, z>)
+  CK(cudaMemsetAsync(h->done, 0, sizeof(int) * nrhs, st));
+  CK(cudaMemsetAsync(h->n_stopped, 0, sizeof(int), st));
+  TRY(run_matvec(h, d_x, h->Az, nrhs, nullptr, st));
+  launch_axpby(d_b, h->v, 1.0, 0.0, n, n, nrhs, st);
+  launch_axpby(h->Az, h->v, -1.0, 1.0, n, n, nrhs, st);
+  CK(cudaMemsetAsync(h->v_old, 0, sizeof(double) * n * nrhs, st));
+  CK(cudaMemsetAsync(h->w, 0, sizeof(double) * n * nrhs, st));
+  CK(cudaMemsetAsync(h->w_old, 0, sizeof(double) * n * nrhs, st));
+  TRY(run_apply(h, h->v, h->z, nrhs, nullptr, st));
+  launch_dot(h->v, h->z, n, n, nrhs, h->partials, h->counters, h->dots, nullptr, st);
+  launch_minres_init(h->state, h->dots, h->done, nrhs, h->n_stopped, st);
+  launch_scale_by_inv_gamma(h->z, h->state, n, n, nrhs, h->done, st);
+  double *v = h->v, *v_old = h->v_old, *w = h->w, *w_old = h->w_old;
+  double *delta = h->dots + nrhs, *g2 = h->dots + 2 * nrhs;
+  const int check_every = 4;
+  int it = 0;
+  while (it < maxit) {
+    size_t e0 = 0;
+    if (h->timing) { mark(); e0 = ev.size() - 1; }
+    TRY(run_matvec(h, h->z, h->Az, nrhs, h->done, st));
+    size_t e1 = 0;
+    if (h->timing) { mark(); e1 = ev.size() - 1; spans.push_back({0, e0, e1}); }
+    launch_dot(h->Az, h->z, n, n, nrhs, h->partials, h->counters, delta, h->done, st);
+    launch_minres_lanczos(h->Az, v, v_old, h->state, delta, n, n, nrhs, h->done, st);
+    size_t e2 = 0;
+    if (h->timing) { mark(); e2 = ev.size() - 1; spans.push_back({2, e1, e2}); }
+    TRY(run_apply(h, v_old, h->z_new, nrhs, h->done, st));
+    size_t e3 = 0;
+    if (h->timing) { mark(); e3 = ev.size() - 1; spans.push_back({1, e2, e3}); }
+    launch_dot(v_old, h->z_new, n, n, nrhs, h->partials, h->counters, g2, h->done, st);
+    launch_minres_scalars(h->state, delta, g2, nrhs, tol, maxit, h->done, h->n_stopped, st);
+    launch_minres_update(w_old, w, d_x, h->z, h->z_new, h->state, n, n, nrhs, h->done, st);
+    launch_minres_commit(h->state, h->done, nrhs, st);
+    if (h->timing) { mark(); spans.push_back({2, e3, ev.size() - 1}); }
+    std::swap(v, v_old);
+    std::swap(w, w_old);
+    ++it;
+    h->n_matvec += 1;
+    h->n_prec += 1;
+    if (it % check_every == 0 || it == maxit) {
+      CK(cudaMemcpyAsync(h->h_n_stopped, h->n_stopped, sizeof(int), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      if (*h->h_n_stopped >= nrhs) break;
+    }
+  }
+  CK(cudaGetLastError());
+  // ---- true residual ||b - A x|| / ||b|| in FP64
+  TRY(run_matvec(h, d_x, h->Az, nrhs, nullptr, st));
+  launch_axpby(d_b, h->v, 1.0, 0.0, n, n, nrhs, st);
+  launch_axpby(h->Az, h->v, -1.0, 1.0, n, n, nrhs, st);
+  launch_dot(h->v, h->v, n, n, nrhs, h->partials, h->counters, h->dots, nullptr, st);
+  launch_dot(d_b, d_b, n, n, nrhs, h->partials, h->counters, h->dots + nrhs, nullptr, st);
+  std::vector<MinresState> hs(nrhs);
+  CK(cudaMemcpyAsync(h->h_dots, h->dots, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(hs.data(), h->state, sizeof(MinresState) * nrhs, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (h->timing) {
+    for (auto &sp : spans) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[sp.a], ev[sp.b]);
+      (sp.kind == 0 ? h->ms_matvec : sp.kind == 1 ? h->ms_prec : h->ms_vector) += ms;
+    }
+    for (auto e : ev) cudaEventDestroy(e);
+  }
+  fdst_status ret = FDST_OK;
+  for (int j = 0; j < nrhs; ++j) {
+    info[j].iterations = hs[j].iters;
+    info[j].status = hs[j].stop || hs[j].status ? hs[j].status : FDST_MAXIT;
+    if (hs[j].eta0 == 0.0 && hs[j].status == 0) info[j].status = FDST_OK;
+    info[j].eta_rel = hs[j].eta0 > 0 ? std::fabs(hs[j].eta) / hs[j].eta0 : 0.0;
+    double bb = h->h_dots[nrhs + j];
+    info[j].true_rel_res = bb > 0 ? std::sqrt(h->h_dots[j] / bb) : std::sqrt(h->h_dots[j]);
+    if (ret == FDST_OK && info[j].status != FDST_OK) ret = (fdst_status)info[j].status;
+  }
+  return ret;
+}
+
+static fdst_status ensure_host_buffers(fdst_handle h) {
+  if (h->hb) return FDST_OK;
+  const size_t nv = (size_t)h->n_total * h->max_rhs;
+  TRY(dalloc(h, &h->hb, nv));
+  TRY(dalloc(h, &h->hx, nv));
+  return FDST_OK;
+}
+
+fdst_status fdst_solve_host(fdst_handle h, const double *h_b, double *h_x, int nrhs, double tol, int maxit,
+                            fdst_solve_info *info, fdst_stream stream) {
+  if (!h || !h_b || !h_x || !info) { set_error("NULL argument"); return FDST_INVALID_ARGUMENT; }
+  if (nrhs < 1 || nrhs > h->max_rhs) { set_error("nrhs out of range [1, max_rhs]"); return FDST_INVALID_ARGUMENT; }
+  TRY(ensure_host_buffers(h));
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bytes = sizeof(double) * h->n_total * nrhs;
+  CK(cudaMemcpyAsync(h->hb, h_b, bytes, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(h->hx, h_x, bytes, cudaMemcpyHostToDevice, st));
+  fdst_status s = fdst_solve(h, h->hb, h->hx, nrhs, tol, maxit, info, stream);
+  CK(cudaMemcpyAsync(h_x, h->hx, bytes, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return s;
+}
+
+fdst_status fdst_apply_prec_host(fdst_handle h, const double *h_r, double *h_s, int nrhs, fdst_stream stream) {
+  if (!h || !h_r || !h_s) { set_error("NULL argument"); return FDST_INVALID_ARGUMENT; }
+  if (nrhs < 1 || nrhs > h->max_rhs) { set_error("nrhs out of range [1, max_rhs]"); return FDST_INVALID_ARGUMENT; }
+  TRY(ensure_host_buffers(h));
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bytes = sizeof(double) * h->n_total * nrhs;
+  CK(cudaMemcpyAsync(h->hb, h_r, bytes, cudaMemcpyHostToDevice, st));
+  TRY(run_apply(h, h->hb, h->hx, nrhs, nullptr, st));
+  CK(cudaMemcpyAsync(h_s, h->hx, bytes, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return FDST_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,90 @@
+// Device kernel launchers (host-callable) used by the C ABI implementation.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace fdst {
+
+constexpr int kMaxGroup = 8;
+
+// process-wide count of kernel launches issued by this library
+void count_launch(long long n);
+long long launch_count();
+
+// One mode contraction of the FD method written as a GEMM with a transposed
+// store: C(r, n) = sum_k A[r*K + k] * B[k*N + n], stored at C[n*R + r].
+// The contracted index is the fastest of the input, so the output's fastest
+// index is the next one to contract (Algorithm 1 steps 2 and 4 as a chain of
+// such steps). Optional: the input scaled by scale_in[r*K + k], the output
+// divided by (lam_row[r] + lam_col[n]) (Algorithm 1 step 3) and scaled by
+// scale_out[n*R + r].
+struct GemmProb {
+  const double *A = nullptr;
+  double *C = nullptr;
+  const double *B = nullptr;
+  int64_t a_rhs_stride = 0, c_rhs_stride = 0;
+  int R = 0, K = 0, N = 0;
+  const double *lam_row = nullptr, *lam_col = nullptr;
+  const double *scale_in = nullptr, *scale_out = nullptr;
+};
+struct GemmGroup {
+  GemmProb p[kMaxGroup];
+  int nprob = 0;
+};
+void launch_gemm_f64(const GemmGroup &g, int nrhs, const int *done, cudaStream_t s);
+
+// Banded mode product: Y = coef * (X x_mode Bd) (or Y += ...), X with dims
+// (d0, d1, d2) (d0 fastest), Bd rows x d_mode banded: row i has entries
+// vals[i*w + j] at columns lo[i] + j.
+struct BandOp {
+  const double *X = nullptr;
+  double *Y = nullptr;
+  const double *vals = nullptr;
+  const int *lo = nullptr;
+  int w = 0, rows = 0;
+  int d0 = 1, d1 = 1, d2 = 1, mode = 0;
+  double coef = 1.0;
+  int accumulate = 0;
+  int64_t x_rhs_stride = 0, y_rhs_stride = 0;
+};
+struct BandGroup {
+  BandOp op[kMaxGroup];
+  int nop = 0;
+};
+void launch_band(const BandGroup &g, int nrhs, const int *done, cudaStream_t s);
+
+// ---- MINRES (per right-hand side state, all device resident)
+struct MinresState {
+  double gamma, gamma_old, delta, c, c_old, s, s_old, eta, eta0;
+  double inv_a1, a2, a3, coef_x, inv_gamma_new, g_pending;
+  int iters, status, stop, pad;
+};
+
+// dot products <a_j, b_j> over n elements for every right-hand side j
+// (vectors at stride `stride`), reduced deterministically into out[j].
+void launch_dot(const double *a, const double *b, int64_t n, int64_t stride, int nrhs, double *partials,
+                unsigned *counters, double *out, const int *done, cudaStream_t s);
+
+// y_j = alpha * x_j + beta * y_j for all j (elementwise, deterministic).
+void launch_axpby(const double *x, double *y, double alpha, double beta, int64_t n, int64_t stride, int nrhs,
+                  cudaStream_t s);
+
+// MINRES init after v = b - A x0, z_new = P^{-1} v and dot g = <v, z_new>.
+void launch_minres_init(MinresState *st, const double *g, int *done, int nrhs, int *n_stopped, cudaStream_t s);
+// v_old <- Az - (delta/gamma) v - (gamma/gamma_old) v_old (delta = <Az, z>, in st).
+void launch_minres_lanczos(const double *Az, const double *v, double *v_old, const MinresState *st,
+                           const double *delta, int64_t n, int64_t stride, int nrhs, const int *done,
+                           cudaStream_t s);
+// scalar QR update from gamma_new^2 = <v_new, z_new> (one thread per right-hand side).
+void launch_minres_scalars(MinresState *st, const double *delta, const double *g2, int nrhs, double tol,
+                           int maxit, const int *done, int *n_stopped, cudaStream_t s);
+// w_old <- (z - a3 w_old - a2 w)/a1; x += coef_x w_old; z <- z_new / gamma_new; then done |= stop.
+void launch_minres_update(double *w_old, const double *w, double *x, double *z, const double *z_new,
+                          MinresState *st, int64_t n, int64_t stride, int nrhs, int *done, cudaStream_t s);
+void launch_minres_commit(MinresState *st, int *done, int nrhs, cudaStream_t s);
+// z <- z / gamma (per right-hand side) used at start.
+void launch_scale_by_inv_gamma(double *z, const MinresState *st, int64_t n, int64_t stride, int nrhs,
+                               const int *done, cudaStream_t s);
+
+}  // namespace fdst

@@ -1,0 +1,404 @@
+// FP64 device kernels: FD mode contractions (rotation GEMM with the
+// Algorithm 1 step 3 divide fused into the epilogue), banded Kronecker mode
+// products of the Stokes matvec, deterministic dot products and the MINRES
+// vector / scalar updates. On GB300 the FP64 pipe (~1.2 TFLOP/s measured) is
+// the bound of every kernel here that does arithmetic; the vector kernels
+// are HBM-bound.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+
+#include "kernels.h"
+
+namespace fdst {
+
+static std::atomic<long long> g_launches{0};
+void count_launch(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+// ------------------------------------------------------------------ rotation GEMM
+
+namespace {
+constexpr int kBR = 64;   // rows per tile
+constexpr int kBK = 16;   // k per smem stage
+constexpr int kThreads = 256;
+}  // namespace
+
+template <int TN>
+__global__ void __launch_bounds__(kThreads) k_gemm_f64(GemmGroup g, int nrhs, const int *done) {
+  constexpr int BN = 16 * TN;
+  const int prob = blockIdx.z % g.nprob;
+  const int rhs = blockIdx.z / g.nprob;
+  if (done && done[rhs]) return;
+  const GemmProb &P = g.p[prob];
+  const int R = P.R, K = P.K, N = P.N;
+  const int r0 = blockIdx.x * kBR, n0 = blockIdx.y * BN;
+  if (r0 >= R || n0 >= N) return;
+  const double *A = P.A + rhs * P.a_rhs_stride;
+  double *C = P.C + rhs * P.c_rhs_stride;
+  const double *B = P.B;
+
+  __shared__ double As[kBK][kBR + 1];
+  __shared__ double Bs[kBK][BN];
+  const int tid = threadIdx.x, tr = tid & 15, tn = tid >> 4;
+  double acc[4][TN];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
+
+  for (int k0 = 0; k0 < K; k0 += kBK) {
+#pragma unroll
+    for (int e = 0; e < (kBR * kBK) / kThreads; ++e) {
+      int idx = tid + e * kThreads;
+      int kk = idx % kBK, rr = idx / kBK;
+      int r = r0 + rr, k = k0 + kk;
+      double v = 0.0;
+      if (r < R && k < K) {
+        int64_t ai = (int64_t)r * K + k;
+        v = A[ai];
+        if (P.scale_in) v *= P.scale_in[ai];
+      }
+      As[kk][rr] = v;
+    }
+#pragma unroll
+    for (int e = 0; e < (BN * kBK) / kThreads; ++e) {
+      int idx = tid + e * kThreads;
+      int nn = idx % BN, kk = idx / BN;
+      int n = n0 + nn, k = k0 + kk;
+      Bs[kk][nn] = (n < N && k < K) ? B[(int64_t)k * N + n] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kBK; ++kk) {
+      double a[4], b[TN];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][tr + 16 * i];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tn + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int r = r0 + tr + 16 * i;
+    if (r >= R) continue;
+    double lr = P.lam_row ? P.lam_row[r] : 0.0;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      int n = n0 + tn + 16 * j;
+      if (n >= N) continue;
+      double v = acc[i][j];
+      if (P.lam_row) v = v / (lr + P.lam_col[n]);
+      int64_t ci = (int64_t)n * R + r;
+      if (P.scale_out) v *= P.scale_out[ci];
+      C[ci] = v;
+    }
+  }
+}
+
+void launch_gemm_f64(const GemmGroup &g, int nrhs, const int *done, cudaStream_t s) {
+  int maxR = 0, maxN = 0;
+  for (int i = 0; i < g.nprob; ++i) {
+    maxR = g.p[i].R > maxR ? g.p[i].R : maxR;
+    maxN = g.p[i].N > maxN ? g.p[i].N : maxN;
+  }
+  // pick the column tile that wastes the fewest padded columns
+  int best = 4, bestpad = 1 << 30;
+  for (int tn = 2; tn <= 4; ++tn) {
+    int bn = 16 * tn;
+    int pad = 0;
+    for (int i = 0; i < g.nprob; ++i) pad += (((g.p[i].N + bn - 1) / bn) * bn - g.p[i].N) * g.p[i].R;
+    if (pad < bestpad || (pad == bestpad && tn > best)) { bestpad = pad; best = tn; }
+  }
+  dim3 grid((maxR + kBR - 1) / kBR, (maxN + 16 * best - 1) / (16 * best), g.nprob * nrhs);
+  count_launch(1);
+  if (best == 2) k_gemm_f64<2><<<grid, kThreads, 0, s>>>(g, nrhs, done);
+  else if (best == 3) k_gemm_f64<3><<<grid, kThreads, 0, s>>>(g, nrhs, done);
+  else k_gemm_f64<4><<<grid, kThreads, 0, s>>>(g, nrhs, done);
+}
+
+// ------------------------------------------------------------------ banded mode product
+
+__global__ void __launch_bounds__(256) k_band(BandGroup g, int nrhs, const int *done) {
+  const int rhs = blockIdx.y;
+  if (done && done[rhs]) return;
+  const BandOp &op = g.op[blockIdx.z];
+  int dims[3] = {op.d0, op.d1, op.d2};
+  int od[3] = {op.d0, op.d1, op.d2};
+  od[op.mode] = op.rows;
+  const int64_t total = (int64_t)od[0] * od[1] * od[2];
+  const int64_t stride_in = op.mode == 0 ? 1 : (op.mode == 1 ? (int64_t)dims[0] : (int64_t)dims[0] * dims[1]);
+  const double *X = op.X + rhs * op.x_rhs_stride;
+  double *Y = op.Y + rhs * op.y_rhs_stride;
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total; o += (int64_t)gridDim.x * blockDim.x) {
+    int o0 = (int)(o % od[0]);
+    int64_t t = o / od[0];
+    int o1 = (int)(t % od[1]);
+    int o2 = (int)(t / od[1]);
+    int i = op.mode == 0 ? o0 : (op.mode == 1 ? o1 : o2);
+    int64_t base;
+    if (op.mode == 0) base = ((int64_t)o2 * dims[1] + o1) * dims[0];
+    else if (op.mode == 1) base = (int64_t)o2 * dims[1] * dims[0] + o0;
+    else base = (int64_t)o1 * dims[0] + o0;
+    const double *v = op.vals + (int64_t)i * op.w;
+    const int l = op.lo[i];
+    double acc = 0.0;
+    for (int j = 0; j < op.w; ++j) acc = fma(v[j], X[base + (int64_t)(l + j) * stride_in], acc);
+    acc *= op.coef;
+    Y[o] = op.accumulate ? Y[o] + acc : acc;
+  }
+}
+
+void launch_band(const BandGroup &g, int nrhs, const int *done, cudaStream_t s) {
+  int64_t maxt = 0;
+  for (int i = 0; i < g.nop; ++i) {
+    int od[3] = {g.op[i].d0, g.op[i].d1, g.op[i].d2};
+    od[g.op[i].mode] = g.op[i].rows;
+    int64_t t = (int64_t)od[0] * od[1] * od[2];
+    maxt = t > maxt ? t : maxt;
+  }
+  int64_t blocks = (maxt + 255) / 256;
+  if (blocks > 2048) blocks = 2048;
+  if (blocks < 1) blocks = 1;
+  dim3 grid((unsigned)blocks, nrhs, g.nop);
+  count_launch(1);
+  k_band<<<grid, 256, 0, s>>>(g, nrhs, done);
+}
+
+// ------------------------------------------------------------------ reductions
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-level partial sums, then the last block to finish (atomic ticket)
+// adds the partials in index order: the result does not depend on timing.
+__global__ void __launch_bounds__(256) k_dot(const double *a, const double *b, int64_t n, int64_t stride,
+                                             double *partials, unsigned *counters, double *out,
+                                             const int *done) {
+  const int rhs = blockIdx.y;
+  if (done && done[rhs]) return;
+  const double *x = a + rhs * stride;
+  const double *y = b + rhs * stride;
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    s = fma(x[i], y[i], s);
+  __shared__ double ws[8];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += ws[w];
+    partials[(int64_t)rhs * gridDim.x + blockIdx.x] = t;
+    __threadfence();
+    unsigned ticket = atomicAdd(&counters[rhs], 1u);
+    last = (ticket == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last && threadIdx.x < 32) {
+    __threadfence();
+    double t = 0.0;
+    const volatile double *pp = partials + (int64_t)rhs * gridDim.x;
+    for (unsigned i = threadIdx.x; i < gridDim.x; i += 32) t += pp[i];
+    t = warp_sum(t);
+    if (threadIdx.x == 0) {
+      out[rhs] = t;
+      counters[rhs] = 0u;
+    }
+  }
+}
+
+void launch_dot(const double *a, const double *b, int64_t n, int64_t stride, int nrhs, double *partials,
+                unsigned *counters, double *out, const int *done, cudaStream_t s) {
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 304) blocks = 304;
+  if (blocks < 1) blocks = 1;
+  count_launch(1);
+  k_dot<<<dim3((unsigned)blocks, nrhs), 256, 0, s>>>(a, b, n, stride, partials, counters, out, done);
+}
+
+__global__ void k_axpby(const double *x, double *y, double alpha, double beta, int64_t n, int64_t stride) {
+  const double *xr = x + blockIdx.y * stride;
+  double *yr = y + blockIdx.y * stride;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    yr[i] = alpha * xr[i] + (beta == 0.0 ? 0.0 : beta * yr[i]);
+}
+
+void launch_axpby(const double *x, double *y, double alpha, double beta, int64_t n, int64_t stride, int nrhs,
+                  cudaStream_t s) {
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  count_launch(1);
+  k_axpby<<<dim3((unsigned)blocks, nrhs), 256, 0, s>>>(x, y, alpha, beta, n, stride);
+}
+
+// ------------------------------------------------------------------ MINRES
+
+__global__ void k_minres_init(MinresState *st, const double *g, int *done, int nrhs, int *n_stopped) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nrhs) return;
+  MinresState S = {};
+  double g2 = g[j];
+  S.iters = 0;
+  S.status = 0;
+  S.stop = 0;
+  if (!(g2 >= 0.0) || isinf(g2)) {
+    S.status = isnan(g2) || isinf(g2) ? 9 : 7;  // FDST_NAN_DETECTED : FDST_BREAKDOWN
+    done[j] = 1;
+    atomicAdd(n_stopped, 1);
+  } else {
+    double gamma = sqrt(g2);
+    S.gamma = gamma;
+    S.gamma_old = 1.0;
+    S.c = S.c_old = 1.0;
+    S.s = S.s_old = 0.0;
+    S.eta = S.eta0 = gamma;
+    S.inv_gamma_new = gamma > 0.0 ? 1.0 / gamma : 0.0;
+    done[j] = gamma == 0.0;
+    if (gamma == 0.0) atomicAdd(n_stopped, 1);
+  }
+  st[j] = S;
+}
+
+void launch_minres_init(MinresState *st, const double *g, int *done, int nrhs, int *n_stopped, cudaStream_t s) {
+  count_launch(1);
+  k_minres_init<<<(nrhs + 63) / 64, 64, 0, s>>>(st, g, done, nrhs, n_stopped);
+}
+
+__global__ void k_scale_inv_gamma(double *z, const MinresState *st, int64_t n, int64_t stride, const int *done) {
+  const int j = blockIdx.y;
+  if (done && done[j]) return;
+  const double f = st[j].inv_gamma_new;
+  double *zr = z + j * stride;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    zr[i] *= f;
+}
+
+void launch_scale_by_inv_gamma(double *z, const MinresState *st, int64_t n, int64_t stride, int nrhs,
+                               const int *done, cudaStream_t s) {
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  count_launch(1);
+  k_scale_inv_gamma<<<dim3((unsigned)blocks, nrhs), 256, 0, s>>>(z, st, n, stride, done);
+}
+
+__global__ void k_minres_lanczos(const double *Az, const double *v, double *v_old, const MinresState *st,
+                                 const double *delta, int64_t n, int64_t stride, const int *done) {
+  const int j = blockIdx.y;
+  if (done[j]) return;
+  const double gamma = st[j].gamma, gamma_old = st[j].gamma_old;
+  const double f1 = delta[j] / gamma, f2 = gamma / gamma_old;
+  const double *a = Az + j * stride, *vv = v + j * stride;
+  double *vo = v_old + j * stride;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    vo[i] = a[i] - f1 * vv[i] - f2 * vo[i];
+}
+
+void launch_minres_lanczos(const double *Az, const double *v, double *v_old, const MinresState *st,
+                           const double *delta, int64_t n, int64_t stride, int nrhs, const int *done,
+                           cudaStream_t s) {
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  count_launch(1);
+  k_minres_lanczos<<<dim3((unsigned)blocks, nrhs), 256, 0, s>>>(Az, v, v_old, st, delta, n, stride, done);
+}
+
+// One thread per right-hand side: Givens QR update of the Lanczos tridiagonal
+// matrix and the residual estimate eta (the QR recurrences of MINRES).
+__global__ void k_minres_scalars(MinresState *st, const double *delta, const double *g2v, int nrhs, double tol,
+                                 int maxit, const int *done, int *n_stopped) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nrhs || done[j]) return;
+  MinresState S = st[j];
+  const double d = delta[j], g2 = g2v[j];
+  S.iters += 1;
+  if (isnan(d) || isinf(d) || isnan(g2) || isinf(g2)) {
+    S.status = 9;  // FDST_NAN_DETECTED
+    S.stop = 1;
+    S.inv_a1 = 0.0; S.a2 = 0.0; S.a3 = 0.0; S.coef_x = 0.0; S.inv_gamma_new = 0.0;
+    st[j] = S;
+    atomicAdd(n_stopped, 1);
+    return;
+  }
+  const bool breakdown = g2 < 0.0;
+  const double gn = breakdown ? 0.0 : sqrt(g2);
+  const double a0 = S.c * d - S.c_old * S.s * S.gamma;
+  const double a1 = sqrt(a0 * a0 + gn * gn);
+  const double a2 = S.s * d + S.c_old * S.c * S.gamma;
+  const double a3 = S.s_old * S.gamma;
+  const double cn = a1 > 0.0 ? a0 / a1 : 1.0, sn = a1 > 0.0 ? gn / a1 : 0.0;
+  S.inv_a1 = a1 > 0.0 ? 1.0 / a1 : 0.0;
+  S.a2 = a2;
+  S.a3 = a3;
+  S.coef_x = cn * S.eta;
+  S.eta = -sn * S.eta;
+  S.inv_gamma_new = gn > 0.0 ? 1.0 / gn : 0.0;
+  S.gamma_old = S.gamma;
+  S.gamma = gn;
+  S.c_old = S.c;
+  S.c = cn;
+  S.s_old = S.s;
+  S.s = sn;
+  const double rel = fabs(S.eta) / S.eta0;
+  if (breakdown) { S.status = 7; S.stop = 1; }
+  else if (rel <= tol || gn == 0.0) { S.status = 0; S.stop = 1; }
+  else if (S.iters >= maxit) { S.status = 5; S.stop = 1; }
+  if (S.stop) atomicAdd(n_stopped, 1);
+  st[j] = S;
+}
+
+void launch_minres_scalars(MinresState *st, const double *delta, const double *g2, int nrhs, double tol,
+                           int maxit, const int *done, int *n_stopped, cudaStream_t s) {
+  count_launch(1);
+  k_minres_scalars<<<(nrhs + 63) / 64, 64, 0, s>>>(st, delta, g2, nrhs, tol, maxit, done, n_stopped);
+}
+
+__global__ void k_minres_update(double *w_old, const double *w, double *x, double *z, const double *z_new,
+                                const MinresState *st, int64_t n, int64_t stride, const int *done) {
+  const int j = blockIdx.y;
+  if (done[j]) return;
+  const MinresState &S = st[j];
+  const double ia1 = S.inv_a1, a2 = S.a2, a3 = S.a3, cx = S.coef_x, ig = S.inv_gamma_new;
+  double *wo = w_old + j * stride, *xx = x + j * stride, *zz = z + j * stride;
+  const double *ww = w + j * stride, *zn = z_new + j * stride;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double wn = (zz[i] - a3 * wo[i] - a2 * ww[i]) * ia1;
+    wo[i] = wn;
+    xx[i] = fma(cx, wn, xx[i]);
+    zz[i] = zn[i] * ig;
+  }
+}
+
+void launch_minres_update(double *w_old, const double *w, double *x, double *z, const double *z_new,
+                          MinresState *st, int64_t n, int64_t stride, int nrhs, int *done, cudaStream_t s) {
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  count_launch(1);
+  k_minres_update<<<dim3((unsigned)blocks, nrhs), 256, 0, s>>>(w_old, w, x, z, z_new, st, n, stride, done);
+}
+
+__global__ void k_minres_commit(MinresState *st, int *done, int nrhs) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < nrhs && !done[j] && st[j].stop) done[j] = 1;
+}
+
+void launch_minres_commit(MinresState *st, int *done, int nrhs, cudaStream_t s) {
+  count_launch(1);
+  k_minres_commit<<<(nrhs + 63) / 64, 64, 0, s>>>(st, done, nrhs);
+}
+
+}  // namespace fdst

@@ -1,0 +1,31 @@
+// Split-TF32 tensor-core (tcgen05) mode contraction: launcher interface.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/fdst.h"
+
+namespace fdst {
+
+// Same contraction as GemmProb (C(r, n) = sum_k A(r, k) B(k, n) stored at
+// C[n*R + r]) with FP32 intermediates: the first step reads the FP64 input,
+// the last writes FP64; B is pre-split into TF32 hi/lo parts.
+struct TcProb {
+  const double *A64 = nullptr;
+  const float *A32 = nullptr;
+  double *C64 = nullptr;
+  float *C32 = nullptr;
+  const float *Bt = nullptr;
+  int64_t rhs_stride = 0;
+  int R = 0, K = 0, N = 0;
+  const float *lam_row = nullptr, *lam_col = nullptr;
+  const double *scale_in = nullptr, *scale_out = nullptr;
+};
+struct TcGroup {
+  TcProb p[8];
+  int nprob = 0;
+};
+fdst_status launch_gemm_tc(const TcGroup &g, int nrhs, const int *done, cudaStream_t s);
+
+}  // namespace fdst

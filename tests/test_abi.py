@@ -1,0 +1,86 @@
+"""The C-ABI library builds, loads and exports every symbol include/fdst.h
+declares; host-side argument validation (no GPU needed)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "fdst.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fdst_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_1712_00403_gb300 as pkg
+    from paper_1712_00403_gb300 import build
+    if not os.path.exists(pkg.LIB_PATH):
+        build.build()
+    return pkg.load_library()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ["fdst_setup", "fdst_destroy", "fdst_apply_prec", "fdst_matvec", "fdst_solve", "fdst_last_error"]:
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    import paper_1712_00403_gb300 as pkg
+    out = subprocess.run(["nm", "-D", "--defined-only", pkg.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (fdst_[a-z_0-9]+)", out))
+    for n in _declared():
+        assert n in exported, n
+        assert hasattr(lib, n)
+    assert set(pkg.ENTRY_POINTS) <= exported
+
+
+def _desc(pkg, knots, p, dim=None, **kw):
+    d = pkg.Desc()
+    d.dim = dim if dim is not None else len(knots)
+    d.degree = p
+    keep = [np.ascontiguousarray(k, dtype=np.float64) for k in knots]
+    for e, k in enumerate(keep):
+        d.h_knots[e] = k.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        d.nknots[e] = len(k)
+    d.viscosity = 1.0
+    d.max_rhs = kw.get("max_rhs", 1)
+    d.fd_precision = kw.get("fd_precision", 0)
+    d.geometry = kw.get("geometry", 0)
+    d.variant = kw.get("variant", 0)
+    d._keep = keep
+    return d
+
+
+@pytest.mark.parametrize("knots,p,why", [
+    ([[0, 0, 0.5, 1, 1]] * 2, 2, "not open"),
+    ([[0, 0, 0, 0.6, 0.4, 1, 1, 1]] * 2, 2, "nondecreasing"),
+    ([[0, 0, 0, 0.5, 0.5, 0.5, 1, 1, 1]] * 2, 2, "multiplicity"),
+    ([[0, 0, 0, 1, 1, 1]] * 2, 0, "degree"),
+])
+def test_invalid_knots_rejected_on_host(lib, knots, p, why):
+    import paper_1712_00403_gb300 as pkg
+    d = _desc(pkg, knots, p)
+    h = ctypes.c_void_p()
+    code = lib.fdst_setup(ctypes.byref(d), ctypes.byref(h))
+    assert code == 1, why          # FDST_INVALID_ARGUMENT
+    assert h.value is None
+    assert len(lib.fdst_last_error()) > 0
+
+
+def test_bad_dim_and_null_arguments(lib):
+    import paper_1712_00403_gb300 as pkg
+    d = _desc(pkg, [[0, 0, 0, 1, 1, 1]] * 2, 2, dim=4)
+    h = ctypes.c_void_p()
+    assert lib.fdst_setup(ctypes.byref(d), ctypes.byref(h)) == 1
+    assert lib.fdst_setup(None, ctypes.byref(h)) == 1
+    assert lib.fdst_apply_prec(None, None, None, 1, None) == 1
+    assert lib.fdst_destroy(None) == 0

@@ -1,0 +1,129 @@
+"""CUDA path vs. the CPU FP64 oracle, through the C ABI.
+
+Bar (FP64 path): norm-wise relative difference <= 1e-12 for the FD
+preconditioner apply (Algorithm 1) and for the Kronecker Stokes matvec
+(Sec. 3); MINRES (Sec. 4, Sec. 7) reaches the same iteration count within
+one iteration and a true relative residual <= 1e-8.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import minres, stokes
+
+from _helpers import gpu_problem, oracle_problem, problem_spec, rel
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+CASES = [
+    problem_spec(2, 2, 16),            # 2D unit square, p=2, 16x16 (n_v = 32, n_q = 18)
+    problem_spec(2, 3, (5, 9)),        # 2D, unequal directions
+    problem_spec(3, 2, 4),             # 3D small cube
+    problem_spec(3, 3, (3, 4, 6)),     # 3D, three different sizes (index-order check)
+    problem_spec(3, 2, 9),             # 3D, rows span several tiles with a ragged tail
+    problem_spec(2, 2, 6, "RT"),       # 2D Raviart-Thomas with Nitsche terms
+    problem_spec(2, 4, (4, 7), "RT"),
+]
+
+
+def _ids(c):
+    return f"{c['disc']}-d{c['dim']}-p{c['p']}-{'x'.join(map(str, c['n_el']))}"
+
+
+@pytest.mark.parametrize("spec", CASES, ids=_ids)
+def test_fd_apply_f64_matches_oracle(spec):
+    P = gpu_problem(spec, max_rhs=3)
+    S = oracle_problem(spec)
+    assert P.block_sizes == S.block_sizes
+    R = np.stack([synth.random_vector(100 + j, P.n_total) for j in range(3)])
+    r = torch.tensor(R.reshape(-1), device="cuda")
+    s = torch.empty_like(r)
+    P.apply_prec(r, s)
+    out = s.cpu().numpy().reshape(3, -1)
+    for j in range(3):
+        ref = stokes.apply_PD_inv(S, R[j], "fd")
+        for b, (o0, o1) in enumerate(zip(P.block_offsets[:-1], P.block_offsets[1:])):
+            assert rel(out[j, o0:o1], ref[o0:o1]) <= 1e-12, (j, b)
+
+
+@pytest.mark.parametrize("spec", CASES, ids=_ids)
+def test_matvec_f64_matches_oracle(spec):
+    P = gpu_problem(spec, max_rhs=2, viscosity=1.0)
+    S = oracle_problem(spec)
+    X = np.stack([synth.random_vector(300 + j, P.n_total) for j in range(2)])
+    x = torch.tensor(X.reshape(-1), device="cuda")
+    y = torch.empty_like(x)
+    P.matvec(x, y)
+    out = y.cpu().numpy().reshape(2, -1)
+    for j in range(2):
+        ref = stokes.matvec(S, X[j])
+        for o0, o1 in zip(P.block_offsets[:-1], P.block_offsets[1:]):
+            assert rel(out[j, o0:o1], ref[o0:o1]) <= 1e-12
+
+
+def test_matvec_constant_pressure_kernel():
+    spec = problem_spec(3, 2, 5)
+    P = gpu_problem(spec)
+    x = torch.zeros(P.n_total, dtype=torch.float64, device="cuda")
+    x[P.block_offsets[-2]:] = 1.0
+    y = torch.empty_like(x)
+    P.matvec(x, y)
+    assert float(y.abs().max()) < 1e-12
+
+
+@pytest.mark.parametrize("spec", [problem_spec(2, 2, 16), problem_spec(3, 2, 4), problem_spec(2, 2, 8, "RT")],
+                         ids=_ids)
+def test_minres_f64_matches_oracle(spec):
+    P = gpu_problem(spec, max_rhs=2)
+    S = oracle_problem(spec)
+    B = np.stack([synth.rhs(1 + j, P.block_sizes) for j in range(2)])
+    b = torch.tensor(B.reshape(-1), device="cuda")
+    x = torch.zeros_like(b)
+    info = P.solve(b, x, tol=1e-8, maxit=500)
+    X = x.cpu().numpy().reshape(2, -1)
+    for j in range(2):
+        xo, io = minres.minres(lambda v: stokes.matvec(S, v), B[j], lambda v: stokes.apply_PD_inv(S, v),
+                               tol=1e-8, maxit=500)
+        assert info[j]["status"] == "OK"
+        assert abs(info[j]["iterations"] - io["iters"]) <= 1
+        assert info[j]["true_rel_res"] <= 1e-8
+        res = np.linalg.norm(B[j] - stokes.matvec(S, X[j])) / np.linalg.norm(B[j])
+        assert res <= 1e-8
+        assert abs(res - info[j]["true_rel_res"]) <= 1e-10
+
+
+def test_multi_rhs_equals_single():
+    spec = problem_spec(3, 2, 5)
+    P4 = gpu_problem(spec, max_rhs=4)
+    P1 = gpu_problem(spec, max_rhs=1)
+    B = np.stack([synth.rhs(40 + j, P4.block_sizes) for j in range(4)])
+    b = torch.tensor(B.reshape(-1), device="cuda")
+    x = torch.zeros_like(b)
+    info4 = P4.solve(b, x, tol=1e-8, maxit=300)
+    X4 = x.cpu().numpy().reshape(4, -1)
+    for j in range(4):
+        bj = torch.tensor(B[j], device="cuda")
+        xj = torch.zeros_like(bj)
+        info1 = P1.solve(bj, xj, tol=1e-8, maxit=300)
+        assert info1[0]["iterations"] == info4[j]["iterations"]
+        assert rel(X4[j], xj.cpu().numpy()) <= 1e-13
+
+
+def test_host_entry_points_match_device():
+    spec = problem_spec(2, 2, 8)
+    P = gpu_problem(spec)
+    bh = synth.rhs(5, P.block_sizes)
+    xh = np.zeros_like(bh)
+    info_h = P.solve_host(bh, xh, tol=1e-8, maxit=300)
+    b = torch.tensor(bh, device="cuda")
+    x = torch.zeros_like(b)
+    info_d = P.solve(b, x, tol=1e-8, maxit=300)
+    assert info_h[0]["iterations"] == info_d[0]["iterations"]
+    assert rel(xh, x.cpu().numpy()) <= 1e-14
+    sh = np.empty_like(bh)
+    P.apply_prec_host(bh, sh)
+    s = torch.empty_like(b)
+    P.apply_prec(b, s)
+    assert rel(sh, s.cpu().numpy()) <= 1e-15
