@@ -161,6 +161,11 @@ fdst_status fdst_get_timing(fdst_handle h, double *ms_matvec, double *ms_prec, d
  * (diagnostics: lets a caller count the kernels inside a timed region). */
 int64_t fdst_kernel_launches(void);
 
+/* *flag = 1 when a bounded device-side wait in a tensor-core kernel expired
+ * (the kernel then skipped its output and returned) since the library loaded;
+ * synchronizes the device. */
+fdst_status fdst_device_error(int *flag);
+
 /* Thread-local description of the last error on this thread. */
 const char *fdst_last_error(void);
 

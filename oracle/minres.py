@@ -4,7 +4,12 @@ Oracle: test infrastructure only.
 
 Lanczos in the P-inner product with the tridiagonal QR by Givens rotations;
 |eta| is the P^{-1}-norm of the current residual. Reading of the stopping
-rule (the paper gives only the tolerance): stop when |eta_j| / |eta_0| <= tol.
+rule (the paper gives only the tolerance 1e-8): the recurrence estimate
+|eta_j| / |eta_0| is compared with a threshold tau (initially tol); when it
+falls below, the true residual ||b - A x_j||_2 / ||b||_2 is computed in FP64
+and the solve ends if it is <= tol; otherwise tau <- 0.5 tau tol / true and
+the iteration continues with its recurrences intact (true_check=True).
+With true_check=False the estimate alone decides.
 
 Pins (tests/test_oracle_minres.py): solution vs. numpy.linalg.solve on
 random symmetric indefinite systems; |eta_j| equals the directly computed
@@ -17,7 +22,7 @@ import math
 import numpy as np
 
 
-def minres(A, b, Pinv, tol=1e-8, maxit=1000, x0=None, history=None):
+def minres(A, b, Pinv, tol=1e-8, maxit=1000, x0=None, history=None, true_check=False):
     """Returns (x, info) with info = dict(iters, status, eta_rel).
     A, Pinv: callables on 1-D float64 arrays. status: "converged", "maxit",
     "breakdown" (P not positive definite on the Krylov vector)."""
@@ -32,6 +37,8 @@ def minres(A, b, Pinv, tol=1e-8, maxit=1000, x0=None, history=None):
     if gamma == 0.0:
         return x, dict(iters=0, status="converged", eta_rel=0.0)
     eta0 = eta = gamma
+    tau = tol
+    bnorm = float(np.linalg.norm(b))
     v_old = np.zeros_like(b)
     w_old = np.zeros_like(b)
     w = np.zeros_like(b)
@@ -67,6 +74,11 @@ def minres(A, b, Pinv, tol=1e-8, maxit=1000, x0=None, history=None):
         gamma_old, gamma = gamma, gamma_new
         c_old, c = c, c_new
         s_old, s = s, s_new
-        if abs(eta) / eta0 <= tol or gamma_new == 0.0:
-            return x, dict(iters=j, status="converged", eta_rel=abs(eta) / eta0)
+        if abs(eta) / eta0 <= tau or gamma_new == 0.0:
+            if not true_check or gamma_new == 0.0:
+                return x, dict(iters=j, status="converged", eta_rel=abs(eta) / eta0)
+            true = float(np.linalg.norm(b - A(x))) / (bnorm if bnorm > 0 else 1.0)
+            if true <= tol:
+                return x, dict(iters=j, status="converged", eta_rel=abs(eta) / eta0, true_rel=true)
+            tau = 0.5 * tau * tol / true
     return x, dict(iters=maxit, status="maxit", eta_rel=abs(eta) / eta0)

@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "libfdst.so")
 
 TH, RT = 0, 1
 FD_F64, FD_TF32X3, FD_BF16X6 = 0, 1, 2
+HAS_TC = True        # the split-TF32 tcgen05 FD contraction is built (sm_103a)
 GEOM_IDENTITY, GEOM_SINE_BUMP = 0, 1
 VARIANT_PD, VARIANT_PD_GEO = 0, 1
 
@@ -51,7 +52,7 @@ class SolveInfo(ctypes.Structure):
 
 ENTRY_POINTS = ["fdst_setup", "fdst_destroy", "fdst_get_sizes", "fdst_apply_prec", "fdst_matvec", "fdst_solve",
                 "fdst_solve_host", "fdst_apply_prec_host", "fdst_set_timing", "fdst_get_timing",
-                "fdst_kernel_launches", "fdst_last_error"]
+                "fdst_device_error", "fdst_kernel_launches", "fdst_last_error"]
 
 _lib = None
 
@@ -74,6 +75,7 @@ def load_library(path=LIB_PATH):
     lib.fdst_solve_host.argtypes = [vp, vp, vp, i, d, i, ctypes.POINTER(SolveInfo), vp]
     lib.fdst_apply_prec_host.argtypes = [vp, vp, vp, i, vp]
     lib.fdst_set_timing.argtypes = [vp, i]
+    lib.fdst_device_error.argtypes = [ctypes.POINTER(i)]
     lib.fdst_get_timing.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d),
                                     ctypes.POINTER(i64), ctypes.POINTER(i64)]
     lib.fdst_last_error.restype = ctypes.c_char_p
@@ -88,6 +90,13 @@ def load_library(path=LIB_PATH):
 def kernel_launches():
     """Kernels launched by the library so far in this process."""
     return int(load_library().fdst_kernel_launches())
+
+
+def device_error():
+    """1 when a bounded device-side wait in a tensor-core kernel expired."""
+    f = ctypes.c_int()
+    _check(load_library().fdst_device_error(ctypes.byref(f)))
+    return f.value
 
 
 def _check(code):

@@ -39,6 +39,7 @@ struct FdChain {
   int div_step = -1;
   const double *B[6] = {};
   const float *Bt[6] = {};     // split-TF32 operand of the same step (pre-split, padded)
+  std::vector<double> Bh[6];   // host copy of B (K x N row-major) for the packing
   int R[6] = {}, K[6] = {}, N[6] = {};
   double *lam_row = nullptr, *lam_col = nullptr;
   float *lam_row_f = nullptr, *lam_col_f = nullptr;
@@ -234,6 +235,7 @@ static fdst_status build_fd(fdst_ctx *h) {
     c.size = h->off[k + 1] - h->off[k];
     std::vector<double> lam[3];
     const double *Uf[3], *Ub[3];
+    std::vector<double> Ufh[3], Ubh[3];
     for (int e = 0; e < dim; ++e) {
       const Space1D &s = h->vel[k][e];
       std::string key = space_key(s);
@@ -249,8 +251,11 @@ static fdst_status build_fd(fdst_ctx *h) {
         it = eig_cache.emplace(key, std::make_pair(l, U)).first;
       }
       lam[e] = it->second.first;
+      Mat Ut = transpose(it->second.second);
       TRY(dev_mat("U" + key, it->second.second, &Uf[e]));
-      TRY(dev_mat("Ut" + key, transpose(it->second.second), &Ub[e]));
+      TRY(dev_mat("Ut" + key, Ut, &Ub[e]));
+      Ufh[e] = it->second.second.a;
+      Ubh[e] = Ut.a;
     }
     const int n1 = h->shape[k][0], n2 = h->shape[k][1], n3 = h->shape[k][2];
     double cf[3];
@@ -264,6 +269,7 @@ static fdst_status build_fd(fdst_ctx *h) {
         c.R[j] = Rs[j];
         c.K[j] = c.N[j] = Ns[j];
         c.B[j] = j < 3 ? Uf[j] : Ub[j - 3];
+        c.Bh[j] = j < 3 ? Ufh[j] : Ubh[j - 3];
       }
       c.div_step = 2;
       lr.resize((size_t)n1 * n2);
@@ -279,6 +285,7 @@ static fdst_status build_fd(fdst_ctx *h) {
         c.R[j] = Rs[j];
         c.K[j] = c.N[j] = Ns[j];
         c.B[j] = j < 2 ? Uf[j] : Ub[j - 2];
+        c.Bh[j] = j < 2 ? Ufh[j] : Ubh[j - 2];
       }
       c.div_step = 1;
       lr.resize(n1);
@@ -299,6 +306,7 @@ static fdst_status build_fd(fdst_ctx *h) {
     c.off = h->off[dim];
     c.size = h->off[dim + 1] - h->off[dim];
     const double *W[3];
+    std::vector<double> Wh[3];
     for (int e = 0; e < dim; ++e) {
       Mat M = mixed_matrix(h->pres[e], 0, h->pres[e], 0, npts), Mi;
       if (!spd_inverse(M, Mi)) {
@@ -306,18 +314,19 @@ static fdst_status build_fd(fdst_ctx *h) {
         return FDST_NOT_SPD;
       }
       TRY(dev_mat("W" + space_key(h->pres[e]), Mi, &W[e]));
+      Wh[e] = Mi.a;
     }
     const int n1 = h->shape[dim][0], n2 = h->shape[dim][1], n3 = h->shape[dim][2];
     if (dim == 3) {
       c.nsteps = 3;
       int Rs[3] = {n2 * n3, n1 * n3, n1 * n2};
       int Ns[3] = {n1, n2, n3};
-      for (int j = 0; j < 3; ++j) { c.R[j] = Rs[j]; c.K[j] = c.N[j] = Ns[j]; c.B[j] = W[j]; }
+      for (int j = 0; j < 3; ++j) { c.R[j] = Rs[j]; c.K[j] = c.N[j] = Ns[j]; c.B[j] = W[j]; c.Bh[j] = Wh[j]; }
     } else {
       c.nsteps = 2;
       int Rs[2] = {n2, n1};
       int Ns[2] = {n1, n2};
-      for (int j = 0; j < 2; ++j) { c.R[j] = Rs[j]; c.K[j] = c.N[j] = Ns[j]; c.B[j] = W[j]; }
+      for (int j = 0; j < 2; ++j) { c.R[j] = Rs[j]; c.K[j] = c.N[j] = Ns[j]; c.B[j] = W[j]; c.Bh[j] = Wh[j]; }
     }
     h->chains.push_back(c);
   }
@@ -488,9 +497,25 @@ static fdst_status build_matvec(fdst_ctx *h) {
 
 // ------------------------------------------------------------------ split-TF32 operands
 
-static fdst_status tc_prepare(fdst_ctx *) {
-  set_error("split-TF32 FD contraction not built");
-  return FDST_NOT_SUPPORTED;
+// Packs every FD step's factor into the tensor-core operand image (TF32
+// hi/lo split, swizzled per stage) and allocates the FP32 intermediates.
+static fdst_status tc_prepare(fdst_ctx *h) {
+  std::map<const double *, const float *> cache;
+  for (auto &c : h->chains)
+    for (int j = 0; j < c.nsteps; ++j) {
+      auto it = cache.find(c.B[j]);
+      if (it != cache.end()) { c.Bt[j] = it->second; continue; }
+      std::vector<float> packed;
+      tc_pack(c.Bh[j].data(), c.K[j], c.N[j], packed);
+      float *d = nullptr;
+      TRY(upload(h, &d, packed));
+      c.Bt[j] = d;
+      cache[c.B[j]] = d;
+    }
+  const size_t nv = (size_t)h->n_total * h->max_rhs;
+  TRY(dalloc(h, &h->work_f[0], nv));
+  TRY(dalloc(h, &h->work_f[1], nv));
+  return FDST_OK;
 }
 
 // ------------------------------------------------------------------ execution
@@ -580,6 +605,11 @@ extern "C" {
 const char *fdst_last_error(void) { return g_err.c_str(); }
 
 int64_t fdst_kernel_launches(void) { return (int64_t)launch_count(); }
+
+fdst_status fdst_device_error(int *flag) {
+  if (!flag) { set_error("NULL argument"); return FDST_INVALID_ARGUMENT; }
+  return tc_error_flag(flag);
+}
 
 fdst_status fdst_destroy(fdst_handle h) {
   if (!h) return FDST_OK;
@@ -748,13 +778,32 @@ fdst_status fdst_solve(fdst_handle h, const double *d_b, double *d_x, int nrhs, 
   CK(cudaMemsetAsync(h->w_old, 0, sizeof(double) * n * nrhs, st));
   TRY(run_apply(h, h->v, h->z, nrhs, nullptr, st));
   launch_dot(h->v, h->z, n, n, nrhs, h->partials, h->counters, h->dots, nullptr, st);
-  launch_minres_init(h->state, h->dots, h->done, nrhs, h->n_stopped, st);
+  launch_minres_init(h->state, h->dots, h->done, nrhs, h->n_stopped, tol, st);
   launch_scale_by_inv_gamma(h->z, h->state, n, n, nrhs, h->done, st);
   double *v = h->v, *v_old = h->v_old, *w = h->w, *w_old = h->w_old;
   double *delta = h->dots + nrhs, *g2 = h->dots + 2 * nrhs;
+  // ||b||_2^2 once (dots[3 nrhs ..])
+  launch_dot(d_b, d_b, n, n, nrhs, h->partials, h->counters, h->dots + 3 * nrhs, nullptr, st);
+  std::vector<double> bb(nrhs), true_rel(nrhs, -1.0);
+  CK(cudaMemcpyAsync(h->h_dots, h->dots + 3 * nrhs, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int j = 0; j < nrhs; ++j) bb[j] = h->h_dots[j];
+  // true relative residual ||b - A x||_2 / ||b||_2 in FP64 (Az is free between iterations)
+  auto true_residuals = [&]() -> fdst_status {
+    TRY(run_matvec(h, d_x, h->Az, nrhs, nullptr, st));
+    launch_axpby(d_b, h->Az, 1.0, -1.0, n, n, nrhs, st);
+    launch_dot(h->Az, h->Az, n, n, nrhs, h->partials, h->counters, h->dots, nullptr, st);
+    CK(cudaMemcpyAsync(h->h_dots, h->dots, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int j = 0; j < nrhs; ++j) true_rel[j] = bb[j] > 0 ? std::sqrt(h->h_dots[j] / bb[j]) : std::sqrt(h->h_dots[j]);
+    return FDST_OK;
+  };
+  std::vector<MinresState> hs(nrhs);
   const int check_every = 4;
   int it = 0;
+  bool residuals_current = false;
   while (it < maxit) {
+    residuals_current = false;
     size_t e0 = 0;
     if (h->timing) { mark(); e0 = ev.size() - 1; }
     TRY(run_matvec(h, h->z, h->Az, nrhs, h->done, st));
@@ -768,7 +817,7 @@ fdst_status fdst_solve(fdst_handle h, const double *d_b, double *d_x, int nrhs, 
     size_t e3 = 0;
     if (h->timing) { mark(); e3 = ev.size() - 1; spans.push_back({1, e2, e3}); }
     launch_dot(v_old, h->z_new, n, n, nrhs, h->partials, h->counters, g2, h->done, st);
-    launch_minres_scalars(h->state, delta, g2, nrhs, tol, maxit, h->done, h->n_stopped, st);
+    launch_minres_scalars(h->state, delta, g2, nrhs, maxit, h->done, h->n_stopped, st);
     launch_minres_update(w_old, w, d_x, h->z, h->z_new, h->state, n, n, nrhs, h->done, st);
     launch_minres_commit(h->state, h->done, nrhs, st);
     if (h->timing) { mark(); spans.push_back({2, e3, ev.size() - 1}); }
@@ -780,18 +829,32 @@ fdst_status fdst_solve(fdst_handle h, const double *d_b, double *d_x, int nrhs, 
     if (it % check_every == 0 || it == maxit) {
       CK(cudaMemcpyAsync(h->h_n_stopped, h->n_stopped, sizeof(int), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
-      if (*h->h_n_stopped >= nrhs) break;
+      if (*h->h_n_stopped >= nrhs) {
+        // every right-hand side met its estimate threshold: check the true residual and
+        // resume the ones above tol with a tighter threshold (recurrences intact)
+        TRY(true_residuals());
+        residuals_current = true;
+        CK(cudaMemcpy(hs.data(), h->state, sizeof(MinresState) * nrhs, cudaMemcpyDeviceToHost));
+        std::vector<int> resume;
+        for (int j = 0; j < nrhs; ++j)
+          if (hs[j].status == 0 && hs[j].stop && hs[j].gamma > 0.0 && true_rel[j] > tol && hs[j].iters < maxit)
+            resume.push_back(j);
+        if (resume.empty()) break;
+        std::vector<int> hd(nrhs, 1);
+        for (int j : resume) {
+          hs[j].tau = 0.5 * hs[j].tau * tol / true_rel[j];
+          hs[j].stop = 0;
+          hd[j] = 0;
+        }
+        int ns = nrhs - (int)resume.size();
+        CK(cudaMemcpy(h->state, hs.data(), sizeof(MinresState) * nrhs, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(h->done, hd.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(h->n_stopped, &ns, sizeof(int), cudaMemcpyHostToDevice));
+      }
     }
   }
   CK(cudaGetLastError());
-  // ---- true residual ||b - A x|| / ||b|| in FP64
-  TRY(run_matvec(h, d_x, h->Az, nrhs, nullptr, st));
-  launch_axpby(d_b, h->v, 1.0, 0.0, n, n, nrhs, st);
-  launch_axpby(h->Az, h->v, -1.0, 1.0, n, n, nrhs, st);
-  launch_dot(h->v, h->v, n, n, nrhs, h->partials, h->counters, h->dots, nullptr, st);
-  launch_dot(d_b, d_b, n, n, nrhs, h->partials, h->counters, h->dots + nrhs, nullptr, st);
-  std::vector<MinresState> hs(nrhs);
-  CK(cudaMemcpyAsync(h->h_dots, h->dots, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost, st));
+  if (!residuals_current) TRY(true_residuals());
   CK(cudaMemcpyAsync(hs.data(), h->state, sizeof(MinresState) * nrhs, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   if (h->timing) {
@@ -808,8 +871,7 @@ fdst_status fdst_solve(fdst_handle h, const double *d_b, double *d_x, int nrhs, 
     info[j].status = hs[j].stop || hs[j].status ? hs[j].status : FDST_MAXIT;
     if (hs[j].eta0 == 0.0 && hs[j].status == 0) info[j].status = FDST_OK;
     info[j].eta_rel = hs[j].eta0 > 0 ? std::fabs(hs[j].eta) / hs[j].eta0 : 0.0;
-    double bb = h->h_dots[nrhs + j];
-    info[j].true_rel_res = bb > 0 ? std::sqrt(h->h_dots[j] / bb) : std::sqrt(h->h_dots[j]);
+    info[j].true_rel_res = true_rel[j];
     if (ret == FDST_OK && info[j].status != FDST_OK) ret = (fdst_status)info[j].status;
   }
   return ret;

@@ -245,10 +245,11 @@ void launch_axpby(const double *x, double *y, double alpha, double beta, int64_t
 
 // ------------------------------------------------------------------ MINRES
 
-__global__ void k_minres_init(MinresState *st, const double *g, int *done, int nrhs, int *n_stopped) {
+__global__ void k_minres_init(MinresState *st, const double *g, int *done, int nrhs, int *n_stopped, double tol) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nrhs) return;
   MinresState S = {};
+  S.tau = tol;
   double g2 = g[j];
   S.iters = 0;
   S.status = 0;
@@ -271,9 +272,10 @@ __global__ void k_minres_init(MinresState *st, const double *g, int *done, int n
   st[j] = S;
 }
 
-void launch_minres_init(MinresState *st, const double *g, int *done, int nrhs, int *n_stopped, cudaStream_t s) {
+void launch_minres_init(MinresState *st, const double *g, int *done, int nrhs, int *n_stopped, double tol,
+                        cudaStream_t s) {
   count_launch(1);
-  k_minres_init<<<(nrhs + 63) / 64, 64, 0, s>>>(st, g, done, nrhs, n_stopped);
+  k_minres_init<<<(nrhs + 63) / 64, 64, 0, s>>>(st, g, done, nrhs, n_stopped, tol);
 }
 
 __global__ void k_scale_inv_gamma(double *z, const MinresState *st, int64_t n, int64_t stride, const int *done) {
@@ -318,8 +320,8 @@ void launch_minres_lanczos(const double *Az, const double *v, double *v_old, con
 
 // One thread per right-hand side: Givens QR update of the Lanczos tridiagonal
 // matrix and the residual estimate eta (the QR recurrences of MINRES).
-__global__ void k_minres_scalars(MinresState *st, const double *delta, const double *g2v, int nrhs, double tol,
-                                 int maxit, const int *done, int *n_stopped) {
+__global__ void k_minres_scalars(MinresState *st, const double *delta, const double *g2v, int nrhs, int maxit,
+                                 const int *done, int *n_stopped) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nrhs || done[j]) return;
   MinresState S = st[j];
@@ -354,16 +356,16 @@ __global__ void k_minres_scalars(MinresState *st, const double *delta, const dou
   S.s = sn;
   const double rel = fabs(S.eta) / S.eta0;
   if (breakdown) { S.status = 7; S.stop = 1; }
-  else if (rel <= tol || gn == 0.0) { S.status = 0; S.stop = 1; }
+  else if (rel <= S.tau || gn == 0.0) { S.status = 0; S.stop = 1; }
   else if (S.iters >= maxit) { S.status = 5; S.stop = 1; }
   if (S.stop) atomicAdd(n_stopped, 1);
   st[j] = S;
 }
 
-void launch_minres_scalars(MinresState *st, const double *delta, const double *g2, int nrhs, double tol,
-                           int maxit, const int *done, int *n_stopped, cudaStream_t s) {
+void launch_minres_scalars(MinresState *st, const double *delta, const double *g2, int nrhs, int maxit,
+                           const int *done, int *n_stopped, cudaStream_t s) {
   count_launch(1);
-  k_minres_scalars<<<(nrhs + 63) / 64, 64, 0, s>>>(st, delta, g2, nrhs, tol, maxit, done, n_stopped);
+  k_minres_scalars<<<(nrhs + 63) / 64, 64, 0, s>>>(st, delta, g2, nrhs, maxit, done, n_stopped);
 }
 
 __global__ void k_minres_update(double *w_old, const double *w, double *x, double *z, const double *z_new,

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <vector>
 
 #include "../../include/fdst.h"
 
@@ -27,5 +28,12 @@ struct TcGroup {
   int nprob = 0;
 };
 fdst_status launch_gemm_tc(const TcGroup &g, int nrhs, const int *done, cudaStream_t s);
+
+// Host packing of B (K x N row-major FP64) into the kernel's per-stage
+// shared-memory image (TF32 hi/lo, SWIZZLE_32B K-major); size in floats.
+size_t tc_packed_floats(int K, int N);
+void tc_pack(const double *B, int K, int N, std::vector<float> &out);
+// 1 when a bounded wait inside the tensor-core kernel expired since start.
+fdst_status tc_error_flag(int *value);
 
 }  // namespace fdst

@@ -85,7 +85,7 @@ def test_minres_f64_matches_oracle(spec):
     X = x.cpu().numpy().reshape(2, -1)
     for j in range(2):
         xo, io = minres.minres(lambda v: stokes.matvec(S, v), B[j], lambda v: stokes.apply_PD_inv(S, v),
-                               tol=1e-8, maxit=500)
+                               tol=1e-8, maxit=500, true_check=True)
         assert info[j]["status"] == "OK"
         assert abs(info[j]["iterations"] - io["iters"]) <= 1
         assert info[j]["true_rel_res"] <= 1e-8

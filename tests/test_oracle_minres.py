@@ -64,3 +64,16 @@ def test_stokes_pd_minres_small():
     PQ = kron.kron_matrix(stokes.pq_factors(S))
     pr = x[-S.block_sizes[-1]:]
     assert abs(np.ones(len(pr)) @ PQ @ pr) < 1e-9 * np.linalg.norm(pr)
+
+
+def test_true_residual_check_reaches_tolerance():
+    """With true_check the returned iterate meets ||b - A x||_2 <= tol ||b||_2
+    (the estimate-only rule can stop above it)."""
+    S = stokes.build_uniform(8, 2, 2)
+    A = stokes.assembled(S)
+    b = synth.rhs(3, S.block_sizes)
+    Pinv = lambda v: stokes.apply_PD_inv(S, v)
+    x1, i1 = minres.minres(lambda v: A @ v, b, Pinv, tol=1e-8, maxit=500)
+    x2, i2 = minres.minres(lambda v: A @ v, b, Pinv, tol=1e-8, maxit=500, true_check=True)
+    assert i2["iters"] >= i1["iters"]
+    assert np.linalg.norm(b - A @ x2) / np.linalg.norm(b) <= 1e-8
