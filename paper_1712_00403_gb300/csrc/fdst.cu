@@ -813,16 +813,14 @@ fdst_status fdst_solve(fdst_handle h, const double *d_b, double *d_x, int nrhs, 
     launch_minres_lanczos(h->Az, v, v_old, h->state, delta, n, n, nrhs, h->done, st);
     size_t e2 = 0;
     if (h->timing) { mark(); e2 = ev.size() - 1; spans.push_back({2, e1, e2}); }
-    TRY(run_apply(h, v_old, h->z_new, nrhs, h->done, st));
+    TRY(run_apply(h, v, h->z_new, nrhs, h->done, st));
     size_t e3 = 0;
     if (h->timing) { mark(); e3 = ev.size() - 1; spans.push_back({1, e2, e3}); }
-    launch_dot(v_old, h->z_new, n, n, nrhs, h->partials, h->counters, g2, h->done, st);
+    launch_dot(v, h->z_new, n, n, nrhs, h->partials, h->counters, g2, h->done, st);
     launch_minres_scalars(h->state, delta, g2, nrhs, maxit, h->done, h->n_stopped, st);
     launch_minres_update(w_old, w, d_x, h->z, h->z_new, h->state, n, n, nrhs, h->done, st);
     launch_minres_commit(h->state, h->done, nrhs, st);
     if (h->timing) { mark(); spans.push_back({2, e3, ev.size() - 1}); }
-    std::swap(v, v_old);
-    std::swap(w, w_old);
     ++it;
     h->n_matvec += 1;
     h->n_prec += 1;

@@ -73,16 +73,16 @@ void launch_axpby(const double *x, double *y, double alpha, double beta, int64_t
 // MINRES init after v = b - A x0, z_new = P^{-1} v and dot g = <v, z_new>.
 void launch_minres_init(MinresState *st, const double *g, int *done, int nrhs, int *n_stopped, double tol,
                         cudaStream_t s);
-// v_old <- Az - (delta/gamma) v - (gamma/gamma_old) v_old (delta = <Az, z>, in st).
-void launch_minres_lanczos(const double *Az, const double *v, double *v_old, const MinresState *st,
+// t = Az - (delta/gamma) v - (gamma/gamma_old) v_old; v_old <- v; v <- t (delta = <Az, z>).
+void launch_minres_lanczos(const double *Az, double *v, double *v_old, const MinresState *st,
                            const double *delta, int64_t n, int64_t stride, int nrhs, const int *done,
                            cudaStream_t s);
 // scalar QR update from gamma_new^2 = <v_new, z_new> (one thread per right-hand side).
 // The estimate |eta|/eta0 is compared with the per-right-hand-side threshold st.tau.
 void launch_minres_scalars(MinresState *st, const double *delta, const double *g2, int nrhs, int maxit,
                            const int *done, int *n_stopped, cudaStream_t s);
-// w_old <- (z - a3 w_old - a2 w)/a1; x += coef_x w_old; z <- z_new / gamma_new; then done |= stop.
-void launch_minres_update(double *w_old, const double *w, double *x, double *z, const double *z_new,
+// w_new = (z - a3 w_old - a2 w)/a1; w_old <- w; w <- w_new; x += coef_x w_new; z <- z_new / gamma_new.
+void launch_minres_update(double *w_old, double *w, double *x, double *z, const double *z_new,
                           MinresState *st, int64_t n, int64_t stride, int nrhs, int *done, cudaStream_t s);
 void launch_minres_commit(MinresState *st, int *done, int nrhs, cudaStream_t s);
 // z <- z / gamma (per right-hand side) used at start.

@@ -296,19 +296,25 @@ void launch_scale_by_inv_gamma(double *z, const MinresState *st, int64_t n, int6
   k_scale_inv_gamma<<<dim3((unsigned)blocks, nrhs), 256, 0, s>>>(z, st, n, stride, done);
 }
 
-__global__ void k_minres_lanczos(const double *Az, const double *v, double *v_old, const MinresState *st,
+// Lanczos step in place, per right-hand side: t = Az - (delta/gamma) v - (gamma/gamma_old) v_old,
+// then v_old <- v, v <- t (no buffer-role swaps: frozen right-hand sides keep their state).
+__global__ void k_minres_lanczos(const double *Az, double *v, double *v_old, const MinresState *st,
                                  const double *delta, int64_t n, int64_t stride, const int *done) {
   const int j = blockIdx.y;
   if (done[j]) return;
   const double gamma = st[j].gamma, gamma_old = st[j].gamma_old;
   const double f1 = delta[j] / gamma, f2 = gamma / gamma_old;
-  const double *a = Az + j * stride, *vv = v + j * stride;
-  double *vo = v_old + j * stride;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    vo[i] = a[i] - f1 * vv[i] - f2 * vo[i];
+  const double *a = Az + j * stride;
+  double *vv = v + j * stride, *vo = v_old + j * stride;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double vi = vv[i];
+    const double t = a[i] - f1 * vi - f2 * vo[i];
+    vo[i] = vi;
+    vv[i] = t;
+  }
 }
 
-void launch_minres_lanczos(const double *Az, const double *v, double *v_old, const MinresState *st,
+void launch_minres_lanczos(const double *Az, double *v, double *v_old, const MinresState *st,
                            const double *delta, int64_t n, int64_t stride, int nrhs, const int *done,
                            cudaStream_t s) {
   int64_t blocks = (n + 255) / 256;
@@ -368,23 +374,27 @@ void launch_minres_scalars(MinresState *st, const double *delta, const double *g
   k_minres_scalars<<<(nrhs + 63) / 64, 64, 0, s>>>(st, delta, g2, nrhs, maxit, done, n_stopped);
 }
 
-__global__ void k_minres_update(double *w_old, const double *w, double *x, double *z, const double *z_new,
+// w_new = (z - a3 w_old - a2 w)/a1; w_old <- w; w <- w_new; x += coef_x w_new;
+// z <- z_new / gamma_new (the next normalized Lanczos vector), all in place.
+__global__ void k_minres_update(double *w_old, double *w, double *x, double *z, const double *z_new,
                                 const MinresState *st, int64_t n, int64_t stride, const int *done) {
   const int j = blockIdx.y;
   if (done[j]) return;
   const MinresState &S = st[j];
   const double ia1 = S.inv_a1, a2 = S.a2, a3 = S.a3, cx = S.coef_x, ig = S.inv_gamma_new;
-  double *wo = w_old + j * stride, *xx = x + j * stride, *zz = z + j * stride;
-  const double *ww = w + j * stride, *zn = z_new + j * stride;
+  double *wo = w_old + j * stride, *ww = w + j * stride, *xx = x + j * stride, *zz = z + j * stride;
+  const double *zn = z_new + j * stride;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double wn = (zz[i] - a3 * wo[i] - a2 * ww[i]) * ia1;
-    wo[i] = wn;
+    const double wi = ww[i];
+    const double wn = (zz[i] - a3 * wo[i] - a2 * wi) * ia1;
+    wo[i] = wi;
+    ww[i] = wn;
     xx[i] = fma(cx, wn, xx[i]);
     zz[i] = zn[i] * ig;
   }
 }
 
-void launch_minres_update(double *w_old, const double *w, double *x, double *z, const double *z_new,
+void launch_minres_update(double *w_old, double *w, double *x, double *z, const double *z_new,
                           MinresState *st, int64_t n, int64_t stride, int nrhs, int *done, cudaStream_t s) {
   int64_t blocks = (n + 255) / 256;
   if (blocks > 4096) blocks = 4096;
