@@ -157,6 +157,36 @@ fdst_status fdst_set_timing(fdst_handle h, int on);
 fdst_status fdst_get_timing(fdst_handle h, double *ms_matvec, double *ms_prec, double *ms_vector,
                             int64_t *n_matvec, int64_t *n_prec);
 
+/*
+ * fdst_fd_apply_static - allocation-free FD solve of one Kronecker-sum block:
+ *   s = (U_d x ... x U_1) Delta^{-1} (U_d x ... x U_1)^T r,
+ *   Delta[i1, i2, (i3)] = sum_d coef[d] * lam_d[i_d],
+ * i.e. the solution of sum_d coef[d] (x)_e (K_e if e == d else M_e) s = r for
+ * pencils K_d U_d = M_d U_d diag(lam_d), U_d^T M_d U_d = I. The paper has no
+ * counterpart of this entry point: it exists for callers that cannot call
+ * cudaMalloc (code inside another framework's memory pool or allocator lock,
+ * hosts that forbid device allocation after start-up, call sites that must
+ * not trigger an allocation). It needs no handle and allocates nothing.
+ *   dim: 2 or 3; n[d]: univariate sizes, 1 <= n[d] <= 256, prod n[d] <= 2359296
+ *   (larger sizes return FDST_INVALID_ARGUMENT with a message);
+ *   d_U[d]: device, n[d] x n[d] row-major eigenvector matrix U_d (U[i][a] =
+ *   component i of eigenvector a); d_lam[d]: device, n[d] eigenvalues;
+ *   coef: host, dim coefficients; d_r, d_s: device, prod n[d] doubles each,
+ *   vec-ordered with i1 fastest, not aliased. d_s is also used as
+ *   intermediate storage during the call. Asynchronous on `stream`.
+ * Scratch: one file-scope __device__ array of 2359296 + 4*256*256 + 256
+ * doubles (about 21 MB) that every GPU which loads the library holds until
+ * the process exits. All calls on a device share it and it keeps the last
+ * call's contents (every call overwrites what it reads), so calls whose
+ * device work overlaps in time (different streams, threads or processes
+ * sharing the context) race and must be serialized by the caller.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.
+ */
+fdst_status fdst_fd_apply_static(int dim, const int n[3], const double *const d_U[3], const double *const d_lam[3],
+                                 const double coef[3], const double *d_r, double *d_s, fdst_stream stream);
+
 /* Number of CUDA kernels this library has launched in the process so far
  * (diagnostics: lets a caller count the kernels inside a timed region). */
 int64_t fdst_kernel_launches(void);

@@ -52,7 +52,7 @@ class SolveInfo(ctypes.Structure):
 
 ENTRY_POINTS = ["fdst_setup", "fdst_destroy", "fdst_get_sizes", "fdst_apply_prec", "fdst_matvec", "fdst_solve",
                 "fdst_solve_host", "fdst_apply_prec_host", "fdst_set_timing", "fdst_get_timing",
-                "fdst_device_error", "fdst_kernel_launches", "fdst_last_error"]
+                "fdst_fd_apply_static", "fdst_device_error", "fdst_kernel_launches", "fdst_last_error"]
 
 _lib = None
 
@@ -76,6 +76,8 @@ def load_library(path=LIB_PATH):
     lib.fdst_apply_prec_host.argtypes = [vp, vp, vp, i, vp]
     lib.fdst_set_timing.argtypes = [vp, i]
     lib.fdst_device_error.argtypes = [ctypes.POINTER(i)]
+    lib.fdst_fd_apply_static.argtypes = [i, ctypes.POINTER(i), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                         ctypes.POINTER(d), vp, vp, vp]
     lib.fdst_get_timing.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d),
                                     ctypes.POINTER(i64), ctypes.POINTER(i64)]
     lib.fdst_last_error.restype = ctypes.c_char_p
@@ -90,6 +92,24 @@ def load_library(path=LIB_PATH):
 def kernel_launches():
     """Kernels launched by the library so far in this process."""
     return int(load_library().fdst_kernel_launches())
+
+
+def fd_apply_static(U, lam, coef, r, s, stream=None):
+    """Allocation-free FD solve of one Kronecker-sum block (fdst_fd_apply_static).
+
+    U, lam: lists (one per direction, 2 or 3) of CUDA float64 tensors holding
+    U_d (n_d x n_d, row-major) and lam_d; coef: per-direction coefficients;
+    r, s: CUDA float64 vectors of prod(n_d) entries (i1 fastest). For callers
+    that cannot allocate device memory; see include/fdst.h for the scratch
+    limits and the rule that overlapping calls race.
+    """
+    lib = load_library()
+    dim = len(U)
+    n = (ctypes.c_int * 3)(*[int(u.shape[0]) for u in U], *([1] * (3 - dim)))
+    up = (ctypes.c_void_p * 3)(*[_dptr(u).value for u in U], *([None] * (3 - dim)))
+    lp = (ctypes.c_void_p * 3)(*[_dptr(l).value for l in lam], *([None] * (3 - dim)))
+    cf = (ctypes.c_double * 3)(*[float(c) for c in coef], *([0.0] * (3 - dim)))
+    _check(lib.fdst_fd_apply_static(dim, n, up, lp, cf, _dptr(r), _dptr(s), _stream_ptr(stream)))
 
 
 def device_error():
