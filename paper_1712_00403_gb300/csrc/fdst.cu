@@ -83,6 +83,8 @@ struct fdst_ctx {
   std::vector<fdst::FdChain> chains;
   double *work[2] = {nullptr, nullptr};
   float *work_f[2] = {nullptr, nullptr};
+  std::vector<int64_t> f_off;   // per-chain offset in the padded FP32 workspace
+  int64_t f_total = 0;          // padded FP32 workspace per right-hand side
   // matvec
   std::vector<fdst::BandDev> bands;
   std::vector<fdst::PlanOp> plan;
@@ -512,7 +514,20 @@ static fdst_status tc_prepare(fdst_ctx *h) {
       c.Bt[j] = d;
       cache[c.B[j]] = d;
     }
-  const size_t nv = (size_t)h->n_total * h->max_rhs;
+  // padded FP32 intermediates: step j's output rows hold the next contracted
+  // index, padded to a multiple of 4 floats (16-byte vector loads)
+  h->f_off.clear();
+  h->f_total = 0;
+  for (auto &c : h->chains) {
+    int64_t fsize = 0;
+    for (int j = 0; j + 1 < c.nsteps; ++j) {
+      const int64_t nv = c.K[j + 1], ld = (nv + 3) & ~3;
+      fsize = std::max(fsize, ((int64_t)c.R[j] * c.N[j] / nv) * ld);
+    }
+    h->f_off.push_back(h->f_total);
+    h->f_total += (fsize + 63) & ~(int64_t)63;
+  }
+  const size_t nv = (size_t)h->f_total * h->max_rhs;
   TRY(dalloc(h, &h->work_f[0], nv));
   TRY(dalloc(h, &h->work_f[1], nv));
   return FDST_OK;
@@ -527,16 +542,31 @@ static fdst_status run_apply(fdst_ctx *h, const double *r, double *s, int nrhs, 
   for (int j = 0; j < maxsteps; ++j) {
     if (tc) {
       TcGroup g;
-      for (auto &c : h->chains) {
+      for (size_t ci = 0; ci < h->chains.size(); ++ci) {
+        const FdChain &c = h->chains[ci];
         if (j >= c.nsteps) continue;
         TcProb &P = g.p[g.nprob++];
         const bool first = j == 0, last = j == c.nsteps - 1;
-        P.A64 = first ? r + c.off : nullptr;
-        P.A32 = first ? nullptr : h->work_f[(j - 1) % 2] + c.off;
-        P.C64 = last ? s + c.off : nullptr;
-        P.C32 = last ? nullptr : h->work_f[j % 2] + c.off;
+        if (first) {
+          P.A64 = r + c.off;
+          P.a_rhs_stride = h->n_total;
+          P.lda = c.K[j];
+        } else {
+          P.A32 = h->work_f[(j - 1) % 2] + h->f_off[ci];
+          P.a_rhs_stride = h->f_total;
+          P.lda = (c.K[j] + 3) & ~3;
+        }
+        if (last) {
+          P.C64 = s + c.off;
+          P.c_rhs_stride = h->n_total;
+          P.out_nv = P.ldc = c.R[j];
+        } else {
+          P.C32 = h->work_f[j % 2] + h->f_off[ci];
+          P.c_rhs_stride = h->f_total;
+          P.out_nv = c.K[j + 1];
+          P.ldc = (c.K[j + 1] + 3) & ~3;
+        }
         P.Bt = c.Bt[j];
-        P.rhs_stride = h->n_total;
         P.R = c.R[j]; P.K = c.K[j]; P.N = c.N[j];
         if (j == c.div_step) { P.lam_row = c.lam_row_f; P.lam_col = c.lam_col_f; }
         P.scale_in = first ? c.scale : nullptr;

@@ -12,14 +12,19 @@ namespace fdst {
 // Same contraction as GemmProb (C(r, n) = sum_k A(r, k) B(k, n) stored at
 // C[n*R + r]) with FP32 intermediates: the first step reads the FP64 input,
 // the last writes FP64; B is pre-split into TF32 hi/lo parts.
+// Row r of A starts at r*lda (lda = K for the FP64 input, a multiple of 4
+// for FP32 intermediates). C(r, n) with r = u*out_nv + v is stored at
+// (n*(R/out_nv) + u)*ldc + v: the output's rows (n, u) hold the next
+// contracted index v, padded to ldc (out_nv = ldc = R writes C[n*R + r]).
 struct TcProb {
   const double *A64 = nullptr;
   const float *A32 = nullptr;
   double *C64 = nullptr;
   float *C32 = nullptr;
   const float *Bt = nullptr;
-  int64_t rhs_stride = 0;
+  int64_t a_rhs_stride = 0, c_rhs_stride = 0;
   int R = 0, K = 0, N = 0;
+  int lda = 0, out_nv = 0, ldc = 0;
   const float *lam_row = nullptr, *lam_col = nullptr;
   const double *scale_in = nullptr, *scale_out = nullptr;
 };
