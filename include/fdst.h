@@ -52,6 +52,11 @@ enum { FDST_TH = 0, FDST_RT = 1 };                          /* discretization (S
 enum { FDST_FD_F64 = 0, FDST_FD_TF32X3 = 1, FDST_FD_BF16X6 = 2 }; /* FD contraction precision */
 enum { FDST_GEOM_IDENTITY = 0, FDST_GEOM_SINE_BUMP = 1 };   /* geometry map G */
 enum { FDST_VARIANT_PD = 0, FDST_VARIANT_PD_GEO = 1 };      /* P_D (Sec. 5) or P_D^G (Sec. 6) */
+/* Matvec arithmetic: FP64 (DFMA), or double-float (each value an unevaluated
+ * sum of two floats, 48-bit significand, error-free FMA products and TwoSum
+ * additions on the FP32 units). fdst_solve always checks the true residual
+ * with the FP64 matvec. */
+enum { FDST_MV_F64 = 0, FDST_MV_DF64 = 1 };
 
 typedef struct {
   int dim;                 /* 2 or 3 */
@@ -65,6 +70,7 @@ typedef struct {
   int fd_precision;        /* FDST_FD_* */
   double cpen;             /* Nitsche penalty C_pen (RT); <= 0 selects 5(alpha+1) (Sec. 7) */
   int max_rhs;             /* most right-hand sides one call will pass (workspace sizing), >= 1 */
+  int matvec_precision;    /* FDST_MV_F64 or FDST_MV_DF64 */
 } fdst_desc;
 
 typedef struct {
@@ -119,7 +125,8 @@ fdst_status fdst_apply_prec(fdst_handle h, const double *d_r, double *d_s, int n
 /*
  * fdst_matvec - y = A x with A the Stokes matrix of eq. Stokes_system:
  * matrix-free Kronecker form on the identity map (blocks A_rs, B_r of Sec. 3
- * with nu constant), assembled CSR on a mapped geometry.
+ * with nu constant), assembled CSR on a mapped geometry; arithmetic as set by
+ * desc.matvec_precision.
  * d_x, d_y: device, nrhs * n_total doubles each, not aliased.
  */
 fdst_status fdst_matvec(fdst_handle h, const double *d_x, double *d_y, int nrhs, fdst_stream stream);

@@ -19,6 +19,7 @@ FD_F64, FD_TF32X3, FD_BF16X6 = 0, 1, 2
 HAS_TC = True        # the split-TF32 tcgen05 FD contraction is built (sm_103a)
 GEOM_IDENTITY, GEOM_SINE_BUMP = 0, 1
 VARIANT_PD, VARIANT_PD_GEO = 0, 1
+MV_F64, MV_DF64 = 0, 1
 
 STATUS = {0: "OK", 1: "INVALID_ARGUMENT", 2: "NOT_SPD", 3: "OUT_OF_MEMORY", 4: "CUDA_ERROR", 5: "MAXIT",
           6: "STAGNATION", 7: "BREAKDOWN", 8: "TIMEOUT", 9: "NAN_DETECTED", 10: "ADMISSION_REJECTED",
@@ -35,7 +36,8 @@ class Desc(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("discretization", ctypes.c_int), ("degree", ctypes.c_int),
                 ("h_knots", ctypes.POINTER(ctypes.c_double) * 3), ("nknots", ctypes.c_int * 3),
                 ("viscosity", ctypes.c_double), ("geometry", ctypes.c_int), ("variant", ctypes.c_int),
-                ("fd_precision", ctypes.c_int), ("cpen", ctypes.c_double), ("max_rhs", ctypes.c_int)]
+                ("fd_precision", ctypes.c_int), ("cpen", ctypes.c_double), ("max_rhs", ctypes.c_int),
+                ("matvec_precision", ctypes.c_int)]
 
 
 class Sizes(ctypes.Structure):
@@ -146,7 +148,7 @@ class Stokes:
     """
 
     def __init__(self, knots, p, disc=TH, viscosity=1.0, fd_precision=FD_F64, max_rhs=1,
-                 geometry=GEOM_IDENTITY, variant=VARIANT_PD, cpen=0.0):
+                 geometry=GEOM_IDENTITY, variant=VARIANT_PD, cpen=0.0, matvec_precision=MV_F64):
         lib = load_library()
         self._knots = [np.ascontiguousarray(k, dtype=np.float64) for k in knots]
         desc = Desc()
@@ -162,6 +164,7 @@ class Stokes:
         desc.fd_precision = fd_precision
         desc.cpen = cpen
         desc.max_rhs = max_rhs
+        desc.matvec_precision = matvec_precision
         h = ctypes.c_void_p()
         _check(lib.fdst_setup(ctypes.byref(desc), ctypes.byref(h)))
         self._h = h

@@ -51,6 +51,7 @@ struct BandDev {
   int rows, cols, w;
   double *vals;
   int *lo;
+  float2 *vals_df;   // the same values split into FP32 pairs (double-float matvec)
 };
 
 struct PlanOp {
@@ -90,6 +91,7 @@ struct fdst_ctx {
   std::vector<fdst::PlanOp> plan;
   std::vector<double *> t1, g;
   std::vector<int64_t> t1_size, g_size;
+  float2 *x2 = nullptr, *y2 = nullptr;   // double-float copies of the matvec input / output
   // MINRES
   double *v = nullptr, *v_old = nullptr, *z = nullptr, *z_new = nullptr, *Az = nullptr, *w = nullptr,
          *w_old = nullptr;
@@ -370,9 +372,15 @@ static fdst_status build_matvec(fdst_ctx *h) {
       lo[i] = l;
       for (int j = 0; j < w; ++j) vals[(size_t)i * w + j] = A(i, l + j);
     }
-    BandDev b{A.rows, A.cols, w, nullptr, nullptr};
+    BandDev b{A.rows, A.cols, w, nullptr, nullptr, nullptr};
     TRY(upload(h, &b.vals, vals));
     TRY(upload(h, &b.lo, lo));
+    std::vector<float2> vdf(vals.size());
+    for (size_t i = 0; i < vals.size(); ++i) {
+      const float hi = (float)vals[i];
+      vdf[i] = make_float2(hi, (float)(vals[i] - (double)hi));
+    }
+    TRY(upload(h, &b.vals_df, vdf));
     *id = (int)h->bands.size();
     h->bands.push_back(b);
     band_ids[key] = *id;
@@ -494,6 +502,10 @@ static fdst_status build_matvec(fdst_ctx *h) {
     TRY(dalloc(h, &b, (size_t)sz * h->max_rhs));
     h->g.push_back(b);
   }
+  if (h->desc.matvec_precision == FDST_MV_DF64) {
+    TRY(dalloc(h, &h->x2, (size_t)h->n_total * h->max_rhs));
+    TRY(dalloc(h, &h->y2, (size_t)h->n_total * h->max_rhs));
+  }
   return FDST_OK;
 }
 
@@ -594,7 +606,8 @@ static fdst_status run_apply(fdst_ctx *h, const double *r, double *s, int nrhs, 
   return FDST_OK;
 }
 
-static fdst_status run_matvec(fdst_ctx *h, const double *x, double *y, int nrhs, const int *done, cudaStream_t st) {
+static fdst_status run_matvec_f64(fdst_ctx *h, const double *x, double *y, int nrhs, const int *done,
+                                  cudaStream_t st) {
   // pack consecutive ops of a stage into launches with pairwise distinct outputs
   size_t i = 0;
   const auto &P = h->plan;
@@ -624,6 +637,51 @@ static fdst_status run_matvec(fdst_ctx *h, const double *x, double *y, int nrhs,
   }
   CK(cudaGetLastError());
   return FDST_OK;
+}
+
+// Same plan in double-float arithmetic: x split once into FP32 pairs, every
+// banded mode product on the FP32 units, the result joined back to FP64.
+static fdst_status run_matvec_df(fdst_ctx *h, const double *x, double *y, int nrhs, const int *done,
+                                 cudaStream_t st) {
+  launch_split_df(x, h->x2, h->n_total, h->n_total, nrhs, done, st);
+  size_t i = 0;
+  const auto &P = h->plan;
+  while (i < P.size()) {
+    BandGroupDF g;
+    std::vector<std::pair<int, int>> outs;
+    int stage = P[i].stage;
+    while (i < P.size() && P[i].stage == stage && g.nop < kMaxGroup) {
+      auto o = std::make_pair(P[i].out_kind, P[i].out_id);
+      if (std::find(outs.begin(), outs.end(), o) != outs.end()) break;
+      outs.push_back(o);
+      const PlanOp &op = P[i];
+      BandOpDF &b = g.op[g.nop++];
+      const BandDev &bd = h->bands[op.band];
+      b.vals = bd.vals_df; b.lo = bd.lo; b.w = bd.w; b.rows = bd.rows;
+      b.d0 = op.dims[0]; b.d1 = op.dims[1]; b.d2 = op.dims[2]; b.mode = op.mode;
+      const float ch = (float)op.coef;
+      b.coef = make_float2(ch, (float)(op.coef - (double)ch));
+      b.accumulate = op.accumulate;
+      if (op.in_kind == 0) { b.X = h->x2 + h->off[op.in_id]; b.x_rhs_stride = h->n_total; }
+      else if (op.in_kind == 1) { b.X = reinterpret_cast<const float2 *>(h->t1[op.in_id]); b.x_rhs_stride = h->t1_size[op.in_id]; }
+      else { b.X = reinterpret_cast<const float2 *>(h->g[op.in_id]); b.x_rhs_stride = h->g_size[op.in_id]; }
+      if (op.out_kind == 3) { b.Y = h->y2 + h->off[op.out_id]; b.y_rhs_stride = h->n_total; }
+      else if (op.out_kind == 1) { b.Y = reinterpret_cast<float2 *>(h->t1[op.out_id]); b.y_rhs_stride = h->t1_size[op.out_id]; }
+      else { b.Y = reinterpret_cast<float2 *>(h->g[op.out_id]); b.y_rhs_stride = h->g_size[op.out_id]; }
+      ++i;
+    }
+    launch_band_df(g, nrhs, done, st);
+  }
+  launch_join_df(h->y2, y, h->n_total, h->n_total, nrhs, done, st);
+  CK(cudaGetLastError());
+  return FDST_OK;
+}
+
+// exact = true forces the FP64 (DFMA) evaluation (true-residual checks).
+static fdst_status run_matvec(fdst_ctx *h, const double *x, double *y, int nrhs, const int *done, cudaStream_t st,
+                              bool exact = false) {
+  if (!exact && h->desc.matvec_precision == FDST_MV_DF64) return run_matvec_df(h, x, y, nrhs, done, st);
+  return run_matvec_f64(h, x, y, nrhs, done, st);
 }
 
 }  // namespace fdst
@@ -664,6 +722,10 @@ fdst_status fdst_setup(const fdst_desc *desc, fdst_handle *out) {
   if (desc->geometry != FDST_GEOM_IDENTITY || desc->variant != FDST_VARIANT_PD) {
     set_error("mapped geometry / P_D^G not available in this build");
     return FDST_NOT_SUPPORTED;
+  }
+  if (desc->matvec_precision != FDST_MV_F64 && desc->matvec_precision != FDST_MV_DF64) {
+    set_error("unknown matvec precision");
+    return FDST_INVALID_ARGUMENT;
   }
   if (desc->fd_precision != FDST_FD_F64 && desc->fd_precision != FDST_FD_TF32X3) {
     set_error("unknown or unsupported FD precision");
@@ -800,7 +862,7 @@ fdst_status fdst_solve(fdst_handle h, const double *d_b, double *d_x, int nrhs, 
   // ---- init: v = b - A x0 ; v_old = w = w_old = 0 ; z = P^{-1} v ; gamma_1 = sqrt(<v, z>)
   CK(cudaMemsetAsync(h->done, 0, sizeof(int) * nrhs, st));
   CK(cudaMemsetAsync(h->n_stopped, 0, sizeof(int), st));
-  TRY(run_matvec(h, d_x, h->Az, nrhs, nullptr, st));
+  TRY(run_matvec(h, d_x, h->Az, nrhs, nullptr, st, true));
   launch_axpby(d_b, h->v, 1.0, 0.0, n, n, nrhs, st);
   launch_axpby(h->Az, h->v, -1.0, 1.0, n, n, nrhs, st);
   CK(cudaMemsetAsync(h->v_old, 0, sizeof(double) * n * nrhs, st));
@@ -820,7 +882,7 @@ fdst_status fdst_solve(fdst_handle h, const double *d_b, double *d_x, int nrhs, 
   for (int j = 0; j < nrhs; ++j) bb[j] = h->h_dots[j];
   // true relative residual ||b - A x||_2 / ||b||_2 in FP64 (Az is free between iterations)
   auto true_residuals = [&]() -> fdst_status {
-    TRY(run_matvec(h, d_x, h->Az, nrhs, nullptr, st));
+    TRY(run_matvec(h, d_x, h->Az, nrhs, nullptr, st, true));
     launch_axpby(d_b, h->Az, 1.0, -1.0, n, n, nrhs, st);
     launch_dot(h->Az, h->Az, n, n, nrhs, h->partials, h->counters, h->dots, nullptr, st);
     CK(cudaMemcpyAsync(h->h_dots, h->dots, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));

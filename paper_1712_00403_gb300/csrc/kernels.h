@@ -54,6 +54,32 @@ struct BandGroup {
 };
 void launch_band(const BandGroup &g, int nrhs, const int *done, cudaStream_t s);
 
+// Double-float variant: tensors and band values are FP32 pairs (hi, lo) with
+// hi + lo the value (48-bit significand); products and sums use error-free
+// transformations (FMA-based exact product, Knuth's TwoSum). Same operation
+// as BandOp; X, Y, vals hold float2.
+struct BandOpDF {
+  const float2 *X = nullptr;
+  float2 *Y = nullptr;
+  const float2 *vals = nullptr;
+  const int *lo = nullptr;
+  int w = 0, rows = 0;
+  int d0 = 1, d1 = 1, d2 = 1, mode = 0;
+  float2 coef = {1.0f, 0.0f};
+  int accumulate = 0;
+  int64_t x_rhs_stride = 0, y_rhs_stride = 0;
+};
+struct BandGroupDF {
+  BandOpDF op[kMaxGroup];
+  int nop = 0;
+};
+void launch_band_df(const BandGroupDF &g, int nrhs, const int *done, cudaStream_t s);
+// y2 = split(x) (double -> FP32 pair) and x = join(y2) over n entries per right-hand side.
+void launch_split_df(const double *x, float2 *y, int64_t n, int64_t stride, int nrhs, const int *done,
+                     cudaStream_t s);
+void launch_join_df(const float2 *x, double *y, int64_t n, int64_t stride, int nrhs, const int *done,
+                    cudaStream_t s);
+
 // ---- MINRES (per right-hand side state, all device resident)
 struct MinresState {
   double gamma, gamma_old, delta, c, c_old, s, s_old, eta, eta0;

@@ -129,23 +129,24 @@ __global__ void __launch_bounds__(256) k_band(BandGroup g, int nrhs, const int *
   const int rhs = blockIdx.y;
   if (done && done[rhs]) return;
   const BandOp &op = g.op[blockIdx.z];
-  int dims[3] = {op.d0, op.d1, op.d2};
-  int od[3] = {op.d0, op.d1, op.d2};
-  od[op.mode] = op.rows;
-  const int64_t total = (int64_t)od[0] * od[1] * od[2];
-  const int64_t stride_in = op.mode == 0 ? 1 : (op.mode == 1 ? (int64_t)dims[0] : (int64_t)dims[0] * dims[1]);
+  const int mode = op.mode;
+  const unsigned od0 = mode == 0 ? op.rows : op.d0, od1 = mode == 1 ? op.rows : op.d1,
+                 od2 = mode == 2 ? op.rows : op.d2;
+  const int64_t total = (int64_t)od0 * od1 * od2;
+  const int64_t stride_in = mode == 0 ? 1 : (mode == 1 ? (int64_t)op.d0 : (int64_t)op.d0 * op.d1);
   const double *X = op.X + rhs * op.x_rhs_stride;
   double *Y = op.Y + rhs * op.y_rhs_stride;
   for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total; o += (int64_t)gridDim.x * blockDim.x) {
-    int o0 = (int)(o % od[0]);
-    int64_t t = o / od[0];
-    int o1 = (int)(t % od[1]);
-    int o2 = (int)(t / od[1]);
-    int i = op.mode == 0 ? o0 : (op.mode == 1 ? o1 : o2);
+    const unsigned ou = (unsigned)o;            // a block has fewer than 2^32 entries
+    const unsigned t = ou / od0;
+    const int o0 = (int)(ou - t * od0);
+    const unsigned o2u = t / od1;
+    const int o1 = (int)(t - o2u * od1), o2 = (int)o2u;
+    const int i = mode == 0 ? o0 : (mode == 1 ? o1 : o2);
     int64_t base;
-    if (op.mode == 0) base = ((int64_t)o2 * dims[1] + o1) * dims[0];
-    else if (op.mode == 1) base = (int64_t)o2 * dims[1] * dims[0] + o0;
-    else base = (int64_t)o1 * dims[0] + o0;
+    if (mode == 0) base = ((int64_t)o2 * op.d1 + o1) * op.d0;
+    else if (mode == 1) base = (int64_t)o2 * op.d1 * op.d0 + o0;
+    else base = (int64_t)o1 * op.d0 + o0;
     const double *v = op.vals + (int64_t)i * op.w;
     const int l = op.lo[i];
     double acc = 0.0;
@@ -158,9 +159,8 @@ __global__ void __launch_bounds__(256) k_band(BandGroup g, int nrhs, const int *
 void launch_band(const BandGroup &g, int nrhs, const int *done, cudaStream_t s) {
   int64_t maxt = 0;
   for (int i = 0; i < g.nop; ++i) {
-    int od[3] = {g.op[i].d0, g.op[i].d1, g.op[i].d2};
-    od[g.op[i].mode] = g.op[i].rows;
-    int64_t t = (int64_t)od[0] * od[1] * od[2];
+    const auto &o = g.op[i];
+    int64_t t = (int64_t)(o.mode == 0 ? o.rows : o.d0) * (o.mode == 1 ? o.rows : o.d1) * (o.mode == 2 ? o.rows : o.d2);
     maxt = t > maxt ? t : maxt;
   }
   int64_t blocks = (maxt + 255) / 256;
@@ -169,6 +169,126 @@ void launch_band(const BandGroup &g, int nrhs, const int *done, cudaStream_t s) 
   dim3 grid((unsigned)blocks, nrhs, g.nop);
   count_launch(1);
   k_band<<<grid, 256, 0, s>>>(g, nrhs, done);
+}
+
+// ------------------------------------------------------------------ double-float banded mode product
+// GB300's FP64 pipe runs at 1/62 of its FP32 rate, so the matvec can also be
+// evaluated in double-float arithmetic on the FP32 units: a value is an
+// unevaluated sum hi + lo of two floats. Products use the exact FMA residual
+// (p = a*b, e = fma(a, b, -p)), sums use Knuth's branch-free TwoSum.
+
+__device__ __forceinline__ void df_fma_acc(float2 a, float2 b, float &sh, float &sl) {
+  const float p = a.x * b.x;
+  float e = fmaf(a.x, b.x, -p);
+  e = fmaf(a.x, b.y, e);
+  e = fmaf(a.y, b.x, e);
+  const float t = sh + p;
+  const float z = t - sh;
+  const float err = (sh - (t - z)) + (p - z);
+  sh = t;
+  sl = sl + (err + e);
+}
+
+__device__ __forceinline__ float2 df_norm(float sh, float sl) {
+  const float h = sh + sl;
+  return make_float2(h, sl - (h - sh));
+}
+
+__global__ void __launch_bounds__(256) k_band_df(BandGroupDF g, int nrhs, const int *done) {
+  const int rhs = blockIdx.y;
+  if (done && done[rhs]) return;
+  const BandOpDF &op = g.op[blockIdx.z];
+  const int mode = op.mode;
+  const unsigned od0 = mode == 0 ? op.rows : op.d0, od1 = mode == 1 ? op.rows : op.d1,
+                 od2 = mode == 2 ? op.rows : op.d2;
+  const int64_t total = (int64_t)od0 * od1 * od2;
+  const int64_t stride_in = mode == 0 ? 1 : (mode == 1 ? (int64_t)op.d0 : (int64_t)op.d0 * op.d1);
+  const float2 *X = op.X + rhs * op.x_rhs_stride;
+  float2 *Y = op.Y + rhs * op.y_rhs_stride;
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total; o += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned ou = (unsigned)o;            // a block has fewer than 2^32 entries
+    const unsigned t = ou / od0;
+    const int o0 = (int)(ou - t * od0);
+    const unsigned o2u = t / od1;
+    const int o1 = (int)(t - o2u * od1), o2 = (int)o2u;
+    const int i = mode == 0 ? o0 : (mode == 1 ? o1 : o2);
+    int64_t base;
+    if (mode == 0) base = ((int64_t)o2 * op.d1 + o1) * op.d0;
+    else if (mode == 1) base = (int64_t)o2 * op.d1 * op.d0 + o0;
+    else base = (int64_t)o1 * op.d0 + o0;
+    const float2 *v = op.vals + (int64_t)i * op.w;
+    const int l = op.lo[i];
+    float sh = 0.0f, sl = 0.0f;
+    for (int j = 0; j < op.w; ++j) df_fma_acc(v[j], X[base + (int64_t)(l + j) * stride_in], sh, sl);
+    float2 acc = df_norm(sh, sl);
+    float rh = 0.0f, rl = 0.0f;
+    df_fma_acc(op.coef, acc, rh, rl);
+    if (op.accumulate) {
+      const float2 yo = Y[o];
+      const float t2 = rh + yo.x;
+      const float z2 = t2 - rh;
+      const float err = (rh - (t2 - z2)) + (yo.x - z2);
+      rl = rl + (err + yo.y);
+      rh = t2;
+    }
+    Y[o] = df_norm(rh, rl);
+  }
+}
+
+void launch_band_df(const BandGroupDF &g, int nrhs, const int *done, cudaStream_t s) {
+  int64_t maxt = 0;
+  for (int i = 0; i < g.nop; ++i) {
+    const auto &o = g.op[i];
+    int64_t t = (int64_t)(o.mode == 0 ? o.rows : o.d0) * (o.mode == 1 ? o.rows : o.d1) * (o.mode == 2 ? o.rows : o.d2);
+    maxt = t > maxt ? t : maxt;
+  }
+  int64_t blocks = (maxt + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  dim3 grid((unsigned)blocks, nrhs, g.nop);
+  count_launch(1);
+  k_band_df<<<grid, 256, 0, s>>>(g, nrhs, done);
+}
+
+__global__ void k_split_df(const double *x, float2 *y, int64_t n, int64_t stride, const int *done) {
+  const int j = blockIdx.y;
+  if (done && done[j]) return;
+  const double *xr = x + j * stride;
+  float2 *yr = y + j * stride;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = xr[i];
+    const float h = __double2float_rn(v);
+    yr[i] = make_float2(h, __double2float_rn(v - (double)h));
+  }
+}
+
+__global__ void k_join_df(const float2 *x, double *y, int64_t n, int64_t stride, const int *done) {
+  const int j = blockIdx.y;
+  if (done && done[j]) return;
+  const float2 *xr = x + j * stride;
+  double *yr = y + j * stride;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 v = xr[i];
+    yr[i] = (double)v.x + (double)v.y;
+  }
+}
+
+void launch_split_df(const double *x, float2 *y, int64_t n, int64_t stride, int nrhs, const int *done,
+                     cudaStream_t s) {
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  count_launch(1);
+  k_split_df<<<dim3((unsigned)blocks, nrhs), 256, 0, s>>>(x, y, n, stride, done);
+}
+
+void launch_join_df(const float2 *x, double *y, int64_t n, int64_t stride, int nrhs, const int *done,
+                    cudaStream_t s) {
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  count_launch(1);
+  k_join_df<<<dim3((unsigned)blocks, nrhs), 256, 0, s>>>(x, y, n, stride, done);
 }
 
 // ------------------------------------------------------------------ reductions

@@ -127,3 +127,35 @@ def test_host_entry_points_match_device():
     s = torch.empty_like(b)
     P.apply_prec(b, s)
     assert rel(sh, s.cpu().numpy()) <= 1e-15
+
+
+@pytest.mark.parametrize("spec", CASES, ids=_ids)
+def test_matvec_df64_matches_oracle(spec):
+    """Double-float matvec (FP32 pairs, error-free transformations) within the FP64 bar."""
+    import paper_1712_00403_gb300 as fd
+    P = gpu_problem(spec, max_rhs=2, matvec_precision=fd.MV_DF64)
+    S = oracle_problem(spec)
+    X = np.stack([synth.random_vector(700 + j, P.n_total) for j in range(2)])
+    x = torch.tensor(X.reshape(-1), device="cuda")
+    y = torch.empty_like(x)
+    P.matvec(x, y)
+    out = y.cpu().numpy().reshape(2, -1)
+    for j in range(2):
+        ref = stokes.matvec(S, X[j])
+        for o0, o1 in zip(P.block_offsets[:-1], P.block_offsets[1:]):
+            assert rel(out[j, o0:o1], ref[o0:o1]) <= 1e-12
+
+
+@pytest.mark.parametrize("spec", [problem_spec(3, 2, 6), problem_spec(2, 2, 16)], ids=_ids)
+def test_minres_df64_matvec_matches_f64(spec):
+    import paper_1712_00403_gb300 as fd
+    Pd = gpu_problem(spec, max_rhs=2, matvec_precision=fd.MV_DF64)
+    Pf = gpu_problem(spec, max_rhs=2, matvec_precision=fd.MV_F64)
+    B = np.stack([synth.rhs(80 + j, Pd.block_sizes) for j in range(2)])
+    b = torch.tensor(B.reshape(-1), device="cuda")
+    xd, xf = torch.zeros_like(b), torch.zeros_like(b)
+    idd = Pd.solve(b, xd, tol=1e-8, maxit=500)
+    iff = Pf.solve(b, xf, tol=1e-8, maxit=500)
+    for a, c in zip(idd, iff):
+        assert a["status"] == "OK" and a["true_rel_res"] <= 1e-8
+        assert abs(a["iterations"] - c["iterations"]) <= 1
