@@ -1,0 +1,325 @@
+"""Mapped geometry, variable viscosity and the geometry-aware preconditioner
+P_D^G (paper Sec. 3 eq. Akk_TH / Q_TH, Sec. 6, Appendix). Oracle: test
+infrastructure only.
+
+Map (analytic stand-in for the paper's spline map, reading A18):
+    G(eta) = eta + a sin(pi eta1) sin(pi eta2) sin(pi eta3) (1, 1, 1),  a = 0.1
+so J = I + 1 (a grad s)^T and det J = 1 + a (1 . grad s); viscosity
+nu(x) = 1 + 0.5 sin(2 pi x1) cos(2 pi x2) evaluated at x = G(eta).
+
+Operator on the mapped domain (TH push-forward phi = e_r B o G^{-1}):
+    a(w, v) = int 2 nu grad^s w : grad^s v,   b(v, q) = -int q div v
+with grad_x B = J^{-T} grad_eta B. Quadrature: Gauss with p+2 points per
+element and direction.
+
+P_D^G (Sec. 6): P_V^G = D_V^{1/2} P~_V D_V^{1/2} with P~_{V,k} the Kronecker
+sum of the weighted pencils (K^k_d with tau^k_d, M^k_d with mu^k_d,
+Appendix), [D_V]_ii = A_ii / (P~_V)_ii; P_Q^G = D_Q^{1/2} P_Q D_Q^{1/2},
+[D_Q]_ii = Q_ii / (P_Q)_ii with Q the nu^{-1} |det J| weighted pressure mass.
+
+Separable approximation (reading A9; the paper cites Diliberto-Straus /
+Wachspress without spelling out the steps): each diagonal entry c^k_jj > 0
+of C_k = nu (J^{-1} J^{-T} + D_k D_k^T) |det J| is fitted at the quadrature
+points as exp(f1(eta1) + f2(eta2) + f3(eta3)) by the Diliberto-Straus
+alternating midrange iteration on log c^k_jj (a fixed 12 sweeps, each
+direction in turn: f_d = (max + min)/2 of the residual over the other two
+variables). Each fit is normalized so that its two non-own factors have
+zero mean log over the quadrature points; then tau^k_j = exp(f^{k,j}_j) and
+mu^k_d = exp(mean of f^{k,j}_d over the two j != d). The D_V scaling absorbs
+what the fit misses.
+
+Pins (tests/test_oracle_geometry.py): brute-force element quadrature of the
+symmetric-gradient form and of b vs. the sum-factorized matvec; amplitude 0
+with nu = 1 reproduces the cube operator; det J closed form vs.
+numpy.linalg.det; the fit reproduces an exactly separable field; on the cube
+P~_V = P_V and D_V = I; diag(P_V^G) = diag(A), diag(P_Q^G) = diag(Q);
+Theorem 2 spectral bounds of P_Q^{-1} Q. Parity unpinned: the separable fit
+on non-separable fields (no independent reference exists; the CUDA path
+runs the same algorithm).
+"""
+import numpy as np
+
+from . import kron, splines, stokes, univariate as uv
+
+AMP = 0.1
+SWEEPS = 12
+
+
+# ---------------------------------------------------------------- map and viscosity
+
+def bump(eta, amp=AMP):
+    """s(eta) = amp sin(pi e1) sin(pi e2) sin(pi e3) and its gradient (..., 3)."""
+    e1, e2, e3 = eta[..., 0], eta[..., 1], eta[..., 2]
+    s1, s2, s3 = np.sin(np.pi * e1), np.sin(np.pi * e2), np.sin(np.pi * e3)
+    c1, c2, c3 = np.cos(np.pi * e1), np.cos(np.pi * e2), np.cos(np.pi * e3)
+    s = amp * s1 * s2 * s3
+    g = amp * np.pi * np.stack([c1 * s2 * s3, s1 * c2 * s3, s1 * s2 * c3], axis=-1)
+    return s, g
+
+
+def geometry(eta, amp=AMP):
+    """x = G(eta), J (..., 3, 3) with J_ij = d x_i / d eta_j, det J, J^{-1}."""
+    s, g = bump(eta, amp)
+    x = eta + s[..., None]
+    J = np.eye(3) + np.ones(3)[:, None] * g[..., None, :]
+    det = 1.0 + g.sum(axis=-1)
+    Jinv = np.linalg.inv(J)
+    return x, J, det, Jinv
+
+
+def viscosity(x):
+    return 1.0 + 0.5 * np.sin(2 * np.pi * x[..., 0]) * np.cos(2 * np.pi * x[..., 1])
+
+
+# ---------------------------------------------------------------- quadrature grid
+
+class Grid:
+    """Tensor Gauss grid (p+2 points per element per direction) with the
+    geometry and viscosity at every point; axis d of the arrays is direction d+1."""
+
+    def __init__(self, S, amp=AMP, nu_const=None, npts=None):
+        self.S = S
+        npts = S.p + 2 if npts is None else npts
+        self.pts, self.wts = [], []
+        for d in range(3):
+            x, w = splines.gauss_rule(S.pres[d].knots, npts)
+            self.pts.append(x)
+            self.wts.append(w)
+        E = np.stack(np.meshgrid(*self.pts, indexing="ij"), axis=-1)
+        self.x, self.J, self.det, self.Jinv = geometry(E, amp)
+        self.nu = np.full(self.det.shape, nu_const) if nu_const is not None else viscosity(self.x)
+        W = self.wts[0][:, None, None] * self.wts[1][None, :, None] * self.wts[2][None, None, :]
+        self.W = W
+        # univariate tables at the points: value and derivative of each space
+        self.vtab = {}
+
+    def table(self, space, d, deriv):
+        key = (id(space), d, deriv)
+        if key not in self.vtab:
+            B, D = splines.basis(space.knots, space.degree, self.pts[d])
+            self.vtab[key] = ((D if deriv else B)[:, space.keep]).T.copy()   # (n, npts)
+        return self.vtab[key]
+
+
+def to_points(G, space3, x, derivs):
+    """Evaluate sum_i x_i prod_d T_d[i_d, q_d] where T_d is the value table of
+    direction d (or its derivative when derivs[d]); x vec-ordered (i1 fastest)."""
+    n = [space3[d].n for d in range(3)]
+    X = np.asarray(x, float).reshape(n[2], n[1], n[0])        # [i3, i2, i1]
+    T = [G.table(space3[d], d, derivs[d]) for d in range(3)]  # (n_d, q_d)
+    # result indexed [q1, q2, q3]
+    Y = np.einsum("cba,ap->cbp", X, T[0])
+    Y = np.einsum("cbp,bq->cpq", Y, T[1])
+    Y = np.einsum("cpq,cr->pqr", Y, T[2])
+    return Y
+
+
+def from_points(G, space3, F, derivs):
+    """Transpose of to_points: y_i = sum_q F[q] prod_d T_d[i_d, q_d] (vec order)."""
+    T = [G.table(space3[d], d, derivs[d]) for d in range(3)]
+    Y = np.einsum("pqr,cr->pqc", F, T[2])
+    Y = np.einsum("pqc,bq->pbc", Y, T[1])
+    Y = np.einsum("pbc,ap->abc", Y, T[0])                      # [i1, i2, i3]
+    return np.transpose(Y, (2, 1, 0)).reshape(-1)
+
+
+# ---------------------------------------------------------------- mapped Stokes operator
+
+def matvec(S, G, x):
+    """y = A x on the mapped domain by sum-factorized quadrature: u and grad_eta u
+    at the points, grad_x u = grad_eta u J^{-1}, stress 2 nu grad^s u - p I, tested
+    with grad_x of the basis (a(.,.) and b(.,.) of Sec. 3)."""
+    blocks = S.split(np.asarray(x, float))
+    u, pr = blocks[:3], blocks[3]
+    wd = G.W * G.det
+    # grad_x u: gx[r][c] = d u_r / d x_c = sum_a d u_r/d eta_a (J^{-1})_{a c}
+    gx = [[None] * 3 for _ in range(3)]
+    for r in range(3):
+        ge = [to_points(G, S.vel[r], u[r], [a == 0, a == 1, a == 2]) for a in range(3)]
+        for c in range(3):
+            gx[r][c] = sum(ge[a] * G.Jinv[..., a, c] for a in range(3))
+    ph = to_points(G, S.pres, pr, [False, False, False])
+    div = gx[0][0] + gx[1][1] + gx[2][2]
+    ys = []
+    for r in range(3):
+        y = np.zeros(S.block_sizes[r])
+        for a in range(3):
+            # F_a = sum_c sigma_rc (J^{-1})_{a c}, sigma = nu (grad u + grad u^T) - p I
+            Fa = np.zeros_like(G.det)
+            for c in range(3):
+                sig = G.nu * (gx[r][c] + gx[c][r]) - (ph if r == c else 0.0)
+                Fa = Fa + sig * G.Jinv[..., a, c]
+            y += from_points(G, S.vel[r], Fa * wd, [a == 0, a == 1, a == 2])
+        ys.append(y)
+    ys.append(from_points(G, S.pres, -div * wd, [False, False, False]))
+    return np.concatenate(ys)
+
+
+def brute_force(S, G):
+    """Dense A (velocity) and B by explicit quadrature of 2 nu grad^s w : grad^s v
+    and -q div v, every vector basis function evaluated on its own (tiny sizes)."""
+    P = np.stack(np.meshgrid(np.arange(len(G.pts[0])), np.arange(len(G.pts[1])), np.arange(len(G.pts[2])),
+                             indexing="ij"), axis=-1).reshape(-1, 3)
+    Jinv = G.Jinv.reshape(-1, 3, 3)
+    wd = (G.W * G.det).reshape(-1)
+    nu = G.nu.reshape(-1)
+
+    def multi(space3):
+        n = [space3[d].n for d in range(3)]
+        idx = np.array(np.unravel_index(np.arange(int(np.prod(n))), n[::-1])).T[:, ::-1]
+        return idx
+
+    def grad_x(space3, m):
+        ge = np.ones((len(P), 3))
+        for a in range(3):
+            v = np.ones(len(P))
+            for d in range(3):
+                T = G.table(space3[d], d, d == a)
+                v = v * T[m[d], P[:, d]]
+            ge[:, a] = v
+        return np.einsum("qa,qac->qc", ge, Jinv)       # d B / d x_c
+
+    idx = multi(S.vel[0])
+    nv = len(idx)
+    grads = np.array([grad_x(S.vel[0], m) for m in idx])          # (nv, q, 3)
+    A = np.zeros((3 * nv, 3 * nv))
+    for r in range(3):
+        for s in range(3):
+            for i in range(nv):
+                Gw = np.zeros((len(P), 3, 3))
+                Gw[:, r, :] = grads[i]
+                Sw = 0.5 * (Gw + Gw.transpose(0, 2, 1))
+                for j in range(nv):
+                    Gv = np.zeros((len(P), 3, 3))
+                    Gv[:, s, :] = grads[j]
+                    Sv = 0.5 * (Gv + Gv.transpose(0, 2, 1))
+                    A[r * nv + i, s * nv + j] = np.sum(wd * 2 * nu * np.einsum("qab,qab->q", Sw, Sv))
+    pidx = multi(S.pres)
+    pval = np.array([np.prod([G.table(S.pres[d], d, False)[m[d], P[:, d]] for d in range(3)], axis=0)
+                     for m in pidx])
+    B = np.zeros((len(pidx), 3 * nv))
+    for r in range(3):
+        for j in range(nv):
+            B[:, r * nv + j] = -(pval * grads[j][:, r][None, :]) @ wd
+    return A, B
+
+
+# ---------------------------------------------------------------- coefficients and separable fit
+
+def c_diag(G, k):
+    """c^k_jj = nu |det J| ((J^{-1} J^{-T})_jj + (J^{-1})_jk^2), j = 0..2 (eq. Q_TH)."""
+    Ji = G.Jinv
+    JJt = np.einsum("...ac,...bc->...ab", Ji, Ji)
+    return [G.nu * np.abs(G.det) * (JJt[..., j, j] + Ji[..., j, k] ** 2) for j in range(3)]
+
+
+def separable_fit(c, sweeps=SWEEPS):
+    """log c ~ f1(q1) + f2(q2) + f3(q3) by Diliberto-Straus midrange sweeps."""
+    L = np.log(c)
+    f = [np.zeros(L.shape[d]) for d in range(3)]
+    shp = [(-1, 1, 1), (1, -1, 1), (1, 1, -1)]
+    for _ in range(sweeps):
+        for d in range(3):
+            R = L - sum(f[e].reshape(shp[e]) for e in range(3) if e != d)
+            axes = tuple(e for e in range(3) if e != d)
+            f[d] = 0.5 * (R.max(axis=axes) + R.min(axis=axes))
+    return f
+
+
+def tau_mu(G, k, sweeps=SWEEPS):
+    """tau^k_d and mu^k_d at the quadrature points of direction d (Appendix form)."""
+    cs = c_diag(G, k)
+    fits = []
+    for j in range(3):
+        f = separable_fit(cs[j], sweeps)
+        # normalize: non-own factors with zero mean log, constant into the own factor
+        for e in range(3):
+            if e != j:
+                m = f[e].mean()
+                f[e] = f[e] - m
+                f[j] = f[j] + m
+        fits.append(f)
+    tau = [np.exp(fits[d][d]) for d in range(3)]
+    mu = [np.exp(0.5 * sum(fits[j][d] for j in range(3) if j != d)) for d in range(3)]
+    return tau, mu
+
+
+def weighted_pencils(S, G, k, sweeps=SWEEPS):
+    """(K^k_d, M^k_d) with weights tau^k_d, mu^k_d given at the quadrature points."""
+    tau, mu = tau_mu(G, k, sweeps)
+    Ks, Ms = [], []
+    for d in range(3):
+        sp = S.vel[k][d]
+        Tv = G.table(sp, d, False)
+        Td = G.table(sp, d, True)
+        w = G.wts[d]
+        Ks.append((Td * (w * tau[d])) @ Td.T)
+        Ms.append((Tv * (w * mu[d])) @ Tv.T)
+    return Ks, Ms
+
+
+# ---------------------------------------------------------------- diagonals and P_D^G
+
+def diag_A(S, G, k):
+    """[A_kk]_ii = sum_ab int C^kk_ab d_a B_i d_b B_i with C^kk = nu |J| (J^-1 J^-T + D_k D_k^T)."""
+    Ji = G.Jinv
+    C = G.nu[..., None, None] * np.abs(G.det)[..., None, None] * (
+        np.einsum("...ac,...bc->...ab", Ji, Ji) + Ji[..., :, k][..., :, None] * Ji[..., :, k][..., None, :])
+    out = 0.0
+    for a in range(3):
+        for b in range(3):
+            T = []
+            for d in range(3):
+                Ta = G.table(S.vel[k][d], d, d == a)
+                Tb = G.table(S.vel[k][d], d, d == b)
+                T.append(Ta * Tb)
+            F = C[..., a, b] * G.W
+            Y = np.einsum("pqr,cr->pqc", F, T[2])
+            Y = np.einsum("pqc,bq->pbc", Y, T[1])
+            Y = np.einsum("pbc,ap->abc", Y, T[0])
+            out = out + np.transpose(Y, (2, 1, 0)).reshape(-1)
+    return out
+
+
+def diag_Q(S, G):
+    """[Q]_ii = int nu^{-1} |det J| B_i^2 (eq. weighted-pressure-mass)."""
+    T = [G.table(S.pres[d], d, False) ** 2 for d in range(3)]
+    F = G.W * np.abs(G.det) / G.nu
+    Y = np.einsum("pqr,cr->pqc", F, T[2])
+    Y = np.einsum("pqc,bq->pbc", Y, T[1])
+    Y = np.einsum("pbc,ap->abc", Y, T[0])
+    return np.transpose(Y, (2, 1, 0)).reshape(-1)
+
+
+def kron_diag(factors):
+    """diag(A_3 x A_2 x A_1) in vec order."""
+    d = np.ones(1)
+    for A in reversed(factors):
+        d = np.kron(d, np.diag(A))
+    return d
+
+
+class PDG:
+    """The geometry-aware block preconditioner P_D^G = diag(P_V^G, P_Q^G)."""
+
+    def __init__(self, S, G, sweeps=SWEEPS):
+        self.S = S
+        self.pencils, self.DV = [], []
+        for k in range(3):
+            Ks, Ms = weighted_pencils(S, G, k, sweeps)
+            self.pencils.append((Ks, Ms, [1.0, 1.0, 1.0]))
+            dP = sum(kron_diag([Ks[e] if e == d else Ms[e] for e in range(3)]) for d in range(3))
+            self.DV.append(diag_A(S, G, k) / dP)
+        self.Mp = stokes.pq_factors(S)
+        self.DQ = diag_Q(S, G) / kron_diag(self.Mp)
+
+    def apply(self, r):
+        b = self.S.split(np.asarray(r, float))
+        out = []
+        for k in range(3):
+            Ks, Ms, coef = self.pencils[k]
+            sc = self.DV[k] ** -0.5
+            out.append(sc * kron.fd_solve(Ks, Ms, coef, sc * b[k]))
+        sq = self.DQ ** -0.5
+        out.append(sq * kron.kron_mass_solve(self.Mp, sq * b[3]))
+        return np.concatenate(out)

@@ -1,0 +1,119 @@
+"""Pins for oracle.geometry (paper Sec. 3 mapped forms, Sec. 6, Appendix)."""
+import numpy as np
+import pytest
+
+from oracle import geometry as geo, kron, stokes
+import synth
+
+
+def _S(n_el, p):
+    return stokes.build([synth.open_uniform_knots(n, p) for n in (n_el if not np.isscalar(n_el) else (n_el,) * 3)], p)
+
+
+def test_det_closed_form_and_jacobian():
+    rng = np.random.default_rng(0)
+    eta = rng.random((50, 3))
+    x, J, det, Jinv = geo.geometry(eta)
+    np.testing.assert_allclose(det, np.linalg.det(J), rtol=1e-14)
+    # J by central differences of the map
+    h = 1e-6
+    for j in range(3):
+        e = np.zeros(3)
+        e[j] = h
+        xp, *_ = geo.geometry(eta + e)
+        xm, *_ = geo.geometry(eta - e)
+        np.testing.assert_allclose(J[:, :, j], (xp - xm) / (2 * h), atol=1e-8)
+    # det J range of the 0.1 sine bump: 1 +- 0.1 pi sqrt(4/3) (max of the gradient sum)
+    g = np.stack(np.meshgrid(*[np.linspace(0, 1, 41)] * 3, indexing="ij"), -1)
+    _, _, d, _ = geo.geometry(g)
+    assert 0.6 < d.min() < 0.7 and 1.3 < d.max() < 1.4
+
+
+def test_sum_factorized_matvec_vs_brute_force():
+    S = _S(2, 1)
+    G = geo.Grid(S)
+    A, B = geo.brute_force(S, G)
+    nv = 3 * S.block_sizes[0]
+    full = np.zeros((S.n_total, S.n_total))
+    full[:nv, :nv] = A
+    full[nv:, :nv] = B
+    full[:nv, nv:] = B.T
+    rng = np.random.default_rng(3)
+    for _ in range(3):
+        x = rng.standard_normal(S.n_total)
+        np.testing.assert_allclose(geo.matvec(S, G, x), full @ x, atol=1e-12 * np.abs(full).max() * 10)
+    np.testing.assert_allclose(A, A.T, atol=1e-13 * np.abs(A).max())
+
+
+def test_identity_limit_is_the_cube_operator():
+    S = _S(3, 2)
+    G = geo.Grid(S, amp=0.0, nu_const=1.0)
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal(S.n_total)
+    np.testing.assert_allclose(geo.matvec(S, G, x), stokes.matvec(S, x), atol=1e-11)
+
+
+def test_separable_fit_exact_on_separable_field():
+    rng = np.random.default_rng(1)
+    g = [rng.standard_normal(n) for n in (7, 5, 6)]
+    c = np.exp(g[0][:, None, None] + g[1][None, :, None] + g[2][None, None, :])
+    f = geo.separable_fit(c)
+    rec = np.exp(f[0][:, None, None] + f[1][None, :, None] + f[2][None, None, :])
+    np.testing.assert_allclose(rec, c, rtol=1e-12)
+
+
+def test_fit_never_increases_the_sup_error():
+    S = _S(3, 2)
+    G = geo.Grid(S)
+    L = np.log(geo.c_diag(G, 0)[1])
+    errs = []
+    for sw in (1, 2, 4, 8, 12):
+        f = geo.separable_fit(np.exp(L), sweeps=sw)
+        errs.append(np.abs(L - f[0][:, None, None] - f[1][None, :, None] - f[2][None, None, :]).max())
+    assert all(b <= a * (1 + 1e-12) for a, b in zip(errs, errs[1:]))
+
+
+def test_cube_limit_weighted_pencils_equal_plain():
+    S = _S(3, 2)
+    G = geo.Grid(S, amp=0.0, nu_const=1.0)
+    pdg = geo.PDG(S, G)
+    for k in range(3):
+        Ks, Ms, _ = pdg.pencils[k]
+        K0, M0, coef = stokes.pv_pencils(S, k)
+        for d in range(3):
+            np.testing.assert_allclose(Ks[d], coef[d] * K0[d], rtol=1e-12, atol=1e-12)
+            np.testing.assert_allclose(Ms[d], M0[d], rtol=1e-12, atol=1e-13)
+        np.testing.assert_allclose(pdg.DV[k], 1.0, rtol=1e-12)
+    np.testing.assert_allclose(pdg.DQ, 1.0, rtol=1e-12)
+    r = np.random.default_rng(2).standard_normal(S.n_total)
+    np.testing.assert_allclose(pdg.apply(r), stokes.apply_PD_inv(S, r), rtol=1e-10, atol=1e-12)
+
+
+def test_scaled_diagonals_match_operator_diagonals():
+    """diag(P_V^G) = diag(A) and diag(P_Q^G) = diag(Q) by construction (Sec. 6)."""
+    S = _S(2, 1)
+    G = geo.Grid(S)
+    pdg = geo.PDG(S, G)
+    A, _ = geo.brute_force(S, G)
+    nv = S.block_sizes[0]
+    for k in range(3):
+        Ks, Ms, _ = pdg.pencils[k]
+        Pk = kron.kron_sum_matrix(Ks, Ms, [1.0, 1.0, 1.0])
+        PG = np.sqrt(pdg.DV[k])[:, None] * Pk * np.sqrt(pdg.DV[k])[None, :]
+        np.testing.assert_allclose(np.diag(PG), np.diag(A)[k * nv:(k + 1) * nv], rtol=1e-12)
+
+
+def test_theorem2_pressure_mass_bounds():
+    """lambda(P_Q^{-1} Q) lies in [min |det J|/nu, max |det J|/nu] (Theorem 2, Remark)."""
+    S = _S(2, 2)
+    G = geo.Grid(S)
+    T = [G.table(S.pres[d], d, False) for d in range(3)]
+    F = (G.W * np.abs(G.det) / G.nu).reshape(-1)
+    Bq = np.einsum("ap,bq,cr->cbapqr", T[0], T[1], T[2]).reshape(S.block_sizes[3], -1)
+    Q = (Bq * F) @ Bq.T
+    PQ = kron.kron_matrix(stokes.pq_factors(S))
+    lam = np.linalg.eigvals(np.linalg.solve(PQ, Q)).real
+    ratio = np.abs(G.det) / G.nu
+    assert lam.min() >= ratio.min() * (1 - 1e-10)
+    assert lam.max() <= ratio.max() * (1 + 1e-10)
+    np.testing.assert_allclose(np.sort(np.diag(Q)), np.sort(geo.diag_Q(S, G)), rtol=1e-12)
