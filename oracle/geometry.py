@@ -323,3 +323,85 @@ class PDG:
         sq = self.DQ ** -0.5
         out.append(sq * kron.kron_mass_solve(self.Mp, sq * b[3]))
         return np.concatenate(out)
+
+
+def operator_row(S, G, blk, i_multi):
+    """All nonzero entries of one row of the mapped operator, by quadrature of the
+    definitions at the points of the row function's support (sampled checks at
+    full size): velocity row blk < 3 (function e_blk B_i) against every velocity
+    and pressure function, pressure row blk == 3 against every velocity function.
+    Returns {global column index: value}."""
+    off = np.concatenate([[0], np.cumsum(S.block_sizes)])
+    row_space = S.vel[blk] if blk < 3 else S.pres
+    # support points of the row function in each direction
+    sup = []
+    for d in range(3):
+        T = G.table(row_space[d], d, False)
+        Td = G.table(row_space[d], d, True)
+        nz = np.nonzero((np.abs(T[i_multi[d]]) + np.abs(Td[i_multi[d]])) > 0)[0]
+        sup.append(nz)
+    ix = np.ix_(sup[0], sup[1], sup[2])
+    Jinv = G.Jinv[ix]
+    wd = (G.W * G.det)[ix]
+    nu = G.nu[ix]
+
+    def fields(space3, m, deriv_dir):
+        v = 1.0
+        for d in range(3):
+            T = G.table(space3[d], d, deriv_dir == d)[m[d]][sup[d]]
+            sh = [1, 1, 1]
+            sh[d] = -1
+            v = v * T.reshape(sh)
+        return v
+
+    def grad_x(space3, m):
+        ge = np.stack([fields(space3, m, a) for a in range(3)], axis=-1)
+        return np.einsum("...a,...ac->...c", ge, Jinv)
+
+    def candidates(space3):
+        out = []
+        for d in range(3):
+            T = G.table(space3[d], d, False)
+            Td = G.table(space3[d], d, True)
+            act = np.nonzero(((np.abs(T[:, sup[d]]) + np.abs(Td[:, sup[d]])) > 0).any(axis=1))[0]
+            out.append(act)
+        return out
+
+    res = {}
+    if blk < 3:
+        gi = grad_x(S.vel[blk], i_multi)
+        for s in range(3):
+            c = candidates(S.vel[s])
+            for j3 in c[2]:
+                for j2 in c[1]:
+                    for j1 in c[0]:
+                        gj = grad_x(S.vel[s], (j1, j2, j3))
+                        # 2 nu grad^s(e_blk B_i) : grad^s(e_s B_j) = nu (delta gi.gj + d_s B_i d_blk B_j)
+                        Gw = np.zeros(gi.shape[:-1] + (3, 3))
+                        Gw[..., blk, :] = gi
+                        Gv = np.zeros(gi.shape[:-1] + (3, 3))
+                        Gv[..., s, :] = gj
+                        Sw = 0.5 * (Gw + np.swapaxes(Gw, -1, -2))
+                        Sv = 0.5 * (Gv + np.swapaxes(Gv, -1, -2))
+                        v = np.sum(wd * 2 * nu * np.einsum("...ab,...ab->...", Sw, Sv))
+                        col = off[s] + (j3 * S.vel[s][1].n + j2) * S.vel[s][0].n + j1
+                        res[int(col)] = v
+        c = candidates(S.pres)
+        for l3 in c[2]:
+            for l2 in c[1]:
+                for l1 in c[0]:
+                    v = -np.sum(wd * fields(S.pres, (l1, l2, l3), -1) * gi[..., blk])
+                    col = off[3] + (l3 * S.pres[1].n + l2) * S.pres[0].n + l1
+                    res[int(col)] = v
+    else:
+        rho = fields(S.pres, i_multi, -1)
+        for r in range(3):
+            c = candidates(S.vel[r])
+            for j3 in c[2]:
+                for j2 in c[1]:
+                    for j1 in c[0]:
+                        gj = grad_x(S.vel[r], (j1, j2, j3))
+                        v = -np.sum(wd * rho * gj[..., r])
+                        col = off[r] + (j3 * S.vel[r][1].n + j2) * S.vel[r][0].n + j1
+                        res[int(col)] = v
+    return res

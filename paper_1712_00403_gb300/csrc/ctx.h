@@ -1,0 +1,137 @@
+// The handle (fdst_ctx) and allocation helpers shared by the C ABI files.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "geometry.h"
+#include "internal.h"
+#include "kernels.h"
+#include "kernels_tc.h"
+
+#define CK(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) {                                                          \
+      set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                  \
+      return FDST_CUDA_ERROR;                                                         \
+    }                                                                                 \
+  } while (0)
+
+namespace fdst {
+
+// ------------------------------------------------------------------ handle
+
+struct FdChain {
+  int nsteps = 0;
+  int div_step = -1;
+  const double *B[6] = {};
+  const float *Bt[6] = {};     // split-TF32 operand of the same step (pre-split, padded)
+  std::vector<double> Bh[6];   // host copy of B (K x N row-major) for the packing
+  int R[6] = {}, K[6] = {}, N[6] = {};
+  double *lam_row = nullptr, *lam_col = nullptr;
+  float *lam_row_f = nullptr, *lam_col_f = nullptr;
+  const double *scale = nullptr;  // D^{-1/2} of P^G (nullptr: identity)
+  int64_t off = 0, size = 0;
+};
+
+struct BandDev {
+  int rows, cols, w;
+  double *vals;
+  int *lo;
+  float2 *vals_df;   // the same values split into FP32 pairs (double-float matvec)
+};
+
+struct PlanOp {
+  int stage;
+  int in_kind, in_id;    // kind: 0 = user x block, 1 = T1 buffer, 2 = G buffer
+  int out_kind, out_id;  // kind: 1 = T1, 2 = G, 3 = user y block
+  int band;
+  int mode;
+  int dims[3];           // input dims
+  double coef;
+  int accumulate;
+};
+
+}  // namespace fdst
+
+struct fdst_ctx {
+  fdst_desc desc{};
+  int dim = 0, p = 0;
+  std::vector<std::vector<double>> knots;
+  std::vector<fdst::Space1D> pres;
+  std::vector<std::vector<fdst::Space1D>> vel;
+  int nblocks = 0;
+  int shape[4][3] = {};
+  int64_t off[5] = {};
+  int64_t n_total = 0;
+  int max_rhs = 1;
+  std::vector<void *> allocs;
+  int64_t device_bytes = 0;
+  // FD
+  std::vector<fdst::FdChain> chains;
+  double *work[2] = {nullptr, nullptr};
+  float *work_f[2] = {nullptr, nullptr};
+  std::vector<int64_t> f_off;   // per-chain offset in the padded FP32 workspace
+  int64_t f_total = 0;          // padded FP32 workspace per right-hand side
+  // matvec
+  std::vector<fdst::BandDev> bands;
+  std::vector<fdst::PlanOp> plan;
+  std::vector<double *> t1, g;
+  std::vector<int64_t> t1_size, g_size;
+  float2 *x2 = nullptr, *y2 = nullptr;   // double-float copies of the matvec input / output
+  // MINRES
+  double *v = nullptr, *v_old = nullptr, *z = nullptr, *z_new = nullptr, *Az = nullptr, *w = nullptr,
+         *w_old = nullptr;
+  double *partials = nullptr, *dots = nullptr;
+  unsigned *counters = nullptr;
+  fdst::MinresState *state = nullptr;
+  int *done = nullptr, *n_stopped = nullptr;
+  int *h_n_stopped = nullptr;
+  double *h_dots = nullptr;
+  double *hb = nullptr, *hx = nullptr;  // device buffers for the host-pointer entry points
+  // mapped geometry (CSR operator, weighted pencils of P_D^G)
+  bool mapped = false;
+  fdst::CsrDev csr;
+  std::vector<std::vector<fdst::Mat>> geo_K, geo_M;   // [component][direction]
+  std::vector<std::vector<double>> geo_scale;          // D^{-1/2} per block (P_D^G)
+  // timing
+  int timing = 0;
+  double ms_matvec = 0, ms_prec = 0, ms_vector = 0;
+  int64_t n_matvec = 0, n_prec = 0;
+};
+
+namespace fdst {
+
+template <typename T>
+inline fdst_status dalloc(fdst_ctx *h, T **p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    *p = nullptr;
+    return e == cudaErrorMemoryAllocation ? FDST_OUT_OF_MEMORY : FDST_CUDA_ERROR;
+  }
+  h->allocs.push_back((void *)*p);
+  h->device_bytes += (int64_t)(count * sizeof(T));
+  return FDST_OK;
+}
+
+template <typename T>
+inline fdst_status upload(fdst_ctx *h, T **p, const std::vector<T> &v) {
+  fdst_status st = dalloc(h, p, v.size());
+  if (st != FDST_OK) return st;
+  CK(cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return FDST_OK;
+}
+
+#define TRY(x)                           \
+  do {                                   \
+    fdst_status s_ = (x);                \
+    if (s_ != FDST_OK) return s_;        \
+  } while (0)
+
+}  // namespace fdst

@@ -14,130 +14,13 @@
 #include <string>
 #include <vector>
 
-#include "internal.h"
-#include "kernels.h"
-#include "kernels_tc.h"
+#include "ctx.h"
+#include "mapped.h"
 
 namespace fdst {
 
 static thread_local std::string g_err;
 void set_error(const std::string &s) { g_err = s; }
-
-#define CK(call)                                                                      \
-  do {                                                                                \
-    cudaError_t e_ = (call);                                                          \
-    if (e_ != cudaSuccess) {                                                          \
-      set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                  \
-      return FDST_CUDA_ERROR;                                                         \
-    }                                                                                 \
-  } while (0)
-
-// ------------------------------------------------------------------ handle
-
-struct FdChain {
-  int nsteps = 0;
-  int div_step = -1;
-  const double *B[6] = {};
-  const float *Bt[6] = {};     // split-TF32 operand of the same step (pre-split, padded)
-  std::vector<double> Bh[6];   // host copy of B (K x N row-major) for the packing
-  int R[6] = {}, K[6] = {}, N[6] = {};
-  double *lam_row = nullptr, *lam_col = nullptr;
-  float *lam_row_f = nullptr, *lam_col_f = nullptr;
-  const double *scale = nullptr;  // D^{-1/2} of P^G (nullptr: identity)
-  int64_t off = 0, size = 0;
-};
-
-struct BandDev {
-  int rows, cols, w;
-  double *vals;
-  int *lo;
-  float2 *vals_df;   // the same values split into FP32 pairs (double-float matvec)
-};
-
-struct PlanOp {
-  int stage;
-  int in_kind, in_id;    // kind: 0 = user x block, 1 = T1 buffer, 2 = G buffer
-  int out_kind, out_id;  // kind: 1 = T1, 2 = G, 3 = user y block
-  int band;
-  int mode;
-  int dims[3];           // input dims
-  double coef;
-  int accumulate;
-};
-
-}  // namespace fdst
-
-struct fdst_ctx {
-  fdst_desc desc{};
-  int dim = 0, p = 0;
-  std::vector<std::vector<double>> knots;
-  std::vector<fdst::Space1D> pres;
-  std::vector<std::vector<fdst::Space1D>> vel;
-  int nblocks = 0;
-  int shape[4][3] = {};
-  int64_t off[5] = {};
-  int64_t n_total = 0;
-  int max_rhs = 1;
-  std::vector<void *> allocs;
-  int64_t device_bytes = 0;
-  // FD
-  std::vector<fdst::FdChain> chains;
-  double *work[2] = {nullptr, nullptr};
-  float *work_f[2] = {nullptr, nullptr};
-  std::vector<int64_t> f_off;   // per-chain offset in the padded FP32 workspace
-  int64_t f_total = 0;          // padded FP32 workspace per right-hand side
-  // matvec
-  std::vector<fdst::BandDev> bands;
-  std::vector<fdst::PlanOp> plan;
-  std::vector<double *> t1, g;
-  std::vector<int64_t> t1_size, g_size;
-  float2 *x2 = nullptr, *y2 = nullptr;   // double-float copies of the matvec input / output
-  // MINRES
-  double *v = nullptr, *v_old = nullptr, *z = nullptr, *z_new = nullptr, *Az = nullptr, *w = nullptr,
-         *w_old = nullptr;
-  double *partials = nullptr, *dots = nullptr;
-  unsigned *counters = nullptr;
-  fdst::MinresState *state = nullptr;
-  int *done = nullptr, *n_stopped = nullptr;
-  int *h_n_stopped = nullptr;
-  double *h_dots = nullptr;
-  double *hb = nullptr, *hx = nullptr;  // device buffers for the host-pointer entry points
-  // timing
-  int timing = 0;
-  double ms_matvec = 0, ms_prec = 0, ms_vector = 0;
-  int64_t n_matvec = 0, n_prec = 0;
-};
-
-namespace fdst {
-
-template <typename T>
-static fdst_status dalloc(fdst_ctx *h, T **p, size_t count) {
-  *p = nullptr;
-  if (count == 0) count = 1;
-  cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
-  if (e != cudaSuccess) {
-    set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
-    *p = nullptr;
-    return e == cudaErrorMemoryAllocation ? FDST_OUT_OF_MEMORY : FDST_CUDA_ERROR;
-  }
-  h->allocs.push_back((void *)*p);
-  h->device_bytes += (int64_t)(count * sizeof(T));
-  return FDST_OK;
-}
-
-template <typename T>
-static fdst_status upload(fdst_ctx *h, T **p, const std::vector<T> &v) {
-  fdst_status st = dalloc(h, p, v.size());
-  if (st != FDST_OK) return st;
-  CK(cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
-  return FDST_OK;
-}
-
-#define TRY(x)                           \
-  do {                                   \
-    fdst_status s_ = (x);                \
-    if (s_ != FDST_OK) return s_;        \
-  } while (0)
 
 static std::string space_key(const Space1D &s) {
   std::ostringstream o;
@@ -243,9 +126,12 @@ static fdst_status build_fd(fdst_ctx *h) {
     for (int e = 0; e < dim; ++e) {
       const Space1D &s = h->vel[k][e];
       std::string key = space_key(s);
+      const bool geo = h->desc.variant == FDST_VARIANT_PD_GEO;
+      if (geo) key = "geo" + std::to_string(k) + "_" + std::to_string(e) + "_" + key;
       auto it = eig_cache.find(key);
       if (it == eig_cache.end()) {
-        Mat K = stiffness_matrix(s, npts), M = mixed_matrix(s, 0, s, 0, npts);
+        Mat K = geo ? h->geo_K[k][e] : stiffness_matrix(s, npts);
+        Mat M = geo ? h->geo_M[k][e] : mixed_matrix(s, 0, s, 0, npts);
         std::vector<double> l;
         Mat U;
         if (!gen_eig(K, M, l, U)) {
@@ -262,8 +148,10 @@ static fdst_status build_fd(fdst_ctx *h) {
       Ubh[e] = Ut.a;
     }
     const int n1 = h->shape[k][0], n2 = h->shape[k][1], n3 = h->shape[k][2];
+    // c_{k,d} = 2 for d = k in P_{V,k} (eq. prec3D_TH); the weighted pencils of P~_V carry
+    // that factor inside C_k (Appendix), so their coefficients are all 1
     double cf[3];
-    for (int e = 0; e < 3; ++e) cf[e] = (e == k) ? 2.0 : 1.0;
+    for (int e = 0; e < 3; ++e) cf[e] = (e == k && h->desc.variant != FDST_VARIANT_PD_GEO) ? 2.0 : 1.0;
     std::vector<double> lr, lc;
     if (dim == 3) {
       c.nsteps = 6;
@@ -680,6 +568,11 @@ static fdst_status run_matvec_df(fdst_ctx *h, const double *x, double *y, int nr
 // exact = true forces the FP64 (DFMA) evaluation (true-residual checks).
 static fdst_status run_matvec(fdst_ctx *h, const double *x, double *y, int nrhs, const int *done, cudaStream_t st,
                               bool exact = false) {
+  if (h->mapped) {
+    launch_spmv(h->csr, x, y, h->n_total, nrhs, done, st);
+    CK(cudaGetLastError());
+    return FDST_OK;
+  }
   if (!exact && h->desc.matvec_precision == FDST_MV_DF64) return run_matvec_df(h, x, y, nrhs, done, st);
   return run_matvec_f64(h, x, y, nrhs, done, st);
 }
@@ -719,8 +612,16 @@ fdst_status fdst_setup(const fdst_desc *desc, fdst_handle *out) {
   }
   if (desc->degree < 1 || desc->degree > 12) { set_error("degree must be in [1, 12]"); return FDST_INVALID_ARGUMENT; }
   if (desc->max_rhs < 1) { set_error("max_rhs must be >= 1"); return FDST_INVALID_ARGUMENT; }
-  if (desc->geometry != FDST_GEOM_IDENTITY || desc->variant != FDST_VARIANT_PD) {
-    set_error("mapped geometry / P_D^G not available in this build");
+  if (desc->geometry != FDST_GEOM_IDENTITY && desc->geometry != FDST_GEOM_SINE_BUMP) {
+    set_error("unknown geometry");
+    return FDST_INVALID_ARGUMENT;
+  }
+  if (desc->variant != FDST_VARIANT_PD && desc->variant != FDST_VARIANT_PD_GEO) {
+    set_error("unknown preconditioner variant");
+    return FDST_INVALID_ARGUMENT;
+  }
+  if (desc->variant == FDST_VARIANT_PD_GEO && desc->geometry == FDST_GEOM_IDENTITY) {
+    set_error("P_D^G is built for the mapped geometry (on the identity map it equals P_D)");
     return FDST_NOT_SUPPORTED;
   }
   if (desc->matvec_precision != FDST_MV_F64 && desc->matvec_precision != FDST_MV_DF64) {
@@ -749,11 +650,13 @@ fdst_status fdst_setup(const fdst_desc *desc, fdst_handle *out) {
   fdst_status st;
   auto fail = [&](fdst_status s) { fdst_destroy(h.release()); return s; };
   if ((st = build_spaces(hp)) != FDST_OK) return fail(st);
+  if (desc->geometry == FDST_GEOM_SINE_BUMP && (st = build_mapped_pre(hp)) != FDST_OK) return fail(st);
   if ((st = build_fd(hp)) != FDST_OK) return fail(st);
+  if (hp->mapped && (st = build_mapped_post(hp)) != FDST_OK) return fail(st);
   if (desc->fd_precision == FDST_FD_TF32X3) {
     if ((st = tc_prepare(hp)) != FDST_OK) return fail(st);
   }
-  if ((st = build_matvec(hp)) != FDST_OK) return fail(st);
+  if (!hp->mapped && (st = build_matvec(hp)) != FDST_OK) return fail(st);
   const size_t nv = (size_t)hp->n_total * hp->max_rhs;
   if ((st = dalloc(hp, &hp->work[0], nv)) != FDST_OK) return fail(st);
   if ((st = dalloc(hp, &hp->work[1], nv)) != FDST_OK) return fail(st);
@@ -798,7 +701,7 @@ fdst_status fdst_get_sizes(fdst_handle h, fdst_sizes *out) {
     fa += 2.0 * (double)c.size * sum_n;   // each step: 2 K N R flops with K = N = n_d, R N = size
   }
   out->flops_apply = fa;
-  double fm = 0.0;
+  double fm = h->mapped ? 2.0 * (double)h->csr.nnz : 0.0;
   for (auto &op : h->plan) {
     int od[3] = {op.dims[0], op.dims[1], op.dims[2]};
     od[op.mode] = h->bands[op.band].rows;

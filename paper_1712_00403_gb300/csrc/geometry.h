@@ -1,0 +1,62 @@
+// Mapped-geometry kernels: quadrature-point geometry, separable fit, weighted
+// pressure-mass diagonal, CSR structure / assembly / SpMV.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/fdst.h"
+
+namespace fdst {
+
+// Geometry at the tensor grid of quadrature points (q1 fastest); device arrays.
+struct GeoPoints {
+  int nq[3] = {0, 0, 0};
+  const double *pts[3] = {}, *wts[3] = {};
+  int64_t Q = 0;
+  double *jinv = nullptr;   // 9 x Q, (J^{-1})_{ij} at [(3i + j) Q + q]
+  double *det = nullptr;    // Q
+  double *nu = nullptr;     // Q
+};
+
+// Per-direction element tables (device arrays) for TH velocity (degree p+1,
+// interior indices) and pressure (degree p).
+struct MeshTables {
+  int ne[3] = {0, 0, 0}, nq = 0, p = 0, np[3] = {0, 0, 0};
+  const int *v_first[3] = {}, *p_first[3] = {};   // first global function index nonzero on element e
+  const int *p_elo[3] = {}, *p_ehi[3] = {};       // element range of pressure function l
+  const double *vtab[3] = {};   // [(e (p+2) + i) nq + a] * 2 + der : value / derivative of local velocity fn i
+  const double *ptab[3] = {};   // [(e (p+1) + l) nq + a]
+};
+
+// CSR layout tables: velocity row (r, i): [3 velocity boxes][pressure box];
+// pressure row l: [3 velocity boxes]; boxes are products of per-direction ranges.
+struct CsrTables {
+  int64_t off[5] = {0, 0, 0, 0, 0};
+  int nv[3] = {0, 0, 0}, np[3] = {0, 0, 0};
+  const int64_t *row_ptr = nullptr;
+  const int *vv_lo[3] = {}, *vv_w[3] = {};
+  const int *vp_lo[3] = {}, *vp_w[3] = {};
+  const int *pv_lo[3] = {}, *pv_w[3] = {};
+};
+
+struct CsrDev {
+  const int64_t *row_ptr = nullptr;
+  const int *col = nullptr;
+  const double *val = nullptr;
+  int64_t nrows = 0, nnz = 0;
+};
+
+void launch_geo_points(const GeoPoints &gp, double amp, cudaStream_t s);
+void launch_logc(const GeoPoints &gp, double *L, cudaStream_t s);
+void launch_fit_sweep(const double *L, double *f, int d, const GeoPoints &gp, int fstride, cudaStream_t s);
+void launch_diag_q(const GeoPoints &gp, const MeshTables &mt, double *dq, cudaStream_t s);
+void launch_csr_cols(const CsrTables &ct, int *col, cudaStream_t s);
+size_t assemble_smem_bytes(int p);
+fdst_status launch_assemble(const GeoPoints &gp, const MeshTables &mt, const CsrTables &ct, double *val,
+                            cudaStream_t s);
+void launch_spmv(const CsrDev &A, const double *x, double *y, int64_t stride, int nrhs, const int *done,
+                 cudaStream_t s);
+void launch_csr_diag(const CsrDev &A, double *d, cudaStream_t s);
+
+}  // namespace fdst

@@ -111,7 +111,7 @@ void span_rule(const std::vector<double> &t, int npts, std::vector<double> &x, s
 // span s (t[s] <= x < t[s+1], last nonzero span closed at 1); N[j], dN[j] are
 // the values of b_{s-p+j}, j = 0..p. Triangular Cox-de Boor scheme with the
 // degree p-1 values kept for the derivative formula.
-static int eval_nonzero(const std::vector<double> &t, int p, double x, double *N, double *dN) {
+int eval_nonzero(const std::vector<double> &t, int p, double x, double *N, double *dN) {
   int m = (int)t.size() - p - 1;
   int s;
   if (x >= t[m]) {

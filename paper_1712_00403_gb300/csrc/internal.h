@@ -43,6 +43,10 @@ std::vector<double> elevate(const std::vector<double> &t);
 // Interior multiplicity of the first interior breakpoint (1 if none).
 int inner_multiplicity(const std::vector<double> &t);
 
+// Nonzero B-splines of degree p at x (and derivatives): returns the span s;
+// N[j], dN[j] belong to function s - p + j, j = 0..p.
+int eval_nonzero(const std::vector<double> &t, int p, double x, double *N, double *dN);
+
 // Gauss-Legendre rule with n points on [-1,1] (Newton on P_n).
 void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w);
 

@@ -1,0 +1,292 @@
+// Setup of the mapped-geometry case (3D, Taylor-Hood): geometry at the
+// quadrature points, separable approximation of diag(C_k) (Appendix) and the
+// weighted pencils of P~_V, the assembled FP64 CSR operator (Sec. 3 forms on
+// the mapped domain) and the diagonal scalings D_V, D_Q of P_D^G (Sec. 6).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "ctx.h"
+#include "mapped.h"
+
+namespace fdst {
+
+namespace {
+constexpr double kAmp = 0.1;     // sine-bump amplitude of the map
+constexpr int kSweeps = 12;      // Diliberto-Straus sweeps
+
+// element ranges [lo, hi] of every function of a space with the given knot vector / degree
+void element_ranges(const std::vector<double> &t, int deg, int ne, const std::vector<int> &first_of_elem,
+                    std::vector<int> &elo, std::vector<int> &ehi) {
+  const int m = (int)t.size() - deg - 1;
+  elo.assign(m, ne);
+  ehi.assign(m, -1);
+  for (int e = 0; e < ne; ++e)
+    for (int j = 0; j <= deg; ++j) {
+      const int g = first_of_elem[e] + j;
+      elo[g] = std::min(elo[g], e);
+      ehi[g] = std::max(ehi[g], e);
+    }
+}
+
+// column range (in the index space of "cols", restricted to [c0, c0 + nc)) of functions
+// whose element ranges intersect that of each row function
+void overlap_ranges(const std::vector<int> &relo, const std::vector<int> &rehi, int r0, int nr,
+                    const std::vector<int> &celo, const std::vector<int> &cehi, int c0, int nc, std::vector<int> &lo,
+                    std::vector<int> &w) {
+  lo.assign(nr, 0);
+  w.assign(nr, 0);
+  for (int i = 0; i < nr; ++i) {
+    int a = -1, b = -2;
+    for (int j = 0; j < nc; ++j) {
+      const bool ov = celo[c0 + j] <= rehi[r0 + i] && relo[r0 + i] <= cehi[c0 + j];
+      if (ov) {
+        if (a < 0) a = j;
+        b = j;
+      }
+    }
+    lo[i] = a < 0 ? 0 : a;
+    w[i] = a < 0 ? 0 : b - a + 1;
+  }
+}
+}  // namespace
+
+fdst_status build_mapped_pre(fdst_ctx *h) {
+  if (h->dim != 3 || h->desc.discretization != FDST_TH) {
+    set_error("the mapped geometry is built for the 3D Taylor-Hood discretization");
+    return FDST_NOT_SUPPORTED;
+  }
+  if (h->p > 3) {
+    set_error("mapped-geometry assembly supports pressure degree p <= 3 (element matrices in shared memory)");
+    return FDST_NOT_SUPPORTED;
+  }
+  if (h->desc.matvec_precision != FDST_MV_F64) {
+    set_error("the assembled CSR operator is evaluated in FP64 only");
+    return FDST_NOT_SUPPORTED;
+  }
+  h->mapped = true;
+  const int p = h->p, q = p + 1, nq = p + 2;
+  cudaStream_t st = 0;
+  // ---- quadrature grid and geometry at the points
+  GeoPoints gp;
+  std::vector<std::vector<double>> px(3), pw(3);
+  for (int d = 0; d < 3; ++d) {
+    span_rule(h->pres[d].knots, nq, px[d], pw[d]);
+    gp.nq[d] = (int)px[d].size();
+    double *dp = nullptr, *dw = nullptr;
+    TRY(upload(h, &dp, px[d]));
+    TRY(upload(h, &dw, pw[d]));
+    gp.pts[d] = dp;
+    gp.wts[d] = dw;
+  }
+  gp.Q = (int64_t)gp.nq[0] * gp.nq[1] * gp.nq[2];
+  TRY(dalloc(h, &gp.jinv, (size_t)9 * gp.Q));
+  TRY(dalloc(h, &gp.det, (size_t)gp.Q));
+  TRY(dalloc(h, &gp.nu, (size_t)gp.Q));
+  launch_geo_points(gp, kAmp, st);
+  // ---- separable fit of the 9 diagonal coefficients c^k_jj (log, midrange sweeps)
+  const int fstride = std::max(gp.nq[0], std::max(gp.nq[1], gp.nq[2]));
+  double *L = nullptr, *f = nullptr;
+  CK(cudaMalloc(&L, sizeof(double) * 9 * gp.Q));
+  if (cudaMalloc(&f, sizeof(double) * 27 * fstride) != cudaSuccess) {
+    cudaFree(L);
+    set_error("cudaMalloc failed for the separable fit");
+    return FDST_OUT_OF_MEMORY;
+  }
+  cudaMemset(f, 0, sizeof(double) * 27 * fstride);
+  launch_logc(gp, L, st);
+  for (int sw = 0; sw < kSweeps; ++sw)
+    for (int d = 0; d < 3; ++d) launch_fit_sweep(L, f, d, gp, fstride, st);
+  std::vector<double> fh((size_t)27 * fstride);
+  cudaError_t e1 = cudaMemcpy(fh.data(), f, sizeof(double) * fh.size(), cudaMemcpyDeviceToHost);
+  cudaFree(L);
+  cudaFree(f);
+  if (e1 != cudaSuccess) {
+    set_error(std::string("separable fit: ") + cudaGetErrorString(e1));
+    return FDST_CUDA_ERROR;
+  }
+  // normalize each fit: the two non-own factors get zero mean log, the constant goes to the own one;
+  // tau^k_d = exp(f^{k,d}_d), mu^k_d = exp(mean over j != d of f^{k,j}_d)
+  auto F = [&](int k, int j, int d) -> double * { return fh.data() + (size_t)((3 * k + j) * 3 + d) * fstride; };
+  for (int k = 0; k < 3; ++k)
+    for (int j = 0; j < 3; ++j)
+      for (int d = 0; d < 3; ++d) {
+        if (d == j) continue;
+        double m = 0.0;
+        for (int t = 0; t < gp.nq[d]; ++t) m += F(k, j, d)[t];
+        m /= gp.nq[d];
+        for (int t = 0; t < gp.nq[d]; ++t) F(k, j, d)[t] -= m;
+        for (int t = 0; t < gp.nq[j]; ++t) F(k, j, j)[t] += m;
+      }
+  h->geo_K.assign(3, std::vector<Mat>(3));
+  h->geo_M.assign(3, std::vector<Mat>(3));
+  for (int k = 0; k < 3; ++k)
+    for (int d = 0; d < 3; ++d) {
+      std::vector<double> tau(gp.nq[d]), mu(gp.nq[d]);
+      for (int t = 0; t < gp.nq[d]; ++t) {
+        tau[t] = std::exp(F(k, d, d)[t]);
+        double s = 0.0;
+        for (int j = 0; j < 3; ++j)
+          if (j != d) s += F(k, j, d)[t];
+        mu[t] = std::exp(0.5 * s);
+      }
+      h->geo_K[k][d] = stiffness_matrix(h->vel[k][d], nq, tau);
+      h->geo_M[k][d] = mixed_matrix(h->vel[k][d], 0, h->vel[k][d], 0, nq, mu);
+    }
+  // ---- element tables per direction
+  MeshTables mt;
+  mt.nq = nq;
+  mt.p = p;
+  std::vector<std::vector<int>> vfirst(3), pfirst(3), velo(3), vehi(3), pelo(3), pehi(3);
+  for (int d = 0; d < 3; ++d) {
+    const Space1D &sv = h->vel[0][d], &sp = h->pres[d];
+    const int ne = gp.nq[d] / nq;
+    mt.ne[d] = ne;
+    mt.np[d] = sp.n;
+    std::vector<double> vt((size_t)ne * (q + 1) * nq * 2), pt((size_t)ne * (p + 1) * nq);
+    vfirst[d].resize(ne);
+    pfirst[d].resize(ne);
+    double N[32], dN[32];
+    for (int e = 0; e < ne; ++e)
+      for (int a = 0; a < nq; ++a) {
+        const double x = px[d][(size_t)e * nq + a];
+        int s = eval_nonzero(sv.knots, q, x, N, dN);
+        vfirst[d][e] = s - q;
+        for (int i = 0; i <= q; ++i) {
+          vt[(((size_t)e * (q + 1) + i) * nq + a) * 2 + 0] = N[i];
+          vt[(((size_t)e * (q + 1) + i) * nq + a) * 2 + 1] = dN[i];
+        }
+        s = eval_nonzero(sp.knots, p, x, N, dN);
+        pfirst[d][e] = s - p;
+        for (int l = 0; l <= p; ++l) pt[((size_t)e * (p + 1) + l) * nq + a] = N[l];
+      }
+    element_ranges(sv.knots, q, ne, vfirst[d], velo[d], vehi[d]);
+    element_ranges(sp.knots, p, ne, pfirst[d], pelo[d], pehi[d]);
+    double *dvt = nullptr, *dpt = nullptr;
+    int *a1 = nullptr, *a2 = nullptr, *a3 = nullptr, *a4 = nullptr;
+    TRY(upload(h, &dvt, vt));
+    TRY(upload(h, &dpt, pt));
+    TRY(upload(h, &a1, vfirst[d]));
+    TRY(upload(h, &a2, pfirst[d]));
+    TRY(upload(h, &a3, pelo[d]));
+    TRY(upload(h, &a4, pehi[d]));
+    mt.vtab[d] = dvt;
+    mt.ptab[d] = dpt;
+    mt.v_first[d] = a1;
+    mt.p_first[d] = a2;
+    mt.p_elo[d] = a3;
+    mt.p_ehi[d] = a4;
+  }
+  // ---- CSR layout
+  CsrTables ct;
+  for (int b = 0; b < 5; ++b) ct.off[b] = h->off[b];
+  std::vector<std::vector<int>> vvlo(3), vvw(3), vplo(3), vpw(3), pvlo(3), pvw(3);
+  for (int d = 0; d < 3; ++d) {
+    const int nv = h->vel[0][d].n, np = h->pres[d].n;
+    ct.nv[d] = nv;
+    ct.np[d] = np;
+    overlap_ranges(velo[d], vehi[d], 1, nv, velo[d], vehi[d], 1, nv, vvlo[d], vvw[d]);
+    overlap_ranges(velo[d], vehi[d], 1, nv, pelo[d], pehi[d], 0, np, vplo[d], vpw[d]);
+    overlap_ranges(pelo[d], pehi[d], 0, np, velo[d], vehi[d], 1, nv, pvlo[d], pvw[d]);
+    int *t[6];
+    TRY(upload(h, &t[0], vvlo[d]));
+    TRY(upload(h, &t[1], vvw[d]));
+    TRY(upload(h, &t[2], vplo[d]));
+    TRY(upload(h, &t[3], vpw[d]));
+    TRY(upload(h, &t[4], pvlo[d]));
+    TRY(upload(h, &t[5], pvw[d]));
+    ct.vv_lo[d] = t[0]; ct.vv_w[d] = t[1];
+    ct.vp_lo[d] = t[2]; ct.vp_w[d] = t[3];
+    ct.pv_lo[d] = t[4]; ct.pv_w[d] = t[5];
+  }
+  const int64_t nrows = h->n_total;
+  std::vector<int64_t> rp(nrows + 1, 0);
+  for (int r = 0; r < 3; ++r)
+    for (int i3 = 0; i3 < ct.nv[2]; ++i3)
+      for (int i2 = 0; i2 < ct.nv[1]; ++i2)
+        for (int i1 = 0; i1 < ct.nv[0]; ++i1) {
+          const int64_t row = h->off[r] + ((int64_t)i3 * ct.nv[1] + i2) * ct.nv[0] + i1;
+          rp[row + 1] = 3LL * vvw[0][i1] * vvw[1][i2] * vvw[2][i3] + (int64_t)vpw[0][i1] * vpw[1][i2] * vpw[2][i3];
+        }
+  for (int l3 = 0; l3 < ct.np[2]; ++l3)
+    for (int l2 = 0; l2 < ct.np[1]; ++l2)
+      for (int l1 = 0; l1 < ct.np[0]; ++l1) {
+        const int64_t row = h->off[3] + ((int64_t)l3 * ct.np[1] + l2) * ct.np[0] + l1;
+        rp[row + 1] = 3LL * pvw[0][l1] * pvw[1][l2] * pvw[2][l3];
+      }
+  for (int64_t r = 0; r < nrows; ++r) rp[r + 1] += rp[r];
+  const int64_t nnz = rp[nrows];
+  int64_t *drp = nullptr;
+  int *dcol = nullptr;
+  double *dval = nullptr;
+  TRY(upload(h, &drp, rp));
+  TRY(dalloc(h, &dcol, (size_t)nnz));
+  TRY(dalloc(h, &dval, (size_t)nnz));
+  ct.row_ptr = drp;
+  CK(cudaMemsetAsync(dval, 0, sizeof(double) * nnz, st));
+  launch_csr_cols(ct, dcol, st);
+  TRY(launch_assemble(gp, mt, ct, dval, st));
+  h->csr.row_ptr = drp;
+  h->csr.col = dcol;
+  h->csr.val = dval;
+  h->csr.nrows = nrows;
+  h->csr.nnz = nnz;
+  // ---- diagonal scalings of P_D^G: D_V = diag(A) / diag(P~_V), D_Q = diag(Q) / diag(P_Q)
+  h->geo_scale.assign(4, std::vector<double>());
+  if (h->desc.variant == FDST_VARIANT_PD_GEO) {
+    double *dA = nullptr, *dQ = nullptr;
+    TRY(dalloc(h, &dA, (size_t)nrows));
+    TRY(dalloc(h, &dQ, (size_t)(h->off[4] - h->off[3])));
+    launch_csr_diag(h->csr, dA, st);
+    launch_diag_q(gp, mt, dQ, st);
+    std::vector<double> diagA(nrows), diagQ(h->off[4] - h->off[3]);
+    CK(cudaMemcpy(diagA.data(), dA, sizeof(double) * nrows, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(diagQ.data(), dQ, sizeof(double) * diagQ.size(), cudaMemcpyDeviceToHost));
+    for (int k = 0; k < 3; ++k) {
+      const int n1 = h->shape[k][0], n2 = h->shape[k][1], n3 = h->shape[k][2];
+      std::vector<double> &sc = h->geo_scale[k];
+      sc.resize((size_t)n1 * n2 * n3);
+      const Mat *Kf = h->geo_K[k].data(), *Mf = h->geo_M[k].data();
+      for (int i3 = 0; i3 < n3; ++i3)
+        for (int i2 = 0; i2 < n2; ++i2)
+          for (int i1 = 0; i1 < n1; ++i1) {
+            const double dp = Kf[2](i3, i3) * Mf[1](i2, i2) * Mf[0](i1, i1) + Mf[2](i3, i3) * Kf[1](i2, i2) * Mf[0](i1, i1) +
+                              Mf[2](i3, i3) * Mf[1](i2, i2) * Kf[0](i1, i1);
+            const size_t li = ((size_t)i3 * n2 + i2) * n1 + i1;
+            sc[li] = 1.0 / std::sqrt(diagA[h->off[k] + li] / dp);
+          }
+    }
+    {
+      const int n1 = h->shape[3][0], n2 = h->shape[3][1], n3 = h->shape[3][2];
+      std::vector<Mat> Mp(3);
+      for (int d = 0; d < 3; ++d) Mp[d] = mixed_matrix(h->pres[d], 0, h->pres[d], 0, nq);
+      std::vector<double> &sc = h->geo_scale[3];
+      sc.resize((size_t)n1 * n2 * n3);
+      for (int i3 = 0; i3 < n3; ++i3)
+        for (int i2 = 0; i2 < n2; ++i2)
+          for (int i1 = 0; i1 < n1; ++i1) {
+            const size_t li = ((size_t)i3 * n2 + i2) * n1 + i1;
+            const double dp = Mp[2](i3, i3) * Mp[1](i2, i2) * Mp[0](i1, i1);
+            sc[li] = 1.0 / std::sqrt(diagQ[li] / dp);
+          }
+    }
+  }
+  CK(cudaDeviceSynchronize());
+  return FDST_OK;
+}
+
+// Attach the D^{-1/2} scalings of P_D^G to the FD chains (after build_fd).
+fdst_status build_mapped_post(fdst_ctx *h) {
+  if (h->desc.variant != FDST_VARIANT_PD_GEO) return FDST_OK;
+  for (size_t c = 0; c < h->chains.size() && c < h->geo_scale.size(); ++c) {
+    double *d = nullptr;
+    TRY(upload(h, &d, h->geo_scale[c]));
+    h->chains[c].scale = d;
+  }
+  return FDST_OK;
+}
+
+}  // namespace fdst

@@ -1,0 +1,107 @@
+"""Mapped geometry (sine-bump map, variable viscosity) through the C ABI:
+assembled FP64 CSR operator vs. the oracle's sum-factorized quadrature
+matvec (<= 1e-12), P_D^G apply vs. the oracle's (FP64 <= 1e-11: the
+separable fit takes a log on each side; split-TF32 <= 1e-5), P_D^G-MINRES to
+1e-8, and sampled columns of the full-size (32^3, p=3) operator against
+rows computed from the definitions."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import geometry as geo, minres
+
+from _helpers import oracle_problem, problem_spec, rel
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+CASES = [problem_spec(3, 2, 3), problem_spec(3, 3, (2, 3, 4)), problem_spec(3, 1, 4)]
+
+
+def _ids(c):
+    return f"p{c['p']}-{'x'.join(map(str, c['n_el']))}"
+
+
+def _gpu(spec, **kw):
+    import paper_1712_00403_gb300 as fd
+    from _helpers import knots_of
+    return fd.Stokes(knots_of(spec), spec["p"], geometry=fd.GEOM_SINE_BUMP, variant=fd.VARIANT_PD_GEO, **kw)
+
+
+@pytest.mark.parametrize("spec", CASES, ids=_ids)
+def test_csr_matvec_matches_oracle(spec):
+    P = _gpu(spec, max_rhs=2)
+    S = oracle_problem(spec)
+    G = geo.Grid(S)
+    X = np.stack([synth.random_vector(40 + j, P.n_total) for j in range(2)])
+    x = torch.tensor(X.reshape(-1), device="cuda")
+    y = torch.empty_like(x)
+    P.matvec(x, y)
+    out = y.cpu().numpy().reshape(2, -1)
+    for j in range(2):
+        ref = geo.matvec(S, G, X[j])
+        for o0, o1 in zip(P.block_offsets[:-1], P.block_offsets[1:]):
+            assert rel(out[j, o0:o1], ref[o0:o1]) <= 1e-12
+
+
+@pytest.mark.parametrize("spec", CASES, ids=_ids)
+def test_pdg_apply_matches_oracle(spec):
+    import paper_1712_00403_gb300 as fd
+    S = oracle_problem(spec)
+    pdg = geo.PDG(S, geo.Grid(S))
+    r_h = synth.random_vector(7, S.n_total)
+    ref = pdg.apply(r_h)
+    for prec, tol in ((fd.FD_F64, 1e-11), (fd.FD_TF32X3, 1e-5)):
+        P = _gpu(spec, fd_precision=prec)
+        r = torch.tensor(r_h, device="cuda")
+        s = torch.empty_like(r)
+        P.apply_prec(r, s)
+        out = s.cpu().numpy()
+        for o0, o1 in zip(P.block_offsets[:-1], P.block_offsets[1:]):
+            assert rel(out[o0:o1], ref[o0:o1]) <= tol, prec
+
+
+def test_pdg_minres_matches_oracle():
+    import paper_1712_00403_gb300 as fd
+    spec = problem_spec(3, 2, 4)
+    S = oracle_problem(spec)
+    G = geo.Grid(S)
+    pdg = geo.PDG(S, G)
+    b_h = synth.rhs(300, S.block_sizes)
+    _, io = minres.minres(lambda v: geo.matvec(S, G, v), b_h, pdg.apply, tol=1e-8, maxit=600, true_check=True)
+    its = {}
+    for prec in (fd.FD_F64, fd.FD_TF32X3):
+        P = _gpu(spec, fd_precision=prec)
+        b = torch.tensor(b_h, device="cuda")
+        x = torch.zeros_like(b)
+        info = P.solve(b, x, tol=1e-8, maxit=600)[0]
+        assert info["status"] == "OK" and info["true_rel_res"] <= 1e-8
+        its[prec] = info["iterations"]
+    # FP64: the oracle's recurrence; split-TF32: at most 2 iterations more than FP64
+    assert abs(its[fd.FD_F64] - io["iters"]) <= 1, (its, io)
+    assert its[fd.FD_TF32X3] <= its[fd.FD_F64] + 2, its
+
+
+def test_full_size_sampled_columns():
+    """32^3 elements, p = 3 (866,750 DoF): columns A e_j of the assembled
+    operator equal rows of A computed from the definitions (A is symmetric)."""
+    spec = problem_spec(3, 3, 32)
+    P = _gpu(spec)
+    S = oracle_problem(spec)
+    G = geo.Grid(S)
+    off = P.block_offsets
+    samples = [(0, (0, 0, 0)), (1, (31, 17, 64)), (2, (64, 40, 3)), (3, (0, 20, 34)), (3, (17, 17, 17))]
+    for blk, m in samples:
+        sh = P.block_shapes[blk]
+        j = off[blk] + (m[2] * sh[1] + m[1]) * sh[0] + m[0]
+        e = torch.zeros(P.n_total, dtype=torch.float64, device="cuda")
+        e[j] = 1.0
+        col = torch.empty_like(e)
+        P.matvec(e, col)
+        col = col.cpu().numpy()
+        ent = geo.operator_row(S, G, blk, m)
+        ref = np.zeros(P.n_total)
+        for c, v in ent.items():
+            ref[c] = v
+        assert np.abs(col - ref).max() <= 1e-12 * np.abs(ref).max(), (blk, m)

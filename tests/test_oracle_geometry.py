@@ -117,3 +117,25 @@ def test_theorem2_pressure_mass_bounds():
     assert lam.min() >= ratio.min() * (1 - 1e-10)
     assert lam.max() <= ratio.max() * (1 + 1e-10)
     np.testing.assert_allclose(np.sort(np.diag(Q)), np.sort(geo.diag_Q(S, G)), rtol=1e-12)
+
+
+def test_operator_row_vs_brute_force():
+    S = _S(2, 1)
+    G = geo.Grid(S)
+    A, B = geo.brute_force(S, G)
+    nv = 3 * S.block_sizes[0]
+    full = np.zeros((S.n_total, S.n_total))
+    full[:nv, :nv] = A
+    full[nv:, :nv] = B
+    full[:nv, nv:] = B.T
+    n = [S.vel[0][d].n for d in range(3)]
+    npr = [S.pres[d].n for d in range(3)]
+    off = np.concatenate([[0], np.cumsum(S.block_sizes)])
+    for blk, m in [(0, (1, 0, 2)), (2, (2, 2, 0)), (1, (0, 1, 1)), (3, (1, 2, 0)), (3, (0, 0, 0))]:
+        sp = n if blk < 3 else npr
+        row = off[blk] + (m[2] * sp[1] + m[1]) * sp[0] + m[0]
+        ent = geo.operator_row(S, G, blk, m)
+        dense = np.zeros(S.n_total)
+        for c, v in ent.items():
+            dense[c] = v
+        np.testing.assert_allclose(dense, full[row], atol=1e-13 * np.abs(full).max())
