@@ -194,6 +194,27 @@ fdst_status fdst_get_timing(fdst_handle h, double *ms_matvec, double *ms_prec, d
 fdst_status fdst_fd_apply_static(int dim, const int n[3], const double *const d_U[3], const double *const d_lam[3],
                                  const double coef[3], const double *d_r, double *d_s, fdst_stream stream);
 
+/*
+ * Batched solves: many independent problems of uneven sizes, one right-hand
+ * side each, advanced together. Every phase of a MINRES iteration (Stokes
+ * matvec rounds, each FD contraction step, inner products, vector updates)
+ * is one grouped launch over all problems, and one iteration is replayed from
+ * a CUDA graph. The handles must share fd_precision and matvec_precision and
+ * use the identity geometry; a handle may belong to one batch at a time and
+ * must not be used on its own while the batch solves (the batch uses the
+ * handle's workspace). autotune != 0 times the tensor-core pipeline depth and
+ * the banded-kernel block size on the batch's own shapes at creation and
+ * keeps the fastest (fdst_batch_info reports them).
+ */
+typedef struct fdst_batch_ctx *fdst_batch;
+fdst_status fdst_batch_create(const fdst_handle *handles, int n, int autotune, fdst_batch *out);
+/* d_b[i], d_x[i]: device vectors of handle i (x: initial guess in, solution out);
+ * info: n entries. Same stopping rule as fdst_solve; synchronizes the stream. */
+fdst_status fdst_batch_solve(fdst_batch b, const double *const *d_b, double *const *d_x, double tol, int maxit,
+                             fdst_solve_info *info, fdst_stream stream);
+fdst_status fdst_batch_info(fdst_batch b, int *tc_ring, int *band_threads, double *ms_apply, double *ms_matvec);
+fdst_status fdst_batch_destroy(fdst_batch b);
+
 /* Number of CUDA kernels this library has launched in the process so far
  * (diagnostics: lets a caller count the kernels inside a timed region). */
 int64_t fdst_kernel_launches(void);

@@ -54,7 +54,8 @@ class SolveInfo(ctypes.Structure):
 
 ENTRY_POINTS = ["fdst_setup", "fdst_destroy", "fdst_get_sizes", "fdst_apply_prec", "fdst_matvec", "fdst_solve",
                 "fdst_solve_host", "fdst_apply_prec_host", "fdst_set_timing", "fdst_get_timing",
-                "fdst_fd_apply_static", "fdst_device_error", "fdst_kernel_launches", "fdst_last_error"]
+                "fdst_fd_apply_static", "fdst_batch_create", "fdst_batch_solve", "fdst_batch_info",
+                "fdst_batch_destroy", "fdst_device_error", "fdst_kernel_launches", "fdst_last_error"]
 
 _lib = None
 
@@ -78,6 +79,10 @@ def load_library(path=LIB_PATH):
     lib.fdst_apply_prec_host.argtypes = [vp, vp, vp, i, vp]
     lib.fdst_set_timing.argtypes = [vp, i]
     lib.fdst_device_error.argtypes = [ctypes.POINTER(i)]
+    lib.fdst_batch_create.argtypes = [ctypes.POINTER(vp), i, i, ctypes.POINTER(vp)]
+    lib.fdst_batch_solve.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), d, i, ctypes.POINTER(SolveInfo), vp]
+    lib.fdst_batch_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(d), ctypes.POINTER(d)]
+    lib.fdst_batch_destroy.argtypes = [vp]
     lib.fdst_fd_apply_static.argtypes = [i, ctypes.POINTER(i), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                          ctypes.POINTER(d), vp, vp, vp]
     lib.fdst_get_timing.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d),
@@ -239,3 +244,43 @@ class Stokes:
         _check(_lib.fdst_get_timing(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(m),
                                     ctypes.byref(p)))
         return dict(ms_matvec=a.value, ms_prec=b.value, ms_vector=c.value, n_matvec=m.value, n_prec=p.value)
+
+
+class Batch:
+    """Grouped solves of several Stokes problems (fdst_batch_*): every phase of a
+    MINRES iteration is one launch over all problems, replayed from a CUDA graph."""
+
+    def __init__(self, problems, autotune=True):
+        lib = load_library()
+        self.problems = list(problems)
+        hs = (ctypes.c_void_p * len(self.problems))(*[p._h.value for p in self.problems])
+        b = ctypes.c_void_p()
+        _check(lib.fdst_batch_create(hs, len(self.problems), int(autotune), ctypes.byref(b)))
+        self._b = b
+
+    def info(self):
+        r, t, a, m = ctypes.c_int(), ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
+        _check(_lib.fdst_batch_info(self._b, ctypes.byref(r), ctypes.byref(t), ctypes.byref(a), ctypes.byref(m)))
+        return dict(tc_ring=r.value, band_threads=t.value, ms_apply=a.value, ms_matvec=m.value)
+
+    def solve(self, bs, xs, tol=1e-8, maxit=1000, stream=None):
+        n = len(self.problems)
+        bp = (ctypes.c_void_p * n)(*[_dptr(v).value for v in bs])
+        xp = (ctypes.c_void_p * n)(*[_dptr(v).value for v in xs])
+        info = (SolveInfo * n)()
+        code = _lib.fdst_batch_solve(self._b, bp, xp, tol, maxit, info, _stream_ptr(stream))
+        if code not in (0, 5, 6, 7, 9):
+            _check(code)
+        return [dict(iterations=i.iterations, status=STATUS.get(i.status, i.status), eta_rel=i.eta_rel,
+                     true_rel_res=i.true_rel_res) for i in info]
+
+    def close(self):
+        if getattr(self, "_b", None):
+            _lib.fdst_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

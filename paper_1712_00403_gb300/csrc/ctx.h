@@ -134,4 +134,9 @@ inline fdst_status upload(fdst_ctx *h, T **p, const std::vector<T> &v) {
     if (s_ != FDST_OK) return s_;        \
   } while (0)
 
+// Preconditioner apply and matvec of one handle (fdst.cu); exact = true forces FP64.
+fdst_status run_apply(fdst_ctx *h, const double *r, double *s, int nrhs, const int *done, cudaStream_t st);
+fdst_status run_matvec(fdst_ctx *h, const double *x, double *y, int nrhs, const int *done, cudaStream_t st,
+                       bool exact = false);
+
 }  // namespace fdst

@@ -435,7 +435,7 @@ static fdst_status tc_prepare(fdst_ctx *h) {
 
 // ------------------------------------------------------------------ execution
 
-static fdst_status run_apply(fdst_ctx *h, const double *r, double *s, int nrhs, const int *done, cudaStream_t st) {
+fdst_status run_apply(fdst_ctx *h, const double *r, double *s, int nrhs, const int *done, cudaStream_t st) {
   int maxsteps = 0;
   for (auto &c : h->chains) maxsteps = std::max(maxsteps, c.nsteps);
   const bool tc = h->desc.fd_precision != FDST_FD_F64;
@@ -566,8 +566,8 @@ static fdst_status run_matvec_df(fdst_ctx *h, const double *x, double *y, int nr
 }
 
 // exact = true forces the FP64 (DFMA) evaluation (true-residual checks).
-static fdst_status run_matvec(fdst_ctx *h, const double *x, double *y, int nrhs, const int *done, cudaStream_t st,
-                              bool exact = false) {
+fdst_status run_matvec(fdst_ctx *h, const double *x, double *y, int nrhs, const int *done, cudaStream_t st,
+                       bool exact) {
   if (h->mapped) {
     launch_spmv(h->csr, x, y, h->n_total, nrhs, done, st);
     CK(cudaGetLastError());
@@ -722,7 +722,7 @@ fdst_status fdst_matvec(fdst_handle h, const double *d_x, double *d_y, int nrhs,
   if (!h || !d_x || !d_y) { set_error("NULL argument"); return FDST_INVALID_ARGUMENT; }
   if (nrhs < 1 || nrhs > h->max_rhs) { set_error("nrhs out of range [1, max_rhs]"); return FDST_INVALID_ARGUMENT; }
   if (d_x == d_y) { set_error("x and y alias"); return FDST_INVALID_ARGUMENT; }
-  return run_matvec(h, d_x, d_y, nrhs, nullptr, (cudaStream_t)stream);
+  return run_matvec(h, d_x, d_y, nrhs, nullptr, (cudaStream_t)stream, false);
 }
 
 fdst_status fdst_set_timing(fdst_handle h, int on) {
@@ -801,7 +801,7 @@ fdst_status fdst_solve(fdst_handle h, const double *d_b, double *d_x, int nrhs, 
     residuals_current = false;
     size_t e0 = 0;
     if (h->timing) { mark(); e0 = ev.size() - 1; }
-    TRY(run_matvec(h, h->z, h->Az, nrhs, h->done, st));
+    TRY(run_matvec(h, h->z, h->Az, nrhs, h->done, st, false));
     size_t e1 = 0;
     if (h->timing) { mark(); e1 = ev.size() - 1; spans.push_back({0, e0, e1}); }
     launch_dot(h->Az, h->z, n, n, nrhs, h->partials, h->counters, delta, h->done, st);

@@ -27,10 +27,14 @@ struct GemmProb {
   int R = 0, K = 0, N = 0;
   const double *lam_row = nullptr, *lam_col = nullptr;
   const double *scale_in = nullptr, *scale_out = nullptr;
+  const int *done_flag = nullptr;   // skipped when *done_flag != 0 (batched solves)
 };
+// Up to kMaxGroup problems by value, or any number from a device table.
 struct GemmGroup {
   GemmProb p[kMaxGroup];
   int nprob = 0;
+  const GemmProb *table = nullptr;
+  int maxR = 0, maxN = 0, tn = 0;   // with a table: largest R, N; tn: forced column tile (0 = pick)
 };
 void launch_gemm_f64(const GemmGroup &g, int nrhs, const int *done, cudaStream_t s);
 
@@ -47,10 +51,14 @@ struct BandOp {
   double coef = 1.0;
   int accumulate = 0;
   int64_t x_rhs_stride = 0, y_rhs_stride = 0;
+  const int *done_flag = nullptr;
 };
 struct BandGroup {
   BandOp op[kMaxGroup];
   int nop = 0;
+  const BandOp *table = nullptr;
+  int64_t maxt = 0;                 // with a table: largest output size
+  int threads = 256;
 };
 void launch_band(const BandGroup &g, int nrhs, const int *done, cudaStream_t s);
 
@@ -68,10 +76,14 @@ struct BandOpDF {
   float2 coef = {1.0f, 0.0f};
   int accumulate = 0;
   int64_t x_rhs_stride = 0, y_rhs_stride = 0;
+  const int *done_flag = nullptr;
 };
 struct BandGroupDF {
   BandOpDF op[kMaxGroup];
   int nop = 0;
+  const BandOpDF *table = nullptr;
+  int64_t maxt = 0;
+  int threads = 256;
 };
 void launch_band_df(const BandGroupDF &g, int nrhs, const int *done, cudaStream_t s);
 // y2 = split(x) (double -> FP32 pair) and x = join(y2) over n entries per right-hand side.

@@ -31,7 +31,8 @@ __global__ void __launch_bounds__(kThreads) k_gemm_f64(GemmGroup g, int nrhs, co
   const int prob = blockIdx.z % g.nprob;
   const int rhs = blockIdx.z / g.nprob;
   if (done && done[rhs]) return;
-  const GemmProb &P = g.p[prob];
+  const GemmProb &P = g.table ? g.table[prob] : g.p[prob];
+  if (P.done_flag && *P.done_flag) return;
   const int R = P.R, K = P.K, N = P.N;
   const int r0 = blockIdx.x * kBR, n0 = blockIdx.y * BN;
   if (r0 >= R || n0 >= N) return;
@@ -103,18 +104,24 @@ __global__ void __launch_bounds__(kThreads) k_gemm_f64(GemmGroup g, int nrhs, co
 }
 
 void launch_gemm_f64(const GemmGroup &g, int nrhs, const int *done, cudaStream_t s) {
-  int maxR = 0, maxN = 0;
-  for (int i = 0; i < g.nprob; ++i) {
-    maxR = g.p[i].R > maxR ? g.p[i].R : maxR;
-    maxN = g.p[i].N > maxN ? g.p[i].N : maxN;
-  }
-  // pick the column tile that wastes the fewest padded columns
-  int best = 4, bestpad = 1 << 30;
-  for (int tn = 2; tn <= 4; ++tn) {
-    int bn = 16 * tn;
-    int pad = 0;
-    for (int i = 0; i < g.nprob; ++i) pad += (((g.p[i].N + bn - 1) / bn) * bn - g.p[i].N) * g.p[i].R;
-    if (pad < bestpad || (pad == bestpad && tn > best)) { bestpad = pad; best = tn; }
+  int maxR = g.maxR, maxN = g.maxN;
+  if (!g.table)
+    for (int i = 0; i < g.nprob; ++i) {
+      maxR = g.p[i].R > maxR ? g.p[i].R : maxR;
+      maxN = g.p[i].N > maxN ? g.p[i].N : maxN;
+    }
+  // column tile: forced (tuned), else the one that wastes the fewest padded columns
+  int best = g.tn, bestpad = 1 << 30;
+  if (!best) {
+    best = 4;
+    for (int tn = 2; tn <= 4; ++tn) {
+      int bn = 16 * tn;
+      long long pad = 0;
+      if (g.table) pad = (long long)((maxN + bn - 1) / bn * bn - maxN);
+      else
+        for (int i = 0; i < g.nprob; ++i) pad += (long long)(((g.p[i].N + bn - 1) / bn) * bn - g.p[i].N) * g.p[i].R;
+      if (pad < bestpad || (pad == bestpad && tn > best)) { bestpad = (int)pad; best = tn; }
+    }
   }
   dim3 grid((maxR + kBR - 1) / kBR, (maxN + 16 * best - 1) / (16 * best), g.nprob * nrhs);
   count_launch(1);
@@ -125,10 +132,11 @@ void launch_gemm_f64(const GemmGroup &g, int nrhs, const int *done, cudaStream_t
 
 // ------------------------------------------------------------------ banded mode product
 
-__global__ void __launch_bounds__(256) k_band(BandGroup g, int nrhs, const int *done) {
+__global__ void __launch_bounds__(512) k_band(BandGroup g, int nrhs, const int *done) {
   const int rhs = blockIdx.y;
   if (done && done[rhs]) return;
-  const BandOp &op = g.op[blockIdx.z];
+  const BandOp &op = g.table ? g.table[blockIdx.z] : g.op[blockIdx.z];
+  if (op.done_flag && *op.done_flag) return;
   const int mode = op.mode;
   const unsigned od0 = mode == 0 ? op.rows : op.d0, od1 = mode == 1 ? op.rows : op.d1,
                  od2 = mode == 2 ? op.rows : op.d2;
@@ -157,18 +165,20 @@ __global__ void __launch_bounds__(256) k_band(BandGroup g, int nrhs, const int *
 }
 
 void launch_band(const BandGroup &g, int nrhs, const int *done, cudaStream_t s) {
-  int64_t maxt = 0;
-  for (int i = 0; i < g.nop; ++i) {
-    const auto &o = g.op[i];
-    int64_t t = (int64_t)(o.mode == 0 ? o.rows : o.d0) * (o.mode == 1 ? o.rows : o.d1) * (o.mode == 2 ? o.rows : o.d2);
-    maxt = t > maxt ? t : maxt;
-  }
-  int64_t blocks = (maxt + 255) / 256;
+  int64_t maxt = g.maxt;
+  if (!g.table)
+    for (int i = 0; i < g.nop; ++i) {
+      const auto &o = g.op[i];
+      int64_t t = (int64_t)(o.mode == 0 ? o.rows : o.d0) * (o.mode == 1 ? o.rows : o.d1) * (o.mode == 2 ? o.rows : o.d2);
+      maxt = t > maxt ? t : maxt;
+    }
+  const int thr = g.threads > 0 ? g.threads : 256;
+  int64_t blocks = (maxt + thr - 1) / thr;
   if (blocks > 2048) blocks = 2048;
   if (blocks < 1) blocks = 1;
   dim3 grid((unsigned)blocks, nrhs, g.nop);
   count_launch(1);
-  k_band<<<grid, 256, 0, s>>>(g, nrhs, done);
+  k_band<<<grid, thr, 0, s>>>(g, nrhs, done);
 }
 
 // ------------------------------------------------------------------ double-float banded mode product
@@ -194,10 +204,11 @@ __device__ __forceinline__ float2 df_norm(float sh, float sl) {
   return make_float2(h, sl - (h - sh));
 }
 
-__global__ void __launch_bounds__(256) k_band_df(BandGroupDF g, int nrhs, const int *done) {
+__global__ void __launch_bounds__(512) k_band_df(BandGroupDF g, int nrhs, const int *done) {
   const int rhs = blockIdx.y;
   if (done && done[rhs]) return;
-  const BandOpDF &op = g.op[blockIdx.z];
+  const BandOpDF &op = g.table ? g.table[blockIdx.z] : g.op[blockIdx.z];
+  if (op.done_flag && *op.done_flag) return;
   const int mode = op.mode;
   const unsigned od0 = mode == 0 ? op.rows : op.d0, od1 = mode == 1 ? op.rows : op.d1,
                  od2 = mode == 2 ? op.rows : op.d2;
@@ -236,18 +247,20 @@ __global__ void __launch_bounds__(256) k_band_df(BandGroupDF g, int nrhs, const 
 }
 
 void launch_band_df(const BandGroupDF &g, int nrhs, const int *done, cudaStream_t s) {
-  int64_t maxt = 0;
-  for (int i = 0; i < g.nop; ++i) {
-    const auto &o = g.op[i];
-    int64_t t = (int64_t)(o.mode == 0 ? o.rows : o.d0) * (o.mode == 1 ? o.rows : o.d1) * (o.mode == 2 ? o.rows : o.d2);
-    maxt = t > maxt ? t : maxt;
-  }
-  int64_t blocks = (maxt + 255) / 256;
+  int64_t maxt = g.maxt;
+  if (!g.table)
+    for (int i = 0; i < g.nop; ++i) {
+      const auto &o = g.op[i];
+      int64_t t = (int64_t)(o.mode == 0 ? o.rows : o.d0) * (o.mode == 1 ? o.rows : o.d1) * (o.mode == 2 ? o.rows : o.d2);
+      maxt = t > maxt ? t : maxt;
+    }
+  const int thr = g.threads > 0 ? g.threads : 256;
+  int64_t blocks = (maxt + thr - 1) / thr;
   if (blocks > 4096) blocks = 4096;
   if (blocks < 1) blocks = 1;
   dim3 grid((unsigned)blocks, nrhs, g.nop);
   count_launch(1);
-  k_band_df<<<grid, 256, 0, s>>>(g, nrhs, done);
+  k_band_df<<<grid, thr, 0, s>>>(g, nrhs, done);
 }
 
 __global__ void k_split_df(const double *x, float2 *y, int64_t n, int64_t stride, const int *done) {

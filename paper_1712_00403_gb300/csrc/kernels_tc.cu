@@ -239,6 +239,8 @@ struct TileInfo {
   bool valid;
 };
 
+__device__ __forceinline__ const TcProb &prob_of(const TcGroup &g, int i) { return g.table ? g.table[i] : g.p[i]; }
+
 __device__ __forceinline__ TileInfo decode_tile(const TcGroup &g, int T, int nrt, int ntn, const int *done) {
   TileInfo t;
   const int rt = T % nrt;
@@ -247,11 +249,11 @@ __device__ __forceinline__ TileInfo decode_tile(const TcGroup &g, int T, int nrt
   const int z = rest / ntn;
   t.prob = z % g.nprob;
   t.rhs = z / g.nprob;
-  const TcProb &P = g.p[t.prob];
+  const TcProb &P = prob_of(g, t.prob);
   const int npad = (P.N + 15) & ~15;
   t.row0 = rt * kM;
   t.n0 = nt * kNTMax;
-  t.valid = t.row0 < P.R && t.n0 < npad && !(done && done[t.rhs]);
+  t.valid = t.row0 < P.R && t.n0 < npad && !(done && done[t.rhs]) && !(P.done_flag && *P.done_flag);
   t.NT = npad - t.n0 < kNTMax ? npad - t.n0 : kNTMax;
   t.kp = (P.K + 7) & ~7;
   t.nstages = (t.kp + kKC - 1) / kKC;
@@ -319,7 +321,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       q_off[it] = j * (kM * 32) + q_rr[it] * 32 + ((cc ^ ((q_rr[it] >> 2) & 1)) * 16);
     }
     auto load = [&](const Cursor &c, float4 (&reg)[kQuads]) {
-      const TcProb &P = g.p[c.t.prob];
+      const TcProb &P = prob_of(g, c.t.prob);
       const int k0 = c.s * kKC;
       if (P.A32) {
         const float *A32 = P.A32 + (int64_t)c.t.rhs * P.a_rhs_stride;
@@ -376,7 +378,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t bbytes = 2u * ks * c.t.NT * 32u;
         const size_t btile = 2 * (size_t)kNTMax * c.t.kp * (size_t)(c.t.n0 / kNTMax);
         mbar_expect_tx(&full[slot], bbytes);
-        bulk_g2s(sB, g.p[c.t.prob].Bt + btile + 2 * (size_t)c.t.NT * k0, bbytes, &full[slot]);
+        bulk_g2s(sB, prob_of(g, c.t.prob).Bt + btile + 2 * (size_t)c.t.NT * k0, bbytes, &full[slot]);
       }
 #pragma unroll
       for (int it = 0; it < kQuads; ++it) {
@@ -424,7 +426,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     int v = 0;
     for (int T = next_tile(g, -1, total, nrt, ntn, done); T < total; T = next_tile(g, T, total, nrt, ntn, done)) {
       const TileInfo t = decode_tile(g, T, nrt, ntn, done);
-      const TcProb &P = g.p[t.prob];
+      const TcProb &P = prob_of(g, t.prob);
       const int acc = v & 1;
       if (!mbar_wait(&tfull[acc], (v >> 1) & 1, abort)) break;
       tc_fence_after();
@@ -540,19 +542,36 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 static int *g_err_flag = nullptr;
 
-fdst_status launch_gemm_tc(const TcGroup &g, int nrhs, const int *done, cudaStream_t s) {
-  int maxR = 0, maxN = 0;
-  for (int i = 0; i < g.nprob; ++i) {
-    if (g.p[i].N > maxN) maxN = g.p[i].N;
-    if (g.p[i].R > maxR) maxR = g.p[i].R;
-  }
+static void tc_dims(const TcGroup &g, int &maxR, int &maxN) {
+  maxR = g.maxR;
+  maxN = g.maxN;
+  if (!g.table)
+    for (int i = 0; i < g.nprob; ++i) {
+      if (g.p[i].N > maxN) maxN = g.p[i].N;
+      if (g.p[i].R > maxR) maxR = g.p[i].R;
+    }
+}
+
+int tc_max_ring(const TcGroup &g) {
+  int maxR, maxN;
+  tc_dims(g, maxR, maxN);
+  const int npad = tc_npad(maxN);
+  const int nt = npad < kNTMax ? npad : kNTMax;
+  const int stage_bytes = kAStageBytes + 2 * 4 * nt * 32;
+  int nring = (kSmemBudget - 2048) / stage_bytes;
+  return nring > 4 ? 4 : nring;
+}
+
+fdst_status launch_gemm_tc(const TcGroup &g, int nrhs, const int *done, cudaStream_t s, int ring) {
+  int maxR, maxN;
+  tc_dims(g, maxR, maxN);
   const int npad = tc_npad(maxN);
   const int ntn = (npad + kNTMax - 1) / kNTMax;
   const int nt = npad < kNTMax ? npad : kNTMax;
   const int ntc = nt <= 32 ? 32 : nt <= 64 ? 64 : nt <= 128 ? 128 : 256;   // TMEM columns per accumulator
   const int stage_bytes = kAStageBytes + 2 * 4 * nt * 32;
-  int nring = (kSmemBudget - 2048) / stage_bytes;
-  if (nring > 4) nring = 4;
+  int nring = tc_max_ring(g);
+  if (ring > 0 && ring < nring) nring = ring;
   if (nring < 2) {
     set_error("tensor-core contraction: shared memory too small for two stages");
     return FDST_NOT_SUPPORTED;

@@ -27,12 +27,19 @@ struct TcProb {
   int lda = 0, out_nv = 0, ldc = 0;
   const float *lam_row = nullptr, *lam_col = nullptr;
   const double *scale_in = nullptr, *scale_out = nullptr;
+  const int *done_flag = nullptr;   // the problem is skipped when *done_flag != 0 (batched solves)
 };
+// Up to 8 problems by value, or any number from a device table (table != nullptr).
 struct TcGroup {
   TcProb p[8];
   int nprob = 0;
+  const TcProb *table = nullptr;
+  int maxR = 0, maxN = 0;           // with a table: largest R and N among its problems
 };
-fdst_status launch_gemm_tc(const TcGroup &g, int nrhs, const int *done, cudaStream_t s);
+// ring: shared-memory stages (0 = as many as fit, capped at 4).
+fdst_status launch_gemm_tc(const TcGroup &g, int nrhs, const int *done, cudaStream_t s, int ring = 0);
+// number of stages that fit for the widest column tile of g
+int tc_max_ring(const TcGroup &g);
 
 // Host packing of B (K x N row-major FP64) into the kernel's per-stage
 // shared-memory image (TF32 hi/lo, SWIZZLE_32B K-major); size in floats.

@@ -1,0 +1,59 @@
+"""Batched solves (fdst_batch_*): uneven problems advanced together by grouped
+launches under a CUDA graph give each problem the result it gets alone
+(same iteration count within one, solution within 1e-7 relative, true
+residual <= 1e-8), for the FP64 and the split-TF32 FD apply."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import minres, stokes
+
+from _helpers import gpu_problem, oracle_problem, problem_spec, rel
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+SPECS = [problem_spec(3, 2, (4, 5, 6)), problem_spec(3, 3, (3, 3, 7)), problem_spec(2, 2, (12, 9)),
+         problem_spec(3, 2, (6, 4, 3)), problem_spec(2, 4, (5, 8))]
+
+
+@pytest.mark.parametrize("tc", [False, True], ids=["f64", "tf32"])
+def test_batch_equals_individual_solves(tc):
+    import paper_1712_00403_gb300 as fd
+    prec = fd.FD_TF32X3 if tc else fd.FD_F64
+    probs = [gpu_problem(s, fd_precision=prec, matvec_precision=fd.MV_DF64) for s in SPECS]
+    bs = [torch.tensor(synth.rhs(401 + i, p.block_sizes), device="cuda") for i, p in enumerate(probs)]
+    batch = fd.Batch(probs, autotune=True)
+    info = batch.info()
+    assert info["band_threads"] in (128, 256, 512)
+    if tc:
+        assert 2 <= info["tc_ring"] <= 4
+    xs = [torch.zeros_like(b) for b in bs]
+    res = batch.solve(bs, xs, tol=1e-8, maxit=500)
+    res2 = batch.solve(bs, [torch.zeros_like(b) for b in bs], tol=1e-8, maxit=500)   # graph replay again
+    batch.close()
+    for i, p in enumerate(probs):
+        x1 = torch.zeros_like(bs[i])
+        single = p.solve(bs[i], x1, tol=1e-8, maxit=500)[0]
+        assert res[i]["status"] == "OK" and res[i]["true_rel_res"] <= 1e-8
+        assert abs(res[i]["iterations"] - single["iterations"]) <= 1
+        assert res2[i]["iterations"] == res[i]["iterations"]
+        assert rel(xs[i].cpu().numpy(), x1.cpu().numpy()) <= 1e-7
+    assert fd.device_error() == 0
+
+
+def test_batch_f64_matches_oracle():
+    import paper_1712_00403_gb300 as fd
+    spec = SPECS[0]
+    probs = [gpu_problem(s, fd_precision=fd.FD_F64, matvec_precision=fd.MV_DF64) for s in SPECS[:3]]
+    bs = [torch.tensor(synth.rhs(501 + i, p.block_sizes), device="cuda") for i, p in enumerate(probs)]
+    xs = [torch.zeros_like(b) for b in bs]
+    batch = fd.Batch(probs, autotune=False)
+    res = batch.solve(bs, xs, tol=1e-8, maxit=500)
+    batch.close()
+    S = oracle_problem(spec)
+    xo, io = minres.minres(lambda v: stokes.matvec(S, v), bs[0].cpu().numpy(), lambda v: stokes.apply_PD_inv(S, v),
+                           tol=1e-8, maxit=500, true_check=True)
+    assert abs(res[0]["iterations"] - io["iters"]) <= 1
+    assert rel(xs[0].cpu().numpy(), xo) <= 1e-7
