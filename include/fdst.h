@@ -215,6 +215,40 @@ fdst_status fdst_batch_solve(fdst_batch b, const double *const *d_b, double *con
 fdst_status fdst_batch_info(fdst_batch b, int *tc_ring, int *band_threads, double *ms_apply, double *ms_matvec);
 fdst_status fdst_batch_destroy(fdst_batch b);
 
+/*
+ * Request server (continuous batching). Requests queue on submission; each
+ * fdst_server_step finishes the active problems whose recurrence stopped and
+ * whose FP64 true residual is <= tol (their solution is copied to host memory
+ * and their device handle returns to an idle cache keyed by problem shape),
+ * admits queued requests while fewer than max_active are active and the
+ * device memory held stays within hbm_budget_bytes (evicting idle handles
+ * least-recently-used first), and advances every active problem by
+ * iters_per_step MINRES iterations with grouped launches. Times are in the
+ * caller's clock (t_arrival given at submission, `now` at each step).
+ */
+typedef struct {
+  int64_t hbm_budget_bytes;  /* device bytes the server may hold in handles; <= 0: 90% of free memory */
+  int max_active;            /* most problems advanced together (>= 1) */
+  int fd_precision;          /* FDST_FD_* for every request */
+  int matvec_precision;      /* FDST_MV_* for every request */
+  double tol;                /* MINRES tolerance (true relative residual) */
+  int maxit;
+  int iters_per_step;        /* MINRES iterations per fdst_server_step (>= 1) */
+} fdst_server_opts;
+typedef struct fdst_server_ctx *fdst_server;
+fdst_status fdst_server_create(const fdst_server_opts *opts, fdst_server *out);
+/* problem: as for fdst_setup (max_rhs and precisions are the server's); h_b: host
+ * right-hand side of the problem's n_total entries, copied. */
+fdst_status fdst_server_submit(fdst_server s, const fdst_desc *problem, const double *h_b, double t_arrival,
+                               int64_t *id);
+fdst_status fdst_server_step(fdst_server s, double now, int *n_active, int *n_queued, int64_t *n_finished);
+/* *finished = 1 once the request is done; then h_x (n_total doubles, may be NULL) and info are filled. */
+fdst_status fdst_server_result(fdst_server s, int64_t id, int *finished, double *h_x, fdst_solve_info *info,
+                               double *t_arrival, double *t_admit, double *t_done);
+fdst_status fdst_server_stats(fdst_server s, int64_t *handles_created, int64_t *handles_reused,
+                              int64_t *handles_evicted, int64_t *bytes_held, int *max_active_seen);
+fdst_status fdst_server_destroy(fdst_server s);
+
 /* Number of CUDA kernels this library has launched in the process so far
  * (diagnostics: lets a caller count the kernels inside a timed region). */
 int64_t fdst_kernel_launches(void);

@@ -47,6 +47,12 @@ class Sizes(ctypes.Structure):
                 ("flops_matvec", ctypes.c_double)]
 
 
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_active", ctypes.c_int), ("fd_precision", ctypes.c_int),
+                ("matvec_precision", ctypes.c_int), ("tol", ctypes.c_double), ("maxit", ctypes.c_int),
+                ("iters_per_step", ctypes.c_int)]
+
+
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("status", ctypes.c_int), ("eta_rel", ctypes.c_double),
                 ("true_rel_res", ctypes.c_double)]
@@ -55,7 +61,9 @@ class SolveInfo(ctypes.Structure):
 ENTRY_POINTS = ["fdst_setup", "fdst_destroy", "fdst_get_sizes", "fdst_apply_prec", "fdst_matvec", "fdst_solve",
                 "fdst_solve_host", "fdst_apply_prec_host", "fdst_set_timing", "fdst_get_timing",
                 "fdst_fd_apply_static", "fdst_batch_create", "fdst_batch_solve", "fdst_batch_info",
-                "fdst_batch_destroy", "fdst_device_error", "fdst_kernel_launches", "fdst_last_error"]
+                "fdst_batch_destroy", "fdst_server_create", "fdst_server_submit", "fdst_server_step",
+                "fdst_server_result", "fdst_server_stats", "fdst_server_destroy", "fdst_device_error",
+                "fdst_kernel_launches", "fdst_last_error"]
 
 _lib = None
 
@@ -83,6 +91,14 @@ def load_library(path=LIB_PATH):
     lib.fdst_batch_solve.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), d, i, ctypes.POINTER(SolveInfo), vp]
     lib.fdst_batch_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(d), ctypes.POINTER(d)]
     lib.fdst_batch_destroy.argtypes = [vp]
+    lib.fdst_server_create.argtypes = [ctypes.POINTER(ServerOpts), ctypes.POINTER(vp)]
+    lib.fdst_server_submit.argtypes = [vp, ctypes.POINTER(Desc), vp, d, ctypes.POINTER(i64)]
+    lib.fdst_server_step.argtypes = [vp, d, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i64)]
+    lib.fdst_server_result.argtypes = [vp, i64, ctypes.POINTER(i), vp, ctypes.POINTER(SolveInfo),
+                                       ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d)]
+    lib.fdst_server_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                      ctypes.POINTER(i64), ctypes.POINTER(i)]
+    lib.fdst_server_destroy.argtypes = [vp]
     lib.fdst_fd_apply_static.argtypes = [i, ctypes.POINTER(i), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                          ctypes.POINTER(d), vp, vp, vp]
     lib.fdst_get_timing.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d),
@@ -278,6 +294,79 @@ class Batch:
         if getattr(self, "_b", None):
             _lib.fdst_batch_destroy(self._b)
             self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _desc_for(knots, p, disc=TH, viscosity=1.0, cpen=0.0):
+    keep = [np.ascontiguousarray(k, dtype=np.float64) for k in knots]
+    d = Desc()
+    d.dim = len(keep)
+    d.discretization = disc
+    d.degree = p
+    for e, k in enumerate(keep):
+        d.h_knots[e] = k.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        d.nknots[e] = len(k)
+    d.viscosity = viscosity
+    d.cpen = cpen
+    d.max_rhs = 1
+    return d, keep
+
+
+class Server:
+    """Continuous-batching request server (fdst_server_*). Times are the caller's clock."""
+
+    def __init__(self, max_active=16, hbm_budget_bytes=0, fd_precision=FD_TF32X3, matvec_precision=MV_DF64,
+                 tol=1e-8, maxit=1000, iters_per_step=4):
+        lib = load_library()
+        o = ServerOpts(hbm_budget_bytes, max_active, fd_precision, matvec_precision, tol, maxit, iters_per_step)
+        s = ctypes.c_void_p()
+        _check(lib.fdst_server_create(ctypes.byref(o), ctypes.byref(s)))
+        self._s = s
+        self.sizes = {}
+
+    def submit(self, knots, p, b, t_arrival, disc=TH):
+        d, keep = _desc_for(knots, p, disc)
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        rid = ctypes.c_int64()
+        _check(_lib.fdst_server_submit(self._s, ctypes.byref(d), ctypes.c_void_p(b.ctypes.data), t_arrival,
+                                       ctypes.byref(rid)))
+        self.sizes[rid.value] = b.size
+        return rid.value
+
+    def step(self, now):
+        a, q, f = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
+        _check(_lib.fdst_server_step(self._s, now, ctypes.byref(a), ctypes.byref(q), ctypes.byref(f)))
+        return a.value, q.value, f.value
+
+    def result(self, rid):
+        fin = ctypes.c_int()
+        x = np.empty(self.sizes[rid])
+        info = SolveInfo()
+        ta, tm, td = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(_lib.fdst_server_result(self._s, rid, ctypes.byref(fin), ctypes.c_void_p(x.ctypes.data),
+                                       ctypes.byref(info), ctypes.byref(ta), ctypes.byref(tm), ctypes.byref(td)))
+        if not fin.value:
+            return None
+        return dict(x=x, iterations=info.iterations, status=STATUS.get(info.status, info.status),
+                    true_rel_res=info.true_rel_res, t_arrival=ta.value, t_admit=tm.value, t_done=td.value)
+
+    def stats(self):
+        c, r, e, b = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        m = ctypes.c_int()
+        _check(_lib.fdst_server_stats(self._s, ctypes.byref(c), ctypes.byref(r), ctypes.byref(e), ctypes.byref(b),
+                                      ctypes.byref(m)))
+        return dict(handles_created=c.value, handles_reused=r.value, handles_evicted=e.value, bytes_held=b.value,
+                    max_active_seen=m.value)
+
+    def close(self):
+        if getattr(self, "_s", None):
+            _lib.fdst_server_destroy(self._s)
+            self._s = None
 
     def __del__(self):
         try:

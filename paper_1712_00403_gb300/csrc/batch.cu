@@ -524,6 +524,59 @@ static fdst_status build_batch(fdst_batch b) {
   return FDST_OK;
 }
 
+// Start of one member's MINRES (right-hand side 0 of its handle, b and x in
+// the handle's hb / hx): v = b - A x0, z = P^{-1} v / gamma_1, |b|^2 in dots[3].
+fdst_status member_init(fdst_ctx *h, int *n_stopped, double tol, cudaStream_t st) {
+  const int64_t m = h->n_total;
+  CK(cudaMemsetAsync(h->done, 0, sizeof(int), st));
+  TRY(run_matvec(h, h->hx, h->Az, 1, nullptr, st, true));
+  launch_axpby(h->hb, h->v, 1.0, 0.0, m, m, 1, st);
+  launch_axpby(h->Az, h->v, -1.0, 1.0, m, m, 1, st);
+  CK(cudaMemsetAsync(h->v_old, 0, sizeof(double) * m, st));
+  CK(cudaMemsetAsync(h->w, 0, sizeof(double) * m, st));
+  CK(cudaMemsetAsync(h->w_old, 0, sizeof(double) * m, st));
+  TRY(run_apply(h, h->v, h->z, 1, nullptr, st));
+  launch_dot(h->v, h->z, m, m, 1, h->partials, h->counters, h->dots, nullptr, st);
+  launch_minres_init(h->state, h->dots, h->done, 1, n_stopped, tol, st);
+  launch_scale_by_inv_gamma(h->z, h->state, m, m, 1, h->done, st);
+  launch_dot(h->hb, h->hb, m, m, 1, h->partials, h->counters, h->dots + 3, nullptr, st);
+  return FDST_OK;
+}
+
+// Enqueues ||b - A x||^2 (FP64 matvec) into dots[0]; the caller syncs and divides by dots[3].
+fdst_status member_residual(fdst_ctx *h, cudaStream_t st) {
+  const int64_t m = h->n_total;
+  TRY(run_matvec(h, h->hx, h->Az, 1, nullptr, st, true));
+  launch_axpby(h->hb, h->Az, 1.0, -1.0, m, m, 1, st);
+  launch_dot(h->Az, h->Az, m, m, 1, h->partials, h->counters, h->dots, nullptr, st);
+  return FDST_OK;
+}
+
+fdst_status batch_step(fdst_batch b, int maxit, cudaStream_t st) { return batch_iterate(b, maxit, st); }
+
+fdst_status batch_new(const std::vector<fdst_ctx *> &hs, int ring, int threads, fdst_batch *out) {
+  *out = nullptr;
+  fdst_batch b = new fdst_batch_ctx();
+  b->n = (int)hs.size();
+  b->hs = hs;
+  b->tc = hs[0]->desc.fd_precision != FDST_FD_F64;
+  b->df = hs[0]->desc.matvec_precision == FDST_MV_DF64;
+  b->use_graph = false;
+  b->ring = ring;
+  b->threads = threads;
+  fdst_status st = build_batch(b);
+  if (st != FDST_OK) {
+    for (void *p : b->allocs) cudaFree(p);
+    if (b->h_n_stopped) cudaFreeHost(b->h_n_stopped);
+    delete b;
+    return st;
+  }
+  *out = b;
+  return FDST_OK;
+}
+
+int *batch_stop_counter(fdst_batch b) { return b->n_stopped; }
+
 }  // namespace fdst
 
 extern "C" {
@@ -603,18 +656,7 @@ fdst_status fdst_batch_solve(fdst_batch b, const double *const *d_b, double *con
     const int64_t m = h->n_total;
     CK(cudaMemcpyAsync(h->hb, d_b[i], sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(h->hx, d_x[i], sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
-    CK(cudaMemsetAsync(h->done, 0, sizeof(int), st));
-    TRY(run_matvec(h, h->hx, h->Az, 1, nullptr, st, true));
-    launch_axpby(h->hb, h->v, 1.0, 0.0, m, m, 1, st);
-    launch_axpby(h->Az, h->v, -1.0, 1.0, m, m, 1, st);
-    CK(cudaMemsetAsync(h->v_old, 0, sizeof(double) * m, st));
-    CK(cudaMemsetAsync(h->w, 0, sizeof(double) * m, st));
-    CK(cudaMemsetAsync(h->w_old, 0, sizeof(double) * m, st));
-    TRY(run_apply(h, h->v, h->z, 1, nullptr, st));
-    launch_dot(h->v, h->z, m, m, 1, h->partials, h->counters, h->dots, nullptr, st);
-    launch_minres_init(h->state, h->dots, h->done, 1, b->n_stopped, tol, st);
-    launch_scale_by_inv_gamma(h->z, h->state, m, m, 1, h->done, st);
-    launch_dot(h->hb, h->hb, m, m, 1, h->partials, h->counters, h->dots + 3, nullptr, st);
+    TRY(member_init(h, b->n_stopped, tol, st));
   }
   std::vector<double> bb(n), true_rel(n, -1.0);
   for (int i = 0; i < n; ++i) CK(cudaMemcpyAsync(&bb[i], b->hs[i]->dots + 3, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -622,12 +664,8 @@ fdst_status fdst_batch_solve(fdst_batch b, const double *const *d_b, double *con
   auto true_residuals = [&]() -> fdst_status {
     std::vector<double> rr(n);
     for (int i = 0; i < n; ++i) {
-      fdst_ctx *h = b->hs[i];
-      const int64_t m = h->n_total;
-      TRY(run_matvec(h, h->hx, h->Az, 1, nullptr, st, true));
-      launch_axpby(h->hb, h->Az, 1.0, -1.0, m, m, 1, st);
-      launch_dot(h->Az, h->Az, m, m, 1, h->partials, h->counters, h->dots, nullptr, st);
-      CK(cudaMemcpyAsync(&rr[i], h->dots, sizeof(double), cudaMemcpyDeviceToHost, st));
+      TRY(member_residual(b->hs[i], st));
+      CK(cudaMemcpyAsync(&rr[i], b->hs[i]->dots, sizeof(double), cudaMemcpyDeviceToHost, st));
     }
     CK(cudaStreamSynchronize(st));
     for (int i = 0; i < n; ++i) true_rel[i] = bb[i] > 0 ? std::sqrt(rr[i] / bb[i]) : std::sqrt(rr[i]);

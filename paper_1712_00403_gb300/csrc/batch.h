@@ -1,0 +1,17 @@
+// Batch internals shared with the request server.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/fdst.h"
+
+struct fdst_ctx;
+
+namespace fdst {
+fdst_status member_init(fdst_ctx *h, int *n_stopped, double tol, cudaStream_t st);
+fdst_status member_residual(fdst_ctx *h, cudaStream_t st);
+fdst_status batch_new(const std::vector<fdst_ctx *> &hs, int ring, int threads, fdst_batch *out);
+fdst_status batch_step(fdst_batch b, int maxit, cudaStream_t st);
+int *batch_stop_counter(fdst_batch b);
+}  // namespace fdst

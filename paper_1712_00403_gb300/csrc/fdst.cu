@@ -10,6 +10,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <sstream>
 #include <string>
 #include <vector>
@@ -98,7 +99,10 @@ static fdst_status build_spaces(fdst_ctx *h) {
 static fdst_status build_fd(fdst_ctx *h) {
   const int dim = h->dim, p = h->p;
   const int npts = p + 2;
-  std::map<std::string, std::pair<std::vector<double>, Mat>> eig_cache;  // key -> (lam, U)
+  // process-wide cache of eigen-factors of identical univariate pencils (handles of
+  // problems that share a direction's space skip the Jacobi solve)
+  static std::mutex cache_mutex;
+  static std::map<std::string, std::pair<std::vector<double>, Mat>> eig_cache;  // key -> (lam, U)
   std::map<std::string, const double *> dev_cache;
   auto dev_mat = [&](const std::string &key, const Mat &A, const double **out) -> fdst_status {
     auto it = dev_cache.find(key);
@@ -128,23 +132,32 @@ static fdst_status build_fd(fdst_ctx *h) {
       std::string key = space_key(s);
       const bool geo = h->desc.variant == FDST_VARIANT_PD_GEO;
       if (geo) key = "geo" + std::to_string(k) + "_" + std::to_string(e) + "_" + key;
-      auto it = eig_cache.find(key);
-      if (it == eig_cache.end()) {
+      // lookups and inserts under the lock; the Jacobi solve itself runs outside it
+      std::pair<std::vector<double>, Mat> fac;
+      bool found = false;
+      if (!geo) {
+        std::lock_guard<std::mutex> lock(cache_mutex);
+        auto it = eig_cache.find(key);
+        if (it != eig_cache.end()) { fac = it->second; found = true; }
+      }
+      if (!found) {
         Mat K = geo ? h->geo_K[k][e] : stiffness_matrix(s, npts);
         Mat M = geo ? h->geo_M[k][e] : mixed_matrix(s, 0, s, 0, npts);
-        std::vector<double> l;
-        Mat U;
-        if (!gen_eig(K, M, l, U)) {
+        if (!gen_eig(K, M, fac.first, fac.second)) {
           set_error("univariate velocity mass matrix is not SPD");
           return FDST_NOT_SPD;
         }
-        it = eig_cache.emplace(key, std::make_pair(l, U)).first;
+        if (!geo) {
+          std::lock_guard<std::mutex> lock(cache_mutex);
+          if (eig_cache.size() > 4096) eig_cache.clear();
+          eig_cache.emplace(key, fac);
+        }
       }
-      lam[e] = it->second.first;
-      Mat Ut = transpose(it->second.second);
-      TRY(dev_mat("U" + key, it->second.second, &Uf[e]));
+      lam[e] = fac.first;
+      Mat Ut = transpose(fac.second);
+      TRY(dev_mat("U" + key, fac.second, &Uf[e]));
       TRY(dev_mat("Ut" + key, Ut, &Ub[e]));
-      Ufh[e] = it->second.second.a;
+      Ufh[e] = fac.second.a;
       Ubh[e] = Ut.a;
     }
     const int n1 = h->shape[k][0], n2 = h->shape[k][1], n3 = h->shape[k][2];
