@@ -7,7 +7,13 @@ MINRES recurrences and inner products). Default workload: 3D unit cube,
 Taylor-Hood, p=3, 64^3 elements (6,740,830 DoF), 16 seeded N(0,1)
 right-hand sides. Prints one JSON line (rank 0).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+Other workloads (--workload): mapped_th_p3_32 (sine-bump map, variable
+viscosity, P_D^G, FP64 CSR operator, 4 right-hand sides), batched_64 (64
+uneven unit-cube instances in grouped launches; split-TF32 and FP64 FD
+compared) and serving (Poisson arrivals swept over rates through the request
+server; p50/p99 latency).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference] [--workload NAME]
 """
 import argparse
 import json
@@ -17,6 +23,8 @@ import subprocess
 import sys
 import tempfile
 import time
+
+import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -108,6 +116,11 @@ def workload(name):
 
 def describe(name, w, nrhs):
     n = "x".join(str(v) for v in w["n_el"])
+    if w.get("geometry") == "sine_bump":
+        return (f"{name}: 3D cube mapped by x = xi + 0.1 sin(pi xi1) sin(pi xi2) sin(pi xi3) (1,1,1), viscosity "
+                f"1 + 0.5 sin(2 pi x1) cos(2 pi x2), TH IGA p={w['p']}, {n} elements, FP64 CSR operator, "
+                f"P_D^G (geometry/viscosity-aware FD), {nrhs} seeded N(0,1) right-hand sides (pressure part "
+                f"mean-free), MINRES tol 1e-8 from x0=0")
     return (f"{name}: {w['dim']}D unit {'cube' if w['dim'] == 3 else 'square'}, {w['disc']} IGA, pressure degree "
             f"p={w['p']}, {n} elements, {nrhs} seeded N(0,1) right-hand sides (pressure part mean-free), "
             f"P_D-MINRES tol 1e-8 from x0=0")
@@ -120,55 +133,132 @@ def peaks():
         return {}
 
 
-def cpu_oracle_sample(w, seeds, iters_per_solve, k_iters=2):
+def oracle_operator(w):
+    """(S, matvec, preconditioner) of the oracle for a workload dict."""
+    import synth
+    from oracle import stokes
+    knots = [synth.open_uniform_knots(n, w["p"]) for n in w["n_el"]]
+    S = stokes.build(knots, w["p"], w.get("disc", "TH"))
+    if w.get("geometry") == "sine_bump":
+        from oracle import geometry as geo
+        G = geo.Grid(S)
+        P = geo.PDG(S, G)
+        return S, (lambda v: geo.matvec(S, G, v)), P.apply
+    return S, (lambda v: stokes.matvec(S, v)), (lambda v: stokes.apply_PD_inv(S, v))
+
+
+def cpu_oracle_sample(w, seeds, iters_per_solve, k_iters=2, op=None):
     """The oracle as it stands on the host cores: k_iters MINRES iterations at
     full workload size on one right-hand side, scaled to solves/s with the
-    iteration count of a full solve."""
-    import numpy as np
-
+    iteration count of a full solve (operator setup not timed)."""
     import synth
-    from oracle import minres, stokes
-    knots = [synth.open_uniform_knots(n, w["p"]) for n in w["n_el"]]
-    S = stokes.build(knots, w["p"], w["disc"])
+    from oracle import minres
+    S, mv, pc = op if op is not None else oracle_operator(w)
     b = synth.rhs(seeds[0], S.block_sizes)
     t0 = time.perf_counter()
-    minres.minres(lambda v: stokes.matvec(S, v), b, lambda v: stokes.apply_PD_inv(S, v), tol=0.0, maxit=k_iters)
+    minres.minres(mv, b, pc, tol=0.0, maxit=k_iters)
     dt = time.perf_counter() - t0
     t_iter = dt / (k_iters + 1)          # k iterations + the initial matvec/apply
     value = 1.0 / (t_iter * iters_per_solve)
     return dict(value=value, unit="solves/s", cores=os.cpu_count(), kind="oracle",
                 sample=(f"{k_iters} MINRES iterations of the NumPy/SciPy FP64 oracle on 1 right-hand side at "
-                        f"full size ({dt:.1f} s incl. the initial matvec+apply), per-iteration time x "
-                        f"{iters_per_solve:.1f} iterations per solve; BLAS threads = default (all cores)"),
+                        f"full size ({dt:.1f} s incl. the initial matvec+apply; operator setup untimed), "
+                        f"per-iteration time x {iters_per_solve:.1f} iterations per solve; BLAS threads = default "
+                        f"(all cores)"),
                 seconds=dt, t_iter_s=t_iter)
 
 
+def cpu_oracle_instances(specs, iters, k_iters=1, max_dof=4.0e6, count=3):
+    """Oracle solves/s over a sample of independent instances: the first
+    `count` instances with at most max_dof unknowns; each instance's solve time
+    = its oracle per-iteration time x its iteration count."""
+    import synth
+    from oracle import minres
+    picked, total, dts = [], 0.0, []
+    for spec, it in zip(specs, iters):
+        if len(picked) == count:
+            break
+        S, mv, pc = oracle_operator(spec)
+        if S.n_total > max_dof:
+            continue
+        b = synth.rhs(spec.get("seed", 1), S.block_sizes)
+        t0 = time.perf_counter()
+        minres.minres(mv, b, pc, tol=0.0, maxit=k_iters)
+        dt = time.perf_counter() - t0
+        dts.append(dt)
+        total += dt / (k_iters + 1) * it
+        picked.append(f"{spec['dim']}D {spec.get('disc', 'TH')} p={spec['p']} n_el={tuple(spec['n_el'])}")
+    value = len(picked) / total if total > 0 else None
+    return dict(value=value, unit="solves/s", cores=os.cpu_count(), kind="oracle",
+                sample=(f"{k_iters} oracle MINRES iteration(s) (+ initial matvec/apply) on each of {len(picked)} "
+                        f"instances ({'; '.join(picked)}; the first with <= {max_dof:.0e} unknowns), solve time = "
+                        f"per-iteration time x that instance's GPU iteration count; {sum(dts):.1f} s of CPU work"))
+
+
 # ------------------------------------------------------------------ reference arm (oracle on CPU)
+
+# Iterations per solve used to scale the oracle's per-iteration time when no GPU
+# run supplies them: 56 for the unit cube (P_D-MINRES, TH, p=3, the paper's cube
+# table), 60 for the others.
+REF_ITERS = {"cube_th_p3_64": 56.0}
+
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     w = workload(args.workload)
-    nrhs = args.nrhs or len(w["seeds"])
-    iters = 56.0   # iterations per solve used for scaling (cube TH P_D-MINRES, paper Table cube_TH)
-    for _ in range(args.warmup):
-        cpu_oracle_sample(w, w["seeds"], iters, k_iters=1)
-    vals, secs = [], []
-    for _ in range(args.steps):
-        r = cpu_oracle_sample(w, w["seeds"], iters, k_iters=1)
-        vals.append(r["value"])
-        secs.append(r["t_iter_s"] * iters)
+    kind = w.get("kind", "single")
+    iters = REF_ITERS.get(args.workload, 60.0)
+    if kind in ("batched", "serving"):
+        specs = instance_specs(args.workload, w)
+        vals, secs, cpu = [], [], None
+        for k in range(args.warmup + args.steps):
+            cpu = cpu_oracle_instances(specs, [iters] * len(specs), k_iters=1)
+            if k >= args.warmup:
+                vals.append(cpu["value"])
+                secs.append(1.0 / cpu["value"])
+        nrhs, cfg = 1, {"workload": args.workload + ": " + w_text(args.workload, w)}
+    else:
+        op = oracle_operator(w)
+        vals, secs = [], []
+        for k in range(args.warmup + args.steps):
+            r = cpu_oracle_sample(w, w["seeds"], iters, k_iters=1, op=op)
+            if k >= args.warmup:
+                vals.append(r["value"])
+                secs.append(r["t_iter_s"] * iters)
+        nrhs, cfg = 1, {"workload": describe(args.workload, w, 1), "nrhs": 1}
+        cpu = {"sample": "per step: 1 MINRES iteration (plus the initial matvec and apply) of the FP64 oracle at "
+                         f"full size on 1 RHS, scaled by {iters:.0f} iterations per solve"}
     value = statistics.median(vals)
     out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(secs), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-           "config": {"workload": describe(args.workload, w, 1), "nrhs": 1},
+           "config": cfg,
            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
-                            "sample": "per step: 1 MINRES iteration (plus the initial matvec and apply) of the "
-                                      "FP64 oracle at full size on 1 RHS, scaled by 56 iterations per solve"},
+                            "sample": cpu["sample"]},
            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
+
+
+def w_text(name, w):
+    if w.get("kind") == "batched":
+        return (f"{w['count']} independent unit-cube Taylor-Hood instances, p ~ U{{2..6}}, elements per direction "
+                f"~ U{{16..96}} (draw seed {w['seed']}), one seeded N(0,1) right-hand side each "
+                f"(seeds {w['rhs_seed0']}..{w['rhs_seed0'] + w['count'] - 1}), MINRES tol 1e-8 from x0=0")
+    return (f"Poisson arrivals at rates {w['rates']} req/s, {w['per_rate']} requests per rate; 50/50 mix of 3D "
+            f"unit-cube TH (p ~ U{{2..6}}, elements per direction ~ U{{16..48}}) and 2D TH/RT (p ~ U{{2..8}}, "
+            f"elements per direction ~ U{{32..256}}); MINRES tol 1e-8")
+
+
+def instance_specs(name, w):
+    import synth
+    if w.get("kind") == "batched":
+        out = synth.batched_instances(w["seed"], w["count"])
+        for i, o in enumerate(out):
+            o["seed"] = w["rhs_seed0"] + i
+        return out
+    return synth.serving_requests(0, w["rates"][0], w["per_rate"], w["seed"], w["mix_seed"])
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -197,9 +287,11 @@ def run_gpu(args):
         prec = fd.FD_F64 if args.fd == "f64" else fd.FD_TF32X3
     knots = synth.knots_for(w)
     t_setup = time.perf_counter()
-    mv = fd.MV_DF64 if args.matvec == "df64" else fd.MV_F64
+    mapped = w.get("geometry") == "sine_bump"
+    mv = fd.MV_DF64 if args.matvec == "df64" and not mapped else fd.MV_F64
+    geo = dict(geometry=fd.GEOM_SINE_BUMP, variant=fd.VARIANT_PD_GEO) if mapped else {}
     P = fd.Stokes(knots, w["p"], disc=fd.TH if w["disc"] == "TH" else fd.RT, fd_precision=prec, max_rhs=nrhs,
-                  matvec_precision=mv)
+                  matvec_precision=mv, **geo)
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t_setup
     # weak scaling: every rank solves its own batch (seeds shifted by rank)
@@ -261,7 +353,7 @@ def run_gpu(args):
     apply_err = None
     if prec != fd.FD_F64:
         P64 = fd.Stokes(knots, w["p"], disc=fd.TH if w["disc"] == "TH" else fd.RT, fd_precision=fd.FD_F64,
-                        max_rhs=1)
+                        max_rhs=1, **geo)
         s64 = torch.empty(P.n_total, dtype=torch.float64, device=dev)
         P64.apply_prec(b[:P.n_total].contiguous(), s64, stream=stream)
         torch.cuda.synchronize()
@@ -272,7 +364,16 @@ def run_gpu(args):
     pk = peaks()
     per_mv = tm["ms_matvec"] / max(tm["n_matvec"], 1)
     per_pc = tm["ms_prec"] / max(tm["n_prec"], 1)
-    if per_mv >= per_pc and mv == fd.MV_F64:
+    if per_mv >= per_pc and mapped:
+        nnz = P.flops_matvec / 2.0
+        kern = "csr_spmv_f64 (assembled mapped Stokes operator, one warp per row, 4 RHS per pass)"
+        # algorithmic bytes per launch: values + column indices + row pointers once, x and y once per RHS
+        flops = None
+        byts = 12.0 * nnz + 8.0 * (P.n_total + 1) + 16.0 * P.n_total * nrhs
+        t_ms = per_mv
+        peak, bound = pk.get("hbm_gbs", 6701.5), "hbm"
+        peak_note = "measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
+    elif per_mv >= per_pc and mv == fd.MV_F64:
         kern, flops, t_ms = "stokes_matvec_f64 (banded Kronecker mode products)", P.flops_matvec * nrhs, per_mv
         peak = FP64_NOMINAL_TFLOPS
         peak_note = "FP64 DFMA nominal 1.25 TFLOP/s (recipe table; measured DFMA chain 1.20)"
@@ -295,8 +396,11 @@ def run_gpu(args):
             bound = "tensor"
             peak_note = "TF32 = measured bf16 sustained x nominal TF32/BF16 ratio"
             flops *= 3  # three split products per contraction
-    achieved = flops / (t_ms / 1e3) / 1e12
-    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+    if bound == "hbm":
+        achieved, unit = byts / (t_ms / 1e3) / 1e9, "GB/s"
+    else:
+        achieved, unit = flops / (t_ms / 1e3) / 1e12, "TFLOP/s"
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
                 "traffic": None, "kernel": kern, "ms_per_launch": t_ms, "peak_source": peak_note}
 
     # end to end through the host-pointer entry point (pinned host buffers)
@@ -316,7 +420,7 @@ def run_gpu(args):
 
     cpu = None
     if rank == 0 and world == 1:
-        cpu = cpu_oracle_sample(w, w["seeds"], float(np.mean(iters)), k_iters=2)
+        cpu = cpu_oracle_sample(w, w["seeds"], float(np.mean(iters)), k_iters=1 if mapped else 2)
         cpu.pop("seconds", None)
         cpu.pop("t_iter_s", None)
 
@@ -330,7 +434,8 @@ def run_gpu(args):
                "config": {"workload": describe(args.workload, w, nrhs), "nrhs_per_gpu": nrhs,
                           "fd_precision": "f64" if prec == fd.FD_F64 else "tf32x3",
                           "matvec": ("double-float (FP32 pairs, 48-bit significand) in the iterations; "
-                                     "true residual in FP64") if mv == fd.MV_DF64 else "FP64",
+                                     "true residual in FP64") if mv == fd.MV_DF64 else
+                                    ("FP64 CSR SpMV (%d nonzeros)" % int(P.flops_matvec / 2) if mapped else "FP64"),
                           "n_total": P.n_total,
                           "l2": "inputs larger than L2 (each step streams %d x %.0f MB vectors)" % (
                               nrhs, P.n_total * 8 / 1e6),
@@ -350,10 +455,330 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------------ batched workload
+
+def _make_handles(fd, specs, local, threads=8, **kw):
+    """Set up one device handle per instance on host threads (the library's
+    setup is thread-safe; each thread selects the rank's GPU)."""
+    import torch
+    from concurrent.futures import ThreadPoolExecutor
+
+    import synth
+
+    def one(spec):
+        torch.cuda.set_device(local)
+        knots = [synth.open_uniform_knots(n, spec["p"]) for n in spec["n_el"]]
+        return fd.Stokes(knots, spec["p"], disc=fd.TH if spec.get("disc", "TH") == "TH" else fd.RT, max_rhs=1, **kw)
+
+    with ThreadPoolExecutor(threads) as ex:
+        return list(ex.map(one, specs))
+
+
+def run_batched(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_1712_00403_gb300 as fd
+    import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = workload(args.workload)
+    specs = instance_specs(args.workload, w)
+    for s_ in specs:
+        s_["seed"] += 1000 * rank
+    stream = torch.cuda.current_stream()
+
+    def timed_batch(prec, steps, warmup, host_e2e=False):
+        t0 = time.perf_counter()
+        hs = _make_handles(fd, specs, local, fd_precision=prec, matvec_precision=fd.MV_DF64)
+        torch.cuda.synchronize()
+        t_setup = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        B = fd.Batch(hs, autotune=True)
+        t_tune = time.perf_counter() - t0
+        bs = [torch.tensor(synth.rhs(sp["seed"], h.block_sizes), device=dev) for sp, h in zip(specs, hs)]
+        xs = [torch.zeros_like(b) for b in bs]
+
+        def step():
+            for x in xs:
+                x.zero_()
+            return B.solve(bs, xs, tol=1e-8, maxit=args.maxit, stream=stream)
+
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        l0 = fd.kernel_launches()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        infos = []
+        with ClockSampler(local) as clk:
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(steps):
+                infos.append(step())
+            e1.record(stream)
+            torch.cuda.synchronize()
+        launches = fd.kernel_launches() - l0
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        res = dict(ms=ms, infos=infos, launches=launches, clocks=clk.summary(), setup_s=t_setup, tune_s=t_tune,
+                   info=B.info(), n_total=[h.n_total for h in hs])
+        if host_e2e:
+            # end to end: pinned host right-hand sides in, solutions out, copies inside the timed region
+            bh = [torch.empty(b.numel(), dtype=torch.float64, pin_memory=True).copy_(b.cpu()) for b in bs]
+            xh = [torch.empty(b.numel(), dtype=torch.float64, pin_memory=True) for b in bs]
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for b, bhost in zip(bs, bh):
+                b.copy_(bhost, non_blocking=True)
+            step()
+            for x, xhost in zip(xs, xh):
+                xhost.copy_(x, non_blocking=True)
+            torch.cuda.synchronize()
+            res["e2e_s"] = time.perf_counter() - t0
+            res["bytes"] = sum(b.numel() for b in bs) * 8
+        # FD apply error vs the FP64 apply on a sample of instances (kept for the FP64 pass)
+        res["apply_out"] = []
+        for i in range(4):
+            s_out = torch.empty_like(bs[i])
+            hs[i].apply_prec(bs[i], s_out, stream=stream)
+            res["apply_out"].append(s_out)
+        torch.cuda.synchronize()
+        B.close()
+        for h in hs:
+            h.close()
+        return res
+
+    tc = timed_batch(fd.FD_TF32X3, args.steps, args.warmup, host_e2e=True)
+    f64 = timed_batch(fd.FD_F64, max(1, args.steps // 3 or 1), max(3, args.warmup // 2))
+    errs = [float(torch.linalg.norm(a - b) / torch.linalg.norm(b)) for a, b in zip(tc["apply_out"], f64["apply_out"])]
+    n = len(specs)
+    value = args.steps * n * world / (tc["ms"] / 1e3)
+    it_tc = [i["iterations"] for inf in tc["infos"] for i in inf]
+    it_64 = [i["iterations"] for inf in f64["infos"] for i in inf]
+    st_tc = sorted(set(i["status"] for inf in tc["infos"] for i in inf))
+    tr_tc = max(i["true_rel_res"] for inf in tc["infos"] for i in inf)
+    tr_64 = max(i["true_rel_res"] for inf in f64["infos"] for i in inf)
+    value64 = len(f64["infos"]) * n * world / (f64["ms"] / 1e3)
+    # roofline of the grouped split-TF32 FD apply (one launch chain over all instances, autotuner timing)
+    flops_apply = 0.0
+    for sp in specs:
+        p = sp["p"]
+        nv = [2 * e + p - 2 for e in sp["n_el"]]
+        nq = [e + p for e in sp["n_el"]]
+        Nv, Nq = float(np.prod(nv)), float(np.prod(nq))
+        flops_apply += 3 * 4 * Nv * sum(nv) + 4 * Nq * sum(nq)
+    pk = peaks()
+    peak = pk.get("bf16_tflops_sustained", 1748.4) * TF32_OVER_BF16
+    ms_apply = tc["info"]["ms_apply"]
+    achieved = 3 * flops_apply / (ms_apply / 1e3) / 1e12 if ms_apply > 0 else None
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if achieved else None, "traffic": None,
+                "kernel": "grouped split-TF32 FD apply over all 64 instances (tcgen05), autotuner's CUDA-event time",
+                "ms_per_launch": ms_apply,
+                "peak_source": "TF32 = measured bf16 sustained x nominal TF32/BF16 ratio; flops = 3 split products "
+                               "x 4 N sum(n_d) per velocity component + 4 N_q sum(n_q) per pressure"}
+    cpu = None
+    if rank == 0 and world == 1:
+        cpu = cpu_oracle_instances(specs, it_tc[:n], k_iters=1)
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": tc["ms"] / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f64+tf32x3 (matvec df64)", "data": "synthetic",
+               "config": {"workload": args.workload + ": " + w_text(args.workload, w),
+                          "total_dof": int(sum(tc["n_total"])), "max_dof": int(max(tc["n_total"])),
+                          "l2": "inputs larger than L2 (%.1f GB of right-hand sides)" % (sum(tc["n_total"]) * 8e-9),
+                          "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+               "minres": {"iterations_min": min(it_tc), "iterations_max": max(it_tc), "iterations_mean":
+                          float(np.mean(it_tc)), "status": st_tc, "true_rel_res_max": tr_tc},
+               "fp64_fd": {"solves_per_s": value64, "ms_per_step": f64["ms"] / len(f64["infos"]),
+                           "iterations_mean": float(np.mean(it_64)), "true_rel_res_max": tr_64,
+                           "ms_apply_grouped": f64["info"]["ms_apply"],
+                           "iteration_delta_max": max(abs(a - b) for a, b in zip(it_tc[:n], it_64[:n]))},
+               "fd_apply_rel_err_vs_f64": errs,
+               "autotune": tc["info"], "setup_s": tc["setup_s"], "autotune_s": tc["tune_s"],
+               "roofline": roofline, "cpu_baseline": cpu,
+               "e2e": {"value": n * world / tc["e2e_s"], "unit": "solves/s", "h2d_bytes_per_step": tc["bytes"],
+                       "d2h_bytes_per_step": tc["bytes"]},
+               "gpu_launches": tc["launches"], "clocks": tc["clocks"]}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ serving workload
+
+def run_serving(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_1712_00403_gb300 as fd
+    import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    w = workload(args.workload)
+
+    def stream_of(reqs):
+        out = []
+        for r in reqs:
+            knots = [synth.open_uniform_knots(n, r["p"]) for n in r["n_el"]]
+            sizes = block_sizes(r)
+            out.append((r, knots, synth.rhs(r["seed"] + 1000 * rank, sizes)))
+        return out
+
+    def serve(reqs, max_active=16):
+        server = fd.Server(max_active=max_active, iters_per_step=4, fd_precision=fd.FD_TF32X3,
+                           matvec_precision=fd.MV_DF64, tol=1e-8, maxit=args.maxit)
+        ids, k = [], 0
+        l0 = fd.kernel_launches()
+        t0 = time.perf_counter()
+        while True:
+            now = time.perf_counter() - t0
+            while k < len(reqs) and reqs[k][0]["t"] <= now:
+                r, knots, b = reqs[k]
+                ids.append(server.submit(knots, r["p"], b, r["t"], disc=fd.TH if r["disc"] == "TH" else fd.RT))
+                k += 1
+            active, queued, finished = server.step(time.perf_counter() - t0)
+            if finished == len(reqs):
+                break
+            if active == 0 and queued == 0 and k < len(reqs):
+                time.sleep(max(0.0, reqs[k][0]["t"] - (time.perf_counter() - t0)))
+        t_end = time.perf_counter() - t0
+        launches = fd.kernel_launches() - l0
+        results = [server.result(i) for i in ids]
+        st = server.stats()
+        server.close()
+        return results, t_end, launches, st
+
+    # warm-up: a short stream of other requests (context, kernels, autotuning paths)
+    warm = stream_of(synth.serving_requests(9, 200.0, 8, w["seed"] + 90, w["mix_seed"] + 90, nel3=(8, 16)))
+    for _ in range(max(1, args.warmup // 3)):
+        serve(warm)
+    per_rate, all_lat, total_solves, total_time, launches, clocks = [], [], 0, 0.0, 0, None
+    err_sample = []
+    with ClockSampler(local) as clk:
+        for ri, rate in enumerate(w["rates"]):
+            reqs = stream_of(synth.serving_requests(ri, rate, w["per_rate"], w["seed"], w["mix_seed"]))
+            torch.cuda.synchronize()
+            res, t_end, nl, st = serve(reqs)
+            launches += nl
+            lat = [r["t_done"] - r["t_arrival"] for r in res]
+            wait = [r["t_admit"] - r["t_arrival"] for r in res]
+            ok = sum(r["status"] == "OK" for r in res)
+            thr = len(res) / (t_end - reqs[0][0]["t"])
+            per_rate.append({"rate_req_s": rate, "requests": len(res), "ok": ok, "solves_per_s": thr,
+                             "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                             "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                             "mean_admission_wait_ms": 1e3 * float(np.mean(wait)),
+                             "true_rel_res_max": max(r["true_rel_res"] for r in res),
+                             "iterations_mean": float(np.mean([r["iterations"] for r in res])),
+                             "handles_created": st["handles_created"], "handles_reused": st["handles_reused"],
+                             "max_active_seen": st["max_active_seen"]})
+            all_lat += lat
+            total_solves += len(res)
+            total_time += t_end - reqs[0][0]["t"]
+            # per-request error vs the FP64 oracle: true residual under the oracle operator for the three
+            # smallest requests of each stream, and distance to the oracle's own solve for the smallest of the first
+            if rank == 0 and world == 1:
+                order = sorted(range(len(reqs)), key=lambda i: int(np.sum(block_sizes(reqs[i][0]))))
+                for j, i in enumerate(order[:3]):
+                    err_sample.append(oracle_error(reqs[i], res[i], solve=(ri == 0 and j == 0)))
+        clocks = clk.summary()
+    tot = torch.tensor([float(total_solves), total_time], dtype=torch.float64)
+    if world > 1:
+        tt = tot.cuda()
+        dist.all_reduce(tt[:1])
+        dist.all_reduce(tt[1:], op=dist.ReduceOp.MAX)
+        tot = tt.cpu()
+    value = float(tot[0]) / float(tot[1])
+    cpu = None
+    if rank == 0 and world == 1:
+        specs = [r for r, _, _ in stream_of(synth.serving_requests(0, w["rates"][0], w["per_rate"], w["seed"],
+                                                                  w["mix_seed"]))]
+        its = [pr["iterations_mean"] for pr in per_rate[:1]] * len(specs)
+        cpu = cpu_oracle_instances(specs, its, k_iters=1)
+        cpu["sample"] += "; iteration count = mean GPU iterations of the 50 req/s stream"
+    if rank == 0:
+        h2d = int(sum(np.sum(block_sizes(r)) for r in
+                      synth.serving_requests(0, w["rates"][0], w["per_rate"], w["seed"], w["mix_seed"])) * 8)
+        out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+               "steps": len(w["rates"]), "warmup": max(1, args.warmup // 3),
+               "ms_per_step": 1e3 * float(tot[1]) / len(w["rates"]), "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f64+tf32x3 (matvec df64)", "data": "synthetic",
+               "config": {"workload": "serving: " + w_text(args.workload, w),
+                          "server": "max_active 16, 4 MINRES iterations per scheduler step, HBM budget 90% of free, "
+                                    "handles set up on 8 host threads",
+                          "timing": "host wall clock from each stream's first arrival to its last completion "
+                                    "(latency = completion - arrival, host clock)",
+                          "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+               "serving": {"per_rate": per_rate, "p50_ms_all": 1e3 * float(np.percentile(all_lat, 50)),
+                           "p99_ms_all": 1e3 * float(np.percentile(all_lat, 99))},
+               "per_request_error_vs_fp64_oracle": err_sample,
+               "cpu_baseline": cpu,
+               "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d,
+                       "note": "requests enter and leave as host arrays; the value above is already end to end"},
+               "roofline": None, "gpu_launches": launches, "clocks": clocks}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def block_sizes(r):
+    p = r["p"]
+    n_el = r["n_el"]
+    if r.get("disc", "TH") == "TH":
+        nv = int(np.prod([2 * e + p - 2 for e in n_el]))
+        return [nv] * len(n_el) + [int(np.prod([e + p for e in n_el]))]
+    out = []
+    for k in range(len(n_el)):
+        out.append(int(np.prod([(e + p - 1) if d == k else (e + p) for d, e in enumerate(n_el)])))
+    return out + [int(np.prod([e + p for e in n_el]))]
+
+
+def oracle_error(req, res, solve=False):
+    """True relative residual of a served solution under the oracle's FP64
+    operator and, with solve=True, its distance to the oracle's own MINRES
+    solution (tolerance 1e-10)."""
+    from oracle import minres
+    r, knots, b = req
+    S, mv, pc = oracle_operator(r)
+    x = res["x"]
+    out = {"request": f"{r['dim']}D {r['disc']} p={r['p']} n_el={tuple(r['n_el'])}", "n": int(S.n_total),
+           "oracle_rel_res": float(np.linalg.norm(b - mv(x)) / np.linalg.norm(b))}
+    if solve:
+        xo, _ = minres.minres(mv, b, pc, tol=1e-10, maxit=2000, true_check=True)
+        out["rel_err_vs_oracle_solve"] = float(np.linalg.norm(x - xo) / np.linalg.norm(xo))
+    return out
+
+
 def main():
     args = parse()
+    kind = workload(args.workload).get("kind", "single")
     if args.impl == "reference":
         run_reference(args)
+    elif kind == "batched":
+        run_batched(args)
+    elif kind == "serving":
+        run_serving(args)
     else:
         run_gpu(args)
 

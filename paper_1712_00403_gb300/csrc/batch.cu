@@ -676,6 +676,8 @@ fdst_status fdst_batch_solve(fdst_batch b, const double *const *d_b, double *con
     b->graph = nullptr;
   }
   std::vector<MinresState> hs(n);
+  std::vector<double> prev_true(n, -1.0);
+  std::vector<int> restarts(n, 0);
   int it = 0;
   bool residuals_current = false;
   const int check_every = 4;
@@ -704,21 +706,32 @@ fdst_status fdst_batch_solve(fdst_batch b, const double *const *d_b, double *con
       if (*b->h_n_stopped >= n) {
         TRY(true_residuals());
         residuals_current = true;
-        std::vector<int> resume;
+        int running = 0;
         for (int i = 0; i < n; ++i) {
-          CK(cudaMemcpy(&hs[i], b->hs[i]->state, sizeof(MinresState), cudaMemcpyDeviceToHost));
-          if (hs[i].status == 0 && hs[i].stop && hs[i].gamma > 0.0 && true_rel[i] > tol && hs[i].iters < maxit)
-            resume.push_back(i);
+          fdst_ctx *h = b->hs[i];
+          CK(cudaMemcpy(&hs[i], h->state, sizeof(MinresState), cudaMemcpyDeviceToHost));
+          const int a = resume_action(hs[i], true_rel[i], prev_true[i], restarts[i], tol, maxit);
+          if (a == kKeepStopped) continue;
+          prev_true[i] = true_rel[i];
+          std::vector<MinresState> one{hs[i]};
+          if (a == kStagnated) {
+            one[0].status = FDST_STAGNATION;
+            CK(cudaMemcpy(h->state, one.data(), sizeof(MinresState), cudaMemcpyHostToDevice));
+          } else if (a == kRestart) {
+            ++restarts[i];
+            TRY(minres_restart(h, h->hb, h->hx, 1, {0}, {true_rel[i]}, tol, one, st));
+            if (!one[0].stop && one[0].status == 0) ++running;
+          } else {
+            one[0].tau = 0.5 * one[0].tau * tol / true_rel[i];
+            one[0].stop = 0;
+            const int zero = 0;
+            CK(cudaMemcpy(h->state, one.data(), sizeof(MinresState), cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(h->done, &zero, sizeof(int), cudaMemcpyHostToDevice));
+            ++running;
+          }
         }
-        if (resume.empty()) break;
-        for (int i : resume) {
-          hs[i].tau = 0.5 * hs[i].tau * tol / true_rel[i];
-          hs[i].stop = 0;
-          const int zero = 0;
-          CK(cudaMemcpy(b->hs[i]->state, &hs[i], sizeof(MinresState), cudaMemcpyHostToDevice));
-          CK(cudaMemcpy(b->hs[i]->done, &zero, sizeof(int), cudaMemcpyHostToDevice));
-        }
-        const int ns = n - (int)resume.size();
+        if (running == 0) break;
+        const int ns = n - running;
         CK(cudaMemcpy(b->n_stopped, &ns, sizeof(int), cudaMemcpyHostToDevice));
       }
     }

@@ -139,4 +139,26 @@ fdst_status run_apply(fdst_ctx *h, const double *r, double *s, int nrhs, const i
 fdst_status run_matvec(fdst_ctx *h, const double *x, double *y, int nrhs, const int *done, cudaStream_t st,
                        bool exact = false);
 
+// What to do with a right-hand side whose recurrence estimate met its
+// threshold, given its FP64 true relative residual now and at its previous
+// check (negative: none). The recurrence is resumed with a tighter threshold
+// (its state intact) while resumes keep lowering the true residual; once a
+// resume leaves it within a factor 0.7 of the previous value the recurrence
+// has drifted away from the true residual (rounding in the iterations'
+// matvec), and MINRES is restarted from the current iterate, at most
+// kMaxRestarts times before the solve is reported as stagnated.
+enum { kKeepStopped = 0, kResume = 1, kRestart = 2, kStagnated = 3 };
+constexpr int kMaxRestarts = 3;
+int resume_action(const MinresState &S, double true_rel, double prev_true, int restarts, double tol, int maxit);
+
+// Restarts MINRES for the right-hand sides listed in `which` from the current
+// iterate x: v = b - A x (FP64), z = P^{-1} v / gamma, direction vectors
+// zeroed; their state keeps eta0 and the iteration count, and the estimate
+// threshold becomes the one that corresponds to tol at the restart point.
+// Leaves h->done[j] = 0 for the listed ones and 1 for every other one;
+// hs (host copy of the states) is updated and uploaded.
+fdst_status minres_restart(fdst_ctx *h, const double *b, double *x, int nrhs, const std::vector<int> &which,
+                           const std::vector<double> &true_rel, double tol, std::vector<MinresState> &hs,
+                           cudaStream_t st);
+
 }  // namespace fdst

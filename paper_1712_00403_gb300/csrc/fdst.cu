@@ -578,6 +578,52 @@ static fdst_status run_matvec_df(fdst_ctx *h, const double *x, double *y, int nr
   return FDST_OK;
 }
 
+int resume_action(const MinresState &S, double true_rel, double prev_true, int restarts, double tol, int maxit) {
+  if (!(S.status == 0 && S.stop && S.gamma > 0.0 && true_rel > tol && S.iters < maxit)) return kKeepStopped;
+  if (prev_true > 0.0 && true_rel > 0.7 * prev_true) return restarts < kMaxRestarts ? kRestart : kStagnated;
+  return kResume;
+}
+
+fdst_status minres_restart(fdst_ctx *h, const double *b, double *x, int nrhs, const std::vector<int> &which,
+                           const std::vector<double> &true_rel, double tol, std::vector<MinresState> &hs,
+                           cudaStream_t st) {
+  const int64_t n = h->n_total;
+  std::vector<int> mask(nrhs, 1);
+  for (int j : which) mask[j] = 0;
+  CK(cudaMemcpyAsync(h->done, mask.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, st));
+  TRY(run_matvec(h, x, h->Az, nrhs, h->done, st, true));
+  launch_restart_vectors(b, h->Az, h->v, h->v_old, h->w, h->w_old, n, n, nrhs, h->done, st);
+  TRY(run_apply(h, h->v, h->z, nrhs, h->done, st));
+  launch_dot(h->v, h->z, n, n, nrhs, h->partials, h->counters, h->dots, h->done, st);
+  std::vector<double> g(nrhs);
+  CK(cudaMemcpyAsync(g.data(), h->dots, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int j : which) {
+    MinresState &S = hs[j];
+    if (!(g[j] > 0.0) || std::isinf(g[j])) {
+      S.status = std::isnan(g[j]) || std::isinf(g[j]) ? FDST_NAN_DETECTED : FDST_BREAKDOWN;
+      S.stop = 1;
+      mask[j] = 1;
+      continue;
+    }
+    const double gamma = std::sqrt(g[j]);
+    S.gamma = gamma;
+    S.gamma_old = 1.0;
+    S.c = S.c_old = 1.0;
+    S.s = S.s_old = 0.0;
+    S.eta = gamma;
+    S.inv_gamma_new = 1.0 / gamma;
+    S.tau = 0.5 * (S.eta0 > 0.0 ? gamma / S.eta0 : 1.0) * tol / true_rel[j];
+    S.stop = 0;
+    S.status = 0;
+  }
+  CK(cudaMemcpyAsync(h->state, hs.data(), sizeof(MinresState) * nrhs, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(h->done, mask.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, st));
+  launch_scale_by_inv_gamma(h->z, h->state, n, n, nrhs, h->done, st);
+  CK(cudaStreamSynchronize(st));
+  return FDST_OK;
+}
+
 // exact = true forces the FP64 (DFMA) evaluation (true-residual checks).
 fdst_status run_matvec(fdst_ctx *h, const double *x, double *y, int nrhs, const int *done, cudaStream_t st,
                        bool exact) {
@@ -688,7 +734,9 @@ fdst_status fdst_setup(const fdst_desc *desc, fdst_handle *out) {
     set_error("pinned host allocation failed");
     return fail(FDST_CUDA_ERROR);
   }
-  if (cudaDeviceSynchronize() != cudaSuccess) {
+  // Setup work runs on the legacy default stream only; waiting on it (not on
+  // the whole device) lets a handle be set up while other streams compute.
+  if (cudaStreamSynchronize(0) != cudaSuccess) {
     set_error(std::string("setup: ") + cudaGetErrorString(cudaGetLastError()));
     return fail(FDST_CUDA_ERROR);
   }
@@ -807,6 +855,8 @@ fdst_status fdst_solve(fdst_handle h, const double *d_b, double *d_x, int nrhs, 
     return FDST_OK;
   };
   std::vector<MinresState> hs(nrhs);
+  std::vector<double> prev_true(nrhs, -1.0);
+  std::vector<int> restarts(nrhs, 0);
   const int check_every = 4;
   int it = 0;
   bool residuals_current = false;
@@ -841,18 +891,32 @@ fdst_status fdst_solve(fdst_handle h, const double *d_b, double *d_x, int nrhs, 
         TRY(true_residuals());
         residuals_current = true;
         CK(cudaMemcpy(hs.data(), h->state, sizeof(MinresState) * nrhs, cudaMemcpyDeviceToHost));
-        std::vector<int> resume;
-        for (int j = 0; j < nrhs; ++j)
-          if (hs[j].status == 0 && hs[j].stop && hs[j].gamma > 0.0 && true_rel[j] > tol && hs[j].iters < maxit)
-            resume.push_back(j);
-        if (resume.empty()) break;
-        std::vector<int> hd(nrhs, 1);
+        std::vector<int> resume, restart;
+        for (int j = 0; j < nrhs; ++j) {
+          const int a = resume_action(hs[j], true_rel[j], prev_true[j], restarts[j], tol, maxit);
+          if (a == kKeepStopped) continue;
+          if (a == kStagnated) hs[j].status = FDST_STAGNATION;
+          else (a == kResume ? resume : restart).push_back(j);
+          prev_true[j] = true_rel[j];
+        }
+        if (resume.empty() && restart.empty()) {
+          CK(cudaMemcpy(h->state, hs.data(), sizeof(MinresState) * nrhs, cudaMemcpyHostToDevice));
+          break;
+        }
         for (int j : resume) {
           hs[j].tau = 0.5 * hs[j].tau * tol / true_rel[j];
           hs[j].stop = 0;
-          hd[j] = 0;
         }
-        int ns = nrhs - (int)resume.size();
+        if (!restart.empty()) {
+          for (int j : restart) ++restarts[j];
+          TRY(minres_restart(h, d_b, d_x, nrhs, restart, true_rel, tol, hs, st));
+        }
+        std::vector<int> hd(nrhs, 1);
+        for (int j : resume) hd[j] = 0;
+        for (int j : restart)
+          if (!hs[j].stop && hs[j].status == 0) hd[j] = 0;
+        int ns = 0;
+        for (int j = 0; j < nrhs; ++j) ns += hd[j];
         CK(cudaMemcpy(h->state, hs.data(), sizeof(MinresState) * nrhs, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(h->done, hd.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(h->n_stopped, &ns, sizeof(int), cudaMemcpyHostToDevice));

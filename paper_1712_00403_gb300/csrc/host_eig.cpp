@@ -1,8 +1,11 @@
 // Host FP64 dense linear algebra for the setup: Cholesky, SPD inverse and the
 // generalized symmetric eigenproblem K U = M U Lambda with U^T M U = I
 // (paper eq. eig_dec; Algorithm 1 step 1). Reduction to a standard problem
-// C = L^{-1} K L^{-T} and cyclic Jacobi rotations (Jacobi 1846; Rutishauser's
-// stable rotation formulas), U = L^{-T} V.
+// C = L^{-1} K L^{-T}, then for n <= 48 cyclic Jacobi rotations (Jacobi 1846;
+// Rutishauser's stable rotation formulas) and for larger n Householder
+// reduction to tridiagonal form followed by the implicit QL iteration with
+// Wilkinson shifts (Bowdler, Martin, Reinsch and Wilkinson 1968), both
+// accumulating the orthogonal V; U = L^{-T} V.
 #include <cmath>
 #include <vector>
 
@@ -98,6 +101,106 @@ static void jacobi(Mat &A, std::vector<double> &lam, Mat &V) {
   for (int i = 0; i < n; ++i) lam[i] = A(i, i);
 }
 
+// Householder reduction of the symmetric matrix A (destroyed) to tridiagonal
+// form A = Q T Q^T (diagonal d, subdiagonal e[1..n-1]), Q accumulated.
+static void tridiagonalize(Mat &A, std::vector<double> &d, std::vector<double> &e, Mat &Q) {
+  const int n = A.rows;
+  d.assign(n, 0.0);
+  e.assign(n, 0.0);
+  Q = Mat(n, n);
+  for (int i = 0; i < n; ++i) Q(i, i) = 1.0;
+  std::vector<double> v(n), p(n), w(n);
+  for (int k = 0; k + 2 < n; ++k) {
+    // reflector H = I - beta v v^T mapping A[k+1:, k] onto a multiple of e_{k+1}
+    double norm = 0.0;
+    for (int i = k + 1; i < n; ++i) norm += A(i, k) * A(i, k);
+    norm = std::sqrt(norm);
+    if (norm == 0.0) continue;
+    const double x0 = A(k + 1, k);
+    const double alpha = x0 >= 0 ? -norm : norm;
+    for (int i = 0; i < n; ++i) v[i] = 0.0;
+    v[k + 1] = x0 - alpha;
+    for (int i = k + 2; i < n; ++i) v[i] = A(i, k);
+    double vv = 0.0;
+    for (int i = k + 1; i < n; ++i) vv += v[i] * v[i];
+    if (vv == 0.0) continue;
+    const double beta = 2.0 / vv;
+    // A <- H A H on the trailing block: p = beta A v, w = p - (beta/2)(v.p) v, A -= v w^T + w v^T
+    for (int i = k; i < n; ++i) {
+      double s = 0.0;
+      for (int j = k + 1; j < n; ++j) s += A(i, j) * v[j];
+      p[i] = beta * s;
+    }
+    double vp = 0.0;
+    for (int i = k + 1; i < n; ++i) vp += v[i] * p[i];
+    const double kk = 0.5 * beta * vp;
+    for (int i = k; i < n; ++i) w[i] = p[i] - kk * v[i];
+    for (int i = k; i < n; ++i)
+      for (int j = k; j < n; ++j) A(i, j) -= v[i] * w[j] + w[i] * v[j];
+    // Q <- Q H
+    for (int i = 0; i < n; ++i) {
+      double s = 0.0;
+      for (int j = k + 1; j < n; ++j) s += Q(i, j) * v[j];
+      s *= beta;
+      for (int j = k + 1; j < n; ++j) Q(i, j) -= s * v[j];
+    }
+  }
+  for (int i = 0; i < n; ++i) d[i] = A(i, i);
+  for (int i = 1; i < n; ++i) e[i] = A(i, i - 1);
+}
+
+// Implicit QL iteration with Wilkinson shifts on the tridiagonal (d, e),
+// rotations accumulated into the columns of Z (eigenvalues in d).
+static bool tridiag_ql(std::vector<double> &d, std::vector<double> &e, Mat &Z) {
+  const int n = (int)d.size();
+  for (int i = 1; i < n; ++i) e[i - 1] = e[i];
+  if (n > 0) e[n - 1] = 0.0;
+  for (int l = 0; l < n; ++l) {
+    int iter = 0;
+    while (true) {
+      int m = l;
+      for (; m < n - 1; ++m) {
+        const double dd = std::fabs(d[m]) + std::fabs(d[m + 1]);
+        if (std::fabs(e[m]) <= 1e-16 * dd) break;
+      }
+      if (m == l) break;
+      if (++iter > 60) return false;
+      double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+      double r = std::hypot(g, 1.0);
+      g = d[m] - d[l] + e[l] / (g + (g >= 0 ? r : -r));
+      double s = 1.0, c = 1.0, pp = 0.0;
+      int i = m - 1;
+      for (; i >= l; --i) {
+        double f = s * e[i], b = c * e[i];
+        r = std::hypot(f, g);
+        e[i + 1] = r;
+        if (r == 0.0) {
+          d[i + 1] -= pp;
+          e[m] = 0.0;
+          break;
+        }
+        s = f / r;
+        c = g / r;
+        g = d[i + 1] - pp;
+        r = (d[i] - g) * s + 2.0 * c * b;
+        pp = s * r;
+        d[i + 1] = g + pp;
+        g = c * r - b;
+        for (int k = 0; k < Z.rows; ++k) {
+          const double zf = Z(k, i + 1);
+          Z(k, i + 1) = s * Z(k, i) + c * zf;
+          Z(k, i) = c * Z(k, i) - s * zf;
+        }
+      }
+      if (r == 0.0 && i >= l) continue;
+      d[l] -= pp;
+      e[l] = g;
+      e[m] = 0.0;
+    }
+  }
+  return true;
+}
+
 bool gen_eig(const Mat &K, const Mat &M, std::vector<double> &lam, Mat &U) {
   Mat L = M;
   if (!cholesky(L)) return false;
@@ -112,7 +215,16 @@ bool gen_eig(const Mat &K, const Mat &M, std::vector<double> &lam, Mat &U) {
       Ct(i, j) = Ct(j, i) = v;
     }
   Mat V;
-  jacobi(Ct, lam, V);
+  if (Ct.rows <= 48) {
+    jacobi(Ct, lam, V);
+  } else {
+    // larger pencils: Householder tridiagonalization + implicit QL (about 4 n^3 flops
+    // instead of about 20 n^3 for the Jacobi sweeps)
+    std::vector<double> d, e;
+    tridiagonalize(Ct, d, e, V);
+    if (!tridiag_ql(d, e, V)) return false;
+    lam = d;
+  }
   U = V;
   upper_t_solve(L, U);        // U = L^{-T} V
   return true;

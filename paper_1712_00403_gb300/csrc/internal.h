@@ -64,7 +64,8 @@ Mat stiffness_matrix(const Space1D &s, int npts, const std::vector<double> &wt =
 // Cholesky M = L L^T in place (lower). Returns false when M is not SPD.
 bool cholesky(Mat &M);
 // Generalized symmetric eigenproblem K U = M U diag(lam), U^T M U = I (eq. eig_dec),
-// by Cholesky reduction and cyclic Jacobi. Returns false when M is not SPD.
+// by Cholesky reduction, then cyclic Jacobi (n <= 48) or Householder
+// tridiagonalization + implicit QL (larger n). Returns false when M is not SPD.
 bool gen_eig(const Mat &K, const Mat &M, std::vector<double> &lam, Mat &U);
 // Inverse of an SPD matrix via Cholesky. Returns false when not SPD.
 bool spd_inverse(const Mat &M, Mat &Minv);

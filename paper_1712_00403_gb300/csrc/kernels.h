@@ -123,6 +123,9 @@ void launch_minres_scalars(MinresState *st, const double *delta, const double *g
 void launch_minres_update(double *w_old, double *w, double *x, double *z, const double *z_new,
                           MinresState *st, int64_t n, int64_t stride, int nrhs, int *done, cudaStream_t s);
 void launch_minres_commit(MinresState *st, int *done, int nrhs, cudaStream_t s);
+// v = b - Ax, v_old = w = w_old = 0 for the right-hand sides with done[j] == 0.
+void launch_restart_vectors(const double *b, const double *Ax, double *v, double *v_old, double *w, double *w_old,
+                            int64_t n, int64_t stride, int nrhs, const int *done, cudaStream_t s);
 // z <- z / gamma (per right-hand side) used at start.
 void launch_scale_by_inv_gamma(double *z, const MinresState *st, int64_t n, int64_t stride, int nrhs,
                                const int *done, cudaStream_t s);

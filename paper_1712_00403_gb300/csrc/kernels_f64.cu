@@ -546,4 +546,28 @@ void launch_minres_commit(MinresState *st, int *done, int nrhs, cudaStream_t s) 
   k_minres_commit<<<(nrhs + 63) / 64, 64, 0, s>>>(st, done, nrhs);
 }
 
+// Restart vectors of the right-hand sides with done[j] == 0: v = b - Ax (Ax
+// precomputed), v_old = w = w_old = 0.
+__global__ void k_restart_vectors(const double *b, const double *Ax, double *v, double *v_old, double *w,
+                                  double *w_old, int64_t n, int64_t stride, const int *done) {
+  const int j = blockIdx.y;
+  if (done[j]) return;
+  const int64_t o = j * stride;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    v[o + i] = b[o + i] - Ax[o + i];
+    v_old[o + i] = 0.0;
+    w[o + i] = 0.0;
+    w_old[o + i] = 0.0;
+  }
+}
+
+void launch_restart_vectors(const double *b, const double *Ax, double *v, double *v_old, double *w, double *w_old,
+                            int64_t n, int64_t stride, int nrhs, const int *done, cudaStream_t s) {
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  count_launch(1);
+  k_restart_vectors<<<dim3((unsigned)blocks, nrhs), 256, 0, s>>>(b, Ax, v, v_old, w, w_old, n, stride, done);
+}
+
 }  // namespace fdst

@@ -33,6 +33,8 @@
 // memory and returns.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include <cstdint>
 #include <cstring>
 #include <vector>
@@ -578,6 +580,8 @@ fdst_status launch_gemm_tc(const TcGroup &g, int nrhs, const int *done, cudaStre
   }
   const int smem = nring * stage_bytes + 1024 + 1024;
   static int configured = 0, nsm = 0;
+  static std::mutex init_mutex;
+  std::lock_guard<std::mutex> lock(init_mutex);
   if (!g_err_flag) {
     if (cudaMalloc(&g_err_flag, sizeof(int)) != cudaSuccess || cudaMemset(g_err_flag, 0, sizeof(int)) != cudaSuccess) {
       set_error("tensor-core error flag allocation failed");

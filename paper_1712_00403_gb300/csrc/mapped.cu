@@ -274,7 +274,7 @@ fdst_status build_mapped_pre(fdst_ctx *h) {
           }
     }
   }
-  CK(cudaDeviceSynchronize());
+  CK(cudaStreamSynchronize(st));
   return FDST_OK;
 }
 

@@ -6,9 +6,11 @@
 // solution to host memory and free their slot (the device handle goes to an
 // idle cache keyed by problem shape, so U_d, Lambda_d, banded factors and
 // workspaces stay resident for the next request of the same shape), the
-// others continue with a tighter threshold; (2) queued requests are admitted
-// while the active-slot limit and the HBM budget allow (idle handles are
-// evicted least-recently-used first); (3) the active set, if it changed, is
+// others continue with a tighter threshold; (2) device handles for queued
+// requests are set up on host threads while the GPU iterates (within the HBM
+// budget, evicting idle handles least-recently-used first), and queued
+// requests whose handle is ready are admitted in arrival order while
+// active slots are free; (3) the active set, if it changed, is
 // re-tabled as one batch, and (4) a few MINRES iterations advance every
 // active problem together with grouped launches. Requests that arrive while
 // others are on the GPU join between steps; their work overlaps on the device.
@@ -16,6 +18,7 @@
 
 #include <cmath>
 #include <deque>
+#include <future>
 #include <list>
 #include <map>
 #include <sstream>
@@ -40,6 +43,11 @@ struct Req {
   fdst_solve_info info{};
   std::string key;
   double bb = 0.0;
+  std::shared_future<fdst_ctx *> prep;   // handle being set up in the background
+  bool preparing = false;
+  fdst_status prep_status = FDST_OK;
+  double prev_true = -1.0;   // true residual at the previous check of a stopped recurrence
+  int restarts = 0;
 };
 
 std::string problem_key(const fdst_desc &d, const std::vector<double> *knots) {
@@ -95,6 +103,8 @@ struct fdst_server_ctx {
   int *dev_counter = nullptr;
   int64_t created = 0, reused = 0, finished = 0, evicted = 0;
   int max_active_seen = 0;
+  int device = 0, preparing = 0;
+  static constexpr int kMaxPrepare = 8;   // handles set up concurrently on host threads
 };
 
 namespace {
@@ -139,6 +149,7 @@ fdst_status fdst_server_create(const fdst_server_opts *o, fdst_server *out) {
   }
   fdst_server s = new fdst_server_ctx();
   s->o = *o;
+  cudaGetDevice(&s->device);
   if (s->o.hbm_budget_bytes <= 0) {
     size_t fr = 0, tot = 0;
     cudaMemGetInfo(&fr, &tot);
@@ -156,6 +167,12 @@ fdst_status fdst_server_create(const fdst_server_opts *o, fdst_server *out) {
 
 fdst_status fdst_server_destroy(fdst_server s) {
   if (!s) return FDST_OK;
+  for (auto &kv : s->reqs)
+    if (kv.second.preparing) {
+      fdst_ctx *h = kv.second.prep.get();
+      if (h) fdst_destroy(h);
+      kv.second.preparing = false;
+    }
   if (s->batch) fdst_batch_destroy(s->batch);
   for (auto &kv : s->reqs)
     if (kv.second.h) fdst_destroy(kv.second.h);
@@ -224,15 +241,27 @@ fdst_status fdst_server_step(fdst_server s, double now, int *n_active, int *n_qu
         const size_t i = stopped[k];
         Req &r = s->reqs[s->active[i]];
         const double tr = r.bb > 0 ? std::sqrt(rr[k] / r.bb) : std::sqrt(rr[k]);
-        if (S[i].status == 0 && S[i].stop && S[i].gamma > 0.0 && tr > s->o.tol && S[i].iters < s->o.maxit) {
-          S[i].tau = 0.5 * S[i].tau * s->o.tol / tr;
-          S[i].stop = 0;
+        const int a = resume_action(S[i], tr, r.prev_true, r.restarts, s->o.tol, s->o.maxit);
+        if (a != kKeepStopped) r.prev_true = tr;
+        std::vector<MinresState> one{S[i]};
+        bool cont = false;
+        if (a == kResume) {
+          one[0].tau = 0.5 * one[0].tau * s->o.tol / tr;
+          one[0].stop = 0;
           const int zero = 0;
-          CK(cudaMemcpyAsync(r.h->state, &S[i], sizeof(MinresState), cudaMemcpyHostToDevice, st));
+          CK(cudaMemcpyAsync(r.h->state, one.data(), sizeof(MinresState), cudaMemcpyHostToDevice, st));
           CK(cudaMemcpyAsync(r.h->done, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
           CK(cudaStreamSynchronize(st));
-        } else {
-          TRY(finish(s, r, S[i], tr, now));
+          cont = true;
+        } else if (a == kRestart) {
+          ++r.restarts;
+          TRY(minres_restart(r.h, r.h->hb, r.h->hx, 1, {0}, {tr}, s->o.tol, one, st));
+          cont = !one[0].stop && one[0].status == 0;
+        } else if (a == kStagnated) {
+          one[0].status = FDST_STAGNATION;
+        }
+        if (!cont) {
+          TRY(finish(s, r, one[0], tr, now));
           gone[i] = true;
         }
       }
@@ -242,9 +271,59 @@ fdst_status fdst_server_step(fdst_server s, double now, int *n_active, int *n_qu
       s->active.swap(keep);
     }
   }
-  // ---- (2) admission by slot limit and HBM budget
-  while (!s->queue.empty() && (int)s->active.size() < s->o.max_active) {
-    Req &r = s->reqs[s->queue.front()];
+  // ---- (2a) set up handles for queued requests in the background (host threads)
+  for (int64_t id : s->queue) {
+    if (s->preparing >= fdst_server_ctx::kMaxPrepare) break;
+    Req &r = s->reqs[id];
+    if (r.preparing || r.h) continue;
+    bool cached = false;
+    for (auto &e : s->idle)
+      if (e.first == r.key) { cached = true; break; }
+    if (cached) continue;
+    const int64_t ndof = problem_size(r.desc, r.knots);
+    const double bpd = s->bytes_per_dof[r.desc.dim] > 0 ? s->bytes_per_dof[r.desc.dim] : 600.0;
+    const int64_t est = (int64_t)(bpd * ndof);
+    while (s->bytes_held + est > s->o.hbm_budget_bytes && !s->idle.empty()) evict_one(s);
+    if (s->bytes_held + est > s->o.hbm_budget_bytes && !(s->active.empty() && s->preparing == 0)) break;
+    s->bytes_held += est;   // reserved until the handle reports its real size
+    fdst_desc d = r.desc;
+    Req *rp = &r;
+    const int dev = s->device;
+    r.prep = std::async(std::launch::async, [d, rp, dev]() -> fdst_ctx * {
+               cudaSetDevice(dev);
+               fdst_desc dd = d;
+               for (int e = 0; e < dd.dim; ++e) {
+                 dd.h_knots[e] = rp->knots[e].data();
+                 dd.nknots[e] = (int)rp->knots[e].size();
+               }
+               fdst_ctx *h = nullptr;
+               rp->prep_status = fdst_setup(&dd, &h);
+               if (h && !h->hb) {
+                 if (dalloc(h, &h->hb, (size_t)h->n_total) != FDST_OK ||
+                     dalloc(h, &h->hx, (size_t)h->n_total) != FDST_OK) {
+                   fdst_destroy(h);
+                   rp->prep_status = FDST_OUT_OF_MEMORY;
+                   return nullptr;
+                 }
+               }
+               return h;
+             }).share();
+    r.preparing = true;
+    r.bb = (double)est;   // remembered reservation until admission
+    ++s->preparing;
+  }
+  // ---- (2b) admission in arrival order among the requests whose handle is ready
+  // (with nothing on the GPU, wait for the earliest handle being set up)
+  if (s->active.empty())
+    for (int64_t id : s->queue) {
+      Req &r = s->reqs[id];
+      if (r.preparing) {
+        r.prep.wait();
+        break;
+      }
+    }
+  for (auto qit = s->queue.begin(); qit != s->queue.end() && (int)s->active.size() < s->o.max_active;) {
+    Req &r = s->reqs[*qit];
     fdst_ctx *h = nullptr;
     for (auto it = s->idle.begin(); it != s->idle.end(); ++it)
       if (it->first == r.key) {
@@ -253,34 +332,25 @@ fdst_status fdst_server_step(fdst_server s, double now, int *n_active, int *n_qu
         ++s->reused;
         break;
       }
-    if (!h) {
-      const int64_t ndof = problem_size(r.desc, r.knots);
-      const double bpd = s->bytes_per_dof[r.desc.dim] > 0 ? s->bytes_per_dof[r.desc.dim] : 600.0;
-      const int64_t est = (int64_t)(bpd * ndof);
-      while (s->bytes_held + est > s->o.hbm_budget_bytes && !s->idle.empty()) evict_one(s);
-      if (s->bytes_held + est > s->o.hbm_budget_bytes && !s->active.empty()) break;   // wait for memory
-      fdst_desc d = r.desc;
-      for (int e = 0; e < d.dim; ++e) {
-        d.h_knots[e] = r.knots[e].data();
-        d.nknots[e] = (int)r.knots[e].size();
-      }
-      fdst_status cs = fdst_setup(&d, &h);
-      if (cs != FDST_OK) {
-        r.info.status = cs;
+    if (!h && r.preparing) {
+      if (r.prep.wait_for(std::chrono::seconds(0)) != std::future_status::ready) { ++qit; continue; }
+      h = r.prep.get();
+      r.preparing = false;
+      --s->preparing;
+      s->bytes_held -= (int64_t)r.bb;
+      if (!h) {
+        r.info.status = r.prep_status;
         r.state = 2;
         r.t_done = now;
         ++s->finished;
-        s->queue.pop_front();
+        qit = s->queue.erase(qit);
         continue;
-      }
-      if (!h->hb) {
-        TRY(dalloc(h, &h->hb, (size_t)h->n_total));
-        TRY(dalloc(h, &h->hx, (size_t)h->n_total));
       }
       s->bytes_held += h->device_bytes;
       s->bytes_per_dof[r.desc.dim] = (double)h->device_bytes / (double)h->n_total;
       ++s->created;
     }
+    if (!h) { ++qit; continue; }
     r.h = h;
     if ((int64_t)r.b.size() != h->n_total) {
       set_error("fdst_server_step: right-hand side length does not match the problem");
@@ -294,7 +364,7 @@ fdst_status fdst_server_step(fdst_server s, double now, int *n_active, int *n_qu
     r.t_admit = now;
     r.state = 1;
     s->active.push_back(r.id);
-    s->queue.pop_front();
+    qit = s->queue.erase(qit);
     s->dirty = true;
   }
   if ((int)s->active.size() > s->max_active_seen) s->max_active_seen = (int)s->active.size();

@@ -15,6 +15,11 @@ WORKLOADS = {
     # 3D mapped cube (sine bump map, variable viscosity), p=3, 32^3 elements, seeds 300..303
     "mapped_th_p3_32": dict(dim=3, disc="TH", p=3, n_el=(32, 32, 32), seeds=list(range(300, 304)),
                             geometry="sine_bump"),
+    # 64 independent unit-cube TH instances, p ~ U{2..6}, elements per direction ~ U{16..96}
+    # (instance draw seed 400, right-hand side seeds 401..464)
+    "batched_64": dict(kind="batched", count=64, seed=400, rhs_seed0=401),
+    # Poisson arrivals of mixed requests (see serving_requests)
+    "serving": dict(kind="serving", rates=[50, 200, 1000, 2000], per_rate=48, seed=500, mix_seed=550),
 }
 
 
@@ -58,4 +63,27 @@ def batched_instances(seed=400, count=64, p_range=(2, 6), nel_range=(16, 96)):
         p = int(rng.integers(p_range[0], p_range[1] + 1))
         n_el = tuple(int(v) for v in rng.integers(nel_range[0], nel_range[1] + 1, size=3))
         out.append(dict(dim=3, disc="TH", p=p, n_el=n_el))
+    return out
+
+
+def serving_requests(rate_index, rate, count, seed=500, mix_seed=550, nel3=(16, 48)):
+    """Poisson arrival times (rate per second, stream seeded seed + rate_index) and a
+    50/50 mix of 3D Taylor-Hood instances (p ~ U{2..6}, elements per direction ~
+    U{nel3}) and 2D instances (Taylor-Hood or Raviart-Thomas with equal odds,
+    p ~ U{2..8}, elements per direction ~ U{32..256}); instance draws from the
+    stream seeded mix_seed + rate_index."""
+    rng_t = np.random.default_rng(seed + rate_index)
+    t = np.cumsum(rng_t.exponential(1.0 / rate, size=count))
+    rng = np.random.default_rng(mix_seed + rate_index)
+    out = []
+    for k in range(count):
+        if rng.random() < 0.5:
+            p = int(rng.integers(2, 7))
+            n_el = tuple(int(v) for v in rng.integers(nel3[0], nel3[1] + 1, size=3))
+            out.append(dict(t=float(t[k]), dim=3, disc="TH", p=p, n_el=n_el, seed=int(rng.integers(1 << 30))))
+        else:
+            p = int(rng.integers(2, 9))
+            n_el = tuple(int(v) for v in rng.integers(32, 257, size=2))
+            disc = "TH" if rng.random() < 0.5 else "RT"
+            out.append(dict(t=float(t[k]), dim=2, disc=disc, p=p, n_el=n_el, seed=int(rng.integers(1 << 30))))
     return out

@@ -25,6 +25,7 @@ CASES = [
     problem_spec(3, 2, 9),             # 3D, rows span several tiles with a ragged tail
     problem_spec(2, 2, 6, "RT"),       # 2D Raviart-Thomas with Nitsche terms
     problem_spec(2, 4, (4, 7), "RT"),
+    problem_spec(2, 3, (26, 5)),       # n_v = 53 > 48: Householder + implicit-QL eigensolver path
 ]
 
 
