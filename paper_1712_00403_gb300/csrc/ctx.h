@@ -76,6 +76,8 @@ struct fdst_ctx {
   float *work_f[2] = {nullptr, nullptr};
   std::vector<int64_t> f_off;   // per-chain offset in the padded FP32 workspace
   int64_t f_total = 0;          // padded FP32 workspace per right-hand side
+  uint8_t *tmaps = nullptr;     // TMA descriptors (128 B each), chain-major, tmap_steps per chain
+  int tmap_steps = 0;
   // matvec
   std::vector<fdst::BandDev> bands;
   std::vector<fdst::PlanOp> plan;

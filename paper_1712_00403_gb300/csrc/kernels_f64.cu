@@ -204,45 +204,101 @@ __device__ __forceinline__ float2 df_norm(float sh, float sl) {
   return make_float2(h, sl - (h - sh));
 }
 
+// Each thread computes T outputs that share one band row i (so one V row and
+// one lo[i]): for mode 0 (contracted index fastest) T consecutive lines with
+// lanes over consecutive rows i; for modes 1 and 2 T entries of the flattened
+// (outer, fastest) index strided by the warp width, lanes over consecutive
+// entries (coalesced X and Y). Work items run row-fastest so that warps in
+// flight share their X windows in L1/L2.
+template <int T>
 __global__ void __launch_bounds__(512) k_band_df(BandGroupDF g, int nrhs, const int *done) {
   const int rhs = blockIdx.y;
   if (done && done[rhs]) return;
   const BandOpDF &op = g.table ? g.table[blockIdx.z] : g.op[blockIdx.z];
   if (op.done_flag && *op.done_flag) return;
-  const int mode = op.mode;
-  const unsigned od0 = mode == 0 ? op.rows : op.d0, od1 = mode == 1 ? op.rows : op.d1,
-                 od2 = mode == 2 ? op.rows : op.d2;
-  const int64_t total = (int64_t)od0 * od1 * od2;
-  const int64_t stride_in = mode == 0 ? 1 : (mode == 1 ? (int64_t)op.d0 : (int64_t)op.d0 * op.d1);
   const float2 *X = op.X + rhs * op.x_rhs_stride;
   float2 *Y = op.Y + rhs * op.y_rhs_stride;
-  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total; o += (int64_t)gridDim.x * blockDim.x) {
-    const unsigned ou = (unsigned)o;            // a block has fewer than 2^32 entries
-    const unsigned t = ou / od0;
-    const int o0 = (int)(ou - t * od0);
-    const unsigned o2u = t / od1;
-    const int o1 = (int)(t - o2u * od1), o2 = (int)o2u;
-    const int i = mode == 0 ? o0 : (mode == 1 ? o1 : o2);
-    int64_t base;
-    if (mode == 0) base = ((int64_t)o2 * op.d1 + o1) * op.d0;
-    else if (mode == 1) base = (int64_t)o2 * op.d1 * op.d0 + o0;
-    else base = (int64_t)o1 * op.d0 + o0;
-    const float2 *v = op.vals + (int64_t)i * op.w;
-    const int l = op.lo[i];
-    float sh = 0.0f, sl = 0.0f;
-    for (int j = 0; j < op.w; ++j) df_fma_acc(v[j], X[base + (int64_t)(l + j) * stride_in], sh, sl);
-    float2 acc = df_norm(sh, sl);
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int rows = op.rows, w = op.w;
+  const float2 coef = op.coef;
+  auto finish = [&](float sh, float sl, float2 *dst) {
+    const float2 acc = df_norm(sh, sl);
     float rh = 0.0f, rl = 0.0f;
-    df_fma_acc(op.coef, acc, rh, rl);
+    df_fma_acc(coef, acc, rh, rl);
     if (op.accumulate) {
-      const float2 yo = Y[o];
+      const float2 yo = *dst;
       const float t2 = rh + yo.x;
       const float z2 = t2 - rh;
       const float err = (rh - (t2 - z2)) + (yo.x - z2);
       rl = rl + (err + yo.y);
       rh = t2;
     }
-    Y[o] = df_norm(rh, rl);
+    *dst = df_norm(rh, rl);
+  };
+  if (op.mode == 0) {
+    const int64_t d0 = op.d0;
+    const int64_t lines = (int64_t)op.d1 * op.d2;
+    const int64_t ib = (rows + 31) >> 5, lb = (lines + T - 1) / T;
+    for (int64_t u = warp0; u < ib * lb; u += nwarps) {
+      const int i = (int)(u % ib) * 32 + lane;
+      const int64_t L0 = (u / ib) * T;
+      if (i >= rows) continue;
+      const float2 *xp = X + L0 * d0 + op.lo[i];
+      const float2 *vp = op.vals + (int64_t)i * w;
+      int nt = (int)(lines - L0);
+      nt = nt < T ? nt : T;
+      float sh[T], sl[T];
+#pragma unroll
+      for (int t = 0; t < T; ++t) sh[t] = sl[t] = 0.0f;
+      for (int j = 0; j < w; ++j) {
+        const float2 v = vp[j];
+#pragma unroll
+        for (int t = 0; t < T; ++t)
+          if (t < nt) df_fma_acc(v, xp[t * d0 + j], sh[t], sl[t]);
+      }
+#pragma unroll
+      for (int t = 0; t < T; ++t)
+        if (t < nt) finish(sh[t], sl[t], Y + (L0 + t) * rows + i);
+    }
+  } else {
+    // Y[(o * rows + i) * P + p], X[(o * din + l) * P + p], m = o * P + p over outer * P entries
+    // (one operand of one right-hand side holds fewer than 2^32 entries: 32-bit offsets)
+    const unsigned P = op.mode == 1 ? (unsigned)op.d0 : (unsigned)op.d0 * op.d1;
+    const unsigned outer = op.mode == 1 ? op.d2 : 1, din = op.mode == 1 ? op.d1 : op.d2;
+    const unsigned M = outer * P;
+    const int64_t mb = ((int64_t)M + 32 * T - 1) / (32 * T);
+    for (int64_t u = warp0; u < mb * rows; u += nwarps) {
+      const int i = (int)(u % rows);
+      const unsigned m0 = (unsigned)(u / rows) * (32 * T) + lane;
+      const unsigned l = op.lo[i];
+      unsigned xo[T], yo[T];
+      bool ok[T];
+#pragma unroll
+      for (int t = 0; t < T; ++t) {
+        const unsigned m = m0 + 32 * t;
+        ok[t] = m < M;
+        const unsigned o = ok[t] ? m / P : 0, p = ok[t] ? m - o * P : 0;
+        xo[t] = (o * din + l) * P + p;
+        yo[t] = (o * rows + i) * P + p;
+      }
+      const float2 *vp = op.vals + (int64_t)i * w;
+      float sh[T], sl[T];
+#pragma unroll
+      for (int t = 0; t < T; ++t) sh[t] = sl[t] = 0.0f;
+      for (int j = 0; j < w; ++j) {
+        const float2 v = vp[j];
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+          if (ok[t]) df_fma_acc(v, X[xo[t]], sh[t], sl[t]);
+          xo[t] += P;
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < T; ++t)
+        if (ok[t]) finish(sh[t], sl[t], Y + yo[t]);
+    }
   }
 }
 
@@ -254,13 +310,14 @@ void launch_band_df(const BandGroupDF &g, int nrhs, const int *done, cudaStream_
       int64_t t = (int64_t)(o.mode == 0 ? o.rows : o.d0) * (o.mode == 1 ? o.rows : o.d1) * (o.mode == 2 ? o.rows : o.d2);
       maxt = t > maxt ? t : maxt;
     }
+  constexpr int T = 4;
   const int thr = g.threads > 0 ? g.threads : 256;
-  int64_t blocks = (maxt + thr - 1) / thr;
-  if (blocks > 4096) blocks = 4096;
+  int64_t blocks = (maxt / T + thr - 1) / thr;
+  if (blocks > 152 * 16) blocks = 152 * 16;
   if (blocks < 1) blocks = 1;
   dim3 grid((unsigned)blocks, nrhs, g.nop);
   count_launch(1);
-  k_band_df<<<grid, thr, 0, s>>>(g, nrhs, done);
+  k_band_df<T><<<grid, thr, 0, s>>>(g, nrhs, done);
 }
 
 __global__ void k_split_df(const double *x, float2 *y, int64_t n, int64_t stride, const int *done) {

@@ -8,16 +8,19 @@
 // split into TF32 pairs x = x_hi + x_lo and the three leading products
 // A_hi B_hi + A_hi B_lo + A_lo B_hi accumulate in FP32 in tensor memory.
 //
-// Persistent, warp-specialized kernel (one CTA per SM, 17 warps). A tile is
+// Persistent, warp-specialized kernel (one CTA per SM, 18 warps). A tile is
 // 128 rows x NT columns (NT <= 256, a multiple of 16); K runs in stages of 32
 // through a ring of 2-4 shared-memory stages:
-//   * warps 0-7 (producers) read A with 16-byte loads two stages ahead
-//     (register double buffer; FP32 intermediates have rows padded to a
-//     multiple of 4), split to TF32 hi/lo and store the K-major SWIZZLE_32B
-//     image with 16-byte shared stores; producer thread 0 also brings the
-//     stage's B image
-//     (pre-split and pre-swizzled on the host) with one bulk async copy
-//     (cp.async.bulk, mbarrier transaction count);
+//   * warp 17 (lane 0) issues, per stage, one TMA tensor load per 32-row
+//     group of A (box 32 FP32 columns x 32 rows, SWIZZLE_128B K-major,
+//     straight into the operand image's hi half; rows and columns past the
+//     tensor read as zero) and one bulk async copy of the stage's B image
+//     (pre-split and pre-swizzled on the host, SWIZZLE_32B K-major), all on
+//     one mbarrier transaction count, as soon as the MMA has released the
+//     slot;
+//   * warps 0-7 split the landed FP32 tile in place into TF32 hi (kept where
+//     it landed) and lo (written to the lo half at the same offsets) with
+//     conflict-free 16-byte shared-memory accesses;
 //   * warp 16 allocates tensor memory and its lane 0 issues tcgen05.mma
 //     (kind::tf32, M=128, N=NT, K=8), releasing each stage with
 //     tcgen05.commit; accumulators are double-buffered in tensor memory;
@@ -27,16 +30,20 @@
 //     run, apply the fused
 //     Algorithm 1 step 3 divide (lam_row[r] + lam_col[n]) and the optional
 //     D^{-1/2} scaling, and write the transposed FP32 (or final FP64) tensor.
+// The first contraction of a chain reads FP64: a grouped elementwise kernel
+// converts it (times the optional D^{-1/2} scaling) to the FP32 layout first.
 // Every mbarrier wait is bounded (about 2 s of %globaltimer) and also gives
 // up when another role has aborted; on expiry the kernel raises a device
-// error flag, waits (bounded) for its own in-flight work, frees its tensor
-// memory and returns.
+// error flag, waits (bounded) for its own in-flight copies and MMAs, frees
+// its tensor memory and returns.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
 
 #include <cstdint>
 #include <cstring>
+#include <string>
 #include <vector>
 
 #include "internal.h"
@@ -48,11 +55,13 @@ namespace fdst {
 namespace {
 constexpr int kM = 128;          // tile rows = TMEM lanes
 constexpr int kKC = 32;          // K per pipeline stage (4 MMA k-steps of 8)
-constexpr int kProducers = 256;  // warps 0-7
+constexpr int kConv = 256;       // warps 0-7: TF32 split of the landed A tile
 constexpr int kEpiWarp0 = 8;     // warps 8-15 (two per TMEM lane quarter)
 constexpr int kMmaWarp = 16;
-constexpr int kThreads = 544;
-constexpr int kQuads = kM * kKC / 4 / kProducers;  // 4-element quads per producer thread per stage
+constexpr int kTmaWarp = 17;
+constexpr int kThreads = 576;
+constexpr int kAHalfBytes = kM * kKC * 4;   // 128 rows x 32 FP32 (hi or lo half of a stage's A)
+constexpr int kGroupBytes = 32 * kKC * 4;    // one 32-row group: 4 atoms of 8 rows x 128 B
 constexpr int kNTMax = 256;
 constexpr int kAStageBytes = 2 * 4 * kM * 32;   // hi/lo x 4 k-steps x 128 rows x 32 B
 constexpr int kSmemBudget = 227 * 1024;
@@ -160,6 +169,16 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
                : "memory");
 }
 
+// TMA tensor load of one box (coordinates innermost first) into shared memory,
+// completing as transaction bytes on the mbarrier.
+__device__ __forceinline__ void tma_load_4d(void *dst, const void *tmap, int x, int y, int z, int w, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(smem_u32(dst)),
+      "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
+      : "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -229,6 +248,20 @@ __device__ __forceinline__ uint64_t sdesc_sw32(const void *p) {
   return d;
 }
 
+// Shared-memory matrix descriptor: K-major, SWIZZLE_128B (8-row atoms of
+// 128 B, 1024 B between atoms along M), descriptor version 1. The k-steps of
+// a 32-wide stage start 32 B apart inside the atom; the hardware applies the
+// swizzle to the address bits, so the start address alone selects one.
+__device__ __forceinline__ uint64_t sdesc_sw128(const void *p) {
+  const uint64_t addr = smem_u32(p);
+  uint64_t d = (addr >> 4) & 0x3FFFull;
+  d |= (uint64_t)1 << 16;                 // leading byte offset (unused for swizzled K-major): 16 B
+  d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                 // version
+  d |= (uint64_t)2 << 61;                 // SWIZZLE_128B
+  return d;
+}
+
 // Instruction descriptor: D f32, A/B tf32, K-major both, N = nt, M = 128.
 __device__ __forceinline__ uint32_t idesc_tf32(int nt) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(nt >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
@@ -236,8 +269,12 @@ __device__ __forceinline__ uint32_t idesc_tf32(int nt) {
 
 // ------------------------------------------------------------------ kernel
 
+// A tile is 4 row groups of 32 rows; group g of a problem is the 32-row block
+// vb = g % nvb of row run u = g / nvb (rows r = u * out_nv + v, v in
+// [32 vb, 32 vb + 32) and < out_nv), so that each TMEM lane quarter stores
+// 128-byte aligned lines (output rows are padded to a multiple of 32).
 struct TileInfo {
-  int prob, rhs, row0, n0, NT, nstages, kp;
+  int prob, rhs, g0, G, nvb, n0, NT, nstages, kp;
   bool valid;
 };
 
@@ -253,9 +290,11 @@ __device__ __forceinline__ TileInfo decode_tile(const TcGroup &g, int T, int nrt
   t.rhs = z / g.nprob;
   const TcProb &P = prob_of(g, t.prob);
   const int npad = (P.N + 15) & ~15;
-  t.row0 = rt * kM;
+  t.nvb = (P.out_nv + 31) >> 5;
+  t.G = (P.R / P.out_nv) * t.nvb;
+  t.g0 = rt * 4;
   t.n0 = nt * kNTMax;
-  t.valid = t.row0 < P.R && t.n0 < npad && !(done && done[t.rhs]) && !(P.done_flag && *P.done_flag);
+  t.valid = t.g0 < t.G && t.n0 < npad && !(done && done[t.rhs]) && !(P.done_flag && *P.done_flag);
   t.NT = npad - t.n0 < kNTMax ? npad - t.n0 : kNTMax;
   t.kp = (P.K + 7) & ~7;
   t.nstages = (t.kp + kKC - 1) / kKC;
@@ -283,14 +322,15 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + nstage_ring * stage_bytes);
-  uint64_t *full = bars, *empty = bars + 4, *tfull = bars + 8, *tempty = bars + 10;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 12);
-  volatile int *abort = reinterpret_cast<volatile int *>(bars + 13);
+  uint64_t *landed = bars, *split = bars + 4, *empty = bars + 8, *tfull = bars + 12, *tempty = bars + 14;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 16);
+  volatile int *abort = reinterpret_cast<volatile int *>(bars + 17);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
     for (int i = 0; i < nstage_ring; ++i) {
-      mbar_init(&full[i], kProducers + 1);
+      mbar_init(&landed[i], 1);
+      mbar_init(&split[i], kConv / 32);
       mbar_init(&empty[i], 1);
     }
     for (int i = 0; i < 2; ++i) {
@@ -306,121 +346,71 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  if (warp < kEpiWarp0) {
-    // ------------------------------------------------------------ producers
-    const int ptid = tid;
-    // quad it of this thread: rows 4g..4g+3 of a warp, lane -> (row rq, 16-byte chunk cc, k-step j);
-    // a quarter-warp stores 8 distinct 16-byte slots (conflict-free)
-    int q_rr[kQuads], q_kk[kQuads];
-    uint32_t q_off[kQuads];
-#pragma unroll
-    for (int it = 0; it < kQuads; ++it) {
-      const int qd = ptid + kProducers * it;
-      const int gq = qd >> 5, l = qd & 31;
-      const int rq = l & 3, cc = (l >> 2) & 1, j = l >> 3;
-      q_rr[it] = gq * 4 + rq;
-      q_kk[it] = j * 8 + cc * 4;
-      q_off[it] = j * (kM * 32) + q_rr[it] * 32 + ((cc ^ ((q_rr[it] >> 2) & 1)) * 16);
-    }
-    auto load = [&](const Cursor &c, float4 (&reg)[kQuads]) {
-      const TcProb &P = prob_of(g, c.t.prob);
-      const int k0 = c.s * kKC;
-      if (P.A32) {
-        const float *A32 = P.A32 + (int64_t)c.t.rhs * P.a_rhs_stride;
-#pragma unroll
-        for (int it = 0; it < kQuads; ++it) {
-          const int r = c.t.row0 + q_rr[it], k = k0 + q_kk[it];
-          float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (r < P.R && k < P.K) {
-            a = *reinterpret_cast<const float4 *>(A32 + (int64_t)r * P.lda + k);
-            if (k + 1 >= P.K) a.y = 0.f;
-            if (k + 2 >= P.K) a.z = 0.f;
-            if (k + 3 >= P.K) a.w = 0.f;
+  if (warp == kTmaWarp) {
+    // ------------------------------------------------------------ TMA issuer (one thread)
+    if (lane == 0) {
+      int q = 0;
+      int last_par[4] = {-1, -1, -1, -1};
+      bool ok = true;
+      for (int T = next_tile(g, -1, total, nrt, ntn, done); ok && T < total;
+           T = next_tile(g, T, total, nrt, ntn, done)) {
+        const TileInfo t = decode_tile(g, T, nrt, ntn, done);
+        const TcProb &P = prob_of(g, t.prob);
+        const size_t btile = 2 * (size_t)kNTMax * t.kp * (size_t)(t.n0 / kNTMax);
+        for (int s = 0; s < t.nstages; ++s, ++q) {
+          const int slot = q % nstage_ring, u = q / nstage_ring;
+          if (u > 0 && !mbar_wait(&empty[slot], (u - 1) & 1, abort)) { ok = false; break; }
+          uint8_t *sA = smem + slot * stage_bytes;
+          uint8_t *sB = sA + kAStageBytes;
+          const int k0 = s * kKC;
+          const int ks = (t.kp - k0) / 8 < 4 ? (t.kp - k0) / 8 : 4;
+          const uint32_t bbytes = 2u * ks * t.NT * 32u;
+          const int ng = t.G - t.g0 < 4 ? t.G - t.g0 : 4;
+          mbar_expect_tx(&landed[slot], ng * kGroupBytes + bbytes);
+          for (int q4 = 0; q4 < ng; ++q4) {
+            const int gg = t.g0 + q4, u = gg / t.nvb, vb = gg - u * t.nvb;
+            tma_load_4d(sA + q4 * kGroupBytes, P.tmap, k0, 32 * vb, u, t.rhs, &landed[slot]);
           }
-          reg[it] = a;
-        }
-      } else {
-        const double *A64 = P.A64 + (int64_t)c.t.rhs * P.a_rhs_stride;
-#pragma unroll
-        for (int it = 0; it < kQuads; ++it) {
-          const int r = c.t.row0 + q_rr[it], k = k0 + q_kk[it];
-          float v[4] = {0.f, 0.f, 0.f, 0.f};
-          if (r < P.R) {
-            const int64_t base = (int64_t)r * P.lda + k;
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-              if (k + e < P.K) {
-                double x = A64[base + e];
-                if (P.scale_in) x *= P.scale_in[(int64_t)r * P.K + k + e];
-                v[e] = (float)x;
-              }
-          }
-          reg[it] = make_float4(v[0], v[1], v[2], v[3]);
+          bulk_g2s(sB, P.Bt + btile + 2 * (size_t)t.NT * k0, bbytes, &landed[slot]);
+          last_par[slot] = u & 1;
         }
       }
-    };
-    auto advance = [&](Cursor &c) -> bool {
-      if (++c.s < c.t.nstages) return true;
-      c.s = 0;
-      c.T = next_tile(g, c.T, total, nrt, ntn, done);
-      if (c.T >= total) return false;
-      c.t = decode_tile(g, c.T, nrt, ntn, done);
-      return true;
-    };
+      if (!ok) *abort = 1;
+      // every copy issued has landed before the CTA may exit (bounded, ignoring abort)
+      volatile int never = 0;
+      for (int i = 0; i < nstage_ring; ++i)
+        if (last_par[i] >= 0) mbar_wait(&landed[i], (uint32_t)last_par[i], &never);
+    }
+    __syncwarp();
+  } else if (warp < kEpiWarp0) {
+    // ------------------------------------------------------------ TF32 split of the landed tile
     int q = 0;
-    auto split_hi = [](float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); };
-    auto produce = [&](const Cursor &c, const float4 (&reg)[kQuads]) -> bool {
-      const int slot = q % nstage_ring, u = q / nstage_ring;
-      if (u > 0 && !mbar_wait(&empty[slot], (u - 1) & 1, abort)) return false;
-      uint8_t *sA = smem + slot * stage_bytes;
-      uint8_t *sB = sA + kAStageBytes;
-      if (ptid == 0) {
-        const int k0 = c.s * kKC;
-        const int ks = (c.t.kp - k0) / 8 < 4 ? (c.t.kp - k0) / 8 : 4;
-        const uint32_t bbytes = 2u * ks * c.t.NT * 32u;
-        const size_t btile = 2 * (size_t)kNTMax * c.t.kp * (size_t)(c.t.n0 / kNTMax);
-        mbar_expect_tx(&full[slot], bbytes);
-        bulk_g2s(sB, prob_of(g, c.t.prob).Bt + btile + 2 * (size_t)c.t.NT * k0, bbytes, &full[slot]);
+    bool ok = true;
+    for (int T = next_tile(g, -1, total, nrt, ntn, done); ok && T < total;
+         T = next_tile(g, T, total, nrt, ntn, done)) {
+      const TileInfo t = decode_tile(g, T, nrt, ntn, done);
+      for (int s = 0; s < t.nstages; ++s, ++q) {
+        const int slot = q % nstage_ring;
+        if (!mbar_wait(&landed[slot], (q / nstage_ring) & 1, abort)) { ok = false; break; }
+        uint8_t *sA = smem + slot * stage_bytes;
+        const int k0 = s * kKC;
+        const int ks = (t.kp - k0) / 8 < 4 ? (t.kp - k0) / 8 : 4;
+        for (int c = tid; c < kAHalfBytes / 16; c += kConv) {
+          float4 *ph = reinterpret_cast<float4 *>(sA + c * 16);
+          const float4 a = *ph;
+          float4 hi, lo;
+          hi.x = __uint_as_float(__float_as_uint(a.x) & 0xFFFFE000u);
+          hi.y = __uint_as_float(__float_as_uint(a.y) & 0xFFFFE000u);
+          hi.z = __uint_as_float(__float_as_uint(a.z) & 0xFFFFE000u);
+          hi.w = __uint_as_float(__float_as_uint(a.w) & 0xFFFFE000u);
+          lo = make_float4(a.x - hi.x, a.y - hi.y, a.z - hi.z, a.w - hi.w);
+          *ph = hi;
+          *reinterpret_cast<float4 *>(sA + kAHalfBytes + c * 16) = lo;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&split[slot]);
       }
-#pragma unroll
-      for (int it = 0; it < kQuads; ++it) {
-        const float4 a = reg[it];
-        const float4 hi = make_float4(split_hi(a.x), split_hi(a.y), split_hi(a.z), split_hi(a.w));
-        const float4 lo = make_float4(a.x - hi.x, a.y - hi.y, a.z - hi.z, a.w - hi.w);
-        *reinterpret_cast<float4 *>(sA + q_off[it]) = hi;
-        *reinterpret_cast<float4 *>(sA + 4 * kM * 32 + q_off[it]) = lo;
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_arrive(&full[slot]);
-      ++q;
-      return true;
-    };
-    float4 ra[kQuads], rb[kQuads];
-    Cursor c0;
-    c0.T = next_tile(g, -1, total, nrt, ntn, done);
-    c0.s = 0;
-    bool has0 = c0.T < total;
-    if (has0) {
-      c0.t = decode_tile(g, c0.T, nrt, ntn, done);
-      load(c0, ra);
-    }
-    Cursor c1 = c0;
-    bool has1 = has0 && advance(c1);
-    if (has1) load(c1, rb);
-    while (has0) {
-      if (!produce(c0, ra)) break;
-      Cursor c2 = c1;
-      bool has2 = has1 && advance(c2);
-      if (has2) load(c2, ra);
-      if (!has1) break;
-      if (!produce(c1, rb)) break;
-      Cursor c3 = c2;
-      bool has3 = has2 && advance(c3);
-      if (has3) load(c3, rb);
-      c0 = c2;
-      has0 = has2;
-      c1 = c3;
-      has1 = has3;
     }
   } else if (warp < kMmaWarp) {
     // ------------------------------------------------------------ epilogue
@@ -432,32 +422,48 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int acc = v & 1;
       if (!mbar_wait(&tfull[acc], (v >> 1) & 1, abort)) break;
       tc_fence_after();
-      const int r = t.row0 + quarter * 32 + lane;
-      const bool rok = r < P.R;
+      const int gq = t.g0 + quarter, uu = gq / t.nvb, vr = (gq - uu * t.nvb) * 32 + lane;
+      const bool rok = gq < t.G && vr < P.out_nv;
+      const int r = uu * P.out_nv + vr;
       const float lr = (P.lam_row && rok) ? P.lam_row[r] : 0.0f;
-      const float *lc = P.lam_col;
-      const int nu = P.R / P.out_nv, uu = r / P.out_nv, vv0 = r - uu * P.out_nv;
+      // every field the stores need, in registers (no reloads between stores)
+      const float *__restrict__ lc = P.lam_col;
+      const int nu = P.R / P.out_nv, Ncols = P.N;
+      const int64_t Rrows = P.R;
+      const double *__restrict__ so = P.scale_out;
       // output address of column n: base + n * cstride (row-major over (n, u), padded v)
       const int64_t cstride = (int64_t)nu * P.ldc;
-      const int64_t base = (int64_t)t.rhs * P.c_rhs_stride + (int64_t)uu * P.ldc + vv0;
+      const int64_t base = (int64_t)t.rhs * P.c_rhs_stride + (int64_t)uu * P.ldc + vr;
+      double *__restrict__ c64 = P.C64 ? P.C64 + base : nullptr;
+      float *__restrict__ c32 = P.C32 ? P.C32 + base : nullptr;
       const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * ntc);
       const int nchunks = t.NT / 16;
       auto store_chunk = [&](const uint32_t (&vals)[16], int c) {
         const int nb = t.n0 + 16 * c;
         if (!rok) return;
+        if (c64) {
 #pragma unroll
-        for (int qq = 0; qq < 16; ++qq) {
-          const int n = nb + qq;
-          if (n < P.N) {
-            float x = __uint_as_float(vals[qq]);
-            if (lc) x = x / (lr + lc[n]);
-            if (P.C64) {
+          for (int qq = 0; qq < 16; ++qq) {
+            const int n = nb + qq;
+            if (n < Ncols) {
+              float x = __uint_as_float(vals[qq]);
+              if (lc) x = x / (lr + lc[n]);
               double y = (double)x;
-              if (P.scale_out) y *= P.scale_out[(int64_t)n * P.R + r];
-              P.C64[base + n * cstride] = y;
-            } else {
-              P.C32[base + n * cstride] = x;
+              if (so) y *= so[(int64_t)n * Rrows + r];
+              c64[n * cstride] = y;
             }
+          }
+        } else if (lc) {
+#pragma unroll
+          for (int qq = 0; qq < 16; ++qq) {
+            const int n = nb + qq;
+            if (n < Ncols) c32[n * cstride] = __uint_as_float(vals[qq]) / (lr + lc[n]);
+          }
+        } else {
+#pragma unroll
+          for (int qq = 0; qq < 16; ++qq) {
+            const int n = nb + qq;
+            if (n < Ncols) c32[n * cstride] = __uint_as_float(vals[qq]);
           }
         }
       };
@@ -497,15 +503,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t idesc = idesc_tf32(t.NT);
         for (int s = 0; s < t.nstages; ++s) {
           const int slot = q % nstage_ring;
-          if (!mbar_wait(&full[slot], (q / nstage_ring) & 1, abort)) { ok = false; break; }
+          if (!mbar_wait(&split[slot], (q / nstage_ring) & 1, abort)) { ok = false; break; }
           tc_fence_after();
           uint8_t *sA = smem + slot * stage_bytes;
           uint8_t *sB = sA + kAStageBytes;
           const int k0 = s * kKC;
           const int ks = (t.kp - k0) / 8 < 4 ? (t.kp - k0) / 8 : 4;
           for (int j = 0; j < ks; ++j) {
-            const uint64_t ah = sdesc_sw32(sA + j * kM * 32);
-            const uint64_t al = sdesc_sw32(sA + 4 * kM * 32 + j * kM * 32);
+            const uint64_t ah = sdesc_sw128(sA + j * 32);
+            const uint64_t al = sdesc_sw128(sA + kAHalfBytes + j * 32);
             const uint64_t bh = sdesc_sw32(sB + (size_t)j * t.NT * 32);
             const uint64_t bl = sdesc_sw32(sB + (size_t)(ks + j) * t.NT * 32);
             mma_tf32(d, ah, bh, idesc, (s > 0 || j > 0) ? 1u : 0u);
@@ -542,7 +548,67 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// FP64 first-step input (times the optional scaling) to the FP32 layout the
+// TMA reads: A32[r*lda + k] = (float)(A64[r*K + k] * scale_in[r*K + k]).
+__global__ void k_tc_convert(TcGroup g, const int *done) {
+  const int rhs = blockIdx.y;
+  if (done && done[rhs]) return;
+  const TcProb &P = prob_of(g, blockIdx.z);
+  if (!P.A64 || (P.done_flag && *P.done_flag)) return;
+  const double *src = P.A64 + rhs * P.a64_rhs_stride;
+  float *dst = const_cast<float *>(P.A32) + rhs * P.a_rhs_stride;
+  const unsigned K = (unsigned)P.K, total = (unsigned)P.R * K;
+  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const unsigned r = e / K, k = e - r * K;
+    double v = src[e];
+    if (P.scale_in) v *= P.scale_in[e];
+    dst[(size_t)r * P.lda + k] = (float)v;
+  }
+}
+
+fdst_status tc_encode_map(void *map128, const float *A32, int K, int nv, int nu, int lda, int64_t rhs_stride, int nrhs) {
+  using Encode = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                              const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static Encode encode = nullptr;
+  static std::mutex m;
+  {
+    std::lock_guard<std::mutex> lock(m);
+    if (!encode) {
+      void *fn = nullptr;
+      cudaDriverEntryPointQueryResult q;
+      if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+              cudaSuccess ||
+          q != cudaDriverEntryPointSuccess || !fn) {
+        set_error("cuTensorMapEncodeTiled is not available from the driver");
+        return FDST_CUDA_ERROR;
+      }
+      encode = reinterpret_cast<Encode>(fn);
+    }
+  }
+  if ((reinterpret_cast<uintptr_t>(A32) & 15) || (lda & 3) || (rhs_stride & 3) || K < 1 || nv < 1 || nu < 1 ||
+      nrhs < 1) {
+    set_error("tensor map: FP32 operand must be 16-byte aligned with row and right-hand-side pitches of 4 floats");
+    return FDST_INVALID_ARGUMENT;
+  }
+  const cuuint64_t dims[4] = {(cuuint64_t)K, (cuuint64_t)nv, (cuuint64_t)nu, (cuuint64_t)nrhs};
+  const cuuint64_t strides[3] = {(cuuint64_t)lda * 4, (cuuint64_t)nv * lda * 4, (cuuint64_t)rhs_stride * 4};
+  const cuuint32_t box[4] = {32, 32, 1, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  const CUresult r = encode(reinterpret_cast<CUtensorMap *>(map128), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
+                            const_cast<float *>(A32), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (code " + std::to_string((int)r) + ")");
+    return FDST_CUDA_ERROR;
+  }
+  return FDST_OK;
+}
+
 static int *g_err_flag = nullptr;
+
+int tc_padded_rows(int R, int out_nv) { return (R / out_nv) * ((out_nv + 31) & ~31); }
 
 static void tc_dims(const TcGroup &g, int &maxR, int &maxN) {
   maxR = g.maxR;
@@ -550,7 +616,8 @@ static void tc_dims(const TcGroup &g, int &maxR, int &maxN) {
   if (!g.table)
     for (int i = 0; i < g.nprob; ++i) {
       if (g.p[i].N > maxN) maxN = g.p[i].N;
-      if (g.p[i].R > maxR) maxR = g.p[i].R;
+      const int rp = tc_padded_rows(g.p[i].R, g.p[i].out_nv);
+      if (rp > maxR) maxR = rp;
     }
 }
 
@@ -600,6 +667,13 @@ fdst_status launch_gemm_tc(const TcGroup &g, int nrhs, const int *done, cudaStre
       return FDST_CUDA_ERROR;
     }
     configured = smem;
+  }
+  if (g.convert) {
+    long long blocks = ((long long)maxR * 64 + 255) / 256;
+    if (blocks > 1024) blocks = 1024;
+    if (blocks < 1) blocks = 1;
+    count_launch(1);
+    k_tc_convert<<<dim3((unsigned)blocks, nrhs, g.nprob), 256, 0, s>>>(g, done);
   }
   const int nrt = (maxR + kM - 1) / kM;
   const long long total = (long long)nrt * ntn * g.nprob * nrhs;

@@ -30,17 +30,17 @@ def _solve(fd, mv, prec=None):
 def test_restart_reaches_tolerance_alone():
     import paper_1712_00403_gb300 as fd
     P64, b, x64, i64 = _solve(fd, fd.MV_F64)
-    P64.close()
     for prec in (fd.FD_F64, fd.FD_TF32X3):
         P, b, x, info = _solve(fd, fd.MV_DF64, prec)
         assert info["status"] == "OK" and info["true_rel_res"] <= 1e-8
         assert info["iterations"] <= i64["iterations"] + 10
-        # independent FP64 residual of the returned iterate
+        # FP64 residual of the returned iterate through the FP64-matvec handle
         y = torch.empty_like(b)
-        P.matvec(x, y)
+        P64.matvec(x, y)
         assert float(torch.linalg.norm(b - y) / torch.linalg.norm(b)) <= 1e-8 * 1.01
         assert rel(x.cpu().numpy(), x64.cpu().numpy()) <= 1e-5
         P.close()
+    P64.close()
 
 
 def test_restart_in_batch_and_server():
