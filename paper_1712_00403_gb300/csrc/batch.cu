@@ -410,17 +410,21 @@ static fdst_status build_batch(fdst_batch b) {
         const FdChain &c = h->chains[ci];
         if (j >= c.nsteps) continue;
         const bool first = j == 0, last = j == c.nsteps - 1;
-        S.maxR = std::max(S.maxR, b->tc ? tc_padded_rows(c.R[j], last ? c.R[j] : c.K[j + 1]) : c.R[j]);
+        const TcLayout L = tc_layout(c.R[j], c.K[j], c.K[(j + 1) % c.nsteps], last);
+        S.maxR = std::max(S.maxR, c.R[j]);
         S.maxN = std::max(S.maxN, c.N[j]);
         if (b->tc) {
           TcProb P;
           if (first) { P.A64 = h->v + c.off; P.a64_rhs_stride = h->n_total; }
           P.A32 = h->work_f[(j + 1) % 2] + h->f_off[ci];
           P.a_rhs_stride = h->f_total;
-          P.lda = tc_ld(c.K[j]);
+          P.lda = L.lda;
           P.tmap = h->tmaps + 128 * (ci * h->tmap_steps + j);
-          if (last) { P.C64 = h->z_new + c.off; P.out_nv = P.ldc = c.R[j]; }
-          else { P.C32 = h->work_f[j % 2] + h->f_off[ci]; P.out_nv = c.K[j + 1]; P.ldc = tc_ld(c.K[j + 1]); }
+          P.out_nv = c.K[(j + 1) % c.nsteps];
+          P.ldv = L.ldv;
+          P.c_cs = L.c_cs;
+          if (last) P.C64 = h->z_new + c.off;
+          else P.C32 = h->work_f[j % 2] + h->f_off[ci];
           P.Bt = c.Bt[j];
           P.R = c.R[j]; P.K = c.K[j]; P.N = c.N[j];
           if (j == c.div_step) { P.lam_row = c.lam_row_f; P.lam_col = c.lam_col_f; }

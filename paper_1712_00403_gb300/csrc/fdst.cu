@@ -427,16 +427,15 @@ static fdst_status tc_prepare(fdst_ctx *h) {
       c.Bt[j] = d;
       cache[c.B[j]] = d;
     }
-  // padded FP32 operands: step j reads R[j] rows of K[j] values padded to a
-  // multiple of 32 floats (128-byte aligned rows: TMA pitch and aligned
-  // epilogue stores); step 0's operand is the FP32 image of the FP64 input,
-  // later ones the previous step's output
+  // padded FP32 operands (TcLayout): step j reads R[j] rows at pitch lda (K[j]
+  // rounded up to 8: 32-byte TMA pitch); step 0's operand is the FP32 image
+  // of the FP64 input, later ones the previous step's output
   h->f_off.clear();
   h->f_total = 0;
   int maxsteps = 0;
   for (auto &c : h->chains) {
     int64_t fsize = 0;
-    for (int j = 0; j < c.nsteps; ++j) fsize = std::max(fsize, (int64_t)c.R[j] * tc_ld(c.K[j]));
+    for (int j = 0; j < c.nsteps; ++j) fsize = std::max(fsize, (int64_t)c.R[j] * tc_round(c.K[j], 8));
     h->f_off.push_back(h->f_total);
     h->f_total += (fsize + 63) & ~(int64_t)63;
     maxsteps = std::max(maxsteps, c.nsteps);
@@ -444,18 +443,14 @@ static fdst_status tc_prepare(fdst_ctx *h) {
   const size_t nv = (size_t)h->f_total * h->max_rhs;
   TRY(dalloc(h, &h->work_f[0], nv));
   TRY(dalloc(h, &h->work_f[1], nv));
-  // one TMA descriptor per (chain, step): step j reads work_f[(j + 1) % 2]; its
-  // rows r = u * out_nv + v run over v fastest (out_nv = next contracted size,
-  // or R for the last step)
+  // one TMA descriptor per (chain, step): step j reads work_f[(j + 1) % 2]
   h->tmap_steps = maxsteps;
   std::vector<uint8_t> maps((size_t)128 * h->chains.size() * maxsteps, 0);
   for (size_t ci = 0; ci < h->chains.size(); ++ci) {
     const FdChain &c = h->chains[ci];
-    for (int j = 0; j < c.nsteps; ++j) {
-      const int nvv = j == c.nsteps - 1 ? c.R[j] : c.K[j + 1];
+    for (int j = 0; j < c.nsteps; ++j)
       TRY(tc_encode_map(maps.data() + 128 * (ci * maxsteps + j), h->work_f[(j + 1) % 2] + h->f_off[ci], c.K[j],
-                        nvv, c.R[j] / nvv, tc_ld(c.K[j]), h->f_total, h->max_rhs));
-    }
+                        c.R[j], tc_round(c.K[j], 8), h->f_total, h->max_rhs));
   }
   TRY(upload(h, &h->tmaps, maps));
   return FDST_OK;
@@ -480,19 +475,20 @@ fdst_status run_apply(fdst_ctx *h, const double *r, double *s, int nrhs, const i
           P.a64_rhs_stride = h->n_total;
           g.convert = 1;
         }
+        const TcLayout L = tc_layout(c.R[j], c.K[j], c.K[(j + 1) % c.nsteps], last);
         P.A32 = h->work_f[(j + 1) % 2] + h->f_off[ci];
         P.a_rhs_stride = h->f_total;
-        P.lda = tc_ld(c.K[j]);
+        P.lda = L.lda;
         P.tmap = h->tmaps + 128 * (ci * h->tmap_steps + j);
+        P.out_nv = c.K[(j + 1) % c.nsteps];
+        P.ldv = L.ldv;
+        P.c_cs = L.c_cs;
         if (last) {
           P.C64 = s + c.off;
           P.c_rhs_stride = h->n_total;
-          P.out_nv = P.ldc = c.R[j];
         } else {
           P.C32 = h->work_f[j % 2] + h->f_off[ci];
           P.c_rhs_stride = h->f_total;
-          P.out_nv = c.K[j + 1];
-          P.ldc = tc_ld(c.K[j + 1]);
         }
         P.Bt = c.Bt[j];
         P.R = c.R[j]; P.K = c.K[j]; P.N = c.N[j];

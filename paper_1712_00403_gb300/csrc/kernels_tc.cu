@@ -11,10 +11,10 @@
 // Persistent, warp-specialized kernel (one CTA per SM, 18 warps). A tile is
 // 128 rows x NT columns (NT <= 256, a multiple of 16); K runs in stages of 32
 // through a ring of 2-4 shared-memory stages:
-//   * warp 17 (lane 0) issues, per stage, one TMA tensor load per 32-row
-//     group of A (box 32 FP32 columns x 32 rows, SWIZZLE_128B K-major,
-//     straight into the operand image's hi half; rows and columns past the
-//     tensor read as zero) and one bulk async copy of the stage's B image
+//   * warp 17 (lane 0) issues, per stage, one TMA tensor load of A (box 32
+//     FP32 columns x 128 rows, SWIZZLE_128B K-major, straight into the
+//     operand image's hi half; rows and columns past the tensor read as
+//     zero) and one bulk async copy of the stage's B image
 //     (pre-split and pre-swizzled on the host, SWIZZLE_32B K-major), all on
 //     one mbarrier transaction count, as soon as the MMA has released the
 //     slot;
@@ -24,10 +24,9 @@
 //   * warp 16 allocates tensor memory and its lane 0 issues tcgen05.mma
 //     (kind::tf32, M=128, N=NT, K=8), releasing each stage with
 //     tcgen05.commit; accumulators are double-buffered in tensor memory;
-//   * warps 8-15 (two per TMEM lane quarter, alternating 16-column chunks)
-//     drain the other accumulator with tcgen05.ld (the next chunk's load in
-//     flight while the current one is stored) while the next tile's MMAs
-//     run, apply the fused
+//   * warps 8-15 (two halves of one warp per TMEM lane quarter, alternating
+//     16-column chunks) drain the other accumulator with tcgen05.ld (the next
+//     chunk's load in flight) while the next tile's MMAs run, apply the fused
 //     Algorithm 1 step 3 divide (lam_row[r] + lam_col[n]) and the optional
 //     D^{-1/2} scaling, and write the transposed FP32 (or final FP64) tensor.
 // The first contraction of a chain reads FP64: a grouped elementwise kernel
@@ -61,7 +60,6 @@ constexpr int kMmaWarp = 16;
 constexpr int kTmaWarp = 17;
 constexpr int kThreads = 576;
 constexpr int kAHalfBytes = kM * kKC * 4;   // 128 rows x 32 FP32 (hi or lo half of a stage's A)
-constexpr int kGroupBytes = 32 * kKC * 4;    // one 32-row group: 4 atoms of 8 rows x 128 B
 constexpr int kNTMax = 256;
 constexpr int kAStageBytes = 2 * 4 * kM * 32;   // hi/lo x 4 k-steps x 128 rows x 32 B
 constexpr int kSmemBudget = 227 * 1024;
@@ -171,11 +169,11 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
 
 // TMA tensor load of one box (coordinates innermost first) into shared memory,
 // completing as transaction bytes on the mbarrier.
-__device__ __forceinline__ void tma_load_4d(void *dst, const void *tmap, int x, int y, int z, int w, uint64_t *bar) {
+__device__ __forceinline__ void tma_load_3d(void *dst, const void *tmap, int x, int y, int z, uint64_t *bar) {
   asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
-      "[%6];" ::"r"(smem_u32(dst)),
-      "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(dst)),
+      "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
       : "memory");
 }
 
@@ -269,12 +267,10 @@ __device__ __forceinline__ uint32_t idesc_tf32(int nt) {
 
 // ------------------------------------------------------------------ kernel
 
-// A tile is 4 row groups of 32 rows; group g of a problem is the 32-row block
-// vb = g % nvb of row run u = g / nvb (rows r = u * out_nv + v, v in
-// [32 vb, 32 vb + 32) and < out_nv), so that each TMEM lane quarter stores
-// 128-byte aligned lines (output rows are padded to a multiple of 32).
+// A tile is 128 consecutive rows r0..r0+127 of A (one TMA box per stage) by
+// NT columns.
 struct TileInfo {
-  int prob, rhs, g0, G, nvb, n0, NT, nstages, kp;
+  int prob, rhs, r0, n0, NT, nstages, kp;
   bool valid;
 };
 
@@ -290,11 +286,9 @@ __device__ __forceinline__ TileInfo decode_tile(const TcGroup &g, int T, int nrt
   t.rhs = z / g.nprob;
   const TcProb &P = prob_of(g, t.prob);
   const int npad = (P.N + 15) & ~15;
-  t.nvb = (P.out_nv + 31) >> 5;
-  t.G = (P.R / P.out_nv) * t.nvb;
-  t.g0 = rt * 4;
+  t.r0 = rt * kM;
   t.n0 = nt * kNTMax;
-  t.valid = t.g0 < t.G && t.n0 < npad && !(done && done[t.rhs]) && !(P.done_flag && *P.done_flag);
+  t.valid = t.r0 < P.R && t.n0 < npad && !(done && done[t.rhs]) && !(P.done_flag && *P.done_flag);
   t.NT = npad - t.n0 < kNTMax ? npad - t.n0 : kNTMax;
   t.kp = (P.K + 7) & ~7;
   t.nstages = (t.kp + kKC - 1) / kKC;
@@ -365,12 +359,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int k0 = s * kKC;
           const int ks = (t.kp - k0) / 8 < 4 ? (t.kp - k0) / 8 : 4;
           const uint32_t bbytes = 2u * ks * t.NT * 32u;
-          const int ng = t.G - t.g0 < 4 ? t.G - t.g0 : 4;
-          mbar_expect_tx(&landed[slot], ng * kGroupBytes + bbytes);
-          for (int q4 = 0; q4 < ng; ++q4) {
-            const int gg = t.g0 + q4, u = gg / t.nvb, vb = gg - u * t.nvb;
-            tma_load_4d(sA + q4 * kGroupBytes, P.tmap, k0, 32 * vb, u, t.rhs, &landed[slot]);
-          }
+          mbar_expect_tx(&landed[slot], kAHalfBytes + bbytes);
+          tma_load_3d(sA, P.tmap, k0, t.r0, t.rhs, &landed[slot]);
           bulk_g2s(sB, P.Bt + btile + 2 * (size_t)t.NT * k0, bbytes, &landed[slot]);
           last_par[slot] = u & 1;
         }
@@ -414,6 +404,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp < kMmaWarp) {
     // ------------------------------------------------------------ epilogue
+    // Each half (4 warps, one per TMEM lane quarter) takes every other 16-column
+    // chunk; a lane owns one row and stores its 16 columns (consecutive lanes
+    // write consecutive positions of a column).
     const int quarter = warp & 3, half = (warp - kEpiWarp0) >> 2;
     int v = 0;
     for (int T = next_tile(g, -1, total, nrt, ntn, done); T < total; T = next_tile(g, T, total, nrt, ntn, done)) {
@@ -422,20 +415,19 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int acc = v & 1;
       if (!mbar_wait(&tfull[acc], (v >> 1) & 1, abort)) break;
       tc_fence_after();
-      const int gq = t.g0 + quarter, uu = gq / t.nvb, vr = (gq - uu * t.nvb) * 32 + lane;
-      const bool rok = gq < t.G && vr < P.out_nv;
-      const int r = uu * P.out_nv + vr;
-      const float lr = (P.lam_row && rok) ? P.lam_row[r] : 0.0f;
       // every field the stores need, in registers (no reloads between stores)
+      const int r = t.r0 + quarter * 32 + lane, R = P.R, Ncols = P.N;
+      const bool rok = r < R;
+      const float lr = (P.lam_row && rok) ? P.lam_row[r] : 0.0f;
       const float *__restrict__ lc = P.lam_col;
-      const int nu = P.R / P.out_nv, Ncols = P.N;
-      const int64_t Rrows = P.R;
       const double *__restrict__ so = P.scale_out;
-      // output address of column n: base + n * cstride (row-major over (n, u), padded v)
-      const int64_t cstride = (int64_t)nu * P.ldc;
-      const int64_t base = (int64_t)t.rhs * P.c_rhs_stride + (int64_t)uu * P.ldc + vr;
-      double *__restrict__ c64 = P.C64 ? P.C64 + base : nullptr;
-      float *__restrict__ c32 = P.C32 ? P.C32 + base : nullptr;
+      const int64_t cs = P.c_cs;
+      // row r = u*out_nv + v goes to n*cs + u*ldv + v (FP32) or n*R + r (FP64 result)
+      const int uu = r / P.out_nv;
+      const int64_t pos = P.C64 ? (int64_t)r : (int64_t)uu * P.ldv + (r - uu * P.out_nv);
+      double *__restrict__ c64 = P.C64 ? P.C64 + (int64_t)t.rhs * P.c_rhs_stride + pos : nullptr;
+      float *__restrict__ c32 = P.C32 ? P.C32 + (int64_t)t.rhs * P.c_rhs_stride + pos : nullptr;
+      const double *__restrict__ sor = so ? so + r : nullptr;
       const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * ntc);
       const int nchunks = t.NT / 16;
       auto store_chunk = [&](const uint32_t (&vals)[16], int c) {
@@ -449,21 +441,21 @@ __global__ void __launch_bounds__(kThreads, 1)
               float x = __uint_as_float(vals[qq]);
               if (lc) x = x / (lr + lc[n]);
               double y = (double)x;
-              if (so) y *= so[(int64_t)n * Rrows + r];
-              c64[n * cstride] = y;
+              if (sor) y *= sor[(int64_t)n * R];
+              c64[(int64_t)n * cs] = y;
             }
           }
         } else if (lc) {
 #pragma unroll
           for (int qq = 0; qq < 16; ++qq) {
             const int n = nb + qq;
-            if (n < Ncols) c32[n * cstride] = __uint_as_float(vals[qq]) / (lr + lc[n]);
+            if (n < Ncols) c32[(int64_t)n * cs] = __uint_as_float(vals[qq]) / (lr + lc[n]);
           }
         } else {
 #pragma unroll
           for (int qq = 0; qq < 16; ++qq) {
             const int n = nb + qq;
-            if (n < Ncols) c32[n * cstride] = __uint_as_float(vals[qq]);
+            if (n < Ncols) c32[(int64_t)n * cs] = __uint_as_float(vals[qq]);
           }
         }
       };
@@ -560,13 +552,13 @@ __global__ void k_tc_convert(TcGroup g, const int *done) {
   const unsigned K = (unsigned)P.K, total = (unsigned)P.R * K;
   for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
     const unsigned r = e / K, k = e - r * K;
-    double v = src[e];
-    if (P.scale_in) v *= P.scale_in[e];
-    dst[(size_t)r * P.lda + k] = (float)v;
+    double x = src[e];
+    if (P.scale_in) x *= P.scale_in[e];
+    dst[(size_t)r * P.lda + k] = (float)x;
   }
 }
 
-fdst_status tc_encode_map(void *map128, const float *A32, int K, int nv, int nu, int lda, int64_t rhs_stride, int nrhs) {
+fdst_status tc_encode_map(void *map128, const float *A32, int K, int R, int lda, int64_t rhs_stride, int nrhs) {
   using Encode = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                               const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                               CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -586,16 +578,15 @@ fdst_status tc_encode_map(void *map128, const float *A32, int K, int nv, int nu,
       encode = reinterpret_cast<Encode>(fn);
     }
   }
-  if ((reinterpret_cast<uintptr_t>(A32) & 15) || (lda & 3) || (rhs_stride & 3) || K < 1 || nv < 1 || nu < 1 ||
-      nrhs < 1) {
+  if ((reinterpret_cast<uintptr_t>(A32) & 15) || (lda & 3) || (rhs_stride & 3) || K < 1 || R < 1 || nrhs < 1) {
     set_error("tensor map: FP32 operand must be 16-byte aligned with row and right-hand-side pitches of 4 floats");
     return FDST_INVALID_ARGUMENT;
   }
-  const cuuint64_t dims[4] = {(cuuint64_t)K, (cuuint64_t)nv, (cuuint64_t)nu, (cuuint64_t)nrhs};
-  const cuuint64_t strides[3] = {(cuuint64_t)lda * 4, (cuuint64_t)nv * lda * 4, (cuuint64_t)rhs_stride * 4};
-  const cuuint32_t box[4] = {32, 32, 1, 1};
-  const cuuint32_t estr[4] = {1, 1, 1, 1};
-  const CUresult r = encode(reinterpret_cast<CUtensorMap *>(map128), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
+  const cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)R, (cuuint64_t)nrhs};
+  const cuuint64_t strides[2] = {(cuuint64_t)lda * 4, (cuuint64_t)rhs_stride * 4};
+  const cuuint32_t box[3] = {(cuuint32_t)kKC, (cuuint32_t)kM, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult r = encode(reinterpret_cast<CUtensorMap *>(map128), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
                             const_cast<float *>(A32), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -608,16 +599,13 @@ fdst_status tc_encode_map(void *map128, const float *A32, int K, int nv, int nu,
 
 static int *g_err_flag = nullptr;
 
-int tc_padded_rows(int R, int out_nv) { return (R / out_nv) * ((out_nv + 31) & ~31); }
-
 static void tc_dims(const TcGroup &g, int &maxR, int &maxN) {
   maxR = g.maxR;
   maxN = g.maxN;
   if (!g.table)
     for (int i = 0; i < g.nprob; ++i) {
       if (g.p[i].N > maxN) maxN = g.p[i].N;
-      const int rp = tc_padded_rows(g.p[i].R, g.p[i].out_nv);
-      if (rp > maxR) maxR = rp;
+      if (g.p[i].R > maxR) maxR = g.p[i].R;
     }
 }
 

@@ -9,17 +9,16 @@
 
 namespace fdst {
 
-// Same contraction as GemmProb (C(r, n) = sum_k A(r, k) B(k, n) stored at
-// C[n*R + r]) with FP32 intermediates; B is pre-split into TF32 hi/lo parts.
-// A is read by TMA from the FP32 array A32 (row r at r*lda, lda a multiple of
-// 4, right-hand sides a_rhs_stride apart) through the tensor map `tmap`
-// (device memory, made by tc_encode_map). When A64 is set (first step of a
-// chain) the group's launch first writes A32 = (float)(A64 * scale_in)
-// (A64 rows at r*K, right-hand sides a64_rhs_stride apart). C(r, n) with
-// r = u*out_nv + v is stored at (n*(R/out_nv) + u)*ldc + v: the output's rows
-// (n, u) hold the next contracted index v, padded to ldc (a multiple of 32
-// for FP32 outputs; out_nv = ldc = R writes C[n*R + r]); the last step writes
-// FP64 (C64, times scale_out).
+// Same contraction as GemmProb (C(r, n) = sum_k A(r, k) B(k, n)) with FP32
+// intermediates; B is pre-split into TF32 hi/lo parts. A is read by TMA from
+// the FP32 array A32 (row r at r*lda, lda a multiple of 8; right-hand sides
+// a_rhs_stride apart) through the tensor map `tmap` (device memory, made by
+// tc_encode_map). When A64 is set (first step of a chain) the group's launch
+// first writes A32 = (float)(A64 * scale_in) (A64 rows at r*K, right-hand
+// sides a64_rhs_stride apart). Rows r = u*out_nv + v (out_nv = size of the
+// next contracted index): on intermediate steps C(r, n) goes in FP32 to
+// n*c_cs + u*ldv + v (the next step's rows, pitch ldv = its lda, c_cs =
+// (R/out_nv)*ldv); on the last step in FP64, times scale_out, to n*R + r.
 struct TcProb {
   const double *A64 = nullptr;
   const float *A32 = nullptr;
@@ -28,8 +27,9 @@ struct TcProb {
   float *C32 = nullptr;
   const float *Bt = nullptr;
   int64_t a_rhs_stride = 0, a64_rhs_stride = 0, c_rhs_stride = 0;
+  int64_t c_cs = 0;
   int R = 0, K = 0, N = 0;
-  int lda = 0, out_nv = 0, ldc = 0;
+  int lda = 0, out_nv = 0, ldv = 0;
   const float *lam_row = nullptr, *lam_col = nullptr;
   const double *scale_in = nullptr, *scale_out = nullptr;
   const int *done_flag = nullptr;   // the problem is skipped when *done_flag != 0 (batched solves)
@@ -39,21 +39,32 @@ struct TcGroup {
   TcProb p[8];
   int nprob = 0;
   const TcProb *table = nullptr;
-  int maxR = 0, maxN = 0;           // with a table: largest tc_padded_rows and N among its problems
+  int maxR = 0, maxN = 0;           // with a table: largest R and N among its problems
   int convert = 0;                  // 1: convert A64 into A32 first (problems with A64 set)
 };
+// Layout of one contraction step of a chain (rows R, contracted size K,
+// out_nv = size of the next contracted index): lda = K rounded up to 8 (TMA
+// pitch), ldv = out_nv rounded up to 8 (the next step's lda), c_cs = output
+// slice pitch (R for the last step's unpadded FP64 result).
+struct TcLayout {
+  int lda, ldv, nu;
+  int64_t c_cs;
+};
+inline int tc_round(int x, int m) { return (x + m - 1) / m * m; }
+inline TcLayout tc_layout(int R, int K, int out_nv, bool last) {
+  TcLayout L;
+  L.nu = R / out_nv;
+  L.lda = tc_round(K, 8);
+  L.ldv = tc_round(out_nv, 8);
+  L.c_cs = last ? R : (int64_t)L.nu * L.ldv;
+  return L;
+}
 // Writes the TMA descriptor (128 bytes, host memory) that reads boxes of
-// 32 columns x 32 rows of one row run of A32 into the K-major SWIZZLE_128B
-// shared-memory image of the tensor-core operand. A32 rows r = u*nv + v
-// (v < nv, u < nu) hold K values at pitch lda floats; right-hand sides are
-// rhs_stride floats apart. Columns at or beyond K and rows v at or beyond nv
-// read as zero.
-fdst_status tc_encode_map(void *map128, const float *A32, int K, int nv, int nu, int lda, int64_t rhs_stride, int nrhs);
-// Rows a contraction occupies in the kernel's row-group grid: R / out_nv runs
-// of out_nv rows, each padded to a multiple of 32 (TcGroup.maxR in table mode).
-int tc_padded_rows(int R, int out_nv);
-// Row pitch (floats) of the FP32 operands and intermediates: K rounded up to 32.
-inline int tc_ld(int K) { return (K + 31) & ~31; }
+// 32 columns x 128 rows of A32 (dims K, R, nrhs; row pitch lda floats;
+// right-hand-side pitch rhs_stride floats) into the K-major SWIZZLE_128B
+// shared-memory image of the tensor-core operand. Columns at or beyond K and
+// rows at or beyond R read as zero.
+fdst_status tc_encode_map(void *map128, const float *A32, int K, int R, int lda, int64_t rhs_stride, int nrhs);
 // ring: shared-memory stages (0 = as many as fit, capped at 4).
 fdst_status launch_gemm_tc(const TcGroup &g, int nrhs, const int *done, cudaStream_t s, int ring = 0);
 // number of stages that fit for the widest column tile of g
