@@ -288,7 +288,7 @@ def run_gpu(args):
     knots = synth.knots_for(w)
     t_setup = time.perf_counter()
     mapped = w.get("geometry") == "sine_bump"
-    mv = fd.MV_DF64 if args.matvec == "df64" and not mapped else fd.MV_F64
+    mv = fd.MV_DF64 if args.matvec == "df64" else fd.MV_F64
     geo = dict(geometry=fd.GEOM_SINE_BUMP, variant=fd.VARIANT_PD_GEO) if mapped else {}
     P = fd.Stokes(knots, w["p"], disc=fd.TH if w["disc"] == "TH" else fd.RT, fd_precision=prec, max_rhs=nrhs,
                   matvec_precision=mv, **geo)
@@ -366,10 +366,12 @@ def run_gpu(args):
     per_pc = tm["ms_prec"] / max(tm["n_prec"], 1)
     if per_mv >= per_pc and mapped:
         nnz = P.flops_matvec / 2.0
-        kern = "csr_spmv_f64 (assembled mapped Stokes operator, one warp per row, 4 RHS per pass)"
-        # algorithmic bytes per launch: values + column indices + row pointers once, x and y once per RHS
+        kern = ("csr_spmv_%s (assembled mapped Stokes operator, one warp per row, 4 RHS per pass)"
+                % ("df64" if mv == fd.MV_DF64 else "f64"))
+        # algorithmic bytes per matvec: values (8 B: FP64 or an FP32 pair) + column indices + row pointers
+        # once, x and y once per RHS (plus, for double-float, the split of x: 16 B per entry and RHS)
         flops = None
-        byts = 12.0 * nnz + 8.0 * (P.n_total + 1) + 16.0 * P.n_total * nrhs
+        byts = 12.0 * nnz + 8.0 * (P.n_total + 1) + 16.0 * P.n_total * nrhs * (2 if mv == fd.MV_DF64 else 1)
         t_ms = per_mv
         peak, bound = pk.get("hbm_gbs", 6701.5), "hbm"
         peak_note = "measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
@@ -433,8 +435,10 @@ def run_gpu(args):
                "vs_baseline": None, "dtype": dtype, "data": "synthetic",
                "config": {"workload": describe(args.workload, w, nrhs), "nrhs_per_gpu": nrhs,
                           "fd_precision": "f64" if prec == fd.FD_F64 else "tf32x3",
-                          "matvec": ("double-float (FP32 pairs, 48-bit significand) in the iterations; "
-                                     "true residual in FP64") if mv == fd.MV_DF64 else
+                          "matvec": (("double-float (FP32 pairs, 48-bit significand) %s in the iterations; "
+                                      "true residual in FP64") % ("CSR SpMV (%d nonzeros)" % int(P.flops_matvec / 2)
+                                                                  if mapped else "banded Kronecker products"))
+                                    if mv == fd.MV_DF64 else
                                     ("FP64 CSR SpMV (%d nonzeros)" % int(P.flops_matvec / 2) if mapped else "FP64"),
                           "n_total": P.n_total,
                           "l2": "inputs larger than L2 (each step streams %d x %.0f MB vectors)" % (

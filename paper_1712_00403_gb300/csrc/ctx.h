@@ -143,14 +143,15 @@ fdst_status run_matvec(fdst_ctx *h, const double *x, double *y, int nrhs, const 
 
 // What to do with a right-hand side whose recurrence estimate met its
 // threshold, given its FP64 true relative residual now and at its previous
-// check (negative: none). The recurrence is resumed with a tighter threshold
-// (its state intact) while resumes keep lowering the true residual; once a
-// resume leaves it within a factor 0.7 of the previous value the recurrence
-// has drifted away from the true residual (rounding in the iterations'
-// matvec), and MINRES is restarted from the current iterate, at most
+// check (negative: none). The first time the true residual is above tol the
+// recurrence is resumed with a tighter threshold (its state intact: the
+// estimate is a P^{-1}-norm residual, the target an l2 one). If that is not
+// enough, the recurrence has drifted from the true residual (rounding in the
+// iterations' arithmetic, loss of orthogonality over long runs), and MINRES
+// is restarted from the current iterate with an FP64 residual, at most
 // kMaxRestarts times before the solve is reported as stagnated.
 enum { kKeepStopped = 0, kResume = 1, kRestart = 2, kStagnated = 3 };
-constexpr int kMaxRestarts = 3;
+constexpr int kMaxRestarts = 8;
 int resume_action(const MinresState &S, double true_rel, double prev_true, int restarts, double tol, int maxit);
 
 // Restarts MINRES for the right-hand sides listed in `which` from the current

@@ -591,8 +591,8 @@ static fdst_status run_matvec_df(fdst_ctx *h, const double *x, double *y, int nr
 
 int resume_action(const MinresState &S, double true_rel, double prev_true, int restarts, double tol, int maxit) {
   if (!(S.status == 0 && S.stop && S.gamma > 0.0 && true_rel > tol && S.iters < maxit)) return kKeepStopped;
-  if (prev_true > 0.0 && true_rel > 0.7 * prev_true) return restarts < kMaxRestarts ? kRestart : kStagnated;
-  return kResume;
+  if (prev_true < 0.0) return kResume;
+  return restarts < kMaxRestarts ? kRestart : kStagnated;
 }
 
 fdst_status minres_restart(fdst_ctx *h, const double *b, double *x, int nrhs, const std::vector<int> &which,
@@ -639,7 +639,12 @@ fdst_status minres_restart(fdst_ctx *h, const double *b, double *x, int nrhs, co
 fdst_status run_matvec(fdst_ctx *h, const double *x, double *y, int nrhs, const int *done, cudaStream_t st,
                        bool exact) {
   if (h->mapped) {
-    launch_spmv(h->csr, x, y, h->n_total, nrhs, done, st);
+    if (!exact && h->csr.val_df) {
+      launch_split_df(x, h->x2, h->n_total, h->n_total, nrhs, done, st);
+      launch_spmv_df(h->csr, h->x2, y, h->n_total, nrhs, done, st);
+    } else {
+      launch_spmv(h->csr, x, y, h->n_total, nrhs, done, st);
+    }
     CK(cudaGetLastError());
     return FDST_OK;
   }

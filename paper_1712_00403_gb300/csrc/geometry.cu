@@ -7,6 +7,7 @@
 
 #include <cmath>
 
+#include "df_arith.cuh"
 #include "geometry.h"
 #include "kernels.h"
 
@@ -444,6 +445,67 @@ void launch_spmv(const CsrDev &A, const double *x, double *y, int64_t stride, in
                  cudaStream_t s) {
   count_launch(1);
   k_spmv<<<152 * 16, 256, 0, s>>>(A.row_ptr, A.col, A.val, A.nrows, x, y, stride, nrhs, done);
+}
+
+// Double-float SpMV: the same row-per-warp pass over 4 right-hand sides with
+// every multiply-add on the FP32 units (12 operations instead of one FP64
+// FMA at 1/64 of the rate); lanes' partial pairs are combined by shuffles.
+__global__ void k_spmv_df(const int64_t *row_ptr, const int *col, const float2 *val, int64_t nrows, const float2 *x,
+                          double *y, int64_t stride, int nrhs, const int *done) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t row = warp; row < nrows; row += nwarps) {
+    const int64_t a = row_ptr[row], b = row_ptr[row + 1];
+    for (int j0 = 0; j0 < nrhs; j0 += 4) {
+      float sh[4] = {0.f, 0.f, 0.f, 0.f}, sl[4] = {0.f, 0.f, 0.f, 0.f};
+      const int nj = nrhs - j0 < 4 ? nrhs - j0 : 4;
+      bool act[4];
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) act[jj] = jj < nj && !(done && done[j0 + jj]);
+      // two nonzeros per lane per pass: their loads are in flight together
+      int64_t k = a + lane;
+      for (; k + 32 < b; k += 64) {
+        const float2 v0 = val[k], v1 = val[k + 32];
+        const int c0 = col[k], c1 = col[k + 32];
+        float2 x0[4], x1[4];
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj)
+          if (act[jj]) {
+            x0[jj] = x[(int64_t)(j0 + jj) * stride + c0];
+            x1[jj] = x[(int64_t)(j0 + jj) * stride + c1];
+          }
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj)
+          if (act[jj]) {
+            df_fma_acc(v0, x0[jj], sh[jj], sl[jj]);
+            df_fma_acc(v1, x1[jj], sh[jj], sl[jj]);
+          }
+      }
+      if (k < b) {
+        const float2 v = val[k];
+        const int c = col[k];
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj)
+          if (act[jj]) df_fma_acc(v, x[(int64_t)(j0 + jj) * stride + c], sh[jj], sl[jj]);
+      }
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) {
+        float h = sh[jj], l = sl[jj];
+        for (int o = 16; o > 0; o >>= 1) {
+          const float oh = __shfl_down_sync(0xffffffffu, h, o), ol = __shfl_down_sync(0xffffffffu, l, o);
+          df_add(h, l, oh, ol);
+        }
+        if (lane == 0 && act[jj]) y[(int64_t)(j0 + jj) * stride + row] = (double)h + (double)l;
+      }
+    }
+  }
+}
+
+void launch_spmv_df(const CsrDev &A, const float2 *x2, double *y, int64_t stride, int nrhs, const int *done,
+                    cudaStream_t s) {
+  count_launch(1);
+  k_spmv_df<<<152 * 16, 256, 0, s>>>(A.row_ptr, A.col, A.val_df, A.nrows, x2, y, stride, nrhs, done);
 }
 
 __global__ void k_csr_diag(const int64_t *row_ptr, const int *col, const double *val, int64_t nrows, double *d) {

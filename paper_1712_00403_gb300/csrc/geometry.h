@@ -44,6 +44,7 @@ struct CsrDev {
   const int64_t *row_ptr = nullptr;
   const int *col = nullptr;
   const double *val = nullptr;
+  const float2 *val_df = nullptr;   // the values as FP32 pairs (double-float SpMV), or nullptr
   int64_t nrows = 0, nnz = 0;
 };
 
@@ -55,6 +56,9 @@ void launch_csr_cols(const CsrTables &ct, int *col, cudaStream_t s);
 size_t assemble_smem_bytes(int p);
 fdst_status launch_assemble(const GeoPoints &gp, const MeshTables &mt, const CsrTables &ct, double *val,
                             cudaStream_t s);
+// y_j = A x_j in double-float arithmetic (x pre-split into FP32 pairs, FP64 result).
+void launch_spmv_df(const CsrDev &A, const float2 *x2, double *y, int64_t stride, int nrhs, const int *done,
+                    cudaStream_t s);
 void launch_spmv(const CsrDev &A, const double *x, double *y, int64_t stride, int nrhs, const int *done,
                  cudaStream_t s);
 void launch_csr_diag(const CsrDev &A, double *d, cudaStream_t s);

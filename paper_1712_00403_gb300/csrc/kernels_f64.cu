@@ -9,6 +9,7 @@
 #include <atomic>
 #include <cmath>
 
+#include "df_arith.cuh"
 #include "kernels.h"
 
 namespace fdst {
@@ -187,23 +188,6 @@ void launch_band(const BandGroup &g, int nrhs, const int *done, cudaStream_t s) 
 // unevaluated sum hi + lo of two floats. Products use the exact FMA residual
 // (p = a*b, e = fma(a, b, -p)), sums use Knuth's branch-free TwoSum.
 
-__device__ __forceinline__ void df_fma_acc(float2 a, float2 b, float &sh, float &sl) {
-  const float p = a.x * b.x;
-  float e = fmaf(a.x, b.x, -p);
-  e = fmaf(a.x, b.y, e);
-  e = fmaf(a.y, b.x, e);
-  const float t = sh + p;
-  const float z = t - sh;
-  const float err = (sh - (t - z)) + (p - z);
-  sh = t;
-  sl = sl + (err + e);
-}
-
-__device__ __forceinline__ float2 df_norm(float sh, float sl) {
-  const float h = sh + sl;
-  return make_float2(h, sl - (h - sh));
-}
-
 // Each thread computes T outputs that share one band row i (so one V row and
 // one lo[i]): for mode 0 (contracted index fastest) T consecutive lines with
 // lanes over consecutive rows i; for modes 1 and 2 T entries of the flattened
@@ -252,6 +236,7 @@ __global__ void __launch_bounds__(512) k_band_df(BandGroupDF g, int nrhs, const 
       float sh[T], sl[T];
 #pragma unroll
       for (int t = 0; t < T; ++t) sh[t] = sl[t] = 0.0f;
+#pragma unroll 2
       for (int j = 0; j < w; ++j) {
         const float2 v = vp[j];
 #pragma unroll
@@ -287,6 +272,8 @@ __global__ void __launch_bounds__(512) k_band_df(BandGroupDF g, int nrhs, const 
       float sh[T], sl[T];
 #pragma unroll
       for (int t = 0; t < T; ++t) sh[t] = sl[t] = 0.0f;
+      // unrolled by 4: the loads of four band columns are in flight together
+#pragma unroll 4
       for (int j = 0; j < w; ++j) {
         const float2 v = vp[j];
 #pragma unroll

@@ -63,10 +63,6 @@ fdst_status build_mapped_pre(fdst_ctx *h) {
     set_error("mapped-geometry assembly supports pressure degree p <= 3 (element matrices in shared memory)");
     return FDST_NOT_SUPPORTED;
   }
-  if (h->desc.matvec_precision != FDST_MV_F64) {
-    set_error("the assembled CSR operator is evaluated in FP64 only");
-    return FDST_NOT_SUPPORTED;
-  }
   h->mapped = true;
   const int p = h->p, q = p + 1, nq = p + 2;
   cudaStream_t st = 0;
@@ -234,6 +230,15 @@ fdst_status build_mapped_pre(fdst_ctx *h) {
   h->csr.val = dval;
   h->csr.nrows = nrows;
   h->csr.nnz = nnz;
+  if (h->desc.matvec_precision == FDST_MV_DF64) {
+    // FP32-pair copy of the values and a split right-hand-side buffer for the
+    // double-float SpMV inside the iterations (true residuals use FP64)
+    float2 *vdf = nullptr;
+    TRY(dalloc(h, &vdf, (size_t)nnz));
+    launch_split_df(dval, vdf, nnz, nnz, 1, nullptr, st);
+    h->csr.val_df = vdf;
+    TRY(dalloc(h, &h->x2, (size_t)h->n_total * h->max_rhs));
+  }
   // ---- diagonal scalings of P_D^G: D_V = diag(A) / diag(P~_V), D_Q = diag(Q) / diag(P_Q)
   h->geo_scale.assign(4, std::vector<double>());
   if (h->desc.variant == FDST_VARIANT_PD_GEO) {

@@ -105,3 +105,39 @@ def test_full_size_sampled_columns():
         for c, v in ent.items():
             ref[c] = v
         assert np.abs(col - ref).max() <= 1e-12 * np.abs(ref).max(), (blk, m)
+
+
+@pytest.mark.parametrize("spec", CASES[:2], ids=_ids)
+def test_double_float_spmv_and_minres(spec):
+    """Double-float CSR SpMV (FP32 pairs) against the oracle's FP64 matvec
+    (<= 1e-12 per block, relative) and P_D^G-MINRES (FP64 FD apply) with it
+    inside the iterations: tolerance reached (FP64 true residual) within 10%
+    of the iterations of the FP64-SpMV solve (these small mapped problems
+    need 100-250 iterations, where 48-bit and 53-bit recurrences drift
+    apart by a few)."""
+    import paper_1712_00403_gb300 as fd
+    S = oracle_problem(spec)
+    G = geo.Grid(S)
+    P = _gpu(spec, max_rhs=2, matvec_precision=fd.MV_DF64, fd_precision=fd.FD_TF32X3)
+    X = np.stack([synth.random_vector(90 + j, P.n_total) for j in range(2)])
+    x = torch.tensor(X.reshape(-1), device="cuda")
+    # fdst_matvec evaluates the iterations' operator (double-float here)
+    y = torch.empty_like(x)
+    P.matvec(x, y)
+    out = y.cpu().numpy().reshape(2, -1)
+    for j in range(2):
+        ref = geo.matvec(S, G, X[j])
+        for o0, o1 in zip(P.block_offsets[:-1], P.block_offsets[1:]):
+            assert rel(out[j, o0:o1], ref[o0:o1]) <= 1e-12
+    if spec["p"] != 2:
+        return   # the p = 3 case converges too slowly for the oracle itself (600+ iterations)
+    b_h = synth.rhs(301, S.block_sizes)
+    its = {}
+    for mv in (fd.MV_F64, fd.MV_DF64):
+        Q = _gpu(spec, fd_precision=fd.FD_F64, matvec_precision=mv)
+        b = torch.tensor(b_h, device="cuda")
+        xx = torch.zeros_like(b)
+        info = Q.solve(b, xx, tol=1e-8, maxit=600)[0]
+        assert info["status"] == "OK" and info["true_rel_res"] <= 1e-8, (mv, info)
+        its[mv] = info["iterations"]
+    assert its[fd.MV_DF64] <= 1.1 * its[fd.MV_F64] + 2, its
