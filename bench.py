@@ -48,6 +48,8 @@ def parse():
                     help="matvec arithmetic inside the iterations (true residual always FP64)")
     ap.add_argument("--nrhs", type=int, default=0, help="right-hand sides per step (default: the workload's)")
     ap.add_argument("--maxit", type=int, default=400)
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="skip the oracle timing (profiling runs of the GPU path)")
     return ap.parse_args()
 
 
@@ -421,7 +423,7 @@ def run_gpu(args):
            "h2d_bytes_per_step": 2 * b.numel() * 8, "d2h_bytes_per_step": b.numel() * 8}
 
     cpu = None
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_sample(w, w["seeds"], float(np.mean(iters)), k_iters=1 if mapped else 2)
         cpu.pop("seconds", None)
         cpu.pop("t_iter_s", None)

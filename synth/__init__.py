@@ -12,6 +12,9 @@ WORKLOADS = {
     "square_th_p2_16": dict(dim=2, disc="TH", p=2, n_el=(16, 16), seeds=[1]),
     # 3D unit cube, Taylor-Hood, p=3, 64^3 elements, 16 right-hand sides, seeds 200..215
     "cube_th_p3_64": dict(dim=3, disc="TH", p=3, n_el=(64, 64, 64), seeds=list(range(200, 216))),
+    # 3D unit cube, Taylor-Hood, p=3, 40^3 elements, 16 right-hand sides (profiling-sized case:
+    # 1,673,830 DoF, 214 MB per 16-vector block, larger than L2)
+    "cube_th_p3_40": dict(dim=3, disc="TH", p=3, n_el=(40, 40, 40), seeds=list(range(200, 216))),
     # 3D mapped cube (sine bump map, variable viscosity), p=3, 32^3 elements, seeds 300..303
     "mapped_th_p3_32": dict(dim=3, disc="TH", p=3, n_el=(32, 32, 32), seeds=list(range(300, 304)),
                             geometry="sine_bump"),
