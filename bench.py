@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="cube_th_p3_64")
-    ap.add_argument("--fd", default="auto", choices=["auto", "f64", "tf32"])
+    ap.add_argument("--fd", default="auto", choices=["auto", "f64", "tf32", "bf16"])
     ap.add_argument("--matvec", default="df64", choices=["f64", "df64"],
                     help="matvec arithmetic inside the iterations (true residual always FP64)")
     ap.add_argument("--nrhs", type=int, default=0, help="right-hand sides per step (default: the workload's)")
@@ -284,9 +284,10 @@ def run_gpu(args):
     w = workload(args.workload)
     nrhs = args.nrhs or len(w["seeds"])
     if args.fd == "auto":
-        prec = fd.FD_TF32X3 if getattr(fd, "HAS_TC", False) else fd.FD_F64
+        # the mapped configuration names the split-BF16 form; the others split-TF32
+        prec = fd.FD_BF16X6 if w.get("geometry") == "sine_bump" else fd.FD_TF32X3
     else:
-        prec = fd.FD_F64 if args.fd == "f64" else fd.FD_TF32X3
+        prec = {"f64": fd.FD_F64, "tf32": fd.FD_TF32X3, "bf16": fd.FD_BF16X6}[args.fd]
     knots = synth.knots_for(w)
     t_setup = time.perf_counter()
     mapped = w.get("geometry") == "sine_bump"
@@ -395,6 +396,11 @@ def run_gpu(args):
         if prec == fd.FD_F64:
             peak, bound = FP64_NOMINAL_TFLOPS, "alu"
             peak_note = "FP64 DFMA nominal 1.25 TFLOP/s (recipe table; measured DFMA chain 1.20)"
+        elif prec == fd.FD_BF16X6:
+            peak = pk.get("bf16_tflops_sustained", 1748.4)
+            bound = "tensor"
+            peak_note = "measured bf16 sustained (MEASURED_PEAKS.json)"
+            flops *= 6  # six split products per contraction
         else:
             peak = pk.get("bf16_tflops_sustained", 1748.4) * TF32_OVER_BF16
             bound = "tensor"
@@ -429,14 +435,14 @@ def run_gpu(args):
         cpu.pop("t_iter_s", None)
 
     if rank == 0:
-        dtype = "f64" if prec == fd.FD_F64 else "f64+tf32x3"
+        dtype = {fd.FD_F64: "f64", fd.FD_TF32X3: "f64+tf32x3", fd.FD_BF16X6: "f64+bf16x6"}[prec]
         if mv == fd.MV_DF64:
             dtype += " (matvec df64)"
         out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": dtype, "data": "synthetic",
                "config": {"workload": describe(args.workload, w, nrhs), "nrhs_per_gpu": nrhs,
-                          "fd_precision": "f64" if prec == fd.FD_F64 else "tf32x3",
+                          "fd_precision": {fd.FD_F64: "f64", fd.FD_TF32X3: "tf32x3", fd.FD_BF16X6: "bf16x6"}[prec],
                           "matvec": (("double-float (FP32 pairs, 48-bit significand) %s in the iterations; "
                                       "true residual in FP64") % ("CSR SpMV (%d nonzeros)" % int(P.flops_matvec / 2)
                                                                   if mapped else "banded Kronecker products"))

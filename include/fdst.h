@@ -49,7 +49,11 @@ typedef enum {
 } fdst_status;
 
 enum { FDST_TH = 0, FDST_RT = 1 };                          /* discretization (Sec. 2.2) */
-enum { FDST_FD_F64 = 0, FDST_FD_TF32X3 = 1, FDST_FD_BF16X6 = 2 }; /* FD contraction precision */
+/* FD contraction arithmetic: FP64 (DFMA); split-TF32 (each operand = TF32 hi +
+ * lo, products hi*hi + hi*lo + lo*hi on tcgen05); split-BF16 (each operand =
+ * three bf16 pieces, the six products with piece indices i + j <= 2). Both
+ * split forms accumulate in FP32 and keep FP32 intermediates. */
+enum { FDST_FD_F64 = 0, FDST_FD_TF32X3 = 1, FDST_FD_BF16X6 = 2 };
 enum { FDST_GEOM_IDENTITY = 0, FDST_GEOM_SINE_BUMP = 1 };   /* geometry map G */
 enum { FDST_VARIANT_PD = 0, FDST_VARIANT_PD_GEO = 1 };      /* P_D (Sec. 5) or P_D^G (Sec. 6) */
 /* Matvec arithmetic: FP64 (DFMA), or double-float (each value an unevaluated

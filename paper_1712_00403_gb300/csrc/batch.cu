@@ -246,6 +246,7 @@ static fdst_status batch_apply(fdst_batch b, cudaStream_t st, int ring) {
     if (S.count == 0) continue;
     if (b->tc) {
       TcGroup g;
+      g.split = b->hs[0]->desc.fd_precision == FDST_FD_BF16X6 ? 1 : 0;
       g.table = static_cast<const TcProb *>(S.tab);
       g.nprob = S.count;
       g.maxR = S.maxR;
@@ -337,6 +338,7 @@ static fdst_status batch_autotune(fdst_batch b) {
     for (auto &S : b->steps) {
       if (S.count == 0) continue;
       TcGroup g;
+      g.split = b->hs[0]->desc.fd_precision == FDST_FD_BF16X6 ? 1 : 0;
       g.table = static_cast<const TcProb *>(S.tab);
       g.nprob = S.count;
       g.maxR = S.maxR;
@@ -619,7 +621,7 @@ fdst_status fdst_batch_create(const fdst_handle *handles, int n, int autotune, f
     const bool tc = h->desc.fd_precision != FDST_FD_F64, df = h->desc.matvec_precision == FDST_MV_DF64;
     if (h->mapped) { fdst_batch_destroy(b); set_error("fdst_batch_create: identity-geometry handles only"); return FDST_NOT_SUPPORTED; }
     if (i == 0) { b->tc = tc; b->df = df; }
-    if (tc != b->tc || df != b->df) {
+    if (tc != b->tc || df != b->df || h->desc.fd_precision != handles[0]->desc.fd_precision) {
       fdst_batch_destroy(b);
       set_error("fdst_batch_create: all handles must share the FD and matvec precision");
       return FDST_INVALID_ARGUMENT;

@@ -28,7 +28,7 @@ struct FdChain {
   int nsteps = 0;
   int div_step = -1;
   const double *B[6] = {};
-  const float *Bt[6] = {};     // split-TF32 operand of the same step (pre-split, padded)
+  const uint8_t *Bt[6] = {};   // tensor-core operand image of the same step (pre-split, padded)
   std::vector<double> Bh[6];   // host copy of B (K x N row-major) for the packing
   int R[6] = {}, K[6] = {}, N[6] = {};
   double *lam_row = nullptr, *lam_col = nullptr;

@@ -413,16 +413,18 @@ static fdst_status build_matvec(fdst_ctx *h) {
 // ------------------------------------------------------------------ split-TF32 operands
 
 // Packs every FD step's factor into the tensor-core operand image (TF32
-// hi/lo split, swizzled per stage) and allocates the FP32 intermediates.
+// hi/lo or three bf16 pieces, swizzled per stage) and allocates the FP32
+// intermediates.
 static fdst_status tc_prepare(fdst_ctx *h) {
-  std::map<const double *, const float *> cache;
+  const int split = h->desc.fd_precision == FDST_FD_BF16X6 ? 1 : 0;
+  std::map<const double *, const uint8_t *> cache;
   for (auto &c : h->chains)
     for (int j = 0; j < c.nsteps; ++j) {
       auto it = cache.find(c.B[j]);
       if (it != cache.end()) { c.Bt[j] = it->second; continue; }
-      std::vector<float> packed;
-      tc_pack(c.Bh[j].data(), c.K[j], c.N[j], packed);
-      float *d = nullptr;
+      std::vector<uint8_t> packed;
+      tc_pack(c.Bh[j].data(), c.K[j], c.N[j], split, packed);
+      uint8_t *d = nullptr;
       TRY(upload(h, &d, packed));
       c.Bt[j] = d;
       cache[c.B[j]] = d;
@@ -465,6 +467,7 @@ fdst_status run_apply(fdst_ctx *h, const double *r, double *s, int nrhs, const i
   for (int j = 0; j < maxsteps; ++j) {
     if (tc) {
       TcGroup g;
+      g.split = h->desc.fd_precision == FDST_FD_BF16X6 ? 1 : 0;
       for (size_t ci = 0; ci < h->chains.size(); ++ci) {
         const FdChain &c = h->chains[ci];
         if (j >= c.nsteps) continue;
@@ -703,9 +706,10 @@ fdst_status fdst_setup(const fdst_desc *desc, fdst_handle *out) {
     set_error("unknown matvec precision");
     return FDST_INVALID_ARGUMENT;
   }
-  if (desc->fd_precision != FDST_FD_F64 && desc->fd_precision != FDST_FD_TF32X3) {
-    set_error("unknown or unsupported FD precision");
-    return FDST_NOT_SUPPORTED;
+  if (desc->fd_precision != FDST_FD_F64 && desc->fd_precision != FDST_FD_TF32X3 &&
+      desc->fd_precision != FDST_FD_BF16X6) {
+    set_error("unknown FD precision");
+    return FDST_INVALID_ARGUMENT;
   }
   std::unique_ptr<fdst_ctx> h(new fdst_ctx());
   h->desc = *desc;
@@ -728,7 +732,7 @@ fdst_status fdst_setup(const fdst_desc *desc, fdst_handle *out) {
   if (desc->geometry == FDST_GEOM_SINE_BUMP && (st = build_mapped_pre(hp)) != FDST_OK) return fail(st);
   if ((st = build_fd(hp)) != FDST_OK) return fail(st);
   if (hp->mapped && (st = build_mapped_post(hp)) != FDST_OK) return fail(st);
-  if (desc->fd_precision == FDST_FD_TF32X3) {
+  if (desc->fd_precision != FDST_FD_F64) {
     if ((st = tc_prepare(hp)) != FDST_OK) return fail(st);
   }
   if (!hp->mapped && (st = build_matvec(hp)) != FDST_OK) return fail(st);

@@ -61,19 +61,50 @@ constexpr int kTmaWarp = 17;
 constexpr int kThreads = 576;
 constexpr int kAHalfBytes = kM * kKC * 4;   // 128 rows x 32 FP32 (hi or lo half of a stage's A)
 constexpr int kNTMax = 256;
-constexpr int kAStageBytes = 2 * 4 * kM * 32;   // hi/lo x 4 k-steps x 128 rows x 32 B
+// A part of a stage: split-TF32: the landed FP32 tile turned into hi in place
+// plus a lo copy (2 x 16 KB); split-BF16: the landed tile plus three bf16
+// planes of 2 k-steps of 16 (16 KB + 3 x 8 KB). B part: bytes per K element
+// and column: 8 (two TF32 parts) or 6 (three bf16 parts).
+template <int SPLIT> struct SplitTraits;
+template <> struct SplitTraits<0> {
+  static constexpr int kAStage = 2 * 4 * kM * 32, kBPE = 8, kKStep = 8;
+};
+template <> struct SplitTraits<1> {
+  static constexpr int kAStage = 4 * kM * 32 + 3 * 2 * kM * 32, kBPE = 6, kKStep = 16;
+};
 constexpr int kSmemBudget = 227 * 1024;
 constexpr unsigned long long kWaitNs = 2000000000ull;
 }  // namespace
 
 int tc_npad(int N) { return (N + 15) & ~15; }
-int tc_kpad(int K) { return (K + 7) & ~7; }
+int tc_kpad(int K, int split) { return split ? (K + 15) & ~15 : (K + 7) & ~7; }
 static int tile_nt(int npad, int t) {
   int rest = npad - t * kNTMax;
   return rest < kNTMax ? rest : kNTMax;
 }
 
-size_t tc_packed_floats(int K, int N) { return 2 * (size_t)tc_kpad(K) * tc_npad(N); }
+size_t tc_packed_bytes(int K, int N, int split) { return (split ? 6 : 8) * (size_t)tc_kpad(K, split) * tc_npad(N); }
+
+// Three bf16 pieces of a float by truncation: x = b0 + b1 + b2 up to the last
+// 8 bits of x's 24-bit significand (each difference is exact in FP32).
+static inline void bf16_split3_host(float x, uint16_t &b0, uint16_t &b1, uint16_t &b2) {
+  uint32_t u, v;
+  std::memcpy(&u, &x, 4);
+  u &= 0xFFFF0000u;
+  float h;
+  std::memcpy(&h, &u, 4);
+  const float r1 = x - h;
+  std::memcpy(&v, &r1, 4);
+  v &= 0xFFFF0000u;
+  float h1;
+  std::memcpy(&h1, &v, 4);
+  const float r2 = r1 - h1;
+  uint32_t w;
+  std::memcpy(&w, &r2, 4);
+  b0 = (uint16_t)(u >> 16);
+  b1 = (uint16_t)(v >> 16);
+  b2 = (uint16_t)(w >> 16);
+}
 
 static inline float tf32_trunc(float x) {
   uint32_t u;
@@ -85,30 +116,41 @@ static inline float tf32_trunc(float x) {
 
 // Packs B (K x N row-major, FP64) into the per-stage shared-memory image the
 // kernel copies: for column tile t, stage s (k in [32 s, 32 s + 32)):
-// [part hi|lo][k-step j][row n of the tile][8 TF32 values, 16-byte chunks
-// swizzled by bit 2 of n (SWIZZLE_32B)].
-void tc_pack(const double *B, int K, int N, std::vector<float> &out) {
-  const int kp = tc_kpad(K), np = tc_npad(N);
-  out.assign(2 * (size_t)kp * np, 0.0f);
+// [part][k-step j][row n of the tile][one k-step of values, 16-byte chunks
+// swizzled by bit 2 of n (SWIZZLE_32B)]; split-TF32: parts hi|lo, k-steps of
+// 8 TF32 values; split-BF16: parts b0|b1|b2, k-steps of 16 bf16 values.
+void tc_pack(const double *B, int K, int N, int split, std::vector<uint8_t> &out) {
+  const int kp = tc_kpad(K, split), np = tc_npad(N), bpe = split ? 6 : 8, kst = split ? 16 : 8;
+  const int nparts = split ? 3 : 2;
+  out.assign((size_t)bpe * kp * np, 0);
   size_t tile_base = 0;
   for (int t = 0; t * kNTMax < np; ++t) {
     const int NT = tile_nt(np, t), n0 = t * kNTMax;
     for (int k0 = 0; k0 < kp; k0 += kKC) {
-      const int ks = (kp - k0) / 8 < 4 ? (kp - k0) / 8 : 4;
-      const size_t sb = tile_base + 2 * (size_t)NT * k0;
-      for (int part = 0; part < 2; ++part)
-        for (int j = 0; j < ks; ++j)
-          for (int nn = 0; nn < NT; ++nn)
-            for (int e = 0; e < 8; ++e) {
-              const int k = k0 + 8 * j + e, n = n0 + nn;
-              const double v = (k < K && n < N) ? B[(size_t)k * N + n] : 0.0;
-              const float hi = tf32_trunc((float)v);
-              const float lo = (float)(v - (double)hi);
-              const int c = (e >> 2) ^ ((nn >> 2) & 1), w = e & 3;
-              out[sb + ((size_t)(part * ks + j) * NT + nn) * 8 + c * 4 + w] = part ? lo : hi;
+      const int ks = (kp - k0) / kst < kKC / kst ? (kp - k0) / kst : kKC / kst;
+      const size_t sb = tile_base + (size_t)bpe * NT * k0;
+      for (int j = 0; j < ks; ++j)
+        for (int nn = 0; nn < NT; ++nn)
+          for (int e = 0; e < kst; ++e) {
+            const int k = k0 + kst * j + e, n = n0 + nn;
+            const double v = (k < K && n < N) ? B[(size_t)k * N + n] : 0.0;
+            const int ebytes = split ? 2 : 4, per_chunk = 16 / ebytes;
+            const int c = (e / per_chunk) ^ ((nn >> 2) & 1), w = e % per_chunk;
+            for (int part = 0; part < nparts; ++part) {
+              uint8_t *dst = out.data() + sb + ((size_t)(part * ks + j) * NT + nn) * 32 + c * 16 + w * ebytes;
+              if (split) {
+                uint16_t b[3];
+                bf16_split3_host((float)v, b[0], b[1], b[2]);
+                std::memcpy(dst, &b[part], 2);
+              } else {
+                const float hi = tf32_trunc((float)v);
+                const float lo = (float)(v - (double)hi);
+                std::memcpy(dst, part ? &lo : &hi, 4);
+              }
             }
+          }
     }
-    tile_base += 2 * (size_t)NT * kp;
+    tile_base += (size_t)bpe * NT * kp;
   }
 }
 
@@ -260,6 +302,37 @@ __device__ __forceinline__ uint64_t sdesc_sw128(const void *p) {
   return d;
 }
 
+// Instruction descriptor: D f32, A/B bf16 (kind::f16), K-major both, N = nt, M = 128.
+__device__ __forceinline__ uint32_t idesc_bf16(int nt) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(nt >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+// Three bf16 pieces (truncation) of each of 8 floats, packed per piece.
+__device__ __forceinline__ void bf16_split3x8(const float (&x)[8], uint4 &p0, uint4 &p1, uint4 &p2) {
+  uint32_t h[8], m[8], l[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const uint32_t u = __float_as_uint(x[e]) & 0xFFFF0000u;
+    const float r1 = x[e] - __uint_as_float(u);
+    const uint32_t v = __float_as_uint(r1) & 0xFFFF0000u;
+    const float r2 = r1 - __uint_as_float(v);
+    h[e] = u >> 16;
+    m[e] = v >> 16;
+    l[e] = __float_as_uint(r2) >> 16;
+  }
+  p0 = make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
+  p1 = make_uint4(m[0] | (m[1] << 16), m[2] | (m[3] << 16), m[4] | (m[5] << 16), m[6] | (m[7] << 16));
+  p2 = make_uint4(l[0] | (l[1] << 16), l[2] | (l[3] << 16), l[4] | (l[5] << 16), l[6] | (l[7] << 16));
+}
+
 // Instruction descriptor: D f32, A/B tf32, K-major both, N = nt, M = 128.
 __device__ __forceinline__ uint32_t idesc_tf32(int nt) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(nt >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
@@ -276,6 +349,7 @@ struct TileInfo {
 
 __device__ __forceinline__ const TcProb &prob_of(const TcGroup &g, int i) { return g.table ? g.table[i] : g.p[i]; }
 
+template <int SPLIT>
 __device__ __forceinline__ TileInfo decode_tile(const TcGroup &g, int T, int nrt, int ntn, const int *done) {
   TileInfo t;
   const int rt = T % nrt;
@@ -290,7 +364,7 @@ __device__ __forceinline__ TileInfo decode_tile(const TcGroup &g, int T, int nrt
   t.n0 = nt * kNTMax;
   t.valid = t.r0 < P.R && t.n0 < npad && !(done && done[t.rhs]) && !(P.done_flag && *P.done_flag);
   t.NT = npad - t.n0 < kNTMax ? npad - t.n0 : kNTMax;
-  t.kp = (P.K + 7) & ~7;
+  t.kp = SPLIT ? (P.K + 15) & ~15 : (P.K + 7) & ~7;
   t.nstages = (t.kp + kKC - 1) / kKC;
   return t;
 }
@@ -298,7 +372,7 @@ __device__ __forceinline__ TileInfo decode_tile(const TcGroup &g, int T, int nrt
 // Next valid tile index after T (T = -1: the first of this CTA); total if none.
 __device__ __forceinline__ int next_tile(const TcGroup &g, int T, int total, int nrt, int ntn, const int *done) {
   T = T < 0 ? (int)blockIdx.x : T + (int)gridDim.x;
-  while (T < total && !decode_tile(g, T, nrt, ntn, done).valid) T += gridDim.x;
+  while (T < total && !decode_tile<0>(g, T, nrt, ntn, done).valid) T += gridDim.x;
   return T;
 }
 
@@ -307,12 +381,14 @@ struct Cursor {
   TileInfo t;
 };
 
+template <int SPLIT>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(TcGroup g, int nrhs, const int *done, int *err, int nrt, int ntn, int nstage_ring, int ntc,
               int ntmax_smem) {
+  using TR = SplitTraits<SPLIT>;
   const int total = nrt * ntn * g.nprob * nrhs;
   // ntmax_smem: widest column tile of the launch (B region); ntc: TMEM columns per accumulator
-  const int stage_bytes = kAStageBytes + 2 * 4 * ntmax_smem * 32;
+  const int stage_bytes = TR::kAStage + TR::kBPE * ntmax_smem * kKC;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + nstage_ring * stage_bytes);
@@ -348,20 +424,19 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool ok = true;
       for (int T = next_tile(g, -1, total, nrt, ntn, done); ok && T < total;
            T = next_tile(g, T, total, nrt, ntn, done)) {
-        const TileInfo t = decode_tile(g, T, nrt, ntn, done);
+        const TileInfo t = decode_tile<SPLIT>(g, T, nrt, ntn, done);
         const TcProb &P = prob_of(g, t.prob);
-        const size_t btile = 2 * (size_t)kNTMax * t.kp * (size_t)(t.n0 / kNTMax);
+        const size_t btile = (size_t)TR::kBPE * kNTMax * t.kp * (size_t)(t.n0 / kNTMax);
         for (int s = 0; s < t.nstages; ++s, ++q) {
           const int slot = q % nstage_ring, u = q / nstage_ring;
           if (u > 0 && !mbar_wait(&empty[slot], (u - 1) & 1, abort)) { ok = false; break; }
           uint8_t *sA = smem + slot * stage_bytes;
-          uint8_t *sB = sA + kAStageBytes;
+          uint8_t *sB = sA + TR::kAStage;
           const int k0 = s * kKC;
-          const int ks = (t.kp - k0) / 8 < 4 ? (t.kp - k0) / 8 : 4;
-          const uint32_t bbytes = 2u * ks * t.NT * 32u;
+          const uint32_t bbytes = (uint32_t)TR::kBPE * t.NT * (t.kp - k0 < kKC ? t.kp - k0 : kKC);
           mbar_expect_tx(&landed[slot], kAHalfBytes + bbytes);
           tma_load_3d(sA, P.tmap, k0, t.r0, t.rhs, &landed[slot]);
-          bulk_g2s(sB, P.Bt + btile + 2 * (size_t)t.NT * k0, bbytes, &landed[slot]);
+          bulk_g2s(sB, P.Bt + btile + (size_t)TR::kBPE * t.NT * k0, bbytes, &landed[slot]);
           last_par[slot] = u & 1;
         }
       }
@@ -378,24 +453,44 @@ __global__ void __launch_bounds__(kThreads, 1)
     bool ok = true;
     for (int T = next_tile(g, -1, total, nrt, ntn, done); ok && T < total;
          T = next_tile(g, T, total, nrt, ntn, done)) {
-      const TileInfo t = decode_tile(g, T, nrt, ntn, done);
+      const TileInfo t = decode_tile<SPLIT>(g, T, nrt, ntn, done);
       for (int s = 0; s < t.nstages; ++s, ++q) {
         const int slot = q % nstage_ring;
         if (!mbar_wait(&landed[slot], (q / nstage_ring) & 1, abort)) { ok = false; break; }
         uint8_t *sA = smem + slot * stage_bytes;
-        const int k0 = s * kKC;
-        const int ks = (t.kp - k0) / 8 < 4 ? (t.kp - k0) / 8 : 4;
-        for (int c = tid; c < kAHalfBytes / 16; c += kConv) {
-          float4 *ph = reinterpret_cast<float4 *>(sA + c * 16);
-          const float4 a = *ph;
-          float4 hi, lo;
-          hi.x = __uint_as_float(__float_as_uint(a.x) & 0xFFFFE000u);
-          hi.y = __uint_as_float(__float_as_uint(a.y) & 0xFFFFE000u);
-          hi.z = __uint_as_float(__float_as_uint(a.z) & 0xFFFFE000u);
-          hi.w = __uint_as_float(__float_as_uint(a.w) & 0xFFFFE000u);
-          lo = make_float4(a.x - hi.x, a.y - hi.y, a.z - hi.z, a.w - hi.w);
-          *ph = hi;
-          *reinterpret_cast<float4 *>(sA + kAHalfBytes + c * 16) = lo;
+        if (SPLIT == 0) {
+          for (int c = tid; c < kAHalfBytes / 16; c += kConv) {
+            float4 *ph = reinterpret_cast<float4 *>(sA + c * 16);
+            const float4 a = *ph;
+            float4 hi, lo;
+            hi.x = __uint_as_float(__float_as_uint(a.x) & 0xFFFFE000u);
+            hi.y = __uint_as_float(__float_as_uint(a.y) & 0xFFFFE000u);
+            hi.z = __uint_as_float(__float_as_uint(a.z) & 0xFFFFE000u);
+            hi.w = __uint_as_float(__float_as_uint(a.w) & 0xFFFFE000u);
+            lo = make_float4(a.x - hi.x, a.y - hi.y, a.z - hi.z, a.w - hi.w);
+            *ph = hi;
+            *reinterpret_cast<float4 *>(sA + kAHalfBytes + c * 16) = lo;
+          }
+        } else {
+          // 128 rows x 4 groups of 8 k: read the landed FP32 (SWIZZLE_128B: 16-byte chunk
+          // c of row r at (r/8)*1024 + (r%8)*128 + ((c ^ r%8) * 16)), write the three bf16
+          // pieces into their planes (k-steps of 16, SWIZZLE_32B: chunk c of row r at
+          // r*32 + ((c ^ (r/4)%2) * 16))
+          for (int it = tid; it < kM * 4; it += kConv) {
+            const int r = it >> 2, kq = it & 3;
+            const uint8_t *row = sA + (r >> 3) * 1024 + (r & 7) * 128;
+            const float4 x0 = *reinterpret_cast<const float4 *>(row + (((2 * kq) ^ (r & 7)) << 4));
+            const float4 x1 = *reinterpret_cast<const float4 *>(row + (((2 * kq + 1) ^ (r & 7)) << 4));
+            const float xs[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+            uint4 p0, p1, p2;
+            bf16_split3x8(xs, p0, p1, p2);
+            const int j = kq >> 1, c = kq & 1;
+            const int off = j * (kM * 32) + r * 32 + ((c ^ ((r >> 2) & 1)) << 4);
+            uint8_t *planes = sA + kAHalfBytes;
+            *reinterpret_cast<uint4 *>(planes + off) = p0;
+            *reinterpret_cast<uint4 *>(planes + 2 * kM * 32 + off) = p1;
+            *reinterpret_cast<uint4 *>(planes + 4 * kM * 32 + off) = p2;
+          }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
@@ -410,7 +505,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int quarter = warp & 3, half = (warp - kEpiWarp0) >> 2;
     int v = 0;
     for (int T = next_tile(g, -1, total, nrt, ntn, done); T < total; T = next_tile(g, T, total, nrt, ntn, done)) {
-      const TileInfo t = decode_tile(g, T, nrt, ntn, done);
+      const TileInfo t = decode_tile<SPLIT>(g, T, nrt, ntn, done);
       const TcProb &P = prob_of(g, t.prob);
       const int acc = v & 1;
       if (!mbar_wait(&tfull[acc], (v >> 1) & 1, abort)) break;
@@ -487,28 +582,46 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool ok = true;
       for (int T = next_tile(g, -1, total, nrt, ntn, done); ok && T < total;
            T = next_tile(g, T, total, nrt, ntn, done)) {
-        const TileInfo t = decode_tile(g, T, nrt, ntn, done);
+        const TileInfo t = decode_tile<SPLIT>(g, T, nrt, ntn, done);
         const int acc = v & 1, u = v >> 1;
         if (u > 0 && !mbar_wait(&tempty[acc], (u - 1) & 1, abort)) { ok = false; break; }
         tc_fence_after();
         const uint32_t d = tmem + (uint32_t)(acc * ntc);
-        const uint32_t idesc = idesc_tf32(t.NT);
+        const uint32_t idesc = SPLIT ? idesc_bf16(t.NT) : idesc_tf32(t.NT);
         for (int s = 0; s < t.nstages; ++s) {
           const int slot = q % nstage_ring;
           if (!mbar_wait(&split[slot], (q / nstage_ring) & 1, abort)) { ok = false; break; }
           tc_fence_after();
           uint8_t *sA = smem + slot * stage_bytes;
-          uint8_t *sB = sA + kAStageBytes;
+          uint8_t *sB = sA + TR::kAStage;
           const int k0 = s * kKC;
-          const int ks = (t.kp - k0) / 8 < 4 ? (t.kp - k0) / 8 : 4;
-          for (int j = 0; j < ks; ++j) {
-            const uint64_t ah = sdesc_sw128(sA + j * 32);
-            const uint64_t al = sdesc_sw128(sA + kAHalfBytes + j * 32);
-            const uint64_t bh = sdesc_sw32(sB + (size_t)j * t.NT * 32);
-            const uint64_t bl = sdesc_sw32(sB + (size_t)(ks + j) * t.NT * 32);
-            mma_tf32(d, ah, bh, idesc, (s > 0 || j > 0) ? 1u : 0u);
-            mma_tf32(d, ah, bl, idesc, 1u);
-            mma_tf32(d, al, bh, idesc, 1u);
+          const int ks = (t.kp - k0) / TR::kKStep < kKC / TR::kKStep ? (t.kp - k0) / TR::kKStep : kKC / TR::kKStep;
+          if (SPLIT == 0) {
+            for (int j = 0; j < ks; ++j) {
+              const uint64_t ah = sdesc_sw128(sA + j * 32);
+              const uint64_t al = sdesc_sw128(sA + kAHalfBytes + j * 32);
+              const uint64_t bh = sdesc_sw32(sB + (size_t)j * t.NT * 32);
+              const uint64_t bl = sdesc_sw32(sB + (size_t)(ks + j) * t.NT * 32);
+              mma_tf32(d, ah, bh, idesc, (s > 0 || j > 0) ? 1u : 0u);
+              mma_tf32(d, ah, bl, idesc, 1u);
+              mma_tf32(d, al, bh, idesc, 1u);
+            }
+          } else {
+            // 6 leading products of (a0 + a1 + a2)(b0 + b1 + b2): pieces i + j <= 2
+            for (int j = 0; j < ks; ++j) {
+              uint64_t a[3], b[3];
+#pragma unroll
+              for (int p = 0; p < 3; ++p) {
+                a[p] = sdesc_sw32(sA + kAHalfBytes + p * 2 * kM * 32 + j * kM * 32);
+                b[p] = sdesc_sw32(sB + (size_t)(p * ks + j) * t.NT * 32);
+              }
+              mma_bf16(d, a[0], b[0], idesc, (s > 0 || j > 0) ? 1u : 0u);
+              mma_bf16(d, a[0], b[1], idesc, 1u);
+              mma_bf16(d, a[1], b[0], idesc, 1u);
+              mma_bf16(d, a[0], b[2], idesc, 1u);
+              mma_bf16(d, a[1], b[1], idesc, 1u);
+              mma_bf16(d, a[2], b[0], idesc, 1u);
+            }
           }
           mma_commit(&empty[slot]);
           last_slot = slot;
@@ -614,7 +727,8 @@ int tc_max_ring(const TcGroup &g) {
   tc_dims(g, maxR, maxN);
   const int npad = tc_npad(maxN);
   const int nt = npad < kNTMax ? npad : kNTMax;
-  const int stage_bytes = kAStageBytes + 2 * 4 * nt * 32;
+  const int stage_bytes = g.split ? SplitTraits<1>::kAStage + SplitTraits<1>::kBPE * nt * kKC
+                                  : SplitTraits<0>::kAStage + SplitTraits<0>::kBPE * nt * kKC;
   int nring = (kSmemBudget - 2048) / stage_bytes;
   return nring > 4 ? 4 : nring;
 }
@@ -626,7 +740,8 @@ fdst_status launch_gemm_tc(const TcGroup &g, int nrhs, const int *done, cudaStre
   const int ntn = (npad + kNTMax - 1) / kNTMax;
   const int nt = npad < kNTMax ? npad : kNTMax;
   const int ntc = nt <= 32 ? 32 : nt <= 64 ? 64 : nt <= 128 ? 128 : 256;   // TMEM columns per accumulator
-  const int stage_bytes = kAStageBytes + 2 * 4 * nt * 32;
+  const int stage_bytes = g.split ? SplitTraits<1>::kAStage + SplitTraits<1>::kBPE * nt * kKC
+                                  : SplitTraits<0>::kAStage + SplitTraits<0>::kBPE * nt * kKC;
   int nring = tc_max_ring(g);
   if (ring > 0 && ring < nring) nring = ring;
   if (nring < 2) {
@@ -634,7 +749,7 @@ fdst_status launch_gemm_tc(const TcGroup &g, int nrhs, const int *done, cudaStre
     return FDST_NOT_SUPPORTED;
   }
   const int smem = nring * stage_bytes + 1024 + 1024;
-  static int configured = 0, nsm = 0;
+  static int configured[2] = {0, 0}, nsm = 0;
   static std::mutex init_mutex;
   std::lock_guard<std::mutex> lock(init_mutex);
   if (!g_err_flag) {
@@ -649,12 +764,15 @@ fdst_status launch_gemm_tc(const TcGroup &g, int nrhs, const int *done, cudaStre
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (nsm < 1) nsm = 1;
   }
-  if (smem > configured) {
-    if (cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
+  const int sp = g.split ? 1 : 0;
+  if (smem > configured[sp]) {
+    const cudaError_t e = sp ? cudaFuncSetAttribute(k_gemm_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
+                             : cudaFuncSetAttribute(k_gemm_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) {
       set_error("cudaFuncSetAttribute(k_gemm_tc) failed");
       return FDST_CUDA_ERROR;
     }
-    configured = smem;
+    configured[sp] = smem;
   }
   if (g.convert) {
     long long blocks = ((long long)maxR * 64 + 255) / 256;
@@ -667,7 +785,10 @@ fdst_status launch_gemm_tc(const TcGroup &g, int nrhs, const int *done, cudaStre
   const long long total = (long long)nrt * ntn * g.nprob * nrhs;
   const int grid = total < nsm ? (int)total : nsm;
   count_launch(1);
-  k_gemm_tc<<<grid, kThreads, smem, s>>>(g, nrhs, done, g_err_flag, nrt, ntn, nring, ntc, nt);
+  if (sp)
+    k_gemm_tc<1><<<grid, kThreads, smem, s>>>(g, nrhs, done, g_err_flag, nrt, ntn, nring, ntc, nt);
+  else
+    k_gemm_tc<0><<<grid, kThreads, smem, s>>>(g, nrhs, done, g_err_flag, nrt, ntn, nring, ntc, nt);
   return FDST_OK;
 }
 

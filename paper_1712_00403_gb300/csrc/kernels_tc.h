@@ -25,7 +25,7 @@ struct TcProb {
   const void *tmap = nullptr;
   double *C64 = nullptr;
   float *C32 = nullptr;
-  const float *Bt = nullptr;
+  const uint8_t *Bt = nullptr;      // B image (tc_pack) of the group's split mode
   int64_t a_rhs_stride = 0, a64_rhs_stride = 0, c_rhs_stride = 0;
   int64_t c_cs = 0;
   int R = 0, K = 0, N = 0;
@@ -41,6 +41,7 @@ struct TcGroup {
   const TcProb *table = nullptr;
   int maxR = 0, maxN = 0;           // with a table: largest R and N among its problems
   int convert = 0;                  // 1: convert A64 into A32 first (problems with A64 set)
+  int split = 0;                    // 0: split-TF32 (hi/lo, 3 products); 1: split-BF16 (3 pieces, 6 products)
 };
 // Layout of one contraction step of a chain (rows R, contracted size K,
 // out_nv = size of the next contracted index): lda = K rounded up to 8 (TMA
@@ -71,9 +72,10 @@ fdst_status launch_gemm_tc(const TcGroup &g, int nrhs, const int *done, cudaStre
 int tc_max_ring(const TcGroup &g);
 
 // Host packing of B (K x N row-major FP64) into the kernel's per-stage
-// shared-memory image (TF32 hi/lo, SWIZZLE_32B K-major); size in floats.
-size_t tc_packed_floats(int K, int N);
-void tc_pack(const double *B, int K, int N, std::vector<float> &out);
+// shared-memory image (SWIZZLE_32B K-major; TF32 hi/lo or three bf16 pieces
+// by split); size in bytes.
+size_t tc_packed_bytes(int K, int N, int split);
+void tc_pack(const double *B, int K, int N, int split, std::vector<uint8_t> &out);
 // 1 when a bounded wait inside the tensor-core kernel expired since start.
 fdst_status tc_error_flag(int *value);
 

@@ -52,7 +52,7 @@ def test_pdg_apply_matches_oracle(spec):
     pdg = geo.PDG(S, geo.Grid(S))
     r_h = synth.random_vector(7, S.n_total)
     ref = pdg.apply(r_h)
-    for prec, tol in ((fd.FD_F64, 1e-11), (fd.FD_TF32X3, 1e-5)):
+    for prec, tol in ((fd.FD_F64, 1e-11), (fd.FD_TF32X3, 1e-5), (fd.FD_BF16X6, 1e-5)):
         P = _gpu(spec, fd_precision=prec)
         r = torch.tensor(r_h, device="cuda")
         s = torch.empty_like(r)
@@ -71,7 +71,7 @@ def test_pdg_minres_matches_oracle():
     b_h = synth.rhs(300, S.block_sizes)
     _, io = minres.minres(lambda v: geo.matvec(S, G, v), b_h, pdg.apply, tol=1e-8, maxit=600, true_check=True)
     its = {}
-    for prec in (fd.FD_F64, fd.FD_TF32X3):
+    for prec in (fd.FD_F64, fd.FD_TF32X3, fd.FD_BF16X6):
         P = _gpu(spec, fd_precision=prec)
         b = torch.tensor(b_h, device="cuda")
         x = torch.zeros_like(b)
@@ -81,6 +81,7 @@ def test_pdg_minres_matches_oracle():
     # FP64: the oracle's recurrence; split-TF32: at most 2 iterations more than FP64
     assert abs(its[fd.FD_F64] - io["iters"]) <= 1, (its, io)
     assert its[fd.FD_TF32X3] <= its[fd.FD_F64] + 2, its
+    assert its[fd.FD_BF16X6] <= its[fd.FD_F64] + 2, its
 
 
 def test_full_size_sampled_columns():

@@ -1,8 +1,11 @@
-"""Split-TF32 tcgen05 FD apply vs. the FP64 oracle, through the C ABI.
+"""Split-TF32 and split-BF16 tcgen05 FD applies vs. the FP64 oracle, through
+the C ABI.
 
-Bar: norm-wise relative error of every block <= 1e-5 (three TF32 products
-with FP32 accumulation and FP32 intermediates); P_D-MINRES with this apply
-reaches the true relative residual 1e-8 within 2 iterations of the FP64 run.
+Bar: norm-wise relative error of every block <= 1e-5 (split-TF32: three TF32
+products; split-BF16: three bf16 pieces per operand and the six leading
+products; FP32 accumulation and FP32 intermediates in both); P_D-MINRES with
+either apply reaches the true relative residual 1e-8 within 2 iterations of
+the FP64 run.
 """
 import numpy as np
 import pytest
@@ -31,10 +34,11 @@ def _ids(c):
     return f"{c['disc']}-d{c['dim']}-p{c['p']}-{'x'.join(map(str, c['n_el']))}"
 
 
+@pytest.mark.parametrize("split", ["tf32", "bf16"])
 @pytest.mark.parametrize("spec", CASES, ids=_ids)
-def test_tf32_apply_matches_oracle(spec):
+def test_tf32_apply_matches_oracle(spec, split):
     import paper_1712_00403_gb300 as fd
-    P = gpu_problem(spec, max_rhs=2, fd_precision=fd.FD_TF32X3)
+    P = gpu_problem(spec, max_rhs=2, fd_precision=fd.FD_TF32X3 if split == "tf32" else fd.FD_BF16X6)
     S = oracle_problem(spec)
     R = np.stack([synth.random_vector(500 + j, P.n_total) for j in range(2)])
     r = torch.tensor(R.reshape(-1), device="cuda")
@@ -48,10 +52,11 @@ def test_tf32_apply_matches_oracle(spec):
             assert rel(out[j, o0:o1], ref[o0:o1]) <= 1e-5
 
 
+@pytest.mark.parametrize("split", ["tf32", "bf16"])
 @pytest.mark.parametrize("spec", [problem_spec(3, 2, 6), problem_spec(2, 2, 16)], ids=_ids)
-def test_tf32_minres_within_two_iterations_of_f64(spec):
+def test_tf32_minres_within_two_iterations_of_f64(spec, split):
     import paper_1712_00403_gb300 as fd
-    P32 = gpu_problem(spec, max_rhs=2, fd_precision=fd.FD_TF32X3)
+    P32 = gpu_problem(spec, max_rhs=2, fd_precision=fd.FD_TF32X3 if split == "tf32" else fd.FD_BF16X6)
     P64 = gpu_problem(spec, max_rhs=2, fd_precision=fd.FD_F64)
     B = np.stack([synth.rhs(60 + j, P32.block_sizes) for j in range(2)])
     b = torch.tensor(B.reshape(-1), device="cuda")
