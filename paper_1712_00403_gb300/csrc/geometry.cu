@@ -463,31 +463,34 @@ __global__ void k_spmv_df(const int64_t *row_ptr, const int *col, const float2 *
       bool act[4];
 #pragma unroll
       for (int jj = 0; jj < 4; ++jj) act[jj] = jj < nj && !(done && done[j0 + jj]);
-      // two nonzeros per lane per pass: their loads are in flight together
+      // four nonzeros per lane per pass, 32 apart (consecutive lanes read consecutive
+      // nonzeros, so the gathers of x stay coalesced); their loads are in flight together
       int64_t k = a + lane;
-      for (; k + 32 < b; k += 64) {
-        const float2 v0 = val[k], v1 = val[k + 32];
-        const int c0 = col[k], c1 = col[k + 32];
-        float2 x0[4], x1[4];
+      for (; k + 96 < b; k += 128) {
+        float2 v[4];
+        int c[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          v[u] = val[k + 32 * u];
+          c[u] = col[k + 32 * u];
+        }
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj)
           if (act[jj]) {
-            x0[jj] = x[(int64_t)(j0 + jj) * stride + c0];
-            x1[jj] = x[(int64_t)(j0 + jj) * stride + c1];
-          }
+            const float2 *xr = x + (int64_t)(j0 + jj) * stride;
+            float2 xv[4];
 #pragma unroll
-        for (int jj = 0; jj < 4; ++jj)
-          if (act[jj]) {
-            df_fma_acc(v0, x0[jj], sh[jj], sl[jj]);
-            df_fma_acc(v1, x1[jj], sh[jj], sl[jj]);
+            for (int u = 0; u < 4; ++u) xv[u] = xr[c[u]];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) df_fma_acc(v[u], xv[u], sh[jj], sl[jj]);
           }
       }
-      if (k < b) {
-        const float2 v = val[k];
-        const int c = col[k];
+      for (; k < b; k += 32) {
+        const float2 vv = val[k];
+        const int cc = col[k];
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj)
-          if (act[jj]) df_fma_acc(v, x[(int64_t)(j0 + jj) * stride + c], sh[jj], sl[jj]);
+          if (act[jj]) df_fma_acc(vv, x[(int64_t)(j0 + jj) * stride + cc], sh[jj], sl[jj]);
       }
 #pragma unroll
       for (int jj = 0; jj < 4; ++jj) {
