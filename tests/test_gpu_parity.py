@@ -160,3 +160,34 @@ def test_minres_df64_matvec_matches_f64(spec):
     for a, c in zip(idd, iff):
         assert a["status"] == "OK" and a["true_rel_res"] <= 1e-8
         assert abs(a["iterations"] - c["iterations"]) <= 1
+
+
+@pytest.mark.parametrize("spec", [problem_spec(3, 2, 5), problem_spec(2, 3, (5, 9))], ids=_ids)
+def test_matvec_df64_six_rhs_matches_oracle(spec):
+    """Six right-hand sides through the double-float matvec: every right-hand
+    side within the FP64 bar, and a solve with six right-hand sides equals the
+    six solves done one at a time."""
+    import paper_1712_00403_gb300 as fd
+    P = gpu_problem(spec, max_rhs=6, matvec_precision=fd.MV_DF64)
+    S = oracle_problem(spec)
+    X = np.stack([synth.random_vector(720 + j, P.n_total) for j in range(6)])
+    x = torch.tensor(X.reshape(-1), device="cuda")
+    y = torch.empty_like(x)
+    P.matvec(x, y)
+    out = y.cpu().numpy().reshape(6, -1)
+    for j in range(6):
+        ref = stokes.matvec(S, X[j])
+        for o0, o1 in zip(P.block_offsets[:-1], P.block_offsets[1:]):
+            assert rel(out[j, o0:o1], ref[o0:o1]) <= 1e-12, j
+    B = np.stack([synth.rhs(90 + j, P.block_sizes) for j in range(6)])
+    b = torch.tensor(B.reshape(-1), device="cuda")
+    xs = torch.zeros_like(b)
+    many = P.solve(b, xs, tol=1e-8, maxit=500)
+    P1 = gpu_problem(spec, max_rhs=1, matvec_precision=fd.MV_DF64)
+    for j in range(6):
+        bj = torch.tensor(B[j], device="cuda")
+        xj = torch.zeros_like(bj)
+        one = P1.solve(bj, xj, tol=1e-8, maxit=500)[0]
+        assert many[j]["status"] == "OK" and many[j]["true_rel_res"] <= 1e-8
+        assert abs(many[j]["iterations"] - one["iterations"]) <= 1
+        assert rel(xs.cpu().numpy().reshape(6, -1)[j], xj.cpu().numpy()) <= 1e-7
