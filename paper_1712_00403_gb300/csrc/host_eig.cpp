@@ -31,26 +31,36 @@ bool cholesky(Mat &M) {
   return true;
 }
 
-// X <- L^{-1} X (forward substitution on every column), L lower triangular.
+// X <- L^{-1} X (forward substitution, row by row: contiguous row updates), L lower triangular.
 static void lower_solve(const Mat &L, Mat &X) {
-  const int n = L.rows;
-  for (int c = 0; c < X.cols; ++c)
-    for (int i = 0; i < n; ++i) {
-      double s = X(i, c);
-      for (int k = 0; k < i; ++k) s -= L(i, k) * X(k, c);
-      X(i, c) = s / L(i, i);
+  const int n = L.rows, m = X.cols;
+  for (int i = 0; i < n; ++i) {
+    double *xi = &X.a[(size_t)i * m];
+    for (int k = 0; k < i; ++k) {
+      const double l = L(i, k);
+      if (l == 0.0) continue;
+      const double *xk = &X.a[(size_t)k * m];
+      for (int c = 0; c < m; ++c) xi[c] -= l * xk[c];
     }
+    const double inv = 1.0 / L(i, i);
+    for (int c = 0; c < m; ++c) xi[c] *= inv;
+  }
 }
 
-// X <- L^{-T} X (back substitution with L^T).
+// X <- L^{-T} X (back substitution with L^T, row by row).
 static void upper_t_solve(const Mat &L, Mat &X) {
-  const int n = L.rows;
-  for (int c = 0; c < X.cols; ++c)
-    for (int i = n - 1; i >= 0; --i) {
-      double s = X(i, c);
-      for (int k = i + 1; k < n; ++k) s -= L(k, i) * X(k, c);
-      X(i, c) = s / L(i, i);
+  const int n = L.rows, m = X.cols;
+  for (int i = n - 1; i >= 0; --i) {
+    double *xi = &X.a[(size_t)i * m];
+    for (int k = i + 1; k < n; ++k) {
+      const double l = L(k, i);
+      if (l == 0.0) continue;
+      const double *xk = &X.a[(size_t)k * m];
+      for (int c = 0; c < m; ++c) xi[c] -= l * xk[c];
     }
+    const double inv = 1.0 / L(i, i);
+    for (int c = 0; c < m; ++c) xi[c] *= inv;
+  }
 }
 
 static Mat transpose(const Mat &A) {
@@ -150,8 +160,9 @@ static void tridiagonalize(Mat &A, std::vector<double> &d, std::vector<double> &
 }
 
 // Implicit QL iteration with Wilkinson shifts on the tridiagonal (d, e),
-// rotations accumulated into the columns of Z (eigenvalues in d).
-static bool tridiag_ql(std::vector<double> &d, std::vector<double> &e, Mat &Z) {
+// rotations accumulated into the rows of Zt (the transposed eigenvector
+// matrix, so that each rotation updates two contiguous rows; eigenvalues in d).
+static bool tridiag_ql(std::vector<double> &d, std::vector<double> &e, Mat &Zt) {
   const int n = (int)d.size();
   for (int i = 1; i < n; ++i) e[i - 1] = e[i];
   if (n > 0) e[n - 1] = 0.0;
@@ -186,10 +197,11 @@ static bool tridiag_ql(std::vector<double> &d, std::vector<double> &e, Mat &Z) {
         pp = s * r;
         d[i + 1] = g + pp;
         g = c * r - b;
-        for (int k = 0; k < Z.rows; ++k) {
-          const double zf = Z(k, i + 1);
-          Z(k, i + 1) = s * Z(k, i) + c * zf;
-          Z(k, i) = c * Z(k, i) - s * zf;
+        double *zi = &Zt.a[(size_t)i * Zt.cols], *zj = &Zt.a[(size_t)(i + 1) * Zt.cols];
+        for (int k = 0; k < Zt.cols; ++k) {
+          const double zf = zj[k];
+          zj[k] = s * zi[k] + c * zf;
+          zi[k] = c * zi[k] - s * zf;
         }
       }
       if (r == 0.0 && i >= l) continue;
@@ -221,8 +233,11 @@ bool gen_eig(const Mat &K, const Mat &M, std::vector<double> &lam, Mat &U) {
     // larger pencils: Householder tridiagonalization + implicit QL (about 4 n^3 flops
     // instead of about 20 n^3 for the Jacobi sweeps)
     std::vector<double> d, e;
-    tridiagonalize(Ct, d, e, V);
-    if (!tridiag_ql(d, e, V)) return false;
+    Mat Q;
+    tridiagonalize(Ct, d, e, Q);
+    Mat Vt = transpose(Q);
+    if (!tridiag_ql(d, e, Vt)) return false;
+    V = transpose(Vt);
     lam = d;
   }
   U = V;
