@@ -355,7 +355,7 @@ static fdst_status batch_autotune(fdst_batch b) {
     b->ms_apply = timed([&] { batch_apply(b, st, 0); });
   }
   float best = 1e30f;
-  for (int thr : {128, 256, 512}) {
+  for (int thr : {128, 256}) {
     float ms = timed([&] { batch_matvec(b, st, thr); });
     if (ms < best) { best = ms; b->threads = thr; }
   }

@@ -83,7 +83,7 @@ struct BandGroupDF {
   int nop = 0;
   const BandOpDF *table = nullptr;
   int64_t maxt = 0;
-  int threads = 256;
+  int threads = 128;                // at most 256
 };
 void launch_band_df(const BandGroupDF &g, int nrhs, const int *done, cudaStream_t s);
 // y2 = split(x) (double -> FP32 pair) and x = join(y2) over n entries per right-hand side.

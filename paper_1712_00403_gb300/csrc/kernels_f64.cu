@@ -194,8 +194,9 @@ void launch_band(const BandGroup &g, int nrhs, const int *done, cudaStream_t s) 
 // (outer, fastest) index strided by the warp width, lanes over consecutive
 // entries (coalesced X and Y). Work items run row-fastest so that warps in
 // flight share their X windows in L1/L2.
+// At most 256 threads per block and 64 registers per thread (4 blocks of 256 per SM).
 template <int T>
-__global__ void __launch_bounds__(512) k_band_df(BandGroupDF g, int nrhs, const int *done) {
+__global__ void __launch_bounds__(256, 4) k_band_df(BandGroupDF g, int nrhs, const int *done) {
   const int rhs = blockIdx.y;
   if (done && done[rhs]) return;
   const BandOpDF &op = g.table ? g.table[blockIdx.z] : g.op[blockIdx.z];
@@ -298,7 +299,7 @@ void launch_band_df(const BandGroupDF &g, int nrhs, const int *done, cudaStream_
       maxt = t > maxt ? t : maxt;
     }
   constexpr int T = 4;
-  const int thr = g.threads > 0 ? g.threads : 256;
+  const int thr = g.threads > 0 && g.threads <= 256 ? g.threads : 128;
   int64_t blocks = (maxt / T + thr - 1) / thr;
   if (blocks > 152 * 16) blocks = 152 * 16;
   if (blocks < 1) blocks = 1;
