@@ -337,6 +337,7 @@ def run_gpu(args):
     value = total_solves / (ms / 1e3)
 
     iters = [i["iterations"] for inf in infos for i in inf]
+    iters_est = [i["iterations_estimate"] for inf in infos for i in inf]
     statuses = sorted(set(i["status"] for inf in infos for i in inf))
     true_res = max(i["true_rel_res"] for inf in infos for i in inf)
 
@@ -453,7 +454,8 @@ def run_gpu(args):
                               nrhs, P.n_total * 8 / 1e6),
                           "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
                "minres": {"iterations_min": min(iters), "iterations_max": max(iters), "status": statuses,
-                          "true_rel_res_max": true_res},
+                          "true_rel_res_max": true_res,
+                          "iterations_estimate_min": min(iters_est), "iterations_estimate_max": max(iters_est)},
                "fd_apply": {"applies_per_s": applies_per_s, "gdof_per_s": applies_per_s * P.n_total / 1e9,
                             "ms_per_batch": ms_apply, "rel_err_vs_f64": apply_err},
                "phases_ms_per_iter": {"matvec": per_mv, "prec": per_pc,
@@ -613,7 +615,9 @@ def run_batched(args):
                           "l2": "inputs larger than L2 (%.1f GB of right-hand sides)" % (sum(tc["n_total"]) * 8e-9),
                           "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
                "minres": {"iterations_min": min(it_tc), "iterations_max": max(it_tc), "iterations_mean":
-                          float(np.mean(it_tc)), "status": st_tc, "true_rel_res_max": tr_tc},
+                          float(np.mean(it_tc)), "status": st_tc, "true_rel_res_max": tr_tc,
+                          "iterations_estimate_mean": float(np.mean([i["iterations_estimate"] for inf in tc["infos"]
+                                                                      for i in inf]))},
                "fp64_fd": {"solves_per_s": value64, "ms_per_step": f64["ms"] / len(f64["infos"]),
                            "iterations_mean": float(np.mean(it_64)), "true_rel_res_max": tr_64,
                            "ms_apply_grouped": f64["info"]["ms_apply"],

@@ -95,6 +95,9 @@ typedef struct {
   int status;              /* FDST_OK (converged), FDST_MAXIT, FDST_BREAKDOWN, FDST_NAN_DETECTED, ... */
   double eta_rel;          /* final ||r||_{P^-1} / ||r_0||_{P^-1} from the MINRES recurrence */
   double true_rel_res;     /* ||b - A x||_2 / ||b||_2 computed in FP64 after the solve */
+  int iterations_estimate; /* iteration at which the recurrence estimate first met tol (a stopping
+                              rule on the estimate alone); iterations continue until the FP64 true
+                              residual meets tol */
 } fdst_solve_info;
 
 /*

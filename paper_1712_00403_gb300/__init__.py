@@ -55,7 +55,7 @@ class ServerOpts(ctypes.Structure):
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("status", ctypes.c_int), ("eta_rel", ctypes.c_double),
-                ("true_rel_res", ctypes.c_double)]
+                ("true_rel_res", ctypes.c_double), ("iterations_estimate", ctypes.c_int)]
 
 
 ENTRY_POINTS = ["fdst_setup", "fdst_destroy", "fdst_get_sizes", "fdst_apply_prec", "fdst_matvec", "fdst_solve",
@@ -233,7 +233,7 @@ class Stokes:
         elif code not in (0, 5, 6, 7, 9):
             _check(code)
         return [dict(iterations=i.iterations, status=STATUS.get(i.status, i.status), eta_rel=i.eta_rel,
-                     true_rel_res=i.true_rel_res) for i in info]
+                     true_rel_res=i.true_rel_res, iterations_estimate=i.iterations_estimate) for i in info]
 
     def solve_host(self, b, x, tol=1e-8, maxit=1000, stream=None):
         """b, x: host numpy float64 arrays (x is the initial guess, overwritten)."""
@@ -244,7 +244,7 @@ class Stokes:
         if code not in (0, 5, 6, 7, 9):
             _check(code)
         return [dict(iterations=i.iterations, status=STATUS.get(i.status, i.status), eta_rel=i.eta_rel,
-                     true_rel_res=i.true_rel_res) for i in info]
+                     true_rel_res=i.true_rel_res, iterations_estimate=i.iterations_estimate) for i in info]
 
     def apply_prec_host(self, r, s, stream=None):
         n = r.size // self.n_total
@@ -288,7 +288,7 @@ class Batch:
         if code not in (0, 5, 6, 7, 9):
             _check(code)
         return [dict(iterations=i.iterations, status=STATUS.get(i.status, i.status), eta_rel=i.eta_rel,
-                     true_rel_res=i.true_rel_res) for i in info]
+                     true_rel_res=i.true_rel_res, iterations_estimate=i.iterations_estimate) for i in info]
 
     def close(self):
         if getattr(self, "_b", None):

@@ -687,7 +687,7 @@ fdst_status fdst_batch_solve(fdst_batch b, const double *const *d_b, double *con
   }
   std::vector<MinresState> hs(n);
   std::vector<double> prev_true(n, -1.0);
-  std::vector<int> restarts(n, 0);
+  std::vector<int> restarts(n, 0), est_iters(n, -1);
   int it = 0;
   bool residuals_current = false;
   const int check_every = 4;
@@ -720,6 +720,7 @@ fdst_status fdst_batch_solve(fdst_batch b, const double *const *d_b, double *con
         for (int i = 0; i < n; ++i) {
           fdst_ctx *h = b->hs[i];
           CK(cudaMemcpy(&hs[i], h->state, sizeof(MinresState), cudaMemcpyDeviceToHost));
+          if (est_iters[i] < 0) est_iters[i] = hs[i].iters;
           const int a = resume_action(hs[i], true_rel[i], prev_true[i], restarts[i], tol, maxit);
           if (a == kKeepStopped) continue;
           prev_true[i] = true_rel[i];
@@ -758,6 +759,7 @@ fdst_status fdst_batch_solve(fdst_batch b, const double *const *d_b, double *con
     if (hs[i].eta0 == 0.0 && hs[i].status == 0) info[i].status = FDST_OK;
     info[i].eta_rel = hs[i].eta0 > 0 ? std::fabs(hs[i].eta) / hs[i].eta0 : 0.0;
     info[i].true_rel_res = true_rel[i];
+    info[i].iterations_estimate = est_iters[i] >= 0 ? est_iters[i] : hs[i].iters;
     if (ret == FDST_OK && info[i].status != FDST_OK) ret = (fdst_status)info[i].status;
   }
   CK(cudaEventRecord(ev, st));

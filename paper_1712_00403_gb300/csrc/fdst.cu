@@ -876,7 +876,7 @@ fdst_status fdst_solve(fdst_handle h, const double *d_b, double *d_x, int nrhs, 
   };
   std::vector<MinresState> hs(nrhs);
   std::vector<double> prev_true(nrhs, -1.0);
-  std::vector<int> restarts(nrhs, 0);
+  std::vector<int> restarts(nrhs, 0), est_iters(nrhs, -1);
   const int check_every = 4;
   int it = 0;
   bool residuals_current = false;
@@ -911,6 +911,8 @@ fdst_status fdst_solve(fdst_handle h, const double *d_b, double *d_x, int nrhs, 
         TRY(true_residuals());
         residuals_current = true;
         CK(cudaMemcpy(hs.data(), h->state, sizeof(MinresState) * nrhs, cudaMemcpyDeviceToHost));
+        for (int j = 0; j < nrhs; ++j)
+          if (est_iters[j] < 0) est_iters[j] = hs[j].iters;
         std::vector<int> resume, restart;
         for (int j = 0; j < nrhs; ++j) {
           const int a = resume_action(hs[j], true_rel[j], prev_true[j], restarts[j], tol, maxit);
@@ -962,6 +964,7 @@ fdst_status fdst_solve(fdst_handle h, const double *d_b, double *d_x, int nrhs, 
     if (hs[j].eta0 == 0.0 && hs[j].status == 0) info[j].status = FDST_OK;
     info[j].eta_rel = hs[j].eta0 > 0 ? std::fabs(hs[j].eta) / hs[j].eta0 : 0.0;
     info[j].true_rel_res = true_rel[j];
+    info[j].iterations_estimate = est_iters[j] >= 0 ? est_iters[j] : hs[j].iters;
     if (ret == FDST_OK && info[j].status != FDST_OK) ret = (fdst_status)info[j].status;
   }
   return ret;

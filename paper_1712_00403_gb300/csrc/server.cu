@@ -48,6 +48,7 @@ struct Req {
   fdst_status prep_status = FDST_OK;
   double prev_true = -1.0;   // true residual at the previous check of a stopped recurrence
   int restarts = 0;
+  int est_iters = -1;        // iteration at which the estimate first met tol
 };
 
 std::string problem_key(const fdst_desc &d, const std::vector<double> *knots) {
@@ -130,6 +131,7 @@ fdst_status finish(fdst_server s, Req &r, const MinresState &S, double true_rel,
   if (S.eta0 == 0.0 && S.status == 0) r.info.status = FDST_OK;
   r.info.eta_rel = S.eta0 > 0 ? std::fabs(S.eta) / S.eta0 : 0.0;
   r.info.true_rel_res = true_rel;
+  r.info.iterations_estimate = r.est_iters >= 0 ? r.est_iters : S.iters;
   r.t_done = now;
   r.state = 2;
   ++s->finished;
@@ -241,6 +243,7 @@ fdst_status fdst_server_step(fdst_server s, double now, int *n_active, int *n_qu
         const size_t i = stopped[k];
         Req &r = s->reqs[s->active[i]];
         const double tr = r.bb > 0 ? std::sqrt(rr[k] / r.bb) : std::sqrt(rr[k]);
+        if (r.est_iters < 0) r.est_iters = S[i].iters;
         const int a = resume_action(S[i], tr, r.prev_true, r.restarts, s->o.tol, s->o.maxit);
         if (a != kKeepStopped) r.prev_true = tr;
         std::vector<MinresState> one{S[i]};

@@ -89,6 +89,11 @@ def test_minres_f64_matches_oracle(spec):
                                tol=1e-8, maxit=500, true_check=True)
         assert info[j]["status"] == "OK"
         assert abs(info[j]["iterations"] - io["iters"]) <= 1
+        # the estimate-only stopping rule: the oracle's recurrence without the true-residual check
+        _, ie = minres.minres(lambda v: stokes.matvec(S, v), B[j], lambda v: stokes.apply_PD_inv(S, v),
+                              tol=1e-8, maxit=500, true_check=False)
+        assert abs(info[j]["iterations_estimate"] - ie["iters"]) <= 1
+        assert info[j]["iterations_estimate"] <= info[j]["iterations"]
         assert info[j]["true_rel_res"] <= 1e-8
         res = np.linalg.norm(B[j] - stokes.matvec(S, X[j])) / np.linalg.norm(B[j])
         assert res <= 1e-8
