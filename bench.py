@@ -32,7 +32,7 @@ sys.path.insert(0, ROOT)
 METRIC = "FD applies/s (GDoF/s) and MINRES solves/s vs plain FP64 at stated error; p99 latency"
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_NOMINAL_TFLOPS = 1.25     # GB300 FP64 (DFMA) nominal, profiling recipe table
-FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flops x max SM clock
+FP32_LANE_TOPS = 152 * 128 * 2.070e9 / 1e12   # SMs x FP32 lanes x max SM clock: lane operations per second
 TF32_OVER_BF16 = 1.1 / 2.25    # nominal dense TF32 / BF16 ratio
 
 
@@ -364,37 +364,46 @@ def run_gpu(args):
         apply_err = float(torch.linalg.norm(s[:P.n_total] - s64) / torch.linalg.norm(s64))
         P64.close()
 
-    # roofline of the dominant phase (timed live inside the timed region)
+    # roofline of the dominant kernel, timed live inside the timed region: for the matvec, CUDA events
+    # around its compute launches alone (fdst_get_kernel_timing); for the FD apply, the preconditioner phase
     pk = peaks()
     per_mv = tm["ms_matvec"] / max(tm["n_matvec"], 1)
     per_pc = tm["ms_prec"] / max(tm["n_prec"], 1)
+    k_ms = tm["ms_matvec_kernels"] / max(tm["n_matvec"], 1)          # compute launches per matvec
+    k_launch_ms = tm["ms_matvec_kernels"] / max(tm["n_matvec_kernel_launches"], 1)
+    unit = "TFLOP/s"
     if per_mv >= per_pc and mapped:
         nnz = P.flops_matvec / 2.0
         kern = ("csr_spmv_%s (assembled mapped Stokes operator, one warp per row, 4 RHS per pass)"
                 % ("df64" if mv == fd.MV_DF64 else "f64"))
-        # algorithmic bytes per matvec: values (8 B: FP64 or an FP32 pair) + column indices + row pointers
-        # once, x and y once per RHS (plus, for double-float, the split of x: 16 B per entry and RHS)
+        # algorithmic bytes per launch: values (8 B: FP64 or an FP32 pair) + column indices once,
+        # row pointers once, x read and y written once per entry and RHS
         flops = None
-        byts = 12.0 * nnz + 8.0 * (P.n_total + 1) + 16.0 * P.n_total * nrhs * (2 if mv == fd.MV_DF64 else 1)
-        t_ms = per_mv
+        byts = 12.0 * nnz + 8.0 * (P.n_total + 1) + 16.0 * P.n_total * nrhs
+        t_ms, launch_ms = k_ms, k_launch_ms
         peak, bound = pk.get("hbm_gbs", 6701.5), "hbm"
         peak_note = "measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
     elif per_mv >= per_pc and mv == fd.MV_F64:
-        kern, flops, t_ms = "stokes_matvec_f64 (banded Kronecker mode products)", P.flops_matvec * nrhs, per_mv
+        kern, flops, t_ms, launch_ms = ("k_band (FP64 banded Kronecker mode products of the matvec)",
+                                        P.flops_matvec * nrhs, k_ms, k_launch_ms)
         peak = FP64_NOMINAL_TFLOPS
         peak_note = "FP64 DFMA nominal 1.25 TFLOP/s (recipe table; measured DFMA chain 1.20)"
         bound = "alu"
     elif per_mv >= per_pc:
-        # double-float: 12 FP32 operations per banded multiply-add (exact product + TwoSum)
-        kern = "stokes_matvec_df64 (banded Kronecker mode products, FP32-pair arithmetic)"
-        flops, t_ms = P.flops_matvec * nrhs * 6.0, per_mv
-        peak = FP32_NOMINAL_TFLOPS
-        peak_note = ("FP32 ALU: 152 SMs x 128 FP32 lanes x 2070 MHz = 80.5 TFLOP/s nominal (FFMA chain measured 75); "
-                     "achieved counts 12 FP32 ops per multiply-add of the plan")
+        # double-float: 12 FP32 lane operations per banded multiply-add of the plan (exact product
+        # with 1 FMUL + 3 FFMA, TwoSum and error accumulation with 8 FADD); the FP32 pipe issues one
+        # lane operation per lane and clock whatever its kind, so the ceiling is the lane rate
+        kern = "k_band_df (double-float banded Kronecker mode products of the matvec)"
+        flops, t_ms, launch_ms = P.flops_matvec / 2.0 * 12.0 * nrhs, k_ms, k_launch_ms
+        peak, unit = FP32_LANE_TOPS, "Top/s"
+        peak_note = ("FP32 lane operations: 152 SMs x 128 FP32 lanes x 2070 MHz = 40.3 T/s nominal "
+                     "(an FFMA chain measured 37.5 T/s); achieved counts 12 per multiply-add of the plan")
         bound = "alu"
     else:
-        kern, flops, t_ms = "fd_apply", P.flops_apply * nrhs, per_pc
+        kern, flops, t_ms = "k_gemm_tc (FD apply phase)", P.flops_apply * nrhs, per_pc
+        launch_ms = per_pc
         if prec == fd.FD_F64:
+            kern = "k_gemm_f64 (FD apply phase)"
             peak, bound = FP64_NOMINAL_TFLOPS, "alu"
             peak_note = "FP64 DFMA nominal 1.25 TFLOP/s (recipe table; measured DFMA chain 1.20)"
         elif prec == fd.FD_BF16X6:
@@ -410,9 +419,10 @@ def run_gpu(args):
     if bound == "hbm":
         achieved, unit = byts / (t_ms / 1e3) / 1e9, "GB/s"
     else:
-        achieved, unit = flops / (t_ms / 1e3) / 1e12, "TFLOP/s"
+        achieved = flops / (t_ms / 1e3) / 1e12
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
-                "traffic": None, "kernel": kern, "ms_per_launch": t_ms, "peak_source": peak_note}
+                "traffic": None, "kernel": kern, "ms_per_launch": launch_ms, "ms_per_phase": t_ms,
+                "peak_source": peak_note}
 
     # end to end through the host-pointer entry point (pinned host buffers)
     bh = torch.empty(b.numel(), dtype=torch.float64, pin_memory=True)

@@ -172,6 +172,17 @@ fdst_status fdst_get_timing(fdst_handle h, double *ms_matvec, double *ms_prec, d
                             int64_t *n_matvec, int64_t *n_prec);
 
 /*
+ * fdst_get_kernel_timing - with timing on, the matvecs inside the MINRES
+ * iterations also record CUDA events around their compute launches alone (the
+ * banded Kronecker mode products of the Cartesian operator, or the CSR SpMV on
+ * mapped geometry; not the FP64 <-> FP32-pair conversions around them). Returns
+ * the summed duration (ms, resolved when fdst_solve returns) and the number of
+ * launches inside those spans since the last fdst_set_timing. FDST_INVALID_ARGUMENT
+ * for a NULL handle; NULL outputs are skipped.
+ */
+fdst_status fdst_get_kernel_timing(fdst_handle h, double *ms, int64_t *launches);
+
+/*
  * fdst_fd_apply_static - allocation-free FD solve of one Kronecker-sum block:
  *   s = (U_d x ... x U_1) Delta^{-1} (U_d x ... x U_1)^T r,
  *   Delta[i1, i2, (i3)] = sum_d coef[d] * lam_d[i_d],

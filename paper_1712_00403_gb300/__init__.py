@@ -59,7 +59,7 @@ class SolveInfo(ctypes.Structure):
 
 
 ENTRY_POINTS = ["fdst_setup", "fdst_destroy", "fdst_get_sizes", "fdst_apply_prec", "fdst_matvec", "fdst_solve",
-                "fdst_solve_host", "fdst_apply_prec_host", "fdst_set_timing", "fdst_get_timing",
+                "fdst_solve_host", "fdst_apply_prec_host", "fdst_set_timing", "fdst_get_timing", "fdst_get_kernel_timing",
                 "fdst_fd_apply_static", "fdst_batch_create", "fdst_batch_solve", "fdst_batch_info",
                 "fdst_batch_destroy", "fdst_server_create", "fdst_server_submit", "fdst_server_step",
                 "fdst_server_result", "fdst_server_stats", "fdst_server_destroy", "fdst_device_error",
@@ -103,6 +103,7 @@ def load_library(path=LIB_PATH):
                                          ctypes.POINTER(d), vp, vp, vp]
     lib.fdst_get_timing.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d),
                                     ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    lib.fdst_get_kernel_timing.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_int64)]
     lib.fdst_last_error.restype = ctypes.c_char_p
     for name in ENTRY_POINTS[:-2]:
         getattr(lib, name).restype = ctypes.c_int
@@ -259,7 +260,10 @@ class Stokes:
         m, p = ctypes.c_int64(), ctypes.c_int64()
         _check(_lib.fdst_get_timing(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(m),
                                     ctypes.byref(p)))
-        return dict(ms_matvec=a.value, ms_prec=b.value, ms_vector=c.value, n_matvec=m.value, n_prec=p.value)
+        k, kn = ctypes.c_double(), ctypes.c_int64()
+        _check(_lib.fdst_get_kernel_timing(self._h, ctypes.byref(k), ctypes.byref(kn)))
+        return dict(ms_matvec=a.value, ms_prec=b.value, ms_vector=c.value, n_matvec=m.value, n_prec=p.value,
+                    ms_matvec_kernels=k.value, n_matvec_kernel_launches=kn.value)
 
 
 class Batch:

@@ -474,10 +474,8 @@ static fdst_status build_batch(fdst_batch b) {
       rmax[key] = std::max(rmax[key], (int64_t)od[0] * od[1] * od[2]);
       if (b->df) {
         BandOpDF o;
-        o.vals = bd.vals_df; o.lo = bd.lo; o.w = bd.w; o.rows = bd.rows;
+        o.vals = op.vals_df; o.lo = bd.lo; o.w = bd.w; o.rows = bd.rows;
         o.d0 = op.dims[0]; o.d1 = op.dims[1]; o.d2 = op.dims[2]; o.mode = op.mode;
-        const float chh = (float)op.coef;
-        o.coef = make_float2(chh, (float)(op.coef - (double)chh));
         o.accumulate = op.accumulate;
         if (op.in_kind == 0) o.X = h->x2 + h->off[op.in_id];
         else if (op.in_kind == 1) o.X = reinterpret_cast<const float2 *>(h->t1[op.in_id]);

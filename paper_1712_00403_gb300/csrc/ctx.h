@@ -42,6 +42,7 @@ struct BandDev {
   double *vals;
   int *lo;
   float2 *vals_df;   // the same values split into FP32 pairs (double-float matvec)
+  std::vector<double> hvals;   // host copy of vals (rows x w)
 };
 
 struct PlanOp {
@@ -53,6 +54,7 @@ struct PlanOp {
   int dims[3];           // input dims
   double coef;
   int accumulate;
+  const float2 *vals_df;  // coef x band values as FP32 pairs (double-float matvec)
 };
 
 }  // namespace fdst
@@ -103,6 +105,11 @@ struct fdst_ctx {
   int timing = 0;
   double ms_matvec = 0, ms_prec = 0, ms_vector = 0;
   int64_t n_matvec = 0, n_prec = 0;
+  // events around the matvec's compute launches alone (banded mode products or CSR SpMV,
+  // without the FP64 <-> FP32-pair conversions), resolved at the end of fdst_solve
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> kev;
+  double ms_kernel = 0;
+  int64_t n_kernel = 0;
 };
 
 namespace fdst {

@@ -282,6 +282,7 @@ static fdst_status build_matvec(fdst_ctx *h) {
       vdf[i] = make_float2(hi, (float)(vals[i] - (double)hi));
     }
     TRY(upload(h, &b.vals_df, vdf));
+    b.hvals = vals;
     *id = (int)h->bands.size();
     h->bands.push_back(b);
     band_ids[key] = *id;
@@ -393,6 +394,26 @@ static fdst_status build_matvec(fdst_ctx *h) {
   h->plan.insert(h->plan.end(), st1.begin(), st1.end());
   h->plan.insert(h->plan.end(), st2.begin(), st2.end());
   h->plan.insert(h->plan.end(), st3.begin(), st3.end());
+  // double-float band values with the op's coefficient folded in (the products are
+  // then summed without a final scaling); one copy per distinct (band, coefficient)
+  std::map<std::pair<int, double>, const float2 *> scaled;
+  for (auto &op : h->plan) {
+    const auto key = std::make_pair(op.band, op.coef);
+    auto it = scaled.find(key);
+    if (it == scaled.end()) {
+      const BandDev &bd = h->bands[op.band];
+      std::vector<float2> v(bd.hvals.size());
+      for (size_t k = 0; k < v.size(); ++k) {
+        const double a = op.coef * bd.hvals[k];
+        const float hi = (float)a;
+        v[k] = make_float2(hi, (float)(a - (double)hi));
+      }
+      float2 *d = nullptr;
+      TRY(upload(h, &d, v));
+      it = scaled.emplace(key, d).first;
+    }
+    op.vals_df = it->second;
+  }
   for (int64_t sz : h->t1_size) {
     double *b = nullptr;
     TRY(dalloc(h, &b, (size_t)sz * h->max_rhs));
@@ -521,9 +542,29 @@ fdst_status run_apply(fdst_ctx *h, const double *r, double *s, int nrhs, const i
   return FDST_OK;
 }
 
+// Timing of the matvec's compute launches alone: an event before the first and
+// after the last launch, kept in h->kev (only when timing is on).
+static cudaEvent_t kernel_mark(fdst_ctx *h, cudaStream_t st) {
+  if (!h->timing) return nullptr;
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  cudaEventRecord(e, st);
+  return e;
+}
+
+static void kernel_span(fdst_ctx *h, cudaEvent_t a, int64_t launches, cudaStream_t st) {
+  if (!a) return;
+  cudaEvent_t b = kernel_mark(h, st);
+  if (!b) { cudaEventDestroy(a); return; }
+  h->kev.emplace_back(a, b);
+  h->n_kernel += launches;
+}
+
 static fdst_status run_matvec_f64(fdst_ctx *h, const double *x, double *y, int nrhs, const int *done,
-                                  cudaStream_t st) {
+                                  cudaStream_t st, bool timed) {
   // pack consecutive ops of a stage into launches with pairwise distinct outputs
+  cudaEvent_t k0 = timed ? kernel_mark(h, st) : nullptr;
+  int64_t nl = 0;
   size_t i = 0;
   const auto &P = h->plan;
   while (i < P.size()) {
@@ -549,7 +590,9 @@ static fdst_status run_matvec_f64(fdst_ctx *h, const double *x, double *y, int n
       ++i;
     }
     launch_band(g, nrhs, done, st);
+    ++nl;
   }
+  kernel_span(h, k0, nl, st);
   CK(cudaGetLastError());
   return FDST_OK;
 }
@@ -559,6 +602,8 @@ static fdst_status run_matvec_f64(fdst_ctx *h, const double *x, double *y, int n
 static fdst_status run_matvec_df(fdst_ctx *h, const double *x, double *y, int nrhs, const int *done,
                                  cudaStream_t st) {
   launch_split_df(x, h->x2, h->n_total, h->n_total, nrhs, done, st);
+  cudaEvent_t k0 = kernel_mark(h, st);
+  int64_t nl = 0;
   size_t i = 0;
   const auto &P = h->plan;
   while (i < P.size()) {
@@ -572,10 +617,8 @@ static fdst_status run_matvec_df(fdst_ctx *h, const double *x, double *y, int nr
       const PlanOp &op = P[i];
       BandOpDF &b = g.op[g.nop++];
       const BandDev &bd = h->bands[op.band];
-      b.vals = bd.vals_df; b.lo = bd.lo; b.w = bd.w; b.rows = bd.rows;
+      b.vals = op.vals_df; b.lo = bd.lo; b.w = bd.w; b.rows = bd.rows;
       b.d0 = op.dims[0]; b.d1 = op.dims[1]; b.d2 = op.dims[2]; b.mode = op.mode;
-      const float ch = (float)op.coef;
-      b.coef = make_float2(ch, (float)(op.coef - (double)ch));
       b.accumulate = op.accumulate;
       if (op.in_kind == 0) { b.X = h->x2 + h->off[op.in_id]; b.x_rhs_stride = h->n_total; }
       else if (op.in_kind == 1) { b.X = reinterpret_cast<const float2 *>(h->t1[op.in_id]); b.x_rhs_stride = h->t1_size[op.in_id]; }
@@ -586,7 +629,9 @@ static fdst_status run_matvec_df(fdst_ctx *h, const double *x, double *y, int nr
       ++i;
     }
     launch_band_df(g, nrhs, done, st);
+    ++nl;
   }
+  kernel_span(h, k0, nl, st);
   launch_join_df(h->y2, y, h->n_total, h->n_total, nrhs, done, st);
   CK(cudaGetLastError());
   return FDST_OK;
@@ -644,15 +689,19 @@ fdst_status run_matvec(fdst_ctx *h, const double *x, double *y, int nrhs, const 
   if (h->mapped) {
     if (!exact && h->csr.val_df) {
       launch_split_df(x, h->x2, h->n_total, h->n_total, nrhs, done, st);
+      cudaEvent_t k0 = kernel_mark(h, st);
       launch_spmv_df(h->csr, h->x2, y, h->n_total, nrhs, done, st);
+      kernel_span(h, k0, 1, st);
     } else {
+      cudaEvent_t k0 = exact ? nullptr : kernel_mark(h, st);
       launch_spmv(h->csr, x, y, h->n_total, nrhs, done, st);
+      kernel_span(h, k0, 1, st);
     }
     CK(cudaGetLastError());
     return FDST_OK;
   }
   if (!exact && h->desc.matvec_precision == FDST_MV_DF64) return run_matvec_df(h, x, y, nrhs, done, st);
-  return run_matvec_f64(h, x, y, nrhs, done, st);
+  return run_matvec_f64(h, x, y, nrhs, done, st, !exact);
 }
 
 }  // namespace fdst
@@ -672,6 +721,10 @@ fdst_status fdst_device_error(int *flag) {
 
 fdst_status fdst_destroy(fdst_handle h) {
   if (!h) return FDST_OK;
+  for (auto &k : h->kev) {
+    cudaEventDestroy(k.first);
+    cudaEventDestroy(k.second);
+  }
   for (void *p : h->allocs) cudaFree(p);
   if (h->h_n_stopped) cudaFreeHost(h->h_n_stopped);
   if (h->h_dots) cudaFreeHost(h->h_dots);
@@ -811,6 +864,15 @@ fdst_status fdst_set_timing(fdst_handle h, int on) {
   h->timing = on;
   h->ms_matvec = h->ms_prec = h->ms_vector = 0;
   h->n_matvec = h->n_prec = 0;
+  h->ms_kernel = 0;
+  h->n_kernel = 0;
+  return FDST_OK;
+}
+
+fdst_status fdst_get_kernel_timing(fdst_handle h, double *ms, int64_t *launches) {
+  if (!h) { set_error("NULL handle"); return FDST_INVALID_ARGUMENT; }
+  if (ms) *ms = h->ms_kernel;
+  if (launches) *launches = h->n_kernel;
   return FDST_OK;
 }
 
@@ -957,6 +1019,14 @@ fdst_status fdst_solve(fdst_handle h, const double *d_b, double *d_x, int nrhs, 
     }
     for (auto e : ev) cudaEventDestroy(e);
   }
+  for (auto &k : h->kev) {
+    float ms = 0.f;
+    if (h->timing) cudaEventElapsedTime(&ms, k.first, k.second);
+    h->ms_kernel += ms;
+    cudaEventDestroy(k.first);
+    cudaEventDestroy(k.second);
+  }
+  h->kev.clear();
   fdst_status ret = FDST_OK;
   for (int j = 0; j < nrhs; ++j) {
     info[j].iterations = hs[j].iters;

@@ -65,7 +65,8 @@ void launch_band(const BandGroup &g, int nrhs, const int *done, cudaStream_t s);
 // Double-float variant: tensors and band values are FP32 pairs (hi, lo) with
 // hi + lo the value (48-bit significand); products and sums use error-free
 // transformations (FMA-based exact product, Knuth's TwoSum). Same operation
-// as BandOp; X, Y, vals hold float2.
+// as BandOp with coef folded into vals: Y = X x_mode Bd (or Y += ...), X, Y,
+// vals hold float2.
 struct BandOpDF {
   const float2 *X = nullptr;
   float2 *Y = nullptr;
@@ -73,7 +74,6 @@ struct BandOpDF {
   const int *lo = nullptr;
   int w = 0, rows = 0;
   int d0 = 1, d1 = 1, d2 = 1, mode = 0;
-  float2 coef = {1.0f, 0.0f};
   int accumulate = 0;
   int64_t x_rhs_stride = 0, y_rhs_stride = 0;
   const int *done_flag = nullptr;

@@ -189,10 +189,13 @@ void launch_band(const BandGroup &g, int nrhs, const int *done, cudaStream_t s) 
 // (p = a*b, e = fma(a, b, -p)), sums use Knuth's branch-free TwoSum.
 
 // Each thread computes T outputs that share one band row i (so one V row and
-// one lo[i]): for mode 0 (contracted index fastest) T consecutive lines with
-// lanes over consecutive rows i; for modes 1 and 2 T entries of the flattened
-// (outer, fastest) index strided by the warp width, lanes over consecutive
-// entries (coalesced X and Y). Work items run row-fastest so that warps in
+// one lo[i]). Mode 0 (contracted index fastest): T consecutive lines, lanes
+// over the flattened (line group, row) pairs, so that no lane idles when the
+// row count is not a multiple of the warp width. Modes 1 and 2: T entries of
+// the flattened (outer, fastest) index strided by the warp width, lanes over
+// consecutive entries (coalesced X and Y); when a warp's 32 T entries lie in
+// one outer slab (always in mode 2 but for the tail) they sit at one base
+// address plus constant offsets. Work items run row-fastest so that warps in
 // flight share their X windows in L1/L2.
 // At most 256 threads per block and 64 registers per thread (4 blocks of 256 per SM).
 template <int T>
@@ -203,89 +206,128 @@ __global__ void __launch_bounds__(256, 4) k_band_df(BandGroupDF g, int nrhs, con
   if (op.done_flag && *op.done_flag) return;
   const float2 *X = op.X + rhs * op.x_rhs_stride;
   float2 *Y = op.Y + rhs * op.y_rhs_stride;
-  const int lane = threadIdx.x & 31;
-  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int rows = op.rows, w = op.w;
-  const float2 coef = op.coef;
-  auto finish = [&](float sh, float sl, float2 *dst) {
-    const float2 acc = df_norm(sh, sl);
-    float rh = 0.0f, rl = 0.0f;
-    df_fma_acc(coef, acc, rh, rl);
-    if (op.accumulate) {
-      const float2 yo = *dst;
-      const float t2 = rh + yo.x;
-      const float z2 = t2 - rh;
-      const float err = (rh - (t2 - z2)) + (yo.x - z2);
-      rl = rl + (err + yo.y);
-      rh = t2;
-    }
-    *dst = df_norm(rh, rl);
+  const unsigned lane = threadIdx.x & 31;
+  // (one operand of one right-hand side holds fewer than 2^32 entries: 32-bit offsets and work indices)
+  const unsigned warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int w = op.w;
+  const unsigned rows = (unsigned)op.rows;
+  // the op's coefficient is folded into vals: store (or add) the renormalized sum.
+  // With accumulation the T old values of Y are loaded together before the first
+  // store, so that their latencies overlap.
+  const bool acc = op.accumulate != 0;
+  auto finish = [&](float sh, float sl, float2 yo, float2 *dst) {
+    if (acc) df_add(sh, sl, yo.x, yo.y);
+    *dst = df_norm(sh, sl);
   };
   if (op.mode == 0) {
-    const int64_t d0 = op.d0;
-    const int64_t lines = (int64_t)op.d1 * op.d2;
-    const int64_t ib = (rows + 31) >> 5, lb = (lines + T - 1) / T;
-    for (int64_t u = warp0; u < ib * lb; u += nwarps) {
-      const int i = (int)(u % ib) * 32 + lane;
-      const int64_t L0 = (u / ib) * T;
-      if (i >= rows) continue;
-      const float2 *xp = X + L0 * d0 + op.lo[i];
-      const float2 *vp = op.vals + (int64_t)i * w;
-      int nt = (int)(lines - L0);
-      nt = nt < T ? nt : T;
+    const unsigned d0 = (unsigned)op.d0;
+    const unsigned lines = (unsigned)op.d1 * (unsigned)op.d2;
+    const unsigned groups = (lines + T - 1) / T;
+    const unsigned nq = groups * rows;          // (line group, row) pairs
+    const unsigned chunks = (nq + 31) >> 5;
+    for (unsigned u = warp0; u < chunks; u += nwarps) {
+      const unsigned q = u * 32u + lane;
+      if (q >= nq) continue;
+      const unsigned grp = q / rows;
+      const unsigned i = q - grp * rows;
+      const unsigned L0 = grp * T;
+      const float2 *xp = X + ((size_t)L0 * d0 + op.lo[i]);
+      const float2 *vp = op.vals + (size_t)i * w;
       float sh[T], sl[T];
 #pragma unroll
       for (int t = 0; t < T; ++t) sh[t] = sl[t] = 0.0f;
+      if (L0 + T <= lines) {
 #pragma unroll 2
-      for (int j = 0; j < w; ++j) {
-        const float2 v = vp[j];
+        for (int j = 0; j < w; ++j) {
+          const float2 v = vp[j];
+#pragma unroll
+          for (int t = 0; t < T; ++t) df_fma_acc(v, xp[t * d0 + j], sh[t], sl[t]);
+        }
+        float2 yo[T];
+#pragma unroll
+        for (int t = 0; t < T; ++t) yo[t] = acc ? Y[(size_t)(L0 + t) * rows + i] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int t = 0; t < T; ++t) finish(sh[t], sl[t], yo[t], Y + ((size_t)(L0 + t) * rows + i));
+      } else {
+        const unsigned nt = lines - L0;
+        for (int j = 0; j < w; ++j) {
+          const float2 v = vp[j];
+#pragma unroll
+          for (int t = 0; t < T; ++t)
+            if (t < nt) df_fma_acc(v, xp[t * d0 + j], sh[t], sl[t]);
+        }
+        float2 yo[T];
 #pragma unroll
         for (int t = 0; t < T; ++t)
-          if (t < nt) df_fma_acc(v, xp[t * d0 + j], sh[t], sl[t]);
-      }
+          yo[t] = acc && t < nt ? Y[(size_t)(L0 + t) * rows + i] : make_float2(0.f, 0.f);
 #pragma unroll
-      for (int t = 0; t < T; ++t)
-        if (t < nt) finish(sh[t], sl[t], Y + (L0 + t) * rows + i);
+        for (int t = 0; t < T; ++t)
+          if (t < nt) finish(sh[t], sl[t], yo[t], Y + ((size_t)(L0 + t) * rows + i));
+      }
     }
   } else {
     // Y[(o * rows + i) * P + p], X[(o * din + l) * P + p], m = o * P + p over outer * P entries
-    // (one operand of one right-hand side holds fewer than 2^32 entries: 32-bit offsets)
     const unsigned P = op.mode == 1 ? (unsigned)op.d0 : (unsigned)op.d0 * op.d1;
     const unsigned outer = op.mode == 1 ? op.d2 : 1, din = op.mode == 1 ? op.d1 : op.d2;
     const unsigned M = outer * P;
-    const int64_t mb = ((int64_t)M + 32 * T - 1) / (32 * T);
-    for (int64_t u = warp0; u < mb * rows; u += nwarps) {
-      const int i = (int)(u % rows);
-      const unsigned m0 = (unsigned)(u / rows) * (32 * T) + lane;
+    const unsigned mb = (M + 32 * T - 1) / (32 * T);
+    for (unsigned u = warp0; u < mb * rows; u += nwarps) {
+      const unsigned cb = u / rows;
+      const unsigned i = u - cb * rows;
+      const unsigned c0 = cb * (32 * T);     // first entry of this warp's chunk
       const unsigned l = op.lo[i];
-      unsigned xo[T], yo[T];
-      bool ok[T];
-#pragma unroll
-      for (int t = 0; t < T; ++t) {
-        const unsigned m = m0 + 32 * t;
-        ok[t] = m < M;
-        const unsigned o = ok[t] ? m / P : 0, p = ok[t] ? m - o * P : 0;
-        xo[t] = (o * din + l) * P + p;
-        yo[t] = (o * rows + i) * P + p;
-      }
-      const float2 *vp = op.vals + (int64_t)i * w;
+      const float2 *vp = op.vals + (size_t)i * w;
       float sh[T], sl[T];
 #pragma unroll
       for (int t = 0; t < T; ++t) sh[t] = sl[t] = 0.0f;
-      // unrolled by 4: the loads of four band columns are in flight together
+      const unsigned o0 = c0 / P;
+      if (c0 + 32 * T <= M && c0 + 32 * T <= (o0 + 1) * P) {
+        // the whole chunk in one outer slab (warp-uniform): offsets 32 t from one base
+        const unsigned p0 = c0 - o0 * P + lane;
+        const float2 *xp = X + ((size_t)(o0 * din + l) * P + p0);
 #pragma unroll 4
-      for (int j = 0; j < w; ++j) {
-        const float2 v = vp[j];
+        for (int j = 0; j < w; ++j) {
+          const float2 v = vp[j];
+#pragma unroll
+          for (int t = 0; t < T; ++t) df_fma_acc(v, xp[32 * t], sh[t], sl[t]);
+          xp += P;
+        }
+        float2 *yp = Y + ((size_t)(o0 * rows + i) * P + p0);
+        float2 yo[T];
+#pragma unroll
+        for (int t = 0; t < T; ++t) yo[t] = acc ? yp[32 * t] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int t = 0; t < T; ++t) finish(sh[t], sl[t], yo[t], yp + 32 * t);
+      } else {
+        const unsigned m0 = c0 + lane;
+        unsigned xo[T], yo[T];
+        bool ok[T];
 #pragma unroll
         for (int t = 0; t < T; ++t) {
-          if (ok[t]) df_fma_acc(v, X[xo[t]], sh[t], sl[t]);
-          xo[t] += P;
+          const unsigned m = m0 + 32 * t;
+          ok[t] = m < M;
+          const unsigned o = ok[t] ? m / P : 0, pp = ok[t] ? m - o * P : 0;
+          xo[t] = (o * din + l) * P + pp;
+          yo[t] = (o * rows + i) * P + pp;
         }
-      }
+        // unrolled by 4: the loads of four band columns are in flight together
+#pragma unroll 4
+        for (int j = 0; j < w; ++j) {
+          const float2 v = vp[j];
 #pragma unroll
-      for (int t = 0; t < T; ++t)
-        if (ok[t]) finish(sh[t], sl[t], Y + yo[t]);
+          for (int t = 0; t < T; ++t) {
+            if (ok[t]) df_fma_acc(v, X[xo[t]], sh[t], sl[t]);
+            xo[t] += P;
+          }
+        }
+        float2 yv[T];
+#pragma unroll
+        for (int t = 0; t < T; ++t) yv[t] = acc && ok[t] ? Y[yo[t]] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int t = 0; t < T; ++t)
+          if (ok[t]) finish(sh[t], sl[t], yv[t], Y + yo[t]);
+      }
     }
   }
 }
