@@ -614,7 +614,7 @@ def run_batched(args):
                 "peak_source": "TF32 = measured bf16 sustained x nominal TF32/BF16 ratio; flops = 3 split products "
                                "x 4 N sum(n_d) per velocity component + 4 N_q sum(n_q) per pressure"}
     cpu = None
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_instances(specs, it_tc[:n], k_iters=1)
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
@@ -736,7 +736,7 @@ def run_serving(args):
         tot = tt.cpu()
     value = float(tot[0]) / float(tot[1])
     cpu = None
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         specs = [r for r, _, _ in stream_of(synth.serving_requests(0, w["rates"][0], w["per_rate"], w["seed"],
                                                                   w["mix_seed"]))]
         its = [pr["iterations_mean"] for pr in per_rate[:1]] * len(specs)

@@ -465,7 +465,7 @@ static fdst_status build_batch(fdst_batch b) {
   std::map<std::pair<int, int>, int64_t> rmax;
   for (auto *h : b->hs) {
     std::map<std::tuple<int, int, int>, int> seen;   // (stage, out_kind, out_id) -> ops so far
-    for (const PlanOp &op : h->plan) {
+    for (const PlanOp &op : b->df ? h->plan_df : h->plan) {
       const int round = seen[std::make_tuple(op.stage, op.out_kind, op.out_id)]++;
       const auto key = std::make_pair(op.stage, round);
       const BandDev &bd = h->bands[op.band];
@@ -477,6 +477,7 @@ static fdst_status build_batch(fdst_batch b) {
         o.vals = op.vals_df; o.lo = bd.lo; o.w = bd.w; o.rows = bd.rows;
         o.d0 = op.dims[0]; o.d1 = op.dims[1]; o.d2 = op.dims[2]; o.mode = op.mode;
         o.accumulate = op.accumulate;
+        o.swap = op.swap;
         if (op.in_kind == 0) o.X = h->x2 + h->off[op.in_id];
         else if (op.in_kind == 1) o.X = reinterpret_cast<const float2 *>(h->t1[op.in_id]);
         else o.X = reinterpret_cast<const float2 *>(h->g[op.in_id]);

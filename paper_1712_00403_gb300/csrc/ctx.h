@@ -55,6 +55,7 @@ struct PlanOp {
   double coef;
   int accumulate;
   const float2 *vals_df;  // coef x band values as FP32 pairs (double-float matvec)
+  int swap;               // output written with its two slow coordinates exchanged
 };
 
 }  // namespace fdst
@@ -83,6 +84,9 @@ struct fdst_ctx {
   // matvec
   std::vector<fdst::BandDev> bands;
   std::vector<fdst::PlanOp> plan;
+  // the same ops for the double-float matvec: in 3D the T1 buffers hold (l1, l2, i0)
+  // with l1 slowest, so that the stage-2 products contract the slowest index
+  std::vector<fdst::PlanOp> plan_df;
   std::vector<double *> t1, g;
   std::vector<int64_t> t1_size, g_size;
   float2 *x2 = nullptr, *y2 = nullptr;   // double-float copies of the matvec input / output

@@ -414,6 +414,20 @@ static fdst_status build_matvec(fdst_ctx *h) {
     }
     op.vals_df = it->second;
   }
+  // double-float plan: stage 1 writes T1 as (l1, l2, i0) (slow coordinates swapped),
+  // stage 2 then contracts l1 as the slowest index (mode 2 over (i0, l2, l1)) and
+  // writes G in its usual (i0, i1, l2) order by swapping back
+  h->plan_df = h->plan;
+  if (dim == 3)
+    for (auto &op : h->plan_df) {
+      if (op.stage == 1) {
+        op.swap = 1;
+      } else if (op.stage == 2) {
+        op.mode = 2;
+        std::swap(op.dims[1], op.dims[2]);
+        op.swap = 1;
+      }
+    }
   for (int64_t sz : h->t1_size) {
     double *b = nullptr;
     TRY(dalloc(h, &b, (size_t)sz * h->max_rhs));
@@ -605,7 +619,7 @@ static fdst_status run_matvec_df(fdst_ctx *h, const double *x, double *y, int nr
   cudaEvent_t k0 = kernel_mark(h, st);
   int64_t nl = 0;
   size_t i = 0;
-  const auto &P = h->plan;
+  const auto &P = h->plan_df;
   while (i < P.size()) {
     BandGroupDF g;
     std::vector<std::pair<int, int>> outs;
@@ -620,6 +634,7 @@ static fdst_status run_matvec_df(fdst_ctx *h, const double *x, double *y, int nr
       b.vals = op.vals_df; b.lo = bd.lo; b.w = bd.w; b.rows = bd.rows;
       b.d0 = op.dims[0]; b.d1 = op.dims[1]; b.d2 = op.dims[2]; b.mode = op.mode;
       b.accumulate = op.accumulate;
+      b.swap = op.swap;
       if (op.in_kind == 0) { b.X = h->x2 + h->off[op.in_id]; b.x_rhs_stride = h->n_total; }
       else if (op.in_kind == 1) { b.X = reinterpret_cast<const float2 *>(h->t1[op.in_id]); b.x_rhs_stride = h->t1_size[op.in_id]; }
       else { b.X = reinterpret_cast<const float2 *>(h->g[op.in_id]); b.x_rhs_stride = h->g_size[op.in_id]; }

@@ -66,7 +66,9 @@ void launch_band(const BandGroup &g, int nrhs, const int *done, cudaStream_t s);
 // hi + lo the value (48-bit significand); products and sums use error-free
 // transformations (FMA-based exact product, Knuth's TwoSum). Same operation
 // as BandOp with coef folded into vals: Y = X x_mode Bd (or Y += ...), X, Y,
-// vals hold float2.
+// vals hold float2. With swap, Y is written with its two slow coordinates
+// exchanged: the output (c0, c1, c2) with extents (e0, e1, e2) (c0 fastest,
+// e_mode = rows) goes to c0 + e0 (c2 + e2 c1).
 struct BandOpDF {
   const float2 *X = nullptr;
   float2 *Y = nullptr;
@@ -75,6 +77,7 @@ struct BandOpDF {
   int w = 0, rows = 0;
   int d0 = 1, d1 = 1, d2 = 1, mode = 0;
   int accumulate = 0;
+  int swap = 0;
   int64_t x_rhs_stride = 0, y_rhs_stride = 0;
   const int *done_flag = nullptr;
 };

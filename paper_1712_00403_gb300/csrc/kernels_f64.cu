@@ -220,9 +220,10 @@ __global__ void __launch_bounds__(256, 4) k_band_df(BandGroupDF g, int nrhs, con
     if (acc) df_add(sh, sl, yo.x, yo.y);
     *dst = df_norm(sh, sl);
   };
+  const bool swap = op.swap != 0;
+  const unsigned d0 = (unsigned)op.d0, d1 = (unsigned)op.d1, d2 = (unsigned)op.d2;
   if (op.mode == 0) {
-    const unsigned d0 = (unsigned)op.d0;
-    const unsigned lines = (unsigned)op.d1 * (unsigned)op.d2;
+    const unsigned lines = d1 * d2;
     const unsigned groups = (lines + T - 1) / T;
     const unsigned nq = groups * rows;          // (line group, row) pairs
     const unsigned chunks = (nq + 31) >> 5;
@@ -234,6 +235,20 @@ __global__ void __launch_bounds__(256, 4) k_band_df(BandGroupDF g, int nrhs, con
       const unsigned L0 = grp * T;
       const float2 *xp = X + ((size_t)L0 * d0 + op.lo[i]);
       const float2 *vp = op.vals + (size_t)i * w;
+      // output offsets of lines L0 + t: (L0 + t) rows + i, or with the slow coordinates
+      // swapped i + rows (l2 + d2 l1) for line l1 + d1 l2
+      unsigned yoff[T];
+      if (!swap) {
+#pragma unroll
+        for (int t = 0; t < T; ++t) yoff[t] = (L0 + t) * rows + i;
+      } else {
+        unsigned l2 = L0 / d1, l1 = L0 - l2 * d1;
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+          yoff[t] = i + rows * (l2 + d2 * l1);
+          if (++l1 == d1) { l1 = 0; ++l2; }
+        }
+      }
       float sh[T], sl[T];
 #pragma unroll
       for (int t = 0; t < T; ++t) sh[t] = sl[t] = 0.0f;
@@ -246,9 +261,9 @@ __global__ void __launch_bounds__(256, 4) k_band_df(BandGroupDF g, int nrhs, con
         }
         float2 yo[T];
 #pragma unroll
-        for (int t = 0; t < T; ++t) yo[t] = acc ? Y[(size_t)(L0 + t) * rows + i] : make_float2(0.f, 0.f);
+        for (int t = 0; t < T; ++t) yo[t] = acc ? Y[yoff[t]] : make_float2(0.f, 0.f);
 #pragma unroll
-        for (int t = 0; t < T; ++t) finish(sh[t], sl[t], yo[t], Y + ((size_t)(L0 + t) * rows + i));
+        for (int t = 0; t < T; ++t) finish(sh[t], sl[t], yo[t], Y + yoff[t]);
       } else {
         const unsigned nt = lines - L0;
         for (int j = 0; j < w; ++j) {
@@ -259,17 +274,25 @@ __global__ void __launch_bounds__(256, 4) k_band_df(BandGroupDF g, int nrhs, con
         }
         float2 yo[T];
 #pragma unroll
-        for (int t = 0; t < T; ++t)
-          yo[t] = acc && t < nt ? Y[(size_t)(L0 + t) * rows + i] : make_float2(0.f, 0.f);
+        for (int t = 0; t < T; ++t) yo[t] = acc && t < nt ? Y[yoff[t]] : make_float2(0.f, 0.f);
 #pragma unroll
         for (int t = 0; t < T; ++t)
-          if (t < nt) finish(sh[t], sl[t], yo[t], Y + ((size_t)(L0 + t) * rows + i));
+          if (t < nt) finish(sh[t], sl[t], yo[t], Y + yoff[t]);
       }
     }
   } else {
     // Y[(o * rows + i) * P + p], X[(o * din + l) * P + p], m = o * P + p over outer * P entries
-    const unsigned P = op.mode == 1 ? (unsigned)op.d0 : (unsigned)op.d0 * op.d1;
-    const unsigned outer = op.mode == 1 ? op.d2 : 1, din = op.mode == 1 ? op.d1 : op.d2;
+    const unsigned P = op.mode == 1 ? d0 : d0 * d1;
+    const unsigned outer = op.mode == 1 ? d2 : 1, din = op.mode == 1 ? d1 : d2;
+    // output offset of entry (o, p) of row i: (o rows + i) P + p, or with the slow
+    // coordinates swapped p + P (o + outer i) (mode 1) and c0 + d0 (i + rows c1) for
+    // p = c0 + d0 c1 (mode 2)
+    auto out12 = [&](unsigned o, unsigned pp, unsigned i) -> unsigned {
+      if (!swap) return (o * rows + i) * P + pp;
+      if (op.mode == 1) return pp + P * (o + outer * i);
+      const unsigned c1 = pp / d0;
+      return (pp - c1 * d0) + d0 * (i + rows * c1);
+    };
     const unsigned M = outer * P;
     const unsigned mb = (M + 32 * T - 1) / (32 * T);
     for (unsigned u = warp0; u < mb * rows; u += nwarps) {
@@ -293,12 +316,26 @@ __global__ void __launch_bounds__(256, 4) k_band_df(BandGroupDF g, int nrhs, con
           for (int t = 0; t < T; ++t) df_fma_acc(v, xp[32 * t], sh[t], sl[t]);
           xp += P;
         }
-        float2 *yp = Y + ((size_t)(o0 * rows + i) * P + p0);
+        unsigned yoff[T];
+        if (!swap || op.mode == 1) {
+          const unsigned y0 = out12(o0, p0, i);
+#pragma unroll
+          for (int t = 0; t < T; ++t) yoff[t] = y0 + 32 * t;
+        } else {
+          // mode 2, swapped: step c0 by 32 per t, carrying into c1
+          unsigned c1 = p0 / d0, c0 = p0 - c1 * d0;
+#pragma unroll
+          for (int t = 0; t < T; ++t) {
+            yoff[t] = c0 + d0 * (i + rows * c1);
+            c0 += 32;
+            while (c0 >= d0) { c0 -= d0; ++c1; }
+          }
+        }
         float2 yo[T];
 #pragma unroll
-        for (int t = 0; t < T; ++t) yo[t] = acc ? yp[32 * t] : make_float2(0.f, 0.f);
+        for (int t = 0; t < T; ++t) yo[t] = acc ? Y[yoff[t]] : make_float2(0.f, 0.f);
 #pragma unroll
-        for (int t = 0; t < T; ++t) finish(sh[t], sl[t], yo[t], yp + 32 * t);
+        for (int t = 0; t < T; ++t) finish(sh[t], sl[t], yo[t], Y + yoff[t]);
       } else {
         const unsigned m0 = c0 + lane;
         unsigned xo[T], yo[T];
@@ -309,7 +346,7 @@ __global__ void __launch_bounds__(256, 4) k_band_df(BandGroupDF g, int nrhs, con
           ok[t] = m < M;
           const unsigned o = ok[t] ? m / P : 0, pp = ok[t] ? m - o * P : 0;
           xo[t] = (o * din + l) * P + pp;
-          yo[t] = (o * rows + i) * P + pp;
+          yo[t] = out12(o, pp, i);
         }
         // unrolled by 4: the loads of four band columns are in flight together
 #pragma unroll 4
