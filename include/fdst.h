@@ -183,6 +183,21 @@ fdst_status fdst_get_timing(fdst_handle h, double *ms_matvec, double *ms_prec, d
 fdst_status fdst_get_kernel_timing(fdst_handle h, double *ms, int64_t *launches);
 
 /*
+ * fdst_convert - the element-wise precision conversions of the mixed-precision
+ * paths, done on the integer units from the IEEE 754 binary64/binary32
+ * encodings (GB300's conversion instructions run on its small FP64 unit):
+ *   kind 0: double -> float, rounded to nearest (ties to even);
+ *   kind 1: double -> double-float pair (hi, lo) as 2 floats per entry, hi the
+ *           truncated leading 24 bits, hi + lo within 2^-48 |x|;
+ *   kind 2: double-float pair (2 floats per entry) -> double (hi + lo, rounded);
+ *   kind 3: float -> double (exact).
+ * d_in, d_out: device buffers of n entries (caller-owned, not overlapping).
+ * Asynchronous on stream. FDST_INVALID_ARGUMENT for a kind outside 0..3,
+ * n < 0 or a NULL buffer with n > 0.
+ */
+fdst_status fdst_convert(int kind, const void *d_in, void *d_out, int64_t n, fdst_stream stream);
+
+/*
  * fdst_fd_apply_static - allocation-free FD solve of one Kronecker-sum block:
  *   s = (U_d x ... x U_1) Delta^{-1} (U_d x ... x U_1)^T r,
  *   Delta[i1, i2, (i3)] = sum_d coef[d] * lam_d[i_d],

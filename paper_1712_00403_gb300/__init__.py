@@ -59,7 +59,7 @@ class SolveInfo(ctypes.Structure):
 
 
 ENTRY_POINTS = ["fdst_setup", "fdst_destroy", "fdst_get_sizes", "fdst_apply_prec", "fdst_matvec", "fdst_solve",
-                "fdst_solve_host", "fdst_apply_prec_host", "fdst_set_timing", "fdst_get_timing", "fdst_get_kernel_timing",
+                "fdst_solve_host", "fdst_apply_prec_host", "fdst_set_timing", "fdst_get_timing", "fdst_get_kernel_timing", "fdst_convert",
                 "fdst_fd_apply_static", "fdst_batch_create", "fdst_batch_solve", "fdst_batch_info",
                 "fdst_batch_destroy", "fdst_server_create", "fdst_server_submit", "fdst_server_step",
                 "fdst_server_result", "fdst_server_stats", "fdst_server_destroy", "fdst_device_error",
@@ -104,6 +104,7 @@ def load_library(path=LIB_PATH):
     lib.fdst_get_timing.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d),
                                     ctypes.POINTER(i64), ctypes.POINTER(i64)]
     lib.fdst_get_kernel_timing.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_int64)]
+    lib.fdst_convert.argtypes = [i, vp, vp, ctypes.c_int64, vp]
     lib.fdst_last_error.restype = ctypes.c_char_p
     for name in ENTRY_POINTS[:-2]:
         getattr(lib, name).restype = ctypes.c_int
@@ -134,6 +135,24 @@ def fd_apply_static(U, lam, coef, r, s, stream=None):
     lp = (ctypes.c_void_p * 3)(*[_dptr(l).value for l in lam], *([None] * (3 - dim)))
     cf = (ctypes.c_double * 3)(*[float(c) for c in coef], *([0.0] * (3 - dim)))
     _check(lib.fdst_fd_apply_static(dim, n, up, lp, cf, _dptr(r), _dptr(s), _stream_ptr(stream)))
+
+
+CONVERT_F64_TO_F32, CONVERT_F64_TO_DF, CONVERT_DF_TO_F64, CONVERT_F32_TO_F64 = 0, 1, 2, 3
+
+
+def convert(kind, src, dst, stream=None):
+    """Element-wise precision conversion on the device (fdst_convert): src and dst
+    contiguous CUDA tensors; a double-float pair is two float32 entries."""
+    import torch
+    want = {CONVERT_F64_TO_F32: (torch.float64, torch.float32), CONVERT_F64_TO_DF: (torch.float64, torch.float32),
+            CONVERT_DF_TO_F64: (torch.float32, torch.float64), CONVERT_F32_TO_F64: (torch.float32, torch.float64)}
+    n = src.numel() if kind != CONVERT_DF_TO_F64 else src.numel() // 2
+    m = n * 2 if kind == CONVERT_F64_TO_DF else n
+    for t, dt, cnt in ((src, want[kind][0], src.numel()), (dst, want[kind][1], m)):
+        if not (t.is_cuda and t.is_contiguous() and t.dtype == dt and t.numel() >= cnt):
+            raise TypeError("convert: expected contiguous CUDA tensors of the kind's dtypes and sizes")
+    _check(load_library().fdst_convert(int(kind), ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(dst.data_ptr()),
+                                       n, _stream_ptr(stream)))
 
 
 def device_error():

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "ctx.h"
+#include "fp_bits.cuh"
 
 namespace fdst {
 
@@ -165,9 +166,7 @@ __global__ void k_bsplit(const BatchSeg *segs, int src) {
   if (*B.done) return;
   const double *x = B.vec[src];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < B.n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double v = x[i];
-    const float h = __double2float_rn(v);
-    B.x2[i] = make_float2(h, __double2float_rn(v - (double)h));
+    B.x2[i] = f64_split(x[i]);
   }
 }
 
@@ -176,8 +175,7 @@ __global__ void k_bjoin(const BatchSeg *segs, int dst) {
   if (*B.done) return;
   double *y = B.vec[dst];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < B.n; i += (int64_t)gridDim.x * blockDim.x) {
-    const float2 v = B.y2[i];
-    y[i] = (double)v.x + (double)v.y;
+    y[i] = f64_join(B.y2[i]);
   }
 }
 

@@ -729,6 +729,17 @@ const char *fdst_last_error(void) { return g_err.c_str(); }
 
 int64_t fdst_kernel_launches(void) { return (int64_t)launch_count(); }
 
+fdst_status fdst_convert(int kind, const void *d_in, void *d_out, int64_t n, fdst_stream stream) {
+  if (kind < 0 || kind > 3 || n < 0 || (n > 0 && (!d_in || !d_out))) {
+    set_error("fdst_convert: kind in 0..3, n >= 0 and device buffers required");
+    return FDST_INVALID_ARGUMENT;
+  }
+  if (n == 0) return FDST_OK;
+  launch_convert(kind, d_in, d_out, n, (cudaStream_t)stream);
+  CK(cudaGetLastError());
+  return FDST_OK;
+}
+
 fdst_status fdst_device_error(int *flag) {
   if (!flag) { set_error("NULL argument"); return FDST_INVALID_ARGUMENT; }
   return tc_error_flag(flag);

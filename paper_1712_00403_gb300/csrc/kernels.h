@@ -89,6 +89,9 @@ struct BandGroupDF {
   int threads = 128;                // at most 256
 };
 void launch_band_df(const BandGroupDF &g, int nrhs, const int *done, cudaStream_t s);
+// Element-wise conversions: kind 0 double -> float (nearest), 1 double -> FP32 pair,
+// 2 FP32 pair -> double, 3 float -> double.
+void launch_convert(int kind, const void *in, void *out, int64_t n, cudaStream_t s);
 // y2 = split(x) (double -> FP32 pair) and x = join(y2) over n entries per right-hand side.
 void launch_split_df(const double *x, float2 *y, int64_t n, int64_t stride, int nrhs, const int *done,
                      cudaStream_t s);

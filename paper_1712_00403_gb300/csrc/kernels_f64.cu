@@ -10,6 +10,7 @@
 #include <cmath>
 
 #include "df_arith.cuh"
+#include "fp_bits.cuh"
 #include "kernels.h"
 
 namespace fdst {
@@ -393,9 +394,7 @@ __global__ void k_split_df(const double *x, float2 *y, int64_t n, int64_t stride
   const double *xr = x + j * stride;
   float2 *yr = y + j * stride;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double v = xr[i];
-    const float h = __double2float_rn(v);
-    yr[i] = make_float2(h, __double2float_rn(v - (double)h));
+    yr[i] = f64_split(xr[i]);
   }
 }
 
@@ -405,9 +404,28 @@ __global__ void k_join_df(const float2 *x, double *y, int64_t n, int64_t stride,
   const float2 *xr = x + j * stride;
   double *yr = y + j * stride;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const float2 v = xr[i];
-    yr[i] = (double)v.x + (double)v.y;
+    yr[i] = f64_join(xr[i]);
   }
+}
+
+// Element-wise precision conversions (the integer-unit forms above) over n entries.
+__global__ void k_convert(int kind, const void *in, void *out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    switch (kind) {
+      case 0: static_cast<float *>(out)[i] = f64_to_f32_rn(static_cast<const double *>(in)[i]); break;
+      case 1: static_cast<float2 *>(out)[i] = f64_split(static_cast<const double *>(in)[i]); break;
+      case 2: static_cast<double *>(out)[i] = f64_join(static_cast<const float2 *>(in)[i]); break;
+      default: static_cast<double *>(out)[i] = f32_to_f64(static_cast<const float *>(in)[i]); break;
+    }
+  }
+}
+
+void launch_convert(int kind, const void *in, void *out, int64_t n, cudaStream_t s) {
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  count_launch(1);
+  k_convert<<<(unsigned)blocks, 256, 0, s>>>(kind, in, out, n);
 }
 
 void launch_split_df(const double *x, float2 *y, int64_t n, int64_t stride, int nrhs, const int *done,

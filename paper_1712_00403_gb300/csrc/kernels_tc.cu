@@ -45,6 +45,7 @@
 #include <string>
 #include <vector>
 
+#include "fp_bits.cuh"
 #include "internal.h"
 #include "kernels.h"
 #include "kernels_tc.h"
@@ -535,7 +536,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (n < Ncols) {
               float x = __uint_as_float(vals[qq]);
               if (lc) x = x / (lr + lc[n]);
-              double y = (double)x;
+              double y = f32_to_f64(x);
               if (sor) y *= sor[(int64_t)n * R];
               c64[(int64_t)n * cs] = y;
             }
@@ -667,7 +668,7 @@ __global__ void k_tc_convert(TcGroup g, const int *done) {
     const unsigned r = e / K, k = e - r * K;
     double x = src[e];
     if (P.scale_in) x *= P.scale_in[e];
-    dst[(size_t)r * P.lda + k] = (float)x;
+    dst[(size_t)r * P.lda + k] = f64_to_f32_rn(x);
   }
 }
 
