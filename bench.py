@@ -34,6 +34,13 @@ MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_NOMINAL_TFLOPS = 1.25     # GB300 FP64 (DFMA) nominal, profiling recipe table
 FP32_LANE_TOPS = 152 * 128 * 2.070e9 / 1e12   # SMs x FP32 lanes x max SM clock: lane operations per second
 TF32_OVER_BF16 = 1.1 / 2.25    # nominal dense TF32 / BF16 ratio
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant matvec kernel from
+# ncu captures of the kernels as they stand: k_band_df summed over the 21 launches of one
+# double-float matvec of the 40^3 cube (16 RHS, 1,673,830 entries each), scaled to a workload
+# by its entry count (every launch streams operands proportional to it); k_spmv_df per launch
+# of the 32^3 mapped operator at 4 RHS, the bench's own size.
+MATVEC_TRAFFIC = {"k_band_df": {"bytes": 5.7966e9, "entries": 1_673_830, "nrhs": 16, "launches": 21},
+                  "k_spmv_df": {"bytes": 18.4215e9, "entries": None, "nrhs": 4, "launches": 1}}
 
 
 def parse():
@@ -420,9 +427,20 @@ def run_gpu(args):
         achieved, unit = byts / (t_ms / 1e3) / 1e9, "GB/s"
     else:
         achieved = flops / (t_ms / 1e3) / 1e12
+    traffic, traffic_note = None, None
+    if per_mv >= per_pc and mv == fd.MV_DF64:
+        tr = MATVEC_TRAFFIC["k_spmv_df" if mapped else "k_band_df"]
+        if tr["nrhs"] == nrhs and (mapped and args.workload == "mapped_th_p3_32" or not mapped):
+            scale = 1.0 if tr["entries"] is None else P.n_total / tr["entries"]
+            # per launch, like achieved: a matvec's bytes over its launches
+            traffic = tr["bytes"] * scale / tr["launches"]
+            traffic_note = ("ncu DRAM bytes per launch (%s), %s" % (
+                "one launch at this size" if tr["entries"] is None else
+                "mean of the %d launches of one matvec captured on 1,673,830 entries per RHS, scaled by "
+                "entry count" % tr["launches"], "B"))
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
-                "traffic": None, "kernel": kern, "ms_per_launch": launch_ms, "ms_per_phase": t_ms,
-                "peak_source": peak_note}
+                "traffic": traffic, "traffic_note": traffic_note, "kernel": kern, "ms_per_launch": launch_ms,
+                "ms_per_phase": t_ms, "peak_source": peak_note}
 
     # end to end through the host-pointer entry point (pinned host buffers)
     bh = torch.empty(b.numel(), dtype=torch.float64, pin_memory=True)
