@@ -25,6 +25,8 @@ CASES = [
     problem_spec(3, 2, 9),             # 3D, rows span several tiles with a ragged tail
     problem_spec(2, 2, 6, "RT"),       # 2D Raviart-Thomas with Nitsche terms
     problem_spec(2, 4, (4, 7), "RT"),
+    problem_spec(3, 2, 4, "RT"),       # 3D Raviart-Thomas: Nitsche terms in two directions per component
+    problem_spec(3, 3, (3, 4, 5), "RT"),
     problem_spec(2, 3, (26, 5)),       # n_v = 53 > 48: Householder + implicit-QL eigensolver path
 ]
 
@@ -74,8 +76,8 @@ def test_matvec_constant_pressure_kernel():
     assert float(y.abs().max()) < 1e-12
 
 
-@pytest.mark.parametrize("spec", [problem_spec(2, 2, 16), problem_spec(3, 2, 4), problem_spec(2, 2, 8, "RT")],
-                         ids=_ids)
+@pytest.mark.parametrize("spec", [problem_spec(2, 2, 16), problem_spec(3, 2, 4), problem_spec(2, 2, 8, "RT"),
+                                  problem_spec(3, 2, 4, "RT")], ids=_ids)
 def test_minres_f64_matches_oracle(spec):
     P = gpu_problem(spec, max_rhs=2)
     S = oracle_problem(spec)

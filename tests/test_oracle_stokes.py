@@ -19,7 +19,8 @@ def test_kronecker_blocks_vs_brute_force_quadrature(dim, p, n_el, velocity):
 
 
 @pytest.mark.parametrize("dim,disc,velocity", [(2, "TH", "th"), (3, "TH", "th"), (2, "RT", "th"),
-                                               (2, "TH", "max_smooth"), (3, "TH", "max_smooth")])
+                                               (3, "RT", "th"), (2, "TH", "max_smooth"),
+                                               (3, "TH", "max_smooth")])
 def test_symmetry_nullspace_and_matvec(dim, disc, velocity):
     S = stokes.build_uniform(3 if dim == 3 else 4, 2, dim, disc, velocity=velocity)
     A = stokes.assembled(S)
@@ -37,22 +38,23 @@ def test_symmetry_nullspace_and_matvec(dim, disc, velocity):
         np.testing.assert_allclose(A[off[k]:off[k + 1], off[k]:off[k + 1]], stokes.pv_matrix(S, k), atol=0)
 
 
-@pytest.mark.parametrize("disc", ["TH", "RT"])
-def test_preconditioner_blocks_spd(disc):
-    S = stokes.build_uniform(3, 2, 2, disc)
-    for k in range(2):
+@pytest.mark.parametrize("disc,dim", [("TH", 2), ("RT", 2), ("RT", 3)])
+def test_preconditioner_blocks_spd(disc, dim):
+    S = stokes.build_uniform(3, 2, dim, disc)
+    for k in range(dim):
         assert np.linalg.eigvalsh(stokes.pv_matrix(S, k)).min() > 0
     assert np.linalg.eigvalsh(kron.kron_matrix(stokes.pq_factors(S))).min() > 0
 
 
-def test_rt_divergence_lands_in_pressure_space():
+@pytest.mark.parametrize("dim,n_el", [(2, 4), (3, 3)])
+def test_rt_divergence_lands_in_pressure_space(dim, n_el):
     """RT (Sec. 2.2.2): d/d eta_k of the direction-k factor space is the pressure
     space, so the velocity-pressure coupling is B = -P_Q D with D the exact
     discrete divergence; hence P_Q^{-1} B has integer-free entries that
     reproduce the divergence of a field exactly."""
-    S = stokes.build_uniform(4, 2, 2, "RT")
+    S = stokes.build_uniform(n_el, 2, dim, "RT")
     A = stokes.assembled(S)
-    nv = sum(S.block_sizes[:2])
+    nv = sum(S.block_sizes[:dim])
     B = A[nv:, :nv]
     D = -np.linalg.solve(kron.kron_matrix(stokes.pq_factors(S)), B)
     # a velocity field with zero discrete divergence has B v = 0 and D v = 0 simultaneously
