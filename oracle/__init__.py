@@ -13,6 +13,7 @@ Stokes system based on the Fast Diagonalization method", arXiv 1712.00403):
 * ``kron``        - Kronecker identities and the FD solve (Sec. 2.3, Sec. 5.2, Algorithm 1)
 * ``stokes``      - Taylor-Hood / Raviart-Thomas Stokes operator, P_V, P_Q (Sec. 3-5)
 * ``minres``      - preconditioned MINRES (Paige-Saunders; cited in Sec. 4)
+* ``gmres``       - left-preconditioned GMRES (Saad-Schultz; cited in Sec. 4) for P_T and P_C
 * ``geometry``    - mapped geometry, separable approximation, P_D^G (Sec. 6, Appendix)
 
 It shares no code with the CUDA path; the only module both sides use is the

@@ -212,6 +212,80 @@ def assembled(S):
 
 # ---------------------------------------------------------------- brute force
 
+def apply_B(S, u_blocks):
+    """B u (pressure block) for velocity blocks u_k (eq. Stokes_system)."""
+    return sum(_apply_terms(b_block_terms(S, r), u_blocks[r]) for r in range(S.dim))
+
+
+def apply_Bt(S, q):
+    """B^T q (velocity blocks) for a pressure block q."""
+    return [_apply_terms_T(b_block_terms(S, r), q) for r in range(S.dim)]
+
+
+def _pv_solve(S, blocks, method):
+    out = []
+    for k in range(S.dim):
+        Ks, Ms, coef = pv_pencils(S, k)
+        out.append(kron.fd_solve(Ks, Ms, coef, blocks[k]) if method == "fd"
+                   else kron.dense_solve(Ks, Ms, coef, blocks[k]))
+    return out
+
+
+def _pq_solve(S, rq, method):
+    Mp = pq_factors(S)
+    return kron.kron_mass_solve(Mp, rq) if method == "fd" else np.linalg.solve(kron.kron_matrix(Mp), rq)
+
+
+def apply_PT_inv(S, r, method="fd"):
+    """s = P_T^{-1} r for the block upper-triangular P_T = [[P_V, B^T], [0, -P_Q]]
+    (eq. P_T): back substitution, q = -P_Q^{-1} r_q, then u = P_V^{-1} (r_u - B^T q)."""
+    blocks = S.split(np.asarray(r, float))
+    q = -_pq_solve(S, blocks[-1], method)
+    bt = apply_Bt(S, q)
+    u = _pv_solve(S, [blocks[k] - bt[k] for k in range(S.dim)], method)
+    return np.concatenate(u + [q])
+
+
+def apply_PC_inv(S, r, method="fd"):
+    """s = P_C^{-1} r for P_C = [[P_V, B^T], [B, B P_V^{-1} B^T - P_Q]] (eq. P_C) by the
+    paper's product form of its inverse, applied right to left: z = P_V^{-1} r_u;
+    t = r_q - B z; q = -P_Q^{-1} t; u = z - P_V^{-1} B^T q."""
+    blocks = S.split(np.asarray(r, float))
+    z = _pv_solve(S, blocks[:S.dim], method)
+    q = -_pq_solve(S, blocks[-1] - apply_B(S, z), method)
+    w = _pv_solve(S, apply_Bt(S, q), method)
+    return np.concatenate([z[k] - w[k] for k in range(S.dim)] + [q])
+
+
+def pt_matrix(S):
+    """Dense P_T (tiny sizes only)."""
+    return _block_prec_matrix(S, lower=False)
+
+
+def pc_matrix(S):
+    """Dense P_C (tiny sizes only)."""
+    return _block_prec_matrix(S, lower=True)
+
+
+def _block_prec_matrix(S, lower):
+    d = S.dim
+    off = np.concatenate([[0], np.cumsum(S.block_sizes)])
+    A = assembled(S)
+    PV = np.zeros((off[d], off[d]))
+    for k in range(d):
+        PV[off[k]:off[k + 1], off[k]:off[k + 1]] = pv_matrix(S, k)
+    PQ = kron.kron_matrix(pq_factors(S))
+    Bt = A[:off[d], off[d]:]
+    P = np.zeros_like(A)
+    P[:off[d], :off[d]] = PV
+    P[:off[d], off[d]:] = Bt
+    P[off[d]:, off[d]:] = -PQ
+    if lower:
+        P[off[d]:, :off[d]] = Bt.T
+        P[off[d]:, off[d]:] += Bt.T @ np.linalg.solve(PV, Bt)
+    return P
+
+
 def brute_force_TH(S, nu=1.0):
     """Dense A and B of the TH system by element-wise tensor Gauss quadrature of
     a(w,v) = int 2 nu grad^s w : grad^s v and b(v,q) = -int q div v, evaluating
