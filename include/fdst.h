@@ -61,6 +61,9 @@ enum { FDST_VARIANT_PD = 0, FDST_VARIANT_PD_GEO = 1 };      /* P_D (Sec. 5) or P
  * additions on the FP32 units). fdst_solve always checks the true residual
  * with the FP64 matvec. */
 enum { FDST_MV_F64 = 0, FDST_MV_DF64 = 1 };
+/* Block preconditioners for GMRES (Sec. 4): P_T = [[P_V, B^T], [0, -P_Q]] (block
+ * triangular) and P_C = [[P_V, B^T], [B, B P_V^{-1} B^T - P_Q]] (constraint). */
+enum { FDST_PREC_PT = 0, FDST_PREC_PC = 1 };
 
 typedef struct {
   int dim;                 /* 2 or 3 */
@@ -149,6 +152,42 @@ fdst_status fdst_matvec(fdst_handle h, const double *d_x, double *d_y, int nrhs,
  */
 fdst_status fdst_solve(fdst_handle h, const double *d_b, double *d_x, int nrhs, double tol, int maxit,
                        fdst_solve_info *info, fdst_stream stream);
+
+/*
+ * fdst_apply_block_prec - s = P^{-1} r for P = P_T (back substitution: q =
+ * -P_Q^{-1} r_q, u = P_V^{-1}(r_u - B^T q)) or P = P_C (the paper's product
+ * form: z = P_V^{-1} r_u, q = -P_Q^{-1}(r_q - B z), u = z - P_V^{-1} B^T q),
+ * Sec. 4; P_V^{-1}, P_Q^{-1} the handle's FD applies, B and B^T in its matvec
+ * precision. Identity map only. Device vectors of nrhs block vectors; r and s
+ * must not alias. Asynchronous on stream (the first call builds the B / B^T
+ * plans and the GMRES work vectors).
+ */
+fdst_status fdst_apply_block_prec(fdst_handle h, int prec, const double *d_r, double *d_s, int nrhs,
+                                  fdst_stream stream);
+
+/*
+ * fdst_solve_gmres - left-preconditioned GMRES (Saad-Schultz) with P_T or P_C
+ * (Sec. 4; eq. P_T, eq. P_C, applied through the product form of P_C^{-1}),
+ * their P_V, P_Q blocks the handle's FD applies and B, B^T the Kronecker parts
+ * of the operator; identity map only (FDST_NOT_SUPPORTED on mapped geometry).
+ *   b, x:    device block vectors (nrhs back to back), x the initial guess in and
+ *            the solution out, as fdst_solve.
+ *   restart: Krylov basis size m in [1, 255]; the handle keeps a basis of
+ *            (m + 1) x max_rhs block vectors (allocated on first use, grown when
+ *            a larger m is asked for) and restarts from the current iterate when
+ *            it is full.
+ * Arnoldi with classical Gram-Schmidt applied twice, Givens rotations on the
+ * Hessenberg matrix; the estimate is ||P^{-1}(b - A x_j)|| / ||P^{-1} b||. When
+ * it meets the threshold (tol at first) x_j is formed and its FP64 true
+ * residual ||b - A x_j|| / ||b|| computed: <= tol ends that right-hand side,
+ * otherwise the threshold drops to 0.5 tau tol / true and the Arnoldi process
+ * continues. info[r]: iterations, status, eta_rel (the estimate),
+ * true_rel_res, iterations_estimate (first iteration with estimate <= tol).
+ * Synchronizes the stream. Matvecs in the iterations use the handle's matvec
+ * precision.
+ */
+fdst_status fdst_solve_gmres(fdst_handle h, int prec, const double *d_b, double *d_x, int nrhs, double tol,
+                             int maxit, int restart, fdst_solve_info *info, fdst_stream stream);
 
 /*
  * fdst_solve_host - fdst_solve with host vectors: copies h_b (and h_x as the

@@ -20,6 +20,7 @@ HAS_TC = True        # the split-TF32 tcgen05 FD contraction is built (sm_103a)
 GEOM_IDENTITY, GEOM_SINE_BUMP = 0, 1
 VARIANT_PD, VARIANT_PD_GEO = 0, 1
 MV_F64, MV_DF64 = 0, 1
+PREC_PT, PREC_PC = 0, 1
 
 STATUS = {0: "OK", 1: "INVALID_ARGUMENT", 2: "NOT_SPD", 3: "OUT_OF_MEMORY", 4: "CUDA_ERROR", 5: "MAXIT",
           6: "STAGNATION", 7: "BREAKDOWN", 8: "TIMEOUT", 9: "NAN_DETECTED", 10: "ADMISSION_REJECTED",
@@ -59,7 +60,7 @@ class SolveInfo(ctypes.Structure):
 
 
 ENTRY_POINTS = ["fdst_setup", "fdst_destroy", "fdst_get_sizes", "fdst_apply_prec", "fdst_matvec", "fdst_solve",
-                "fdst_solve_host", "fdst_apply_prec_host", "fdst_set_timing", "fdst_get_timing", "fdst_get_kernel_timing", "fdst_convert",
+                "fdst_solve_host", "fdst_apply_prec_host", "fdst_solve_gmres", "fdst_apply_block_prec", "fdst_set_timing", "fdst_get_timing", "fdst_get_kernel_timing", "fdst_convert",
                 "fdst_fd_apply_static", "fdst_batch_create", "fdst_batch_solve", "fdst_batch_info",
                 "fdst_batch_destroy", "fdst_server_create", "fdst_server_submit", "fdst_server_step",
                 "fdst_server_result", "fdst_server_stats", "fdst_server_destroy", "fdst_device_error",
@@ -83,6 +84,8 @@ def load_library(path=LIB_PATH):
     lib.fdst_apply_prec.argtypes = [vp, vp, vp, i, vp]
     lib.fdst_matvec.argtypes = [vp, vp, vp, i, vp]
     lib.fdst_solve.argtypes = [vp, vp, vp, i, d, i, ctypes.POINTER(SolveInfo), vp]
+    lib.fdst_solve_gmres.argtypes = [vp, i, vp, vp, i, d, i, i, ctypes.POINTER(SolveInfo), vp]
+    lib.fdst_apply_block_prec.argtypes = [vp, i, vp, vp, i, vp]
     lib.fdst_solve_host.argtypes = [vp, vp, vp, i, d, i, ctypes.POINTER(SolveInfo), vp]
     lib.fdst_apply_prec_host.argtypes = [vp, vp, vp, i, vp]
     lib.fdst_set_timing.argtypes = [vp, i]
@@ -243,6 +246,23 @@ class Stokes:
 
     def matvec(self, x, y, stream=None):
         _check(_lib.fdst_matvec(self._h, _dptr(x), _dptr(y), self._nrhs(x), _stream_ptr(stream)))
+
+    def apply_block_prec(self, r, s, prec=None, stream=None):
+        """s = P^{-1} r for P_T (PREC_PT, default) or P_C (PREC_PC)."""
+        _check(_lib.fdst_apply_block_prec(self._h, PREC_PT if prec is None else prec, _dptr(r), _dptr(s),
+                                          self._nrhs(r), _stream_ptr(stream)))
+
+    def solve_gmres(self, b, x, prec=None, tol=1e-8, maxit=1000, restart=60, stream=None, check=False):
+        """Left-preconditioned GMRES with the block triangular (PREC_PT) or constraint
+        (PREC_PC) preconditioner built from this handle's FD blocks (fdst_solve_gmres)."""
+        n = self._nrhs(b)
+        info = (SolveInfo * n)()
+        code = _lib.fdst_solve_gmres(self._h, PREC_PT if prec is None else prec, _dptr(b), _dptr(x), n, tol, maxit,
+                                     restart, info, _stream_ptr(stream))
+        if check:
+            _check(code)
+        return [dict(iterations=i.iterations, status=STATUS.get(i.status, i.status), eta_rel=i.eta_rel,
+                     true_rel_res=i.true_rel_res, iterations_estimate=i.iterations_estimate) for i in info]
 
     def solve(self, b, x, tol=1e-8, maxit=1000, stream=None, check=False):
         n = self._nrhs(b)

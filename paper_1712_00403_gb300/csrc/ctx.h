@@ -45,6 +45,13 @@ struct BandDev {
   std::vector<double> hvals;   // host copy of vals (rows x w)
 };
 
+// One Kronecker term of the operator: block dst += coef (F2 x F1 x F0) block src.
+struct Term {
+  int dst, src;
+  double coef;
+  int f[3];  // band ids (mode order); -1 for the unused mode in 2D
+};
+
 struct PlanOp {
   int stage;
   int in_kind, in_id;    // kind: 0 = user x block, 1 = T1 buffer, 2 = G buffer
@@ -87,6 +94,20 @@ struct fdst_ctx {
   // the same ops for the double-float matvec: in 3D the T1 buffers hold (l1, l2, i0)
   // with l1 slowest, so that the stage-2 products contract the slowest index
   std::vector<fdst::PlanOp> plan_df;
+  std::vector<fdst::Term> terms;   // the operator's Kronecker terms (identity map)
+  // the B and B^T parts of the operator alone (block preconditioners P_T, P_C), built
+  // with the GMRES workspace on first use
+  struct SubPlan {
+    std::vector<fdst::PlanOp> ops, ops_df;
+    std::vector<int64_t> t1_size, g_size;
+    std::vector<double *> t1, g;
+  } plan_b, plan_bt;
+  // GMRES: Krylov basis of gm_cap + 1 block vectors (max_rhs right-hand sides each),
+  // three work vectors, device scalars
+  int gm_cap = 0;
+  double *gm_V = nullptr, *gm_w = nullptr, *gm_t = nullptr, *gm_u = nullptr;
+  double *gm_coef = nullptr, *gm_part = nullptr, *gm_scal = nullptr;
+  int *gm_mask = nullptr;
   std::vector<double *> t1, g;
   std::vector<int64_t> t1_size, g_size;
   float2 *x2 = nullptr, *y2 = nullptr;   // double-float copies of the matvec input / output
@@ -148,7 +169,9 @@ inline fdst_status upload(fdst_ctx *h, T **p, const std::vector<T> &v) {
   } while (0)
 
 // Preconditioner apply and matvec of one handle (fdst.cu); exact = true forces FP64.
-fdst_status run_apply(fdst_ctx *h, const double *r, double *s, int nrhs, const int *done, cudaStream_t st);
+// s = P_D^{-1} r on the blocks in block_mask (bit b: block b; velocity 0..dim-1, pressure dim).
+fdst_status run_apply(fdst_ctx *h, const double *r, double *s, int nrhs, const int *done, cudaStream_t st,
+                      unsigned block_mask = ~0u);
 fdst_status run_matvec(fdst_ctx *h, const double *x, double *y, int nrhs, const int *done, cudaStream_t st,
                        bool exact = false);
 

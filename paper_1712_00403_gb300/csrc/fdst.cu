@@ -240,11 +240,145 @@ static fdst_status build_fd(fdst_ctx *h) {
 
 // ------------------------------------------------------------------ setup: matvec plan
 
-struct Term {
-  int dst, src;
-  double coef;
-  int f[3];  // band ids (mode order); -1 for the unused mode in 2D
-};
+// The common-subexpression plan of a set of Kronecker terms: stage 1 = distinct
+// (src, f0); stage 2 (3D) = each term into the accumulator G(dst, f2); stage 3 =
+// dst += G x_3 f2. In 2D stage 2 writes dst. Also its double-float form
+// (coefficients folded into the band values; in 3D T1 held with its slow
+// coordinates swapped). T1/G buffer sizes per right-hand side are appended.
+static fdst_status build_plan(fdst_ctx *h, const std::vector<Term> &terms, std::vector<PlanOp> &plan,
+                              std::vector<PlanOp> &plan_df, std::vector<int64_t> &t1_size,
+                              std::vector<int64_t> &g_size) {
+  const int dim = h->dim;
+  plan.clear();
+  plan_df.clear();
+  t1_size.clear();
+  g_size.clear();
+  std::map<std::pair<int, int>, int> t1_ids;
+  std::map<std::pair<int, int>, int> g_ids;
+  std::vector<PlanOp> st1, st2, st3;
+  std::vector<int> g_first;            // whether the G buffer was written yet
+  std::vector<int> dst_written(dim + 1, 0);
+  auto srcdims = [&](int b, int out[3]) { for (int e = 0; e < 3; ++e) out[e] = h->shape[b][e]; };
+  for (const Term &t : terms) {
+    auto k1 = std::make_pair(t.src, t.f[0]);
+    int t1;
+    auto it = t1_ids.find(k1);
+    if (it == t1_ids.end()) {
+      t1 = (int)t1_size.size();
+      t1_ids[k1] = t1;
+      PlanOp op{};
+      op.stage = 1;
+      op.in_kind = 0; op.in_id = t.src;
+      op.out_kind = 1; op.out_id = t1;
+      op.band = t.f[0]; op.mode = 0;
+      srcdims(t.src, op.dims);
+      op.coef = 1.0; op.accumulate = 0;
+      st1.push_back(op);
+      int64_t sz = (int64_t)h->bands[t.f[0]].rows * op.dims[1] * op.dims[2];
+      t1_size.push_back(sz);
+    } else t1 = it->second;
+    int d1[3];
+    srcdims(t.src, d1);
+    d1[0] = h->bands[t.f[0]].rows;
+    if (dim == 2) {
+      PlanOp op{};
+      op.stage = 2;
+      op.in_kind = 1; op.in_id = t1;
+      op.out_kind = 3; op.out_id = t.dst;
+      op.band = t.f[1]; op.mode = 1;
+      for (int e = 0; e < 3; ++e) op.dims[e] = d1[e];
+      op.coef = t.coef;
+      op.accumulate = dst_written[t.dst];
+      dst_written[t.dst] = 1;
+      st2.push_back(op);
+    } else {
+      auto kg = std::make_pair(t.dst, t.f[2]);
+      int gid;
+      auto ig = g_ids.find(kg);
+      if (ig == g_ids.end()) {
+        gid = (int)g_size.size();
+        g_ids[kg] = gid;
+        g_size.push_back((int64_t)d1[0] * h->bands[t.f[1]].rows * d1[2]);
+        g_first.push_back(0);
+        PlanOp op3{};
+        op3.stage = 3;
+        op3.in_kind = 2; op3.in_id = gid;
+        op3.out_kind = 3; op3.out_id = t.dst;
+        op3.band = t.f[2]; op3.mode = 2;
+        op3.dims[0] = d1[0]; op3.dims[1] = h->bands[t.f[1]].rows; op3.dims[2] = d1[2];
+        op3.coef = 1.0;
+        op3.accumulate = dst_written[t.dst];
+        dst_written[t.dst] = 1;
+        st3.push_back(op3);
+      } else gid = ig->second;
+      PlanOp op{};
+      op.stage = 2;
+      op.in_kind = 1; op.in_id = t1;
+      op.out_kind = 2; op.out_id = gid;
+      op.band = t.f[1]; op.mode = 1;
+      for (int e = 0; e < 3; ++e) op.dims[e] = d1[e];
+      op.coef = t.coef;
+      op.accumulate = g_first[gid];
+      g_first[gid] = 1;
+      st2.push_back(op);
+    }
+  }
+  plan.clear();
+  plan.insert(plan.end(), st1.begin(), st1.end());
+  plan.insert(plan.end(), st2.begin(), st2.end());
+  plan.insert(plan.end(), st3.begin(), st3.end());
+  // double-float band values with the op's coefficient folded in (the products are
+  // then summed without a final scaling); one copy per distinct (band, coefficient)
+  std::map<std::pair<int, double>, const float2 *> scaled;
+  for (auto &op : plan) {
+    const auto key = std::make_pair(op.band, op.coef);
+    auto it = scaled.find(key);
+    if (it == scaled.end()) {
+      const BandDev &bd = h->bands[op.band];
+      std::vector<float2> v(bd.hvals.size());
+      for (size_t k = 0; k < v.size(); ++k) {
+        const double a = op.coef * bd.hvals[k];
+        const float hi = (float)a;
+        v[k] = make_float2(hi, (float)(a - (double)hi));
+      }
+      float2 *d = nullptr;
+      TRY(upload(h, &d, v));
+      it = scaled.emplace(key, d).first;
+    }
+    op.vals_df = it->second;
+  }
+  // double-float plan: stage 1 writes T1 as (l1, l2, i0) (slow coordinates swapped),
+  // stage 2 then contracts l1 as the slowest index (mode 2 over (i0, l2, l1)) and
+  // writes G in its usual (i0, i1, l2) order by swapping back
+  plan_df = plan;
+  if (dim == 3)
+    for (auto &op : plan_df) {
+      if (op.stage == 1) {
+        op.swap = 1;
+      } else if (op.stage == 2) {
+        op.mode = 2;
+        std::swap(op.dims[1], op.dims[2]);
+        op.swap = 1;
+      }
+    }
+  return FDST_OK;
+}
+
+static fdst_status alloc_plan_buffers(fdst_ctx *h, const std::vector<int64_t> &t1_size,
+                                      const std::vector<int64_t> &g_size, std::vector<double *> &t1,
+                                      std::vector<double *> &g) {
+  for (int64_t sz : t1_size) {
+    double *b = nullptr;
+    TRY(dalloc(h, &b, (size_t)sz * h->max_rhs));
+    t1.push_back(b);
+  }
+  for (int64_t sz : g_size) {
+    double *b = nullptr;
+    TRY(dalloc(h, &b, (size_t)sz * h->max_rhs));
+    g.push_back(b);
+  }
+  return FDST_OK;
+}
 
 static fdst_status build_matvec(fdst_ctx *h) {
   const int dim = h->dim, p = h->p, npts = p + 2;
@@ -318,126 +452,9 @@ static fdst_status build_matvec(fdst_ctx *h) {
     for (int e = 0; e < dim; ++e) TRY(band_of(h->pres[e], 0, h->vel[r][e], e == r, &t.f[e]));
     terms.push_back(t);
   }
-  // ---- common-subexpression plan: stage 1 = distinct (src, f0); stage 2 (3D) = each term
-  // into the accumulator G(dst, f2); stage 3 = dst += G x_3 f2. In 2D stage 2 writes dst.
-  std::map<std::pair<int, int>, int> t1_ids;
-  std::map<std::pair<int, int>, int> g_ids;
-  std::vector<PlanOp> st1, st2, st3;
-  std::vector<int> g_first;            // whether the G buffer was written yet
-  std::vector<int> dst_written(dim + 1, 0);
-  auto srcdims = [&](int b, int out[3]) { for (int e = 0; e < 3; ++e) out[e] = h->shape[b][e]; };
-  for (const Term &t : terms) {
-    auto k1 = std::make_pair(t.src, t.f[0]);
-    int t1;
-    auto it = t1_ids.find(k1);
-    if (it == t1_ids.end()) {
-      t1 = (int)h->t1_size.size();
-      t1_ids[k1] = t1;
-      PlanOp op{};
-      op.stage = 1;
-      op.in_kind = 0; op.in_id = t.src;
-      op.out_kind = 1; op.out_id = t1;
-      op.band = t.f[0]; op.mode = 0;
-      srcdims(t.src, op.dims);
-      op.coef = 1.0; op.accumulate = 0;
-      st1.push_back(op);
-      int64_t sz = (int64_t)h->bands[t.f[0]].rows * op.dims[1] * op.dims[2];
-      h->t1_size.push_back(sz);
-    } else t1 = it->second;
-    int d1[3];
-    srcdims(t.src, d1);
-    d1[0] = h->bands[t.f[0]].rows;
-    if (dim == 2) {
-      PlanOp op{};
-      op.stage = 2;
-      op.in_kind = 1; op.in_id = t1;
-      op.out_kind = 3; op.out_id = t.dst;
-      op.band = t.f[1]; op.mode = 1;
-      for (int e = 0; e < 3; ++e) op.dims[e] = d1[e];
-      op.coef = t.coef;
-      op.accumulate = dst_written[t.dst];
-      dst_written[t.dst] = 1;
-      st2.push_back(op);
-    } else {
-      auto kg = std::make_pair(t.dst, t.f[2]);
-      int gid;
-      auto ig = g_ids.find(kg);
-      if (ig == g_ids.end()) {
-        gid = (int)h->g_size.size();
-        g_ids[kg] = gid;
-        h->g_size.push_back((int64_t)d1[0] * h->bands[t.f[1]].rows * d1[2]);
-        g_first.push_back(0);
-        PlanOp op3{};
-        op3.stage = 3;
-        op3.in_kind = 2; op3.in_id = gid;
-        op3.out_kind = 3; op3.out_id = t.dst;
-        op3.band = t.f[2]; op3.mode = 2;
-        op3.dims[0] = d1[0]; op3.dims[1] = h->bands[t.f[1]].rows; op3.dims[2] = d1[2];
-        op3.coef = 1.0;
-        op3.accumulate = dst_written[t.dst];
-        dst_written[t.dst] = 1;
-        st3.push_back(op3);
-      } else gid = ig->second;
-      PlanOp op{};
-      op.stage = 2;
-      op.in_kind = 1; op.in_id = t1;
-      op.out_kind = 2; op.out_id = gid;
-      op.band = t.f[1]; op.mode = 1;
-      for (int e = 0; e < 3; ++e) op.dims[e] = d1[e];
-      op.coef = t.coef;
-      op.accumulate = g_first[gid];
-      g_first[gid] = 1;
-      st2.push_back(op);
-    }
-  }
-  h->plan.clear();
-  h->plan.insert(h->plan.end(), st1.begin(), st1.end());
-  h->plan.insert(h->plan.end(), st2.begin(), st2.end());
-  h->plan.insert(h->plan.end(), st3.begin(), st3.end());
-  // double-float band values with the op's coefficient folded in (the products are
-  // then summed without a final scaling); one copy per distinct (band, coefficient)
-  std::map<std::pair<int, double>, const float2 *> scaled;
-  for (auto &op : h->plan) {
-    const auto key = std::make_pair(op.band, op.coef);
-    auto it = scaled.find(key);
-    if (it == scaled.end()) {
-      const BandDev &bd = h->bands[op.band];
-      std::vector<float2> v(bd.hvals.size());
-      for (size_t k = 0; k < v.size(); ++k) {
-        const double a = op.coef * bd.hvals[k];
-        const float hi = (float)a;
-        v[k] = make_float2(hi, (float)(a - (double)hi));
-      }
-      float2 *d = nullptr;
-      TRY(upload(h, &d, v));
-      it = scaled.emplace(key, d).first;
-    }
-    op.vals_df = it->second;
-  }
-  // double-float plan: stage 1 writes T1 as (l1, l2, i0) (slow coordinates swapped),
-  // stage 2 then contracts l1 as the slowest index (mode 2 over (i0, l2, l1)) and
-  // writes G in its usual (i0, i1, l2) order by swapping back
-  h->plan_df = h->plan;
-  if (dim == 3)
-    for (auto &op : h->plan_df) {
-      if (op.stage == 1) {
-        op.swap = 1;
-      } else if (op.stage == 2) {
-        op.mode = 2;
-        std::swap(op.dims[1], op.dims[2]);
-        op.swap = 1;
-      }
-    }
-  for (int64_t sz : h->t1_size) {
-    double *b = nullptr;
-    TRY(dalloc(h, &b, (size_t)sz * h->max_rhs));
-    h->t1.push_back(b);
-  }
-  for (int64_t sz : h->g_size) {
-    double *b = nullptr;
-    TRY(dalloc(h, &b, (size_t)sz * h->max_rhs));
-    h->g.push_back(b);
-  }
+  h->terms = terms;
+  TRY(build_plan(h, terms, h->plan, h->plan_df, h->t1_size, h->g_size));
+  TRY(alloc_plan_buffers(h, h->t1_size, h->g_size, h->t1, h->g));
   if (h->desc.matvec_precision == FDST_MV_DF64) {
     TRY(dalloc(h, &h->x2, (size_t)h->n_total * h->max_rhs));
     TRY(dalloc(h, &h->y2, (size_t)h->n_total * h->max_rhs));
@@ -495,9 +512,19 @@ static fdst_status tc_prepare(fdst_ctx *h) {
 
 // ------------------------------------------------------------------ execution
 
-fdst_status run_apply(fdst_ctx *h, const double *r, double *s, int nrhs, const int *done, cudaStream_t st) {
+// The block of the block vector a chain applies to (velocity components 0..dim-1, pressure dim).
+static int chain_block(const fdst_ctx *h, const FdChain &c) {
+  for (int b = 0; b <= h->dim; ++b)
+    if (h->off[b] == c.off) return b;
+  return -1;
+}
+
+fdst_status run_apply(fdst_ctx *h, const double *r, double *s, int nrhs, const int *done, cudaStream_t st,
+                      unsigned block_mask) {
+  auto in_mask = [&](const FdChain &c) { return ((block_mask >> chain_block(h, c)) & 1u) != 0; };
   int maxsteps = 0;
-  for (auto &c : h->chains) maxsteps = std::max(maxsteps, c.nsteps);
+  for (auto &c : h->chains)
+    if (in_mask(c)) maxsteps = std::max(maxsteps, c.nsteps);
   const bool tc = h->desc.fd_precision != FDST_FD_F64;
   for (int j = 0; j < maxsteps; ++j) {
     if (tc) {
@@ -505,7 +532,7 @@ fdst_status run_apply(fdst_ctx *h, const double *r, double *s, int nrhs, const i
       g.split = h->desc.fd_precision == FDST_FD_BF16X6 ? 1 : 0;
       for (size_t ci = 0; ci < h->chains.size(); ++ci) {
         const FdChain &c = h->chains[ci];
-        if (j >= c.nsteps) continue;
+        if (j >= c.nsteps || !in_mask(c)) continue;
         TcProb &P = g.p[g.nprob++];
         const bool first = j == 0, last = j == c.nsteps - 1;
         if (first) {
@@ -534,11 +561,11 @@ fdst_status run_apply(fdst_ctx *h, const double *r, double *s, int nrhs, const i
         P.scale_in = first ? c.scale : nullptr;
         P.scale_out = last ? c.scale : nullptr;
       }
-      TRY(launch_gemm_tc(g, nrhs, done, st));
+      if (g.nprob) TRY(launch_gemm_tc(g, nrhs, done, st));
     } else {
       GemmGroup g;
       for (auto &c : h->chains) {
-        if (j >= c.nsteps) continue;
+        if (j >= c.nsteps || !in_mask(c)) continue;
         GemmProb &P = g.p[g.nprob++];
         P.A = j == 0 ? r + c.off : h->work[(j - 1) % 2] + c.off;
         P.C = j == c.nsteps - 1 ? s + c.off : h->work[j % 2] + c.off;
@@ -549,7 +576,7 @@ fdst_status run_apply(fdst_ctx *h, const double *r, double *s, int nrhs, const i
         P.scale_in = j == 0 ? c.scale : nullptr;
         P.scale_out = j == c.nsteps - 1 ? c.scale : nullptr;
       }
-      launch_gemm_f64(g, nrhs, done, st);
+      if (g.nprob) launch_gemm_f64(g, nrhs, done, st);
     }
   }
   CK(cudaGetLastError());
@@ -574,13 +601,24 @@ static void kernel_span(fdst_ctx *h, cudaEvent_t a, int64_t launches, cudaStream
   h->n_kernel += launches;
 }
 
-static fdst_status run_matvec_f64(fdst_ctx *h, const double *x, double *y, int nrhs, const int *done,
-                                  cudaStream_t st, bool timed) {
+// A plan's ops over the buffers of that plan (the full operator, or its B or B^T part).
+struct PlanView {
+  const std::vector<PlanOp> *ops;
+  const std::vector<double *> *t1, *g;
+  const std::vector<int64_t> *t1_size, *g_size;
+};
+
+static PlanView full_view(fdst_ctx *h, bool df) {
+  return PlanView{df ? &h->plan_df : &h->plan, &h->t1, &h->g, &h->t1_size, &h->g_size};
+}
+
+static fdst_status run_plan_f64(fdst_ctx *h, const PlanView &V, const double *x, double *y, int nrhs,
+                                const int *done, cudaStream_t st, bool timed) {
   // pack consecutive ops of a stage into launches with pairwise distinct outputs
   cudaEvent_t k0 = timed ? kernel_mark(h, st) : nullptr;
   int64_t nl = 0;
   size_t i = 0;
-  const auto &P = h->plan;
+  const auto &P = *V.ops;
   while (i < P.size()) {
     BandGroup g;
     std::vector<std::pair<int, int>> outs;
@@ -596,11 +634,11 @@ static fdst_status run_matvec_f64(fdst_ctx *h, const double *x, double *y, int n
       b.d0 = op.dims[0]; b.d1 = op.dims[1]; b.d2 = op.dims[2]; b.mode = op.mode;
       b.coef = op.coef; b.accumulate = op.accumulate;
       if (op.in_kind == 0) { b.X = x + h->off[op.in_id]; b.x_rhs_stride = h->n_total; }
-      else if (op.in_kind == 1) { b.X = h->t1[op.in_id]; b.x_rhs_stride = h->t1_size[op.in_id]; }
-      else { b.X = h->g[op.in_id]; b.x_rhs_stride = h->g_size[op.in_id]; }
+      else if (op.in_kind == 1) { b.X = (*V.t1)[op.in_id]; b.x_rhs_stride = (*V.t1_size)[op.in_id]; }
+      else { b.X = (*V.g)[op.in_id]; b.x_rhs_stride = (*V.g_size)[op.in_id]; }
       if (op.out_kind == 3) { b.Y = y + h->off[op.out_id]; b.y_rhs_stride = h->n_total; }
-      else if (op.out_kind == 1) { b.Y = h->t1[op.out_id]; b.y_rhs_stride = h->t1_size[op.out_id]; }
-      else { b.Y = h->g[op.out_id]; b.y_rhs_stride = h->g_size[op.out_id]; }
+      else if (op.out_kind == 1) { b.Y = (*V.t1)[op.out_id]; b.y_rhs_stride = (*V.t1_size)[op.out_id]; }
+      else { b.Y = (*V.g)[op.out_id]; b.y_rhs_stride = (*V.g_size)[op.out_id]; }
       ++i;
     }
     launch_band(g, nrhs, done, st);
@@ -611,15 +649,17 @@ static fdst_status run_matvec_f64(fdst_ctx *h, const double *x, double *y, int n
   return FDST_OK;
 }
 
-// Same plan in double-float arithmetic: x split once into FP32 pairs, every
-// banded mode product on the FP32 units, the result joined back to FP64.
-static fdst_status run_matvec_df(fdst_ctx *h, const double *x, double *y, int nrhs, const int *done,
-                                 cudaStream_t st) {
-  launch_split_df(x, h->x2, h->n_total, h->n_total, nrhs, done, st);
+// Same plan in double-float arithmetic: the entries [in_lo, in_hi) of x split once
+// into FP32 pairs, every banded mode product on the FP32 units, the entries
+// [out_lo, out_hi) of the result joined back to FP64.
+static fdst_status run_plan_df(fdst_ctx *h, const PlanView &V, const double *x, double *y, int nrhs,
+                               const int *done, cudaStream_t st, int64_t in_lo, int64_t in_hi, int64_t out_lo,
+                               int64_t out_hi) {
+  launch_split_df(x + in_lo, h->x2 + in_lo, in_hi - in_lo, h->n_total, nrhs, done, st);
   cudaEvent_t k0 = kernel_mark(h, st);
   int64_t nl = 0;
   size_t i = 0;
-  const auto &P = h->plan_df;
+  const auto &P = *V.ops;
   while (i < P.size()) {
     BandGroupDF g;
     std::vector<std::pair<int, int>> outs;
@@ -636,18 +676,18 @@ static fdst_status run_matvec_df(fdst_ctx *h, const double *x, double *y, int nr
       b.accumulate = op.accumulate;
       b.swap = op.swap;
       if (op.in_kind == 0) { b.X = h->x2 + h->off[op.in_id]; b.x_rhs_stride = h->n_total; }
-      else if (op.in_kind == 1) { b.X = reinterpret_cast<const float2 *>(h->t1[op.in_id]); b.x_rhs_stride = h->t1_size[op.in_id]; }
-      else { b.X = reinterpret_cast<const float2 *>(h->g[op.in_id]); b.x_rhs_stride = h->g_size[op.in_id]; }
+      else if (op.in_kind == 1) { b.X = reinterpret_cast<const float2 *>((*V.t1)[op.in_id]); b.x_rhs_stride = (*V.t1_size)[op.in_id]; }
+      else { b.X = reinterpret_cast<const float2 *>((*V.g)[op.in_id]); b.x_rhs_stride = (*V.g_size)[op.in_id]; }
       if (op.out_kind == 3) { b.Y = h->y2 + h->off[op.out_id]; b.y_rhs_stride = h->n_total; }
-      else if (op.out_kind == 1) { b.Y = reinterpret_cast<float2 *>(h->t1[op.out_id]); b.y_rhs_stride = h->t1_size[op.out_id]; }
-      else { b.Y = reinterpret_cast<float2 *>(h->g[op.out_id]); b.y_rhs_stride = h->g_size[op.out_id]; }
+      else if (op.out_kind == 1) { b.Y = reinterpret_cast<float2 *>((*V.t1)[op.out_id]); b.y_rhs_stride = (*V.t1_size)[op.out_id]; }
+      else { b.Y = reinterpret_cast<float2 *>((*V.g)[op.out_id]); b.y_rhs_stride = (*V.g_size)[op.out_id]; }
       ++i;
     }
     launch_band_df(g, nrhs, done, st);
     ++nl;
   }
   kernel_span(h, k0, nl, st);
-  launch_join_df(h->y2, y, h->n_total, h->n_total, nrhs, done, st);
+  launch_join_df(h->y2 + out_lo, y + out_lo, out_hi - out_lo, h->n_total, nrhs, done, st);
   CK(cudaGetLastError());
   return FDST_OK;
 }
@@ -715,8 +755,96 @@ fdst_status run_matvec(fdst_ctx *h, const double *x, double *y, int nrhs, const 
     CK(cudaGetLastError());
     return FDST_OK;
   }
-  if (!exact && h->desc.matvec_precision == FDST_MV_DF64) return run_matvec_df(h, x, y, nrhs, done, st);
-  return run_matvec_f64(h, x, y, nrhs, done, st, !exact);
+  if (!exact && h->desc.matvec_precision == FDST_MV_DF64)
+    return run_plan_df(h, full_view(h, true), x, y, nrhs, done, st, 0, h->n_total, 0, h->n_total);
+  return run_plan_f64(h, full_view(h, false), x, y, nrhs, done, st, !exact);
+}
+
+// ------------------------------------------------------------------ P_T, P_C and GMRES workspace
+
+// The B and B^T parts of the operator as plans of their own (built on first use),
+// the GMRES work vectors and a Krylov basis of cap + 1 block vectors.
+static fdst_status ensure_gmres(fdst_ctx *h, int cap) {
+  if (h->mapped) {
+    set_error("P_T/P_C-GMRES runs on the identity map (Kronecker form of B and B^T)");
+    return FDST_NOT_SUPPORTED;
+  }
+  if (!h->gm_w) {
+    std::vector<Term> tb, tbt;
+    for (const Term &t : h->terms) {
+      if (t.dst == h->dim) tb.push_back(t);
+      else if (t.src == h->dim) tbt.push_back(t);
+    }
+    auto &B = h->plan_b, &Bt = h->plan_bt;
+    TRY(build_plan(h, tb, B.ops, B.ops_df, B.t1_size, B.g_size));
+    TRY(alloc_plan_buffers(h, B.t1_size, B.g_size, B.t1, B.g));
+    TRY(build_plan(h, tbt, Bt.ops, Bt.ops_df, Bt.t1_size, Bt.g_size));
+    TRY(alloc_plan_buffers(h, Bt.t1_size, Bt.g_size, Bt.t1, Bt.g));
+    const size_t nv = (size_t)h->n_total * h->max_rhs;
+    TRY(dalloc(h, &h->gm_t, nv));
+    TRY(dalloc(h, &h->gm_u, nv));
+    TRY(dalloc(h, &h->gm_part, (size_t)8 * 304 * h->max_rhs));
+    TRY(dalloc(h, &h->gm_scal, (size_t)4 * h->max_rhs));
+    TRY(dalloc(h, &h->gm_mask, (size_t)h->max_rhs));
+    TRY(dalloc(h, &h->gm_w, nv));
+  }
+  if (cap > h->gm_cap) {
+    if (h->gm_V) {
+      cudaFree(h->gm_V);
+      h->allocs.erase(std::find(h->allocs.begin(), h->allocs.end(), (void *)h->gm_V));
+      cudaFree(h->gm_coef);
+      h->allocs.erase(std::find(h->allocs.begin(), h->allocs.end(), (void *)h->gm_coef));
+      h->device_bytes -= (int64_t)((size_t)(h->gm_cap + 1) * h->n_total * h->max_rhs * sizeof(double) +
+                                   (size_t)3 * (h->gm_cap + 1) * h->max_rhs * sizeof(double));
+      h->gm_V = h->gm_coef = nullptr;
+    }
+    TRY(dalloc(h, &h->gm_V, (size_t)(cap + 1) * h->n_total * h->max_rhs));
+    TRY(dalloc(h, &h->gm_coef, (size_t)3 * (cap + 1) * h->max_rhs));
+    h->gm_cap = cap;
+  }
+  return FDST_OK;
+}
+
+// y[velocity blocks] = B^T x[pressure block]; y[pressure block] = B x[velocity blocks]
+// (the iterations' matvec arithmetic).
+static fdst_status apply_coupling(fdst_ctx *h, bool transpose, const double *x, double *y, int nrhs,
+                                  const int *done, cudaStream_t st) {
+  const auto &S = transpose ? h->plan_bt : h->plan_b;
+  const bool df = h->desc.matvec_precision == FDST_MV_DF64;
+  const PlanView V{df ? &S.ops_df : &S.ops, &S.t1, &S.g, &S.t1_size, &S.g_size};
+  const int64_t nv = h->off[h->dim], n = h->n_total;
+  if (df)
+    return transpose ? run_plan_df(h, V, x, y, nrhs, done, st, nv, n, 0, nv)
+                     : run_plan_df(h, V, x, y, nrhs, done, st, 0, nv, nv, n);
+  return run_plan_f64(h, V, x, y, nrhs, done, st, false);
+}
+
+// s = P^{-1} r for the block triangular P_T = [[P_V, B^T], [0, -P_Q]] (back
+// substitution) or the constraint P_C = [[P_V, B^T], [B, B P_V^{-1} B^T - P_Q]]
+// (the paper's product form of P_C^{-1}); P_V^{-1}, P_Q^{-1} are the FD applies.
+static fdst_status apply_block_prec(fdst_ctx *h, int kind, const double *r, double *s, int nrhs, const int *done,
+                                    cudaStream_t st) {
+  const int dim = h->dim;
+  const int64_t n = h->n_total, nv = h->off[dim], nq = n - nv;
+  const unsigned vel = (1u << dim) - 1u, pres = 1u << dim;
+  double *t = h->gm_t, *u = h->gm_u;
+  if (kind == FDST_PREC_PT) {
+    TRY(run_apply(h, r, s, nrhs, done, st, pres));             // s_q = P_Q^{-1} r_q (q = -s_q)
+    TRY(apply_coupling(h, true, s, t, nrhs, done, st));        // t_u = B^T s_q
+    launch_axpby(r, t, 1.0, 1.0, nv, n, nrhs, st);             // t_u = r_u - B^T q
+    TRY(run_apply(h, t, s, nrhs, done, st, vel));              // s_u = P_V^{-1} t_u
+  } else {
+    TRY(run_apply(h, r, s, nrhs, done, st, vel));              // z = P_V^{-1} r_u in s_u
+    TRY(apply_coupling(h, false, s, t, nrhs, done, st));       // t_q = B z
+    launch_axpby(r + nv, t + nv, 1.0, -1.0, nq, n, nrhs, st);  // t_q = r_q - B z
+    TRY(run_apply(h, t, s, nrhs, done, st, pres));             // s_q = P_Q^{-1} t_q (q = -s_q)
+    TRY(apply_coupling(h, true, s, u, nrhs, done, st));        // u_u = B^T s_q = -B^T q
+    TRY(run_apply(h, u, t, nrhs, done, st, vel));              // t_u = P_V^{-1} u_u
+    launch_axpby(t, s, 1.0, 1.0, nv, n, nrhs, st);             // s_u = z - P_V^{-1} B^T q
+  }
+  launch_axpby(s + nv, s + nv, 0.0, -1.0, nq, n, nrhs, st);    // q = -s_q
+  CK(cudaGetLastError());
+  return FDST_OK;
 }
 
 }  // namespace fdst
@@ -911,6 +1039,188 @@ fdst_status fdst_get_timing(fdst_handle h, double *ms_matvec, double *ms_prec, d
   if (n_matvec) *n_matvec = h->n_matvec;
   if (n_prec) *n_prec = h->n_prec;
   return FDST_OK;
+}
+
+fdst_status fdst_apply_block_prec(fdst_handle h, int prec, const double *d_r, double *d_s, int nrhs,
+                                  fdst_stream stream) {
+  if (!h || !d_r || !d_s) { set_error("NULL argument"); return FDST_INVALID_ARGUMENT; }
+  if (d_r == d_s) { set_error("r and s must not alias"); return FDST_INVALID_ARGUMENT; }
+  if (nrhs < 1 || nrhs > h->max_rhs) { set_error("nrhs out of range [1, max_rhs]"); return FDST_INVALID_ARGUMENT; }
+  if (prec != FDST_PREC_PT && prec != FDST_PREC_PC) { set_error("prec must be FDST_PREC_PT or FDST_PREC_PC");
+    return FDST_INVALID_ARGUMENT; }
+  TRY(ensure_gmres(h, 1));
+  return apply_block_prec(h, prec, d_r, d_s, nrhs, nullptr, (cudaStream_t)stream);
+}
+
+fdst_status fdst_solve_gmres(fdst_handle h, int prec, const double *d_b, double *d_x, int nrhs, double tol,
+                             int maxit, int restart, fdst_solve_info *info, fdst_stream stream) {
+  if (!h || !d_b || !d_x || !info) { set_error("NULL argument"); return FDST_INVALID_ARGUMENT; }
+  if (nrhs < 1 || nrhs > h->max_rhs) { set_error("nrhs out of range [1, max_rhs]"); return FDST_INVALID_ARGUMENT; }
+  if (!(tol >= 0.0) || maxit < 1) { set_error("tol must be >= 0 and maxit >= 1"); return FDST_INVALID_ARGUMENT; }
+  if (prec != FDST_PREC_PT && prec != FDST_PREC_PC) { set_error("prec must be FDST_PREC_PT or FDST_PREC_PC");
+    return FDST_INVALID_ARGUMENT; }
+  if (restart < 1 || restart > 255) { set_error("restart must be in [1, 255]"); return FDST_INVALID_ARGUMENT; }
+  TRY(ensure_gmres(h, restart));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = h->n_total;
+  const int m = restart, ld = m + 1;
+  const int64_t vstride = n * h->max_rhs;    // basis vector k at V + k * vstride, right-hand side r at + r * n
+  double *V = h->gm_V, *w = h->gm_w, *u = h->gm_u;
+  double *c1 = h->gm_coef, *c2 = h->gm_coef + (size_t)ld * h->max_rhs, *cy = h->gm_coef + (size_t)2 * ld * h->max_rhs;
+  std::vector<double> H((size_t)nrhs * ld * m, 0.0), cs((size_t)nrhs * m), sn((size_t)nrhs * m), g((size_t)nrhs * ld);
+  std::vector<double> bn(nrhs), bref(nrhs), tau(nrhs, tol), est(nrhs, 1.0), true_rel(nrhs, -1.0);
+  std::vector<double> hc1((size_t)nrhs * ld), hc2((size_t)nrhs * ld), hy((size_t)nrhs * ld), hs(nrhs);
+  std::vector<int> iters(nrhs, 0), done(nrhs, 0), status(nrhs, FDST_MAXIT), est_it(nrhs, -1);
+  auto sync_done = [&](const std::vector<int> &mask, int *dst) -> fdst_status {
+    CK(cudaMemcpyAsync(dst, mask.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, st));
+    return FDST_OK;
+  };
+  auto norms2 = [&](const double *a, const int *skip) -> fdst_status {   // hs[r] = <a_r, a_r>
+    launch_dot(a, a, n, n, nrhs, h->partials, h->counters, h->dots, skip, st);
+    CK(cudaMemcpyAsync(hs.data(), h->dots, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return FDST_OK;
+  };
+  // ||b||, ||P^{-1} b||
+  TRY(norms2(d_b, nullptr));
+  for (int r = 0; r < nrhs; ++r) bn[r] = std::sqrt(hs[r]);
+  TRY(apply_block_prec(h, prec, d_b, w, nrhs, nullptr, st));
+  TRY(norms2(w, nullptr));
+  for (int r = 0; r < nrhs; ++r) {
+    bref[r] = std::sqrt(hs[r]);
+    if (bn[r] == 0.0 || bref[r] == 0.0) { done[r] = 1; status[r] = FDST_OK; est[r] = 0.0; true_rel[r] = 0.0; }
+  }
+  for (int r = 0; r < nrhs; ++r)
+    if (bn[r] == 0.0) CK(cudaMemsetAsync(d_x + (size_t)r * n, 0, sizeof(double) * n, st));
+  TRY(sync_done(done, h->done));
+  auto active = [&]() { for (int r = 0; r < nrhs; ++r) if (!done[r]) return true; return false; };
+  // x_try_r = x_r + V_{0..j-1} y_r for the right-hand sides with mask[r] == 0 (into u)
+  auto form = [&](int j, const std::vector<int> &mask) -> fdst_status {
+    for (int r = 0; r < nrhs; ++r) {
+      double *yr = &hy[(size_t)r * ld];
+      std::fill(yr, yr + ld, 0.0);
+      if (mask[r]) continue;
+      const double *Hr = &H[(size_t)r * ld * m];
+      const double *gr = &g[(size_t)r * ld];
+      for (int i = j - 1; i >= 0; --i) {
+        double a = gr[i];
+        for (int k = i + 1; k < j; ++k) a -= Hr[(size_t)i * m + k] * yr[k];
+        yr[i] = Hr[(size_t)i * m + i] != 0.0 ? a / Hr[(size_t)i * m + i] : 0.0;
+      }
+    }
+    CK(cudaMemcpyAsync(cy, hy.data(), sizeof(double) * nrhs * ld, cudaMemcpyHostToDevice, st));
+    TRY(sync_done(mask, h->gm_mask));
+    launch_axpby(d_x, u, 1.0, 0.0, n, n, nrhs, st);
+    launch_basis_axpy(V, vstride, j, cy, ld, 1.0, u, n, n, nrhs, h->gm_mask, st);
+    return FDST_OK;
+  };
+  int it = 0;
+  while (active() && it < maxit) {
+    // r0 = P^{-1}(b - A x), V_0 = r0 / ||r0||
+    TRY(run_matvec(h, d_x, h->Az, nrhs, h->done, st, false));
+    launch_axpby(d_b, h->Az, 1.0, -1.0, n, n, nrhs, st);
+    TRY(apply_block_prec(h, prec, h->Az, w, nrhs, h->done, st));
+    TRY(norms2(w, h->done));
+    for (int r = 0; r < nrhs; ++r) {
+      if (done[r]) continue;
+      g[(size_t)r * ld] = std::sqrt(hs[r]);
+      for (int i = 1; i < ld; ++i) g[(size_t)r * ld + i] = 0.0;
+    }
+    launch_scale_by_norm(w, V, h->dots, n, n, nrhs, h->done, st);
+    int j = 0;
+    while (j < m && it < maxit && active()) {
+      // w = P^{-1} A V_j, then classical Gram-Schmidt twice against V_0..V_j
+      TRY(run_matvec(h, V + (size_t)j * vstride, h->Az, nrhs, h->done, st, false));
+      TRY(apply_block_prec(h, prec, h->Az, w, nrhs, h->done, st));
+      launch_basis_dots(V, vstride, 0, j + 1, w, n, n, nrhs, h->gm_part, c1, ld, h->done, st);
+      launch_basis_axpy(V, vstride, j + 1, c1, ld, -1.0, w, n, n, nrhs, h->done, st);
+      launch_basis_dots(V, vstride, 0, j + 1, w, n, n, nrhs, h->gm_part, c2, ld, h->done, st);
+      launch_basis_axpy(V, vstride, j + 1, c2, ld, -1.0, w, n, n, nrhs, h->done, st);
+      launch_dot(w, w, n, n, nrhs, h->partials, h->counters, h->dots, h->done, st);
+      launch_scale_by_norm(w, V + (size_t)(j + 1) * vstride, h->dots, n, n, nrhs, h->done, st);
+      CK(cudaMemcpyAsync(hc1.data(), c1, sizeof(double) * nrhs * ld, cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(hc2.data(), c2, sizeof(double) * nrhs * ld, cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(hs.data(), h->dots, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      std::vector<int> cand(nrhs, 1);   // 0: estimate below its threshold (true residual to check)
+      bool any = false;
+      for (int r = 0; r < nrhs; ++r) {
+        if (done[r]) continue;
+        double *Hr = &H[(size_t)r * ld * m];
+        double *gr = &g[(size_t)r * ld];
+        double *csr = &cs[(size_t)r * m], *snr = &sn[(size_t)r * m];
+        for (int i = 0; i <= j; ++i) Hr[(size_t)i * m + j] = hc1[(size_t)r * ld + i] + hc2[(size_t)r * ld + i];
+        double hn = std::sqrt(std::max(hs[r], 0.0));
+        for (int i = 0; i < j; ++i) {   // earlier rotations on the new column
+          const double a = Hr[(size_t)i * m + j], b = Hr[(size_t)(i + 1) * m + j];
+          Hr[(size_t)i * m + j] = csr[i] * a + snr[i] * b;
+          Hr[(size_t)(i + 1) * m + j] = -snr[i] * a + csr[i] * b;
+        }
+        const double a = Hr[(size_t)j * m + j];
+        const double den = std::hypot(a, hn);
+        csr[j] = den == 0.0 ? 1.0 : a / den;
+        snr[j] = den == 0.0 ? 0.0 : hn / den;
+        Hr[(size_t)j * m + j] = csr[j] * a + snr[j] * hn;
+        gr[j + 1] = -snr[j] * gr[j];
+        gr[j] = csr[j] * gr[j];
+        iters[r] += 1;
+        est[r] = std::fabs(gr[j + 1]) / bref[r];
+        if (est[r] <= tol && est_it[r] < 0) est_it[r] = iters[r];
+        if (!(std::isfinite(est[r]))) { status[r] = FDST_NAN_DETECTED; done[r] = 1; continue; }
+        if (est[r] <= tau[r]) { cand[r] = 0; any = true; }
+      }
+      ++j;
+      ++it;
+      if (any) {
+        // true residual of x + V y for the candidates (FP64 matvec)
+        TRY(form(j, cand));
+        TRY(run_matvec(h, u, h->Az, nrhs, h->gm_mask, st, true));
+        launch_axpby(d_b, h->Az, 1.0, -1.0, n, n, nrhs, st);
+        TRY(norms2(h->Az, h->gm_mask));
+        for (int r = 0; r < nrhs; ++r) {
+          if (cand[r]) continue;
+          const double tr = std::sqrt(hs[r]) / bn[r];
+          true_rel[r] = tr;
+          if (tr <= tol) {
+            CK(cudaMemcpyAsync(d_x + (size_t)r * n, u + (size_t)r * n, sizeof(double) * n,
+                               cudaMemcpyDeviceToDevice, st));
+            status[r] = FDST_OK;
+            done[r] = 1;
+          } else {
+            tau[r] = 0.5 * tau[r] * tol / tr;
+          }
+        }
+      }
+      TRY(sync_done(done, h->done));
+    }
+    if (active()) {
+      // basis full (or maxit): x <- x + V y for the right-hand sides still running
+      TRY(form(j, done));
+      for (int r = 0; r < nrhs; ++r)
+        if (!done[r])
+          CK(cudaMemcpyAsync(d_x + (size_t)r * n, u + (size_t)r * n, sizeof(double) * n, cudaMemcpyDeviceToDevice,
+                             st));
+    }
+  }
+  // FP64 true residuals of the returned iterates
+  std::vector<int> none(nrhs, 0);
+  TRY(sync_done(none, h->gm_mask));
+  TRY(run_matvec(h, d_x, h->Az, nrhs, h->gm_mask, st, true));
+  launch_axpby(d_b, h->Az, 1.0, -1.0, n, n, nrhs, st);
+  TRY(norms2(h->Az, h->gm_mask));
+  fdst_status ret = FDST_OK;
+  for (int r = 0; r < nrhs; ++r) {
+    true_rel[r] = bn[r] > 0.0 ? std::sqrt(hs[r]) / bn[r] : 0.0;
+    if (status[r] == FDST_MAXIT && true_rel[r] <= tol) status[r] = FDST_OK;
+    info[r].iterations = iters[r];
+    info[r].status = status[r];
+    info[r].eta_rel = est[r];
+    info[r].true_rel_res = true_rel[r];
+    info[r].iterations_estimate = est_it[r] >= 0 ? est_it[r] : iters[r];
+    if (ret == FDST_OK && status[r] != FDST_OK) ret = (fdst_status)status[r];
+  }
+  TRY(sync_done(none, h->done));
+  return ret;
 }
 
 fdst_status fdst_solve(fdst_handle h, const double *d_b, double *d_x, int nrhs, double tol, int maxit,

@@ -110,6 +110,19 @@ struct MinresState {
 void launch_dot(const double *a, const double *b, int64_t n, int64_t stride, int nrhs, double *partials,
                 unsigned *counters, double *out, const int *done, cudaStream_t s);
 
+// GMRES basis operations; basis vector k of right-hand side r at V + k * vstride + r * stride,
+// rows with skip[r] != 0 left alone.
+// out[r * ldo + k0 + k] = <V_{k0+k}, w> for k < kc (fixed-order reductions; part: 8 * 304 * nrhs doubles).
+void launch_basis_dots(const double *V, int64_t vstride, int k0, int kc, const double *w, int64_t n,
+                       int64_t stride, int nrhs, double *part, double *out, int ldo, const int *skip,
+                       cudaStream_t s);
+// w_r += sign * sum_{k < kc} c[r * ldc + k] V_k, kc <= 256.
+void launch_basis_axpy(const double *V, int64_t vstride, int kc, const double *c, int ldc, double sign, double *w,
+                       int64_t n, int64_t stride, int nrhs, const int *skip, cudaStream_t s);
+// dst_r = src_r / sqrt(nrm2[r]).
+void launch_scale_by_norm(const double *src, double *dst, const double *nrm2, int64_t n, int64_t stride, int nrhs,
+                          const int *skip, cudaStream_t s);
+
 // y_j = alpha * x_j + beta * y_j for all j (elementwise, deterministic).
 void launch_axpby(const double *x, double *y, double alpha, double beta, int64_t n, int64_t stride, int nrhs,
                   cudaStream_t s);

@@ -712,4 +712,113 @@ void launch_restart_vectors(const double *b, const double *Ax, double *v, double
   k_restart_vectors<<<dim3((unsigned)blocks, nrhs), 256, 0, s>>>(b, Ax, v, v_old, w, w_old, n, stride, done);
 }
 
+// ------------------------------------------------------------------ GMRES basis operations
+// Basis vector k of right-hand side r at V + k * vstride + r * stride; rows are
+// skipped where skip[r] != 0. Reductions run in a fixed order (per-block
+// partial sums, then the blocks in index order): results do not depend on timing.
+
+constexpr int kDotChunk = 8;       // basis vectors per dot launch
+constexpr int kDotBlocks = 304;    // 2 blocks per SM
+
+__global__ void __launch_bounds__(256) k_mdot_part(const double *V, int64_t vstride, int kc, const double *w,
+                                                   int64_t n, int64_t stride, double *part, const int *skip) {
+  const int r = blockIdx.y;
+  if (skip && skip[r]) return;
+  const double *wr = w + r * stride;
+  const double *vr = V + r * stride;
+  double acc[kDotChunk];
+#pragma unroll
+  for (int k = 0; k < kDotChunk; ++k) acc[k] = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double wi = wr[i];
+#pragma unroll
+    for (int k = 0; k < kDotChunk; ++k)
+      if (k < kc) acc[k] = fma(vr[k * vstride + i], wi, acc[k]);
+  }
+  __shared__ double ws[kDotChunk][8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < kDotChunk; ++k) {
+    const double t = warp_sum(acc[k]);
+    if (lane == 0) ws[k][wid] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < kc) {
+    double t = 0.0;
+    for (int q = 0; q < 8; ++q) t += ws[threadIdx.x][q];
+    part[((int64_t)r * kDotChunk + threadIdx.x) * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+__global__ void k_mdot_final(const double *part, int nblk, int kc, double *out, int ldo, int k0, int nrhs,
+                             const int *skip) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = t / kDotChunk, k = t % kDotChunk;
+  if (r >= nrhs || k >= kc || (skip && skip[r])) return;
+  const double *pp = part + ((int64_t)r * kDotChunk + k) * nblk;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += pp[b];
+  out[(int64_t)r * ldo + k0 + k] = s;
+}
+
+void launch_basis_dots(const double *V, int64_t vstride, int k0, int kc, const double *w, int64_t n,
+                       int64_t stride, int nrhs, double *part, double *out, int ldo, const int *skip,
+                       cudaStream_t s) {
+  for (int k = 0; k < kc; k += kDotChunk) {
+    const int c = kc - k < kDotChunk ? kc - k : kDotChunk;
+    count_launch(2);
+    k_mdot_part<<<dim3(kDotBlocks, nrhs), 256, 0, s>>>(V + (int64_t)(k0 + k) * vstride, vstride, c, w, n,
+                                                       stride, part, skip);
+    k_mdot_final<<<(nrhs * kDotChunk + 127) / 128, 128, 0, s>>>(part, kDotBlocks, c, out, ldo, k0 + k, nrhs, skip);
+  }
+}
+
+// w_r += sign * sum_{k < kc} c[r * ldc + k] * V_k (one pass over the kc vectors and w)
+__global__ void k_basis_axpy(const double *V, int64_t vstride, int kc, const double *c, int ldc, double sign,
+                             double *w, int64_t n, int64_t stride, const int *skip) {
+  const int r = blockIdx.y;
+  if (skip && skip[r]) return;
+  __shared__ double cs[256];
+  for (int k = threadIdx.x; k < kc; k += blockDim.x) cs[k] = sign * c[(int64_t)r * ldc + k];
+  __syncthreads();
+  double *wr = w + r * stride;
+  const double *vr = V + r * stride;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double a = wr[i];
+    for (int k = 0; k < kc; ++k) a = fma(cs[k], vr[k * vstride + i], a);
+    wr[i] = a;
+  }
+}
+
+void launch_basis_axpy(const double *V, int64_t vstride, int kc, const double *c, int ldc, double sign, double *w,
+                       int64_t n, int64_t stride, int nrhs, const int *skip, cudaStream_t s) {
+  if (kc <= 0) return;
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 1216) blocks = 1216;
+  if (blocks < 1) blocks = 1;
+  count_launch(1);
+  k_basis_axpy<<<dim3((unsigned)blocks, nrhs), 256, 0, s>>>(V, vstride, kc, c, ldc, sign, w, n, stride, skip);
+}
+
+// dst_r = src_r / sqrt(nrm2[r]) (0 where the norm is 0)
+__global__ void k_scale_by_norm(const double *src, double *dst, const double *nrm2, int64_t n, int64_t stride,
+                                const int *skip) {
+  const int r = blockIdx.y;
+  if (skip && skip[r]) return;
+  const double q = nrm2[r] > 0.0 ? 1.0 / sqrt(nrm2[r]) : 0.0;
+  const double *a = src + r * stride;
+  double *b = dst + r * stride;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = a[i] * q;
+}
+
+void launch_scale_by_norm(const double *src, double *dst, const double *nrm2, int64_t n, int64_t stride, int nrhs,
+                          const int *skip, cudaStream_t s) {
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  count_launch(1);
+  k_scale_by_norm<<<dim3((unsigned)blocks, nrhs), 256, 0, s>>>(src, dst, nrm2, n, stride, skip);
+}
+
 }  // namespace fdst
