@@ -64,6 +64,10 @@ enum { FDST_MV_F64 = 0, FDST_MV_DF64 = 1 };
 /* Block preconditioners for GMRES (Sec. 4): P_T = [[P_V, B^T], [0, -P_Q]] (block
  * triangular) and P_C = [[P_V, B^T], [B, B P_V^{-1} B^T - P_Q]] (constraint). */
 enum { FDST_PREC_PT = 0, FDST_PREC_PC = 1 };
+/* GMRES form: left-preconditioned (Arnoldi on P^{-1} A), flexible right-preconditioned
+ * (Arnoldi on A with z_j = P^{-1} v_j kept: exact Arnoldi relation whatever the
+ * precision of P^{-1}), or AUTO (left with the FP64 FD apply, flexible with the split ones). */
+enum { FDST_GMRES_LEFT = 0, FDST_GMRES_FLEXIBLE = 1, FDST_GMRES_AUTO = 2 };
 
 typedef struct {
   int dim;                 /* 2 or 3 */
@@ -166,18 +170,20 @@ fdst_status fdst_apply_block_prec(fdst_handle h, int prec, const double *d_r, do
                                   fdst_stream stream);
 
 /*
- * fdst_solve_gmres - left-preconditioned GMRES (Saad-Schultz) with P_T or P_C
- * (Sec. 4; eq. P_T, eq. P_C, applied through the product form of P_C^{-1}),
- * their P_V, P_Q blocks the handle's FD applies and B, B^T the Kronecker parts
- * of the operator; identity map only (FDST_NOT_SUPPORTED on mapped geometry).
+ * fdst_solve_gmres - GMRES (Saad-Schultz) with P_T or P_C (Sec. 4; eq. P_T,
+ * eq. P_C, applied through the product form of P_C^{-1}), their P_V, P_Q
+ * blocks the handle's FD applies and B, B^T the Kronecker parts of the
+ * operator; identity map only (FDST_NOT_SUPPORTED on mapped geometry).
+ *   form:    FDST_GMRES_LEFT, FDST_GMRES_FLEXIBLE or FDST_GMRES_AUTO (above).
  *   b, x:    device block vectors (nrhs back to back), x the initial guess in and
  *            the solution out, as fdst_solve.
  *   restart: Krylov basis size m in [1, 255]; the handle keeps a basis of
- *            (m + 1) x max_rhs block vectors (allocated on first use, grown when
- *            a larger m is asked for) and restarts from the current iterate when
- *            it is full.
+ *            (m + 1) x max_rhs block vectors (and m more for the flexible form),
+ *            allocated on first use and grown when a larger m is asked for, and
+ *            restarts from the current iterate when it is full.
  * Arnoldi with classical Gram-Schmidt applied twice, Givens rotations on the
- * Hessenberg matrix; the estimate is ||P^{-1}(b - A x_j)|| / ||P^{-1} b||. When
+ * Hessenberg matrix; the estimate is ||P^{-1}(b - A x_j)|| / ||P^{-1} b||
+ * (left) or ||b - A x_j|| / ||b|| (flexible). When
  * it meets the threshold (tol at first) x_j is formed and its FP64 true
  * residual ||b - A x_j|| / ||b|| computed: <= tol ends that right-hand side,
  * otherwise the threshold drops to 0.5 tau tol / true and the Arnoldi process
@@ -186,8 +192,8 @@ fdst_status fdst_apply_block_prec(fdst_handle h, int prec, const double *d_r, do
  * Synchronizes the stream. Matvecs in the iterations use the handle's matvec
  * precision.
  */
-fdst_status fdst_solve_gmres(fdst_handle h, int prec, const double *d_b, double *d_x, int nrhs, double tol,
-                             int maxit, int restart, fdst_solve_info *info, fdst_stream stream);
+fdst_status fdst_solve_gmres(fdst_handle h, int prec, int form, const double *d_b, double *d_x, int nrhs,
+                             double tol, int maxit, int restart, fdst_solve_info *info, fdst_stream stream);
 
 /*
  * fdst_solve_host - fdst_solve with host vectors: copies h_b (and h_x as the

@@ -14,6 +14,12 @@ intact (true_check=True). With true_check=False the estimate alone decides.
 The basis holds at most `restart` vectors; when it is full, x is formed and
 the process starts again from the new residual.
 
+flexible=True gives the right-preconditioned flexible form (Saad's FGMRES):
+Arnoldi on A with z_j = P^{-1} v_j kept, x_j = x_0 + Z_j y_j, so that the
+estimate |g_{j+1}| / ||b|| is the unpreconditioned relative residual and the
+Arnoldi relation A Z_j = V_{j+1} H_j holds however P^{-1} was evaluated (the
+form for preconditioners applied in reduced precision).
+
 Pins (tests/test_oracle_gmres.py): solution vs. numpy.linalg.solve on random
 nonsymmetric systems (exact after n steps); the estimate equals the directly
 computed ||P^{-1}(b - A x_j)|| and never increases; with the ideal block
@@ -24,23 +30,24 @@ preconditioner P_C equals A and GMRES stops after 1 step.
 import numpy as np
 
 
-def gmres(A, b, Pinv, tol=1e-8, maxit=1000, restart=200, x0=None, history=None, true_check=False):
+def gmres(A, b, Pinv, tol=1e-8, maxit=1000, restart=200, x0=None, history=None, true_check=False, flexible=False):
     """Returns (x, info) with info = dict(iters, status, est_rel, true_rel).
     A, Pinv: callables on 1-D float64 arrays. status: "converged" or "maxit"."""
     b = np.asarray(b, float)
     x = np.zeros_like(b) if x0 is None else np.array(x0, float)
     nb = np.linalg.norm(b)
-    beta_ref = np.linalg.norm(Pinv(b))
+    beta_ref = nb if flexible else np.linalg.norm(Pinv(b))
     if nb == 0.0 or beta_ref == 0.0:
         return np.zeros_like(b), dict(iters=0, status="converged", est_rel=0.0, true_rel=0.0)
     tau = tol
     it = 0
     est = np.inf
     while it < maxit:
-        r = Pinv(b - A(x))
+        r = (b - A(x)) if flexible else Pinv(b - A(x))
         beta = np.linalg.norm(r)
         m = min(restart, maxit - it)
         V = np.zeros((m + 1, b.size))
+        Z = np.zeros((m, b.size)) if flexible else None
         H = np.zeros((m + 1, m))
         cs, sn = np.zeros(m), np.zeros(m)
         g = np.zeros(m + 1)
@@ -51,7 +58,11 @@ def gmres(A, b, Pinv, tol=1e-8, maxit=1000, restart=200, x0=None, history=None, 
         j = 0
         done = False
         while j < m:
-            w = Pinv(A(V[j]))
+            if flexible:
+                Z[j] = Pinv(V[j])
+                w = A(Z[j])
+            else:
+                w = Pinv(A(V[j]))
             for i in range(j + 1):                       # modified Gram-Schmidt
                 H[i, j] = np.dot(w, V[i])
                 w = w - H[i, j] * V[i]
@@ -74,7 +85,7 @@ def gmres(A, b, Pinv, tol=1e-8, maxit=1000, restart=200, x0=None, history=None, 
             if history is not None:
                 history.append(est)
             if est <= tau:
-                xj = x + _combine(V, H, g, j)
+                xj = x + _combine(Z if flexible else V, H, g, j)
                 if not true_check:
                     x = xj
                     done = True
@@ -90,12 +101,12 @@ def gmres(A, b, Pinv, tol=1e-8, maxit=1000, restart=200, x0=None, history=None, 
         if done:
             return x, dict(iters=it, status="converged", est_rel=est,
                            true_rel=np.linalg.norm(b - A(x)) / nb)
-        x = x + _combine(V, H, g, j)
+        x = x + _combine(Z if flexible else V, H, g, j)
     return x, dict(iters=it, status="maxit", est_rel=est, true_rel=np.linalg.norm(b - A(x)) / nb)
 
 
 def _combine(V, H, g, j):
-    """V_j y with y the solution of the rotated (upper triangular) j x j system."""
+    """V_j y (or Z_j y) with y the solution of the rotated (upper triangular) j x j system."""
     y = np.zeros(j)
     for i in range(j - 1, -1, -1):
         y[i] = (g[i] - np.dot(H[i, i + 1:j], y[i + 1:j])) / H[i, i]

@@ -21,6 +21,7 @@ GEOM_IDENTITY, GEOM_SINE_BUMP = 0, 1
 VARIANT_PD, VARIANT_PD_GEO = 0, 1
 MV_F64, MV_DF64 = 0, 1
 PREC_PT, PREC_PC = 0, 1
+GMRES_LEFT, GMRES_FLEXIBLE, GMRES_AUTO = 0, 1, 2
 
 STATUS = {0: "OK", 1: "INVALID_ARGUMENT", 2: "NOT_SPD", 3: "OUT_OF_MEMORY", 4: "CUDA_ERROR", 5: "MAXIT",
           6: "STAGNATION", 7: "BREAKDOWN", 8: "TIMEOUT", 9: "NAN_DETECTED", 10: "ADMISSION_REJECTED",
@@ -84,7 +85,7 @@ def load_library(path=LIB_PATH):
     lib.fdst_apply_prec.argtypes = [vp, vp, vp, i, vp]
     lib.fdst_matvec.argtypes = [vp, vp, vp, i, vp]
     lib.fdst_solve.argtypes = [vp, vp, vp, i, d, i, ctypes.POINTER(SolveInfo), vp]
-    lib.fdst_solve_gmres.argtypes = [vp, i, vp, vp, i, d, i, i, ctypes.POINTER(SolveInfo), vp]
+    lib.fdst_solve_gmres.argtypes = [vp, i, i, vp, vp, i, d, i, i, ctypes.POINTER(SolveInfo), vp]
     lib.fdst_apply_block_prec.argtypes = [vp, i, vp, vp, i, vp]
     lib.fdst_solve_host.argtypes = [vp, vp, vp, i, d, i, ctypes.POINTER(SolveInfo), vp]
     lib.fdst_apply_prec_host.argtypes = [vp, vp, vp, i, vp]
@@ -252,13 +253,14 @@ class Stokes:
         _check(_lib.fdst_apply_block_prec(self._h, PREC_PT if prec is None else prec, _dptr(r), _dptr(s),
                                           self._nrhs(r), _stream_ptr(stream)))
 
-    def solve_gmres(self, b, x, prec=None, tol=1e-8, maxit=1000, restart=60, stream=None, check=False):
-        """Left-preconditioned GMRES with the block triangular (PREC_PT) or constraint
-        (PREC_PC) preconditioner built from this handle's FD blocks (fdst_solve_gmres)."""
+    def solve_gmres(self, b, x, prec=None, form=None, tol=1e-8, maxit=1000, restart=60, stream=None, check=False):
+        """GMRES with the block triangular (PREC_PT) or constraint (PREC_PC) preconditioner
+        built from this handle's FD blocks (fdst_solve_gmres); form GMRES_LEFT,
+        GMRES_FLEXIBLE or GMRES_AUTO (default)."""
         n = self._nrhs(b)
         info = (SolveInfo * n)()
-        code = _lib.fdst_solve_gmres(self._h, PREC_PT if prec is None else prec, _dptr(b), _dptr(x), n, tol, maxit,
-                                     restart, info, _stream_ptr(stream))
+        code = _lib.fdst_solve_gmres(self._h, PREC_PT if prec is None else prec, GMRES_AUTO if form is None else form,
+                                     _dptr(b), _dptr(x), n, tol, maxit, restart, info, _stream_ptr(stream))
         if check:
             _check(code)
         return [dict(iterations=i.iterations, status=STATUS.get(i.status, i.status), eta_rel=i.eta_rel,

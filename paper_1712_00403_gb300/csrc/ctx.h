@@ -104,8 +104,8 @@ struct fdst_ctx {
   } plan_b, plan_bt;
   // GMRES: Krylov basis of gm_cap + 1 block vectors (max_rhs right-hand sides each),
   // three work vectors, device scalars
-  int gm_cap = 0;
-  double *gm_V = nullptr, *gm_w = nullptr, *gm_t = nullptr, *gm_u = nullptr;
+  int gm_cap = 0, gm_zcap = 0;
+  double *gm_V = nullptr, *gm_Z = nullptr, *gm_w = nullptr, *gm_t = nullptr, *gm_u = nullptr;
   double *gm_coef = nullptr, *gm_part = nullptr, *gm_scal = nullptr;
   int *gm_mask = nullptr;
   std::vector<double *> t1, g;

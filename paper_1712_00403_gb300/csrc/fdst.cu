@@ -764,7 +764,15 @@ fdst_status run_matvec(fdst_ctx *h, const double *x, double *y, int nrhs, const 
 
 // The B and B^T parts of the operator as plans of their own (built on first use),
 // the GMRES work vectors and a Krylov basis of cap + 1 block vectors.
-static fdst_status ensure_gmres(fdst_ctx *h, int cap) {
+static void release(fdst_ctx *h, double *&p, size_t count) {
+  if (!p) return;
+  cudaFree(p);
+  h->allocs.erase(std::find(h->allocs.begin(), h->allocs.end(), (void *)p));
+  h->device_bytes -= (int64_t)(count * sizeof(double));
+  p = nullptr;
+}
+
+static fdst_status ensure_gmres(fdst_ctx *h, int cap, bool flexible) {
   if (h->mapped) {
     set_error("P_T/P_C-GMRES runs on the identity map (Kronecker form of B and B^T)");
     return FDST_NOT_SUPPORTED;
@@ -788,19 +796,20 @@ static fdst_status ensure_gmres(fdst_ctx *h, int cap) {
     TRY(dalloc(h, &h->gm_mask, (size_t)h->max_rhs));
     TRY(dalloc(h, &h->gm_w, nv));
   }
+  const size_t nv = (size_t)h->n_total * h->max_rhs;
   if (cap > h->gm_cap) {
-    if (h->gm_V) {
-      cudaFree(h->gm_V);
-      h->allocs.erase(std::find(h->allocs.begin(), h->allocs.end(), (void *)h->gm_V));
-      cudaFree(h->gm_coef);
-      h->allocs.erase(std::find(h->allocs.begin(), h->allocs.end(), (void *)h->gm_coef));
-      h->device_bytes -= (int64_t)((size_t)(h->gm_cap + 1) * h->n_total * h->max_rhs * sizeof(double) +
-                                   (size_t)3 * (h->gm_cap + 1) * h->max_rhs * sizeof(double));
-      h->gm_V = h->gm_coef = nullptr;
-    }
-    TRY(dalloc(h, &h->gm_V, (size_t)(cap + 1) * h->n_total * h->max_rhs));
+    release(h, h->gm_V, (size_t)(h->gm_cap + 1) * nv);
+    release(h, h->gm_coef, (size_t)3 * (h->gm_cap + 1) * h->max_rhs);
+    h->gm_cap = 0;
+    TRY(dalloc(h, &h->gm_V, (size_t)(cap + 1) * nv));
     TRY(dalloc(h, &h->gm_coef, (size_t)3 * (cap + 1) * h->max_rhs));
     h->gm_cap = cap;
+  }
+  if (flexible && cap > h->gm_zcap) {
+    release(h, h->gm_Z, (size_t)h->gm_zcap * nv);
+    h->gm_zcap = 0;
+    TRY(dalloc(h, &h->gm_Z, (size_t)cap * nv));
+    h->gm_zcap = cap;
   }
   return FDST_OK;
 }
@@ -1048,24 +1057,30 @@ fdst_status fdst_apply_block_prec(fdst_handle h, int prec, const double *d_r, do
   if (nrhs < 1 || nrhs > h->max_rhs) { set_error("nrhs out of range [1, max_rhs]"); return FDST_INVALID_ARGUMENT; }
   if (prec != FDST_PREC_PT && prec != FDST_PREC_PC) { set_error("prec must be FDST_PREC_PT or FDST_PREC_PC");
     return FDST_INVALID_ARGUMENT; }
-  TRY(ensure_gmres(h, 1));
+  TRY(ensure_gmres(h, 1, false));
   return apply_block_prec(h, prec, d_r, d_s, nrhs, nullptr, (cudaStream_t)stream);
 }
 
-fdst_status fdst_solve_gmres(fdst_handle h, int prec, const double *d_b, double *d_x, int nrhs, double tol,
-                             int maxit, int restart, fdst_solve_info *info, fdst_stream stream) {
+fdst_status fdst_solve_gmres(fdst_handle h, int prec, int form, const double *d_b, double *d_x, int nrhs,
+                             double tol, int maxit, int restart, fdst_solve_info *info, fdst_stream stream) {
   if (!h || !d_b || !d_x || !info) { set_error("NULL argument"); return FDST_INVALID_ARGUMENT; }
   if (nrhs < 1 || nrhs > h->max_rhs) { set_error("nrhs out of range [1, max_rhs]"); return FDST_INVALID_ARGUMENT; }
   if (!(tol >= 0.0) || maxit < 1) { set_error("tol must be >= 0 and maxit >= 1"); return FDST_INVALID_ARGUMENT; }
   if (prec != FDST_PREC_PT && prec != FDST_PREC_PC) { set_error("prec must be FDST_PREC_PT or FDST_PREC_PC");
     return FDST_INVALID_ARGUMENT; }
   if (restart < 1 || restart > 255) { set_error("restart must be in [1, 255]"); return FDST_INVALID_ARGUMENT; }
-  TRY(ensure_gmres(h, restart));
+  if (form != FDST_GMRES_LEFT && form != FDST_GMRES_FLEXIBLE && form != FDST_GMRES_AUTO) {
+    set_error("form must be FDST_GMRES_LEFT, FDST_GMRES_FLEXIBLE or FDST_GMRES_AUTO");
+    return FDST_INVALID_ARGUMENT;
+  }
+  const bool flex = form == FDST_GMRES_FLEXIBLE || (form == FDST_GMRES_AUTO && h->desc.fd_precision != FDST_FD_F64);
+  TRY(ensure_gmres(h, restart, flex));
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t n = h->n_total;
   const int m = restart, ld = m + 1;
   const int64_t vstride = n * h->max_rhs;    // basis vector k at V + k * vstride, right-hand side r at + r * n
-  double *V = h->gm_V, *w = h->gm_w, *u = h->gm_u;
+  double *V = h->gm_V, *Z = h->gm_Z, *w = h->gm_w, *u = h->gm_u;
+  double *X = flex ? Z : V;   // the basis the iterate is formed from
   double *c1 = h->gm_coef, *c2 = h->gm_coef + (size_t)ld * h->max_rhs, *cy = h->gm_coef + (size_t)2 * ld * h->max_rhs;
   std::vector<double> H((size_t)nrhs * ld * m, 0.0), cs((size_t)nrhs * m), sn((size_t)nrhs * m), g((size_t)nrhs * ld);
   std::vector<double> bn(nrhs), bref(nrhs), tau(nrhs, tol), est(nrhs, 1.0), true_rel(nrhs, -1.0);
@@ -1081,11 +1096,13 @@ fdst_status fdst_solve_gmres(fdst_handle h, int prec, const double *d_b, double 
     CK(cudaStreamSynchronize(st));
     return FDST_OK;
   };
-  // ||b||, ||P^{-1} b||
+  // ||b|| and the estimate's reference: ||P^{-1} b|| (left) or ||b|| (flexible)
   TRY(norms2(d_b, nullptr));
   for (int r = 0; r < nrhs; ++r) bn[r] = std::sqrt(hs[r]);
-  TRY(apply_block_prec(h, prec, d_b, w, nrhs, nullptr, st));
-  TRY(norms2(w, nullptr));
+  if (!flex) {
+    TRY(apply_block_prec(h, prec, d_b, w, nrhs, nullptr, st));
+    TRY(norms2(w, nullptr));
+  }
   for (int r = 0; r < nrhs; ++r) {
     bref[r] = std::sqrt(hs[r]);
     if (bn[r] == 0.0 || bref[r] == 0.0) { done[r] = 1; status[r] = FDST_OK; est[r] = 0.0; true_rel[r] = 0.0; }
@@ -1095,7 +1112,7 @@ fdst_status fdst_solve_gmres(fdst_handle h, int prec, const double *d_b, double 
   TRY(sync_done(done, h->done));
   auto active = [&]() { for (int r = 0; r < nrhs; ++r) if (!done[r]) return true; return false; };
   // x_try_r = x_r + V_{0..j-1} y_r for the right-hand sides with mask[r] == 0 (into u)
-  auto form = [&](int j, const std::vector<int> &mask) -> fdst_status {
+  auto form_x = [&](int j, const std::vector<int> &mask) -> fdst_status {
     for (int r = 0; r < nrhs; ++r) {
       double *yr = &hy[(size_t)r * ld];
       std::fill(yr, yr + ld, 0.0);
@@ -1111,15 +1128,16 @@ fdst_status fdst_solve_gmres(fdst_handle h, int prec, const double *d_b, double 
     CK(cudaMemcpyAsync(cy, hy.data(), sizeof(double) * nrhs * ld, cudaMemcpyHostToDevice, st));
     TRY(sync_done(mask, h->gm_mask));
     launch_axpby(d_x, u, 1.0, 0.0, n, n, nrhs, st);
-    launch_basis_axpy(V, vstride, j, cy, ld, 1.0, u, n, n, nrhs, h->gm_mask, st);
+    launch_basis_axpy(X, vstride, j, cy, ld, 1.0, u, n, n, nrhs, h->gm_mask, st);
     return FDST_OK;
   };
   int it = 0;
   while (active() && it < maxit) {
-    // r0 = P^{-1}(b - A x), V_0 = r0 / ||r0||
+    // r0 = P^{-1}(b - A x) (left) or b - A x (flexible), V_0 = r0 / ||r0||
     TRY(run_matvec(h, d_x, h->Az, nrhs, h->done, st, false));
     launch_axpby(d_b, h->Az, 1.0, -1.0, n, n, nrhs, st);
-    TRY(apply_block_prec(h, prec, h->Az, w, nrhs, h->done, st));
+    if (flex) launch_axpby(h->Az, w, 1.0, 0.0, n, n, nrhs, st);
+    else TRY(apply_block_prec(h, prec, h->Az, w, nrhs, h->done, st));
     TRY(norms2(w, h->done));
     for (int r = 0; r < nrhs; ++r) {
       if (done[r]) continue;
@@ -1129,9 +1147,15 @@ fdst_status fdst_solve_gmres(fdst_handle h, int prec, const double *d_b, double 
     launch_scale_by_norm(w, V, h->dots, n, n, nrhs, h->done, st);
     int j = 0;
     while (j < m && it < maxit && active()) {
-      // w = P^{-1} A V_j, then classical Gram-Schmidt twice against V_0..V_j
-      TRY(run_matvec(h, V + (size_t)j * vstride, h->Az, nrhs, h->done, st, false));
-      TRY(apply_block_prec(h, prec, h->Az, w, nrhs, h->done, st));
+      // w = P^{-1} A V_j (left) or A Z_j with Z_j = P^{-1} V_j (flexible), then classical
+      // Gram-Schmidt twice against V_0..V_j
+      if (flex) {
+        TRY(apply_block_prec(h, prec, V + (size_t)j * vstride, Z + (size_t)j * vstride, nrhs, h->done, st));
+        TRY(run_matvec(h, Z + (size_t)j * vstride, w, nrhs, h->done, st, false));
+      } else {
+        TRY(run_matvec(h, V + (size_t)j * vstride, h->Az, nrhs, h->done, st, false));
+        TRY(apply_block_prec(h, prec, h->Az, w, nrhs, h->done, st));
+      }
       launch_basis_dots(V, vstride, 0, j + 1, w, n, n, nrhs, h->gm_part, c1, ld, h->done, st);
       launch_basis_axpy(V, vstride, j + 1, c1, ld, -1.0, w, n, n, nrhs, h->done, st);
       launch_basis_dots(V, vstride, 0, j + 1, w, n, n, nrhs, h->gm_part, c2, ld, h->done, st);
@@ -1173,7 +1197,7 @@ fdst_status fdst_solve_gmres(fdst_handle h, int prec, const double *d_b, double 
       ++it;
       if (any) {
         // true residual of x + V y for the candidates (FP64 matvec)
-        TRY(form(j, cand));
+        TRY(form_x(j, cand));
         TRY(run_matvec(h, u, h->Az, nrhs, h->gm_mask, st, true));
         launch_axpby(d_b, h->Az, 1.0, -1.0, n, n, nrhs, st);
         TRY(norms2(h->Az, h->gm_mask));
@@ -1195,7 +1219,7 @@ fdst_status fdst_solve_gmres(fdst_handle h, int prec, const double *d_b, double 
     }
     if (active()) {
       // basis full (or maxit): x <- x + V y for the right-hand sides still running
-      TRY(form(j, done));
+      TRY(form_x(j, done));
       for (int r = 0; r < nrhs; ++r)
         if (!done[r])
           CK(cudaMemcpyAsync(d_x + (size_t)r * n, u + (size_t)r * n, sizeof(double) * n, cudaMemcpyDeviceToDevice,

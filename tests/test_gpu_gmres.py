@@ -1,9 +1,10 @@
 """P_T / P_C block preconditioners and GMRES (paper Sec. 4, eq. P_T, eq. P_C and
 the product form of P_C^{-1}) against the oracle: the applies element by
-element (FP64, 1e-12), GMRES iterations within one of the oracle's
-(modified Gram-Schmidt there, classical Gram-Schmidt twice here) with the FP64
-true residual at the tolerance, and the mixed-precision form (split-TF32 FD,
-double-float matvec) within two iterations of the FP64 one."""
+element (FP64, 1e-12), GMRES (left and flexible forms) iterations within one
+of the oracle's (modified Gram-Schmidt there, classical Gram-Schmidt twice
+here) with the FP64 true residual at the tolerance, and the mixed-precision
+solve (split-TF32 FD, double-float matvec, flexible form) within two
+iterations of the FP64 one."""
 import numpy as np
 import pytest
 
@@ -45,7 +46,8 @@ def test_block_prec_apply_matches_oracle(spec, which):
 @pytest.mark.parametrize("spec", [problem_spec(2, 2, 12), problem_spec(3, 2, 4), problem_spec(2, 2, 6, "RT")],
                          ids=_ids)
 @pytest.mark.parametrize("which", ["PT", "PC"])
-def test_gmres_matches_oracle(spec, which):
+@pytest.mark.parametrize("flexible", [False, True], ids=["left", "flexible"])
+def test_gmres_matches_oracle(spec, which, flexible):
     import paper_1712_00403_gb300 as fd
     P = gpu_problem(spec, max_rhs=2)
     S = oracle_problem(spec)
@@ -53,12 +55,13 @@ def test_gmres_matches_oracle(spec, which):
     b = torch.tensor(B.reshape(-1), device="cuda")
     x = torch.zeros_like(b)
     prec = fd.PREC_PT if which == "PT" else fd.PREC_PC
-    info = P.solve_gmres(b, x, prec=prec, tol=1e-8, maxit=300)
+    info = P.solve_gmres(b, x, prec=prec, form=fd.GMRES_FLEXIBLE if flexible else fd.GMRES_LEFT, tol=1e-8,
+                         maxit=300)
     X = x.cpu().numpy().reshape(2, -1)
     apply = stokes.apply_PT_inv if which == "PT" else stokes.apply_PC_inv
     for j in range(2):
         xo, io = gmres.gmres(lambda v: stokes.matvec(S, v), B[j], lambda v: apply(S, v), tol=1e-8, maxit=300,
-                             true_check=True)
+                             true_check=True, flexible=flexible)
         assert info[j]["status"] == "OK"
         assert abs(info[j]["iterations"] - io["iters"]) <= 1
         assert info[j]["true_rel_res"] <= 1e-8
@@ -75,16 +78,18 @@ def test_gmres_mixed_precision_and_restart():
     spec = problem_spec(3, 2, 6)
     B = synth.rhs(77, gpu_problem(spec).block_sizes)
     its = {}
-    for name, kw, restart in (("f64", {}, 60), ("mixed", dict(fd_precision=fd.FD_TF32X3, matvec_precision=fd.MV_DF64),
-                                                 60), ("restarted", {}, 8)):
+    mixed = dict(fd_precision=fd.FD_TF32X3, matvec_precision=fd.MV_DF64)
+    for name, kw, restart, form in (("f64", {}, 60, fd.GMRES_FLEXIBLE), ("mixed", mixed, 60, fd.GMRES_AUTO),
+                                    ("f64-left", {}, 60, fd.GMRES_LEFT), ("restarted", {}, 8, fd.GMRES_LEFT)):
         P = gpu_problem(spec, **kw)
         b = torch.tensor(B, device="cuda")
         x = torch.zeros_like(b)
-        info = P.solve_gmres(b, x, prec=fd.PREC_PT, tol=1e-8, maxit=400, restart=restart)[0]
+        info = P.solve_gmres(b, x, prec=fd.PREC_PT, form=form, tol=1e-8, maxit=400, restart=restart)[0]
         assert info["status"] == "OK" and info["true_rel_res"] <= 1e-8, (name, info)
         its[name] = info["iterations"]
+    # split-TF32 FD apply in the flexible form: within two iterations of the FP64 flexible solve
     assert its["mixed"] <= its["f64"] + 2
-    assert its["restarted"] >= its["f64"]
+    assert its["restarted"] >= its["f64-left"]
 
 
 def test_gmres_zero_rhs_and_lockstep():

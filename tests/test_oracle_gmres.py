@@ -103,3 +103,38 @@ def test_pt_gmres_on_the_stokes_system():
         x, ig = gmres.gmres(A, b, lambda v: apply(S, v), tol=1e-8, maxit=300, true_check=True)
         assert ig["status"] == "converged" and ig["true_rel"] <= 1e-8
         assert ig["iters"] < im["iters"]
+
+
+def test_flexible_gmres_solves_and_tracks_the_true_residual():
+    rng = np.random.default_rng(11)
+    n = 20
+    A = rng.standard_normal((n, n)) + 4 * np.eye(n)
+    Mi = np.diag(1.0 / rng.uniform(1.0, 3.0, n))
+    b = rng.standard_normal(n)
+    x, info = gmres.gmres(lambda v: A @ v, b, lambda v: Mi @ v, tol=1e-12, maxit=n, flexible=True)
+    np.testing.assert_allclose(x, np.linalg.solve(A, b), rtol=1e-9, atol=1e-11)
+    hist = []
+    for k in range(1, 7):
+        hist.clear()
+        x, _ = gmres.gmres(lambda v: A @ v, b, lambda v: Mi @ v, tol=0.0, maxit=k, history=hist, flexible=True)
+        direct = np.linalg.norm(b - A @ x) / np.linalg.norm(b)
+        assert abs(hist[-1] - direct) <= 1e-12 * max(1.0, direct)
+
+
+def test_flexible_gmres_with_a_varying_preconditioner():
+    """The flexible form keeps A Z_j = V_{j+1} H_j for a preconditioner that changes
+    from step to step (here: a diagonal perturbed by 1e-3 at every call), so it
+    still reaches 1e-10 with an accurate estimate."""
+    rng = np.random.default_rng(12)
+    n = 40
+    A = rng.standard_normal((n, n)) + 6 * np.eye(n)
+    d = rng.uniform(1.0, 3.0, n)
+    calls = [0]
+
+    def Pinv(v):
+        calls[0] += 1
+        return v / (d * (1 + 1e-3 * np.sin(calls[0] + np.arange(n))))
+    b = rng.standard_normal(n)
+    x, info = gmres.gmres(lambda v: A @ v, b, Pinv, tol=1e-10, maxit=n, flexible=True)
+    assert info["status"] == "converged"
+    assert np.linalg.norm(b - A @ x) / np.linalg.norm(b) <= 1e-10 * 1.01
