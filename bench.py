@@ -55,6 +55,9 @@ def parse():
                     help="matvec arithmetic inside the iterations (true residual always FP64)")
     ap.add_argument("--nrhs", type=int, default=0, help="right-hand sides per step (default: the workload's)")
     ap.add_argument("--maxit", type=int, default=400)
+    ap.add_argument("--solver", default="minres", choices=["minres", "gmres-pt", "gmres-pc"],
+                    help="P_D-MINRES (the default), or GMRES with the block triangular P_T / constraint P_C")
+    ap.add_argument("--restart", type=int, default=60, help="GMRES Krylov basis size")
     ap.add_argument("--no-cpu-baseline", action="store_true",
                     help="skip the oracle timing (profiling runs of the GPU path)")
     return ap.parse_args()
@@ -132,7 +135,7 @@ def describe(name, w, nrhs):
                 f"mean-free), MINRES tol 1e-8 from x0=0")
     return (f"{name}: {w['dim']}D unit {'cube' if w['dim'] == 3 else 'square'}, {w['disc']} IGA, pressure degree "
             f"p={w['p']}, {n} elements, {nrhs} seeded N(0,1) right-hand sides (pressure part mean-free), "
-            f"P_D-MINRES tol 1e-8 from x0=0")
+            f"tol 1e-8 from x0=0")
 
 
 def peaks():
@@ -311,9 +314,18 @@ def run_gpu(args):
     x = torch.zeros_like(b)
     stream = torch.cuda.current_stream()
 
+    gm = args.solver != "minres"
+    gm_prec = fd.PREC_PC if args.solver == "gmres-pc" else fd.PREC_PT
+
+    def solve_dev(bb, xx):
+        if gm:
+            return P.solve_gmres(bb, xx, prec=gm_prec, tol=1e-8, maxit=args.maxit, restart=args.restart,
+                                 stream=stream)
+        return P.solve(bb, xx, tol=1e-8, maxit=args.maxit, stream=stream)
+
     def step():
         x.zero_()
-        return P.solve(b, x, tol=1e-8, maxit=args.maxit, stream=stream)
+        return solve_dev(b, x)
 
     for _ in range(args.warmup):
         info = step()
@@ -442,7 +454,8 @@ def run_gpu(args):
                 "traffic": traffic, "traffic_note": traffic_note, "kernel": kern, "ms_per_launch": launch_ms,
                 "ms_per_phase": t_ms, "peak_source": peak_note}
 
-    # end to end through the host-pointer entry point (pinned host buffers)
+    # end to end through the host-pointer entry point (pinned host buffers); GMRES has no
+    # host-pointer entry point, so its copies are made here around the device call
     bh = torch.empty(b.numel(), dtype=torch.float64, pin_memory=True)
     bh.copy_(b.cpu())
     xh = torch.zeros(b.numel(), dtype=torch.float64, pin_memory=True)
@@ -452,13 +465,20 @@ def run_gpu(args):
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         xn[:] = 0.0
-        P.solve_host(bn, xn, tol=1e-8, maxit=args.maxit, stream=stream)
+        if gm:
+            bd = bh.to(dev, non_blocking=True)
+            xd = xh.to(dev, non_blocking=True)
+            solve_dev(bd, xd)
+            xh.copy_(xd, non_blocking=True)
+            torch.cuda.synchronize()
+        else:
+            P.solve_host(bn, xn, tol=1e-8, maxit=args.maxit, stream=stream)
     e2e_s = time.perf_counter() - t0
     e2e = {"value": e2e_steps * nrhs * world / e2e_s, "unit": "solves/s",
            "h2d_bytes_per_step": 2 * b.numel() * 8, "d2h_bytes_per_step": b.numel() * 8}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not gm:
         cpu = cpu_oracle_sample(w, w["seeds"], float(np.mean(iters)), k_iters=1 if mapped else 2)
         cpu.pop("seconds", None)
         cpu.pop("t_iter_s", None)
@@ -471,6 +491,9 @@ def run_gpu(args):
                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": dtype, "data": "synthetic",
                "config": {"workload": describe(args.workload, w, nrhs), "nrhs_per_gpu": nrhs,
+                          "solver": ("P_D-MINRES" if not gm else "%s-GMRES (%s form, Krylov basis %d)" % (
+                              "P_C" if args.solver == "gmres-pc" else "P_T",
+                              "left" if prec == fd.FD_F64 else "flexible", args.restart)),
                           "fd_precision": {fd.FD_F64: "f64", fd.FD_TF32X3: "tf32x3", fd.FD_BF16X6: "bf16x6"}[prec],
                           "matvec": (("double-float (FP32 pairs, 48-bit significand) %s in the iterations; "
                                       "true residual in FP64") % ("CSR SpMV (%d nonzeros)" % int(P.flops_matvec / 2)
@@ -481,13 +504,14 @@ def run_gpu(args):
                           "l2": "inputs larger than L2 (each step streams %d x %.0f MB vectors)" % (
                               nrhs, P.n_total * 8 / 1e6),
                           "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
-               "minres": {"iterations_min": min(iters), "iterations_max": max(iters), "status": statuses,
-                          "true_rel_res_max": true_res,
-                          "iterations_estimate_min": min(iters_est), "iterations_estimate_max": max(iters_est)},
+               ("gmres" if gm else "minres"): {
+                   "iterations_min": min(iters), "iterations_max": max(iters), "status": statuses,
+                   "true_rel_res_max": true_res,
+                   "iterations_estimate_min": min(iters_est), "iterations_estimate_max": max(iters_est)},
                "fd_apply": {"applies_per_s": applies_per_s, "gdof_per_s": applies_per_s * P.n_total / 1e9,
                             "ms_per_batch": ms_apply, "rel_err_vs_f64": apply_err},
-               "phases_ms_per_iter": {"matvec": per_mv, "prec": per_pc,
-                                      "vector": tm["ms_vector"] / max(tm["n_matvec"], 1)},
+               "phases_ms_per_iter": None if gm else {"matvec": per_mv, "prec": per_pc,
+                                                      "vector": tm["ms_vector"] / max(tm["n_matvec"], 1)},
                "setup_s": t_setup, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": launches, "clocks": clocks}
         print(json.dumps(out), flush=True)

@@ -612,6 +612,19 @@ static PlanView full_view(fdst_ctx *h, bool df) {
   return PlanView{df ? &h->plan_df : &h->plan, &h->t1, &h->g, &h->t1_size, &h->g_size};
 }
 
+// Adds the durations of the recorded compute-launch spans to ms_kernel (the stream
+// has been synchronized) and releases their events.
+static void resolve_kernel_events(fdst_ctx *h) {
+  for (auto &k : h->kev) {
+    float ms = 0.f;
+    if (h->timing) cudaEventElapsedTime(&ms, k.first, k.second);
+    h->ms_kernel += ms;
+    cudaEventDestroy(k.first);
+    cudaEventDestroy(k.second);
+  }
+  h->kev.clear();
+}
+
 static fdst_status run_plan_f64(fdst_ctx *h, const PlanView &V, const double *x, double *y, int nrhs,
                                 const int *done, cudaStream_t st, bool timed) {
   // pack consecutive ops of a stage into launches with pairwise distinct outputs
@@ -1156,6 +1169,8 @@ fdst_status fdst_solve_gmres(fdst_handle h, int prec, int form, const double *d_
         TRY(run_matvec(h, V + (size_t)j * vstride, h->Az, nrhs, h->done, st, false));
         TRY(apply_block_prec(h, prec, h->Az, w, nrhs, h->done, st));
       }
+      h->n_matvec += 1;
+      h->n_prec += 1;
       launch_basis_dots(V, vstride, 0, j + 1, w, n, n, nrhs, h->gm_part, c1, ld, h->done, st);
       launch_basis_axpy(V, vstride, j + 1, c1, ld, -1.0, w, n, n, nrhs, h->done, st);
       launch_basis_dots(V, vstride, 0, j + 1, w, n, n, nrhs, h->gm_part, c2, ld, h->done, st);
@@ -1244,6 +1259,8 @@ fdst_status fdst_solve_gmres(fdst_handle h, int prec, int form, const double *d_
     if (ret == FDST_OK && status[r] != FDST_OK) ret = (fdst_status)status[r];
   }
   TRY(sync_done(none, h->done));
+  CK(cudaStreamSynchronize(st));
+  resolve_kernel_events(h);
   return ret;
 }
 
@@ -1379,14 +1396,7 @@ fdst_status fdst_solve(fdst_handle h, const double *d_b, double *d_x, int nrhs, 
     }
     for (auto e : ev) cudaEventDestroy(e);
   }
-  for (auto &k : h->kev) {
-    float ms = 0.f;
-    if (h->timing) cudaEventElapsedTime(&ms, k.first, k.second);
-    h->ms_kernel += ms;
-    cudaEventDestroy(k.first);
-    cudaEventDestroy(k.second);
-  }
-  h->kev.clear();
+  resolve_kernel_events(h);
   fdst_status ret = FDST_OK;
   for (int j = 0; j < nrhs; ++j) {
     info[j].iterations = hs[j].iters;
