@@ -667,9 +667,9 @@ static fdst_status run_plan_f64(fdst_ctx *h, const PlanView &V, const double *x,
 // [out_lo, out_hi) of the result joined back to FP64.
 static fdst_status run_plan_df(fdst_ctx *h, const PlanView &V, const double *x, double *y, int nrhs,
                                const int *done, cudaStream_t st, int64_t in_lo, int64_t in_hi, int64_t out_lo,
-                               int64_t out_hi) {
+                               int64_t out_hi, bool timed) {
   launch_split_df(x + in_lo, h->x2 + in_lo, in_hi - in_lo, h->n_total, nrhs, done, st);
-  cudaEvent_t k0 = kernel_mark(h, st);
+  cudaEvent_t k0 = timed ? kernel_mark(h, st) : nullptr;
   int64_t nl = 0;
   size_t i = 0;
   const auto &P = *V.ops;
@@ -769,7 +769,7 @@ fdst_status run_matvec(fdst_ctx *h, const double *x, double *y, int nrhs, const 
     return FDST_OK;
   }
   if (!exact && h->desc.matvec_precision == FDST_MV_DF64)
-    return run_plan_df(h, full_view(h, true), x, y, nrhs, done, st, 0, h->n_total, 0, h->n_total);
+    return run_plan_df(h, full_view(h, true), x, y, nrhs, done, st, 0, h->n_total, 0, h->n_total, true);
   return run_plan_f64(h, full_view(h, false), x, y, nrhs, done, st, !exact);
 }
 
@@ -836,8 +836,8 @@ static fdst_status apply_coupling(fdst_ctx *h, bool transpose, const double *x, 
   const PlanView V{df ? &S.ops_df : &S.ops, &S.t1, &S.g, &S.t1_size, &S.g_size};
   const int64_t nv = h->off[h->dim], n = h->n_total;
   if (df)
-    return transpose ? run_plan_df(h, V, x, y, nrhs, done, st, nv, n, 0, nv)
-                     : run_plan_df(h, V, x, y, nrhs, done, st, 0, nv, nv, n);
+    return transpose ? run_plan_df(h, V, x, y, nrhs, done, st, nv, n, 0, nv, false)
+                     : run_plan_df(h, V, x, y, nrhs, done, st, 0, nv, nv, n, false);
   return run_plan_f64(h, V, x, y, nrhs, done, st, false);
 }
 
