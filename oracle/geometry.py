@@ -315,14 +315,52 @@ class PDG:
 
     def apply(self, r):
         b = self.S.split(np.asarray(r, float))
+        return np.concatenate(self.apply_v(b[:3]) + [self.apply_q(b[3])])
+
+    def apply_v(self, blocks):
+        """(P_V^G)^{-1} on the three velocity blocks."""
         out = []
         for k in range(3):
             Ks, Ms, coef = self.pencils[k]
             sc = self.DV[k] ** -0.5
-            out.append(sc * kron.fd_solve(Ks, Ms, coef, sc * b[k]))
+            out.append(sc * kron.fd_solve(Ks, Ms, coef, sc * blocks[k]))
+        return out
+
+    def apply_q(self, rq):
+        """(P_Q^G)^{-1} on the pressure block."""
         sq = self.DQ ** -0.5
-        out.append(sq * kron.kron_mass_solve(self.Mp, sq * b[3]))
-        return np.concatenate(out)
+        return sq * kron.kron_mass_solve(self.Mp, sq * rq)
+
+
+def coupling(S, G, u_blocks=None, q=None):
+    """B u (pressure block) or B^T q (velocity blocks) on the mapped domain: the
+    off-diagonal blocks of the operator, read off the matvec with the other
+    unknowns zero."""
+    z = [np.zeros(n) for n in S.block_sizes]
+    if q is not None:
+        z[3] = q
+        return S.split(matvec(S, G, np.concatenate(z)))[:3]
+    z[:3] = u_blocks
+    return S.split(matvec(S, G, np.concatenate(z)))[3]
+
+
+def apply_PTG_inv(S, G, pdg, r):
+    """P_T^G = [[P_V^G, B^T], [0, -P_Q^G]] (Sec. 6, eq. P_T with the geometry-aware
+    blocks): q = -(P_Q^G)^{-1} r_q, u = (P_V^G)^{-1} (r_u - B^T q)."""
+    b = S.split(np.asarray(r, float))
+    q = -pdg.apply_q(b[3])
+    bt = coupling(S, G, q=q)
+    u = pdg.apply_v([b[k] - bt[k] for k in range(3)])
+    return np.concatenate(u + [q])
+
+
+def apply_PCG_inv(S, G, pdg, r):
+    """P_C^G by the product form of its inverse (Sec. 4) with the geometry-aware blocks."""
+    b = S.split(np.asarray(r, float))
+    z = pdg.apply_v(b[:3])
+    q = -pdg.apply_q(b[3] - coupling(S, G, u_blocks=z))
+    w = pdg.apply_v(coupling(S, G, q=q))
+    return np.concatenate([z[k] - w[k] for k in range(3)] + [q])
 
 
 def operator_row(S, G, blk, i_multi):

@@ -124,6 +124,7 @@ struct fdst_ctx {
   // mapped geometry (CSR operator, weighted pencils of P_D^G)
   bool mapped = false;
   fdst::CsrDev csr;
+  fdst::CsrDev csr_b, csr_bt;   // its B and B^T blocks (built with the GMRES workspace)
   std::vector<std::vector<fdst::Mat>> geo_K, geo_M;   // [component][direction]
   std::vector<std::vector<double>> geo_scale;          // D^{-1/2} per block (P_D^G)
   // timing
@@ -170,6 +171,8 @@ inline fdst_status upload(fdst_ctx *h, T **p, const std::vector<T> &v) {
 
 // Preconditioner apply and matvec of one handle (fdst.cu); exact = true forces FP64.
 // s = P_D^{-1} r on the blocks in block_mask (bit b: block b; velocity 0..dim-1, pressure dim).
+// B and B^T blocks of the assembled mapped operator (csr_b, csr_bt).
+fdst_status build_coupling_csr(fdst_ctx *h);
 fdst_status run_apply(fdst_ctx *h, const double *r, double *s, int nrhs, const int *done, cudaStream_t st,
                       unsigned block_mask = ~0u);
 fdst_status run_matvec(fdst_ctx *h, const double *x, double *y, int nrhs, const int *done, cudaStream_t st,

@@ -786,11 +786,8 @@ static void release(fdst_ctx *h, double *&p, size_t count) {
 }
 
 static fdst_status ensure_gmres(fdst_ctx *h, int cap, bool flexible) {
-  if (h->mapped) {
-    set_error("P_T/P_C-GMRES runs on the identity map (Kronecker form of B and B^T)");
-    return FDST_NOT_SUPPORTED;
-  }
-  if (!h->gm_w) {
+  if (!h->gm_w && h->mapped) TRY(build_coupling_csr(h));
+  if (!h->gm_w && !h->mapped) {
     std::vector<Term> tb, tbt;
     for (const Term &t : h->terms) {
       if (t.dst == h->dim) tb.push_back(t);
@@ -801,6 +798,8 @@ static fdst_status ensure_gmres(fdst_ctx *h, int cap, bool flexible) {
     TRY(alloc_plan_buffers(h, B.t1_size, B.g_size, B.t1, B.g));
     TRY(build_plan(h, tbt, Bt.ops, Bt.ops_df, Bt.t1_size, Bt.g_size));
     TRY(alloc_plan_buffers(h, Bt.t1_size, Bt.g_size, Bt.t1, Bt.g));
+  }
+  if (!h->gm_w) {
     const size_t nv = (size_t)h->n_total * h->max_rhs;
     TRY(dalloc(h, &h->gm_t, nv));
     TRY(dalloc(h, &h->gm_u, nv));
@@ -831,8 +830,21 @@ static fdst_status ensure_gmres(fdst_ctx *h, int cap, bool flexible) {
 // (the iterations' matvec arithmetic).
 static fdst_status apply_coupling(fdst_ctx *h, bool transpose, const double *x, double *y, int nrhs,
                                   const int *done, cudaStream_t st) {
-  const auto &S = transpose ? h->plan_bt : h->plan_b;
   const bool df = h->desc.matvec_precision == FDST_MV_DF64;
+  if (h->mapped) {
+    const CsrDev &C = transpose ? h->csr_bt : h->csr_b;
+    const int64_t nv = h->off[h->dim], n = h->n_total;
+    const int64_t in_lo = transpose ? nv : 0, in_hi = transpose ? n : nv, out_lo = transpose ? 0 : nv;
+    if (df && C.val_df) {
+      launch_split_df(x + in_lo, h->x2 + in_lo, in_hi - in_lo, n, nrhs, done, st);
+      launch_spmv_df(C, h->x2, y + out_lo, n, nrhs, done, st);
+    } else {
+      launch_spmv(C, x, y + out_lo, n, nrhs, done, st);
+    }
+    CK(cudaGetLastError());
+    return FDST_OK;
+  }
+  const auto &S = transpose ? h->plan_bt : h->plan_b;
   const PlanView V{df ? &S.ops_df : &S.ops, &S.t1, &S.g, &S.t1_size, &S.g_size};
   const int64_t nv = h->off[h->dim], n = h->n_total;
   if (df)

@@ -526,4 +526,62 @@ void launch_csr_diag(const CsrDev &A, double *d, cudaStream_t s) {
   k_csr_diag<<<2048, 256, 0, s>>>(A.row_ptr, A.col, A.val, A.nrows, d);
 }
 
+// ------------------------------------------------------------------ CSR blocks
+// Rows [r0, r0 + nr) of a CSR matrix restricted to the columns [c_lo, c_hi): a warp
+// per row, entries kept in their order (ballot prefix within each 32-entry chunk).
+
+__global__ void k_csr_count_range(const int64_t *row_ptr, const int *col, int64_t r0, int64_t nr, int c_lo,
+                                  int c_hi, int64_t *cnt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t q = warp; q < nr; q += nwarps) {
+    const int64_t a = row_ptr[r0 + q], b = row_ptr[r0 + q + 1];
+    int64_t c = 0;
+    for (int64_t k0 = a; k0 < b; k0 += 32) {
+      const int64_t k = k0 + lane;
+      const bool in = k < b && col[k] >= c_lo && col[k] < c_hi;
+      c += __popc(__ballot_sync(0xffffffffu, in));
+    }
+    if (lane == 0) cnt[q] = c;
+  }
+}
+
+__global__ void k_csr_copy_range(const int64_t *row_ptr, const int *col, const double *val, const float2 *val_df,
+                                 int64_t r0, int64_t nr, int c_lo, int c_hi, const int64_t *out_ptr, int *ocol,
+                                 double *oval, float2 *oval_df) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t q = warp; q < nr; q += nwarps) {
+    const int64_t a = row_ptr[r0 + q], b = row_ptr[r0 + q + 1];
+    int64_t pos = out_ptr[q];
+    for (int64_t k0 = a; k0 < b; k0 += 32) {
+      const int64_t k = k0 + lane;
+      const bool in = k < b && col[k] >= c_lo && col[k] < c_hi;
+      const unsigned m = __ballot_sync(0xffffffffu, in);
+      if (in) {
+        const int64_t o = pos + __popc(m & ((1u << lane) - 1u));
+        ocol[o] = col[k];
+        oval[o] = val[k];
+        if (oval_df) oval_df[o] = val_df[k];
+      }
+      pos += __popc(m);
+    }
+  }
+}
+
+void launch_csr_count_range(const CsrDev &A, int64_t r0, int64_t nr, int c_lo, int c_hi, int64_t *cnt,
+                            cudaStream_t s) {
+  count_launch(1);
+  k_csr_count_range<<<152 * 16, 256, 0, s>>>(A.row_ptr, A.col, r0, nr, c_lo, c_hi, cnt);
+}
+
+void launch_csr_copy_range(const CsrDev &A, int64_t r0, int64_t nr, int c_lo, int c_hi, const int64_t *out_ptr,
+                           int *ocol, double *oval, float2 *oval_df, cudaStream_t s) {
+  count_launch(1);
+  k_csr_copy_range<<<152 * 16, 256, 0, s>>>(A.row_ptr, A.col, A.val, A.val_df, r0, nr, c_lo, c_hi, out_ptr, ocol,
+                                            oval, oval_df);
+}
+
 }  // namespace fdst

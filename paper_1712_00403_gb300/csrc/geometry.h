@@ -62,5 +62,11 @@ void launch_spmv_df(const CsrDev &A, const float2 *x2, double *y, int64_t stride
 void launch_spmv(const CsrDev &A, const double *x, double *y, int64_t stride, int nrhs, const int *done,
                  cudaStream_t s);
 void launch_csr_diag(const CsrDev &A, double *d, cudaStream_t s);
+// Rows [r0, r0 + nr) restricted to columns [c_lo, c_hi): cnt[q] = entries of row r0 + q
+// kept; the copy writes them (in order) at out_ptr[q] of the new arrays.
+void launch_csr_count_range(const CsrDev &A, int64_t r0, int64_t nr, int c_lo, int c_hi, int64_t *cnt,
+                            cudaStream_t s);
+void launch_csr_copy_range(const CsrDev &A, int64_t r0, int64_t nr, int c_lo, int c_hi, const int64_t *out_ptr,
+                           int *ocol, double *oval, float2 *oval_df, cudaStream_t s);
 
 }  // namespace fdst

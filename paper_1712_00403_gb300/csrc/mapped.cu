@@ -294,4 +294,40 @@ fdst_status build_mapped_post(fdst_ctx *h) {
   return FDST_OK;
 }
 
+// The B and B^T blocks of the assembled operator as CSR matrices of their own
+// (rows of the pressure block with the velocity columns; rows of the velocity
+// blocks with the pressure columns), for the block preconditioners P_T^G, P_C^G.
+fdst_status build_coupling_csr(fdst_ctx *h) {
+  const int64_t nv = h->off[h->dim], n = h->n_total;
+  auto extract = [&](int64_t r0, int64_t nr, int c_lo, int c_hi, CsrDev &out) -> fdst_status {
+    int64_t *dcnt = nullptr;
+    TRY(dalloc(h, &dcnt, (size_t)nr));
+    launch_csr_count_range(h->csr, r0, nr, c_lo, c_hi, dcnt, 0);
+    std::vector<int64_t> cnt((size_t)nr), rp((size_t)nr + 1, 0);
+    CK(cudaMemcpy(cnt.data(), dcnt, sizeof(int64_t) * nr, cudaMemcpyDeviceToHost));
+    for (int64_t q = 0; q < nr; ++q) rp[q + 1] = rp[q] + cnt[q];
+    const int64_t nnz = rp[nr];
+    int64_t *drp = nullptr;
+    int *dcol = nullptr;
+    double *dval = nullptr;
+    float2 *ddf = nullptr;
+    TRY(upload(h, &drp, rp));
+    TRY(dalloc(h, &dcol, (size_t)nnz));
+    TRY(dalloc(h, &dval, (size_t)nnz));
+    if (h->csr.val_df) TRY(dalloc(h, &ddf, (size_t)nnz));
+    launch_csr_copy_range(h->csr, r0, nr, c_lo, c_hi, drp, dcol, dval, ddf, 0);
+    CK(cudaStreamSynchronize(0));
+    out.row_ptr = drp;
+    out.col = dcol;
+    out.val = dval;
+    out.val_df = ddf;
+    out.nrows = nr;
+    out.nnz = nnz;
+    return FDST_OK;
+  };
+  TRY(extract(nv, n - nv, 0, (int)nv, h->csr_b));          // B: pressure rows, velocity columns
+  TRY(extract(0, nv, (int)nv, (int)n, h->csr_bt));         // B^T: velocity rows, pressure columns
+  return FDST_OK;
+}
+
 }  // namespace fdst

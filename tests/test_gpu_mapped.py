@@ -142,3 +142,50 @@ def test_double_float_spmv_and_minres(spec):
         assert info["status"] == "OK" and info["true_rel_res"] <= 1e-8, (mv, info)
         its[mv] = info["iterations"]
     assert its[fd.MV_DF64] <= 1.1 * its[fd.MV_F64] + 2, its
+
+
+@pytest.mark.parametrize("spec", CASES[:2], ids=_ids)
+@pytest.mark.parametrize("which", ["PT", "PC"])
+def test_block_prec_geo_apply_matches_oracle(spec, which):
+    """P_T^G and P_C^G (the geometry-aware blocks in eq. P_T, eq. P_C), B and B^T cut
+    out of the assembled operator: FP64 within the P_D^G bar."""
+    import paper_1712_00403_gb300 as fd
+    S = oracle_problem(spec)
+    G = geo.Grid(S)
+    pdg = geo.PDG(S, G)
+    r_h = synth.random_vector(17, S.n_total)
+    ref = (geo.apply_PTG_inv if which == "PT" else geo.apply_PCG_inv)(S, G, pdg, r_h)
+    for mv in (fd.MV_F64, fd.MV_DF64):
+        P = _gpu(spec, matvec_precision=mv)
+        r = torch.tensor(r_h, device="cuda")
+        s = torch.empty_like(r)
+        P.apply_block_prec(r, s, prec=fd.PREC_PT if which == "PT" else fd.PREC_PC)
+        out = s.cpu().numpy()
+        for o0, o1 in zip(P.block_offsets[:-1], P.block_offsets[1:]):
+            assert rel(out[o0:o1], ref[o0:o1]) <= 1e-11, mv
+
+
+def test_ptg_gmres_matches_oracle():
+    """P_T^G-GMRES on the mapped cube: iterations within one of the oracle's (left
+    form, FP64), true residual at the tolerance; the mixed-precision run (split
+    FD, double-float SpMV, flexible form) reaches it too."""
+    from oracle import gmres
+    import paper_1712_00403_gb300 as fd
+    spec = problem_spec(3, 2, 4)
+    S = oracle_problem(spec)
+    G = geo.Grid(S)
+    pdg = geo.PDG(S, G)
+    b_h = synth.rhs(301, S.block_sizes)
+    _, io = gmres.gmres(lambda v: geo.matvec(S, G, v), b_h, lambda v: geo.apply_PTG_inv(S, G, pdg, v), tol=1e-8,
+                        maxit=300, true_check=True)
+    P = _gpu(spec)
+    b = torch.tensor(b_h, device="cuda")
+    x = torch.zeros_like(b)
+    info = P.solve_gmres(b, x, prec=fd.PREC_PT, form=fd.GMRES_LEFT, tol=1e-8, maxit=300)[0]
+    assert info["status"] == "OK" and info["true_rel_res"] <= 1e-8
+    assert abs(info["iterations"] - io["iters"]) <= 1
+    Pm = _gpu(spec, fd_precision=fd.FD_TF32X3, matvec_precision=fd.MV_DF64)
+    x.zero_()
+    im = Pm.solve_gmres(b, x, prec=fd.PREC_PT, tol=1e-8, maxit=300)[0]
+    assert im["status"] == "OK" and im["true_rel_res"] <= 1e-8
+    assert im["iterations"] <= io["iters"] + 4
