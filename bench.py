@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--solver", default="minres", choices=["minres", "gmres-pt", "gmres-pc"],
                     help="P_D-MINRES (the default), or GMRES with the block triangular P_T / constraint P_C")
     ap.add_argument("--restart", type=int, default=60, help="GMRES Krylov basis size")
+    ap.add_argument("--matrix-free", action="store_true",
+                    help="mapped workloads: sum-factorized matvec in the iterations instead of the CSR SpMV")
     ap.add_argument("--no-cpu-baseline", action="store_true",
                     help="skip the oracle timing (profiling runs of the GPU path)")
     return ap.parse_args()
@@ -303,6 +305,9 @@ def run_gpu(args):
     mapped = w.get("geometry") == "sine_bump"
     mv = fd.MV_DF64 if args.matvec == "df64" else fd.MV_F64
     geo = dict(geometry=fd.GEOM_SINE_BUMP, variant=fd.VARIANT_PD_GEO) if mapped else {}
+    mfree = mapped and args.matrix_free
+    if mfree:
+        geo["matvec_form"] = fd.MATVEC_MATRIX_FREE
     P = fd.Stokes(knots, w["p"], disc=fd.TH if w["disc"] == "TH" else fd.RT, fd_precision=prec, max_rhs=nrhs,
                   matvec_precision=mv, **geo)
     torch.cuda.synchronize()
@@ -391,7 +396,7 @@ def run_gpu(args):
     k_ms = tm["ms_matvec_kernels"] / max(tm["n_matvec"], 1)          # compute launches per matvec
     k_launch_ms = tm["ms_matvec_kernels"] / max(tm["n_matvec_kernel_launches"], 1)
     unit = "TFLOP/s"
-    if per_mv >= per_pc and mapped:
+    if per_mv >= per_pc and mapped and not mfree:
         nnz = P.flops_matvec / 2.0
         kern = ("csr_spmv_%s (assembled mapped Stokes operator, one warp per row, 4 RHS per pass)"
                 % ("df64" if mv == fd.MV_DF64 else "f64"))
@@ -412,7 +417,9 @@ def run_gpu(args):
         # double-float: 12 FP32 lane operations per banded multiply-add of the plan (exact product
         # with 1 FMUL + 3 FFMA, TwoSum and error accumulation with 8 FADD); the FP32 pipe issues one
         # lane operation per lane and clock whatever its kind, so the ceiling is the lane rate
-        kern = "k_band_df (double-float banded Kronecker mode products of the matvec)"
+        kern = ("k_band_df (double-float banded products of the sum-factorized mapped matvec: point-basis "
+                "values/derivatives and their transposes; the point stage not counted)" if mfree else
+                "k_band_df (double-float banded Kronecker mode products of the matvec)")
         flops, t_ms, launch_ms = P.flops_matvec / 2.0 * 12.0 * nrhs, k_ms, k_launch_ms
         peak, unit = FP32_LANE_TOPS, "Top/s"
         peak_note = ("FP32 lane operations: 152 SMs x 128 FP32 lanes x 2070 MHz = 40.3 T/s nominal "
@@ -440,7 +447,7 @@ def run_gpu(args):
     else:
         achieved = flops / (t_ms / 1e3) / 1e12
     traffic, traffic_note = None, None
-    if per_mv >= per_pc and mv == fd.MV_DF64:
+    if per_mv >= per_pc and mv == fd.MV_DF64 and not mfree:
         tr = MATVEC_TRAFFIC["k_spmv_df" if mapped else "k_band_df"]
         if tr["nrhs"] == nrhs and (mapped and args.workload == "mapped_th_p3_32" or not mapped):
             scale = 1.0 if tr["entries"] is None else P.n_total / tr["entries"]
@@ -496,8 +503,10 @@ def run_gpu(args):
                               "left" if prec == fd.FD_F64 else "flexible", args.restart)),
                           "fd_precision": {fd.FD_F64: "f64", fd.FD_TF32X3: "tf32x3", fd.FD_BF16X6: "bf16x6"}[prec],
                           "matvec": (("double-float (FP32 pairs, 48-bit significand) %s in the iterations; "
-                                      "true residual in FP64") % ("CSR SpMV (%d nonzeros)" % int(P.flops_matvec / 2)
-                                                                  if mapped else "banded Kronecker products"))
+                                      "true residual in FP64") % (
+                                          "sum-factorized matrix-free operator" if mfree else
+                                          "CSR SpMV (%d nonzeros)" % int(P.flops_matvec / 2)
+                                          if mapped else "banded Kronecker products"))
                                     if mv == fd.MV_DF64 else
                                     ("FP64 CSR SpMV (%d nonzeros)" % int(P.flops_matvec / 2) if mapped else "FP64"),
                           "n_total": P.n_total,

@@ -61,6 +61,7 @@ enum { FDST_VARIANT_PD = 0, FDST_VARIANT_PD_GEO = 1 };      /* P_D (Sec. 5) or P
  * additions on the FP32 units). fdst_solve always checks the true residual
  * with the FP64 matvec. */
 enum { FDST_MV_F64 = 0, FDST_MV_DF64 = 1 };
+enum { FDST_MATVEC_ASSEMBLED = 0, FDST_MATVEC_MATRIX_FREE = 1 };
 /* Block preconditioners for GMRES (Sec. 4): P_T = [[P_V, B^T], [0, -P_Q]] (block
  * triangular) and P_C = [[P_V, B^T], [B, B P_V^{-1} B^T - P_Q]] (constraint). */
 enum { FDST_PREC_PT = 0, FDST_PREC_PC = 1 };
@@ -82,6 +83,10 @@ typedef struct {
   double cpen;             /* Nitsche penalty C_pen (RT); <= 0 selects 5(alpha+1) (Sec. 7) */
   int max_rhs;             /* most right-hand sides one call will pass (workspace sizing), >= 1 */
   int matvec_precision;    /* FDST_MV_F64 or FDST_MV_DF64 */
+  int matvec_form;         /* mapped geometry: FDST_MATVEC_ASSEMBLED (CSR) or FDST_MATVEC_MATRIX_FREE
+                              (sum factorization at the quadrature points in the iterations; the CSR
+                              is still assembled for diag(A), B, B^T and the FP64 true residual);
+                              ignored on the identity map (Kronecker operator) */
 } fdst_desc;
 
 typedef struct {
@@ -94,7 +99,9 @@ typedef struct {
   double flops_apply;      /* algorithmic flops of one preconditioner apply (one right-hand side):
                               velocity 4 N sum_d n_d (Algorithm 1 steps 2 and 4), pressure 2 N sum_d n_d */
   double flops_matvec;     /* algorithmic flops of one matvec: 2 x (band entries used) over the
-                              banded Kronecker factors of the evaluation plan */
+                              banded Kronecker factors of the evaluation plan (identity map, or
+                              the matrix-free plans of the mapped operator without their point
+                              stage), or 2 x nonzeros of the assembled CSR */
 } fdst_sizes;
 
 typedef struct {

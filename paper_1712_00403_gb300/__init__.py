@@ -20,6 +20,7 @@ HAS_TC = True        # the split-TF32 tcgen05 FD contraction is built (sm_103a)
 GEOM_IDENTITY, GEOM_SINE_BUMP = 0, 1
 VARIANT_PD, VARIANT_PD_GEO = 0, 1
 MV_F64, MV_DF64 = 0, 1
+MATVEC_ASSEMBLED, MATVEC_MATRIX_FREE = 0, 1
 PREC_PT, PREC_PC = 0, 1
 GMRES_LEFT, GMRES_FLEXIBLE, GMRES_AUTO = 0, 1, 2
 
@@ -39,7 +40,7 @@ class Desc(ctypes.Structure):
                 ("h_knots", ctypes.POINTER(ctypes.c_double) * 3), ("nknots", ctypes.c_int * 3),
                 ("viscosity", ctypes.c_double), ("geometry", ctypes.c_int), ("variant", ctypes.c_int),
                 ("fd_precision", ctypes.c_int), ("cpen", ctypes.c_double), ("max_rhs", ctypes.c_int),
-                ("matvec_precision", ctypes.c_int)]
+                ("matvec_precision", ctypes.c_int), ("matvec_form", ctypes.c_int)]
 
 
 class Sizes(ctypes.Structure):
@@ -193,7 +194,8 @@ class Stokes:
     """
 
     def __init__(self, knots, p, disc=TH, viscosity=1.0, fd_precision=FD_F64, max_rhs=1,
-                 geometry=GEOM_IDENTITY, variant=VARIANT_PD, cpen=0.0, matvec_precision=MV_F64):
+                 geometry=GEOM_IDENTITY, variant=VARIANT_PD, cpen=0.0, matvec_precision=MV_F64,
+                 matvec_form=MATVEC_ASSEMBLED):
         lib = load_library()
         self._knots = [np.ascontiguousarray(k, dtype=np.float64) for k in knots]
         desc = Desc()
@@ -210,6 +212,7 @@ class Stokes:
         desc.cpen = cpen
         desc.max_rhs = max_rhs
         desc.matvec_precision = matvec_precision
+        desc.matvec_form = matvec_form
         h = ctypes.c_void_p()
         _check(lib.fdst_setup(ctypes.byref(desc), ctypes.byref(h)))
         self._h = h

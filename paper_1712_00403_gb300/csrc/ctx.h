@@ -125,6 +125,18 @@ struct fdst_ctx {
   bool mapped = false;
   fdst::CsrDev csr;
   fdst::CsrDev csr_b, csr_bt;   // its B and B^T blocks (built with the GMRES workspace)
+  fdst::GeoPoints gp;           // geometry at the quadrature points
+  // matrix-free mapped operator (sum factorization): fields at the points (10 per
+  // right-hand side: G[r][a] then P, Q entries each), the plans from the solution to
+  // the fields and back, the geometry as FP32 pairs
+  bool mf = false;
+  int64_t mf_Q = 0;
+  int64_t mf_foff[10] = {};
+  std::vector<fdst::PlanOp> mf_fwd, mf_fwd_df, mf_bwd, mf_bwd_df;
+  std::vector<int64_t> mf_fwd_t1s, mf_fwd_gs, mf_bwd_t1s, mf_bwd_gs;
+  std::vector<double *> mf_fwd_t1, mf_fwd_g, mf_bwd_t1, mf_bwd_g;
+  double *mf_F = nullptr;
+  float2 *mf_Fw = nullptr, *mf_jd = nullptr, *mf_wd = nullptr, *mf_nu = nullptr;
   std::vector<std::vector<fdst::Mat>> geo_K, geo_M;   // [component][direction]
   std::vector<std::vector<double>> geo_scale;          // D^{-1/2} per block (P_D^G)
   // timing

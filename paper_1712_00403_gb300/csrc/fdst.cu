@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -247,7 +248,8 @@ static fdst_status build_fd(fdst_ctx *h) {
 // coordinates swapped). T1/G buffer sizes per right-hand side are appended.
 static fdst_status build_plan(fdst_ctx *h, const std::vector<Term> &terms, std::vector<PlanOp> &plan,
                               std::vector<PlanOp> &plan_df, std::vector<int64_t> &t1_size,
-                              std::vector<int64_t> &g_size) {
+                              std::vector<int64_t> &g_size, const std::vector<std::array<int, 3>> *shapes = nullptr,
+                              int ndst = 0) {
   const int dim = h->dim;
   plan.clear();
   plan_df.clear();
@@ -257,8 +259,11 @@ static fdst_status build_plan(fdst_ctx *h, const std::vector<Term> &terms, std::
   std::map<std::pair<int, int>, int> g_ids;
   std::vector<PlanOp> st1, st2, st3;
   std::vector<int> g_first;            // whether the G buffer was written yet
-  std::vector<int> dst_written(dim + 1, 0);
-  auto srcdims = [&](int b, int out[3]) { for (int e = 0; e < 3; ++e) out[e] = h->shape[b][e]; };
+  std::vector<int> dst_written(std::max(dim + 1, ndst), 0);
+  // source block shapes: the solution blocks, or the given ones (quadrature-point fields)
+  auto srcdims = [&](int b, int out[3]) {
+    for (int e = 0; e < 3; ++e) out[e] = shapes ? (*shapes)[b][e] : h->shape[b][e];
+  };
   for (const Term &t : terms) {
     auto k1 = std::make_pair(t.src, t.f[0]);
     int t1;
@@ -380,6 +385,40 @@ static fdst_status alloc_plan_buffers(fdst_ctx *h, const std::vector<int64_t> &t
   return FDST_OK;
 }
 
+// Banded device form of a matrix (rows x w values, first column per row; FP64
+// and FP32 pairs), appended to h->bands.
+static fdst_status band_from_mat(fdst_ctx *h, const Mat &A, int *id) {
+  int w = 0;
+  std::vector<int> first(A.rows, 0), last(A.rows, -1);
+  for (int i = 0; i < A.rows; ++i) {
+    for (int j = 0; j < A.cols; ++j)
+      if (A(i, j) != 0.0) { if (last[i] < 0) first[i] = j; last[i] = j; }
+    if (last[i] >= 0) w = std::max(w, last[i] - first[i] + 1);
+  }
+  if (w == 0) w = 1;
+  std::vector<int> lo(A.rows);
+  std::vector<double> vals((size_t)A.rows * w, 0.0);
+  for (int i = 0; i < A.rows; ++i) {
+    int l = last[i] < 0 ? 0 : first[i];
+    if (l + w > A.cols) l = A.cols - w;
+    lo[i] = l;
+    for (int j = 0; j < w; ++j) vals[(size_t)i * w + j] = A(i, l + j);
+  }
+  BandDev b{A.rows, A.cols, w, nullptr, nullptr, nullptr};
+  TRY(upload(h, &b.vals, vals));
+  TRY(upload(h, &b.lo, lo));
+  std::vector<float2> vdf(vals.size());
+  for (size_t i = 0; i < vals.size(); ++i) {
+    const float hi = (float)vals[i];
+    vdf[i] = make_float2(hi, (float)(vals[i] - (double)hi));
+  }
+  TRY(upload(h, &b.vals_df, vdf));
+  b.hvals = vals;
+  *id = (int)h->bands.size();
+  h->bands.push_back(b);
+  return FDST_OK;
+}
+
 static fdst_status build_matvec(fdst_ctx *h) {
   const int dim = h->dim, p = h->p, npts = p + 2;
   const double nu = h->desc.viscosity > 0.0 ? h->desc.viscosity : 1.0;
@@ -391,34 +430,7 @@ static fdst_status build_matvec(fdst_ctx *h) {
     if (it != band_ids.end()) { *id = it->second; return FDST_OK; }
     Mat A = (da == 1 && db == 1 && space_key(sa) == space_key(sb)) ? stiffness_matrix(sa, npts)
                                                                     : mixed_matrix(sa, da, sb, db, npts);
-    int w = 0;
-    std::vector<int> first(A.rows, 0), last(A.rows, -1);
-    for (int i = 0; i < A.rows; ++i) {
-      for (int j = 0; j < A.cols; ++j)
-        if (A(i, j) != 0.0) { if (last[i] < 0) first[i] = j; last[i] = j; }
-      if (last[i] >= 0) w = std::max(w, last[i] - first[i] + 1);
-    }
-    if (w == 0) w = 1;
-    std::vector<int> lo(A.rows);
-    std::vector<double> vals((size_t)A.rows * w, 0.0);
-    for (int i = 0; i < A.rows; ++i) {
-      int l = last[i] < 0 ? 0 : first[i];
-      if (l + w > A.cols) l = A.cols - w;
-      lo[i] = l;
-      for (int j = 0; j < w; ++j) vals[(size_t)i * w + j] = A(i, l + j);
-    }
-    BandDev b{A.rows, A.cols, w, nullptr, nullptr, nullptr};
-    TRY(upload(h, &b.vals, vals));
-    TRY(upload(h, &b.lo, lo));
-    std::vector<float2> vdf(vals.size());
-    for (size_t i = 0; i < vals.size(); ++i) {
-      const float hi = (float)vals[i];
-      vdf[i] = make_float2(hi, (float)(vals[i] - (double)hi));
-    }
-    TRY(upload(h, &b.vals_df, vdf));
-    b.hvals = vals;
-    *id = (int)h->bands.size();
-    h->bands.push_back(b);
+    TRY(band_from_mat(h, A, id));
     band_ids[key] = *id;
     return FDST_OK;
   };
@@ -459,6 +471,88 @@ static fdst_status build_matvec(fdst_ctx *h) {
     TRY(dalloc(h, &h->x2, (size_t)h->n_total * h->max_rhs));
     TRY(dalloc(h, &h->y2, (size_t)h->n_total * h->max_rhs));
   }
+  return FDST_OK;
+}
+
+// ------------------------------------------------------------------ setup: matrix-free mapped operator
+
+// Sum factorization of the mapped operator (Sec. 3 forms on the mapped domain,
+// the quadrature of the assembly): per direction d the values Bv_d and
+// derivatives Dv_d of the velocity basis and the values Bp_d of the pressure
+// basis at the quadrature points (banded: a point sees p + 2 functions), and
+// their transposes. Forward plan: G[r][a] = (x)_e (e == a ? Dv_e : Bv_e) u_r,
+// P = (x)_e Bp_e p; backward plan: y_r = sum_a (x)_e (e == a ? Dv_e : Bv_e)^T F[r][a],
+// y_p = (x)_e Bp_e^T E, with the point stage (launch_mf_points_*) in between.
+static fdst_status build_matrix_free(fdst_ctx *h) {
+  const GeoPoints &gp = h->gp;
+  int bv[3], dv[3], bp[3], bvt[3], dvt[3], bpt[3];
+  for (int d = 0; d < 3; ++d) {
+    std::vector<double> x, w;
+    span_rule(h->pres[d].knots, h->p + 2, x, w);
+    if ((int)x.size() != gp.nq[d]) { set_error("quadrature grid mismatch"); return FDST_CUDA_ERROR; }
+    const Space1D &sv = h->vel[0][d], &sp = h->pres[d];
+    Mat Bv((int)x.size(), sv.n), Dv((int)x.size(), sv.n), Bp((int)x.size(), sp.n);
+    double N[32], dN[32];
+    for (size_t q = 0; q < x.size(); ++q) {
+      int s_ = eval_nonzero(sv.knots, sv.degree, x[q], N, dN);
+      for (int i = 0; i <= sv.degree; ++i) {
+        const int gi = s_ - sv.degree + i - sv.first;
+        if (gi < 0 || gi >= sv.n) continue;
+        Bv((int)q, gi) = N[i];
+        Dv((int)q, gi) = dN[i];
+      }
+      s_ = eval_nonzero(sp.knots, sp.degree, x[q], N, dN);
+      for (int i = 0; i <= sp.degree; ++i) {
+        const int gi = s_ - sp.degree + i - sp.first;
+        if (gi < 0 || gi >= sp.n) continue;
+        Bp((int)q, gi) = N[i];
+      }
+    }
+    auto tr = [](const Mat &A) {
+      Mat T(A.cols, A.rows);
+      for (int i = 0; i < A.rows; ++i)
+        for (int j = 0; j < A.cols; ++j) T(j, i) = A(i, j);
+      return T;
+    };
+    TRY(band_from_mat(h, Bv, &bv[d]));
+    TRY(band_from_mat(h, Dv, &dv[d]));
+    TRY(band_from_mat(h, Bp, &bp[d]));
+    TRY(band_from_mat(h, tr(Bv), &bvt[d]));
+    TRY(band_from_mat(h, tr(Dv), &dvt[d]));
+    TRY(band_from_mat(h, tr(Bp), &bpt[d]));
+  }
+  std::vector<Term> fwd, bwd;
+  for (int r = 0; r < 3; ++r)
+    for (int a = 0; a < 3; ++a) {
+      Term t{3 * r + a, r, 1.0, {-1, -1, -1}};
+      for (int e = 0; e < 3; ++e) t.f[e] = e == a ? dv[e] : bv[e];
+      fwd.push_back(t);
+      Term u{r, 3 * r + a, 1.0, {-1, -1, -1}};
+      for (int e = 0; e < 3; ++e) u.f[e] = e == a ? dvt[e] : bvt[e];
+      bwd.push_back(u);
+    }
+  fwd.push_back(Term{9, 3, 1.0, {bp[0], bp[1], bp[2]}});
+  bwd.push_back(Term{3, 9, 1.0, {bpt[0], bpt[1], bpt[2]}});
+  const std::array<int, 3> pts{gp.nq[0], gp.nq[1], gp.nq[2]};
+  std::vector<std::array<int, 3>> shapes(10, pts);
+  TRY(build_plan(h, fwd, h->mf_fwd, h->mf_fwd_df, h->mf_fwd_t1s, h->mf_fwd_gs, nullptr, 10));
+  TRY(build_plan(h, bwd, h->mf_bwd, h->mf_bwd_df, h->mf_bwd_t1s, h->mf_bwd_gs, &shapes, 4));
+  TRY(alloc_plan_buffers(h, h->mf_fwd_t1s, h->mf_fwd_gs, h->mf_fwd_t1, h->mf_fwd_g));
+  TRY(alloc_plan_buffers(h, h->mf_bwd_t1s, h->mf_bwd_gs, h->mf_bwd_t1, h->mf_bwd_g));
+  h->mf_Q = gp.Q;
+  for (int f = 0; f < 10; ++f) h->mf_foff[f] = f * gp.Q;
+  const size_t nf = (size_t)10 * gp.Q * h->max_rhs;
+  if (h->desc.matvec_precision == FDST_MV_DF64) {
+    TRY(dalloc(h, &h->mf_Fw, nf));
+    TRY(dalloc(h, &h->mf_jd, (size_t)9 * gp.Q));
+    TRY(dalloc(h, &h->mf_wd, (size_t)gp.Q));
+    TRY(dalloc(h, &h->mf_nu, (size_t)gp.Q));
+    if (!h->y2) TRY(dalloc(h, &h->y2, (size_t)h->n_total * h->max_rhs));
+    launch_mf_geo_df(gp, h->mf_jd, h->mf_wd, h->mf_nu, 0);
+  } else {
+    TRY(dalloc(h, &h->mf_F, nf));
+  }
+  h->mf = true;
   return FDST_OK;
 }
 
@@ -602,14 +696,21 @@ static void kernel_span(fdst_ctx *h, cudaEvent_t a, int64_t launches, cudaStream
 }
 
 // A plan's ops over the buffers of that plan (the full operator, or its B or B^T part).
+// Source blocks (in_kind 0) at x + in_off[id] and result blocks (out_kind 3) at
+// y + out_off[id], right-hand sides in_stride / out_stride apart; xw, yw the
+// double-float images of x and y (same offsets and strides).
 struct PlanView {
   const std::vector<PlanOp> *ops;
   const std::vector<double *> *t1, *g;
   const std::vector<int64_t> *t1_size, *g_size;
+  const int64_t *in_off, *out_off;
+  int64_t in_stride, out_stride;
+  float2 *xw, *yw;
 };
 
 static PlanView full_view(fdst_ctx *h, bool df) {
-  return PlanView{df ? &h->plan_df : &h->plan, &h->t1, &h->g, &h->t1_size, &h->g_size};
+  return PlanView{df ? &h->plan_df : &h->plan, &h->t1, &h->g, &h->t1_size, &h->g_size,
+                  h->off, h->off, h->n_total, h->n_total, h->x2, h->y2};
 }
 
 // Adds the durations of the recorded compute-launch spans to ms_kernel (the stream
@@ -646,10 +747,10 @@ static fdst_status run_plan_f64(fdst_ctx *h, const PlanView &V, const double *x,
       b.vals = bd.vals; b.lo = bd.lo; b.w = bd.w; b.rows = bd.rows;
       b.d0 = op.dims[0]; b.d1 = op.dims[1]; b.d2 = op.dims[2]; b.mode = op.mode;
       b.coef = op.coef; b.accumulate = op.accumulate;
-      if (op.in_kind == 0) { b.X = x + h->off[op.in_id]; b.x_rhs_stride = h->n_total; }
+      if (op.in_kind == 0) { b.X = x + V.in_off[op.in_id]; b.x_rhs_stride = V.in_stride; }
       else if (op.in_kind == 1) { b.X = (*V.t1)[op.in_id]; b.x_rhs_stride = (*V.t1_size)[op.in_id]; }
       else { b.X = (*V.g)[op.in_id]; b.x_rhs_stride = (*V.g_size)[op.in_id]; }
-      if (op.out_kind == 3) { b.Y = y + h->off[op.out_id]; b.y_rhs_stride = h->n_total; }
+      if (op.out_kind == 3) { b.Y = y + V.out_off[op.out_id]; b.y_rhs_stride = V.out_stride; }
       else if (op.out_kind == 1) { b.Y = (*V.t1)[op.out_id]; b.y_rhs_stride = (*V.t1_size)[op.out_id]; }
       else { b.Y = (*V.g)[op.out_id]; b.y_rhs_stride = (*V.g_size)[op.out_id]; }
       ++i;
@@ -668,7 +769,7 @@ static fdst_status run_plan_f64(fdst_ctx *h, const PlanView &V, const double *x,
 static fdst_status run_plan_df(fdst_ctx *h, const PlanView &V, const double *x, double *y, int nrhs,
                                const int *done, cudaStream_t st, int64_t in_lo, int64_t in_hi, int64_t out_lo,
                                int64_t out_hi, bool timed) {
-  launch_split_df(x + in_lo, h->x2 + in_lo, in_hi - in_lo, h->n_total, nrhs, done, st);
+  if (x) launch_split_df(x + in_lo, V.xw + in_lo, in_hi - in_lo, V.in_stride, nrhs, done, st);
   cudaEvent_t k0 = timed ? kernel_mark(h, st) : nullptr;
   int64_t nl = 0;
   size_t i = 0;
@@ -688,10 +789,10 @@ static fdst_status run_plan_df(fdst_ctx *h, const PlanView &V, const double *x, 
       b.d0 = op.dims[0]; b.d1 = op.dims[1]; b.d2 = op.dims[2]; b.mode = op.mode;
       b.accumulate = op.accumulate;
       b.swap = op.swap;
-      if (op.in_kind == 0) { b.X = h->x2 + h->off[op.in_id]; b.x_rhs_stride = h->n_total; }
+      if (op.in_kind == 0) { b.X = V.xw + V.in_off[op.in_id]; b.x_rhs_stride = V.in_stride; }
       else if (op.in_kind == 1) { b.X = reinterpret_cast<const float2 *>((*V.t1)[op.in_id]); b.x_rhs_stride = (*V.t1_size)[op.in_id]; }
       else { b.X = reinterpret_cast<const float2 *>((*V.g)[op.in_id]); b.x_rhs_stride = (*V.g_size)[op.in_id]; }
-      if (op.out_kind == 3) { b.Y = h->y2 + h->off[op.out_id]; b.y_rhs_stride = h->n_total; }
+      if (op.out_kind == 3) { b.Y = V.yw + V.out_off[op.out_id]; b.y_rhs_stride = V.out_stride; }
       else if (op.out_kind == 1) { b.Y = reinterpret_cast<float2 *>((*V.t1)[op.out_id]); b.y_rhs_stride = (*V.t1_size)[op.out_id]; }
       else { b.Y = reinterpret_cast<float2 *>((*V.g)[op.out_id]); b.y_rhs_stride = (*V.g_size)[op.out_id]; }
       ++i;
@@ -700,7 +801,32 @@ static fdst_status run_plan_df(fdst_ctx *h, const PlanView &V, const double *x, 
     ++nl;
   }
   kernel_span(h, k0, nl, st);
-  launch_join_df(h->y2 + out_lo, y + out_lo, out_hi - out_lo, h->n_total, nrhs, done, st);
+  if (y) launch_join_df(V.yw + out_lo, y + out_lo, out_hi - out_lo, V.out_stride, nrhs, done, st);
+  CK(cudaGetLastError());
+  return FDST_OK;
+}
+
+// y = A x by sum factorization (the iterations' arithmetic).
+static fdst_status run_matvec_mf(fdst_ctx *h, const double *x, double *y, int nrhs, const int *done,
+                                 cudaStream_t st) {
+  const int64_t fs = 10 * h->mf_Q, n = h->n_total;
+  if (h->mf_Fw) {
+    const PlanView Vf{&h->mf_fwd_df, &h->mf_fwd_t1, &h->mf_fwd_g, &h->mf_fwd_t1s, &h->mf_fwd_gs,
+                      h->off, h->mf_foff, n, fs, h->x2, h->mf_Fw};
+    const PlanView Vb{&h->mf_bwd_df, &h->mf_bwd_t1, &h->mf_bwd_g, &h->mf_bwd_t1s, &h->mf_bwd_gs,
+                      h->mf_foff, h->off, fs, n, h->mf_Fw, h->y2};
+    TRY(run_plan_df(h, Vf, x, nullptr, nrhs, done, st, 0, n, 0, 0, true));
+    launch_mf_points_df(h->mf_Fw, h->mf_Q, fs, nrhs, h->mf_jd, h->mf_wd, h->mf_nu, done, st);
+    TRY(run_plan_df(h, Vb, nullptr, y, nrhs, done, st, 0, 0, 0, n, true));
+  } else {
+    const PlanView Vf{&h->mf_fwd, &h->mf_fwd_t1, &h->mf_fwd_g, &h->mf_fwd_t1s, &h->mf_fwd_gs,
+                      h->off, h->mf_foff, n, fs, nullptr, nullptr};
+    const PlanView Vb{&h->mf_bwd, &h->mf_bwd_t1, &h->mf_bwd_g, &h->mf_bwd_t1s, &h->mf_bwd_gs,
+                      h->mf_foff, h->off, fs, n, nullptr, nullptr};
+    TRY(run_plan_f64(h, Vf, x, h->mf_F, nrhs, done, st, true));
+    launch_mf_points_f64(h->mf_F, h->mf_Q, fs, nrhs, h->gp, done, st);
+    TRY(run_plan_f64(h, Vb, h->mf_F, y, nrhs, done, st, true));
+  }
   CK(cudaGetLastError());
   return FDST_OK;
 }
@@ -754,6 +880,7 @@ fdst_status minres_restart(fdst_ctx *h, const double *b, double *x, int nrhs, co
 // exact = true forces the FP64 (DFMA) evaluation (true-residual checks).
 fdst_status run_matvec(fdst_ctx *h, const double *x, double *y, int nrhs, const int *done, cudaStream_t st,
                        bool exact) {
+  if (h->mapped && h->mf && !exact) return run_matvec_mf(h, x, y, nrhs, done, st);
   if (h->mapped) {
     if (!exact && h->csr.val_df) {
       launch_split_df(x, h->x2, h->n_total, h->n_total, nrhs, done, st);
@@ -845,7 +972,8 @@ static fdst_status apply_coupling(fdst_ctx *h, bool transpose, const double *x, 
     return FDST_OK;
   }
   const auto &S = transpose ? h->plan_bt : h->plan_b;
-  const PlanView V{df ? &S.ops_df : &S.ops, &S.t1, &S.g, &S.t1_size, &S.g_size};
+  const PlanView V{df ? &S.ops_df : &S.ops, &S.t1, &S.g, &S.t1_size, &S.g_size, h->off, h->off, h->n_total,
+                   h->n_total, h->x2, h->y2};
   const int64_t nv = h->off[h->dim], n = h->n_total;
   if (df)
     return transpose ? run_plan_df(h, V, x, y, nrhs, done, st, nv, n, 0, nv, false)
@@ -943,6 +1071,10 @@ fdst_status fdst_setup(const fdst_desc *desc, fdst_handle *out) {
     set_error("P_D^G is built for the mapped geometry (on the identity map it equals P_D)");
     return FDST_NOT_SUPPORTED;
   }
+  if (desc->matvec_form != FDST_MATVEC_ASSEMBLED && desc->matvec_form != FDST_MATVEC_MATRIX_FREE) {
+    set_error("unknown matvec form");
+    return FDST_INVALID_ARGUMENT;
+  }
   if (desc->matvec_precision != FDST_MV_F64 && desc->matvec_precision != FDST_MV_DF64) {
     set_error("unknown matvec precision");
     return FDST_INVALID_ARGUMENT;
@@ -977,6 +1109,8 @@ fdst_status fdst_setup(const fdst_desc *desc, fdst_handle *out) {
     if ((st = tc_prepare(hp)) != FDST_OK) return fail(st);
   }
   if (!hp->mapped && (st = build_matvec(hp)) != FDST_OK) return fail(st);
+  if (hp->mapped && desc->matvec_form == FDST_MATVEC_MATRIX_FREE && (st = build_matrix_free(hp)) != FDST_OK)
+    return fail(st);
   const size_t nv = (size_t)hp->n_total * hp->max_rhs;
   if ((st = dalloc(hp, &hp->work[0], nv)) != FDST_OK) return fail(st);
   if ((st = dalloc(hp, &hp->work[1], nv)) != FDST_OK) return fail(st);
@@ -1023,12 +1157,19 @@ fdst_status fdst_get_sizes(fdst_handle h, fdst_sizes *out) {
     fa += 2.0 * (double)c.size * sum_n;   // each step: 2 K N R flops with K = N = n_d, R N = size
   }
   out->flops_apply = fa;
-  double fm = h->mapped ? 2.0 * (double)h->csr.nnz : 0.0;
-  for (auto &op : h->plan) {
-    int od[3] = {op.dims[0], op.dims[1], op.dims[2]};
-    od[op.mode] = h->bands[op.band].rows;
-    fm += 2.0 * h->bands[op.band].w * (double)od[0] * od[1] * od[2];
-  }
+  // matvec flops: 2 x nonzeros of the CSR, or 2 x (band entries used) over the banded
+  // products of the Kronecker plan or of the matrix-free plans (their point stage not counted)
+  double fm = h->mapped && !h->mf ? 2.0 * (double)h->csr.nnz : 0.0;
+  auto add_plan = [&](const std::vector<PlanOp> &P) {
+    for (auto &op : P) {
+      int od[3] = {op.dims[0], op.dims[1], op.dims[2]};
+      od[op.mode] = h->bands[op.band].rows;
+      fm += 2.0 * h->bands[op.band].w * (double)od[0] * od[1] * od[2];
+    }
+  };
+  add_plan(h->plan);
+  add_plan(h->mf_fwd);
+  add_plan(h->mf_bwd);
   out->flops_matvec = fm;
   return FDST_OK;
 }

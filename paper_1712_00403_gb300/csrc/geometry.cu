@@ -8,6 +8,7 @@
 #include <cmath>
 
 #include "df_arith.cuh"
+#include "fp_bits.cuh"
 #include "geometry.h"
 #include "kernels.h"
 
@@ -582,6 +583,146 @@ void launch_csr_copy_range(const CsrDev &A, int64_t r0, int64_t nr, int c_lo, in
   count_launch(1);
   k_csr_copy_range<<<152 * 16, 256, 0, s>>>(A.row_ptr, A.col, A.val, A.val_df, r0, nr, c_lo, c_hi, out_ptr, ocol,
                                             oval, oval_df);
+}
+
+// ------------------------------------------------------------------ matrix-free mapped operator: the points
+// At each quadrature point q (q0 fastest) and right-hand side, from the fields
+// G[r][a] = d u_r / d eta_a (r, a < 3) and P = p(q) (field 3 r + a and 9, Q apart):
+//   gx[r][c] = sum_a G[r][a] (J^{-1})_{ac},  sigma = nu (gx + gx^T) - P I,
+//   F[r][a]  = wd sum_c sigma[r][c] (J^{-1})_{ac},  E = -wd (gx[0][0] + gx[1][1] + gx[2][2]),
+// wd = w0 w1 w2 det J; F and E overwrite G and P (Sec. 3 forms a, b on the mapped domain).
+
+__global__ void k_mf_points_f64(double *Fd, int64_t Q, int64_t fstride, const double *jinv, const double *det,
+                                const double *nu, const double *w0, const double *w1, const double *w2, int q0,
+                                int q1, const int *done) {
+  const int rhs = blockIdx.y;
+  if (done && done[rhs]) return;
+  double *F = Fd + rhs * fstride;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < Q; q += (int64_t)gridDim.x * blockDim.x) {
+    const int i0 = (int)(q % q0);
+    const int64_t t = q / q0;
+    const int i1 = (int)(t % q1), i2 = (int)(t / q1);
+    const double wd = w0[i0] * w1[i1] * w2[i2] * det[q];
+    double Ji[3][3], G[3][3], gx[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        Ji[a][c] = jinv[(3 * a + c) * Q + q];
+        G[a][c] = F[(3 * a + c) * Q + q];
+      }
+    const double P = F[9 * Q + q], nq = nu[q];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) gx[r][c] = G[r][0] * Ji[0][c] + G[r][1] * Ji[1][c] + G[r][2] * Ji[2][c];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      double sg[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) sg[c] = nq * (gx[r][c] + gx[c][r]) - (r == c ? P : 0.0);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) F[(3 * r + a) * Q + q] = wd * (sg[0] * Ji[a][0] + sg[1] * Ji[a][1] + sg[2] * Ji[a][2]);
+    }
+    F[9 * Q + q] = -wd * (gx[0][0] + gx[1][1] + gx[2][2]);
+  }
+}
+
+__device__ __forceinline__ float2 dfx_mul(float2 a, float2 b) {
+  float sh = 0.f, sl = 0.f;
+  df_fma_acc(a, b, sh, sl);
+  return df_norm(sh, sl);
+}
+
+__device__ __forceinline__ float2 dfx_add(float2 a, float2 b) {
+  float sh = a.x, sl = a.y;
+  df_add(sh, sl, b.x, b.y);
+  return df_norm(sh, sl);
+}
+
+__device__ __forceinline__ float2 dfx_dot3(float2 a0, float2 b0, float2 a1, float2 b1, float2 a2, float2 b2) {
+  float sh = 0.f, sl = 0.f;
+  df_fma_acc(a0, b0, sh, sl);
+  df_fma_acc(a1, b1, sh, sl);
+  df_fma_acc(a2, b2, sh, sl);
+  return df_norm(sh, sl);
+}
+
+// The same in double-float arithmetic on FP32 pairs (geometry: J^{-1}, wd and nu as pairs).
+__global__ void k_mf_points_df(float2 *Fd, int64_t Q, int64_t fstride, const float2 *jinv, const float2 *wd2,
+                               const float2 *nu2, const int *done) {
+  const int rhs = blockIdx.y;
+  if (done && done[rhs]) return;
+  float2 *F = Fd + rhs * fstride;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < Q; q += (int64_t)gridDim.x * blockDim.x) {
+    float2 Ji[3][3], gx[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) Ji[a][c] = jinv[(3 * a + c) * Q + q];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const float2 g0 = F[(3 * r) * Q + q], g1 = F[(3 * r + 1) * Q + q], g2 = F[(3 * r + 2) * Q + q];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) gx[r][c] = dfx_dot3(g0, Ji[0][c], g1, Ji[1][c], g2, Ji[2][c]);
+    }
+    const float2 P = F[9 * Q + q], nq = nu2[q], wd = wd2[q];
+    const float2 mP = make_float2(-P.x, -P.y);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      float2 sg[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        sg[c] = dfx_mul(nq, dfx_add(gx[r][c], gx[c][r]));
+        if (r == c) sg[c] = dfx_add(sg[c], mP);
+      }
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        F[(3 * r + a) * Q + q] = dfx_mul(wd, dfx_dot3(sg[0], Ji[a][0], sg[1], Ji[a][1], sg[2], Ji[a][2]));
+    }
+    const float2 dv = dfx_add(dfx_add(gx[0][0], gx[1][1]), gx[2][2]);
+    const float2 e = dfx_mul(wd, dv);
+    F[9 * Q + q] = make_float2(-e.x, -e.y);
+  }
+}
+
+// Geometry as FP32 pairs: J^{-1} (9 x Q), wd = w0 w1 w2 det J, nu.
+__global__ void k_mf_geo_df(const double *jinv, const double *det, const double *nu, const double *w0,
+                            const double *w1, const double *w2, int q0, int q1, int64_t Q, float2 *jd, float2 *wdd,
+                            float2 *nud) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < Q; q += (int64_t)gridDim.x * blockDim.x) {
+    const int i0 = (int)(q % q0);
+    const int64_t t = q / q0;
+    const int i1 = (int)(t % q1), i2 = (int)(t / q1);
+    for (int k = 0; k < 9; ++k) jd[k * Q + q] = f64_split(jinv[k * Q + q]);
+    wdd[q] = f64_split(w0[i0] * w1[i1] * w2[i2] * det[q]);
+    nud[q] = f64_split(nu[q]);
+  }
+}
+
+void launch_mf_points_f64(double *F, int64_t Q, int64_t fstride, int nrhs, const GeoPoints &gp, const int *done,
+                          cudaStream_t s) {
+  int64_t blocks = (Q + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  count_launch(1);
+  k_mf_points_f64<<<dim3((unsigned)blocks, nrhs), 256, 0, s>>>(F, Q, fstride, gp.jinv, gp.det, gp.nu, gp.wts[0],
+                                                                gp.wts[1], gp.wts[2], gp.nq[0], gp.nq[1], done);
+}
+
+void launch_mf_points_df(float2 *F, int64_t Q, int64_t fstride, int nrhs, const float2 *jd, const float2 *wdd,
+                         const float2 *nud, const int *done, cudaStream_t s) {
+  int64_t blocks = (Q + 127) / 128;
+  if (blocks > 4096) blocks = 4096;
+  count_launch(1);
+  k_mf_points_df<<<dim3((unsigned)blocks, nrhs), 128, 0, s>>>(F, Q, fstride, jd, wdd, nud, done);
+}
+
+void launch_mf_geo_df(const GeoPoints &gp, float2 *jd, float2 *wdd, float2 *nud, cudaStream_t s) {
+  int64_t blocks = (gp.Q + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  count_launch(1);
+  k_mf_geo_df<<<(unsigned)blocks, 256, 0, s>>>(gp.jinv, gp.det, gp.nu, gp.wts[0], gp.wts[1], gp.wts[2], gp.nq[0],
+                                               gp.nq[1], gp.Q, jd, wdd, nud);
 }
 
 }  // namespace fdst

@@ -62,6 +62,14 @@ void launch_spmv_df(const CsrDev &A, const float2 *x2, double *y, int64_t stride
 void launch_spmv(const CsrDev &A, const double *x, double *y, int64_t stride, int nrhs, const int *done,
                  cudaStream_t s);
 void launch_csr_diag(const CsrDev &A, double *d, cudaStream_t s);
+// Matrix-free mapped operator, the point stage: fields G[r][a] (3 r + a) and P (9) of each
+// right-hand side (Q entries each, fstride apart per right-hand side) replaced by the fluxes
+// F[r][a] and the pressure test field E (FP64, or FP32 pairs with the geometry as pairs).
+void launch_mf_points_f64(double *F, int64_t Q, int64_t fstride, int nrhs, const GeoPoints &gp, const int *done,
+                          cudaStream_t s);
+void launch_mf_points_df(float2 *F, int64_t Q, int64_t fstride, int nrhs, const float2 *jd, const float2 *wdd,
+                         const float2 *nud, const int *done, cudaStream_t s);
+void launch_mf_geo_df(const GeoPoints &gp, float2 *jd, float2 *wdd, float2 *nud, cudaStream_t s);
 // Rows [r0, r0 + nr) restricted to columns [c_lo, c_hi): cnt[q] = entries of row r0 + q
 // kept; the copy writes them (in order) at out_ptr[q] of the new arrays.
 void launch_csr_count_range(const CsrDev &A, int64_t r0, int64_t nr, int c_lo, int c_hi, int64_t *cnt,

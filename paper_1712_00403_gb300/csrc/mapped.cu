@@ -83,6 +83,7 @@ fdst_status build_mapped_pre(fdst_ctx *h) {
   TRY(dalloc(h, &gp.det, (size_t)gp.Q));
   TRY(dalloc(h, &gp.nu, (size_t)gp.Q));
   launch_geo_points(gp, kAmp, st);
+  h->gp = gp;
   // ---- separable fit of the 9 diagonal coefficients c^k_jj (log, midrange sweeps)
   const int fstride = std::max(gp.nq[0], std::max(gp.nq[1], gp.nq[2]));
   double *L = nullptr, *f = nullptr;

@@ -189,3 +189,43 @@ def test_ptg_gmres_matches_oracle():
     im = Pm.solve_gmres(b, x, prec=fd.PREC_PT, tol=1e-8, maxit=300)[0]
     assert im["status"] == "OK" and im["true_rel_res"] <= 1e-8
     assert im["iterations"] <= io["iters"] + 4
+
+
+@pytest.mark.parametrize("spec", CASES, ids=_ids)
+def test_matrix_free_matvec_matches_oracle(spec):
+    """Sum-factorized mapped operator (point-basis products, the point stage, the
+    transposed products) against the oracle's sum-factorized matvec: FP64 and
+    double-float within 1e-12."""
+    import paper_1712_00403_gb300 as fd
+    S = oracle_problem(spec)
+    G = geo.Grid(S)
+    X = np.stack([synth.random_vector(60 + j, S.n_total) for j in range(2)])
+    for mv in (fd.MV_F64, fd.MV_DF64):
+        P = _gpu(spec, max_rhs=2, matvec_precision=mv, matvec_form=fd.MATVEC_MATRIX_FREE)
+        A = _gpu(spec, max_rhs=2, matvec_precision=mv)
+        assert P.flops_matvec != A.flops_matvec          # the plans' flops, not 2 x nonzeros
+        x = torch.tensor(X.reshape(-1), device="cuda")
+        y = torch.empty_like(x)
+        k0 = fd.kernel_launches()
+        P.matvec(x, y)
+        assert fd.kernel_launches() - k0 >= 10           # banded products and the point stage, not one SpMV
+        out = y.cpu().numpy().reshape(2, -1)
+        for j in range(2):
+            ref = geo.matvec(S, G, X[j])
+            for o0, o1 in zip(P.block_offsets[:-1], P.block_offsets[1:]):
+                assert rel(out[j, o0:o1], ref[o0:o1]) <= 1e-12, mv
+
+
+def test_matrix_free_minres_matches_assembled():
+    import paper_1712_00403_gb300 as fd
+    spec = problem_spec(3, 2, 4)
+    b_h = synth.rhs(302, oracle_problem(spec).block_sizes)
+    its = {}
+    for form in (fd.MATVEC_ASSEMBLED, fd.MATVEC_MATRIX_FREE):
+        P = _gpu(spec, fd_precision=fd.FD_TF32X3, matvec_precision=fd.MV_DF64, matvec_form=form)
+        b = torch.tensor(b_h, device="cuda")
+        x = torch.zeros_like(b)
+        info = P.solve(b, x, tol=1e-8, maxit=600)[0]
+        assert info["status"] == "OK" and info["true_rel_res"] <= 1e-8
+        its[form] = info["iterations"]
+    assert abs(its[fd.MATVEC_MATRIX_FREE] - its[fd.MATVEC_ASSEMBLED]) <= 2
