@@ -649,24 +649,26 @@ __device__ __forceinline__ float2 dfx_dot3(float2 a0, float2 b0, float2 a1, floa
 }
 
 // The same in double-float arithmetic on FP32 pairs (geometry: J^{-1}, wd and nu as pairs).
-__global__ void k_mf_points_df(float2 *Fd, int64_t Q, int64_t fstride, const float2 *jinv, const float2 *wd2,
-                               const float2 *nu2, const int *done) {
-  const int rhs = blockIdx.y;
-  if (done && done[rhs]) return;
-  float2 *F = Fd + rhs * fstride;
+__global__ void k_mf_points_df(float2 *Fd, int64_t Q, int64_t fstride, int nrhs, const float2 *jinv,
+                               const float2 *wd2, const float2 *nu2, const int *done) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < Q; q += (int64_t)gridDim.x * blockDim.x) {
+    // the geometry of the point once, then every right-hand side
     float2 Ji[3][3], gx[3][3];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
       for (int c = 0; c < 3; ++c) Ji[a][c] = jinv[(3 * a + c) * Q + q];
+    const float2 nq = nu2[q], wd = wd2[q];
+    for (int rhs = 0; rhs < nrhs; ++rhs) {
+    if (done && done[rhs]) continue;
+    float2 *F = Fd + rhs * fstride;
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
       const float2 g0 = F[(3 * r) * Q + q], g1 = F[(3 * r + 1) * Q + q], g2 = F[(3 * r + 2) * Q + q];
 #pragma unroll
       for (int c = 0; c < 3; ++c) gx[r][c] = dfx_dot3(g0, Ji[0][c], g1, Ji[1][c], g2, Ji[2][c]);
     }
-    const float2 P = F[9 * Q + q], nq = nu2[q], wd = wd2[q];
+    const float2 P = F[9 * Q + q];
     const float2 mP = make_float2(-P.x, -P.y);
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
@@ -683,6 +685,7 @@ __global__ void k_mf_points_df(float2 *Fd, int64_t Q, int64_t fstride, const flo
     const float2 dv = dfx_add(dfx_add(gx[0][0], gx[1][1]), gx[2][2]);
     const float2 e = dfx_mul(wd, dv);
     F[9 * Q + q] = make_float2(-e.x, -e.y);
+    }
   }
 }
 
@@ -712,9 +715,9 @@ void launch_mf_points_f64(double *F, int64_t Q, int64_t fstride, int nrhs, const
 void launch_mf_points_df(float2 *F, int64_t Q, int64_t fstride, int nrhs, const float2 *jd, const float2 *wdd,
                          const float2 *nud, const int *done, cudaStream_t s) {
   int64_t blocks = (Q + 127) / 128;
-  if (blocks > 4096) blocks = 4096;
+  if (blocks > 152 * 16) blocks = 152 * 16;
   count_launch(1);
-  k_mf_points_df<<<dim3((unsigned)blocks, nrhs), 128, 0, s>>>(F, Q, fstride, jd, wdd, nud, done);
+  k_mf_points_df<<<(unsigned)blocks, 128, 0, s>>>(F, Q, fstride, nrhs, jd, wdd, nud, done);
 }
 
 void launch_mf_geo_df(const GeoPoints &gp, float2 *jd, float2 *wdd, float2 *nud, cudaStream_t s) {
