@@ -83,6 +83,9 @@ typedef struct {
   double cpen;             /* Nitsche penalty C_pen (RT); <= 0 selects 5(alpha+1) (Sec. 7) */
   int max_rhs;             /* most right-hand sides one call will pass (workspace sizing), >= 1 */
   int matvec_precision;    /* FDST_MV_F64 or FDST_MV_DF64 */
+  double geometry_amplitude;  /* sine-bump amplitude a of the mapped geometry, in (0, 0.25]; <= 0 selects 0.1 */
+  double viscosity_contrast;  /* mapped geometry: k >= 1 selects nu(x) = 1 + (k - 1)(1 - cos(2 pi x1)) / 2
+                                 (values in [1, k]); <= 0 selects nu(x) = 1 + 0.5 sin(2 pi x1) cos(2 pi x2) */
   int matvec_form;         /* mapped geometry: FDST_MATVEC_ASSEMBLED (CSR) or FDST_MATVEC_MATRIX_FREE
                               (sum factorization at the quadrature points in the iterations; the CSR
                               is still assembled for diag(A), B, B^T and the FP64 true residual);

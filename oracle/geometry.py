@@ -67,7 +67,12 @@ def geometry(eta, amp=AMP):
     return x, J, det, Jinv
 
 
-def viscosity(x):
+def viscosity(x, contrast=None):
+    """nu(x) = 1 + 0.5 sin(2 pi x1) cos(2 pi x2); with a contrast k >= 1 the
+    one-coordinate family nu(x) = 1 + (k - 1)(1 - cos(2 pi x1)) / 2, values in
+    [1, k] (the analytic stand-in for the paper's variable-viscosity test)."""
+    if contrast is not None:
+        return 1.0 + (contrast - 1.0) * (1.0 - np.cos(2 * np.pi * x[..., 0])) / 2.0
     return 1.0 + 0.5 * np.sin(2 * np.pi * x[..., 0]) * np.cos(2 * np.pi * x[..., 1])
 
 
@@ -77,7 +82,7 @@ class Grid:
     """Tensor Gauss grid (p+2 points per element per direction) with the
     geometry and viscosity at every point; axis d of the arrays is direction d+1."""
 
-    def __init__(self, S, amp=AMP, nu_const=None, npts=None):
+    def __init__(self, S, amp=AMP, nu_const=None, npts=None, contrast=None):
         self.S = S
         npts = S.p + 2 if npts is None else npts
         self.pts, self.wts = [], []
@@ -87,7 +92,7 @@ class Grid:
             self.wts.append(w)
         E = np.stack(np.meshgrid(*self.pts, indexing="ij"), axis=-1)
         self.x, self.J, self.det, self.Jinv = geometry(E, amp)
-        self.nu = np.full(self.det.shape, nu_const) if nu_const is not None else viscosity(self.x)
+        self.nu = np.full(self.det.shape, nu_const) if nu_const is not None else viscosity(self.x, contrast)
         W = self.wts[0][:, None, None] * self.wts[1][None, :, None] * self.wts[2][None, None, :]
         self.W = W
         # univariate tables at the points: value and derivative of each space

@@ -40,7 +40,8 @@ class Desc(ctypes.Structure):
                 ("h_knots", ctypes.POINTER(ctypes.c_double) * 3), ("nknots", ctypes.c_int * 3),
                 ("viscosity", ctypes.c_double), ("geometry", ctypes.c_int), ("variant", ctypes.c_int),
                 ("fd_precision", ctypes.c_int), ("cpen", ctypes.c_double), ("max_rhs", ctypes.c_int),
-                ("matvec_precision", ctypes.c_int), ("matvec_form", ctypes.c_int)]
+                ("matvec_precision", ctypes.c_int), ("geometry_amplitude", ctypes.c_double),
+                ("viscosity_contrast", ctypes.c_double), ("matvec_form", ctypes.c_int)]
 
 
 class Sizes(ctypes.Structure):
@@ -195,7 +196,7 @@ class Stokes:
 
     def __init__(self, knots, p, disc=TH, viscosity=1.0, fd_precision=FD_F64, max_rhs=1,
                  geometry=GEOM_IDENTITY, variant=VARIANT_PD, cpen=0.0, matvec_precision=MV_F64,
-                 matvec_form=MATVEC_ASSEMBLED):
+                 matvec_form=MATVEC_ASSEMBLED, geometry_amplitude=0.0, viscosity_contrast=0.0):
         lib = load_library()
         self._knots = [np.ascontiguousarray(k, dtype=np.float64) for k in knots]
         desc = Desc()
@@ -213,6 +214,8 @@ class Stokes:
         desc.max_rhs = max_rhs
         desc.matvec_precision = matvec_precision
         desc.matvec_form = matvec_form
+        desc.geometry_amplitude = geometry_amplitude
+        desc.viscosity_contrast = viscosity_contrast
         h = ctypes.c_void_p()
         _check(lib.fdst_setup(ctypes.byref(desc), ctypes.byref(h)))
         self._h = h

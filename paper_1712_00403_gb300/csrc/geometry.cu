@@ -18,8 +18,9 @@ namespace fdst {
 
 // x = eta + a s(eta) 1, s = sin(pi e1) sin(pi e2) sin(pi e3); J = I + 1 g^T with
 // g = a grad s; det J = 1 + 1.g; J^{-1} = I - 1 g^T / det (Sherman-Morrison);
-// nu(x) = 1 + 0.5 sin(2 pi x1) cos(2 pi x2).
-__global__ void k_geo_points(GeoPoints gp, double amp) {
+// nu(x) = 1 + 0.5 sin(2 pi x1) cos(2 pi x2), or with a contrast k >= 1
+// nu(x) = 1 + (k - 1)(1 - cos(2 pi x1)) / 2 (values in [1, k]).
+__global__ void k_geo_points(GeoPoints gp, double amp, double contrast) {
   const int64_t Q = gp.Q;
   const double pi = 3.14159265358979323846;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < Q; q += (int64_t)gridDim.x * blockDim.x) {
@@ -36,15 +37,16 @@ __global__ void k_geo_points(GeoPoints gp, double amp) {
       for (int j = 0; j < 3; ++j) gp.jinv[(int64_t)(i * 3 + j) * Q + q] = (i == j ? 1.0 : 0.0) - g[j] / det;
     gp.det[q] = det;
     const double x1 = e1 + s, x2 = e2 + s;
-    gp.nu[q] = 1.0 + 0.5 * sin(2.0 * pi * x1) * cos(2.0 * pi * x2);
+    gp.nu[q] = contrast > 0.0 ? 1.0 + (contrast - 1.0) * (1.0 - cos(2.0 * pi * x1)) * 0.5
+                              : 1.0 + 0.5 * sin(2.0 * pi * x1) * cos(2.0 * pi * x2);
   }
 }
 
-void launch_geo_points(const GeoPoints &gp, double amp, cudaStream_t s) {
+void launch_geo_points(const GeoPoints &gp, double amp, double contrast, cudaStream_t s) {
   int64_t blocks = (gp.Q + 255) / 256;
   if (blocks > 8192) blocks = 8192;
   count_launch(1);
-  k_geo_points<<<(unsigned)blocks, 256, 0, s>>>(gp, amp);
+  k_geo_points<<<(unsigned)blocks, 256, 0, s>>>(gp, amp, contrast);
 }
 
 // ------------------------------------------------------------------ separable fit

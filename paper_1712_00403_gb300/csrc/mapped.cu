@@ -82,7 +82,16 @@ fdst_status build_mapped_pre(fdst_ctx *h) {
   TRY(dalloc(h, &gp.jinv, (size_t)9 * gp.Q));
   TRY(dalloc(h, &gp.det, (size_t)gp.Q));
   TRY(dalloc(h, &gp.nu, (size_t)gp.Q));
-  launch_geo_points(gp, kAmp, st);
+  const double amp = h->desc.geometry_amplitude > 0.0 ? h->desc.geometry_amplitude : kAmp;
+  if (amp > 0.25) {
+    set_error("geometry_amplitude must be at most 0.25 (det J stays positive)");
+    return FDST_INVALID_ARGUMENT;
+  }
+  if (h->desc.viscosity_contrast > 0.0 && h->desc.viscosity_contrast < 1.0) {
+    set_error("viscosity_contrast must be >= 1 (or <= 0 for the default field)");
+    return FDST_INVALID_ARGUMENT;
+  }
+  launch_geo_points(gp, amp, h->desc.viscosity_contrast, st);
   h->gp = gp;
   // ---- separable fit of the 9 diagonal coefficients c^k_jj (log, midrange sweeps)
   const int fstride = std::max(gp.nq[0], std::max(gp.nq[1], gp.nq[2]));

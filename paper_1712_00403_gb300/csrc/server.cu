@@ -55,7 +55,8 @@ std::string problem_key(const fdst_desc &d, const std::vector<double> *knots) {
   std::ostringstream o;
   o.precision(17);
   o << d.dim << "|" << d.discretization << "|" << d.degree << "|" << d.viscosity << "|" << d.fd_precision << "|"
-    << d.matvec_precision << "|" << d.cpen;
+    << d.matvec_precision << "|" << d.cpen << "|" << d.geometry << "|" << d.variant << "|" << d.geometry_amplitude
+    << "|" << d.viscosity_contrast << "|" << d.matvec_form;
   for (int e = 0; e < d.dim; ++e) {
     o << "#";
     for (double v : knots[e]) o << v << ",";

@@ -8,9 +8,9 @@ import numpy as np
 import pytest
 
 import synth
-from oracle import geometry as geo, minres
+from oracle import geometry as geo, minres, stokes
 
-from _helpers import oracle_problem, problem_spec, rel
+from _helpers import knots_of, oracle_problem, problem_spec, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -229,3 +229,55 @@ def test_matrix_free_minres_matches_assembled():
         assert info["status"] == "OK" and info["true_rel_res"] <= 1e-8
         its[form] = info["iterations"]
     assert abs(its[fd.MATVEC_MATRIX_FREE] - its[fd.MATVEC_ASSEMBLED]) <= 2
+
+
+def test_contrast_and_amplitude_parity():
+    """Map amplitude 0.15 and viscosity contrast 100 (nu in [1, 100]): CSR matvec and
+    P_D^G apply against the oracle at the FP64 bars."""
+    import paper_1712_00403_gb300 as fd
+    spec = CASES[0]
+    S = oracle_problem(spec)
+    G = geo.Grid(S, amp=0.15, contrast=100.0)
+    pdg = geo.PDG(S, G)
+    P = _gpu(spec, geometry_amplitude=0.15, viscosity_contrast=100.0)
+    X = synth.random_vector(61, S.n_total)
+    x = torch.tensor(X, device="cuda")
+    y = torch.empty_like(x)
+    P.matvec(x, y)
+    ref = geo.matvec(S, G, X)
+    s = torch.empty_like(x)
+    P.apply_prec(x, s)
+    ref_s = pdg.apply(X)
+    out, out_s = y.cpu().numpy(), s.cpu().numpy()
+    for o0, o1 in zip(P.block_offsets[:-1], P.block_offsets[1:]):
+        assert rel(out[o0:o1], ref[o0:o1]) <= 1e-12
+        assert rel(out_s[o0:o1], ref_s[o0:o1]) <= 1e-11
+
+
+def test_viscosity_contrast_robustness():
+    """The variable-viscosity trend of the paper's torus test on the analytic
+    stand-in (nu in [1, k]): with the estimate-only stopping rule P_D^G-MINRES needs
+    about the same iterations for k = 1, 100, 1e4 while P_D (cube blocks, no
+    geometry or viscosity) needs several times more as k grows; GPU counts match
+    the oracle's."""
+    import paper_1712_00403_gb300 as fd
+    spec = problem_spec(3, 2, 4)
+    S = oracle_problem(spec)
+    b_h = synth.rhs(5, S.block_sizes)
+    its = {}
+    for k in (1.0, 100.0, 1.0e4):
+        G = geo.Grid(S, contrast=k)
+        pdg = geo.PDG(S, G)
+        A = lambda v: geo.matvec(S, G, v)
+        for name, variant, apply in (("PDG", fd.VARIANT_PD_GEO, pdg.apply),
+                                     ("PD", fd.VARIANT_PD, lambda v: stokes.apply_PD_inv(S, v))):
+            _, io = minres.minres(A, b_h, apply, tol=1e-8, maxit=4000, true_check=False)
+            P = fd.Stokes(knots_of(spec), spec["p"], geometry=fd.GEOM_SINE_BUMP, variant=variant,
+                          viscosity_contrast=k)
+            b = torch.tensor(b_h, device="cuda")
+            x = torch.zeros_like(b)
+            info = P.solve(b, x, tol=1e-8, maxit=io["iters"] + 20)[0]
+            its[(name, k)] = info["iterations_estimate"]
+            assert abs(info["iterations_estimate"] - io["iters"]) <= max(2, 0.02 * io["iters"]), (name, k, info, io)
+    assert its[("PDG", 1e4)] <= 2 * its[("PDG", 1.0)] + 150
+    assert its[("PD", 1e4)] >= 4 * its[("PDG", 1e4)]

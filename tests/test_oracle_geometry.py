@@ -167,3 +167,23 @@ def test_mapped_block_preconditioners_match_dense_inverses():
     for apply, P in ((geo.apply_PTG_inv, PT), (geo.apply_PCG_inv, PC)):
         ref = np.linalg.solve(P, r)
         np.testing.assert_allclose(apply(S, G, pdg, r), ref, rtol=1e-9, atol=1e-9 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("k", [1.0, 100.0, 1.0e4])
+def test_viscosity_contrast_family_and_exact_fit_on_the_cube(k):
+    """nu_k(x) = 1 + (k - 1)(1 - cos(2 pi x1)) / 2 takes values in [1, k]; on the
+    identity map it depends on eta1 alone, so the separable fit is exact and the
+    weighted Kronecker sum equals the velocity diagonal block A_kk (D_V = 1)."""
+    x = np.stack(np.meshgrid(np.linspace(0, 1, 9), np.linspace(0, 1, 5), [0.3], indexing="ij"), -1)
+    nu = geo.viscosity(x, k)
+    assert nu.min() >= 1.0 - 1e-15 and nu.max() <= k * (1 + 1e-15)
+    S = stokes.build_uniform((3, 2, 2), 2, 3)
+    G = geo.Grid(S, amp=0.0, contrast=k)
+    pdg = geo.PDG(S, G)
+    A_bf, _ = geo.brute_force(S, G)
+    off = np.concatenate([[0], np.cumsum(S.block_sizes[:3])])
+    for c in range(3):
+        Ks, Ms, coef = pdg.pencils[c]
+        np.testing.assert_allclose(pdg.DV[c], 1.0, rtol=1e-9)
+        Akk = A_bf[off[c]:off[c + 1], off[c]:off[c + 1]]
+        np.testing.assert_allclose(kron.kron_sum_matrix(Ks, Ms, coef), Akk, atol=1e-9 * np.abs(Akk).max())
