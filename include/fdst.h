@@ -87,8 +87,8 @@ typedef struct {
   double viscosity_contrast;  /* mapped geometry: k >= 1 selects nu(x) = 1 + (k - 1)(1 - cos(2 pi x1)) / 2
                                  (values in [1, k]); <= 0 selects nu(x) = 1 + 0.5 sin(2 pi x1) cos(2 pi x2) */
   int matvec_form;         /* mapped geometry: FDST_MATVEC_ASSEMBLED (CSR) or FDST_MATVEC_MATRIX_FREE
-                              (sum factorization at the quadrature points in the iterations; the CSR
-                              is still assembled for diag(A), B, B^T and the FP64 true residual);
+                              (no CSR: the operator, its B and B^T parts and diag(A) by sum
+                              factorization at the quadrature points, FP64 for the true residual);
                               ignored on the identity map (Kronecker operator) */
 } fdst_desc;
 

@@ -137,6 +137,15 @@ struct fdst_ctx {
   std::vector<double *> mf_fwd_t1, mf_fwd_g, mf_bwd_t1, mf_bwd_g;
   double *mf_F = nullptr;
   float2 *mf_Fw = nullptr, *mf_jd = nullptr, *mf_wd = nullptr, *mf_nu = nullptr;
+  std::vector<fdst::Term> mf_fwd_terms, mf_bwd_terms;
+  // the B^T and B parts (pressure -> P -> fluxes -> velocity; velocity -> G -> E -> pressure)
+  struct MfPart {
+    std::vector<fdst::PlanOp> fwd, fwd_df, bwd, bwd_df;
+    std::vector<int64_t> fwd_t1s, fwd_gs, bwd_t1s, bwd_gs;
+    std::vector<double *> fwd_t1, fwd_g, bwd_t1, bwd_g;
+  } mf_bt, mf_b;
+  bool mf_parts = false;
+  int mf_bv[3] = {}, mf_dv[3] = {};   // band ids of the velocity point-basis values / derivatives
   std::vector<std::vector<fdst::Mat>> geo_K, geo_M;   // [component][direction]
   std::vector<std::vector<double>> geo_scale;          // D^{-1/2} per block (P_D^G)
   // timing
@@ -185,6 +194,8 @@ inline fdst_status upload(fdst_ctx *h, T **p, const std::vector<T> &v) {
 // s = P_D^{-1} r on the blocks in block_mask (bit b: block b; velocity 0..dim-1, pressure dim).
 // B and B^T blocks of the assembled mapped operator (csr_b, csr_bt).
 fdst_status build_coupling_csr(fdst_ctx *h);
+// D_V^{-1/2} of P_D^G (h->geo_scale[0..2]) from diag(A) over the block vector.
+void set_velocity_scaling(fdst_ctx *h, const std::vector<double> &diagA);
 fdst_status run_apply(fdst_ctx *h, const double *r, double *s, int nrhs, const int *done, cudaStream_t st,
                       unsigned block_mask = ~0u);
 fdst_status run_matvec(fdst_ctx *h, const double *x, double *y, int nrhs, const int *done, cudaStream_t st,

@@ -533,6 +533,8 @@ static fdst_status build_matrix_free(fdst_ctx *h) {
     }
   fwd.push_back(Term{9, 3, 1.0, {bp[0], bp[1], bp[2]}});
   bwd.push_back(Term{3, 9, 1.0, {bpt[0], bpt[1], bpt[2]}});
+  h->mf_fwd_terms = fwd;
+  h->mf_bwd_terms = bwd;
   const std::array<int, 3> pts{gp.nq[0], gp.nq[1], gp.nq[2]};
   std::vector<std::array<int, 3>> shapes(10, pts);
   TRY(build_plan(h, fwd, h->mf_fwd, h->mf_fwd_df, h->mf_fwd_t1s, h->mf_fwd_gs, nullptr, 10));
@@ -542,6 +544,7 @@ static fdst_status build_matrix_free(fdst_ctx *h) {
   h->mf_Q = gp.Q;
   for (int f = 0; f < 10; ++f) h->mf_foff[f] = f * gp.Q;
   const size_t nf = (size_t)10 * gp.Q * h->max_rhs;
+  TRY(dalloc(h, &h->mf_F, nf));            // FP64 fields (true residuals; FP64 iterations)
   if (h->desc.matvec_precision == FDST_MV_DF64) {
     TRY(dalloc(h, &h->mf_Fw, nf));
     TRY(dalloc(h, &h->mf_jd, (size_t)9 * gp.Q));
@@ -549,10 +552,12 @@ static fdst_status build_matrix_free(fdst_ctx *h) {
     TRY(dalloc(h, &h->mf_nu, (size_t)gp.Q));
     if (!h->y2) TRY(dalloc(h, &h->y2, (size_t)h->n_total * h->max_rhs));
     launch_mf_geo_df(gp, h->mf_jd, h->mf_wd, h->mf_nu, 0);
-  } else {
-    TRY(dalloc(h, &h->mf_F, nf));
   }
   h->mf = true;
+  for (int d = 0; d < 3; ++d) {
+    h->mf_bv[d] = bv[d];
+    h->mf_dv[d] = dv[d];
+  }
   return FDST_OK;
 }
 
@@ -806,26 +811,58 @@ static fdst_status run_plan_df(fdst_ctx *h, const PlanView &V, const double *x, 
   return FDST_OK;
 }
 
-// y = A x by sum factorization (the iterations' arithmetic).
+// The B^T and B parts of the sum-factorized operator (built on first use):
+// B^T: pressure -> P -> fluxes of sigma = -P I -> velocity; B: velocity -> G -> E -> pressure.
+static fdst_status mf_build_parts(fdst_ctx *h) {
+  if (h->mf_parts) return FDST_OK;
+  const GeoPoints &gp = h->gp;
+  const std::array<int, 3> pts{gp.nq[0], gp.nq[1], gp.nq[2]};
+  std::vector<std::array<int, 3>> shapes(10, pts);
+  for (int part = 0; part < 2; ++part) {
+    auto &P = part == 0 ? h->mf_bt : h->mf_b;
+    std::vector<Term> f, b;
+    for (const Term &t : h->mf_fwd_terms)
+      if ((part == 0) == (t.src == 3)) f.push_back(t);
+    for (const Term &t : h->mf_bwd_terms)
+      if ((part == 0) == (t.dst < 3)) b.push_back(t);
+    TRY(build_plan(h, f, P.fwd, P.fwd_df, P.fwd_t1s, P.fwd_gs, nullptr, 10));
+    TRY(build_plan(h, b, P.bwd, P.bwd_df, P.bwd_t1s, P.bwd_gs, &shapes, 4));
+    TRY(alloc_plan_buffers(h, P.fwd_t1s, P.fwd_gs, P.fwd_t1, P.fwd_g));
+    TRY(alloc_plan_buffers(h, P.bwd_t1s, P.bwd_gs, P.bwd_t1, P.bwd_g));
+  }
+  h->mf_parts = true;
+  return FDST_OK;
+}
+
+// y = A x (which = 0), y_u = B^T x_p (1) or y_p = B x_u (2) by sum factorization, in
+// double-float (fields kept as FP32 pairs between the stages) or FP64.
 static fdst_status run_matvec_mf(fdst_ctx *h, const double *x, double *y, int nrhs, const int *done,
-                                 cudaStream_t st) {
-  const int64_t fs = 10 * h->mf_Q, n = h->n_total;
-  if (h->mf_Fw) {
-    const PlanView Vf{&h->mf_fwd_df, &h->mf_fwd_t1, &h->mf_fwd_g, &h->mf_fwd_t1s, &h->mf_fwd_gs,
-                      h->off, h->mf_foff, n, fs, h->x2, h->mf_Fw};
-    const PlanView Vb{&h->mf_bwd_df, &h->mf_bwd_t1, &h->mf_bwd_g, &h->mf_bwd_t1s, &h->mf_bwd_gs,
-                      h->mf_foff, h->off, fs, n, h->mf_Fw, h->y2};
-    TRY(run_plan_df(h, Vf, x, nullptr, nrhs, done, st, 0, n, 0, 0, true));
-    launch_mf_points_df(h->mf_Fw, h->mf_Q, fs, nrhs, h->mf_jd, h->mf_wd, h->mf_nu, done, st);
-    TRY(run_plan_df(h, Vb, nullptr, y, nrhs, done, st, 0, 0, 0, n, true));
+                                 cudaStream_t st, bool df, int which = 0) {
+  const int64_t fs = 10 * h->mf_Q, n = h->n_total, nv = h->off[3];
+  if (which) TRY(mf_build_parts(h));
+  const auto *P = which == 1 ? &h->mf_bt : which == 2 ? &h->mf_b : nullptr;
+  const auto &fo = P ? (df ? P->fwd_df : P->fwd) : (df ? h->mf_fwd_df : h->mf_fwd);
+  const auto &bo = P ? (df ? P->bwd_df : P->bwd) : (df ? h->mf_bwd_df : h->mf_bwd);
+  const auto &ft1 = P ? P->fwd_t1 : h->mf_fwd_t1, &fg = P ? P->fwd_g : h->mf_fwd_g;
+  const auto &bt1 = P ? P->bwd_t1 : h->mf_bwd_t1, &bg = P ? P->bwd_g : h->mf_bwd_g;
+  const auto &ft1s = P ? P->fwd_t1s : h->mf_fwd_t1s, &fgs = P ? P->fwd_gs : h->mf_fwd_gs;
+  const auto &bt1s = P ? P->bwd_t1s : h->mf_bwd_t1s, &bgs = P ? P->bwd_gs : h->mf_bwd_gs;
+  // entries read and written: all (operator), pressure -> velocity (B^T), velocity -> pressure (B)
+  const int64_t in_lo = which == 1 ? nv : 0, in_hi = which == 2 ? nv : n;
+  const int64_t out_lo = which == 2 ? nv : 0, out_hi = which == 1 ? nv : n;
+  const bool timed = which == 0;
+  if (df) {
+    const PlanView Vf{&fo, &ft1, &fg, &ft1s, &fgs, h->off, h->mf_foff, n, fs, h->x2, h->mf_Fw};
+    const PlanView Vb{&bo, &bt1, &bg, &bt1s, &bgs, h->mf_foff, h->off, fs, n, h->mf_Fw, h->y2};
+    TRY(run_plan_df(h, Vf, x, nullptr, nrhs, done, st, in_lo, in_hi, 0, 0, timed));
+    launch_mf_points_df(h->mf_Fw, h->mf_Q, fs, nrhs, h->mf_jd, h->mf_wd, h->mf_nu, done, which, st);
+    TRY(run_plan_df(h, Vb, nullptr, y, nrhs, done, st, 0, 0, out_lo, out_hi, timed));
   } else {
-    const PlanView Vf{&h->mf_fwd, &h->mf_fwd_t1, &h->mf_fwd_g, &h->mf_fwd_t1s, &h->mf_fwd_gs,
-                      h->off, h->mf_foff, n, fs, nullptr, nullptr};
-    const PlanView Vb{&h->mf_bwd, &h->mf_bwd_t1, &h->mf_bwd_g, &h->mf_bwd_t1s, &h->mf_bwd_gs,
-                      h->mf_foff, h->off, fs, n, nullptr, nullptr};
-    TRY(run_plan_f64(h, Vf, x, h->mf_F, nrhs, done, st, true));
-    launch_mf_points_f64(h->mf_F, h->mf_Q, fs, nrhs, h->gp, done, st);
-    TRY(run_plan_f64(h, Vb, h->mf_F, y, nrhs, done, st, true));
+    const PlanView Vf{&fo, &ft1, &fg, &ft1s, &fgs, h->off, h->mf_foff, n, fs, nullptr, nullptr};
+    const PlanView Vb{&bo, &bt1, &bg, &bt1s, &bgs, h->mf_foff, h->off, fs, n, nullptr, nullptr};
+    TRY(run_plan_f64(h, Vf, x, h->mf_F, nrhs, done, st, timed));
+    launch_mf_points_f64(h->mf_F, h->mf_Q, fs, nrhs, h->gp, done, which, st);
+    TRY(run_plan_f64(h, Vb, h->mf_F, y, nrhs, done, st, timed));
   }
   CK(cudaGetLastError());
   return FDST_OK;
@@ -880,7 +917,8 @@ fdst_status minres_restart(fdst_ctx *h, const double *b, double *x, int nrhs, co
 // exact = true forces the FP64 (DFMA) evaluation (true-residual checks).
 fdst_status run_matvec(fdst_ctx *h, const double *x, double *y, int nrhs, const int *done, cudaStream_t st,
                        bool exact) {
-  if (h->mapped && h->mf && !exact) return run_matvec_mf(h, x, y, nrhs, done, st);
+  if (h->mapped && h->mf)
+    return run_matvec_mf(h, x, y, nrhs, done, st, !exact && h->desc.matvec_precision == FDST_MV_DF64);
   if (h->mapped) {
     if (!exact && h->csr.val_df) {
       launch_split_df(x, h->x2, h->n_total, h->n_total, nrhs, done, st);
@@ -913,7 +951,7 @@ static void release(fdst_ctx *h, double *&p, size_t count) {
 }
 
 static fdst_status ensure_gmres(fdst_ctx *h, int cap, bool flexible) {
-  if (!h->gm_w && h->mapped) TRY(build_coupling_csr(h));
+  if (!h->gm_w && h->mapped && !h->mf) TRY(build_coupling_csr(h));
   if (!h->gm_w && !h->mapped) {
     std::vector<Term> tb, tbt;
     for (const Term &t : h->terms) {
@@ -958,6 +996,7 @@ static fdst_status ensure_gmres(fdst_ctx *h, int cap, bool flexible) {
 static fdst_status apply_coupling(fdst_ctx *h, bool transpose, const double *x, double *y, int nrhs,
                                   const int *done, cudaStream_t st) {
   const bool df = h->desc.matvec_precision == FDST_MV_DF64;
+  if (h->mapped && h->mf) return run_matvec_mf(h, x, y, nrhs, done, st, df, transpose ? 1 : 2);
   if (h->mapped) {
     const CsrDev &C = transpose ? h->csr_bt : h->csr_b;
     const int64_t nv = h->off[h->dim], n = h->n_total;
@@ -1006,6 +1045,72 @@ static fdst_status apply_block_prec(fdst_ctx *h, int kind, const double *r, doub
   }
   launch_axpby(s + nv, s + nv, 0.0, -1.0, nq, n, nrhs, st);    // q = -s_q
   CK(cudaGetLastError());
+  return FDST_OK;
+}
+
+// D_V of P_D^G for a matrix-free handle: diag(A) by sum factorization (the squared
+// point-basis bands tested against the 18 coefficient fields of launch_mf_diag_coef).
+static fdst_status mf_velocity_scaling(fdst_ctx *h) {
+  const GeoPoints &gp = h->gp;
+  const std::array<int, 3> pts{gp.nq[0], gp.nq[1], gp.nq[2]};
+  // diag(A) by sum factorization: the squared point-basis bands tested against the
+  // 18 coefficient fields of launch_mf_diag_coef, for D_V of P_D^G
+  int sq[3][3];   // [d][0: B.B, 1: B.D, 2: D.D], transposed (functions x points)
+  for (int d = 0; d < 3; ++d) {
+    const BandDev &B = h->bands[h->mf_bv[d]], &D = h->bands[h->mf_dv[d]];
+    const int nr = B.rows, nc = B.cols;
+    Mat bb(nc, nr), bd(nc, nr), dd(nc, nr);
+    std::vector<double> Bd((size_t)nr * nc, 0.0), Dd((size_t)nr * nc, 0.0);
+    std::vector<int> blo(nr), dlo(nr);
+    CK(cudaMemcpy(blo.data(), B.lo, sizeof(int) * nr, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(dlo.data(), D.lo, sizeof(int) * nr, cudaMemcpyDeviceToHost));
+    for (int i = 0; i < nr; ++i) {
+      for (int j = 0; j < B.w; ++j) Bd[(size_t)i * nc + blo[i] + j] = B.hvals[(size_t)i * B.w + j];
+      for (int j = 0; j < D.w; ++j) Dd[(size_t)i * nc + dlo[i] + j] = D.hvals[(size_t)i * D.w + j];
+    }
+    for (int i = 0; i < nr; ++i)
+      for (int j = 0; j < nc; ++j) {
+        const double b = Bd[(size_t)i * nc + j], e = Dd[(size_t)i * nc + j];
+        bb(j, i) = b * b;
+        bd(j, i) = b * e;
+        dd(j, i) = e * e;
+      }
+    TRY(band_from_mat(h, bb, &sq[d][0]));
+    TRY(band_from_mat(h, bd, &sq[d][1]));
+    TRY(band_from_mat(h, dd, &sq[d][2]));
+  }
+  std::vector<Term> dterms;
+  for (int r = 0; r < 3; ++r) {
+    int pi = 0;
+    for (int a = 0; a < 3; ++a)
+      for (int b = a; b < 3; ++b, ++pi) {
+        Term t{r, 6 * r + pi, 1.0, {-1, -1, -1}};
+        for (int d = 0; d < 3; ++d) t.f[d] = sq[d][(d == a) + (d == b)];
+        dterms.push_back(t);
+      }
+  }
+  std::vector<std::array<int, 3>> dshapes(18, pts);
+  std::vector<PlanOp> dops, dops_df;
+  std::vector<int64_t> dt1s, dgs;
+  std::vector<double *> dt1, dg;
+  TRY(build_plan(h, dterms, dops, dops_df, dt1s, dgs, &dshapes, 4));
+  TRY(alloc_plan_buffers(h, dt1s, dgs, dt1, dg));
+  double *C = nullptr, *dA = nullptr;
+  TRY(dalloc(h, &C, (size_t)18 * gp.Q));
+  TRY(dalloc(h, &dA, (size_t)h->n_total));
+  launch_mf_diag_coef(C, gp, 0);
+  int64_t coff[18];
+  for (int f = 0; f < 18; ++f) coff[f] = f * gp.Q;
+  const PlanView V{&dops, &dt1, &dg, &dt1s, &dgs, coff, h->off, 18 * gp.Q, h->n_total, nullptr, nullptr};
+  TRY(run_plan_f64(h, V, C, dA, 1, nullptr, 0, false));
+  std::vector<double> diagA((size_t)h->n_total);
+  CK(cudaMemcpy(diagA.data(), dA, sizeof(double) * h->off[3], cudaMemcpyDeviceToHost));
+  set_velocity_scaling(h, diagA);
+  // the coefficient fields and the diagonal plan's buffers are not needed again
+  release(h, C, (size_t)18 * gp.Q);
+  release(h, dA, (size_t)h->n_total);
+  for (size_t k = 0; k < dt1.size(); ++k) release(h, dt1[k], (size_t)dt1s[k] * h->max_rhs);
+  for (size_t k = 0; k < dg.size(); ++k) release(h, dg[k], (size_t)dgs[k] * h->max_rhs);
   return FDST_OK;
 }
 
@@ -1103,14 +1208,16 @@ fdst_status fdst_setup(const fdst_desc *desc, fdst_handle *out) {
   auto fail = [&](fdst_status s) { fdst_destroy(h.release()); return s; };
   if ((st = build_spaces(hp)) != FDST_OK) return fail(st);
   if (desc->geometry == FDST_GEOM_SINE_BUMP && (st = build_mapped_pre(hp)) != FDST_OK) return fail(st);
+  if (hp->mapped && desc->matvec_form == FDST_MATVEC_MATRIX_FREE) {
+    if ((st = build_matrix_free(hp)) != FDST_OK) return fail(st);
+    if (desc->variant == FDST_VARIANT_PD_GEO && (st = mf_velocity_scaling(hp)) != FDST_OK) return fail(st);
+  }
   if ((st = build_fd(hp)) != FDST_OK) return fail(st);
   if (hp->mapped && (st = build_mapped_post(hp)) != FDST_OK) return fail(st);
   if (desc->fd_precision != FDST_FD_F64) {
     if ((st = tc_prepare(hp)) != FDST_OK) return fail(st);
   }
   if (!hp->mapped && (st = build_matvec(hp)) != FDST_OK) return fail(st);
-  if (hp->mapped && desc->matvec_form == FDST_MATVEC_MATRIX_FREE && (st = build_matrix_free(hp)) != FDST_OK)
-    return fail(st);
   const size_t nv = (size_t)hp->n_total * hp->max_rhs;
   if ((st = dalloc(hp, &hp->work[0], nv)) != FDST_OK) return fail(st);
   if ((st = dalloc(hp, &hp->work[1], nv)) != FDST_OK) return fail(st);

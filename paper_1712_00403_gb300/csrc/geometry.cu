@@ -596,7 +596,7 @@ void launch_csr_copy_range(const CsrDev &A, int64_t r0, int64_t nr, int c_lo, in
 
 __global__ void k_mf_points_f64(double *Fd, int64_t Q, int64_t fstride, const double *jinv, const double *det,
                                 const double *nu, const double *w0, const double *w1, const double *w2, int q0,
-                                int q1, const int *done) {
+                                int q1, const int *done, int mode) {
   const int rhs = blockIdx.y;
   if (done && done[rhs]) return;
   double *F = Fd + rhs * fstride;
@@ -611,9 +611,9 @@ __global__ void k_mf_points_f64(double *Fd, int64_t Q, int64_t fstride, const do
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         Ji[a][c] = jinv[(3 * a + c) * Q + q];
-        G[a][c] = F[(3 * a + c) * Q + q];
+        G[a][c] = mode == 1 ? 0.0 : F[(3 * a + c) * Q + q];
       }
-    const double P = F[9 * Q + q], nq = nu[q];
+    const double P = mode == 2 ? 0.0 : F[9 * Q + q], nq = nu[q];
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
@@ -623,10 +623,12 @@ __global__ void k_mf_points_f64(double *Fd, int64_t Q, int64_t fstride, const do
       double sg[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) sg[c] = nq * (gx[r][c] + gx[c][r]) - (r == c ? P : 0.0);
+      if (mode != 2)
 #pragma unroll
-      for (int a = 0; a < 3; ++a) F[(3 * r + a) * Q + q] = wd * (sg[0] * Ji[a][0] + sg[1] * Ji[a][1] + sg[2] * Ji[a][2]);
+        for (int a = 0; a < 3; ++a)
+          F[(3 * r + a) * Q + q] = wd * (sg[0] * Ji[a][0] + sg[1] * Ji[a][1] + sg[2] * Ji[a][2]);
     }
-    F[9 * Q + q] = -wd * (gx[0][0] + gx[1][1] + gx[2][2]);
+    if (mode != 1) F[9 * Q + q] = -wd * (gx[0][0] + gx[1][1] + gx[2][2]);
   }
 }
 
@@ -652,7 +654,7 @@ __device__ __forceinline__ float2 dfx_dot3(float2 a0, float2 b0, float2 a1, floa
 
 // The same in double-float arithmetic on FP32 pairs (geometry: J^{-1}, wd and nu as pairs).
 __global__ void k_mf_points_df(float2 *Fd, int64_t Q, int64_t fstride, int nrhs, const float2 *jinv,
-                               const float2 *wd2, const float2 *nu2, const int *done) {
+                               const float2 *wd2, const float2 *nu2, const int *done, int mode) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < Q; q += (int64_t)gridDim.x * blockDim.x) {
     // the geometry of the point once, then every right-hand side
     float2 Ji[3][3], gx[3][3];
@@ -666,11 +668,13 @@ __global__ void k_mf_points_df(float2 *Fd, int64_t Q, int64_t fstride, int nrhs,
     float2 *F = Fd + rhs * fstride;
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-      const float2 g0 = F[(3 * r) * Q + q], g1 = F[(3 * r + 1) * Q + q], g2 = F[(3 * r + 2) * Q + q];
+      const float2 z = make_float2(0.f, 0.f);
+      const float2 g0 = mode == 1 ? z : F[(3 * r) * Q + q], g1 = mode == 1 ? z : F[(3 * r + 1) * Q + q],
+                   g2 = mode == 1 ? z : F[(3 * r + 2) * Q + q];
 #pragma unroll
       for (int c = 0; c < 3; ++c) gx[r][c] = dfx_dot3(g0, Ji[0][c], g1, Ji[1][c], g2, Ji[2][c]);
     }
-    const float2 P = F[9 * Q + q];
+    const float2 P = mode == 2 ? make_float2(0.f, 0.f) : F[9 * Q + q];
     const float2 mP = make_float2(-P.x, -P.y);
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
@@ -680,13 +684,16 @@ __global__ void k_mf_points_df(float2 *Fd, int64_t Q, int64_t fstride, int nrhs,
         sg[c] = dfx_mul(nq, dfx_add(gx[r][c], gx[c][r]));
         if (r == c) sg[c] = dfx_add(sg[c], mP);
       }
+      if (mode != 2)
 #pragma unroll
-      for (int a = 0; a < 3; ++a)
-        F[(3 * r + a) * Q + q] = dfx_mul(wd, dfx_dot3(sg[0], Ji[a][0], sg[1], Ji[a][1], sg[2], Ji[a][2]));
+        for (int a = 0; a < 3; ++a)
+          F[(3 * r + a) * Q + q] = dfx_mul(wd, dfx_dot3(sg[0], Ji[a][0], sg[1], Ji[a][1], sg[2], Ji[a][2]));
     }
-    const float2 dv = dfx_add(dfx_add(gx[0][0], gx[1][1]), gx[2][2]);
-    const float2 e = dfx_mul(wd, dv);
-    F[9 * Q + q] = make_float2(-e.x, -e.y);
+    if (mode != 1) {
+      const float2 dv = dfx_add(dfx_add(gx[0][0], gx[1][1]), gx[2][2]);
+      const float2 e = dfx_mul(wd, dv);
+      F[9 * Q + q] = make_float2(-e.x, -e.y);
+    }
     }
   }
 }
@@ -705,21 +712,54 @@ __global__ void k_mf_geo_df(const double *jinv, const double *det, const double 
   }
 }
 
+// Coefficient fields of diag(A) at the points: for velocity component r and the
+// direction pair (a, b), a <= b, C = m wd nu (sum_c Ji[a][c] Ji[b][c] + Ji[a][r] Ji[b][r])
+// with m = 2 for a < b, so that A_ii = sum_pairs sum_q C (d_a phi_i)(d_b phi_i)
+// (the symmetric-gradient form a(e_r phi, e_r phi)); field 6 r + pair, Q apart.
+__global__ void k_mf_diag_coef(double *C, int64_t Q, const double *jinv, const double *det, const double *nu,
+                               const double *w0, const double *w1, const double *w2, int q0, int q1) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < Q; q += (int64_t)gridDim.x * blockDim.x) {
+    const int i0 = (int)(q % q0);
+    const int64_t t = q / q0;
+    const int i1 = (int)(t % q1), i2 = (int)(t / q1);
+    const double wn = w0[i0] * w1[i1] * w2[i2] * det[q] * nu[q];
+    double Ji[3][3];
+    for (int a = 0; a < 3; ++a)
+      for (int c = 0; c < 3; ++c) Ji[a][c] = jinv[(3 * a + c) * Q + q];
+    for (int r = 0; r < 3; ++r) {
+      int pi = 0;
+      for (int a = 0; a < 3; ++a)
+        for (int b = a; b < 3; ++b, ++pi) {
+          const double g = Ji[a][0] * Ji[b][0] + Ji[a][1] * Ji[b][1] + Ji[a][2] * Ji[b][2] + Ji[a][r] * Ji[b][r];
+          C[(6 * r + pi) * Q + q] = (a == b ? 1.0 : 2.0) * wn * g;
+        }
+    }
+  }
+}
+
+void launch_mf_diag_coef(double *C, const GeoPoints &gp, cudaStream_t s) {
+  int64_t blocks = (gp.Q + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  count_launch(1);
+  k_mf_diag_coef<<<(unsigned)blocks, 256, 0, s>>>(C, gp.Q, gp.jinv, gp.det, gp.nu, gp.wts[0], gp.wts[1], gp.wts[2],
+                                                  gp.nq[0], gp.nq[1]);
+}
+
 void launch_mf_points_f64(double *F, int64_t Q, int64_t fstride, int nrhs, const GeoPoints &gp, const int *done,
-                          cudaStream_t s) {
+                          int mode, cudaStream_t s) {
   int64_t blocks = (Q + 255) / 256;
   if (blocks > 4096) blocks = 4096;
   count_launch(1);
   k_mf_points_f64<<<dim3((unsigned)blocks, nrhs), 256, 0, s>>>(F, Q, fstride, gp.jinv, gp.det, gp.nu, gp.wts[0],
-                                                                gp.wts[1], gp.wts[2], gp.nq[0], gp.nq[1], done);
+                                                                gp.wts[1], gp.wts[2], gp.nq[0], gp.nq[1], done, mode);
 }
 
 void launch_mf_points_df(float2 *F, int64_t Q, int64_t fstride, int nrhs, const float2 *jd, const float2 *wdd,
-                         const float2 *nud, const int *done, cudaStream_t s) {
+                         const float2 *nud, const int *done, int mode, cudaStream_t s) {
   int64_t blocks = (Q + 127) / 128;
   if (blocks > 152 * 16) blocks = 152 * 16;
   count_launch(1);
-  k_mf_points_df<<<(unsigned)blocks, 128, 0, s>>>(F, Q, fstride, nrhs, jd, wdd, nud, done);
+  k_mf_points_df<<<(unsigned)blocks, 128, 0, s>>>(F, Q, fstride, nrhs, jd, wdd, nud, done, mode);
 }
 
 void launch_mf_geo_df(const GeoPoints &gp, float2 *jd, float2 *wdd, float2 *nud, cudaStream_t s) {

@@ -65,10 +65,13 @@ void launch_csr_diag(const CsrDev &A, double *d, cudaStream_t s);
 // Matrix-free mapped operator, the point stage: fields G[r][a] (3 r + a) and P (9) of each
 // right-hand side (Q entries each, fstride apart per right-hand side) replaced by the fluxes
 // F[r][a] and the pressure test field E (FP64, or FP32 pairs with the geometry as pairs).
+// mode 0: the operator; 1: B^T only (P in, F out: sigma = -P I); 2: B only (G in, E out).
 void launch_mf_points_f64(double *F, int64_t Q, int64_t fstride, int nrhs, const GeoPoints &gp, const int *done,
-                          cudaStream_t s);
+                          int mode, cudaStream_t s);
 void launch_mf_points_df(float2 *F, int64_t Q, int64_t fstride, int nrhs, const float2 *jd, const float2 *wdd,
-                         const float2 *nud, const int *done, cudaStream_t s);
+                         const float2 *nud, const int *done, int mode, cudaStream_t s);
+// Coefficient fields of diag(A) (18 fields: velocity component r, direction pair (a <= b)).
+void launch_mf_diag_coef(double *C, const GeoPoints &gp, cudaStream_t s);
 void launch_mf_geo_df(const GeoPoints &gp, float2 *jd, float2 *wdd, float2 *nud, cudaStream_t s);
 // Rows [r0, r0 + nr) restricted to columns [c_lo, c_hi): cnt[q] = entries of row r0 + q
 // kept; the copy writes them (in order) at out_ptr[q] of the new arrays.

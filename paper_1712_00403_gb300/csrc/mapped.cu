@@ -54,6 +54,25 @@ void overlap_ranges(const std::vector<int> &relo, const std::vector<int> &rehi, 
 }
 }  // namespace
 
+// D_V^{-1/2} of P_D^G from diag(A) (the velocity entries of the block vector):
+// [D_V]_ii = A_ii / (P~_V)_ii with diag(P~_V) the Kronecker sum of the pencils' diagonals.
+void set_velocity_scaling(fdst_ctx *h, const std::vector<double> &diagA) {
+  for (int k = 0; k < 3; ++k) {
+    const int n1 = h->shape[k][0], n2 = h->shape[k][1], n3 = h->shape[k][2];
+    std::vector<double> &sc = h->geo_scale[k];
+    sc.resize((size_t)n1 * n2 * n3);
+    const Mat *Kf = h->geo_K[k].data(), *Mf = h->geo_M[k].data();
+    for (int i3 = 0; i3 < n3; ++i3)
+      for (int i2 = 0; i2 < n2; ++i2)
+        for (int i1 = 0; i1 < n1; ++i1) {
+          const double dp = Kf[2](i3, i3) * Mf[1](i2, i2) * Mf[0](i1, i1) + Mf[2](i3, i3) * Kf[1](i2, i2) * Mf[0](i1, i1) +
+                            Mf[2](i3, i3) * Mf[1](i2, i2) * Kf[0](i1, i1);
+          const size_t li = ((size_t)i3 * n2 + i2) * n1 + i1;
+          sc[li] = 1.0 / std::sqrt(diagA[h->off[k] + li] / dp);
+        }
+  }
+}
+
 fdst_status build_mapped_pre(fdst_ctx *h) {
   if (h->dim != 3 || h->desc.discretization != FDST_TH) {
     set_error("the mapped geometry is built for the 3D Taylor-Hood discretization");
@@ -186,93 +205,91 @@ fdst_status build_mapped_pre(fdst_ctx *h) {
     mt.p_elo[d] = a3;
     mt.p_ehi[d] = a4;
   }
-  // ---- CSR layout
-  CsrTables ct;
-  for (int b = 0; b < 5; ++b) ct.off[b] = h->off[b];
-  std::vector<std::vector<int>> vvlo(3), vvw(3), vplo(3), vpw(3), pvlo(3), pvw(3);
-  for (int d = 0; d < 3; ++d) {
-    const int nv = h->vel[0][d].n, np = h->pres[d].n;
-    ct.nv[d] = nv;
-    ct.np[d] = np;
-    overlap_ranges(velo[d], vehi[d], 1, nv, velo[d], vehi[d], 1, nv, vvlo[d], vvw[d]);
-    overlap_ranges(velo[d], vehi[d], 1, nv, pelo[d], pehi[d], 0, np, vplo[d], vpw[d]);
-    overlap_ranges(pelo[d], pehi[d], 0, np, velo[d], vehi[d], 1, nv, pvlo[d], pvw[d]);
-    int *t[6];
-    TRY(upload(h, &t[0], vvlo[d]));
-    TRY(upload(h, &t[1], vvw[d]));
-    TRY(upload(h, &t[2], vplo[d]));
-    TRY(upload(h, &t[3], vpw[d]));
-    TRY(upload(h, &t[4], pvlo[d]));
-    TRY(upload(h, &t[5], pvw[d]));
-    ct.vv_lo[d] = t[0]; ct.vv_w[d] = t[1];
-    ct.vp_lo[d] = t[2]; ct.vp_w[d] = t[3];
-    ct.pv_lo[d] = t[4]; ct.pv_w[d] = t[5];
-  }
+  // ---- CSR (not built for a matrix-free handle: its operator, diag(A), B and B^T are
+  // evaluated by sum factorization)
+  const bool mf_only = h->desc.matvec_form == FDST_MATVEC_MATRIX_FREE;
   const int64_t nrows = h->n_total;
-  std::vector<int64_t> rp(nrows + 1, 0);
-  for (int r = 0; r < 3; ++r)
-    for (int i3 = 0; i3 < ct.nv[2]; ++i3)
-      for (int i2 = 0; i2 < ct.nv[1]; ++i2)
-        for (int i1 = 0; i1 < ct.nv[0]; ++i1) {
-          const int64_t row = h->off[r] + ((int64_t)i3 * ct.nv[1] + i2) * ct.nv[0] + i1;
-          rp[row + 1] = 3LL * vvw[0][i1] * vvw[1][i2] * vvw[2][i3] + (int64_t)vpw[0][i1] * vpw[1][i2] * vpw[2][i3];
+  if (!mf_only) {
+    // ---- CSR layout
+    CsrTables ct;
+    for (int b = 0; b < 5; ++b) ct.off[b] = h->off[b];
+    std::vector<std::vector<int>> vvlo(3), vvw(3), vplo(3), vpw(3), pvlo(3), pvw(3);
+    for (int d = 0; d < 3; ++d) {
+      const int nv = h->vel[0][d].n, np = h->pres[d].n;
+      ct.nv[d] = nv;
+      ct.np[d] = np;
+      overlap_ranges(velo[d], vehi[d], 1, nv, velo[d], vehi[d], 1, nv, vvlo[d], vvw[d]);
+      overlap_ranges(velo[d], vehi[d], 1, nv, pelo[d], pehi[d], 0, np, vplo[d], vpw[d]);
+      overlap_ranges(pelo[d], pehi[d], 0, np, velo[d], vehi[d], 1, nv, pvlo[d], pvw[d]);
+      int *t[6];
+      TRY(upload(h, &t[0], vvlo[d]));
+      TRY(upload(h, &t[1], vvw[d]));
+      TRY(upload(h, &t[2], vplo[d]));
+      TRY(upload(h, &t[3], vpw[d]));
+      TRY(upload(h, &t[4], pvlo[d]));
+      TRY(upload(h, &t[5], pvw[d]));
+      ct.vv_lo[d] = t[0]; ct.vv_w[d] = t[1];
+      ct.vp_lo[d] = t[2]; ct.vp_w[d] = t[3];
+      ct.pv_lo[d] = t[4]; ct.pv_w[d] = t[5];
+    }
+    std::vector<int64_t> rp(nrows + 1, 0);
+    for (int r = 0; r < 3; ++r)
+      for (int i3 = 0; i3 < ct.nv[2]; ++i3)
+        for (int i2 = 0; i2 < ct.nv[1]; ++i2)
+          for (int i1 = 0; i1 < ct.nv[0]; ++i1) {
+            const int64_t row = h->off[r] + ((int64_t)i3 * ct.nv[1] + i2) * ct.nv[0] + i1;
+            rp[row + 1] = 3LL * vvw[0][i1] * vvw[1][i2] * vvw[2][i3] + (int64_t)vpw[0][i1] * vpw[1][i2] * vpw[2][i3];
+          }
+    for (int l3 = 0; l3 < ct.np[2]; ++l3)
+      for (int l2 = 0; l2 < ct.np[1]; ++l2)
+        for (int l1 = 0; l1 < ct.np[0]; ++l1) {
+          const int64_t row = h->off[3] + ((int64_t)l3 * ct.np[1] + l2) * ct.np[0] + l1;
+          rp[row + 1] = 3LL * pvw[0][l1] * pvw[1][l2] * pvw[2][l3];
         }
-  for (int l3 = 0; l3 < ct.np[2]; ++l3)
-    for (int l2 = 0; l2 < ct.np[1]; ++l2)
-      for (int l1 = 0; l1 < ct.np[0]; ++l1) {
-        const int64_t row = h->off[3] + ((int64_t)l3 * ct.np[1] + l2) * ct.np[0] + l1;
-        rp[row + 1] = 3LL * pvw[0][l1] * pvw[1][l2] * pvw[2][l3];
-      }
-  for (int64_t r = 0; r < nrows; ++r) rp[r + 1] += rp[r];
-  const int64_t nnz = rp[nrows];
-  int64_t *drp = nullptr;
-  int *dcol = nullptr;
-  double *dval = nullptr;
-  TRY(upload(h, &drp, rp));
-  TRY(dalloc(h, &dcol, (size_t)nnz));
-  TRY(dalloc(h, &dval, (size_t)nnz));
-  ct.row_ptr = drp;
-  CK(cudaMemsetAsync(dval, 0, sizeof(double) * nnz, st));
-  launch_csr_cols(ct, dcol, st);
-  TRY(launch_assemble(gp, mt, ct, dval, st));
-  h->csr.row_ptr = drp;
-  h->csr.col = dcol;
-  h->csr.val = dval;
-  h->csr.nrows = nrows;
-  h->csr.nnz = nnz;
-  if (h->desc.matvec_precision == FDST_MV_DF64) {
-    // FP32-pair copy of the values and a split right-hand-side buffer for the
-    // double-float SpMV inside the iterations (true residuals use FP64)
-    float2 *vdf = nullptr;
-    TRY(dalloc(h, &vdf, (size_t)nnz));
-    launch_split_df(dval, vdf, nnz, nnz, 1, nullptr, st);
-    h->csr.val_df = vdf;
-    TRY(dalloc(h, &h->x2, (size_t)h->n_total * h->max_rhs));
+    for (int64_t r = 0; r < nrows; ++r) rp[r + 1] += rp[r];
+    const int64_t nnz = rp[nrows];
+    int64_t *drp = nullptr;
+    int *dcol = nullptr;
+    double *dval = nullptr;
+    TRY(upload(h, &drp, rp));
+    TRY(dalloc(h, &dcol, (size_t)nnz));
+    TRY(dalloc(h, &dval, (size_t)nnz));
+    ct.row_ptr = drp;
+    CK(cudaMemsetAsync(dval, 0, sizeof(double) * nnz, st));
+    launch_csr_cols(ct, dcol, st);
+    TRY(launch_assemble(gp, mt, ct, dval, st));
+    h->csr.row_ptr = drp;
+    h->csr.col = dcol;
+    h->csr.val = dval;
+    h->csr.nrows = nrows;
+    h->csr.nnz = nnz;
+    if (h->desc.matvec_precision == FDST_MV_DF64) {
+      // FP32-pair copy of the values and a split right-hand-side buffer for the
+      // double-float SpMV inside the iterations (true residuals use FP64)
+      float2 *vdf = nullptr;
+      TRY(dalloc(h, &vdf, (size_t)nnz));
+      launch_split_df(dval, vdf, nnz, nnz, 1, nullptr, st);
+      h->csr.val_df = vdf;
+      TRY(dalloc(h, &h->x2, (size_t)h->n_total * h->max_rhs));
+    }
   }
+  if (h->desc.matvec_precision == FDST_MV_DF64 && !h->x2)
+    TRY(dalloc(h, &h->x2, (size_t)h->n_total * h->max_rhs));
   // ---- diagonal scalings of P_D^G: D_V = diag(A) / diag(P~_V), D_Q = diag(Q) / diag(P_Q)
   h->geo_scale.assign(4, std::vector<double>());
   if (h->desc.variant == FDST_VARIANT_PD_GEO) {
-    double *dA = nullptr, *dQ = nullptr;
-    TRY(dalloc(h, &dA, (size_t)nrows));
+    double *dQ = nullptr;
     TRY(dalloc(h, &dQ, (size_t)(h->off[4] - h->off[3])));
-    launch_csr_diag(h->csr, dA, st);
     launch_diag_q(gp, mt, dQ, st);
-    std::vector<double> diagA(nrows), diagQ(h->off[4] - h->off[3]);
-    CK(cudaMemcpy(diagA.data(), dA, sizeof(double) * nrows, cudaMemcpyDeviceToHost));
+    std::vector<double> diagQ(h->off[4] - h->off[3]);
     CK(cudaMemcpy(diagQ.data(), dQ, sizeof(double) * diagQ.size(), cudaMemcpyDeviceToHost));
-    for (int k = 0; k < 3; ++k) {
-      const int n1 = h->shape[k][0], n2 = h->shape[k][1], n3 = h->shape[k][2];
-      std::vector<double> &sc = h->geo_scale[k];
-      sc.resize((size_t)n1 * n2 * n3);
-      const Mat *Kf = h->geo_K[k].data(), *Mf = h->geo_M[k].data();
-      for (int i3 = 0; i3 < n3; ++i3)
-        for (int i2 = 0; i2 < n2; ++i2)
-          for (int i1 = 0; i1 < n1; ++i1) {
-            const double dp = Kf[2](i3, i3) * Mf[1](i2, i2) * Mf[0](i1, i1) + Mf[2](i3, i3) * Kf[1](i2, i2) * Mf[0](i1, i1) +
-                              Mf[2](i3, i3) * Mf[1](i2, i2) * Kf[0](i1, i1);
-            const size_t li = ((size_t)i3 * n2 + i2) * n1 + i1;
-            sc[li] = 1.0 / std::sqrt(diagA[h->off[k] + li] / dp);
-          }
+    if (!mf_only) {
+      double *dA = nullptr;
+      TRY(dalloc(h, &dA, (size_t)nrows));
+      launch_csr_diag(h->csr, dA, st);
+      std::vector<double> diagA(nrows);
+      CK(cudaMemcpy(diagA.data(), dA, sizeof(double) * nrows, cudaMemcpyDeviceToHost));
+      set_velocity_scaling(h, diagA);
     }
     {
       const int n1 = h->shape[3][0], n2 = h->shape[3][1], n3 = h->shape[3][2];
