@@ -128,11 +128,12 @@ def workload(name):
     return w
 
 
-def describe(name, w, nrhs):
+def describe(name, w, nrhs, matrix_free=False):
     n = "x".join(str(v) for v in w["n_el"])
     if w.get("geometry") == "sine_bump":
+        op = "matrix-free operator (sum factorization, no CSR)" if matrix_free else "FP64 CSR operator"
         return (f"{name}: 3D cube mapped by x = xi + 0.1 sin(pi xi1) sin(pi xi2) sin(pi xi3) (1,1,1), viscosity "
-                f"1 + 0.5 sin(2 pi x1) cos(2 pi x2), TH IGA p={w['p']}, {n} elements, FP64 CSR operator, "
+                f"1 + 0.5 sin(2 pi x1) cos(2 pi x2), TH IGA p={w['p']}, {n} elements, {op}, "
                 f"P_D^G (geometry/viscosity-aware FD), {nrhs} seeded N(0,1) right-hand sides (pressure part "
                 f"mean-free), MINRES tol 1e-8 from x0=0")
     return (f"{name}: {w['dim']}D unit {'cube' if w['dim'] == 3 else 'square'}, {w['disc']} IGA, pressure degree "
@@ -497,7 +498,8 @@ def run_gpu(args):
         out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": dtype, "data": "synthetic",
-               "config": {"workload": describe(args.workload, w, nrhs), "nrhs_per_gpu": nrhs,
+               "config": {"workload": describe(args.workload, w, nrhs, mfree), "nrhs_per_gpu": nrhs,
+                          "device_bytes": P.device_bytes,
                           "solver": ("P_D-MINRES" if not gm else "%s-GMRES (%s form, Krylov basis %d)" % (
                               "P_C" if args.solver == "gmres-pc" else "P_T",
                               "left" if prec == fd.FD_F64 else "flexible", args.restart)),
