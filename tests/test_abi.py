@@ -84,3 +84,18 @@ def test_bad_dim_and_null_arguments(lib):
     assert lib.fdst_setup(None, ctypes.byref(h)) == 1
     assert lib.fdst_apply_prec(None, None, None, 1, None) == 1
     assert lib.fdst_destroy(None) == 0
+
+
+def test_new_entry_points_validate_on_the_host(lib):
+    """Argument checks that return before any device work: the block preconditioner,
+    GMRES, the conversions and the kernel timing reject NULL handles and bad codes."""
+    import paper_1712_00403_gb300 as pkg
+    info = (pkg.SolveInfo * 1)()
+    vp = ctypes.c_void_p
+    assert lib.fdst_apply_block_prec(None, pkg.PREC_PT, vp(1), vp(2), 1, None) == 1
+    assert lib.fdst_solve_gmres(None, pkg.PREC_PT, pkg.GMRES_AUTO, vp(1), vp(2), 1, 1e-8, 10, 10, info, None) == 1
+    assert lib.fdst_convert(7, vp(1), vp(2), 4, None) == 1          # unknown kind
+    assert lib.fdst_convert(0, None, vp(2), 4, None) == 1           # NULL input with n > 0
+    assert lib.fdst_convert(0, None, None, 0, None) == 0            # nothing to do
+    assert lib.fdst_get_kernel_timing(None, None, None) == 1
+    assert "NULL" in lib.fdst_last_error().decode()
