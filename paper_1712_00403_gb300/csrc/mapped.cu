@@ -78,8 +78,13 @@ fdst_status build_mapped_pre(fdst_ctx *h) {
     set_error("the mapped geometry is built for the 3D Taylor-Hood discretization");
     return FDST_NOT_SUPPORTED;
   }
-  if (h->p > 3) {
-    set_error("mapped-geometry assembly supports pressure degree p <= 3 (element matrices in shared memory)");
+  if (h->p > 3 && h->desc.matvec_form != FDST_MATVEC_MATRIX_FREE) {
+    set_error("mapped-geometry assembly supports pressure degree p <= 3 (element matrices in shared memory); "
+              "the matrix-free operator takes p <= 8");
+    return FDST_NOT_SUPPORTED;
+  }
+  if (h->p > 8) {
+    set_error("mapped geometry supports pressure degree p <= 8");
     return FDST_NOT_SUPPORTED;
   }
   h->mapped = true;

@@ -312,3 +312,30 @@ def test_matrix_free_handle_blocks_match_oracle(spec):
             out = t.cpu().numpy()
         for o0, o1 in zip(P.block_offsets[:-1], P.block_offsets[1:]):
             assert rel(out[o0:o1], ref[o0:o1]) <= 1e-11, which
+
+
+@pytest.mark.parametrize("spec", [problem_spec(3, 4, (2, 3, 2)), problem_spec(3, 5, 2)], ids=_ids)
+def test_matrix_free_higher_degree(spec):
+    """The matrix-free handle has no element-matrix size limit: p = 4, 5 on the
+    mapped cube, operator (FP64 and double-float) and P_D^G apply against the oracle,
+    and a P_D^G-MINRES solve to the tolerance."""
+    import paper_1712_00403_gb300 as fd
+    S = oracle_problem(spec)
+    G = geo.Grid(S)
+    pdg = geo.PDG(S, G)
+    X = synth.random_vector(71, S.n_total)
+    ref_y, ref_s = geo.matvec(S, G, X), pdg.apply(X)
+    for mv in (fd.MV_F64, fd.MV_DF64):
+        P = _gpu(spec, matvec_precision=mv, matvec_form=fd.MATVEC_MATRIX_FREE)
+        x = torch.tensor(X, device="cuda")
+        y, s = torch.empty_like(x), torch.empty_like(x)
+        P.matvec(x, y)
+        P.apply_prec(x, s)
+        for o0, o1 in zip(P.block_offsets[:-1], P.block_offsets[1:]):
+            assert rel(y.cpu().numpy()[o0:o1], ref_y[o0:o1]) <= 1e-12, mv
+            assert rel(s.cpu().numpy()[o0:o1], ref_s[o0:o1]) <= 1e-11, mv
+    P = _gpu(spec, fd_precision=fd.FD_TF32X3, matvec_precision=fd.MV_DF64, matvec_form=fd.MATVEC_MATRIX_FREE)
+    b = torch.tensor(synth.rhs(303, S.block_sizes), device="cuda")
+    x = torch.zeros_like(b)
+    info = P.solve(b, x, tol=1e-8, maxit=1500)[0]
+    assert info["status"] == "OK" and info["true_rel_res"] <= 1e-8
