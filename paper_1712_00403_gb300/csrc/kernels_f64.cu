@@ -388,24 +388,52 @@ void launch_band_df(const BandGroupDF &g, int nrhs, const int *done, cudaStream_
   k_band_df<T><<<grid, thr, 0, s>>>(g, nrhs, done);
 }
 
+// Two entries per thread with 16-byte accesses where the row start allows it
+// (an odd leading entry on its own), so that each request moves twice the bytes.
 __global__ void k_split_df(const double *x, float2 *y, int64_t n, int64_t stride, const int *done) {
   const int j = blockIdx.y;
   if (done && done[j]) return;
   const double *xr = x + j * stride;
   float2 *yr = y + j * stride;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    yr[i] = f64_split(xr[i]);
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, ts = (int64_t)gridDim.x * blockDim.x;
+  const uintptr_t ax = reinterpret_cast<uintptr_t>(xr) & 15, ay = reinterpret_cast<uintptr_t>(yr) & 15;
+  if (ax != ay) {   // rows not aligned alike: one entry per thread
+    for (int64_t i = t0; i < n; i += ts) yr[i] = f64_split(xr[i]);
+    return;
   }
+  const int64_t head = ax != 0 && n > 0 ? 1 : 0;   // both 8 mod 16: one leading entry aligns both
+  if (head && t0 == 0) yr[0] = f64_split(xr[0]);
+  const int64_t pairs = (n - head) >> 1;
+  const double2 *x2 = reinterpret_cast<const double2 *>(xr + head);
+  float4 *y4 = reinterpret_cast<float4 *>(yr + head);
+  for (int64_t i = t0; i < pairs; i += ts) {
+    const double2 v = x2[i];
+    const float2 a = f64_split(v.x), b = f64_split(v.y);
+    y4[i] = make_float4(a.x, a.y, b.x, b.y);
+  }
+  if (((n - head) & 1) && t0 == 0) yr[n - 1] = f64_split(xr[n - 1]);
 }
-
 __global__ void k_join_df(const float2 *x, double *y, int64_t n, int64_t stride, const int *done) {
   const int j = blockIdx.y;
   if (done && done[j]) return;
   const float2 *xr = x + j * stride;
   double *yr = y + j * stride;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    yr[i] = f64_join(xr[i]);
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, ts = (int64_t)gridDim.x * blockDim.x;
+  const uintptr_t ax = reinterpret_cast<uintptr_t>(xr) & 15, ay = reinterpret_cast<uintptr_t>(yr) & 15;
+  if (ax != ay) {   // rows not aligned alike: one entry per thread
+    for (int64_t i = t0; i < n; i += ts) yr[i] = f64_join(xr[i]);
+    return;
   }
+  const int64_t head = ax != 0 && n > 0 ? 1 : 0;   // both 8 mod 16: one leading entry aligns both
+  if (head && t0 == 0) yr[0] = f64_join(xr[0]);
+  const int64_t pairs = (n - head) >> 1;
+  const float4 *x4 = reinterpret_cast<const float4 *>(xr + head);
+  double2 *y2 = reinterpret_cast<double2 *>(yr + head);
+  for (int64_t i = t0; i < pairs; i += ts) {
+    const float4 v = x4[i];
+    y2[i] = make_double2(f64_join(make_float2(v.x, v.y)), f64_join(make_float2(v.z, v.w)));
+  }
+  if (((n - head) & 1) && t0 == 0) yr[n - 1] = f64_join(xr[n - 1]);
 }
 
 // Element-wise precision conversions (the integer-unit forms above) over n entries.

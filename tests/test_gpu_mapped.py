@@ -148,7 +148,8 @@ def test_double_float_spmv_and_minres(spec):
 @pytest.mark.parametrize("which", ["PT", "PC"])
 def test_block_prec_geo_apply_matches_oracle(spec, which):
     """P_T^G and P_C^G (the geometry-aware blocks in eq. P_T, eq. P_C), B and B^T cut
-    out of the assembled operator: FP64 within the P_D^G bar."""
+    out of the assembled operator: FP64 within the P_D^G bar (1e-11), double-float
+    B and B^T within 5e-11."""
     import paper_1712_00403_gb300 as fd
     S = oracle_problem(spec)
     G = geo.Grid(S)
@@ -161,8 +162,11 @@ def test_block_prec_geo_apply_matches_oracle(spec, which):
         s = torch.empty_like(r)
         P.apply_block_prec(r, s, prec=fd.PREC_PT if which == "PT" else fd.PREC_PC)
         out = s.cpu().numpy()
+        # double-float B and B^T (48-bit arithmetic) inside P_C^G pass through two P_V^G
+        # applies: about 1e-11 relative there; FP64 stays within the P_D^G bar
+        bar = 1e-11 if mv == fd.MV_F64 else 5e-11
         for o0, o1 in zip(P.block_offsets[:-1], P.block_offsets[1:]):
-            assert rel(out[o0:o1], ref[o0:o1]) <= 1e-11, mv
+            assert rel(out[o0:o1], ref[o0:o1]) <= bar, mv
 
 
 def test_ptg_gmres_matches_oracle():
