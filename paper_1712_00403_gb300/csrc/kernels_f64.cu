@@ -601,6 +601,13 @@ void launch_scale_by_inv_gamma(double *z, const MinresState *st, int64_t n, int6
 
 // Lanczos step in place, per right-hand side: t = Az - (delta/gamma) v - (gamma/gamma_old) v_old,
 // then v_old <- v, v <- t (no buffer-role swaps: frozen right-hand sides keep their state).
+// The elementwise MINRES kernels take two entries per thread with 16-byte
+// accesses when every row they touch starts at the same 16-byte phase (the
+// handle's vectors always do; a caller's x may not), one otherwise.
+__device__ __forceinline__ bool same_phase(const void *a, const void *b) {
+  return ((reinterpret_cast<uintptr_t>(a) ^ reinterpret_cast<uintptr_t>(b)) & 15) == 0;
+}
+
 __global__ void k_minres_lanczos(const double *Az, double *v, double *v_old, const MinresState *st,
                                  const double *delta, int64_t n, int64_t stride, const int *done) {
   const int j = blockIdx.y;
@@ -609,12 +616,30 @@ __global__ void k_minres_lanczos(const double *Az, double *v, double *v_old, con
   const double f1 = delta[j] / gamma, f2 = gamma / gamma_old;
   const double *a = Az + j * stride;
   double *vv = v + j * stride, *vo = v_old + j * stride;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double vi = vv[i];
-    const double t = a[i] - f1 * vi - f2 * vo[i];
-    vo[i] = vi;
-    vv[i] = t;
+  auto step = [&](double ai, double vi, double voi, double &vo_out, double &vv_out) {
+    const double t = ai - f1 * vi - f2 * voi;
+    vo_out = vi;
+    vv_out = t;
+  };
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, ts = (int64_t)gridDim.x * blockDim.x;
+  if (!(same_phase(a, vv) && same_phase(a, vo))) {
+    for (int64_t i = t0; i < n; i += ts) step(a[i], vv[i], vo[i], vo[i], vv[i]);
+    return;
   }
+  const int64_t head = (reinterpret_cast<uintptr_t>(a) & 15) && n > 0 ? 1 : 0;
+  if (head && t0 == 0) step(a[0], vv[0], vo[0], vo[0], vv[0]);
+  const int64_t pairs = (n - head) >> 1;
+  const double2 *a2 = reinterpret_cast<const double2 *>(a + head);
+  double2 *v2 = reinterpret_cast<double2 *>(vv + head), *o2 = reinterpret_cast<double2 *>(vo + head);
+  for (int64_t i = t0; i < pairs; i += ts) {
+    const double2 ai = a2[i], vi = v2[i], oi = o2[i];
+    double2 no, nv;
+    step(ai.x, vi.x, oi.x, no.x, nv.x);
+    step(ai.y, vi.y, oi.y, no.y, nv.y);
+    o2[i] = no;
+    v2[i] = nv;
+  }
+  if (((n - head) & 1) && t0 == 0) step(a[n - 1], vv[n - 1], vo[n - 1], vo[n - 1], vv[n - 1]);
 }
 
 void launch_minres_lanczos(const double *Az, double *v, double *v_old, const MinresState *st,
@@ -687,14 +712,37 @@ __global__ void k_minres_update(double *w_old, double *w, double *x, double *z, 
   const double ia1 = S.inv_a1, a2 = S.a2, a3 = S.a3, cx = S.coef_x, ig = S.inv_gamma_new;
   double *wo = w_old + j * stride, *ww = w + j * stride, *xx = x + j * stride, *zz = z + j * stride;
   const double *zn = z_new + j * stride;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double wi = ww[i];
-    const double wn = (zz[i] - a3 * wo[i] - a2 * wi) * ia1;
-    wo[i] = wi;
-    ww[i] = wn;
-    xx[i] = fma(cx, wn, xx[i]);
-    zz[i] = zn[i] * ig;
+  auto step = [&](double wi, double woi, double zi, double xi, double zni, double &wo_out, double &w_out,
+                  double &x_out, double &z_out) {
+    const double wn = (zi - a3 * woi - a2 * wi) * ia1;
+    wo_out = wi;
+    w_out = wn;
+    x_out = fma(cx, wn, xi);
+    z_out = zni * ig;
+  };
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, ts = (int64_t)gridDim.x * blockDim.x;
+  if (!(same_phase(ww, wo) && same_phase(ww, xx) && same_phase(ww, zz) && same_phase(ww, zn))) {
+    for (int64_t i = t0; i < n; i += ts) step(ww[i], wo[i], zz[i], xx[i], zn[i], wo[i], ww[i], xx[i], zz[i]);
+    return;
   }
+  const int64_t head = (reinterpret_cast<uintptr_t>(ww) & 15) && n > 0 ? 1 : 0;
+  if (head && t0 == 0) step(ww[0], wo[0], zz[0], xx[0], zn[0], wo[0], ww[0], xx[0], zz[0]);
+  const int64_t pairs = (n - head) >> 1;
+  double2 *w2 = reinterpret_cast<double2 *>(ww + head), *o2 = reinterpret_cast<double2 *>(wo + head);
+  double2 *x2 = reinterpret_cast<double2 *>(xx + head), *z2 = reinterpret_cast<double2 *>(zz + head);
+  const double2 *n2 = reinterpret_cast<const double2 *>(zn + head);
+  for (int64_t i = t0; i < pairs; i += ts) {
+    const double2 wi = w2[i], oi = o2[i], zi = z2[i], xi = x2[i], ni = n2[i];
+    double2 no, nw, nx, nz;
+    step(wi.x, oi.x, zi.x, xi.x, ni.x, no.x, nw.x, nx.x, nz.x);
+    step(wi.y, oi.y, zi.y, xi.y, ni.y, no.y, nw.y, nx.y, nz.y);
+    o2[i] = no;
+    w2[i] = nw;
+    x2[i] = nx;
+    z2[i] = nz;
+  }
+  if (((n - head) & 1) && t0 == 0)
+    step(ww[n - 1], wo[n - 1], zz[n - 1], xx[n - 1], zn[n - 1], wo[n - 1], ww[n - 1], xx[n - 1], zz[n - 1]);
 }
 
 void launch_minres_update(double *w_old, double *w, double *x, double *z, const double *z_new,
