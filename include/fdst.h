@@ -341,6 +341,16 @@ fdst_status fdst_server_destroy(fdst_server s);
  * (diagnostics: lets a caller count the kernels inside a timed region). */
 int64_t fdst_kernel_launches(void);
 
+/*
+ * fdst_check_bounded_wait - self-test of the failure detection, without a fault:
+ * launches one thread that waits, through the bounded mbarrier wait of the
+ * tensor-core kernel, on a barrier nothing arrives on. *gave_up = 1 when the
+ * wait expired after its limit (about 2 s) and raised its abort flag, and the
+ * kernel returned; *seconds = the launch's duration. The device stays usable.
+ * FDST_INVALID_ARGUMENT for NULL outputs; synchronous.
+ */
+fdst_status fdst_check_bounded_wait(int *gave_up, double *seconds);
+
 /* *flag = 1 when a bounded device-side wait in a tensor-core kernel expired
  * (the kernel then skipped its output and returned) since the library loaded;
  * synchronizes the device. */

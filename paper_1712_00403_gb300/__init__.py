@@ -66,7 +66,7 @@ ENTRY_POINTS = ["fdst_setup", "fdst_destroy", "fdst_get_sizes", "fdst_apply_prec
                 "fdst_solve_host", "fdst_apply_prec_host", "fdst_solve_gmres", "fdst_apply_block_prec", "fdst_set_timing", "fdst_get_timing", "fdst_get_kernel_timing", "fdst_convert",
                 "fdst_fd_apply_static", "fdst_batch_create", "fdst_batch_solve", "fdst_batch_info",
                 "fdst_batch_destroy", "fdst_server_create", "fdst_server_submit", "fdst_server_step",
-                "fdst_server_result", "fdst_server_stats", "fdst_server_destroy", "fdst_device_error",
+                "fdst_server_result", "fdst_server_stats", "fdst_server_destroy", "fdst_check_bounded_wait", "fdst_device_error",
                 "fdst_kernel_launches", "fdst_last_error"]
 
 _lib = None
@@ -89,6 +89,7 @@ def load_library(path=LIB_PATH):
     lib.fdst_solve.argtypes = [vp, vp, vp, i, d, i, ctypes.POINTER(SolveInfo), vp]
     lib.fdst_solve_gmres.argtypes = [vp, i, i, vp, vp, i, d, i, i, ctypes.POINTER(SolveInfo), vp]
     lib.fdst_apply_block_prec.argtypes = [vp, i, vp, vp, i, vp]
+    lib.fdst_check_bounded_wait.argtypes = [ctypes.POINTER(i), ctypes.POINTER(d)]
     lib.fdst_solve_host.argtypes = [vp, vp, vp, i, d, i, ctypes.POINTER(SolveInfo), vp]
     lib.fdst_apply_prec_host.argtypes = [vp, vp, vp, i, vp]
     lib.fdst_set_timing.argtypes = [vp, i]
@@ -159,6 +160,13 @@ def convert(kind, src, dst, stream=None):
             raise TypeError("convert: expected contiguous CUDA tensors of the kind's dtypes and sizes")
     _check(load_library().fdst_convert(int(kind), ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(dst.data_ptr()),
                                        n, _stream_ptr(stream)))
+
+
+def check_bounded_wait():
+    """Failure-detection self-test (fdst_check_bounded_wait): (gave_up, seconds)."""
+    g, t = ctypes.c_int(), ctypes.c_double()
+    _check(load_library().fdst_check_bounded_wait(ctypes.byref(g), ctypes.byref(t)))
+    return bool(g.value), t.value
 
 
 def device_error():

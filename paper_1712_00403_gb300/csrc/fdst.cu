@@ -1135,6 +1135,11 @@ fdst_status fdst_convert(int kind, const void *d_in, void *d_out, int64_t n, fds
   return FDST_OK;
 }
 
+fdst_status fdst_check_bounded_wait(int *gave_up, double *seconds) {
+  if (!gave_up || !seconds) { set_error("NULL argument"); return FDST_INVALID_ARGUMENT; }
+  return tc_wait_selftest(gave_up, seconds);
+}
+
 fdst_status fdst_device_error(int *flag) {
   if (!flag) { set_error("NULL argument"); return FDST_INVALID_ARGUMENT; }
   return tc_error_flag(flag);

@@ -793,6 +793,54 @@ fdst_status launch_gemm_tc(const TcGroup &g, int nrhs, const int *done, cudaStre
   return FDST_OK;
 }
 
+// Self-test of the failure detection: one thread waits, through the same bounded
+// wait the contraction kernel uses, on an mbarrier nothing ever arrives on; the
+// wait must give up after its limit and raise the abort flag, and the kernel
+// must then return normally.
+__global__ void k_wait_selftest(int *out) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    abort_flag = 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const bool completed = mbar_wait(&bar, 0, &abort_flag);
+    out[0] = completed ? 1 : 0;
+    out[1] = abort_flag;
+  }
+}
+
+fdst_status tc_wait_selftest(int *gave_up, double *seconds) {
+  int *d = nullptr;
+  if (cudaMalloc(&d, 2 * sizeof(int)) != cudaSuccess) {
+    set_error("self-test allocation failed");
+    return FDST_OUT_OF_MEMORY;
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, 0);
+  count_launch(1);
+  k_wait_selftest<<<1, 32>>>(d);
+  cudaEventRecord(e1, 0);
+  int h[2] = {1, 0};
+  const cudaError_t e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(d);
+  if (e != cudaSuccess) {
+    set_error(std::string("self-test: ") + cudaGetErrorString(e));
+    return FDST_CUDA_ERROR;
+  }
+  *gave_up = (h[0] == 0 && h[1] == 1) ? 1 : 0;
+  *seconds = ms * 1e-3;
+  return FDST_OK;
+}
+
 fdst_status tc_error_flag(int *value) {
   *value = 0;
   if (!g_err_flag) return FDST_OK;

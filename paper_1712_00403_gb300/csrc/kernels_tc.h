@@ -78,5 +78,8 @@ size_t tc_packed_bytes(int K, int N, int split);
 void tc_pack(const double *B, int K, int N, int split, std::vector<uint8_t> &out);
 // 1 when a bounded wait inside the tensor-core kernel expired since start.
 fdst_status tc_error_flag(int *value);
+// Runs the bounded-wait self-test kernel: *gave_up = 1 when the wait expired and
+// reported it; *seconds = its duration.
+fdst_status tc_wait_selftest(int *gave_up, double *seconds);
 
 }  // namespace fdst

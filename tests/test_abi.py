@@ -98,4 +98,5 @@ def test_new_entry_points_validate_on_the_host(lib):
     assert lib.fdst_convert(0, None, vp(2), 4, None) == 1           # NULL input with n > 0
     assert lib.fdst_convert(0, None, None, 0, None) == 0            # nothing to do
     assert lib.fdst_get_kernel_timing(None, None, None) == 1
+    assert lib.fdst_check_bounded_wait(None, None) == 1
     assert "NULL" in lib.fdst_last_error().decode()
