@@ -122,6 +122,85 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ helpers
 
+# ------------------------------------------------------------------ replicas (one process per GPU)
+
+class Replicas:
+    """Multi-GPU layout: the path does not shard, so N GPUs run N independent replicas,
+    one process per GPU under torchrun (WORLD_SIZE / RANK / LOCAL_RANK from the
+    environment). Each rank solves its own right-hand sides (seeds shifted by
+    SEED_STRIDE x rank) and nothing crosses ranks on the data path. The collectives are
+    the timing ones only: a barrier on both sides of a timed region, the max over ranks
+    of its duration and the sum over ranks of the units solved, so that the job's value
+    is all units / the slowest rank's time. backend "nccl" reduces on the rank's GPU;
+    "gloo" on the host (the multi-process tests run it on CPU)."""
+
+    SEED_STRIDE = 1000
+
+    def __init__(self, backend="nccl", env=None):
+        env = os.environ if env is None else env
+        self.world = int(env.get("WORLD_SIZE", "1"))
+        self.rank = int(env.get("RANK", "0"))
+        self.local = int(env.get("LOCAL_RANK", "0"))
+        self.backend = backend
+        if backend == "nccl":
+            import torch
+            torch.cuda.set_device(self.local)
+        if self.world > 1:
+            import torch.distributed as dist
+            if not dist.is_initialized():
+                dist.init_process_group(backend)
+            if dist.get_world_size() != self.world or dist.get_rank() != self.rank:
+                raise RuntimeError("process group (%d of %d) disagrees with RANK/WORLD_SIZE (%d of %d)" % (
+                    dist.get_rank(), dist.get_world_size(), self.rank, self.world))
+
+    @property
+    def parallelism(self):
+        return f"replicas x{self.world}" if self.world > 1 else "1 GPU"
+
+    def seed(self, s):
+        """This rank's copy of a workload seed."""
+        return s + self.SEED_STRIDE * self.rank
+
+    def seeds(self, base, n):
+        """n right-hand-side seeds of this rank: the workload's list cycled, then shifted."""
+        return [self.seed(base[j % len(base)]) for j in range(n)]
+
+    def barrier(self):
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def reduce(self, values, op):
+        """Floats reduced elementwise over ranks; op "max" or "sum" (FP64 on the wire)."""
+        vals = [float(v) for v in values]
+        if self.world == 1:
+            return vals
+        import torch
+        import torch.distributed as dist
+        dev = torch.device("cuda", torch.cuda.current_device()) if self.backend == "nccl" else torch.device("cpu")
+        t = torch.tensor(vals, dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op={"max": dist.ReduceOp.MAX, "sum": dist.ReduceOp.SUM}[op])
+        return [float(v) for v in t.cpu()]
+
+    def max(self, v):
+        return self.reduce([v], "max")[0]
+
+    def sum(self, v):
+        return self.reduce([v], "sum")[0]
+
+    def job_rate(self, units, seconds):
+        """Whole-job throughput: this rank's units summed over ranks / the slowest rank's seconds."""
+        tot, = self.reduce([units], "sum")
+        worst, = self.reduce([seconds], "max")
+        return tot / worst
+
+    def close(self):
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            dist.destroy_process_group()
+
+
 def workload(name):
     import synth
     w = dict(synth.WORKLOADS[name])
@@ -281,17 +360,12 @@ def instance_specs(name, w):
 def run_gpu(args):
     import numpy as np
     import torch
-    import torch.distributed as dist
 
     import paper_1712_00403_gb300 as fd
     import synth
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
+    rep = Replicas("nccl")
+    world, rank, local = rep.world, rep.rank, rep.local
     dev = torch.device("cuda", local)
 
     w = workload(args.workload)
@@ -314,7 +388,7 @@ def run_gpu(args):
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t_setup
     # weak scaling: every rank solves its own batch (seeds shifted by rank)
-    seeds = [w["seeds"][j % len(w["seeds"])] + 1000 * rank for j in range(nrhs)]
+    seeds = rep.seeds(w["seeds"], nrhs)
     B = np.stack([synth.rhs(s, P.block_sizes) for s in seeds])
     b = torch.tensor(B.reshape(-1), device=dev)
     x = torch.zeros_like(b)
@@ -336,8 +410,7 @@ def run_gpu(args):
     for _ in range(args.warmup):
         info = step()
     torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+    rep.barrier()
     P.set_timing(True)
     launches0 = fd.kernel_launches()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -352,13 +425,9 @@ def run_gpu(args):
     launches = fd.kernel_launches() - launches0
     tm = P.get_timing()
     P.set_timing(False)
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = rep.max(e0.elapsed_time(e1))
     clocks = clk.summary()
-    total_solves = args.steps * nrhs * world
+    total_solves = rep.sum(args.steps * nrhs)
     value = total_solves / (ms / 1e3)
 
     iters = [i["iterations"] for inf in infos for i in inf]
@@ -470,6 +539,7 @@ def run_gpu(args):
     bn, xn = bh.numpy(), xh.numpy()
     e2e_steps = max(1, args.steps // 3)
     torch.cuda.synchronize()
+    rep.barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         xn[:] = 0.0
@@ -482,7 +552,7 @@ def run_gpu(args):
         else:
             P.solve_host(bn, xn, tol=1e-8, maxit=args.maxit, stream=stream)
     e2e_s = time.perf_counter() - t0
-    e2e = {"value": e2e_steps * nrhs * world / e2e_s, "unit": "solves/s",
+    e2e = {"value": rep.job_rate(e2e_steps * nrhs, e2e_s), "unit": "solves/s",
            "h2d_bytes_per_step": 2 * b.numel() * 8, "d2h_bytes_per_step": b.numel() * 8}
 
     cpu = None
@@ -514,7 +584,7 @@ def run_gpu(args):
                           "n_total": P.n_total,
                           "l2": "inputs larger than L2 (each step streams %d x %.0f MB vectors)" % (
                               nrhs, P.n_total * 8 / 1e6),
-                          "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+                          "parallelism": rep.parallelism},
                ("gmres" if gm else "minres"): {
                    "iterations_min": min(iters), "iterations_max": max(iters), "status": statuses,
                    "true_rel_res_max": true_res,
@@ -527,9 +597,7 @@ def run_gpu(args):
                "gpu_launches": launches, "clocks": clocks}
         print(json.dumps(out), flush=True)
     P.close()
-    if world > 1:
-        dist.barrier()
-        dist.destroy_process_group()
+    rep.close()
 
 
 # ------------------------------------------------------------------ batched workload
@@ -554,22 +622,17 @@ def _make_handles(fd, specs, local, threads=8, **kw):
 def run_batched(args):
     import numpy as np
     import torch
-    import torch.distributed as dist
 
     import paper_1712_00403_gb300 as fd
     import synth
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
+    rep = Replicas("nccl")
+    world, rank, local = rep.world, rep.rank, rep.local
     dev = torch.device("cuda", local)
     w = workload(args.workload)
     specs = instance_specs(args.workload, w)
     for s_ in specs:
-        s_["seed"] += 1000 * rank
+        s_["seed"] = rep.seed(s_["seed"])
     stream = torch.cuda.current_stream()
 
     def timed_batch(prec, steps, warmup, host_e2e=False):
@@ -591,8 +654,7 @@ def run_batched(args):
         for _ in range(warmup):
             step()
         torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
+        rep.barrier()
         l0 = fd.kernel_launches()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         infos = []
@@ -604,11 +666,7 @@ def run_batched(args):
             e1.record(stream)
             torch.cuda.synchronize()
         launches = fd.kernel_launches() - l0
-        ms = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = rep.max(e0.elapsed_time(e1))
         res = dict(ms=ms, infos=infos, launches=launches, clocks=clk.summary(), setup_s=t_setup, tune_s=t_tune,
                    info=B.info(), n_total=[h.n_total for h in hs])
         if host_e2e:
@@ -616,6 +674,7 @@ def run_batched(args):
             bh = [torch.empty(b.numel(), dtype=torch.float64, pin_memory=True).copy_(b.cpu()) for b in bs]
             xh = [torch.empty(b.numel(), dtype=torch.float64, pin_memory=True) for b in bs]
             torch.cuda.synchronize()
+            rep.barrier()
             t0 = time.perf_counter()
             for b, bhost in zip(bs, bh):
                 b.copy_(bhost, non_blocking=True)
@@ -641,13 +700,14 @@ def run_batched(args):
     f64 = timed_batch(fd.FD_F64, max(1, args.steps // 3 or 1), max(3, args.warmup // 2))
     errs = [float(torch.linalg.norm(a - b) / torch.linalg.norm(b)) for a, b in zip(tc["apply_out"], f64["apply_out"])]
     n = len(specs)
-    value = args.steps * n * world / (tc["ms"] / 1e3)
+    value = rep.sum(args.steps * n) / (tc["ms"] / 1e3)
+    e2e_value = rep.job_rate(n, tc["e2e_s"])
     it_tc = [i["iterations"] for inf in tc["infos"] for i in inf]
     it_64 = [i["iterations"] for inf in f64["infos"] for i in inf]
     st_tc = sorted(set(i["status"] for inf in tc["infos"] for i in inf))
     tr_tc = max(i["true_rel_res"] for inf in tc["infos"] for i in inf)
     tr_64 = max(i["true_rel_res"] for inf in f64["infos"] for i in inf)
-    value64 = len(f64["infos"]) * n * world / (f64["ms"] / 1e3)
+    value64 = rep.sum(len(f64["infos"]) * n) / (f64["ms"] / 1e3)
     # roofline of the grouped split-TF32 FD apply (one launch chain over all instances, autotuner timing)
     flops_apply = 0.0
     for sp in specs:
@@ -676,7 +736,7 @@ def run_batched(args):
                "config": {"workload": args.workload + ": " + w_text(args.workload, w),
                           "total_dof": int(sum(tc["n_total"])), "max_dof": int(max(tc["n_total"])),
                           "l2": "inputs larger than L2 (%.1f GB of right-hand sides)" % (sum(tc["n_total"]) * 8e-9),
-                          "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+                          "parallelism": rep.parallelism},
                "minres": {"iterations_min": min(it_tc), "iterations_max": max(it_tc), "iterations_mean":
                           float(np.mean(it_tc)), "status": st_tc, "true_rel_res_max": tr_tc,
                           "iterations_estimate_mean": float(np.mean([i["iterations_estimate"] for inf in tc["infos"]
@@ -688,13 +748,11 @@ def run_batched(args):
                "fd_apply_rel_err_vs_f64": errs,
                "autotune": tc["info"], "setup_s": tc["setup_s"], "autotune_s": tc["tune_s"],
                "roofline": roofline, "cpu_baseline": cpu,
-               "e2e": {"value": n * world / tc["e2e_s"], "unit": "solves/s", "h2d_bytes_per_step": tc["bytes"],
+               "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": tc["bytes"],
                        "d2h_bytes_per_step": tc["bytes"]},
                "gpu_launches": tc["launches"], "clocks": tc["clocks"]}
         print(json.dumps(out), flush=True)
-    if world > 1:
-        dist.barrier()
-        dist.destroy_process_group()
+    rep.close()
 
 
 # ------------------------------------------------------------------ serving workload
@@ -702,17 +760,12 @@ def run_batched(args):
 def run_serving(args):
     import numpy as np
     import torch
-    import torch.distributed as dist
 
     import paper_1712_00403_gb300 as fd
     import synth
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
+    rep = Replicas("nccl")
+    world, rank, local = rep.world, rep.rank, rep.local
     w = workload(args.workload)
 
     def stream_of(reqs):
@@ -720,7 +773,7 @@ def run_serving(args):
         for r in reqs:
             knots = [synth.open_uniform_knots(n, r["p"]) for n in r["n_el"]]
             sizes = block_sizes(r)
-            out.append((r, knots, synth.rhs(r["seed"] + 1000 * rank, sizes)))
+            out.append((r, knots, synth.rhs(rep.seed(r["seed"]), sizes)))
         return out
 
     def serve(reqs, max_active=16):
@@ -781,13 +834,8 @@ def run_serving(args):
                 for j, i in enumerate(order[:3]):
                     err_sample.append(oracle_error(reqs[i], res[i], solve=(ri == 0 and j == 0)))
         clocks = clk.summary()
-    tot = torch.tensor([float(total_solves), total_time], dtype=torch.float64)
-    if world > 1:
-        tt = tot.cuda()
-        dist.all_reduce(tt[:1])
-        dist.all_reduce(tt[1:], op=dist.ReduceOp.MAX)
-        tot = tt.cpu()
-    value = float(tot[0]) / float(tot[1])
+    tot = [rep.sum(total_solves), rep.max(total_time)]
+    value = tot[0] / tot[1]
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         specs = [r for r, _, _ in stream_of(synth.serving_requests(0, w["rates"][0], w["per_rate"], w["seed"],
@@ -807,7 +855,7 @@ def run_serving(args):
                                     "handles set up on 8 host threads",
                           "timing": "host wall clock from each stream's first arrival to its last completion "
                                     "(latency = completion - arrival, host clock)",
-                          "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+                          "parallelism": rep.parallelism},
                "serving": {"per_rate": per_rate, "p50_ms_all": 1e3 * float(np.percentile(all_lat, 50)),
                            "p99_ms_all": 1e3 * float(np.percentile(all_lat, 99))},
                "per_request_error_vs_fp64_oracle": err_sample,
@@ -816,9 +864,7 @@ def run_serving(args):
                        "note": "requests enter and leave as host arrays; the value above is already end to end"},
                "roofline": None, "gpu_launches": launches, "clocks": clocks}
         print(json.dumps(out), flush=True)
-    if world > 1:
-        dist.barrier()
-        dist.destroy_process_group()
+    rep.close()
 
 
 def block_sizes(r):
