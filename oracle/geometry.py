@@ -2,10 +2,15 @@
 P_D^G (paper Sec. 3 eq. Akk_TH / Q_TH, Sec. 6, Appendix). Oracle: test
 infrastructure only.
 
-Map (analytic stand-in for the paper's spline map, reading A18):
-    G(eta) = eta + a sin(pi eta1) sin(pi eta2) sin(pi eta3) (1, 1, 1),  a = 0.1
-so J = I + 1 (a grad s)^T and det J = 1 + a (1 . grad s); viscosity
-nu(x) = 1 + 0.5 sin(2 pi x1) cos(2 pi x2) evaluated at x = G(eta).
+Maps (analytic stand-ins for the paper's spline maps, reading A18):
+  sine bump   G(eta) = eta + a sin(pi eta1) sin(pi eta2) sin(pi eta3) (1, 1, 1),
+              a = 0.1, so J = I + 1 (a grad s)^T and det J = 1 + a (1 . grad s);
+              viscosity nu(x) = 1 + 0.5 sin(2 pi x1) cos(2 pi x2) at x = G(eta).
+  annulus     the eighth of a thick annulus of Sec. 7 (inner radius 1, outer
+              radius 2, height 1, opening angle pi/4) in polar form:
+              r = 1 + eta1, theta = pi eta2 / 4, x = (r cos theta, r sin theta,
+              eta3), so det J = pi r / 4; viscosity nu = 1 (constant, as in the
+              paper's test). Its P_D lacks the geometry while P_D^G has it.
 
 Operator on the mapped domain (TH push-forward phi = e_r B o G^{-1}):
     a(w, v) = int 2 nu grad^s w : grad^s v,   b(v, q) = -int q div v
@@ -29,9 +34,11 @@ mu^k_d = exp(mean of f^{k,j}_d over the two j != d). The D_V scaling absorbs
 what the fit misses.
 
 Pins (tests/test_oracle_geometry.py): brute-force element quadrature of the
-symmetric-gradient form and of b vs. the sum-factorized matvec; amplitude 0
-with nu = 1 reproduces the cube operator; det J closed form vs.
-numpy.linalg.det; the fit reproduces an exactly separable field; on the cube
+symmetric-gradient form and of b vs. the sum-factorized matvec (both maps);
+amplitude 0 with nu = 1 reproduces the cube operator; det J closed form vs.
+numpy.linalg.det; on the annulus the quadrature volume 3 pi / 8 and the
+moment int x1 dx = 7 sqrt(2) / 6 in closed form, and the chain rule
+J^{-T} grad_eta (f o G) = grad_x f for polynomials f; the fit reproduces an exactly separable field; on the cube
 P~_V = P_V and D_V = I; diag(P_V^G) = diag(A), diag(P_Q^G) = diag(Q);
 Theorem 2 spectral bounds of P_Q^{-1} Q. Parity unpinned: the separable fit
 on non-separable fields (no independent reference exists; the CUDA path
@@ -57,8 +64,26 @@ def bump(eta, amp=AMP):
     return s, g
 
 
-def geometry(eta, amp=AMP):
+def annulus(eta):
+    """The eighth of a thick annulus: x, J, det J, J^{-1} of the polar map."""
+    r = 1.0 + eta[..., 0]
+    th = 0.25 * np.pi * eta[..., 1]
+    c, s = np.cos(th), np.sin(th)
+    x = np.stack([r * c, r * s, eta[..., 2]], axis=-1)
+    J = np.zeros(eta.shape[:-1] + (3, 3))
+    J[..., 0, 0], J[..., 1, 0] = c, s                                   # d x / d eta1 (radial)
+    J[..., 0, 1], J[..., 1, 1] = -0.25 * np.pi * r * s, 0.25 * np.pi * r * c   # d x / d eta2 (angular)
+    J[..., 2, 2] = 1.0
+    det = 0.25 * np.pi * r
+    return x, J, det, np.linalg.inv(J)
+
+
+def geometry(eta, amp=AMP, kind="sine_bump"):
     """x = G(eta), J (..., 3, 3) with J_ij = d x_i / d eta_j, det J, J^{-1}."""
+    if kind == "annulus":
+        return annulus(eta)
+    if kind != "sine_bump":
+        raise ValueError("unknown geometry %r" % (kind,))
     s, g = bump(eta, amp)
     x = eta + s[..., None]
     J = np.eye(3) + np.ones(3)[:, None] * g[..., None, :]
@@ -82,8 +107,11 @@ class Grid:
     """Tensor Gauss grid (p+2 points per element per direction) with the
     geometry and viscosity at every point; axis d of the arrays is direction d+1."""
 
-    def __init__(self, S, amp=AMP, nu_const=None, npts=None, contrast=None):
+    def __init__(self, S, amp=AMP, nu_const=None, npts=None, contrast=None, geometry_kind="sine_bump"):
         self.S = S
+        self.kind = geometry_kind
+        if geometry_kind == "annulus" and contrast is None and nu_const is None:
+            nu_const = 1.0
         npts = S.p + 2 if npts is None else npts
         self.pts, self.wts = [], []
         for d in range(3):
@@ -91,7 +119,7 @@ class Grid:
             self.pts.append(x)
             self.wts.append(w)
         E = np.stack(np.meshgrid(*self.pts, indexing="ij"), axis=-1)
-        self.x, self.J, self.det, self.Jinv = geometry(E, amp)
+        self.x, self.J, self.det, self.Jinv = geometry(E, amp, geometry_kind)
         self.nu = np.full(self.det.shape, nu_const) if nu_const is not None else viscosity(self.x, contrast)
         W = self.wts[0][:, None, None] * self.wts[1][None, :, None] * self.wts[2][None, None, :]
         self.W = W

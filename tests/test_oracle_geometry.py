@@ -187,3 +187,87 @@ def test_viscosity_contrast_family_and_exact_fit_on_the_cube(k):
         np.testing.assert_allclose(pdg.DV[c], 1.0, rtol=1e-9)
         Akk = A_bf[off[c]:off[c + 1], off[c]:off[c + 1]]
         np.testing.assert_allclose(kron.kron_sum_matrix(Ks, Ms, coef), Akk, atol=1e-9 * np.abs(Akk).max())
+
+
+# ---------------------------------------------------------------- eighth of a thick annulus
+
+def test_annulus_map_closed_forms():
+    """Polar map of the eighth of a thick annulus (Sec. 7: radii 1 and 2, height 1):
+    det J = pi r / 4, J by central differences, boundary faces on the circles and
+    planes, quadrature volume 3 pi / 8 and moment int x1 dx = 7 sqrt(2) / 6."""
+    rng = np.random.default_rng(7)
+    eta = rng.random((60, 3))
+    x, J, det, Jinv = geo.geometry(eta, kind="annulus")
+    np.testing.assert_allclose(det, np.pi * (1 + eta[:, 0]) / 4, rtol=1e-14)
+    np.testing.assert_allclose(det, np.linalg.det(J), rtol=1e-13)
+    np.testing.assert_allclose(np.einsum("qab,qbc->qac", J, Jinv), np.broadcast_to(np.eye(3), J.shape), atol=1e-14)
+    h = 1e-6
+    for j in range(3):
+        e = np.zeros(3)
+        e[j] = h
+        xp, *_ = geo.geometry(eta + e, kind="annulus")
+        xm, *_ = geo.geometry(eta - e, kind="annulus")
+        np.testing.assert_allclose(J[:, :, j], (xp - xm) / (2 * h), atol=1e-8)
+    t = rng.random(20)
+    for face, rad in ((0.0, 1.0), (1.0, 2.0)):
+        xf, *_ = geo.geometry(np.stack([np.full(20, face), t, t[::-1]], -1), kind="annulus")
+        np.testing.assert_allclose(np.hypot(xf[:, 0], xf[:, 1]), rad, rtol=1e-14)
+    x0, *_ = geo.geometry(np.stack([t, np.zeros(20), t], -1), kind="annulus")
+    x1, *_ = geo.geometry(np.stack([t, np.ones(20), t], -1), kind="annulus")
+    assert np.all(x0[:, 1] == 0.0)
+    np.testing.assert_allclose(x1[:, 0], x1[:, 1], rtol=1e-14)
+    S = _S(4, 2)
+    G = geo.Grid(S, geometry_kind="annulus")
+    assert np.all(G.nu == 1.0)
+    np.testing.assert_allclose(np.sum(G.W * G.det), 3 * np.pi / 8, rtol=1e-14)
+    np.testing.assert_allclose(np.sum(G.W * G.det * G.x[..., 0]), 7 * np.sqrt(2) / 6, rtol=1e-10)
+
+
+def test_annulus_chain_rule():
+    """J^{-T} grad_eta (f o G) = grad_x f for f = x1^2 x2 + x2 x3 - x1 x3^2 (the
+    eta-gradient by central differences, independent of J)."""
+    f = lambda x: x[..., 0] ** 2 * x[..., 1] + x[..., 1] * x[..., 2] - x[..., 0] * x[..., 2] ** 2
+    gf = lambda x: np.stack([2 * x[..., 0] * x[..., 1] - x[..., 2] ** 2, x[..., 0] ** 2 + x[..., 2],
+                             x[..., 1] - 2 * x[..., 0] * x[..., 2]], -1)
+    eta = np.random.default_rng(8).random((40, 3)) * 0.98 + 0.01
+    x, _, _, Jinv = geo.geometry(eta, kind="annulus")
+    h = 1e-5
+    ge = np.zeros_like(eta)
+    for a in range(3):
+        e = np.zeros(3)
+        e[a] = h
+        ge[:, a] = (f(geo.geometry(eta + e, kind="annulus")[0]) - f(geo.geometry(eta - e, kind="annulus")[0])) / (2 * h)
+    np.testing.assert_allclose(np.einsum("qa,qac->qc", ge, Jinv), gf(x), atol=1e-8)
+
+
+@pytest.mark.parametrize("kind", ["sine_bump", "annulus"])
+def test_divergence_of_zero_trace_fields_integrates_to_zero(kind):
+    """B^T 1 = 0: int div v dx = 0 for every v vanishing on the boundary (any map).
+    With a high-order rule the quadrature error is negligible, so a transposed J^{-1}
+    or a missing det J factor shows."""
+    S = _S(3, 2)
+    G = geo.Grid(S, npts=14, geometry_kind=kind)
+    nv = 3 * S.block_sizes[0]
+    x = np.zeros(S.n_total)
+    x[nv:] = 1.0
+    y = geo.matvec(S, G, x)
+    x[nv:] = np.random.default_rng(4).standard_normal(S.n_total - nv)
+    scale = np.abs(geo.matvec(S, G, x)[:nv]).max()
+    assert np.abs(y[:nv]).max() <= 1e-12 * scale
+
+
+def test_annulus_sum_factorized_matvec_vs_brute_force():
+    S = _S(2, 1)
+    G = geo.Grid(S, geometry_kind="annulus")
+    A, B = geo.brute_force(S, G)
+    nv = 3 * S.block_sizes[0]
+    full = np.zeros((S.n_total, S.n_total))
+    full[:nv, :nv] = A
+    full[nv:, :nv] = B
+    full[:nv, nv:] = B.T
+    rng = np.random.default_rng(9)
+    for _ in range(3):
+        x = rng.standard_normal(S.n_total)
+        np.testing.assert_allclose(geo.matvec(S, G, x), full @ x, atol=1e-12 * np.abs(full).max() * 10)
+    np.testing.assert_allclose(A, A.T, atol=1e-13 * np.abs(A).max())
+    assert np.all(np.linalg.eigvalsh(A) > 0)
