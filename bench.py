@@ -8,7 +8,9 @@ Taylor-Hood, p=3, 64^3 elements (6,740,830 DoF), 16 seeded N(0,1)
 right-hand sides. Prints one JSON line (rank 0).
 
 Other workloads (--workload): mapped_th_p3_32 (sine-bump map, variable
-viscosity, P_D^G, FP64 CSR operator, 4 right-hand sides), batched_64 (64
+viscosity, P_D^G, FP64 CSR operator, 4 right-hand sides), annulus_th_p3_32
+(the eighth of a thick annulus, nu = 1, otherwise the same; --matrix-free
+selects the sum-factorized operator on either), batched_64 (64
 uneven unit-cube instances in grouped launches; split-TF32 and FP64 FD
 compared) and serving (Poisson arrivals swept over rates through the request
 server; p50/p99 latency).
@@ -209,10 +211,13 @@ def workload(name):
 
 def describe(name, w, nrhs, matrix_free=False):
     n = "x".join(str(v) for v in w["n_el"])
-    if w.get("geometry") == "sine_bump":
+    if w.get("geometry") in ("sine_bump", "annulus"):
         op = "matrix-free operator (sum factorization, no CSR)" if matrix_free else "FP64 CSR operator"
-        return (f"{name}: 3D cube mapped by x = xi + 0.1 sin(pi xi1) sin(pi xi2) sin(pi xi3) (1,1,1), viscosity "
-                f"1 + 0.5 sin(2 pi x1) cos(2 pi x2), TH IGA p={w['p']}, {n} elements, {op}, "
+        dom = ("3D cube mapped by x = xi + 0.1 sin(pi xi1) sin(pi xi2) sin(pi xi3) (1,1,1), viscosity "
+               "1 + 0.5 sin(2 pi x1) cos(2 pi x2)" if w["geometry"] == "sine_bump" else
+               "eighth of a thick annulus (radii 1 and 2, height 1; polar map r = 1 + xi1, angle pi xi2 / 4), "
+               "viscosity 1")
+        return (f"{name}: {dom}, TH IGA p={w['p']}, {n} elements, {op}, "
                 f"P_D^G (geometry/viscosity-aware FD), {nrhs} seeded N(0,1) right-hand sides (pressure part "
                 f"mean-free), MINRES tol 1e-8 from x0=0")
     return (f"{name}: {w['dim']}D unit {'cube' if w['dim'] == 3 else 'square'}, {w['disc']} IGA, pressure degree "
@@ -233,9 +238,9 @@ def oracle_operator(w):
     from oracle import stokes
     knots = [synth.open_uniform_knots(n, w["p"]) for n in w["n_el"]]
     S = stokes.build(knots, w["p"], w.get("disc", "TH"))
-    if w.get("geometry") == "sine_bump":
+    if w.get("geometry") in ("sine_bump", "annulus"):
         from oracle import geometry as geo
-        G = geo.Grid(S)
+        G = geo.Grid(S, geometry_kind=w["geometry"])
         P = geo.PDG(S, G)
         return S, (lambda v: geo.matvec(S, G, v)), P.apply
     return S, (lambda v: stokes.matvec(S, v)), (lambda v: stokes.apply_PD_inv(S, v))
@@ -372,14 +377,15 @@ def run_gpu(args):
     nrhs = args.nrhs or len(w["seeds"])
     if args.fd == "auto":
         # the mapped configuration names the split-BF16 form; the others split-TF32
-        prec = fd.FD_BF16X6 if w.get("geometry") == "sine_bump" else fd.FD_TF32X3
+        prec = fd.FD_BF16X6 if w.get("geometry") in ("sine_bump", "annulus") else fd.FD_TF32X3
     else:
         prec = {"f64": fd.FD_F64, "tf32": fd.FD_TF32X3, "bf16": fd.FD_BF16X6}[args.fd]
     knots = synth.knots_for(w)
     t_setup = time.perf_counter()
-    mapped = w.get("geometry") == "sine_bump"
+    mapped = w.get("geometry") in ("sine_bump", "annulus")
     mv = fd.MV_DF64 if args.matvec == "df64" else fd.MV_F64
-    geo = dict(geometry=fd.GEOM_SINE_BUMP, variant=fd.VARIANT_PD_GEO) if mapped else {}
+    geo = dict(geometry=fd.GEOM_ANNULUS if w["geometry"] == "annulus" else fd.GEOM_SINE_BUMP,
+               variant=fd.VARIANT_PD_GEO) if mapped else {}
     mfree = mapped and args.matrix_free
     if mfree:
         geo["matvec_form"] = fd.MATVEC_MATRIX_FREE

@@ -54,7 +54,11 @@ enum { FDST_TH = 0, FDST_RT = 1 };                          /* discretization (S
  * three bf16 pieces, the six products with piece indices i + j <= 2). Both
  * split forms accumulate in FP32 and keep FP32 intermediates. */
 enum { FDST_FD_F64 = 0, FDST_FD_TF32X3 = 1, FDST_FD_BF16X6 = 2 };
-enum { FDST_GEOM_IDENTITY = 0, FDST_GEOM_SINE_BUMP = 1 };   /* geometry map G */
+/* Geometry map G of the parametric cube (3D Taylor-Hood): the identity; the sine
+ * bump x = eta + a sin(pi eta1) sin(pi eta2) sin(pi eta3) (1,1,1); or the eighth
+ * of a thick annulus of Sec. 7 (inner radius 1, outer 2, height 1) in polar form
+ * x = (r cos t, r sin t, eta3), r = 1 + eta1, t = pi eta2 / 4. */
+enum { FDST_GEOM_IDENTITY = 0, FDST_GEOM_SINE_BUMP = 1, FDST_GEOM_ANNULUS = 2 };
 enum { FDST_VARIANT_PD = 0, FDST_VARIANT_PD_GEO = 1 };      /* P_D (Sec. 5) or P_D^G (Sec. 6) */
 /* Matvec arithmetic: FP64 (DFMA), or double-float (each value an unevaluated
  * sum of two floats, 48-bit significand, error-free FMA products and TwoSum
@@ -76,16 +80,17 @@ typedef struct {
   int degree;              /* pressure spline degree p >= 1; velocity degree is p+1 (Sec. 2.2) */
   const double *h_knots[3];/* open pressure knot vector of each direction on [0,1] (Sec. 2.1) */
   int nknots[3];           /* its length m + p + 1 */
-  double viscosity;        /* constant nu > 0 (identity geometry); ignored for SINE_BUMP */
+  double viscosity;        /* constant nu > 0 (identity geometry); ignored on the mapped geometries */
   int geometry;            /* FDST_GEOM_* */
   int variant;             /* FDST_VARIANT_* */
   int fd_precision;        /* FDST_FD_* */
   double cpen;             /* Nitsche penalty C_pen (RT); <= 0 selects 5(alpha+1) (Sec. 7) */
   int max_rhs;             /* most right-hand sides one call will pass (workspace sizing), >= 1 */
   int matvec_precision;    /* FDST_MV_F64 or FDST_MV_DF64 */
-  double geometry_amplitude;  /* sine-bump amplitude a of the mapped geometry, in (0, 0.25]; <= 0 selects 0.1 */
+  double geometry_amplitude;  /* sine-bump amplitude a, in (0, 0.25]; <= 0 selects 0.1; ignored by the annulus */
   double viscosity_contrast;  /* mapped geometry: k >= 1 selects nu(x) = 1 + (k - 1)(1 - cos(2 pi x1)) / 2
-                                 (values in [1, k]); <= 0 selects nu(x) = 1 + 0.5 sin(2 pi x1) cos(2 pi x2) */
+                                 (values in [1, k]); <= 0 selects the map's own field: nu(x) = 1 + 0.5
+                                 sin(2 pi x1) cos(2 pi x2) on the sine bump, nu = 1 on the annulus */
   int matvec_form;         /* mapped geometry: FDST_MATVEC_ASSEMBLED (CSR) or FDST_MATVEC_MATRIX_FREE
                               (no CSR: the operator, its B and B^T parts and diag(A) by sum
                               factorization at the quadrature points, FP64 for the true residual);

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libfdst.so")
 TH, RT = 0, 1
 FD_F64, FD_TF32X3, FD_BF16X6 = 0, 1, 2
 HAS_TC = True        # the split-TF32 tcgen05 FD contraction is built (sm_103a)
-GEOM_IDENTITY, GEOM_SINE_BUMP = 0, 1
+GEOM_IDENTITY, GEOM_SINE_BUMP, GEOM_ANNULUS = 0, 1, 2
 VARIANT_PD, VARIANT_PD_GEO = 0, 1
 MV_F64, MV_DF64 = 0, 1
 MATVEC_ASSEMBLED, MATVEC_MATRIX_FREE = 0, 1

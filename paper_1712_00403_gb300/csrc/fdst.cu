@@ -1169,7 +1169,8 @@ fdst_status fdst_setup(const fdst_desc *desc, fdst_handle *out) {
   }
   if (desc->degree < 1 || desc->degree > 12) { set_error("degree must be in [1, 12]"); return FDST_INVALID_ARGUMENT; }
   if (desc->max_rhs < 1) { set_error("max_rhs must be >= 1"); return FDST_INVALID_ARGUMENT; }
-  if (desc->geometry != FDST_GEOM_IDENTITY && desc->geometry != FDST_GEOM_SINE_BUMP) {
+  if (desc->geometry != FDST_GEOM_IDENTITY && desc->geometry != FDST_GEOM_SINE_BUMP &&
+      desc->geometry != FDST_GEOM_ANNULUS) {
     set_error("unknown geometry");
     return FDST_INVALID_ARGUMENT;
   }
@@ -1212,7 +1213,7 @@ fdst_status fdst_setup(const fdst_desc *desc, fdst_handle *out) {
   fdst_status st;
   auto fail = [&](fdst_status s) { fdst_destroy(h.release()); return s; };
   if ((st = build_spaces(hp)) != FDST_OK) return fail(st);
-  if (desc->geometry == FDST_GEOM_SINE_BUMP && (st = build_mapped_pre(hp)) != FDST_OK) return fail(st);
+  if (desc->geometry != FDST_GEOM_IDENTITY && (st = build_mapped_pre(hp)) != FDST_OK) return fail(st);
   if (hp->mapped && desc->matvec_form == FDST_MATVEC_MATRIX_FREE) {
     if ((st = build_matrix_free(hp)) != FDST_OK) return fail(st);
     if (desc->variant == FDST_VARIANT_PD_GEO && (st = mf_velocity_scaling(hp)) != FDST_OK) return fail(st);

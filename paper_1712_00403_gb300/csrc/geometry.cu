@@ -16,11 +16,15 @@ namespace fdst {
 
 // ------------------------------------------------------------------ points
 
-// x = eta + a s(eta) 1, s = sin(pi e1) sin(pi e2) sin(pi e3); J = I + 1 g^T with
-// g = a grad s; det J = 1 + 1.g; J^{-1} = I - 1 g^T / det (Sherman-Morrison);
-// nu(x) = 1 + 0.5 sin(2 pi x1) cos(2 pi x2), or with a contrast k >= 1
-// nu(x) = 1 + (k - 1)(1 - cos(2 pi x1)) / 2 (values in [1, k]).
-__global__ void k_geo_points(GeoPoints gp, double amp, double contrast) {
+// Sine bump: x = eta + a s(eta) 1, s = sin(pi e1) sin(pi e2) sin(pi e3); J = I + 1 g^T
+// with g = a grad s; det J = 1 + 1.g; J^{-1} = I - 1 g^T / det (Sherman-Morrison);
+// nu(x) = 1 + 0.5 sin(2 pi x1) cos(2 pi x2).
+// Annulus (eighth of a thick annulus, Sec. 7): r = 1 + e1, t = pi e2 / 4,
+// x = (r cos t, r sin t, e3); the columns of J are (cos t, sin t, 0), (pi r / 4)
+// (-sin t, cos t, 0) and e3, so det J = pi r / 4 and the rows of J^{-1} are
+// (cos t, sin t, 0), (-sin t, cos t, 0) / (pi r / 4) and e3; nu = 1.
+// Either map with a contrast k >= 1: nu(x) = 1 + (k - 1)(1 - cos(2 pi x1)) / 2.
+__global__ void k_geo_points(GeoPoints gp, int kind, double amp, double contrast) {
   const int64_t Q = gp.Q;
   const double pi = 3.14159265358979323846;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < Q; q += (int64_t)gridDim.x * blockDim.x) {
@@ -28,6 +32,14 @@ __global__ void k_geo_points(GeoPoints gp, double amp, double contrast) {
     const int64_t t = q / gp.nq[0];
     const int q2 = (int)(t % gp.nq[1]), q3 = (int)(t / gp.nq[1]);
     const double e1 = gp.pts[0][q1], e2 = gp.pts[1][q2], e3 = gp.pts[2][q3];
+    if (kind == kGeoAnnulus) {
+      const double r = 1.0 + e1, t = 0.25 * pi * e2, c = cos(t), s = sin(t), dt = 0.25 * pi * r;
+      const double Ji[9] = {c, s, 0.0, -s / dt, c / dt, 0.0, 0.0, 0.0, 1.0};
+      for (int i = 0; i < 9; ++i) gp.jinv[(int64_t)i * Q + q] = Ji[i];
+      gp.det[q] = dt;
+      gp.nu[q] = contrast > 0.0 ? 1.0 + (contrast - 1.0) * (1.0 - cos(2.0 * pi * r * c)) * 0.5 : 1.0;
+      continue;
+    }
     const double s1 = sin(pi * e1), s2 = sin(pi * e2), s3 = sin(pi * e3);
     const double c1 = cos(pi * e1), c2 = cos(pi * e2), c3 = cos(pi * e3);
     const double s = amp * s1 * s2 * s3;
@@ -42,11 +54,11 @@ __global__ void k_geo_points(GeoPoints gp, double amp, double contrast) {
   }
 }
 
-void launch_geo_points(const GeoPoints &gp, double amp, double contrast, cudaStream_t s) {
+void launch_geo_points(const GeoPoints &gp, int kind, double amp, double contrast, cudaStream_t s) {
   int64_t blocks = (gp.Q + 255) / 256;
   if (blocks > 8192) blocks = 8192;
   count_launch(1);
-  k_geo_points<<<(unsigned)blocks, 256, 0, s>>>(gp, amp, contrast);
+  k_geo_points<<<(unsigned)blocks, 256, 0, s>>>(gp, kind, amp, contrast);
 }
 
 // ------------------------------------------------------------------ separable fit

@@ -48,7 +48,9 @@ struct CsrDev {
   int64_t nrows = 0, nnz = 0;
 };
 
-void launch_geo_points(const GeoPoints &gp, double amp, double contrast, cudaStream_t s);
+// kind: kGeoSineBump or kGeoAnnulus (the values of FDST_GEOM_SINE_BUMP / FDST_GEOM_ANNULUS)
+constexpr int kGeoSineBump = 1, kGeoAnnulus = 2;
+void launch_geo_points(const GeoPoints &gp, int kind, double amp, double contrast, cudaStream_t s);
 void launch_logc(const GeoPoints &gp, double *L, cudaStream_t s);
 void launch_fit_sweep(const double *L, double *f, int d, const GeoPoints &gp, int fstride, cudaStream_t s);
 void launch_diag_q(const GeoPoints &gp, const MeshTables &mt, double *dq, cudaStream_t s);

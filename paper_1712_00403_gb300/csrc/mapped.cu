@@ -107,7 +107,7 @@ fdst_status build_mapped_pre(fdst_ctx *h) {
   TRY(dalloc(h, &gp.det, (size_t)gp.Q));
   TRY(dalloc(h, &gp.nu, (size_t)gp.Q));
   const double amp = h->desc.geometry_amplitude > 0.0 ? h->desc.geometry_amplitude : kAmp;
-  if (amp > 0.25) {
+  if (h->desc.geometry == FDST_GEOM_SINE_BUMP && amp > 0.25) {
     set_error("geometry_amplitude must be at most 0.25 (det J stays positive)");
     return FDST_INVALID_ARGUMENT;
   }
@@ -115,7 +115,8 @@ fdst_status build_mapped_pre(fdst_ctx *h) {
     set_error("viscosity_contrast must be >= 1 (or <= 0 for the default field)");
     return FDST_INVALID_ARGUMENT;
   }
-  launch_geo_points(gp, amp, h->desc.viscosity_contrast, st);
+  launch_geo_points(gp, h->desc.geometry == FDST_GEOM_ANNULUS ? kGeoAnnulus : kGeoSineBump, amp,
+                    h->desc.viscosity_contrast, st);
   h->gp = gp;
   // ---- separable fit of the 9 diagonal coefficients c^k_jj (log, midrange sweeps)
   const int fstride = std::max(gp.nq[0], std::max(gp.nq[1], gp.nq[2]));

@@ -22,6 +22,9 @@ WORKLOADS = {
     # matrix-free operator (its CSR would hold about 1.1e10 nonzeros)
     "mapped_th_p3_64": dict(dim=3, disc="TH", p=3, n_el=(64, 64, 64), seeds=list(range(300, 304)),
                             geometry="sine_bump"),
+    # the eighth of a thick annulus (radii 1 and 2, height 1, nu = 1) in polar form, p=3, 32^3 elements
+    "annulus_th_p3_32": dict(dim=3, disc="TH", p=3, n_el=(32, 32, 32), seeds=list(range(300, 304)),
+                             geometry="annulus"),
     # 64 independent unit-cube TH instances, p ~ U{2..6}, elements per direction ~ U{16..96}
     # (instance draw seed 400, right-hand side seeds 401..464)
     "batched_64": dict(kind="batched", count=64, seed=400, rhs_seed0=401),
