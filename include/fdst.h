@@ -218,6 +218,15 @@ fdst_status fdst_solve_gmres(fdst_handle h, int prec, int form, const double *d_
 fdst_status fdst_solve_host(fdst_handle h, const double *h_b, double *h_x, int nrhs, double tol, int maxit,
                             fdst_solve_info *info, fdst_stream stream);
 
+/*
+ * fdst_solve_host_zero - fdst_solve_host from the zero initial guess (the
+ * paper's x0 = 0, Sec. 7): h_x is output only (never read), the device
+ * iterate is cleared on the device, so only h_b travels to the GPU and only
+ * the solutions come back. Same arguments, errors and info as fdst_solve_host.
+ */
+fdst_status fdst_solve_host_zero(fdst_handle h, const double *h_b, double *h_x, int nrhs, double tol, int maxit,
+                                 fdst_solve_info *info, fdst_stream stream);
+
 /* fdst_apply_prec_host - fdst_apply_prec with host vectors (copies in and out). */
 fdst_status fdst_apply_prec_host(fdst_handle h, const double *h_r, double *h_s, int nrhs, fdst_stream stream);
 

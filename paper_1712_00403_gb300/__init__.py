@@ -63,7 +63,7 @@ class SolveInfo(ctypes.Structure):
 
 
 ENTRY_POINTS = ["fdst_setup", "fdst_destroy", "fdst_get_sizes", "fdst_apply_prec", "fdst_matvec", "fdst_solve",
-                "fdst_solve_host", "fdst_apply_prec_host", "fdst_solve_gmres", "fdst_apply_block_prec", "fdst_set_timing", "fdst_get_timing", "fdst_get_kernel_timing", "fdst_convert",
+                "fdst_solve_host", "fdst_solve_host_zero", "fdst_apply_prec_host", "fdst_solve_gmres", "fdst_apply_block_prec", "fdst_set_timing", "fdst_get_timing", "fdst_get_kernel_timing", "fdst_convert",
                 "fdst_fd_apply_static", "fdst_batch_create", "fdst_batch_solve", "fdst_batch_info",
                 "fdst_batch_destroy", "fdst_server_create", "fdst_server_submit", "fdst_server_step",
                 "fdst_server_result", "fdst_server_stats", "fdst_server_destroy", "fdst_check_bounded_wait", "fdst_device_error",
@@ -291,12 +291,14 @@ class Stokes:
         return [dict(iterations=i.iterations, status=STATUS.get(i.status, i.status), eta_rel=i.eta_rel,
                      true_rel_res=i.true_rel_res, iterations_estimate=i.iterations_estimate) for i in info]
 
-    def solve_host(self, b, x, tol=1e-8, maxit=1000, stream=None):
-        """b, x: host numpy float64 arrays (x is the initial guess, overwritten)."""
+    def solve_host(self, b, x, tol=1e-8, maxit=1000, stream=None, zero_guess=False):
+        """b, x: host numpy float64 arrays. x is the initial guess, overwritten by the
+        solution; with zero_guess=True the solve starts from x0 = 0 and x is output only."""
         n = b.size // self.n_total
         info = (SolveInfo * n)()
-        code = _lib.fdst_solve_host(self._h, ctypes.c_void_p(b.ctypes.data), ctypes.c_void_p(x.ctypes.data), n,
-                                    tol, maxit, info, _stream_ptr(stream))
+        entry = _lib.fdst_solve_host_zero if zero_guess else _lib.fdst_solve_host
+        code = entry(self._h, ctypes.c_void_p(b.ctypes.data), ctypes.c_void_p(x.ctypes.data), n,
+                     tol, maxit, info, _stream_ptr(stream))
         if code not in (0, 5, 6, 7, 9):
             _check(code)
         return [dict(iterations=i.iterations, status=STATUS.get(i.status, i.status), eta_rel=i.eta_rel,

@@ -1699,6 +1699,21 @@ fdst_status fdst_solve_host(fdst_handle h, const double *h_b, double *h_x, int n
   return s;
 }
 
+fdst_status fdst_solve_host_zero(fdst_handle h, const double *h_b, double *h_x, int nrhs, double tol, int maxit,
+                                 fdst_solve_info *info, fdst_stream stream) {
+  if (!h || !h_b || !h_x || !info) { set_error("NULL argument"); return FDST_INVALID_ARGUMENT; }
+  if (nrhs < 1 || nrhs > h->max_rhs) { set_error("nrhs out of range [1, max_rhs]"); return FDST_INVALID_ARGUMENT; }
+  TRY(ensure_host_buffers(h));
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bytes = sizeof(double) * h->n_total * nrhs;
+  CK(cudaMemcpyAsync(h->hb, h_b, bytes, cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(h->hx, 0, bytes, st));
+  fdst_status s = fdst_solve(h, h->hb, h->hx, nrhs, tol, maxit, info, stream);
+  CK(cudaMemcpyAsync(h_x, h->hx, bytes, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return s;
+}
+
 fdst_status fdst_apply_prec_host(fdst_handle h, const double *h_r, double *h_s, int nrhs, fdst_stream stream) {
   if (!h || !h_r || !h_s) { set_error("NULL argument"); return FDST_INVALID_ARGUMENT; }
   if (nrhs < 1 || nrhs > h->max_rhs) { set_error("nrhs out of range [1, max_rhs]"); return FDST_INVALID_ARGUMENT; }

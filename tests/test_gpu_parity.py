@@ -130,6 +130,11 @@ def test_host_entry_points_match_device():
     info_d = P.solve(b, x, tol=1e-8, maxit=300)
     assert info_h[0]["iterations"] == info_d[0]["iterations"]
     assert rel(xh, x.cpu().numpy()) <= 1e-14
+    # zero initial guess: whatever the output array holds is never read
+    xz = np.full_like(bh, np.nan)
+    info_z = P.solve_host(bh, xz, tol=1e-8, maxit=300, zero_guess=True)
+    assert info_z[0]["iterations"] == info_d[0]["iterations"]
+    assert np.array_equal(xz, xh)
     sh = np.empty_like(bh)
     P.apply_prec_host(bh, sh)
     s = torch.empty_like(b)
