@@ -62,7 +62,7 @@ enum { FDST_GEOM_IDENTITY = 0, FDST_GEOM_SINE_BUMP = 1, FDST_GEOM_ANNULUS = 2 };
 enum { FDST_VARIANT_PD = 0, FDST_VARIANT_PD_GEO = 1 };      /* P_D (Sec. 5) or P_D^G (Sec. 6) */
 /* Matvec arithmetic: FP64 (DFMA), or double-float (each value an unevaluated
  * sum of two floats, 48-bit significand, error-free FMA products and TwoSum
- * additions on the FP32 units). fdst_solve always checks the true residual
+ * additions on the FP32 units). fdst_solve ends on a true residual computed
  * with the FP64 matvec. */
 enum { FDST_MV_F64 = 0, FDST_MV_DF64 = 1 };
 enum { FDST_MATVEC_ASSEMBLED = 0, FDST_MATVEC_MATRIX_FREE = 1 };
@@ -165,9 +165,14 @@ fdst_status fdst_matvec(fdst_handle h, const double *d_x, double *d_y, int nrhs,
  * 1e-8, x0 = 0) on nrhs independent right-hand sides at once. Every
  * right-hand side keeps its own recurrence and stops on its own when
  * ||r_j||_{P^-1} <= tol ||r_0||_{P^-1}. d_x holds the initial guesses on entry
- * and the solutions on exit. info: host array of nrhs entries, filled when
- * the call returns (the call synchronizes the stream). Returns FDST_OK when
- * every right-hand side converged, otherwise the first non-OK per-RHS status.
+ * and the solutions on exit (an all-zero d_x is detected and r_0 = b taken
+ * without a matvec). The true residual ||b - A x||_2 / ||b||_2 is checked when
+ * the estimates meet their thresholds: with the double-float matvec in that
+ * arithmetic while the check only decides whether to go on, always in FP64
+ * before the call returns (info.true_rel_res is the FP64 value). info: host
+ * array of nrhs entries, filled when the call returns (the call synchronizes
+ * the stream). Returns FDST_OK when every right-hand side converged,
+ * otherwise the first non-OK per-RHS status.
  */
 fdst_status fdst_solve(fdst_handle h, const double *d_b, double *d_x, int nrhs, double tol, int maxit,
                        fdst_solve_info *info, fdst_stream stream);

@@ -532,13 +532,16 @@ static fdst_status build_batch(fdst_batch b) {
 }
 
 // Start of one member's MINRES (right-hand side 0 of its handle, b and x in
-// the handle's hb / hx): v = b - A x0, z = P^{-1} v / gamma_1, |b|^2 in dots[3].
-fdst_status member_init(fdst_ctx *h, int *n_stopped, double tol, cudaStream_t st) {
+// the handle's hb / hx): v = b - A x0 (v = b when x0 = 0), z = P^{-1} v / gamma_1,
+// |b|^2 in dots[3].
+fdst_status member_init(fdst_ctx *h, int *n_stopped, double tol, cudaStream_t st, bool x0_zero) {
   const int64_t m = h->n_total;
   CK(cudaMemsetAsync(h->done, 0, sizeof(int), st));
-  TRY(run_matvec(h, h->hx, h->Az, 1, nullptr, st, true));
   launch_axpby(h->hb, h->v, 1.0, 0.0, m, m, 1, st);
-  launch_axpby(h->Az, h->v, -1.0, 1.0, m, m, 1, st);
+  if (!x0_zero) {
+    TRY(run_matvec(h, h->hx, h->Az, 1, nullptr, st, true));
+    launch_axpby(h->Az, h->v, -1.0, 1.0, m, m, 1, st);
+  }
   CK(cudaMemsetAsync(h->v_old, 0, sizeof(double) * m, st));
   CK(cudaMemsetAsync(h->w, 0, sizeof(double) * m, st));
   CK(cudaMemsetAsync(h->w_old, 0, sizeof(double) * m, st));
@@ -550,10 +553,11 @@ fdst_status member_init(fdst_ctx *h, int *n_stopped, double tol, cudaStream_t st
   return FDST_OK;
 }
 
-// Enqueues ||b - A x||^2 (FP64 matvec) into dots[0]; the caller syncs and divides by dots[3].
-fdst_status member_residual(fdst_ctx *h, cudaStream_t st) {
+// Enqueues ||b - A x||^2 (FP64 matvec, or the handle's arithmetic when !exact) into
+// dots[0]; the caller syncs and divides by dots[3].
+fdst_status member_residual(fdst_ctx *h, cudaStream_t st, bool exact) {
   const int64_t m = h->n_total;
-  TRY(run_matvec(h, h->hx, h->Az, 1, nullptr, st, true));
+  TRY(run_matvec(h, h->hx, h->Az, 1, nullptr, st, exact));
   launch_axpby(h->hb, h->Az, 1.0, -1.0, m, m, 1, st);
   launch_dot(h->Az, h->Az, m, m, 1, h->partials, h->counters, h->dots, nullptr, st);
   return FDST_OK;
@@ -656,22 +660,29 @@ fdst_status fdst_batch_solve(fdst_batch b, const double *const *d_b, double *con
   CK(cudaEventRecord(ev, us));
   CK(cudaStreamWaitEvent(st, ev, 0));
   const int n = b->n;
-  // ---- per-problem start: v = b - A x0, z = P^{-1} v, gamma_1, |b|^2
+  // ---- per-problem start: v = b - A x0, z = P^{-1} v, gamma_1, |b|^2 (x0 = 0, found on
+  // the device in one pass over all members, spares the FP64 matvec)
   CK(cudaMemsetAsync(b->n_stopped, 0, sizeof(int), st));
+  std::vector<int> nz(n, 1);
   for (int i = 0; i < n; ++i) {
     fdst_ctx *h = b->hs[i];
     const int64_t m = h->n_total;
     CK(cudaMemcpyAsync(h->hb, d_b[i], sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(h->hx, d_x[i], sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
-    TRY(member_init(h, b->n_stopped, tol, st));
+    launch_any_nonzero(h->hx, m, h->n_stopped, st);
+    CK(cudaMemcpyAsync(&nz[i], h->n_stopped, sizeof(int), cudaMemcpyDeviceToHost, st));
   }
+  CK(cudaStreamSynchronize(st));
+  for (int i = 0; i < n; ++i) TRY(member_init(b->hs[i], b->n_stopped, tol, st, nz[i] == 0));
   std::vector<double> bb(n), true_rel(n, -1.0);
   for (int i = 0; i < n; ++i) CK(cudaMemcpyAsync(&bb[i], b->hs[i]->dots + 3, sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  auto true_residuals = [&]() -> fdst_status {
+  // checks that only decide whether to go on use the members' double-float matvec (a relative
+  // error near 1e-13 of |A||x|); a batch ends on FP64 residuals
+  auto true_residuals = [&](bool exact = true) -> fdst_status {
     std::vector<double> rr(n);
     for (int i = 0; i < n; ++i) {
-      TRY(member_residual(b->hs[i], st));
+      TRY(member_residual(b->hs[i], st, exact));
       CK(cudaMemcpyAsync(&rr[i], b->hs[i]->dots, sizeof(double), cudaMemcpyDeviceToHost, st));
     }
     CK(cudaStreamSynchronize(st));
@@ -711,8 +722,16 @@ fdst_status fdst_batch_solve(fdst_batch b, const double *const *d_b, double *con
       CK(cudaMemcpyAsync(b->h_n_stopped, b->n_stopped, sizeof(int), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
       if (*b->h_n_stopped >= n) {
-        TRY(true_residuals());
-        residuals_current = true;
+        TRY(true_residuals(!b->df));
+        residuals_current = !b->df;   // current = computed in FP64
+        if (b->df) {
+          bool all_at_tol = true;
+          for (int i = 0; i < n; ++i) all_at_tol = all_at_tol && true_rel[i] <= tol;
+          if (all_at_tol) {
+            TRY(true_residuals(true));
+            residuals_current = true;
+          }
+        }
         int running = 0;
         for (int i = 0; i < n; ++i) {
           fdst_ctx *h = b->hs[i];
@@ -745,7 +764,7 @@ fdst_status fdst_batch_solve(fdst_batch b, const double *const *d_b, double *con
     }
   }
   CK(cudaGetLastError());
-  if (!residuals_current) TRY(true_residuals());
+  if (!residuals_current) TRY(true_residuals(true));
   fdst_status ret = FDST_OK;
   for (int i = 0; i < n; ++i) {
     fdst_ctx *h = b->hs[i];

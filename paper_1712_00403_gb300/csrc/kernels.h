@@ -123,6 +123,9 @@ void launch_basis_axpy(const double *V, int64_t vstride, int kc, const double *c
 void launch_scale_by_norm(const double *src, double *dst, const double *nrm2, int64_t n, int64_t stride, int nrhs,
                           const int *skip, cudaStream_t s);
 
+// *flag = 1 when some x[i], 0 <= i < n, differs from zero (NaN counts as nonzero), else 0.
+void launch_any_nonzero(const double *x, int64_t n, int *flag, cudaStream_t s);
+
 // y_j = alpha * x_j + beta * y_j for all j (elementwise, deterministic).
 void launch_axpby(const double *x, double *y, double alpha, double beta, int64_t n, int64_t stride, int nrhs,
                   cudaStream_t s);

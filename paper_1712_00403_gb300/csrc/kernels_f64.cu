@@ -530,6 +530,22 @@ void launch_dot(const double *a, const double *b, int64_t n, int64_t stride, int
   k_dot<<<dim3((unsigned)blocks, nrhs), 256, 0, s>>>(a, b, n, stride, partials, counters, out, done);
 }
 
+__global__ void k_any_nonzero(const double *x, int64_t n, int *flag) {
+  bool nz = false;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    nz |= !(x[i] == 0.0);
+  if (__syncthreads_or(nz) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
+void launch_any_nonzero(const double *x, int64_t n, int *flag, cudaStream_t s) {
+  cudaMemsetAsync(flag, 0, sizeof(int), s);
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks < 1) blocks = 1;
+  count_launch(1);
+  k_any_nonzero<<<(unsigned)blocks, 256, 0, s>>>(x, n, flag);
+}
+
 __global__ void k_axpby(const double *x, double *y, double alpha, double beta, int64_t n, int64_t stride) {
   const double *xr = x + blockIdx.y * stride;
   double *yr = y + blockIdx.y * stride;

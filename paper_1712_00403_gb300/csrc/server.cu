@@ -362,7 +362,7 @@ fdst_status fdst_server_step(fdst_server s, double now, int *n_active, int *n_qu
     }
     CK(cudaMemcpyAsync(h->hb, r.b.data(), sizeof(double) * h->n_total, cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(h->hx, 0, sizeof(double) * h->n_total, st));
-    TRY(member_init(h, s->dev_counter, s->o.tol, st));
+    TRY(member_init(h, s->dev_counter, s->o.tol, st, true));   // hx was just cleared
     CK(cudaMemcpyAsync(&r.bb, h->dots + 3, sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     r.t_admit = now;
