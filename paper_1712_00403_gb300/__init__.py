@@ -91,6 +91,7 @@ def load_library(path=LIB_PATH):
     lib.fdst_apply_block_prec.argtypes = [vp, i, vp, vp, i, vp]
     lib.fdst_check_bounded_wait.argtypes = [ctypes.POINTER(i), ctypes.POINTER(d)]
     lib.fdst_solve_host.argtypes = [vp, vp, vp, i, d, i, ctypes.POINTER(SolveInfo), vp]
+    lib.fdst_solve_host_zero.argtypes = [vp, vp, vp, i, d, i, ctypes.POINTER(SolveInfo), vp]
     lib.fdst_apply_prec_host.argtypes = [vp, vp, vp, i, vp]
     lib.fdst_set_timing.argtypes = [vp, i]
     lib.fdst_device_error.argtypes = [ctypes.POINTER(i)]
@@ -113,6 +114,7 @@ def load_library(path=LIB_PATH):
     lib.fdst_get_kernel_timing.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_int64)]
     lib.fdst_convert.argtypes = [i, vp, vp, ctypes.c_int64, vp]
     lib.fdst_last_error.restype = ctypes.c_char_p
+    lib.fdst_last_error.argtypes = []
     for name in ENTRY_POINTS[:-2]:
         getattr(lib, name).restype = ctypes.c_int
     lib.fdst_kernel_launches.restype = ctypes.c_int64

@@ -41,6 +41,11 @@ def test_every_declared_symbol_is_exported(lib):
         assert n in exported, n
         assert hasattr(lib, n)
     assert set(pkg.ENTRY_POINTS) <= exported
+    # every declared entry point is bound, with its argument types (ctypes cannot convert
+    # a Python float without them)
+    assert set(_declared()) <= set(pkg.ENTRY_POINTS)
+    for n in pkg.ENTRY_POINTS:
+        assert getattr(lib, n).argtypes is not None, n
 
 
 def _desc(pkg, knots, p, dim=None, **kw):
