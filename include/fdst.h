@@ -166,10 +166,8 @@ fdst_status fdst_matvec(fdst_handle h, const double *d_x, double *d_y, int nrhs,
  * right-hand side keeps its own recurrence and stops on its own when
  * ||r_j||_{P^-1} <= tol ||r_0||_{P^-1}. d_x holds the initial guesses on entry
  * and the solutions on exit (an all-zero d_x is detected and r_0 = b taken
- * without a matvec). The true residual ||b - A x||_2 / ||b||_2 is checked when
- * the estimates meet their thresholds: with the double-float matvec in that
- * arithmetic while the check only decides whether to go on, always in FP64
- * before the call returns (info.true_rel_res is the FP64 value). info: host
+ * without a matvec). The true residual ||b - A x||_2 / ||b||_2 is checked in
+ * FP64 when the estimates meet their thresholds. info: host
  * array of nrhs entries, filled when the call returns (the call synchronizes
  * the stream). Returns FDST_OK when every right-hand side converged,
  * otherwise the first non-OK per-RHS status.

@@ -553,11 +553,10 @@ fdst_status member_init(fdst_ctx *h, int *n_stopped, double tol, cudaStream_t st
   return FDST_OK;
 }
 
-// Enqueues ||b - A x||^2 (FP64 matvec, or the handle's arithmetic when !exact) into
-// dots[0]; the caller syncs and divides by dots[3].
-fdst_status member_residual(fdst_ctx *h, cudaStream_t st, bool exact) {
+// Enqueues ||b - A x||^2 (FP64 matvec) into dots[0]; the caller syncs and divides by dots[3].
+fdst_status member_residual(fdst_ctx *h, cudaStream_t st) {
   const int64_t m = h->n_total;
-  TRY(run_matvec(h, h->hx, h->Az, 1, nullptr, st, exact));
+  TRY(run_matvec(h, h->hx, h->Az, 1, nullptr, st, true));
   launch_axpby(h->hb, h->Az, 1.0, -1.0, m, m, 1, st);
   launch_dot(h->Az, h->Az, m, m, 1, h->partials, h->counters, h->dots, nullptr, st);
   return FDST_OK;
@@ -677,12 +676,10 @@ fdst_status fdst_batch_solve(fdst_batch b, const double *const *d_b, double *con
   std::vector<double> bb(n), true_rel(n, -1.0);
   for (int i = 0; i < n; ++i) CK(cudaMemcpyAsync(&bb[i], b->hs[i]->dots + 3, sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  // checks that only decide whether to go on use the members' double-float matvec (a relative
-  // error near 1e-13 of |A||x|); a batch ends on FP64 residuals
-  auto true_residuals = [&](bool exact = true) -> fdst_status {
+  auto true_residuals = [&]() -> fdst_status {
     std::vector<double> rr(n);
     for (int i = 0; i < n; ++i) {
-      TRY(member_residual(b->hs[i], st, exact));
+      TRY(member_residual(b->hs[i], st));
       CK(cudaMemcpyAsync(&rr[i], b->hs[i]->dots, sizeof(double), cudaMemcpyDeviceToHost, st));
     }
     CK(cudaStreamSynchronize(st));
@@ -722,16 +719,8 @@ fdst_status fdst_batch_solve(fdst_batch b, const double *const *d_b, double *con
       CK(cudaMemcpyAsync(b->h_n_stopped, b->n_stopped, sizeof(int), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
       if (*b->h_n_stopped >= n) {
-        TRY(true_residuals(!b->df));
-        residuals_current = !b->df;   // current = computed in FP64
-        if (b->df) {
-          bool all_at_tol = true;
-          for (int i = 0; i < n; ++i) all_at_tol = all_at_tol && true_rel[i] <= tol;
-          if (all_at_tol) {
-            TRY(true_residuals(true));
-            residuals_current = true;
-          }
-        }
+        TRY(true_residuals());
+        residuals_current = true;
         int running = 0;
         for (int i = 0; i < n; ++i) {
           fdst_ctx *h = b->hs[i];
@@ -764,7 +753,7 @@ fdst_status fdst_batch_solve(fdst_batch b, const double *const *d_b, double *con
     }
   }
   CK(cudaGetLastError());
-  if (!residuals_current) TRY(true_residuals(true));
+  if (!residuals_current) TRY(true_residuals());
   fdst_status ret = FDST_OK;
   for (int i = 0; i < n; ++i) {
     fdst_ctx *h = b->hs[i];
