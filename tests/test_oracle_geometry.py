@@ -89,10 +89,11 @@ def test_cube_limit_weighted_pencils_equal_plain():
     np.testing.assert_allclose(pdg.apply(r), stokes.apply_PD_inv(S, r), rtol=1e-10, atol=1e-12)
 
 
-def test_scaled_diagonals_match_operator_diagonals():
+@pytest.mark.parametrize("kind", ["sine_bump", "annulus"])
+def test_scaled_diagonals_match_operator_diagonals(kind):
     """diag(P_V^G) = diag(A) and diag(P_Q^G) = diag(Q) by construction (Sec. 6)."""
     S = _S(2, 1)
-    G = geo.Grid(S)
+    G = geo.Grid(S, geometry_kind=kind)
     pdg = geo.PDG(S, G)
     A, _ = geo.brute_force(S, G)
     nv = S.block_sizes[0]
@@ -103,10 +104,11 @@ def test_scaled_diagonals_match_operator_diagonals():
         np.testing.assert_allclose(np.diag(PG), np.diag(A)[k * nv:(k + 1) * nv], rtol=1e-12)
 
 
-def test_theorem2_pressure_mass_bounds():
+@pytest.mark.parametrize("kind", ["sine_bump", "annulus"])
+def test_theorem2_pressure_mass_bounds(kind):
     """lambda(P_Q^{-1} Q) lies in [min |det J|/nu, max |det J|/nu] (Theorem 2, Remark)."""
     S = _S(2, 2)
-    G = geo.Grid(S)
+    G = geo.Grid(S, geometry_kind=kind)
     T = [G.table(S.pres[d], d, False) for d in range(3)]
     F = (G.W * np.abs(G.det) / G.nu).reshape(-1)
     Bq = np.einsum("ap,bq,cr->cbapqr", T[0], T[1], T[2]).reshape(S.block_sizes[3], -1)
@@ -271,3 +273,28 @@ def test_annulus_sum_factorized_matvec_vs_brute_force():
         np.testing.assert_allclose(geo.matvec(S, G, x), full @ x, atol=1e-12 * np.abs(full).max() * 10)
     np.testing.assert_allclose(A, A.T, atol=1e-13 * np.abs(A).max())
     assert np.all(np.linalg.eigvalsh(A) > 0)
+
+
+@pytest.mark.parametrize("kind", ["sine_bump", "annulus"])
+def test_theorem1_velocity_bounds(kind):
+    """Theorem 1 with the Korn constants 1/2 (Sec. 5, TH): the eigenvalues of P_V^{-1} A
+    lie in [nu_min inf(|det J| / ||J||^2) / 2, 2 nu_max sup(|det J| ||J^{-1}||^2)]. The
+    upper bound holds pointwise at the quadrature points (|grad^s v| <= |grad v|), so
+    exactly; the lower one rests on Korn's identity, exact only for exact integration,
+    so it is checked with a 10% margin on these non-polynomial maps."""
+    import scipy.linalg
+    S = _S(2, 1)
+    G = geo.Grid(S, geometry_kind=kind)
+    A, _ = geo.brute_force(S, G)
+    blocks = []
+    for k in range(3):
+        K0, M0, coef = stokes.pv_pencils(S, k)
+        blocks.append(kron.kron_sum_matrix(K0, M0, coef))
+    PV = scipy.linalg.block_diag(*blocks)
+    lam = scipy.linalg.eigh(A, PV, eigvals_only=True)
+    J, Ji = G.J.reshape(-1, 3, 3), G.Jinv.reshape(-1, 3, 3)
+    det = np.abs(G.det.reshape(-1))
+    lo = 0.5 * G.nu.min() * np.min(det / np.linalg.norm(J, 2, axis=(1, 2)) ** 2)
+    hi = 2.0 * G.nu.max() * np.max(det * np.linalg.norm(Ji, 2, axis=(1, 2)) ** 2)
+    assert lam.max() <= hi * (1 + 1e-10)
+    assert lam.min() >= 0.9 * lo
