@@ -40,7 +40,8 @@ numpy.linalg.det; on the annulus the quadrature volume 3 pi / 8 and the
 moment int x1 dx = 7 sqrt(2) / 6 in closed form, and the chain rule
 J^{-T} grad_eta (f o G) = grad_x f for polynomials f; the fit reproduces an exactly separable field; on the cube
 P~_V = P_V and D_V = I; diag(P_V^G) = diag(A), diag(P_Q^G) = diag(Q);
-Theorem 2 spectral bounds of P_Q^{-1} Q. Parity unpinned: the separable fit
+Theorem 2 spectral bounds of P_Q^{-1} Q and Theorem 1 bounds of P_V^{-1} A
+(Korn constants 1/2), on both maps. Parity unpinned: the separable fit
 on non-separable fields (no independent reference exists; the CUDA path
 runs the same algorithm).
 """
