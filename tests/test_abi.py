@@ -105,3 +105,47 @@ def test_new_entry_points_validate_on_the_host(lib):
     assert lib.fdst_get_kernel_timing(None, None, None) == 1
     assert lib.fdst_check_bounded_wait(None, None) == 1
     assert "NULL" in lib.fdst_last_error().decode()
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The binding's ctypes mirrors of fdst_desc, fdst_sizes, fdst_solve_info and
+    fdst_server_opts have the header's sizes and field offsets (a C program compiled
+    against include/fdst.h prints them)."""
+    import shutil
+
+    import paper_1712_00403_gb300 as pkg
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc is not available")
+    mirrors = {"fdst_desc": pkg.Desc, "fdst_sizes": pkg.Sizes, "fdst_solve_info": pkg.SolveInfo,
+               "fdst_server_opts": pkg.ServerOpts}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "fdst.h"', "int main(void) {"]
+    for c, py in mirrors.items():
+        lines.append(f'  printf("{c} size %zu\\n", sizeof({c}));')
+        for name, _ in py._fields_:
+            lines.append(f'  printf("{c} {name} %zu\\n", offsetof({c}, {name}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True,
+                   capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(ln.split()[:2]): int(ln.split()[2]) for ln in out if ln}
+    for c, py in mirrors.items():
+        assert got[(c, "size")] == ctypes.sizeof(py), c
+        for name, _ in py._fields_:
+            assert got[(c, name)] == getattr(py, name).offset, (c, name)
+
+
+def test_struct_members_match_the_header():
+    """Same member names in the same order as the header declares them (an extra
+    trailing int could hide in padding from the size check)."""
+    import paper_1712_00403_gb300 as pkg
+    text = open(HEADER).read()
+    mirrors = {"fdst_desc": pkg.Desc, "fdst_sizes": pkg.Sizes, "fdst_solve_info": pkg.SolveInfo,
+               "fdst_server_opts": pkg.ServerOpts}
+    for c, py in mirrors.items():
+        body = re.search(r"typedef struct \{((?:(?!typedef struct).)*?)\}\s*" + c + r"\s*;", text, re.S).group(1)
+        body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+        names = re.findall(r"\**\s*([A-Za-z_][A-Za-z_0-9]*)\s*(?:\[[^\]]*\])*\s*;", body)
+        assert names == [n for n, _ in py._fields_], (c, names)
