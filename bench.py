@@ -138,7 +138,7 @@ class Replicas:
 
     SEED_STRIDE = 1000
 
-    def __init__(self, backend="nccl", env=None):
+    def __init__(self, backend="nccl", env=None, timeout_s=None):
         env = os.environ if env is None else env
         self.world = int(env.get("WORLD_SIZE", "1"))
         self.rank = int(env.get("RANK", "0"))
@@ -150,7 +150,12 @@ class Replicas:
         if self.world > 1:
             import torch.distributed as dist
             if not dist.is_initialized():
-                dist.init_process_group(backend)
+                if timeout_s is None:
+                    dist.init_process_group(backend)
+                else:
+                    import datetime
+                    # a collective that a departed rank never joins fails after this long
+                    dist.init_process_group(backend, timeout=datetime.timedelta(seconds=timeout_s))
             if dist.get_world_size() != self.world or dist.get_rank() != self.rank:
                 raise RuntimeError("process group (%d of %d) disagrees with RANK/WORLD_SIZE (%d of %d)" % (
                     dist.get_rank(), dist.get_world_size(), self.rank, self.world))

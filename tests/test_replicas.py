@@ -36,33 +36,57 @@ print("RESULT " + json.dumps(out), flush=True)
 """
 
 
+DEPARTING = r"""
+import sys, time
+sys.path.insert(0, sys.argv[1])
+import bench
+rep = bench.Replicas("gloo", timeout_s=20)
+rep.barrier()
+if rep.rank == 1:
+    sys.exit(0)                     # leaves between steps, with no collective in flight
+t0 = time.time()
+try:
+    rep.max(1.0)
+    print("RESULT joined", flush=True)
+except Exception as e:
+    print("RESULT raised %.1f %s" % (time.time() - t0, type(e).__name__), flush=True)
+"""
+
+
 def _free_port():
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
         return s.getsockname()[1]
 
 
-def _run_ranks(world):
+def _launch(world, script):
     port = _free_port()
     procs = []
     for r in range(world):
         env = dict(os.environ, RANK=str(r), LOCAL_RANK=str(r), WORLD_SIZE=str(world), MASTER_ADDR="127.0.0.1",
                    MASTER_PORT=str(port), CUDA_VISIBLE_DEVICES="")
-        procs.append(subprocess.Popen([sys.executable, "-c", WORKER, ROOT], env=env, stdout=subprocess.PIPE,
+        procs.append(subprocess.Popen([sys.executable, "-c", script, ROOT], env=env, stdout=subprocess.PIPE,
                                       stderr=subprocess.STDOUT, text=True))
-    outs = []
+    texts = []
     try:
         for p in procs:
             text, _ = p.communicate(timeout=240)
-            assert p.returncode == 0, text
-            line = [ln for ln in text.splitlines() if ln.startswith("RESULT ")]
-            assert line, text
-            outs.append(json.loads(line[-1][len("RESULT "):]))
+            texts.append((p.returncode, text))
     finally:
         for p in procs:
             if p.poll() is None:
                 p.kill()
                 p.wait()
+    return texts
+
+
+def _run_ranks(world):
+    outs = []
+    for rc, text in _launch(world, WORKER):
+        assert rc == 0, text
+        line = [ln for ln in text.splitlines() if ln.startswith("RESULT ")]
+        assert line, text
+        outs.append(json.loads(line[-1][len("RESULT "):]))
     return sorted(outs, key=lambda o: o["rank"])
 
 
@@ -96,3 +120,14 @@ def test_single_rank_needs_no_process_group():
     assert rep.max(2.5) == 2.5 and rep.sum(4) == 4.0 and rep.job_rate(10, 2.0) == 5.0
     rep.barrier()
     rep.close()
+
+
+def test_departed_rank_ends_the_next_collective_with_an_error():
+    """Failure detection on the host: rank 1 leaves between steps; rank 0's next
+    timing collective fails with an error (the peer's closed connection, at the latest
+    the process group's 20 s timeout) instead of waiting forever."""
+    (rc0, t0), (rc1, t1) = _launch(2, DEPARTING)
+    assert rc1 == 0, t1
+    line = [ln for ln in t0.splitlines() if ln.startswith("RESULT ")]
+    assert line and line[-1].startswith("RESULT raised"), t0
+    assert float(line[-1].split()[2]) <= 30.0
