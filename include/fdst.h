@@ -180,9 +180,12 @@ fdst_status fdst_solve(fdst_handle h, const double *d_b, double *d_x, int nrhs, 
  * -P_Q^{-1} r_q, u = P_V^{-1}(r_u - B^T q)) or P = P_C (the paper's product
  * form: z = P_V^{-1} r_u, q = -P_Q^{-1}(r_q - B z), u = z - P_V^{-1} B^T q),
  * Sec. 4; P_V^{-1}, P_Q^{-1} the handle's FD applies, B and B^T in its matvec
- * precision. Identity map only. Device vectors of nrhs block vectors; r and s
- * must not alias. Asynchronous on stream (the first call builds the B / B^T
- * plans and the GMRES work vectors).
+ * precision: Kronecker plans on the identity map, the B and B^T blocks of the
+ * assembled CSR on a mapped handle, the velocity-only / pressure-only parts of
+ * the sum-factorization plans on a matrix-free mapped handle (there P_V, P_Q
+ * are the P_D^G blocks when the handle's variant is P_D^G). Device vectors of
+ * nrhs block vectors; r and s must not alias. Asynchronous on stream (the
+ * first call builds the B / B^T plans and the GMRES work vectors).
  */
 fdst_status fdst_apply_block_prec(fdst_handle h, int prec, const double *d_r, double *d_s, int nrhs,
                                   fdst_stream stream);
@@ -191,10 +194,11 @@ fdst_status fdst_apply_block_prec(fdst_handle h, int prec, const double *d_r, do
  * fdst_solve_gmres - GMRES (Saad-Schultz) with P_T or P_C (Sec. 4; eq. P_T,
  * eq. P_C, applied through the product form of P_C^{-1}), their P_V, P_Q
  * blocks the handle's FD applies and B, B^T the Kronecker parts of the
- * operator; identity map only (FDST_NOT_SUPPORTED on mapped geometry).
+ * operator (identity map) or of the mapped operator, as fdst_apply_block_prec.
  *   form:    FDST_GMRES_LEFT, FDST_GMRES_FLEXIBLE or FDST_GMRES_AUTO (above).
  *   b, x:    device block vectors (nrhs back to back), x the initial guess in and
- *            the solution out, as fdst_solve.
+ *            the solution out, as fdst_solve; an all-zero x (the paper's start)
+ *            is detected on the device and the first residual taken as b.
  *   restart: Krylov basis size m in [1, 255]; the handle keeps a basis of
  *            (m + 1) x max_rhs block vectors (and m more for the flexible form),
  *            allocated on first use and grown when a larger m is asked for, and

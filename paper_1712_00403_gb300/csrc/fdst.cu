@@ -1389,6 +1389,13 @@ fdst_status fdst_solve_gmres(fdst_handle h, int prec, int form, const double *d_
   for (int r = 0; r < nrhs; ++r)
     if (bn[r] == 0.0) CK(cudaMemsetAsync(d_x + (size_t)r * n, 0, sizeof(double) * n, st));
   TRY(sync_done(done, h->done));
+  // x0 = 0 (the paper's start) is detected on the device: the first cycle's residual
+  // is then b itself and spares a matvec
+  launch_any_nonzero(d_x, n * nrhs, h->n_stopped, st);
+  CK(cudaMemcpyAsync(h->h_n_stopped, h->n_stopped, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  bool x_zero = *h->h_n_stopped == 0;
+  CK(cudaMemsetAsync(h->n_stopped, 0, sizeof(int), st));
   auto active = [&]() { for (int r = 0; r < nrhs; ++r) if (!done[r]) return true; return false; };
   // x_try_r = x_r + V_{0..j-1} y_r for the right-hand sides with mask[r] == 0 (into u)
   auto form_x = [&](int j, const std::vector<int> &mask) -> fdst_status {
@@ -1413,8 +1420,13 @@ fdst_status fdst_solve_gmres(fdst_handle h, int prec, int form, const double *d_
   int it = 0;
   while (active() && it < maxit) {
     // r0 = P^{-1}(b - A x) (left) or b - A x (flexible), V_0 = r0 / ||r0||
-    TRY(run_matvec(h, d_x, h->Az, nrhs, h->done, st, false));
-    launch_axpby(d_b, h->Az, 1.0, -1.0, n, n, nrhs, st);
+    if (x_zero) {
+      launch_axpby(d_b, h->Az, 1.0, 0.0, n, n, nrhs, st);
+      x_zero = false;
+    } else {
+      TRY(run_matvec(h, d_x, h->Az, nrhs, h->done, st, false));
+      launch_axpby(d_b, h->Az, 1.0, -1.0, n, n, nrhs, st);
+    }
     if (flex) launch_axpby(h->Az, w, 1.0, 0.0, n, n, nrhs, st);
     else TRY(apply_block_prec(h, prec, h->Az, w, nrhs, h->done, st));
     TRY(norms2(w, h->done));
