@@ -38,12 +38,14 @@ symmetric-gradient form and of b vs. the sum-factorized matvec (both maps);
 amplitude 0 with nu = 1 reproduces the cube operator; det J closed form vs.
 numpy.linalg.det; on the annulus the quadrature volume 3 pi / 8 and the
 moment int x1 dx = 7 sqrt(2) / 6 in closed form, and the chain rule
-J^{-T} grad_eta (f o G) = grad_x f for polynomials f; the fit reproduces an exactly separable field; on the cube
+J^{-T} grad_eta (f o G) = grad_x f for polynomials f; the fit reproduces an exactly separable field,
+and on the non-separable field a x y (plus separable terms) on an uneven tensor grid
+it reaches the closed-form sup-norm distance a (x_max - x_min)(y_max - y_min) / 4; on the cube
 P~_V = P_V and D_V = I; diag(P_V^G) = diag(A), diag(P_Q^G) = diag(Q);
 Theorem 2 spectral bounds of P_Q^{-1} Q and Theorem 1 bounds of P_V^{-1} A
-(Korn constants 1/2), on both maps. Parity unpinned: the separable fit
-on non-separable fields (no independent reference exists; the CUDA path
-runs the same algorithm).
+(Korn constants 1/2), on both maps. The fit on the mapped domains' own
+fields has no closed form: there it is pinned only through the separable
+and bilinear cases above (the CUDA path runs the same algorithm).
 """
 import numpy as np
 

@@ -62,6 +62,38 @@ def test_separable_fit_exact_on_separable_field():
     np.testing.assert_allclose(rec, c, rtol=1e-12)
 
 
+def test_separable_fit_reaches_the_closed_form_distance_on_a_bilinear_field():
+    """On a tensor grid, log c = a x y + (separable terms) is at sup-norm distance
+    exactly a (x_max - x_min)(y_max - y_min) / 4 from the sums f1 + f2 + f3: every
+    sum cancels in the alternating sum over the four corners (x_min|x_max, y_min|y_max)
+    while a x y leaves a dx dy there (the lower bound), and a (x - c_x)(y - c_y) with
+    c the grid midpoints attains it. The midrange sweeps must reach that optimum; a
+    mean in place of the midrange misses it on the uneven grid used here."""
+    rng = np.random.default_rng(3)
+    x, y, z = np.sort(rng.uniform(-1, 2, 7)), np.sort(rng.uniform(0.5, 3, 5)), rng.uniform(0, 1, 4)
+    a = 0.7
+    g = [rng.standard_normal(n) for n in (7, 5, 4)]
+    dist = a * np.ptp(x) * np.ptp(y) / 4
+    bilinear = a * x[:, None, None] * y[None, :, None]
+    cx, cy = 0.5 * (x.max() + x.min()), 0.5 * (y.max() + y.min())
+    optimal = a * (x[:, None, None] - cx) * (y[None, :, None] - cy) * np.ones((1, 1, 4))
+    for L, exact_residual in ((bilinear + g[0][:, None, None] + g[2][None, None, :], True),
+                              (bilinear + g[0][:, None, None] + g[1][None, :, None] + g[2][None, None, :], False)):
+        f = geo.separable_fit(np.exp(L))
+        R = L - f[0][:, None, None] - f[1][None, :, None] - f[2][None, None, :]
+        assert abs(np.abs(R).max() - dist) <= 1e-12 * dist
+        if exact_residual:   # separable terms only in x and z: the optimal residual itself
+            np.testing.assert_allclose(R, optimal, atol=1e-12)
+    # the same bound in the (x, z) pair
+    L = a * x[:, None, None] * z[None, None, :] + g[1][None, :, None]
+    f = geo.separable_fit(np.exp(L))
+    R = L - f[0][:, None, None] - f[1][None, :, None] - f[2][None, None, :]
+    assert abs(np.abs(R).max() - a * np.ptp(x) * np.ptp(z) / 4) <= 1e-12
+    # a mean in place of the midrange would leave a larger error on this grid
+    mean_fit = np.abs(a * (x[:, None] - x.mean()) * (y[None, :] - y.mean())).max()
+    assert mean_fit > 1.1 * dist
+
+
 def test_fit_never_increases_the_sup_error():
     S = _S(3, 2)
     G = geo.Grid(S)
