@@ -3,8 +3,9 @@ the isogeometric Stokes system (Montardini, Sangalli, Tani, arXiv 1712.00403).
 
 Thin ctypes binding over the C ABI declared in include/fdst.h: argument
 marshalling only, every step of the computation runs in the library's CUDA
-kernels. PyTorch supplies device memory and streams. Importing this package
-fails loudly when the compiled library is missing; there is no CPU fallback.
+kernels. PyTorch supplies device memory and streams. The compiled library
+is loaded on first use (Stokes, Batch, Server and the module functions), which
+raises ImportError when it is missing; there is no CPU fallback.
 """
 import ctypes
 import os
