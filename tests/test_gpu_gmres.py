@@ -108,3 +108,32 @@ def test_gmres_zero_rhs_and_lockstep():
         xj = torch.ones(P.n_total, dtype=torch.float64, device="cuda")
         i1 = one.solve_gmres(torch.tensor(B[j], device="cuda"), xj, prec=fd.PREC_PC, tol=1e-8, maxit=200)[0]
         assert abs(i1["iterations"] - info[j]["iterations"]) <= 1
+
+
+def test_zero_initial_guess_spares_the_first_matvec():
+    """x0 = 0 (the paper's start, Sec. 7) is detected on the device and the first
+    residual taken as b. An x0 with one entry of 1e-300 leaves r0 = b to the last
+    bit (its product with the operator vanishes against b's ulp, and underflows in
+    the double-float split), so both starts take the same iterations; only the
+    nonzero one pays for the first matvec's launches."""
+    import paper_1712_00403_gb300 as fd
+    spec = problem_spec(2, 2, 8)
+    P = gpu_problem(spec)
+    b = torch.tensor(synth.rhs(41, P.block_sizes), device="cuda")
+
+    def run(solve, tiny):
+        x = torch.zeros_like(b)
+        if tiny:
+            x[0] = 1e-300
+        torch.cuda.synchronize()
+        k0 = fd.kernel_launches()
+        info = solve(b, x)[0]
+        torch.cuda.synchronize()
+        return info, fd.kernel_launches() - k0
+
+    for solve in (lambda b, x: P.solve(b, x, tol=1e-8, maxit=300),
+                  lambda b, x: P.solve_gmres(b, x, prec=fd.PREC_PT, tol=1e-8, maxit=300)):
+        (iz, lz), (it, lt) = run(solve, False), run(solve, True)
+        assert iz["status"] == "OK" and it["status"] == "OK"
+        assert iz["iterations"] == it["iterations"]
+        assert lt > lz, (lz, lt)
