@@ -19,8 +19,11 @@ normal to it).
 
 Pins (tests/test_oracle_stokes.py): Kronecker blocks vs. brute-force
 element quadrature of a(.,.) and b(.,.) written from the symmetric-gradient
-definition (TH); A_kk = P_{V,k}; B^T 1 = 0 (constant pressure in the
-kernel); symmetry of the assembled operator; P_V, P_Q SPD.
+definition (TH), and for RT of a(.,.) + sigma(.,.) (the Nitsche form of
+eq. theta, face by face with outward normals) and b(.,.), all blocks A_rs
+including r != s, which pins the reading that sigma adds only to A_kk on the
+cube; A_kk = P_{V,k}; B^T 1 = 0 (constant pressure in the kernel); symmetry
+of the assembled operator; P_V, P_Q SPD.
 """
 from dataclasses import dataclass
 
@@ -351,4 +354,104 @@ def brute_force_TH(S, nu=1.0):
         for j in range(nv):
             div = grad[j][r]          # div(e_r B_j) = d_r B_j
             Bm[:, r * nv + j] = -(pval * div[None, :]) @ W
+    return A, Bm
+
+
+def _tensor_points(rules, fixed=None):
+    """Tensor-product points (N, d) and weights (N,) from per-direction rules;
+    fixed = (e, t) pins coordinate e to t and drops its weight (a face)."""
+    d = len(rules)
+    axes, wts = [], []
+    for e in range(d):
+        if fixed is not None and fixed[0] == e:
+            axes.append(np.array([float(fixed[1])]))
+            wts.append(np.array([1.0]))
+        else:
+            axes.append(rules[e][0])
+            wts.append(rules[e][1])
+    grid = np.meshgrid(*axes, indexing="ij")
+    W = np.ones_like(grid[0])
+    for e in range(d):
+        sh = [1] * d
+        sh[e] = -1
+        W = W * wts[e].reshape(sh)
+    return np.stack([g.reshape(-1) for g in grid], axis=1), W.reshape(-1)
+
+
+def _vector_basis(spaces, k, d, X):
+    """Values (n, d, N) and gradients (n, d, d, N) of every vector basis
+    function e_k B_i of component k at the points X, B_i the tensor product of
+    the component's univariate spaces (index 1 fastest); [G]_{a,b} = d_b v_a."""
+    vals, ders = [], []
+    for e in range(d):
+        s = spaces[e]
+        B, D = splines.basis(s.knots, s.degree, X[:, e])
+        vals.append(B[:, s.keep])
+        ders.append(D[:, s.keep])
+    shape = [vals[e].shape[1] for e in range(d)]
+    n = int(np.prod(shape))
+    multi = np.array(np.unravel_index(np.arange(n), shape[::-1])).T[:, ::-1]   # (n, d), index 1 fastest
+    V = np.zeros((n, d, len(X)))
+    G = np.zeros((n, d, d, len(X)))
+    for f, m in enumerate(multi):
+        V[f, k] = np.prod([vals[e][:, m[e]] for e in range(d)], axis=0)
+        for b in range(d):
+            G[f, k, b] = np.prod([(ders[e] if e == b else vals[e])[:, m[e]] for e in range(d)], axis=0)
+    return V, G
+
+
+def brute_force_RT(S, cpen, h, nu=1.0, faces=True):
+    """Dense A (with the Nitsche form) and B of the RT system on the unit
+    square / cube, written straight from the forms of Sec. 3 (eq. RT_dis):
+      a(w, v)     = int_Omega 2 nu grad^s w : grad^s v,
+      sigma(w, v) = int_dOmega 2 nu [C_pen/h w.v - ((grad^s w) n).v - ((grad^s v) n).w]   (eq. theta),
+      b(v, q)     = - int_Omega q div v,
+    with every vector basis function e_k B_i evaluated on its own, the volume
+    integrals by tensor Gauss quadrature and the boundary integral face by
+    face (outward unit normal -e_d on eta_d = 0 and +e_d on eta_d = 1) with
+    the same rule on the face's own directions. Nothing here uses the
+    univariate factors, so it pins the Kronecker blocks of A_rs for all r, s
+    (the claim that sigma adds only to A_kk included). faces=False leaves
+    sigma out (the volume form alone). Tiny sizes only."""
+    assert S.disc == "RT"
+    d = S.dim
+    npts = S.p + 2
+    rules = []
+    for e in range(d):
+        z = np.unique(np.concatenate([S.vel[k][e].knots for k in range(d)] + [S.pres[e].knots]))
+        rules.append(splines.gauss_rule(z, npts))
+    X, W = _tensor_points(rules)
+    face_rules = []
+    for e in range(d if faces else 0):
+        for t, sgn in ((0.0, -1.0), (1.0, 1.0)):
+            Xf, Wf = _tensor_points(rules, fixed=(e, t))
+            nrm = np.zeros(d)
+            nrm[e] = sgn
+            face_rules.append((Xf, Wf, nrm))
+
+    def all_vel(P):
+        Vs, Gs = zip(*[_vector_basis(S.vel[k], k, d, P) for k in range(d)])
+        V = np.concatenate(Vs)
+        G = np.concatenate(Gs)
+        return V, 0.5 * (G + G.transpose(0, 2, 1, 3)), G
+
+    V, Sg, G = all_vel(X)
+    A = np.einsum("iabp,jabp,p->ij", Sg, Sg, 2.0 * nu * W)
+    for Xf, Wf, nrm in face_rules:
+        Vf, Sf, _ = all_vel(Xf)
+        Sn = np.einsum("iabp,b->iap", Sf, nrm)                 # (grad^s v) n
+        pen = np.einsum("iap,jap,p->ij", Vf, Vf, Wf)
+        cons = np.einsum("iap,jap,p->ij", Sn, Vf, Wf)          # ((grad^s phi_i) n) . phi_j
+        A += 2.0 * nu * (cpen / h * pen - cons - cons.T)
+    # pressure basis at the volume points (all functions kept)
+    pv = []
+    for e in range(d):
+        s = S.pres[e]
+        B, _ = splines.basis(s.knots, s.degree, X[:, e])
+        pv.append(B[:, s.keep])
+    shape = [pv[e].shape[1] for e in range(d)]
+    multi = np.array(np.unravel_index(np.arange(int(np.prod(shape))), shape[::-1])).T[:, ::-1]
+    Q = np.array([np.prod([pv[e][:, m[e]] for e in range(d)], axis=0) for m in multi])
+    div = np.einsum("iaap->ip", G)
+    Bm = -np.einsum("lp,jp,p->lj", Q, div, W)
     return A, Bm

@@ -91,3 +91,121 @@ def test_max_smooth_velocity_is_not_inf_sup_stable(dim, n_el, expected):
         B = A[nv:, :nv]
         rank = np.linalg.matrix_rank(B, tol=1e-10 * np.abs(B).max())
         assert B.shape[0] - rank == want
+
+
+def _rt_constants(S):
+    """C_pen = 5(alpha + 1) (Sec. 7) with alpha the pressure regularity, h the
+    element size: read off the pressure knots, not the velocity spaces."""
+    t = S.pres[0].knots
+    z = np.unique(t)
+    alpha = S.p - int(np.sum(t == z[1]))
+    return 5.0 * (alpha + 1), float(np.max(np.diff(z)))
+
+
+def _rt_compare(S):
+    cpen, h = _rt_constants(S)
+    A_bf, B_bf = stokes.brute_force_RT(S, cpen, h)
+    A = stokes.assembled(S)
+    nv = sum(S.block_sizes[:S.dim])
+    return (np.abs(A[:nv, :nv] - A_bf).max() / np.abs(A_bf).max(),
+            np.abs(A[nv:, :nv] - B_bf).max() / np.abs(B_bf).max(),
+            np.abs(A[:nv, nv:] - B_bf.T).max() / np.abs(B_bf).max())
+
+
+@pytest.mark.parametrize("dim,p,n_el", [(2, 2, 3), (2, 3, 3), (3, 2, 2), (3, 3, 2), (2, 2, (3, 4))])
+def test_rt_blocks_vs_brute_force_nitsche_quadrature(dim, p, n_el):
+    """Every block of the RT system (A_rs for all r, s, with the Nitsche form
+    sigma of eq. theta, and B) equals an element-by-element quadrature of
+    a + sigma and b written from their definitions (Sec. 3, eq. RT_dis)."""
+    S = stokes.build_uniform(n_el, p, dim, "RT")
+    if not np.isscalar(n_el):
+        # uneven meshes: the oracle's per-direction h is that direction's span; sigma's h
+        # is one number, so compare on the common largest span
+        h = max(1.0 / n for n in n_el)
+        for k in range(dim):
+            for d in range(dim):
+                if S.vel[k][d].nitsche:
+                    S.vel[k][d].h = h
+        cpen, _ = _rt_constants(S)
+        A_bf, B_bf = stokes.brute_force_RT(S, cpen, h)
+        A = stokes.assembled(S)
+        nv = sum(S.block_sizes[:dim])
+        assert np.abs(A[:nv, :nv] - A_bf).max() <= 1e-12 * np.abs(A_bf).max()
+        assert np.abs(A[nv:, :nv] - B_bf).max() <= 1e-12 * np.abs(B_bf).max()
+        return
+    ea, eb, ebt = _rt_compare(S)
+    assert ea <= 1e-12 and eb <= 1e-12 and ebt <= 1e-12, (ea, eb, ebt)
+
+
+def _boundary_outer(sa, sb, at, db=0):
+    from oracle import splines
+    Ba, _ = splines.basis(sa.knots, sa.degree, np.array([at]))
+    Bb, Db = splines.basis(sb.knots, sb.degree, np.array([at]))
+    return np.outer(Ba[0, sa.keep], (Bb, Db)[db][0, sb.keep])
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("mistake", ["drop_nitsche", "penalty_doubled", "consistency_sign",
+                                     "nitsche_in_cross_block"])
+def test_rt_brute_force_catches_planted_mistakes(monkeypatch, dim, mistake):
+    """A mistake planted in the oracle's RT assembly (the Nitsche terms
+    dropped, a wrong penalty, a flipped consistency sign, a boundary term put
+    into a cross block A_rs) moves it away from the brute-force quadrature by
+    far more than the 1e-12 bar."""
+    from oracle import univariate as uv
+    S = stokes.build_uniform(2, 2, dim, "RT")
+    if mistake == "drop_nitsche":
+        for k in range(dim):
+            for d in range(dim):
+                S.vel[k][d].nitsche = False
+    elif mistake == "penalty_doubled":
+        for k in range(dim):
+            for d in range(dim):
+                S.vel[k][d].cpen *= 2.0
+    elif mistake == "consistency_sign":
+        orig = uv.stiffness
+
+        def flipped(s, weight=None, npts=None, tau0=1.0, tau1=1.0):
+            if not s.nitsche:
+                return orig(s, weight, npts, tau0, tau1)
+            # K~ with the consistency terms' sign flipped: K~' = 2 K - K~ + penalty twice
+            K0 = uv.mixed(s, 1, s, 1, weight, npts)
+            Kn = orig(s, weight, npts, tau0, tau1)
+            pen = 2.0 * s.cpen / s.h * (_boundary_outer(s, s, 1.0) + _boundary_outer(s, s, 0.0))
+            return 2.0 * K0 - Kn + 2.0 * pen
+        monkeypatch.setattr(uv, "stiffness", flipped)
+    elif mistake == "nitsche_in_cross_block":
+        orig_terms = stokes.a_block_terms
+
+        def moved(S_, r, s):
+            terms = orig_terms(S_, r, s)
+            if r == s:
+                return terms
+            # a consistency-type face term of direction s (value of component r's
+            # tangential factor times the normal derivative of component s's factor)
+            f = [uv.mixed(S_.vel[r][e], 0, S_.vel[s][e], 0) for e in range(S_.dim)]
+            f[s] = (_boundary_outer(S_.vel[r][s], S_.vel[s][s], 1.0, db=1)
+                    - _boundary_outer(S_.vel[r][s], S_.vel[s][s], 0.0, db=1))
+            return terms + [(S_.nu, f)]
+        monkeypatch.setattr(stokes, "a_block_terms", moved)
+    ea, _, _ = _rt_compare(S)
+    assert ea > 1e-3, (mistake, ea)
+
+
+def test_rt_nitsche_adds_nothing_to_cross_blocks_on_the_cube():
+    """The reading that sigma contributes only to A_kk on the cube: the face
+    integrals of sigma over the cross pairs (e_r B_i, e_s B_j), r != s, taken
+    alone from the brute force (a + sigma minus a), vanish."""
+    S = stokes.build_uniform(2, 2, 3, "RT")
+    cpen, h = _rt_constants(S)
+    A_full, _ = stokes.brute_force_RT(S, cpen, h)
+    A_vol, _ = stokes.brute_force_RT(S, 0.0, h, nu=1.0, faces=False)
+    sig = A_full - A_vol
+    off = np.concatenate([[0], np.cumsum(S.block_sizes[:3])])
+    for r in range(3):
+        for s in range(3):
+            blk = sig[off[r]:off[r + 1], off[s]:off[s + 1]]
+            if r == s:
+                assert np.abs(blk).max() > 0.1 * np.abs(sig).max()
+            else:
+                assert np.abs(blk).max() <= 1e-13 * np.abs(sig).max()
