@@ -10,7 +10,6 @@
 // which every GPU that loads the library holds until the process exits.
 #include <cuda_runtime.h>
 
-#include <mutex>
 #include <string>
 
 #include "internal.h"
@@ -23,34 +22,29 @@ constexpr int64_t kStaticMaxN = 2359296;   // block entries (>= 129^3)
 constexpr int kStaticMaxDim = 256;          // univariate size n_d
 constexpr int64_t kStaticDoubles =
     kStaticMaxN + 3 * (int64_t)kStaticMaxDim * kStaticMaxDim + (int64_t)kStaticMaxDim * kStaticMaxDim + kStaticMaxDim;
-constexpr int kMaxDevices = 64;
 }  // namespace
 
 // Scratch shared by every call on a device: [intermediate tensor | U_1^T U_2^T U_3^T | lam_row | lam_col].
 static __device__ __align__(256) double g_static_scratch[kStaticDoubles];
 
-static std::mutex g_static_mutex;
-static double *g_static_ptr[kMaxDevices] = {};
-
-// Device address of the scratch on the current device (looked up once per device).
+// Device address of the scratch on the current device. Looked up on every
+// call (not cached), so a context that was reset and re-created since the
+// last call gets its own address.
 static fdst_status static_scratch(double **out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-    set_error("fdst_fd_apply_static: no current CUDA device");
+  void *p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+  if (e != cudaSuccess || !p) {
+    set_error(std::string("fdst_fd_apply_static: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
     return FDST_CUDA_ERROR;
   }
-  std::lock_guard<std::mutex> lock(g_static_mutex);
-  if (!g_static_ptr[dev]) {
-    void *p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess || !p) {
-      set_error(std::string("fdst_fd_apply_static: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
-      return FDST_CUDA_ERROR;
-    }
-    g_static_ptr[dev] = static_cast<double *>(p);
-  }
-  *out = g_static_ptr[dev];
+  *out = static_cast<double *>(p);
   return FDST_OK;
+}
+
+// True when the byte ranges [a, a + na) and [b, b + nb) share a byte.
+static bool ranges_overlap(const void *a, size_t na, const void *b, size_t nb) {
+  const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+  return x < y + nb && y < x + na;
 }
 
 __global__ void k_static_transpose(const double *U, double *Ut, int n) {
@@ -86,10 +80,6 @@ extern "C" fdst_status fdst_fd_apply_static(int dim, const int n[3], const doubl
     set_error("fdst_fd_apply_static: dim must be 2 or 3");
     return FDST_INVALID_ARGUMENT;
   }
-  if (d_r == d_s) {
-    set_error("fdst_fd_apply_static: r and s alias");
-    return FDST_INVALID_ARGUMENT;
-  }
   int64_t N = 1;
   for (int d = 0; d < dim; ++d) {
     if (n[d] < 1 || n[d] > kStaticMaxDim) {
@@ -110,6 +100,15 @@ extern "C" fdst_status fdst_fd_apply_static(int dim, const int n[3], const doubl
   double *base = nullptr;
   fdst_status st = static_scratch(&base);
   if (st != FDST_OK) return st;
+  const size_t bytes = (size_t)N * sizeof(double), scratch_bytes = (size_t)kStaticDoubles * sizeof(double);
+  if (ranges_overlap(d_r, bytes, d_s, bytes)) {
+    set_error("fdst_fd_apply_static: r and s overlap");
+    return FDST_INVALID_ARGUMENT;
+  }
+  if (ranges_overlap(d_r, bytes, base, scratch_bytes) || ranges_overlap(d_s, bytes, base, scratch_bytes)) {
+    set_error("fdst_fd_apply_static: r or s lies inside the library's static scratch array");
+    return FDST_INVALID_ARGUMENT;
+  }
   cudaStream_t s = (cudaStream_t)stream;
   double *buf = base;
   double *Ut[3] = {base + kStaticMaxN, base + kStaticMaxN + (int64_t)kStaticMaxDim * kStaticMaxDim,
