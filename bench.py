@@ -62,6 +62,9 @@ def parse():
     ap.add_argument("--restart", type=int, default=60, help="GMRES Krylov basis size")
     ap.add_argument("--matrix-free", action="store_true",
                     help="mapped workloads: sum-factorized matvec in the iterations instead of the CSR SpMV")
+    ap.add_argument("--no-fp64", action="store_true",
+                    help="skip the plain-FP64 leg (FD apply and matvec in FP64) of single-problem workloads")
+    ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the plain-FP64 leg")
     ap.add_argument("--no-cpu-baseline", action="store_true",
                     help="skip the oracle timing (profiling runs of the GPU path)")
     return ap.parse_args()
@@ -272,6 +275,29 @@ def cpu_oracle_sample(w, seeds, iters_per_solve, k_iters=2, op=None):
                 seconds=dt, t_iter_s=t_iter)
 
 
+def cpu_oracle_single_thread(workload_name, iters_per_solve, k_iters=1):
+    """cpu_oracle_sample with one BLAS/OpenMP thread (the paper's setting: one
+    core), in a child process started with those limits (they bind only before
+    NumPy loads). The child execs a fresh interpreter and touches no GPU."""
+    import subprocess
+    import sys
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    code = ("import json, bench; w = bench.workload(%r); "
+            "r = bench.cpu_oracle_sample(w, w['seeds'], %r, k_iters=%d); "
+            "print(json.dumps({'value': r['value'], 'seconds': r['seconds']}))") % (
+                workload_name, float(iters_per_solve), k_iters)
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                         cwd=os.path.dirname(os.path.abspath(__file__)), timeout=600)
+    if out.returncode != 0:
+        return {"unavailable": out.stderr.strip().splitlines()[-1] if out.stderr.strip() else "child failed"}
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    return {"value": r["value"], "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": (f"{k_iters} MINRES iteration(s) of the oracle on 1 right-hand side at full size with one "
+                       f"BLAS thread ({r['seconds']:.1f} s incl. the initial matvec+apply), per-iteration time x "
+                       f"{iters_per_solve:.1f} iterations per solve")}
+
+
 def cpu_oracle_instances(specs, iters, k_iters=1, max_dof=4.0e6, count=3):
     """Oracle solves/s over a sample of independent instances: the first
     `count` instances with at most max_dof unknowns; each instance's solve time
@@ -301,10 +327,16 @@ def cpu_oracle_instances(specs, iters, k_iters=1, max_dof=4.0e6, count=3):
 
 # ------------------------------------------------------------------ reference arm (oracle on CPU)
 
-# Iterations per solve used to scale the oracle's per-iteration time when no GPU
-# run supplies them: 56 for the unit cube (P_D-MINRES, TH, p=3, the paper's cube
-# table), 60 for the others.
-REF_ITERS = {"cube_th_p3_64": 56.0}
+def oracle_full_solve(w, seed, op=None, maxit=2000):
+    """One complete oracle P_D-MINRES solve (1 right-hand side, tol 1e-8, x0 = 0)
+    on the host cores: (seconds, iterations)."""
+    import synth
+    from oracle import minres
+    S, mv, pc = op if op is not None else oracle_operator(w)
+    b = synth.rhs(seed, S.block_sizes)
+    t0 = time.perf_counter()
+    _, info = minres.minres(mv, b, pc, tol=1e-8, maxit=maxit, true_check=True)
+    return time.perf_counter() - t0, int(info["iters"])
 
 
 def run_reference(args):
@@ -313,9 +345,9 @@ def run_reference(args):
         return
     w = workload(args.workload)
     kind = w.get("kind", "single")
-    iters = REF_ITERS.get(args.workload, 60.0)
     if kind in ("batched", "serving"):
         specs = instance_specs(args.workload, w)
+        iters = 60.0
         vals, secs, cpu = [], [], None
         for k in range(args.warmup + args.steps):
             cpu = cpu_oracle_instances(specs, [iters] * len(specs), k_iters=1)
@@ -323,8 +355,13 @@ def run_reference(args):
                 vals.append(cpu["value"])
                 secs.append(1.0 / cpu["value"])
         nrhs, cfg = 1, {"workload": args.workload + ": " + w_text(args.workload, w)}
+        full = None
     else:
         op = oracle_operator(w)
+        # the iteration count the per-iteration times are scaled by is the oracle's own, from one
+        # complete solve of the first right-hand side (timed once, reported beside the steps)
+        t_full, iters = oracle_full_solve(w, w["seeds"][0], op=op)
+        full = {"seconds": t_full, "iterations": iters, "solves_per_s": 1.0 / t_full}
         vals, secs = [], []
         for k in range(args.warmup + args.steps):
             r = cpu_oracle_sample(w, w["seeds"], iters, k_iters=1, op=op)
@@ -333,7 +370,8 @@ def run_reference(args):
                 secs.append(r["t_iter_s"] * iters)
         nrhs, cfg = 1, {"workload": describe(args.workload, w, 1), "nrhs": 1}
         cpu = {"sample": "per step: 1 MINRES iteration (plus the initial matvec and apply) of the FP64 oracle at "
-                         f"full size on 1 RHS, scaled by {iters:.0f} iterations per solve"}
+                         f"full size on 1 RHS, scaled by the {iters} iterations of the oracle's own complete "
+                         f"solve of seed {w['seeds'][0]} (that solve: {t_full:.1f} s, timed once before the steps)"}
     value = statistics.median(vals)
     out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(secs), "higher_is_better": True,
@@ -341,6 +379,7 @@ def run_reference(args):
            "config": cfg,
            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
                             "sample": cpu["sample"]},
+           "oracle_full_solve": full,
            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -569,9 +608,20 @@ def run_gpu(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not gm:
-        cpu = cpu_oracle_sample(w, w["seeds"], float(np.mean(iters)), k_iters=1 if mapped else 2)
+        mean_it = float(np.mean(iters))
+        cpu = cpu_oracle_sample(w, w["seeds"], mean_it, k_iters=1 if mapped else 2)
         cpu.pop("seconds", None)
         cpu.pop("t_iter_s", None)
+        cpu["sample"] += f" (the GPU solves' mean iteration count, {mean_it:.2f})"
+        if not mapped:
+            cpu["single_thread"] = cpu_oracle_single_thread(args.workload, mean_it)
+
+    # the plain-FP64 form of the same solve (FD apply and matvec in FP64), same right-hand sides
+    fp64 = None
+    if not gm and not args.no_fp64 and not (prec == fd.FD_F64 and mv == fd.MV_F64):
+        P.close()
+        P = None
+        fp64 = fp64_leg(args, w, knots, nrhs, b, stream, geo, rep)
 
     if rank == 0:
         dtype = {fd.FD_F64: "f64", fd.FD_TF32X3: "f64+tf32x3", fd.FD_BF16X6: "f64+bf16x6"}[prec]
@@ -607,9 +657,57 @@ def run_gpu(args):
                                                       "vector": tm["ms_vector"] / max(tm["n_matvec"], 1)},
                "setup_s": t_setup, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": launches, "clocks": clocks}
+        if fp64 is not None:
+            out["fp64"] = fp64
         print(json.dumps(out), flush=True)
-    P.close()
+    if P is not None:
+        P.close()
     rep.close()
+
+
+def fp64_leg(args, w, knots, nrhs, b, stream, geo, rep):
+    """The same solve with the FD apply and the matvec in plain FP64 (the paper's
+    precision): one warm-up solve step, then args.fp64_steps timed steps on the
+    launching stream; plus the FP64 FD apply alone."""
+    import torch
+
+    import paper_1712_00403_gb300 as fd
+    P = fd.Stokes(knots, w["p"], disc=fd.TH if w["disc"] == "TH" else fd.RT, fd_precision=fd.FD_F64,
+                  max_rhs=nrhs, matvec_precision=fd.MV_F64, **geo)
+    x = torch.zeros_like(b)
+    x.zero_()
+    P.solve(b, x, tol=1e-8, maxit=args.maxit, stream=stream)
+    torch.cuda.synchronize()
+    rep.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    infos = []
+    e0.record(stream)
+    for _ in range(args.fp64_steps):
+        x.zero_()
+        infos.append(P.solve(b, x, tol=1e-8, maxit=args.maxit, stream=stream))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = rep.max(e0.elapsed_time(e1))
+    s = torch.empty_like(b)
+    P.apply_prec(b, s, stream=stream)
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(3):
+        P.apply_prec(b, s, stream=stream)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    ms_apply = a0.elapsed_time(a1) / 3
+    its = [i["iterations"] for inf in infos for i in inf]
+    out = {"value": rep.sum(args.fp64_steps * nrhs) / (ms / 1e3), "unit": "solves/s", "steps": args.fp64_steps,
+           "warmup": 1, "ms_per_step": ms / args.fp64_steps, "dtype": "f64", "fd_precision": "f64", "matvec": "FP64",
+           "minres": {"iterations_min": min(its), "iterations_max": max(its),
+                      "status": sorted(set(i["status"] for inf in infos for i in inf)),
+                      "true_rel_res_max": max(i["true_rel_res"] for inf in infos for i in inf)},
+           "fd_apply": {"ms_per_batch": ms_apply, "applies_per_s": nrhs / (ms_apply / 1e3),
+                        "gdof_per_s": nrhs / (ms_apply / 1e3) * P.n_total / 1e9},
+           "note": "same right-hand sides and stopping rule; warm-up: one full solve step"}
+    P.close()
+    return out
 
 
 # ------------------------------------------------------------------ batched workload

@@ -45,7 +45,8 @@ typedef enum {
   FDST_TIMEOUT = 8,          /* a bounded device-side wait expired */
   FDST_NAN_DETECTED = 9,     /* NaN/Inf in a MINRES inner product */
   FDST_ADMISSION_REJECTED = 10,
-  FDST_NOT_SUPPORTED = 11    /* combination of options not implemented */
+  FDST_NOT_SUPPORTED = 11,   /* combination of options not implemented */
+  FDST_CANCELLED = 12        /* a server request cancelled before it finished (fdst_server_cancel) */
 } fdst_status;
 
 enum { FDST_TH = 0, FDST_RT = 1 };                          /* discretization (Sec. 2.2) */
@@ -170,7 +171,13 @@ fdst_status fdst_matvec(fdst_handle h, const double *d_x, double *d_y, int nrhs,
  * FP64 when the estimates meet their thresholds. info: host
  * array of nrhs entries, filled when the call returns (the call synchronizes
  * the stream). Returns FDST_OK when every right-hand side converged,
- * otherwise the first non-OK per-RHS status.
+ * otherwise the first non-OK per-RHS status. Per-RHS statuses: FDST_OK,
+ * FDST_MAXIT (maxit reached), FDST_STAGNATION (the true residual stayed
+ * above tol through the restarts), FDST_BREAKDOWN (<P^-1 v, v> < 0: the
+ * preconditioner is not positive definite on a Krylov vector),
+ * FDST_NAN_DETECTED (NaN/Inf in an inner product, e.g. from a non-finite
+ * right-hand side), FDST_TIMEOUT (a bounded wait in a tensor-core kernel
+ * expired during the solve; the iterates are not trustworthy).
  */
 fdst_status fdst_solve(fdst_handle h, const double *d_b, double *d_x, int nrhs, double tol, int maxit,
                        fdst_solve_info *info, fdst_stream stream);
@@ -288,17 +295,22 @@ fdst_status fdst_convert(int kind, const void *d_in, void *d_out, int64_t n, fds
  *   d_U[d]: device, n[d] x n[d] row-major eigenvector matrix U_d (U[i][a] =
  *   component i of eigenvector a); d_lam[d]: device, n[d] eigenvalues;
  *   coef: host, dim coefficients; d_r, d_s: device, prod n[d] doubles each,
- *   vec-ordered with i1 fastest, not aliased. d_s is also used as
- *   intermediate storage during the call. Asynchronous on `stream`.
+ *   vec-ordered with i1 fastest. d_s is also used as intermediate storage
+ *   during the call. r and s must not overlap, and neither may lie inside the
+ *   static scratch array (FDST_INVALID_ARGUMENT otherwise). The library cannot
+ *   see buffer lengths: U_d, lam_d, r and s must hold the sizes above.
+ *   Asynchronous on `stream`.
  * Scratch: one file-scope __device__ array of 2359296 + 4*256*256 + 256
  * doubles (about 21 MB) that every GPU which loads the library holds until
  * the process exits. All calls on a device share it and it keeps the last
  * call's contents (every call overwrites what it reads), so calls whose
  * device work overlaps in time (different streams, threads or processes
  * sharing the context) race and must be serialized by the caller.
- * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.
+ * Every call looks up the array's device address (cudaGetSymbolAddress) on
+ * the current device instead of caching it, so the address stays right after
+ * the context is reset and re-created. The first call on a device also loads
+ * the library's device code there; make that first call before any stream
+ * capture.
  */
 fdst_status fdst_fd_apply_static(int dim, const int n[3], const double *const d_U[3], const double *const d_lam[3],
                                  const double coef[3], const double *d_r, double *d_s, fdst_stream stream);
@@ -334,6 +346,12 @@ fdst_status fdst_batch_destroy(fdst_batch b);
  * least-recently-used first), and advances every active problem by
  * iters_per_step MINRES iterations with grouped launches. Times are in the
  * caller's clock (t_arrival given at submission, `now` at each step).
+ * A request whose device handle, once set up, needs more than the whole
+ * budget can never be admitted: it finishes with FDST_ADMISSION_REJECTED.
+ * A request whose handle set-up fails finishes with that status
+ * (FDST_OUT_OF_MEMORY when a device allocation failed); the server goes on
+ * with the others. If a bounded wait in a tensor-core kernel expires during a
+ * step, every request active in that step finishes with FDST_TIMEOUT.
  */
 typedef struct {
   int64_t hbm_budget_bytes;  /* device bytes the server may hold in handles; <= 0: 90% of free memory */
@@ -356,6 +374,16 @@ fdst_status fdst_server_result(fdst_server s, int64_t id, int *finished, double 
                                double *t_arrival, double *t_admit, double *t_done);
 fdst_status fdst_server_stats(fdst_server s, int64_t *handles_created, int64_t *handles_reused,
                               int64_t *handles_evicted, int64_t *bytes_held, int *max_active_seen);
+/*
+ * fdst_server_cancel - withdraws request `id`. A queued request finishes at
+ * once with status FDST_CANCELLED (a device handle still being set up for it
+ * in the background goes to the idle cache when ready); an active one is
+ * retired at the start of the next fdst_server_step with FDST_CANCELLED, its
+ * handle returned to the idle cache. A cancelled request returns no solution
+ * (h_x of fdst_server_result is left as it is). A finished request is left
+ * as it is. FDST_INVALID_ARGUMENT for an unknown id or a NULL server.
+ */
+fdst_status fdst_server_cancel(fdst_server s, int64_t id);
 fdst_status fdst_server_destroy(fdst_server s);
 
 /* Number of CUDA kernels this library has launched in the process so far
@@ -368,6 +396,8 @@ int64_t fdst_kernel_launches(void);
  * tensor-core kernel, on a barrier nothing arrives on. *gave_up = 1 when the
  * wait expired after its limit (about 2 s) and raised its abort flag, and the
  * kernel returned; *seconds = the launch's duration. The device stays usable.
+ * Returns FDST_TIMEOUT (the status a real expiry gives) when the wait expired
+ * as designed, FDST_OK if it did not expire (the test failed);
  * FDST_INVALID_ARGUMENT for NULL outputs; synchronous.
  */
 fdst_status fdst_check_bounded_wait(int *gave_up, double *seconds);
@@ -376,6 +406,17 @@ fdst_status fdst_check_bounded_wait(int *gave_up, double *seconds);
  * (the kernel then skipped its output and returned) since the library loaded;
  * synchronizes the device. */
 fdst_status fdst_device_error(int *flag);
+
+/*
+ * fdst_inject_alloc_failure - host-side fault injection for tests: the nth
+ * device allocation the library makes for a handle from now on (nth >= 1,
+ * counted across threads) fails without calling cudaMalloc, with `status`:
+ * FDST_OUT_OF_MEMORY (as when device memory runs out) or FDST_CUDA_ERROR (as
+ * when the runtime reports another error). fdst_setup then returns that
+ * status (a server request finishes with it). nth <= 0 disarms. Nothing on
+ * the GPU is touched. FDST_INVALID_ARGUMENT for another status.
+ */
+fdst_status fdst_inject_alloc_failure(int64_t nth, int status);
 
 /* Thread-local description of the last error on this thread. */
 const char *fdst_last_error(void);

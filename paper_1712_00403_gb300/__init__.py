@@ -27,7 +27,7 @@ GMRES_LEFT, GMRES_FLEXIBLE, GMRES_AUTO = 0, 1, 2
 
 STATUS = {0: "OK", 1: "INVALID_ARGUMENT", 2: "NOT_SPD", 3: "OUT_OF_MEMORY", 4: "CUDA_ERROR", 5: "MAXIT",
           6: "STAGNATION", 7: "BREAKDOWN", 8: "TIMEOUT", 9: "NAN_DETECTED", 10: "ADMISSION_REJECTED",
-          11: "NOT_SUPPORTED"}
+          11: "NOT_SUPPORTED", 12: "CANCELLED"}
 
 
 class FdstError(RuntimeError):
@@ -67,7 +67,8 @@ ENTRY_POINTS = ["fdst_setup", "fdst_destroy", "fdst_get_sizes", "fdst_apply_prec
                 "fdst_solve_host", "fdst_solve_host_zero", "fdst_apply_prec_host", "fdst_solve_gmres", "fdst_apply_block_prec", "fdst_set_timing", "fdst_get_timing", "fdst_get_kernel_timing", "fdst_convert",
                 "fdst_fd_apply_static", "fdst_batch_create", "fdst_batch_solve", "fdst_batch_info",
                 "fdst_batch_destroy", "fdst_server_create", "fdst_server_submit", "fdst_server_step",
-                "fdst_server_result", "fdst_server_stats", "fdst_server_destroy", "fdst_check_bounded_wait", "fdst_device_error",
+                "fdst_server_result", "fdst_server_stats", "fdst_server_cancel", "fdst_server_destroy",
+                "fdst_check_bounded_wait", "fdst_device_error", "fdst_inject_alloc_failure",
                 "fdst_kernel_launches", "fdst_last_error"]
 
 _lib = None
@@ -108,6 +109,8 @@ def load_library(path=LIB_PATH):
     lib.fdst_server_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64),
                                       ctypes.POINTER(i64), ctypes.POINTER(i)]
     lib.fdst_server_destroy.argtypes = [vp]
+    lib.fdst_server_cancel.argtypes = [vp, i64]
+    lib.fdst_inject_alloc_failure.argtypes = [i64, i]
     lib.fdst_fd_apply_static.argtypes = [i, ctypes.POINTER(i), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                          ctypes.POINTER(d), vp, vp, vp]
     lib.fdst_get_timing.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d),
@@ -137,14 +140,39 @@ def fd_apply_static(U, lam, coef, r, s, stream=None):
     r, s: CUDA float64 vectors of prod(n_d) entries (i1 fastest). For callers
     that cannot allocate device memory; see include/fdst.h for the scratch
     limits and the rule that overlapping calls race.
+
+    The C entry point cannot see buffer lengths, so every size is checked
+    here before the call: ValueError for a dimension outside {2, 3}, unequal
+    list lengths, a non-square U_d, a lam_d, r or s of the wrong length;
+    TypeError for a tensor that is not a contiguous float64 CUDA tensor.
     """
-    lib = load_library()
     dim = len(U)
-    n = (ctypes.c_int * 3)(*[int(u.shape[0]) for u in U], *([1] * (3 - dim)))
-    up = (ctypes.c_void_p * 3)(*[_dptr(u).value for u in U], *([None] * (3 - dim)))
-    lp = (ctypes.c_void_p * 3)(*[_dptr(l).value for l in lam], *([None] * (3 - dim)))
+    if dim not in (2, 3):
+        raise ValueError(f"fd_apply_static: 2 or 3 directions, got {dim}")
+    if len(lam) != dim or len(coef) != dim:
+        raise ValueError(f"fd_apply_static: {dim} factors need {dim} eigenvalue vectors and {dim} coefficients, "
+                         f"got {len(lam)} and {len(coef)}")
+    n = []
+    for d in range(dim):
+        if U[d].dim() != 2 or U[d].shape[0] != U[d].shape[1]:
+            raise ValueError(f"fd_apply_static: U_{d + 1} must be square, got shape {tuple(U[d].shape)}")
+        n.append(int(U[d].shape[0]))
+        if lam[d].numel() != n[d]:
+            raise ValueError(f"fd_apply_static: lam_{d + 1} has {lam[d].numel()} entries, U_{d + 1} is {n[d]} x {n[d]}")
+    N = 1
+    for v in n:
+        N *= v
+    for name, t in (("r", r), ("s", s)):
+        if t.numel() != N:
+            raise ValueError(f"fd_apply_static: {name} has {t.numel()} entries, the block has {N}")
+    ptrs = [_dptr(t).value for t in (*U, *lam, r, s)]
+    lib = load_library()
+    nn = (ctypes.c_int * 3)(*n, *([1] * (3 - dim)))
+    up = (ctypes.c_void_p * 3)(*ptrs[:dim], *([None] * (3 - dim)))
+    lp = (ctypes.c_void_p * 3)(*ptrs[dim:2 * dim], *([None] * (3 - dim)))
     cf = (ctypes.c_double * 3)(*[float(c) for c in coef], *([0.0] * (3 - dim)))
-    _check(lib.fdst_fd_apply_static(dim, n, up, lp, cf, _dptr(r), _dptr(s), _stream_ptr(stream)))
+    _check(lib.fdst_fd_apply_static(dim, nn, up, lp, cf, ctypes.c_void_p(ptrs[-2]), ctypes.c_void_p(ptrs[-1]),
+                                    _stream_ptr(stream)))
 
 
 CONVERT_F64_TO_F32, CONVERT_F64_TO_DF, CONVERT_DF_TO_F64, CONVERT_F32_TO_F64 = 0, 1, 2, 3
@@ -166,10 +194,20 @@ def convert(kind, src, dst, stream=None):
 
 
 def check_bounded_wait():
-    """Failure-detection self-test (fdst_check_bounded_wait): (gave_up, seconds)."""
+    """Failure-detection self-test (fdst_check_bounded_wait): (status, gave_up,
+    seconds); status is "TIMEOUT" when the wait expired as designed."""
     g, t = ctypes.c_int(), ctypes.c_double()
-    _check(load_library().fdst_check_bounded_wait(ctypes.byref(g), ctypes.byref(t)))
-    return bool(g.value), t.value
+    code = load_library().fdst_check_bounded_wait(ctypes.byref(g), ctypes.byref(t))
+    if code not in (0, 8):
+        _check(code)
+    return STATUS[code], bool(g.value), t.value
+
+
+def inject_alloc_failure(nth, status=3):
+    """Host-side fault injection (fdst_inject_alloc_failure): the nth device
+    allocation of a handle from now on fails with status (3 OUT_OF_MEMORY or
+    4 CUDA_ERROR) without touching the GPU; nth <= 0 disarms."""
+    _check(load_library().fdst_inject_alloc_failure(int(nth), int(status)))
 
 
 def device_error():
@@ -418,6 +456,10 @@ class Server:
             return None
         return dict(x=x, iterations=info.iterations, status=STATUS.get(info.status, info.status),
                     true_rel_res=info.true_rel_res, t_arrival=ta.value, t_admit=tm.value, t_done=td.value)
+
+    def cancel(self, rid):
+        """Withdraw a request: a queued one finishes at once, an active one at the next step (CANCELLED)."""
+        _check(_lib.fdst_server_cancel(self._s, rid))
 
     def stats(self):
         c, r, e, b = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()

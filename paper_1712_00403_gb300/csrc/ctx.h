@@ -161,10 +161,20 @@ struct fdst_ctx {
 
 namespace fdst {
 
+// Host-side allocation-failure injection (fdst_inject_alloc_failure): the
+// status this allocation must fail with, or FDST_OK when it is not the one
+// armed to fail.
+fdst_status injected_alloc_failure();
+
 template <typename T>
 inline fdst_status dalloc(fdst_ctx *h, T **p, size_t count) {
   *p = nullptr;
   if (count == 0) count = 1;
+  if (const fdst_status inj = injected_alloc_failure()) {
+    set_error(inj == FDST_OUT_OF_MEMORY ? "cudaMalloc: out of memory (injected by fdst_inject_alloc_failure)"
+                                        : "cudaMalloc: CUDA error (injected by fdst_inject_alloc_failure)");
+    return inj;
+  }
   cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
   if (e != cudaSuccess) {
     set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));

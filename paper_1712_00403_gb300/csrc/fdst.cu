@@ -5,6 +5,8 @@
 // and the multi-right-hand-side MINRES driver (Sec. 4, Sec. 7).
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -1137,7 +1139,38 @@ fdst_status fdst_convert(int kind, const void *d_in, void *d_out, int64_t n, fds
 
 fdst_status fdst_check_bounded_wait(int *gave_up, double *seconds) {
   if (!gave_up || !seconds) { set_error("NULL argument"); return FDST_INVALID_ARGUMENT; }
-  return tc_wait_selftest(gave_up, seconds);
+  TRY(tc_wait_selftest(gave_up, seconds));
+  if (*gave_up) {
+    set_error("bounded device-side wait expired (self-test: expected)");
+    return FDST_TIMEOUT;
+  }
+  return FDST_OK;
+}
+
+}  // extern "C"
+
+namespace fdst {
+static std::atomic<int64_t> g_alloc_countdown{0};
+static std::atomic<int> g_alloc_status{FDST_OUT_OF_MEMORY};
+
+fdst_status injected_alloc_failure() {
+  int64_t c = g_alloc_countdown.load();
+  while (c > 0)
+    if (g_alloc_countdown.compare_exchange_weak(c, c - 1)) return c == 1 ? (fdst_status)g_alloc_status.load() : FDST_OK;
+  return FDST_OK;
+}
+}  // namespace fdst
+
+extern "C" {
+
+fdst_status fdst_inject_alloc_failure(int64_t nth, int status) {
+  if (status != FDST_OUT_OF_MEMORY && status != FDST_CUDA_ERROR) {
+    set_error("fdst_inject_alloc_failure: status must be FDST_OUT_OF_MEMORY or FDST_CUDA_ERROR");
+    return FDST_INVALID_ARGUMENT;
+  }
+  fdst::g_alloc_status.store(status);
+  fdst::g_alloc_countdown.store(nth > 0 ? nth : 0);
+  return FDST_OK;
 }
 
 fdst_status fdst_device_error(int *flag) {
@@ -1338,6 +1371,18 @@ fdst_status fdst_apply_block_prec(fdst_handle h, int prec, const double *d_r, do
     return FDST_INVALID_ARGUMENT; }
   TRY(ensure_gmres(h, 1, false));
   return apply_block_prec(h, prec, d_r, d_s, nrhs, nullptr, (cudaStream_t)stream);
+}
+
+// A bounded wait inside a tensor-core contraction that expired during a solve
+// (the kernel then skipped its output) makes every right-hand side of the solve
+// FDST_TIMEOUT: its iterates are not trustworthy.
+static fdst_status timeout_check(int err0, fdst_solve_info *info, int nrhs, fdst_status ret) {
+  int err1 = err0;
+  TRY(tc_error_count(&err1));
+  if (err1 == err0) return ret;
+  for (int j = 0; j < nrhs; ++j) info[j].status = FDST_TIMEOUT;
+  set_error("a bounded device-side wait in the tensor-core FD contraction expired during the solve");
+  return FDST_TIMEOUT;
 }
 
 fdst_status fdst_solve_gmres(fdst_handle h, int prec, int form, const double *d_b, double *d_x, int nrhs,
@@ -1549,6 +1594,8 @@ fdst_status fdst_solve(fdst_handle h, const double *d_b, double *d_x, int nrhs, 
   if (!(tol >= 0.0) || maxit < 1) { set_error("tol must be >= 0 and maxit >= 1"); return FDST_INVALID_ARGUMENT; }
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t n = h->n_total;
+  int tc_err0 = 0;
+  TRY(tc_error_count(&tc_err0));
   // timing events: (matvec, prec, vector) per phase
   std::vector<cudaEvent_t> ev;
   auto mark = [&](void) -> cudaEvent_t {
@@ -1694,7 +1741,7 @@ fdst_status fdst_solve(fdst_handle h, const double *d_b, double *d_x, int nrhs, 
     info[j].iterations_estimate = est_iters[j] >= 0 ? est_iters[j] : hs[j].iters;
     if (ret == FDST_OK && info[j].status != FDST_OK) ret = (fdst_status)info[j].status;
   }
-  return ret;
+  return timeout_check(tc_err0, info, nrhs, ret);
 }
 
 static fdst_status ensure_host_buffers(fdst_handle h) {

@@ -645,7 +645,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     __syncwarp();
   }
-  if (*abort && tid == 0) atomicExch(err, 1);
+  if (*abort && tid == 0) atomicAdd(err, 1);
   tc_fence_before();
   __syncthreads();
   if (warp == kMmaWarp) {
@@ -841,13 +841,20 @@ fdst_status tc_wait_selftest(int *gave_up, double *seconds) {
   return FDST_OK;
 }
 
-fdst_status tc_error_flag(int *value) {
+fdst_status tc_error_count(int *value) {
   *value = 0;
   if (!g_err_flag) return FDST_OK;
   if (cudaMemcpy(value, g_err_flag, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
     set_error("reading the tensor-core error flag failed");
     return FDST_CUDA_ERROR;
   }
+  return FDST_OK;
+}
+
+fdst_status tc_error_flag(int *value) {
+  const fdst_status st = tc_error_count(value);
+  if (st != FDST_OK) return st;
+  *value = *value > 0 ? 1 : 0;
   return FDST_OK;
 }
 

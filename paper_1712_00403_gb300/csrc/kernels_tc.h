@@ -78,6 +78,9 @@ size_t tc_packed_bytes(int K, int N, int split);
 void tc_pack(const double *B, int K, int N, int split, std::vector<uint8_t> &out);
 // 1 when a bounded wait inside the tensor-core kernel expired since start.
 fdst_status tc_error_flag(int *value);
+// How many tensor-core CTAs gave up on an expired bounded wait since start
+// (read synchronously; compare two readings to see whether a span of work had one).
+fdst_status tc_error_count(int *value);
 // Runs the bounded-wait self-test kernel: *gave_up = 1 when the wait expired and
 // reported it; *seconds = its duration.
 fdst_status tc_wait_selftest(int *gave_up, double *seconds);

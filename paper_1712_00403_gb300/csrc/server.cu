@@ -27,6 +27,7 @@
 
 #include "batch.h"
 #include "ctx.h"
+#include "kernels_tc.h"
 
 using namespace fdst;
 
@@ -49,6 +50,7 @@ struct Req {
   double prev_true = -1.0;   // true residual at the previous check of a stopped recurrence
   int restarts = 0;
   int est_iters = -1;        // iteration at which the estimate first met tol
+  bool cancel_pending = false;   // active and cancelled: retired at the next step
 };
 
 std::string problem_key(const fdst_desc &d, const std::vector<double> *knots) {
@@ -106,6 +108,9 @@ struct fdst_server_ctx {
   int64_t created = 0, reused = 0, finished = 0, evicted = 0;
   int max_active_seen = 0;
   int device = 0, preparing = 0;
+  std::vector<int64_t> orphans;   // cancelled while their handle was being set up
+  double last_now = 0.0;
+  int tc_err = 0;                 // expired tensor-core waits seen so far
   static constexpr int kMaxPrepare = 8;   // handles set up concurrently on host threads
 };
 
@@ -122,6 +127,18 @@ void evict_one(fdst_server s) {
   fdst_destroy(e.second);
   s->idle.pop_back();
   ++s->evicted;
+}
+
+// Retires an active request without a solution (cancelled, or its step's
+// tensor-core work gave up on an expired wait).
+void retire(fdst_server s, Req &r, int status, double now) {
+  r.info = fdst_solve_info{};
+  r.info.status = status;
+  r.info.true_rel_res = -1.0;
+  r.t_done = now;
+  r.state = 2;
+  ++s->finished;
+  release(s, r);
 }
 
 fdst_status finish(fdst_server s, Req &r, const MinresState &S, double true_rel, double now) {
@@ -153,6 +170,10 @@ fdst_status fdst_server_create(const fdst_server_opts *o, fdst_server *out) {
   fdst_server s = new fdst_server_ctx();
   s->o = *o;
   cudaGetDevice(&s->device);
+  if (tc_error_count(&s->tc_err) != FDST_OK) {
+    delete s;
+    return FDST_CUDA_ERROR;
+  }
   if (s->o.hbm_budget_bytes <= 0) {
     size_t fr = 0, tot = 0;
     cudaMemGetInfo(&fr, &tot);
@@ -216,7 +237,49 @@ fdst_status fdst_server_submit(fdst_server s, const fdst_desc *problem, const do
 fdst_status fdst_server_step(fdst_server s, double now, int *n_active, int *n_queued, int64_t *n_finished) {
   if (!s) { set_error("NULL server"); return FDST_INVALID_ARGUMENT; }
   cudaStream_t st = s->st;
+  s->last_now = now;
+  // ---- (0a) requests cancelled while their handle was being set up: the handle joins the idle cache
+  for (auto it = s->orphans.begin(); it != s->orphans.end();) {
+    Req &r = s->reqs[*it];
+    if (r.prep.wait_for(std::chrono::seconds(0)) != std::future_status::ready) { ++it; continue; }
+    fdst_ctx *h = r.prep.get();
+    r.preparing = false;
+    --s->preparing;
+    s->bytes_held -= (int64_t)r.bb;
+    if (h) {
+      s->bytes_held += h->device_bytes;
+      ++s->created;
+      s->idle.emplace_front(r.key, h);
+    }
+    it = s->orphans.erase(it);
+  }
+  // ---- (0b) active requests cancelled since the last step retire (their device work is ordered on st)
+  {
+    std::vector<int64_t> keep;
+    for (int64_t id : s->active) {
+      Req &r = s->reqs[id];
+      if (r.cancel_pending) retire(s, r, FDST_CANCELLED, now);
+      else keep.push_back(id);
+    }
+    if (keep.size() != s->active.size()) {
+      s->active.swap(keep);
+      s->dirty = true;
+    }
+  }
   // ---- (1) stopped recurrences: true residual, finish or continue
+  if (!s->active.empty()) {
+    CK(cudaStreamSynchronize(st));
+    int err = 0;
+    TRY(tc_error_count(&err));
+    if (err != s->tc_err) {
+      // a tensor-core wait expired in the last step: none of its results can be trusted
+      s->tc_err = err;
+      for (int64_t id : s->active) retire(s, s->reqs[id], FDST_TIMEOUT, now);
+      s->active.clear();
+      s->dirty = true;
+      set_error("fdst_server_step: a bounded device-side wait expired; the active requests finished with FDST_TIMEOUT");
+    }
+  }
   if (!s->active.empty()) {
     const size_t na = s->active.size();
     std::vector<MinresState> S(na);
@@ -350,8 +413,18 @@ fdst_status fdst_server_step(fdst_server s, double now, int *n_active, int *n_qu
         qit = s->queue.erase(qit);
         continue;
       }
-      s->bytes_held += h->device_bytes;
       s->bytes_per_dof[r.desc.dim] = (double)h->device_bytes / (double)h->n_total;
+      if (h->device_bytes > s->o.hbm_budget_bytes) {
+        // this problem alone needs more than the whole budget: it can never be admitted
+        fdst_destroy(h);
+        r.info.status = FDST_ADMISSION_REJECTED;
+        r.state = 2;
+        r.t_done = now;
+        ++s->finished;
+        qit = s->queue.erase(qit);
+        continue;
+      }
+      s->bytes_held += h->device_bytes;
       ++s->created;
     }
     if (!h) { ++qit; continue; }
@@ -406,6 +479,31 @@ fdst_status fdst_server_result(fdst_server s, int64_t id, int *finished, double 
     if (info) *info = r.info;
     if (h_x && !r.x.empty()) std::copy(r.x.begin(), r.x.end(), h_x);
   }
+  return FDST_OK;
+}
+
+fdst_status fdst_server_cancel(fdst_server s, int64_t id) {
+  if (!s) { set_error("NULL server"); return FDST_INVALID_ARGUMENT; }
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) { set_error("fdst_server_cancel: unknown request id"); return FDST_INVALID_ARGUMENT; }
+  Req &r = it->second;
+  if (r.state == 2) return FDST_OK;
+  if (r.state == 1) {
+    r.cancel_pending = true;
+    return FDST_OK;
+  }
+  for (auto q = s->queue.begin(); q != s->queue.end(); ++q)
+    if (*q == id) {
+      s->queue.erase(q);
+      break;
+    }
+  if (r.preparing) s->orphans.push_back(id);
+  r.info = fdst_solve_info{};
+  r.info.status = FDST_CANCELLED;
+  r.info.true_rel_res = -1.0;
+  r.t_done = s->last_now > r.t_arrival ? s->last_now : r.t_arrival;
+  r.state = 2;
+  ++s->finished;
   return FDST_OK;
 }
 

@@ -16,8 +16,8 @@ torch = pytest.importorskip("torch")
 
 def test_bounded_wait_expires_and_device_stays_usable():
     import paper_1712_00403_gb300 as fd
-    gave_up, seconds = fd.check_bounded_wait()
-    assert gave_up
+    status, gave_up, seconds = fd.check_bounded_wait()
+    assert status == "TIMEOUT" and gave_up
     assert 1.5 <= seconds <= 20.0
     assert fd.device_error() == 0          # the contraction kernel's flag is untouched
     P = gpu_problem(problem_spec(2, 2, 8), fd_precision=fd.FD_TF32X3)

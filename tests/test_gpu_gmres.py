@@ -11,7 +11,7 @@ import pytest
 import synth
 from oracle import gmres, stokes
 
-from _helpers import gpu_problem, oracle_problem, problem_spec, rel
+from _helpers import gpu_problem, oracle_problem, problem_spec, max_rel
 
 pytestmark = pytest.mark.gpu
 
@@ -40,7 +40,7 @@ def test_block_prec_apply_matches_oracle(spec, which):
     for j in range(2):
         ref = ref_fn(S, R[j])
         for o0, o1 in zip(P.block_offsets[:-1], P.block_offsets[1:]):
-            assert rel(out[j, o0:o1], ref[o0:o1]) <= 1e-12
+            assert max_rel(out[j, o0:o1], ref[o0:o1]) <= 1e-12
 
 
 @pytest.mark.parametrize("spec", [problem_spec(2, 2, 12), problem_spec(3, 2, 4), problem_spec(2, 2, 6, "RT")],
@@ -70,7 +70,7 @@ def test_gmres_matches_oracle(spec, which, flexible):
         # the same velocity as the oracle's to the accuracy the tolerance allows (the
         # pressure is defined up to a constant)
         nv = P.block_offsets[-2]
-        assert rel(X[j, :nv], xo[:nv]) <= 1e-5
+        assert max_rel(X[j, :nv], xo[:nv]) <= 1e-5
 
 
 def test_gmres_mixed_precision_and_restart():

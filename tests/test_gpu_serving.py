@@ -1,6 +1,7 @@
 """Request server (fdst_server_*): requests that arrive while others are on
 the GPU join between steps; every result equals the problem's solve alone
-(iterations within one, solution within 1e-7 relative, true residual <= 1e-8);
+(iterations within one, solution within 1e-7 relative, true residual <= 1e-8,
+and the true residual under the oracle's FP64 operator <= 1e-8 as well);
 the active-slot limit and the HBM budget hold; idle device handles are reused
 for repeated problem shapes."""
 import numpy as np
@@ -8,7 +9,7 @@ import pytest
 
 import synth
 
-from _helpers import knots_of, problem_spec, rel
+from _helpers import knots_of, problem_spec, max_rel
 
 pytestmark = pytest.mark.gpu
 
@@ -65,21 +66,32 @@ def test_results_same_alone_and_in_the_mix():
         assert r["t_done"] >= r["t_admit"] >= r["t_arrival"]
         x1, info = _alone(spec, b, fd)
         assert abs(r["iterations"] - info["iterations"]) <= 1
-        assert rel(r["x"], x1) <= 1e-7
+        assert max_rel(r["x"], x1) <= 1e-7
+        # the served solution solves the oracle's FP64 system
+        S = _s.build(knots_of(spec), spec["p"], spec["disc"])
+        res = np.linalg.norm(b - _s.matvec(S, r["x"])) / np.linalg.norm(b)
+        assert res <= 1e-8, (spec, res)
     server.close()
 
 
 def test_hbm_budget_limits_admission():
+    """A budget of one and a half handles of a shape admits one request of that
+    shape at a time (the idle handle is reused; a second one does not fit)."""
     import paper_1712_00403_gb300 as fd
-    reqs = []
     from oracle import stokes as _s
-    for k, spec in enumerate(MIX[:4]):
-        sizes = _s.build([synth.open_uniform_knots(nn, spec["p"]) for nn in spec["n_el"]], spec["p"],
-                         spec["disc"]).block_sizes
-        reqs.append((spec, synth.rhs(700 + k, sizes)))
-    server = fd.Server(max_active=8, hbm_budget_bytes=1, iters_per_step=4, tol=1e-8, maxit=800)
+    spec = MIX[0]
+    sizes = _s.build([synth.open_uniform_knots(nn, spec["p"]) for nn in spec["n_el"]], spec["p"],
+                     spec["disc"]).block_sizes
+    reqs = [(spec, synth.rhs(700 + k, sizes)) for k in range(4)]
+    probe = fd.Server(max_active=8, iters_per_step=4, tol=1e-8, maxit=800)
+    _run(probe, reqs[:1])
+    one = probe.stats()["bytes_held"]          # one idle handle of this shape
+    probe.close()
+    assert one > 0
+    server = fd.Server(max_active=8, hbm_budget_bytes=one + one // 2, iters_per_step=4, tol=1e-8, maxit=800)
     ids, max_active = _run(server, reqs, arrive_every=0)
-    assert max_active == 1                   # a budget of one byte admits one problem at a time
+    assert max_active == 1
+    assert server.stats()["handles_created"] == 1
     for rid in ids:
         r = server.result(rid)
         assert r["status"] == "OK" and r["true_rel_res"] <= 1e-8
