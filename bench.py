@@ -617,6 +617,7 @@ def run_gpu(args):
             cpu["single_thread"] = cpu_oracle_single_thread(args.workload, mean_it)
 
     # the plain-FP64 form of the same solve (FD apply and matvec in FP64), same right-hand sides
+    dev_bytes, flops_mv, n_tot = P.device_bytes, P.flops_matvec, P.n_total
     fp64 = None
     if not gm and not args.no_fp64 and not (prec == fd.FD_F64 and mv == fd.MV_F64):
         P.close()
@@ -631,7 +632,7 @@ def run_gpu(args):
                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": dtype, "data": "synthetic",
                "config": {"workload": describe(args.workload, w, nrhs, mfree), "nrhs_per_gpu": nrhs,
-                          "device_bytes": P.device_bytes,
+                          "device_bytes": dev_bytes,
                           "solver": ("P_D-MINRES" if not gm else "%s-GMRES (%s form, Krylov basis %d)" % (
                               "P_C" if args.solver == "gmres-pc" else "P_T",
                               "left" if prec == fd.FD_F64 else "flexible", args.restart)),
@@ -639,19 +640,19 @@ def run_gpu(args):
                           "matvec": (("double-float (FP32 pairs, 48-bit significand) %s in the iterations; "
                                       "true residual in FP64") % (
                                           "sum-factorized matrix-free operator" if mfree else
-                                          "CSR SpMV (%d nonzeros)" % int(P.flops_matvec / 2)
+                                          "CSR SpMV (%d nonzeros)" % int(flops_mv / 2)
                                           if mapped else "banded Kronecker products"))
                                     if mv == fd.MV_DF64 else
-                                    ("FP64 CSR SpMV (%d nonzeros)" % int(P.flops_matvec / 2) if mapped else "FP64"),
-                          "n_total": P.n_total,
+                                    ("FP64 CSR SpMV (%d nonzeros)" % int(flops_mv / 2) if mapped else "FP64"),
+                          "n_total": n_tot,
                           "l2": "inputs larger than L2 (each step streams %d x %.0f MB vectors)" % (
-                              nrhs, P.n_total * 8 / 1e6),
+                              nrhs, n_tot * 8 / 1e6),
                           "parallelism": rep.parallelism},
                ("gmres" if gm else "minres"): {
                    "iterations_min": min(iters), "iterations_max": max(iters), "status": statuses,
                    "true_rel_res_max": true_res,
                    "iterations_estimate_min": min(iters_est), "iterations_estimate_max": max(iters_est)},
-               "fd_apply": {"applies_per_s": applies_per_s, "gdof_per_s": applies_per_s * P.n_total / 1e9,
+               "fd_apply": {"applies_per_s": applies_per_s, "gdof_per_s": applies_per_s * n_tot / 1e9,
                             "ms_per_batch": ms_apply, "rel_err_vs_f64": apply_err},
                "phases_ms_per_iter": None if gm else {"matvec": per_mv, "prec": per_pc,
                                                       "vector": tm["ms_vector"] / max(tm["n_matvec"], 1)},

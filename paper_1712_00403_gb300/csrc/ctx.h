@@ -222,6 +222,12 @@ fdst_status run_matvec(fdst_ctx *h, const double *x, double *y, int nrhs, const 
 // kMaxRestarts times before the solve is reported as stagnated.
 enum { kKeepStopped = 0, kResume = 1, kRestart = 2, kStagnated = 3 };
 constexpr int kMaxRestarts = 8;
+// Lowest estimate threshold |eta_j| / |eta_0| the MINRES recurrence is asked to
+// reach: below about this the recurrence runs on rounding noise (its Lanczos
+// vectors are divided by tiny beta) and the iterate can be driven away from the
+// solution. A check that would need a lower threshold restarts from the current
+// iterate instead, and a tolerance below reach ends in FDST_STAGNATION.
+constexpr double kTauFloor = 1e-14;
 int resume_action(const MinresState &S, double true_rel, double prev_true, int restarts, double tol, int maxit);
 
 // Restarts MINRES for the right-hand sides listed in `which` from the current

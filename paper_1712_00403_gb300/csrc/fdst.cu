@@ -872,7 +872,7 @@ static fdst_status run_matvec_mf(fdst_ctx *h, const double *x, double *y, int nr
 
 int resume_action(const MinresState &S, double true_rel, double prev_true, int restarts, double tol, int maxit) {
   if (!(S.status == 0 && S.stop && S.gamma > 0.0 && true_rel > tol && S.iters < maxit)) return kKeepStopped;
-  if (prev_true < 0.0) return kResume;
+  if (prev_true < 0.0 && 0.5 * S.tau * tol / true_rel >= kTauFloor) return kResume;
   return restarts < kMaxRestarts ? kRestart : kStagnated;
 }
 
@@ -905,7 +905,7 @@ fdst_status minres_restart(fdst_ctx *h, const double *b, double *x, int nrhs, co
     S.s = S.s_old = 0.0;
     S.eta = gamma;
     S.inv_gamma_new = 1.0 / gamma;
-    S.tau = 0.5 * (S.eta0 > 0.0 ? gamma / S.eta0 : 1.0) * tol / true_rel[j];
+    S.tau = std::max(kTauFloor, 0.5 * (S.eta0 > 0.0 ? gamma / S.eta0 : 1.0) * tol / true_rel[j]);
     S.stop = 0;
     S.status = 0;
   }

@@ -568,7 +568,7 @@ __global__ void k_minres_init(MinresState *st, const double *g, int *done, int n
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nrhs) return;
   MinresState S = {};
-  S.tau = tol;
+  S.tau = tol > 1e-14 ? tol : 1e-14;   // the recurrence's floor (kTauFloor)
   double g2 = g[j];
   S.iters = 0;
   S.status = 0;

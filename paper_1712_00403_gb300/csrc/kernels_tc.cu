@@ -5,7 +5,7 @@
 //
 // A is the tensor being contracted (its contracted index is the fastest, see
 // kernels.h), B a univariate factor U_d, U_d^T or M_d^{-1}. Both operands are
-// split into TF32 pairs x = x_hi + x_lo and the three leading products
+// split into TF32 pairs x = x_hi + x_lo (both rounded to nearest) and the three leading products
 // A_hi B_hi + A_hi B_lo + A_lo B_hi accumulate in FP32 in tensor memory.
 //
 // Persistent, warp-specialized kernel (one CTA per SM, 18 warps). A tile is
@@ -14,10 +14,14 @@
 //   * warp 17 (lane 0) issues, per stage, one TMA tensor load of A (box 32
 //     FP32 columns x 128 rows, SWIZZLE_128B K-major, straight into the
 //     operand image's hi half; rows and columns past the tensor read as
-//     zero) and one bulk async copy of the stage's B image
+//     zero) and, when B streams, one bulk async copy of the stage's B image
 //     (pre-split and pre-swizzled on the host, SWIZZLE_32B K-major), all on
 //     one mbarrier transaction count, as soon as the MMA has released the
-//     slot;
+//     slot. When the B image of a (problem, column tile) fits beside two A
+//     stages it stays resident instead: it is copied once into its own
+//     region and again only when the CTA's next tile needs another B (after
+//     every MMA issued so far has completed); tiles are ordered row tile
+//     fastest, then right-hand side, so a CTA keeps one B for long runs;
 //   * warps 0-7 split the landed FP32 tile in place into TF32 hi (kept where
 //     it landed) and lo (written to the lo half at the same offsets) with
 //     conflict-free 16-byte shared-memory accesses;
@@ -38,6 +42,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include <cstdint>
@@ -107,10 +112,14 @@ static inline void bf16_split3_host(float x, uint16_t &b0, uint16_t &b1, uint16_
   b2 = (uint16_t)(w >> 16);
 }
 
-static inline float tf32_trunc(float x) {
+// Nearest TF32 value of a float (10 stored mantissa bits; ties away from zero),
+// on the encoding: adding half a TF32 ulp to the magnitude bits and clearing
+// the 13 low bits rounds the magnitude to nearest (a carry moves into the
+// exponent as it should).
+static inline float tf32_rn(float x) {
   uint32_t u;
   std::memcpy(&u, &x, 4);
-  u &= 0xFFFFE000u;
+  u = (u + 0x1000u) & 0xFFFFE000u;
   std::memcpy(&x, &u, 4);
   return x;
 }
@@ -144,8 +153,8 @@ void tc_pack(const double *B, int K, int N, int split, std::vector<uint8_t> &out
                 bf16_split3_host((float)v, b[0], b[1], b[2]);
                 std::memcpy(dst, &b[part], 2);
               } else {
-                const float hi = tf32_trunc((float)v);
-                const float lo = (float)(v - (double)hi);
+                const float hi = tf32_rn((float)v);
+                const float lo = tf32_rn((float)(v - (double)hi));
                 std::memcpy(dst, part ? &lo : &hi, 4);
               }
             }
@@ -334,6 +343,9 @@ __device__ __forceinline__ void bf16_split3x8(const float (&x)[8], uint4 &p0, ui
   p2 = make_uint4(l[0] | (l[1] << 16), l[2] | (l[3] << 16), l[4] | (l[5] << 16), l[6] | (l[7] << 16));
 }
 
+// Nearest TF32 value (ties away from zero) on the encoding, as tf32_rn on the host.
+__device__ __forceinline__ float tf32_rn_dev(float x) { return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u); }
+
 // Instruction descriptor: D f32, A/B tf32, K-major both, N = nt, M = 128.
 __device__ __forceinline__ uint32_t idesc_tf32(int nt) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(nt >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
@@ -351,14 +363,17 @@ struct TileInfo {
 __device__ __forceinline__ const TcProb &prob_of(const TcGroup &g, int i) { return g.table ? g.table[i] : g.p[i]; }
 
 template <int SPLIT>
-__device__ __forceinline__ TileInfo decode_tile(const TcGroup &g, int T, int nrt, int ntn, const int *done) {
+__device__ __forceinline__ TileInfo decode_tile(const TcGroup &g, int T, int nrt, int ntn, int nrhs,
+                                                const int *done) {
+  // row tile fastest, then right-hand side, then column tile, then problem: the
+  // tiles a CTA takes (gridDim.x apart) share one B operand for long runs
   TileInfo t;
   const int rt = T % nrt;
-  const int rest = T / nrt;
+  int rest = T / nrt;
+  t.rhs = g.rhs0 + rest % nrhs;
+  rest /= nrhs;
   const int nt = rest % ntn;
-  const int z = rest / ntn;
-  t.prob = z % g.nprob;
-  t.rhs = z / g.nprob;
+  t.prob = rest / ntn;
   const TcProb &P = prob_of(g, t.prob);
   const int npad = (P.N + 15) & ~15;
   t.r0 = rt * kM;
@@ -371,9 +386,10 @@ __device__ __forceinline__ TileInfo decode_tile(const TcGroup &g, int T, int nrt
 }
 
 // Next valid tile index after T (T = -1: the first of this CTA); total if none.
-__device__ __forceinline__ int next_tile(const TcGroup &g, int T, int total, int nrt, int ntn, const int *done) {
+__device__ __forceinline__ int next_tile(const TcGroup &g, int T, int total, int nrt, int ntn, int nrhs,
+                                         const int *done) {
   T = T < 0 ? (int)blockIdx.x : T + (int)gridDim.x;
-  while (T < total && !decode_tile<0>(g, T, nrt, ntn, done).valid) T += gridDim.x;
+  while (T < total && !decode_tile<0>(g, T, nrt, ntn, nrhs, done).valid) T += gridDim.x;
   return T;
 }
 
@@ -385,17 +401,25 @@ struct Cursor {
 template <int SPLIT>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(TcGroup g, int nrhs, const int *done, int *err, int nrt, int ntn, int nstage_ring, int ntc,
-              int ntmax_smem) {
+              int ntmax_smem, int bres) {
   using TR = SplitTraits<SPLIT>;
   const int total = nrt * ntn * g.nprob * nrhs;
-  // ntmax_smem: widest column tile of the launch (B region); ntc: TMEM columns per accumulator
-  const int stage_bytes = TR::kAStage + TR::kBPE * ntmax_smem * kKC;
+  // Two ways to feed B. Streaming (bres == 0): every stage carries its slice of
+  // B next to A (ntmax_smem: widest column tile of the launch). Resident
+  // (bres > 0): the whole B image of the current (problem, column tile) sits in
+  // a region of bres bytes after the ring and is copied again only when a
+  // CTA's next tile needs another one, so the ring moves A alone.
+  // ntc: TMEM columns per accumulator.
+  const bool resident = bres > 0;
+  const int stage_bytes = resident ? TR::kAStage : TR::kAStage + TR::kBPE * ntmax_smem * kKC;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + nstage_ring * stage_bytes);
+  uint8_t *Bres = smem + nstage_ring * stage_bytes;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(Bres + (resident ? bres : 0));
   uint64_t *landed = bars, *split = bars + 4, *empty = bars + 8, *tfull = bars + 12, *tempty = bars + 14;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 16);
   volatile int *abort = reinterpret_cast<volatile int *>(bars + 17);
+  uint64_t *bfull = bars + 18;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
@@ -408,6 +432,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&tfull[i], 1);
       mbar_init(&tempty[i], 8);
     }
+    mbar_init(bfull, 1);
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -420,25 +445,41 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == kTmaWarp) {
     // ------------------------------------------------------------ TMA issuer (one thread)
     if (lane == 0) {
-      int q = 0;
+      int q = 0, last_q = -1, bkey = -1, nb = 0;
       int last_par[4] = {-1, -1, -1, -1};
       bool ok = true;
-      for (int T = next_tile(g, -1, total, nrt, ntn, done); ok && T < total;
-           T = next_tile(g, T, total, nrt, ntn, done)) {
-        const TileInfo t = decode_tile<SPLIT>(g, T, nrt, ntn, done);
+      for (int T = next_tile(g, -1, total, nrt, ntn, nrhs, done); ok && T < total;
+           T = next_tile(g, T, total, nrt, ntn, nrhs, done)) {
+        const TileInfo t = decode_tile<SPLIT>(g, T, nrt, ntn, nrhs, done);
         const TcProb &P = prob_of(g, t.prob);
         const size_t btile = (size_t)TR::kBPE * kNTMax * t.kp * (size_t)(t.n0 / kNTMax);
+        const int key = t.prob * ntn + t.n0 / kNTMax;
+        if (resident && key != bkey) {
+          // the resident B is overwritten only after every MMA issued so far has
+          // completed: the commit of the last stage issued covers them all
+          if (last_q >= 0 && !mbar_wait(&empty[last_q % nstage_ring], (last_q / nstage_ring) & 1, abort)) {
+            ok = false;
+            break;
+          }
+          const uint32_t bb = (uint32_t)TR::kBPE * t.NT * t.kp;
+          mbar_expect_tx(bfull, bb);
+          for (uint32_t o = 0; o < bb; o += 32768u)
+            bulk_g2s(Bres + o, P.Bt + btile + o, bb - o < 32768u ? bb - o : 32768u, bfull);
+          bkey = key;
+          ++nb;
+        }
         for (int s = 0; s < t.nstages; ++s, ++q) {
           const int slot = q % nstage_ring, u = q / nstage_ring;
           if (u > 0 && !mbar_wait(&empty[slot], (u - 1) & 1, abort)) { ok = false; break; }
           uint8_t *sA = smem + slot * stage_bytes;
-          uint8_t *sB = sA + TR::kAStage;
           const int k0 = s * kKC;
-          const uint32_t bbytes = (uint32_t)TR::kBPE * t.NT * (t.kp - k0 < kKC ? t.kp - k0 : kKC);
+          const uint32_t bbytes =
+              resident ? 0u : (uint32_t)TR::kBPE * t.NT * (t.kp - k0 < kKC ? t.kp - k0 : kKC);
           mbar_expect_tx(&landed[slot], kAHalfBytes + bbytes);
           tma_load_3d(sA, P.tmap, k0, t.r0, t.rhs, &landed[slot]);
-          bulk_g2s(sB, P.Bt + btile + (size_t)TR::kBPE * t.NT * k0, bbytes, &landed[slot]);
+          if (!resident) bulk_g2s(sA + TR::kAStage, P.Bt + btile + (size_t)TR::kBPE * t.NT * k0, bbytes, &landed[slot]);
           last_par[slot] = u & 1;
+          last_q = q;
         }
       }
       if (!ok) *abort = 1;
@@ -446,15 +487,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       volatile int never = 0;
       for (int i = 0; i < nstage_ring; ++i)
         if (last_par[i] >= 0) mbar_wait(&landed[i], (uint32_t)last_par[i], &never);
+      if (nb > 0) mbar_wait(bfull, (uint32_t)((nb - 1) & 1), &never);
     }
     __syncwarp();
   } else if (warp < kEpiWarp0) {
     // ------------------------------------------------------------ TF32 split of the landed tile
     int q = 0;
     bool ok = true;
-    for (int T = next_tile(g, -1, total, nrt, ntn, done); ok && T < total;
-         T = next_tile(g, T, total, nrt, ntn, done)) {
-      const TileInfo t = decode_tile<SPLIT>(g, T, nrt, ntn, done);
+    for (int T = next_tile(g, -1, total, nrt, ntn, nrhs, done); ok && T < total;
+         T = next_tile(g, T, total, nrt, ntn, nrhs, done)) {
+      const TileInfo t = decode_tile<SPLIT>(g, T, nrt, ntn, nrhs, done);
       for (int s = 0; s < t.nstages; ++s, ++q) {
         const int slot = q % nstage_ring;
         if (!mbar_wait(&landed[slot], (q / nstage_ring) & 1, abort)) { ok = false; break; }
@@ -463,12 +505,15 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int c = tid; c < kAHalfBytes / 16; c += kConv) {
             float4 *ph = reinterpret_cast<float4 *>(sA + c * 16);
             const float4 a = *ph;
+            // hi = nearest TF32 value of a, lo = nearest TF32 value of the exact
+            // remainder a - hi (at most 12 significant bits): a = hi + lo to 2^-24 |a|
             float4 hi, lo;
-            hi.x = __uint_as_float(__float_as_uint(a.x) & 0xFFFFE000u);
-            hi.y = __uint_as_float(__float_as_uint(a.y) & 0xFFFFE000u);
-            hi.z = __uint_as_float(__float_as_uint(a.z) & 0xFFFFE000u);
-            hi.w = __uint_as_float(__float_as_uint(a.w) & 0xFFFFE000u);
-            lo = make_float4(a.x - hi.x, a.y - hi.y, a.z - hi.z, a.w - hi.w);
+            hi.x = tf32_rn_dev(a.x);
+            hi.y = tf32_rn_dev(a.y);
+            hi.z = tf32_rn_dev(a.z);
+            hi.w = tf32_rn_dev(a.w);
+            lo = make_float4(tf32_rn_dev(a.x - hi.x), tf32_rn_dev(a.y - hi.y), tf32_rn_dev(a.z - hi.z),
+                             tf32_rn_dev(a.w - hi.w));
             *ph = hi;
             *reinterpret_cast<float4 *>(sA + kAHalfBytes + c * 16) = lo;
           }
@@ -505,8 +550,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     // write consecutive positions of a column).
     const int quarter = warp & 3, half = (warp - kEpiWarp0) >> 2;
     int v = 0;
-    for (int T = next_tile(g, -1, total, nrt, ntn, done); T < total; T = next_tile(g, T, total, nrt, ntn, done)) {
-      const TileInfo t = decode_tile<SPLIT>(g, T, nrt, ntn, done);
+    for (int T = next_tile(g, -1, total, nrt, ntn, nrhs, done); T < total; T = next_tile(g, T, total, nrt, ntn, nrhs, done)) {
+      const TileInfo t = decode_tile<SPLIT>(g, T, nrt, ntn, nrhs, done);
       const TcProb &P = prob_of(g, t.prob);
       const int acc = v & 1;
       if (!mbar_wait(&tfull[acc], (v >> 1) & 1, abort)) break;
@@ -579,13 +624,19 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else {
     // ------------------------------------------------------------ MMA issuer (one thread)
     if (lane == 0) {
-      int q = 0, v = 0, last_slot = -1, last_par = 0;
+      int q = 0, v = 0, last_slot = -1, last_par = 0, bkey = -1, nb = 0;
       bool ok = true;
-      for (int T = next_tile(g, -1, total, nrt, ntn, done); ok && T < total;
-           T = next_tile(g, T, total, nrt, ntn, done)) {
-        const TileInfo t = decode_tile<SPLIT>(g, T, nrt, ntn, done);
+      for (int T = next_tile(g, -1, total, nrt, ntn, nrhs, done); ok && T < total;
+           T = next_tile(g, T, total, nrt, ntn, nrhs, done)) {
+        const TileInfo t = decode_tile<SPLIT>(g, T, nrt, ntn, nrhs, done);
         const int acc = v & 1, u = v >> 1;
         if (u > 0 && !mbar_wait(&tempty[acc], (u - 1) & 1, abort)) { ok = false; break; }
+        const int key = t.prob * ntn + t.n0 / kNTMax;
+        if (resident && key != bkey) {
+          if (!mbar_wait(bfull, (uint32_t)(nb & 1), abort)) { ok = false; break; }
+          bkey = key;
+          ++nb;
+        }
         tc_fence_after();
         const uint32_t d = tmem + (uint32_t)(acc * ntc);
         const uint32_t idesc = SPLIT ? idesc_bf16(t.NT) : idesc_tf32(t.NT);
@@ -594,8 +645,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (!mbar_wait(&split[slot], (q / nstage_ring) & 1, abort)) { ok = false; break; }
           tc_fence_after();
           uint8_t *sA = smem + slot * stage_bytes;
-          uint8_t *sB = sA + TR::kAStage;
           const int k0 = s * kKC;
+          uint8_t *sB = resident ? Bres + (size_t)TR::kBPE * t.NT * k0 : sA + TR::kAStage;
           const int ks = (t.kp - k0) / TR::kKStep < kKC / TR::kKStep ? (t.kp - k0) / TR::kKStep : kKC / TR::kKStep;
           if (SPLIT == 0) {
             for (int j = 0; j < ks; ++j) {
@@ -657,7 +708,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 // FP64 first-step input (times the optional scaling) to the FP32 layout the
 // TMA reads: A32[r*lda + k] = (float)(A64[r*K + k] * scale_in[r*K + k]).
 __global__ void k_tc_convert(TcGroup g, const int *done) {
-  const int rhs = blockIdx.y;
+  const int rhs = g.rhs0 + (int)blockIdx.y;
   if (done && done[rhs]) return;
   const TcProb &P = prob_of(g, blockIdx.z);
   if (!P.A64 || (P.done_flag && *P.done_flag)) return;
@@ -741,15 +792,31 @@ fdst_status launch_gemm_tc(const TcGroup &g, int nrhs, const int *done, cudaStre
   const int ntn = (npad + kNTMax - 1) / kNTMax;
   const int nt = npad < kNTMax ? npad : kNTMax;
   const int ntc = nt <= 32 ? 32 : nt <= 64 ? 64 : nt <= 128 ? 128 : 256;   // TMEM columns per accumulator
-  const int stage_bytes = g.split ? SplitTraits<1>::kAStage + SplitTraits<1>::kBPE * nt * kKC
-                                  : SplitTraits<0>::kAStage + SplitTraits<0>::kBPE * nt * kKC;
+  const int astage = g.split ? SplitTraits<1>::kAStage : SplitTraits<0>::kAStage;
+  const int bpe = g.split ? SplitTraits<1>::kBPE : SplitTraits<0>::kBPE;
+  int stage_bytes = astage + bpe * nt * kKC;
   int nring = tc_max_ring(g);
+  // resident B when the largest (problem, column tile) image fits beside two A stages
+  int bres = 0;
+  if (!g.table) {
+    int bmax = 0;
+    for (int i = 0; i < g.nprob; ++i) {
+      const int kp = tc_kpad(g.p[i].K, g.split), np = tc_npad(g.p[i].N);
+      for (int t = 0; t * kNTMax < np; ++t) bmax = std::max(bmax, bpe * tile_nt(np, t) * kp);
+    }
+    const int nr = std::min(4, (kSmemBudget - 2048 - bmax) / astage);
+    if (nr >= 2) {
+      bres = (bmax + 1023) & ~1023;
+      nring = std::min(4, (kSmemBudget - 2048 - bres) / astage);
+      stage_bytes = astage;
+    }
+  }
   if (ring > 0 && ring < nring) nring = ring;
   if (nring < 2) {
     set_error("tensor-core contraction: shared memory too small for two stages");
     return FDST_NOT_SUPPORTED;
   }
-  const int smem = nring * stage_bytes + 1024 + 1024;
+  const int smem = nring * stage_bytes + bres + 1024 + 1024;
   static int configured[2] = {0, 0}, nsm = 0;
   static std::mutex init_mutex;
   std::lock_guard<std::mutex> lock(init_mutex);
@@ -787,9 +854,9 @@ fdst_status launch_gemm_tc(const TcGroup &g, int nrhs, const int *done, cudaStre
   const int grid = total < nsm ? (int)total : nsm;
   count_launch(1);
   if (sp)
-    k_gemm_tc<1><<<grid, kThreads, smem, s>>>(g, nrhs, done, g_err_flag, nrt, ntn, nring, ntc, nt);
+    k_gemm_tc<1><<<grid, kThreads, smem, s>>>(g, nrhs, done, g_err_flag, nrt, ntn, nring, ntc, nt, bres);
   else
-    k_gemm_tc<0><<<grid, kThreads, smem, s>>>(g, nrhs, done, g_err_flag, nrt, ntn, nring, ntc, nt);
+    k_gemm_tc<0><<<grid, kThreads, smem, s>>>(g, nrhs, done, g_err_flag, nrt, ntn, nring, ntc, nt, bres);
   return FDST_OK;
 }
 

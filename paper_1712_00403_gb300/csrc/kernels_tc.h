@@ -42,6 +42,7 @@ struct TcGroup {
   int maxR = 0, maxN = 0;           // with a table: largest R and N among its problems
   int convert = 0;                  // 1: convert A64 into A32 first (problems with A64 set)
   int split = 0;                    // 0: split-TF32 (hi/lo, 3 products); 1: split-BF16 (3 pieces, 6 products)
+  int rhs0 = 0;                     // the launch covers right-hand sides rhs0 .. rhs0 + nrhs - 1
 };
 // Layout of one contraction step of a chain (rows R, contracted size K,
 // out_nv = size of the next contracted index): lda = K rounded up to 8 (TMA
