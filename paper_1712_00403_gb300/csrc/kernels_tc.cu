@@ -79,6 +79,7 @@ template <> struct SplitTraits<1> {
   static constexpr int kAStage = 4 * kM * 32 + 3 * 2 * kM * 32, kBPE = 6, kKStep = 16;
 };
 constexpr int kSmemBudget = 227 * 1024;
+constexpr int kMaxRhsLaunch = 640;   // stop flags copied into the barrier region (bytes 192..831)
 constexpr unsigned long long kWaitNs = 2000000000ull;
 }  // namespace
 
@@ -195,7 +196,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 
 // Bounded wait for the phase with the given parity to complete; gives up
 // after about 2 s or as soon as *abort is set by another role.
-__device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort) {
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
   while (true) {
@@ -249,6 +250,27 @@ __device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uin
       "l"(a), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
 }
+
+// The same MMA with the A operand in tensor memory (lane = row of A, one 32-bit
+// column per TF32 element along K).
+__device__ __forceinline__ void mma_tf32_ta(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(
+          d),
+      "r"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+// 16 consecutive 32-bit columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+                   taddr),
+               "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]),
+               "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
@@ -362,9 +384,11 @@ struct TileInfo {
 
 __device__ __forceinline__ const TcProb &prob_of(const TcGroup &g, int i) { return g.table ? g.table[i] : g.p[i]; }
 
+// `done` here is the launch's copy of the per-right-hand-side stop flags in
+// shared memory (index rhs - rhs0), read once when the CTA starts.
 template <int SPLIT>
 __device__ __forceinline__ TileInfo decode_tile(const TcGroup &g, int T, int nrt, int ntn, int nrhs,
-                                                const int *done) {
+                                                const uint8_t *done) {
   // row tile fastest, then right-hand side, then column tile, then problem: the
   // tiles a CTA takes (gridDim.x apart) share one B operand for long runs
   TileInfo t;
@@ -378,7 +402,7 @@ __device__ __forceinline__ TileInfo decode_tile(const TcGroup &g, int T, int nrt
   const int npad = (P.N + 15) & ~15;
   t.r0 = rt * kM;
   t.n0 = nt * kNTMax;
-  t.valid = t.r0 < P.R && t.n0 < npad && !(done && done[t.rhs]) && !(P.done_flag && *P.done_flag);
+  t.valid = t.r0 < P.R && t.n0 < npad && !done[t.rhs - g.rhs0] && !(P.done_flag && *P.done_flag);
   t.NT = npad - t.n0 < kNTMax ? npad - t.n0 : kNTMax;
   t.kp = SPLIT ? (P.K + 15) & ~15 : (P.K + 7) & ~7;
   t.nstages = (t.kp + kKC - 1) / kKC;
@@ -387,7 +411,7 @@ __device__ __forceinline__ TileInfo decode_tile(const TcGroup &g, int T, int nrt
 
 // Next valid tile index after T (T = -1: the first of this CTA); total if none.
 __device__ __forceinline__ int next_tile(const TcGroup &g, int T, int total, int nrt, int ntn, int nrhs,
-                                         const int *done) {
+                                         const uint8_t *done) {
   T = T < 0 ? (int)blockIdx.x : T + (int)gridDim.x;
   while (T < total && !decode_tile<0>(g, T, nrt, ntn, nrhs, done).valid) T += gridDim.x;
   return T;
@@ -401,7 +425,7 @@ struct Cursor {
 template <int SPLIT>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(TcGroup g, int nrhs, const int *done, int *err, int nrt, int ntn, int nstage_ring, int ntc,
-              int ntmax_smem, int bres) {
+              int ntmax_smem, int bres, int amode, int tmem_cols) {
   using TR = SplitTraits<SPLIT>;
   const int total = nrt * ntn * g.nprob * nrhs;
   // Two ways to feed B. Streaming (bres == 0): every stage carries its slice of
@@ -409,9 +433,15 @@ __global__ void __launch_bounds__(kThreads, 1)
   // (bres > 0): the whole B image of the current (problem, column tile) sits in
   // a region of bres bytes after the ring and is copied again only when a
   // CTA's next tile needs another one, so the ring moves A alone.
-  // ntc: TMEM columns per accumulator.
+  // ntc: TMEM columns per accumulator (the second starts at column ntc).
+  // amode 1 (split-TF32 with resident B): the split warps write A's TF32 hi/lo
+  // pieces into tensor memory (two stages of 64 columns from column 2 ntc: hi
+  // in the first 32, lo in the next 32) and release the landed shared-memory
+  // slot as soon as they have read it, so a ring slot holds only the 16 KB the
+  // TMA lands and the MMAs read A from tensor memory.
   const bool resident = bres > 0;
-  const int stage_bytes = resident ? TR::kAStage : TR::kAStage + TR::kBPE * ntmax_smem * kKC;
+  const bool atm = amode != 0;
+  const int stage_bytes = atm ? kAHalfBytes : resident ? TR::kAStage : TR::kAStage + TR::kBPE * ntmax_smem * kKC;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint8_t *Bres = smem + nstage_ring * stage_bytes;
@@ -420,14 +450,20 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 16);
   volatile int *abort = reinterpret_cast<volatile int *>(bars + 17);
   uint64_t *bfull = bars + 18;
+  uint64_t *a_empty = bars + 19;                              // amode 1: TMEM A stage free (MMA commit)
+  uint64_t *bfree = bars + 21;   // amode 1: every MMA on the resident B done before a tile needing another B
+  uint8_t *done_s = reinterpret_cast<uint8_t *>(bars + 24);   // nrhs <= kMaxRhsLaunch flags
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int i = tid; i < nrhs; i += kThreads) done_s[i] = done ? (done[g.rhs0 + i] != 0) : 0;
   if (tid == 0) {
     for (int i = 0; i < nstage_ring; ++i) {
       mbar_init(&landed[i], 1);
       mbar_init(&split[i], kConv / 32);
-      mbar_init(&empty[i], 1);
+      mbar_init(&empty[i], atm ? kConv / 32 : 1);
     }
+    for (int i = 0; i < 2; ++i) mbar_init(&a_empty[i], 1);
+    mbar_init(bfree, 1);
     for (int i = 0; i < 2; ++i) {
       mbar_init(&tfull[i], 1);
       mbar_init(&tempty[i], 8);
@@ -436,7 +472,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == kMmaWarp) tmem_alloc(tmem_slot, 2 * ntc);
+  if (warp == kMmaWarp) tmem_alloc(tmem_slot, (uint32_t)tmem_cols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -448,16 +484,19 @@ __global__ void __launch_bounds__(kThreads, 1)
       int q = 0, last_q = -1, bkey = -1, nb = 0;
       int last_par[4] = {-1, -1, -1, -1};
       bool ok = true;
-      for (int T = next_tile(g, -1, total, nrt, ntn, nrhs, done); ok && T < total;
-           T = next_tile(g, T, total, nrt, ntn, nrhs, done)) {
-        const TileInfo t = decode_tile<SPLIT>(g, T, nrt, ntn, nrhs, done);
+      for (int T = next_tile(g, -1, total, nrt, ntn, nrhs, done_s); ok && T < total;
+           T = next_tile(g, T, total, nrt, ntn, nrhs, done_s)) {
+        const TileInfo t = decode_tile<SPLIT>(g, T, nrt, ntn, nrhs, done_s);
         const TcProb &P = prob_of(g, t.prob);
         const size_t btile = (size_t)TR::kBPE * kNTMax * t.kp * (size_t)(t.n0 / kNTMax);
         const int key = t.prob * ntn + t.n0 / kNTMax;
         if (resident && key != bkey) {
           // the resident B is overwritten only after every MMA issued so far has
           // completed: the commit of the last stage issued covers them all
-          if (last_q >= 0 && !mbar_wait(&empty[last_q % nstage_ring], (last_q / nstage_ring) & 1, abort)) {
+          // (amode 1: the MMA thread commits bfree once before each change of B, so the
+          // nb-th reload waits for phase nb - 1 and no phase can be skipped or aliased)
+          if (last_q >= 0 && !(atm ? mbar_wait(bfree, (uint32_t)((nb - 1) & 1), abort)
+                                   : mbar_wait(&empty[last_q % nstage_ring], (last_q / nstage_ring) & 1, abort))) {
             ok = false;
             break;
           }
@@ -490,13 +529,61 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (nb > 0) mbar_wait(bfull, (uint32_t)((nb - 1) & 1), &never);
     }
     __syncwarp();
+  } else if (warp < kEpiWarp0 && atm) {
+    // ------------------------------------------------------------ TF32 split into tensor memory
+    // Warps w and w + 4 share TMEM lane quarter w % 4 (rows 32 (w % 4) + lane) and take
+    // K columns 0-15 and 16-31 of the stage.
+    const int quarter = warp & 3, khalf = warp >> 2, r = quarter * 32 + lane;
+    const uint32_t tlane = (uint32_t)(quarter * 32) << 16;
+    int q = 0;
+    bool ok = true;
+    for (int T = next_tile(g, -1, total, nrt, ntn, nrhs, done_s); ok && T < total;
+         T = next_tile(g, T, total, nrt, ntn, nrhs, done_s)) {
+      const TileInfo t = decode_tile<SPLIT>(g, T, nrt, ntn, nrhs, done_s);
+      for (int s = 0; s < t.nstages; ++s, ++q) {
+        const int slot = q % nstage_ring, as = q & 1, au = q >> 1;
+        if (!mbar_wait(&landed[slot], (q / nstage_ring) & 1, abort)) { ok = false; break; }
+        // the row's 16 FP32 values: chunks 4 khalf .. 4 khalf + 3 of the SWIZZLE_128B row
+        const uint8_t *row = smem + slot * stage_bytes + (r >> 3) * 1024 + (r & 7) * 128;
+        float x[16];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const float4 v = *reinterpret_cast<const float4 *>(row + (((4 * khalf + c) ^ (r & 7)) << 4));
+          x[4 * c] = v.x;
+          x[4 * c + 1] = v.y;
+          x[4 * c + 2] = v.z;
+          x[4 * c + 3] = v.w;
+        }
+        uint32_t hi[16], lo[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          const float h = tf32_rn_dev(x[e]);
+          hi[e] = __float_as_uint(h);
+          lo[e] = __float_as_uint(tf32_rn_dev(x[e] - h));
+        }
+        // the slot's values are consumed (in registers) before it is handed back to
+        // the TMA: order these generic-proxy reads before its async-proxy writes
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[slot]);   // the slot may be landed again
+        if (au > 0 && !mbar_wait(&a_empty[as], (au - 1) & 1, abort)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t ta = tmem + tlane + (uint32_t)(2 * ntc + 64 * as + 16 * khalf);
+        tmem_st16(ta, hi);
+        tmem_st16(ta + 32, lo);
+        tmem_wait_st();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&split[as]);
+      }
+    }
   } else if (warp < kEpiWarp0) {
     // ------------------------------------------------------------ TF32 split of the landed tile
     int q = 0;
     bool ok = true;
-    for (int T = next_tile(g, -1, total, nrt, ntn, nrhs, done); ok && T < total;
-         T = next_tile(g, T, total, nrt, ntn, nrhs, done)) {
-      const TileInfo t = decode_tile<SPLIT>(g, T, nrt, ntn, nrhs, done);
+    for (int T = next_tile(g, -1, total, nrt, ntn, nrhs, done_s); ok && T < total;
+         T = next_tile(g, T, total, nrt, ntn, nrhs, done_s)) {
+      const TileInfo t = decode_tile<SPLIT>(g, T, nrt, ntn, nrhs, done_s);
       for (int s = 0; s < t.nstages; ++s, ++q) {
         const int slot = q % nstage_ring;
         if (!mbar_wait(&landed[slot], (q / nstage_ring) & 1, abort)) { ok = false; break; }
@@ -550,8 +637,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     // write consecutive positions of a column).
     const int quarter = warp & 3, half = (warp - kEpiWarp0) >> 2;
     int v = 0;
-    for (int T = next_tile(g, -1, total, nrt, ntn, nrhs, done); T < total; T = next_tile(g, T, total, nrt, ntn, nrhs, done)) {
-      const TileInfo t = decode_tile<SPLIT>(g, T, nrt, ntn, nrhs, done);
+    for (int T = next_tile(g, -1, total, nrt, ntn, nrhs, done_s); T < total; T = next_tile(g, T, total, nrt, ntn, nrhs, done_s)) {
+      const TileInfo t = decode_tile<SPLIT>(g, T, nrt, ntn, nrhs, done_s);
       const TcProb &P = prob_of(g, t.prob);
       const int acc = v & 1;
       if (!mbar_wait(&tfull[acc], (v >> 1) & 1, abort)) break;
@@ -571,32 +658,42 @@ __global__ void __launch_bounds__(kThreads, 1)
       const double *__restrict__ sor = so ? so + r : nullptr;
       const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * ntc);
       const int nchunks = t.NT / 16;
+      // Stores walk a pointer down the columns (c_cs or R apart); the divide's
+      // 16 column eigenvalue sums are loaded once per chunk (lane l holds column
+      // nb + l % 16) and broadcast by shuffles; the divide is x * (1/Delta) with
+      // the fast reciprocal (2 ulp in FP32, far below the split products' error).
       auto store_chunk = [&](const uint32_t (&vals)[16], int c) {
         const int nb = t.n0 + 16 * c;
-        if (!rok) return;
+        float lcv = 0.0f;
+        if (lc) lcv = nb + (lane & 15) < Ncols ? lc[nb + (lane & 15)] : 1.0f;
         if (c64) {
+          double *p = c64 + (int64_t)nb * cs;
+          const double *ps = sor ? sor + (int64_t)nb * R : nullptr;
 #pragma unroll
           for (int qq = 0; qq < 16; ++qq) {
-            const int n = nb + qq;
-            if (n < Ncols) {
-              float x = __uint_as_float(vals[qq]);
-              if (lc) x = x / (lr + lc[n]);
+            float x = __uint_as_float(vals[qq]);
+            if (lc) x = __fdividef(x, lr + __shfl_sync(0xffffffffu, lcv, qq));
+            if (rok && nb + qq < Ncols) {
               double y = f32_to_f64(x);
-              if (sor) y *= sor[(int64_t)n * R];
-              c64[(int64_t)n * cs] = y;
+              if (ps) y *= ps[(int64_t)qq * R];
+              *p = y;
             }
+            p += cs;
           }
         } else if (lc) {
+          float *p = c32 + (int64_t)nb * cs;
 #pragma unroll
           for (int qq = 0; qq < 16; ++qq) {
-            const int n = nb + qq;
-            if (n < Ncols) c32[(int64_t)n * cs] = __uint_as_float(vals[qq]) / (lr + lc[n]);
+            const float lq = __shfl_sync(0xffffffffu, lcv, qq);
+            if (rok && nb + qq < Ncols) *p = __fdividef(__uint_as_float(vals[qq]), lr + lq);
+            p += cs;
           }
         } else {
+          float *p = c32 + (int64_t)nb * cs;
 #pragma unroll
           for (int qq = 0; qq < 16; ++qq) {
-            const int n = nb + qq;
-            if (n < Ncols) c32[(int64_t)n * cs] = __uint_as_float(vals[qq]);
+            if (rok && nb + qq < Ncols) *p = __uint_as_float(vals[qq]);
+            p += cs;
           }
         }
       };
@@ -626,9 +723,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       int q = 0, v = 0, last_slot = -1, last_par = 0, bkey = -1, nb = 0;
       bool ok = true;
-      for (int T = next_tile(g, -1, total, nrt, ntn, nrhs, done); ok && T < total;
-           T = next_tile(g, T, total, nrt, ntn, nrhs, done)) {
-        const TileInfo t = decode_tile<SPLIT>(g, T, nrt, ntn, nrhs, done);
+      for (int T = next_tile(g, -1, total, nrt, ntn, nrhs, done_s); ok && T < total;
+           T = next_tile(g, T, total, nrt, ntn, nrhs, done_s)) {
+        const TileInfo t = decode_tile<SPLIT>(g, T, nrt, ntn, nrhs, done_s);
         const int acc = v & 1, u = v >> 1;
         if (u > 0 && !mbar_wait(&tempty[acc], (u - 1) & 1, abort)) { ok = false; break; }
         const int key = t.prob * ntn + t.n0 / kNTMax;
@@ -638,41 +735,78 @@ __global__ void __launch_bounds__(kThreads, 1)
           ++nb;
         }
         tc_fence_after();
-        const uint32_t d = tmem + (uint32_t)(acc * ntc);
+        const uint32_t d = tmem + (uint32_t)(acc * ntc);   // accumulator columns [acc ntc, acc ntc + NT)
         const uint32_t idesc = SPLIT ? idesc_bf16(t.NT) : idesc_tf32(t.NT);
         for (int s = 0; s < t.nstages; ++s) {
           const int slot = q % nstage_ring;
+          if (atm) {
+            const int as = q & 1;
+            if (!mbar_wait(&split[as], (q >> 1) & 1, abort)) { ok = false; break; }
+            tc_fence_after();
+            const int k0 = s * kKC;
+            const int ks = (t.kp - k0) / 8 < 4 ? (t.kp - k0) / 8 : 4;
+            const uint8_t *sB = Bres + (size_t)8 * t.NT * k0;
+            const uint64_t bh0 = sdesc_sw32(sB), bl0 = sdesc_sw32(sB + (size_t)ks * t.NT * 32);
+            const uint64_t bstep = (uint64_t)t.NT * 2;
+            const uint32_t ah0 = tmem + (uint32_t)(2 * ntc + 64 * as);
+            const uint32_t acc0 = s > 0 ? 1u : 0u;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              if (j < ks) {
+                const uint32_t ah = ah0 + 8u * j, al = ah + 32u;
+                const uint64_t bh = bh0 + bstep * j, bl = bl0 + bstep * j;
+                mma_tf32_ta(d, ah, bh, idesc, j > 0 ? 1u : acc0);
+                mma_tf32_ta(d, ah, bl, idesc, 1u);
+                mma_tf32_ta(d, al, bh, idesc, 1u);
+              }
+            }
+            mma_commit(&a_empty[as]);
+            last_slot = as;
+            last_par = (q >> 1) & 1;
+            ++q;
+            continue;
+          }
           if (!mbar_wait(&split[slot], (q / nstage_ring) & 1, abort)) { ok = false; break; }
           tc_fence_after();
           uint8_t *sA = smem + slot * stage_bytes;
           const int k0 = s * kKC;
           uint8_t *sB = resident ? Bres + (size_t)TR::kBPE * t.NT * k0 : sA + TR::kAStage;
           const int ks = (t.kp - k0) / TR::kKStep < kKC / TR::kKStep ? (t.kp - k0) / TR::kKStep : kKC / TR::kKStep;
+          // Descriptors are built once per stage; a k-step moves the start address
+          // field (16-byte units, bits 0-13) by a constant, so the issue loop is a
+          // few adds per MMA (one thread must keep the tensor pipe fed)
+          const uint32_t acc0 = s > 0 ? 1u : 0u;
           if (SPLIT == 0) {
-            for (int j = 0; j < ks; ++j) {
-              const uint64_t ah = sdesc_sw128(sA + j * 32);
-              const uint64_t al = sdesc_sw128(sA + kAHalfBytes + j * 32);
-              const uint64_t bh = sdesc_sw32(sB + (size_t)j * t.NT * 32);
-              const uint64_t bl = sdesc_sw32(sB + (size_t)(ks + j) * t.NT * 32);
-              mma_tf32(d, ah, bh, idesc, (s > 0 || j > 0) ? 1u : 0u);
-              mma_tf32(d, ah, bl, idesc, 1u);
-              mma_tf32(d, al, bh, idesc, 1u);
+            const uint64_t ah0 = sdesc_sw128(sA), al0 = sdesc_sw128(sA + kAHalfBytes);
+            const uint64_t bh0 = sdesc_sw32(sB), bl0 = sdesc_sw32(sB + (size_t)ks * t.NT * 32);
+            const uint64_t bstep = (uint64_t)t.NT * 2;   // NT rows x 32 B per k-step
+#pragma unroll
+            for (int j = 0; j < kKC / TR::kKStep; ++j) {
+              if (j < ks) {
+                const uint64_t ah = ah0 + 2u * j, al = al0 + 2u * j;   // 32 B per k-step inside the atom
+                const uint64_t bh = bh0 + bstep * j, bl = bl0 + bstep * j;
+                mma_tf32(d, ah, bh, idesc, j > 0 ? 1u : acc0);
+                mma_tf32(d, ah, bl, idesc, 1u);
+                mma_tf32(d, al, bh, idesc, 1u);
+              }
             }
           } else {
             // 6 leading products of (a0 + a1 + a2)(b0 + b1 + b2): pieces i + j <= 2
-            for (int j = 0; j < ks; ++j) {
-              uint64_t a[3], b[3];
+            const uint64_t a00 = sdesc_sw32(sA + kAHalfBytes), b00 = sdesc_sw32(sB);
+            const uint64_t apart = (uint64_t)(2 * kM * 32) >> 4, astep = (uint64_t)(kM * 32) >> 4;
+            const uint64_t bstep = (uint64_t)t.NT * 2, bpart = bstep * ks;
 #pragma unroll
-              for (int p = 0; p < 3; ++p) {
-                a[p] = sdesc_sw32(sA + kAHalfBytes + p * 2 * kM * 32 + j * kM * 32);
-                b[p] = sdesc_sw32(sB + (size_t)(p * ks + j) * t.NT * 32);
+            for (int j = 0; j < kKC / TR::kKStep; ++j) {
+              if (j < ks) {
+                const uint64_t a0 = a00 + astep * j, a1 = a0 + apart, a2 = a1 + apart;
+                const uint64_t b0 = b00 + bstep * j, b1 = b0 + bpart, b2 = b1 + bpart;
+                mma_bf16(d, a0, b0, idesc, j > 0 ? 1u : acc0);
+                mma_bf16(d, a0, b1, idesc, 1u);
+                mma_bf16(d, a1, b0, idesc, 1u);
+                mma_bf16(d, a0, b2, idesc, 1u);
+                mma_bf16(d, a1, b1, idesc, 1u);
+                mma_bf16(d, a2, b0, idesc, 1u);
               }
-              mma_bf16(d, a[0], b[0], idesc, (s > 0 || j > 0) ? 1u : 0u);
-              mma_bf16(d, a[0], b[1], idesc, 1u);
-              mma_bf16(d, a[1], b[0], idesc, 1u);
-              mma_bf16(d, a[0], b[2], idesc, 1u);
-              mma_bf16(d, a[1], b[1], idesc, 1u);
-              mma_bf16(d, a[2], b[0], idesc, 1u);
             }
           }
           mma_commit(&empty[slot]);
@@ -683,6 +817,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!ok) break;
         mma_commit(&tfull[acc]);
         ++v;
+        if (atm) {
+          // the TMA may overwrite the resident B only once every MMA on it has completed
+          const int T2 = next_tile(g, T, total, nrt, ntn, nrhs, done_s);
+          if (T2 < total) {
+            const TileInfo t2 = decode_tile<SPLIT>(g, T2, nrt, ntn, nrhs, done_s);
+            if (t2.prob * ntn + t2.n0 / kNTMax != key) mma_commit(bfree);
+          }
+        }
       }
       if (!ok) {
         atomicExch(err, 1);
@@ -691,7 +833,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       // drain: the last commit covers every MMA issued before it (bounded wait, ignoring abort)
       if (last_slot >= 0) {
         volatile int never = 0;
-        mbar_wait(&empty[last_slot], last_par, &never);
+        mbar_wait(atm ? &a_empty[last_slot] : &empty[last_slot], last_par, &never);
       }
     }
     __syncwarp();
@@ -701,7 +843,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   if (warp == kMmaWarp) {
     tc_fence_after();
-    tmem_dealloc(tmem, 2 * ntc);
+    tmem_dealloc(tmem, (uint32_t)tmem_cols);
   }
 }
 
@@ -714,12 +856,33 @@ __global__ void k_tc_convert(TcGroup g, const int *done) {
   if (!P.A64 || (P.done_flag && *P.done_flag)) return;
   const double *src = P.A64 + rhs * P.a64_rhs_stride;
   float *dst = const_cast<float *>(P.A32) + rhs * P.a_rhs_stride;
-  const unsigned K = (unsigned)P.K, total = (unsigned)P.R * K;
-  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
-    const unsigned r = e / K, k = e - r * K;
-    double x = src[e];
-    if (P.scale_in) x *= P.scale_in[e];
-    dst[(size_t)r * P.lda + k] = f64_to_f32_rn(x);
+  // a warp per row (lanes along k, coalesced FP64 loads and FP32 stores), four
+  // loads per lane in flight before the conversions
+  const int K = P.K, R = P.R, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int r = blockIdx.x * nw + (threadIdx.x >> 5); r < R; r += gridDim.x * nw) {
+    const double *s = src + (size_t)r * K;
+    const double *sc = P.scale_in ? P.scale_in + (size_t)r * K : nullptr;
+    float *d = dst + (size_t)r * P.lda;
+    for (int k0 = 0; k0 < K; k0 += 128) {
+      double x[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int k = k0 + 32 * u + lane;
+        x[u] = k < K ? s[k] : 0.0;
+      }
+      if (sc) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int k = k0 + 32 * u + lane;
+          if (k < K) x[u] *= sc[k];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int k = k0 + 32 * u + lane;
+        if (k < K) d[k] = f64_to_f32_rn(x[u]);
+      }
+    }
   }
 }
 
@@ -786,12 +949,22 @@ int tc_max_ring(const TcGroup &g) {
 }
 
 fdst_status launch_gemm_tc(const TcGroup &g, int nrhs, const int *done, cudaStream_t s, int ring) {
+  if (nrhs > kMaxRhsLaunch) {
+    // the kernel keeps the stop flags of its right-hand sides in shared memory
+    TcGroup h = g;
+    for (int r0 = 0; r0 < nrhs; r0 += kMaxRhsLaunch) {
+      h.rhs0 = g.rhs0 + r0;
+      const fdst_status st = launch_gemm_tc(h, std::min(kMaxRhsLaunch, nrhs - r0), done, s, ring);
+      if (st != FDST_OK) return st;
+    }
+    return FDST_OK;
+  }
   int maxR, maxN;
   tc_dims(g, maxR, maxN);
   const int npad = tc_npad(maxN);
   const int ntn = (npad + kNTMax - 1) / kNTMax;
   const int nt = npad < kNTMax ? npad : kNTMax;
-  const int ntc = nt <= 32 ? 32 : nt <= 64 ? 64 : nt <= 128 ? 128 : 256;   // TMEM columns per accumulator
+  int ntc = nt <= 32 ? 32 : nt <= 64 ? 64 : nt <= 128 ? 128 : 256;   // TMEM columns per accumulator
   const int astage = g.split ? SplitTraits<1>::kAStage : SplitTraits<0>::kAStage;
   const int bpe = g.split ? SplitTraits<1>::kBPE : SplitTraits<0>::kBPE;
   int stage_bytes = astage + bpe * nt * kKC;
@@ -810,6 +983,16 @@ fdst_status launch_gemm_tc(const TcGroup &g, int nrhs, const int *done, cudaStre
       nring = std::min(4, (kSmemBudget - 2048 - bres) / astage);
       stage_bytes = astage;
     }
+  }
+  // split-TF32 with resident B: A's pieces go to tensor memory when both accumulators
+  // (32-column multiples) and two 64-column A stages fit in its 512 columns
+  int amode = 0, tmem_cols = 2 * ntc;
+  if (bres > 0 && !g.split && 2 * ((nt + 31) & ~31) + 128 <= 512) {
+    amode = 1;
+    ntc = (nt + 31) & ~31;
+    tmem_cols = 512;
+    stage_bytes = kAHalfBytes;
+    nring = std::min(4, (kSmemBudget - 2048 - bres) / kAHalfBytes);
   }
   if (ring > 0 && ring < nring) nring = ring;
   if (nring < 2) {
@@ -843,7 +1026,7 @@ fdst_status launch_gemm_tc(const TcGroup &g, int nrhs, const int *done, cudaStre
     configured[sp] = smem;
   }
   if (g.convert) {
-    long long blocks = ((long long)maxR * 64 + 255) / 256;
+    long long blocks = ((long long)maxR + 7) / 8;   // 8 rows (warps) per block
     if (blocks > 1024) blocks = 1024;
     if (blocks < 1) blocks = 1;
     count_launch(1);
@@ -854,9 +1037,11 @@ fdst_status launch_gemm_tc(const TcGroup &g, int nrhs, const int *done, cudaStre
   const int grid = total < nsm ? (int)total : nsm;
   count_launch(1);
   if (sp)
-    k_gemm_tc<1><<<grid, kThreads, smem, s>>>(g, nrhs, done, g_err_flag, nrt, ntn, nring, ntc, nt, bres);
+    k_gemm_tc<1><<<grid, kThreads, smem, s>>>(g, nrhs, done, g_err_flag, nrt, ntn, nring, ntc, nt, bres, amode,
+                                              tmem_cols);
   else
-    k_gemm_tc<0><<<grid, kThreads, smem, s>>>(g, nrhs, done, g_err_flag, nrt, ntn, nring, ntc, nt, bres);
+    k_gemm_tc<0><<<grid, kThreads, smem, s>>>(g, nrhs, done, g_err_flag, nrt, ntn, nring, ntc, nt, bres, amode,
+                                              tmem_cols);
   return FDST_OK;
 }
 
