@@ -1651,11 +1651,21 @@ fdst_status fdst_solve(fdst_handle h, const double *d_b, double *d_x, int nrhs, 
   const int check_every = 4;
   int it = 0;
   bool residuals_current = false;
+  // Double-float banded matvec on the identity map: the update writes the FP32 pairs of
+  // the next z alongside z, so no separate split pass runs per iteration. (The matvec's
+  // result is joined to FP64 for the dot and the Lanczos step: folding the join into them
+  // moves FP64 work onto GB300's slow FP64 pipe and measured slower.)
+  const bool dfp = !h->mapped && h->desc.matvec_precision == FDST_MV_DF64;
+  bool z_pairs = false;   // h->x2 holds the pairs of the current z
   while (it < maxit) {
     residuals_current = false;
     size_t e0 = 0;
     if (h->timing) { mark(); e0 = ev.size() - 1; }
-    TRY(run_matvec(h, h->z, h->Az, nrhs, h->done, st, false));
+    if (dfp)
+      TRY(run_plan_df(h, full_view(h, true), z_pairs ? nullptr : h->z, h->Az, nrhs, h->done, st, 0, n, 0, n,
+                      true));
+    else
+      TRY(run_matvec(h, h->z, h->Az, nrhs, h->done, st, false));
     size_t e1 = 0;
     if (h->timing) { mark(); e1 = ev.size() - 1; spans.push_back({0, e0, e1}); }
     launch_dot(h->Az, h->z, n, n, nrhs, h->partials, h->counters, delta, h->done, st);
@@ -1667,7 +1677,8 @@ fdst_status fdst_solve(fdst_handle h, const double *d_b, double *d_x, int nrhs, 
     if (h->timing) { mark(); e3 = ev.size() - 1; spans.push_back({1, e2, e3}); }
     launch_dot(v, h->z_new, n, n, nrhs, h->partials, h->counters, g2, h->done, st);
     launch_minres_scalars(h->state, delta, g2, nrhs, maxit, h->done, h->n_stopped, st);
-    launch_minres_update(w_old, w, d_x, h->z, h->z_new, h->state, n, n, nrhs, h->done, st);
+    launch_minres_update(w_old, w, d_x, h->z, h->z_new, h->state, n, n, nrhs, h->done, st, dfp ? h->x2 : nullptr);
+    z_pairs = dfp;
     launch_minres_commit(h->state, h->done, nrhs, st);
     if (h->timing) { mark(); spans.push_back({2, e3, ev.size() - 1}); }
     ++it;
@@ -1705,6 +1716,7 @@ fdst_status fdst_solve(fdst_handle h, const double *d_b, double *d_x, int nrhs, 
         if (!restart.empty()) {
           for (int j : restart) ++restarts[j];
           TRY(minres_restart(h, d_b, d_x, nrhs, restart, true_rel, tol, hs, st));
+          z_pairs = false;   // the restarted right-hand sides have a new z
         }
         std::vector<int> hd(nrhs, 1);
         for (int j : resume) hd[j] = 0;

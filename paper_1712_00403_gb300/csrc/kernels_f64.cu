@@ -719,15 +719,18 @@ void launch_minres_scalars(MinresState *st, const double *delta, const double *g
 }
 
 // w_new = (z - a3 w_old - a2 w)/a1; w_old <- w; w <- w_new; x += coef_x w_new;
-// z <- z_new / gamma_new (the next normalized Lanczos vector), all in place.
+// z <- z_new / gamma_new (the next normalized Lanczos vector), all in place; with z_df
+// set, also the double-float pairs of the new z (the next banded matvec reads them
+// instead of a separate split pass).
 __global__ void k_minres_update(double *w_old, double *w, double *x, double *z, const double *z_new,
-                                const MinresState *st, int64_t n, int64_t stride, const int *done) {
+                                const MinresState *st, int64_t n, int64_t stride, const int *done, float2 *z_df) {
   const int j = blockIdx.y;
   if (done[j]) return;
   const MinresState &S = st[j];
   const double ia1 = S.inv_a1, a2 = S.a2, a3 = S.a3, cx = S.coef_x, ig = S.inv_gamma_new;
   double *wo = w_old + j * stride, *ww = w + j * stride, *xx = x + j * stride, *zz = z + j * stride;
   const double *zn = z_new + j * stride;
+  float2 *zd = z_df ? z_df + j * stride : nullptr;
   auto step = [&](double wi, double woi, double zi, double xi, double zni, double &wo_out, double &w_out,
                   double &x_out, double &z_out) {
     const double wn = (zi - a3 * woi - a2 * wi) * ia1;
@@ -737,12 +740,19 @@ __global__ void k_minres_update(double *w_old, double *w, double *x, double *z, 
     z_out = zni * ig;
   };
   const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, ts = (int64_t)gridDim.x * blockDim.x;
-  if (!(same_phase(ww, wo) && same_phase(ww, xx) && same_phase(ww, zz) && same_phase(ww, zn))) {
-    for (int64_t i = t0; i < n; i += ts) step(ww[i], wo[i], zz[i], xx[i], zn[i], wo[i], ww[i], xx[i], zz[i]);
+  const bool zd_ok = !zd || (((reinterpret_cast<uintptr_t>(zd) >> 3) ^ (reinterpret_cast<uintptr_t>(ww) >> 3)) & 1) == 0;
+  if (!(same_phase(ww, wo) && same_phase(ww, xx) && same_phase(ww, zz) && same_phase(ww, zn) && zd_ok)) {
+    for (int64_t i = t0; i < n; i += ts) {
+      step(ww[i], wo[i], zz[i], xx[i], zn[i], wo[i], ww[i], xx[i], zz[i]);
+      if (zd) zd[i] = f64_split(zz[i]);
+    }
     return;
   }
   const int64_t head = (reinterpret_cast<uintptr_t>(ww) & 15) && n > 0 ? 1 : 0;
-  if (head && t0 == 0) step(ww[0], wo[0], zz[0], xx[0], zn[0], wo[0], ww[0], xx[0], zz[0]);
+  if (head && t0 == 0) {
+    step(ww[0], wo[0], zz[0], xx[0], zn[0], wo[0], ww[0], xx[0], zz[0]);
+    if (zd) zd[0] = f64_split(zz[0]);
+  }
   const int64_t pairs = (n - head) >> 1;
   double2 *w2 = reinterpret_cast<double2 *>(ww + head), *o2 = reinterpret_cast<double2 *>(wo + head);
   double2 *x2 = reinterpret_cast<double2 *>(xx + head), *z2 = reinterpret_cast<double2 *>(zz + head);
@@ -756,18 +766,25 @@ __global__ void k_minres_update(double *w_old, double *w, double *x, double *z, 
     w2[i] = nw;
     x2[i] = nx;
     z2[i] = nz;
+    if (zd) {
+      const float2 a = f64_split(nz.x), b = f64_split(nz.y);
+      reinterpret_cast<float4 *>(zd + head)[i] = make_float4(a.x, a.y, b.x, b.y);
+    }
   }
-  if (((n - head) & 1) && t0 == 0)
+  if (((n - head) & 1) && t0 == 0) {
     step(ww[n - 1], wo[n - 1], zz[n - 1], xx[n - 1], zn[n - 1], wo[n - 1], ww[n - 1], xx[n - 1], zz[n - 1]);
+    if (zd) zd[n - 1] = f64_split(zz[n - 1]);
+  }
 }
 
 void launch_minres_update(double *w_old, double *w, double *x, double *z, const double *z_new,
-                          MinresState *st, int64_t n, int64_t stride, int nrhs, int *done, cudaStream_t s) {
+                          MinresState *st, int64_t n, int64_t stride, int nrhs, int *done, cudaStream_t s,
+                          float2 *z_df) {
   int64_t blocks = (n + 255) / 256;
   if (blocks > 4096) blocks = 4096;
   if (blocks < 1) blocks = 1;
   count_launch(1);
-  k_minres_update<<<dim3((unsigned)blocks, nrhs), 256, 0, s>>>(w_old, w, x, z, z_new, st, n, stride, done);
+  k_minres_update<<<dim3((unsigned)blocks, nrhs), 256, 0, s>>>(w_old, w, x, z, z_new, st, n, stride, done, z_df);
 }
 
 __global__ void k_minres_commit(MinresState *st, int *done, int nrhs) {
