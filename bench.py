@@ -65,8 +65,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true",
                     help="skip the plain-FP64 leg (FD apply and matvec in FP64) of single-problem workloads")
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the plain-FP64 leg")
-    ap.add_argument("--serving-nel3-max", type=int, default=48,
-                    help="largest elements per direction of the served 3D instances (the batched range is 16..96)")
+    ap.add_argument("--serving-nel3-max", type=int, default=96,
+                    help="largest elements per direction of the served 3D instances (default: the batched range 16..96)")
     ap.add_argument("--no-cpu-baseline", action="store_true",
                     help="skip the oracle timing (profiling runs of the GPU path)")
     return ap.parse_args()
@@ -392,7 +392,7 @@ def w_text(name, w):
                 f"~ U{{16..96}} (draw seed {w['seed']}), one seeded N(0,1) right-hand side each "
                 f"(seeds {w['rhs_seed0']}..{w['rhs_seed0'] + w['count'] - 1}), MINRES tol 1e-8 from x0=0")
     return (f"Poisson arrivals at rates {w['rates']} req/s, {w['per_rate']} requests per rate; 50/50 mix of 3D "
-            f"unit-cube TH (p ~ U{{2..6}}, elements per direction ~ U{{16..48}}) and 2D TH/RT (p ~ U{{2..8}}, "
+            f"unit-cube TH (p ~ U{{2..6}}, elements per direction ~ U{{16..96}}) and 2D TH/RT (p ~ U{{2..8}}, "
             f"elements per direction ~ U{{32..256}}); MINRES tol 1e-8")
 
 

@@ -76,7 +76,7 @@ def batched_instances(seed=400, count=64, p_range=(2, 6), nel_range=(16, 96)):
     return out
 
 
-def serving_requests(rate_index, rate, count, seed=500, mix_seed=550, nel3=(16, 48)):
+def serving_requests(rate_index, rate, count, seed=500, mix_seed=550, nel3=(16, 96)):
     """Poisson arrival times (rate per second, stream seeded seed + rate_index) and a
     50/50 mix of 3D Taylor-Hood instances (p ~ U{2..6}, elements per direction ~
     U{nel3}) and 2D instances (Taylor-Hood or Raviart-Thomas with equal odds,
