@@ -42,7 +42,8 @@ TF32_OVER_BF16 = 1.1 / 2.25    # nominal dense TF32 / BF16 ratio
 # by its entry count (every launch streams operands proportional to it); k_spmv_df per launch
 # of the 32^3 mapped operator at 4 RHS, the bench's own size.
 MATVEC_TRAFFIC = {"k_band_df": {"bytes": 5.7966e9, "entries": 1_673_830, "nrhs": 16, "launches": 21},
-                  "k_spmv_df": {"bytes": 18.4215e9, "entries": None, "nrhs": 4, "launches": 1}}
+                  # captured on the 16^3 mapped cube (168,894,405 nonzeros), scaled by nonzero count
+                  "k_spmv_df": {"bytes": 2.0534e9, "nnz": 168_894_405, "nrhs": 4, "launches": 1}}
 
 
 def parse():
@@ -571,12 +572,12 @@ def run_gpu(args):
     traffic, traffic_note = None, None
     if per_mv >= per_pc and mv == fd.MV_DF64 and not mfree:
         tr = MATVEC_TRAFFIC["k_spmv_df" if mapped else "k_band_df"]
-        if tr["nrhs"] == nrhs and (mapped and args.workload == "mapped_th_p3_32" or not mapped):
-            scale = 1.0 if tr["entries"] is None else P.n_total / tr["entries"]
+        if tr["nrhs"] == nrhs:
+            scale = (P.flops_matvec / 2.0) / tr["nnz"] if mapped else P.n_total / tr["entries"]
             # per launch, like achieved: a matvec's bytes over its launches
             traffic = tr["bytes"] * scale / tr["launches"]
             traffic_note = ("ncu DRAM bytes per launch (%s), %s" % (
-                "one launch at this size" if tr["entries"] is None else
+                "one launch captured on the 16^3 mapped cube, scaled by nonzero count" if mapped else
                 "mean of the %d launches of one matvec captured on 1,673,830 entries per RHS, scaled by "
                 "entry count" % tr["launches"], "B"))
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,

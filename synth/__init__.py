@@ -18,6 +18,9 @@ WORKLOADS = {
     # 3D mapped cube (sine bump map, variable viscosity), p=3, 32^3 elements, seeds 300..303
     "mapped_th_p3_32": dict(dim=3, disc="TH", p=3, n_el=(32, 32, 32), seeds=list(range(300, 304)),
                             geometry="sine_bump"),
+    # the mapped cube at 16^3 elements (profiling-sized: about 1.8e8 nonzeros, a few GB on the device)
+    "mapped_th_p3_16": dict(dim=3, disc="TH", p=3, n_el=(16, 16, 16), seeds=list(range(300, 304)),
+                            geometry="sine_bump"),
     # the same mapped cube at 64^3 elements (6,740,830 DoF, 32.8 M quadrature points): sized for the
     # matrix-free operator (its CSR would hold about 1.1e10 nonzeros)
     "mapped_th_p3_64": dict(dim=3, disc="TH", p=3, n_el=(64, 64, 64), seeds=list(range(300, 304)),
