@@ -781,6 +781,18 @@ static fdst_status run_plan_df(fdst_ctx *h, const PlanView &V, const double *x, 
   int64_t nl = 0;
   size_t i = 0;
   const auto &P = *V.ops;
+  // With an FP64 result requested, the last product into each result block writes
+  // the joined FP64 value itself, so no separate join pass reads the pairs back.
+  std::vector<int> last_writer(P.size(), 0);
+  bool all_joined = y != nullptr;
+  if (y) {
+    std::map<int, size_t> last;
+    for (size_t k = 0; k < P.size(); ++k)
+      if (P[k].out_kind == 3) last[P[k].out_id] = k;
+    for (auto &kv : last) last_writer[kv.second] = 1;
+    for (int64_t b = 0; b < (int64_t)h->dim + 1 && all_joined; ++b)
+      if (V.out_off[b] >= out_lo && V.out_off[b] < out_hi && !last.count((int)b)) all_joined = false;
+  }
   while (i < P.size()) {
     BandGroupDF g;
     std::vector<std::pair<int, int>> outs;
@@ -799,7 +811,11 @@ static fdst_status run_plan_df(fdst_ctx *h, const PlanView &V, const double *x, 
       if (op.in_kind == 0) { b.X = V.xw + V.in_off[op.in_id]; b.x_rhs_stride = V.in_stride; }
       else if (op.in_kind == 1) { b.X = reinterpret_cast<const float2 *>((*V.t1)[op.in_id]); b.x_rhs_stride = (*V.t1_size)[op.in_id]; }
       else { b.X = reinterpret_cast<const float2 *>((*V.g)[op.in_id]); b.x_rhs_stride = (*V.g_size)[op.in_id]; }
-      if (op.out_kind == 3) { b.Y = V.yw + V.out_off[op.out_id]; b.y_rhs_stride = V.out_stride; }
+      if (op.out_kind == 3) {
+        b.Y = V.yw + V.out_off[op.out_id];
+        b.y_rhs_stride = V.out_stride;
+        if (all_joined && last_writer[i]) b.Y64 = y + V.out_off[op.out_id];
+      }
       else if (op.out_kind == 1) { b.Y = reinterpret_cast<float2 *>((*V.t1)[op.out_id]); b.y_rhs_stride = (*V.t1_size)[op.out_id]; }
       else { b.Y = reinterpret_cast<float2 *>((*V.g)[op.out_id]); b.y_rhs_stride = (*V.g_size)[op.out_id]; }
       ++i;
@@ -808,7 +824,7 @@ static fdst_status run_plan_df(fdst_ctx *h, const PlanView &V, const double *x, 
     ++nl;
   }
   kernel_span(h, k0, nl, st);
-  if (y) launch_join_df(V.yw + out_lo, y + out_lo, out_hi - out_lo, V.out_stride, nrhs, done, st);
+  if (y && !all_joined) launch_join_df(V.yw + out_lo, y + out_lo, out_hi - out_lo, V.out_stride, nrhs, done, st);
   CK(cudaGetLastError());
   return FDST_OK;
 }

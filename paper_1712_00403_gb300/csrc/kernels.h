@@ -72,6 +72,8 @@ void launch_band(const BandGroup &g, int nrhs, const int *done, cudaStream_t s);
 struct BandOpDF {
   const float2 *X = nullptr;
   float2 *Y = nullptr;
+  double *Y64 = nullptr;            // set: the result (after accumulating Y) is written as FP64 here, same offsets
+                                    // (the last product into a block writes the joined value; Y is not written)
   const float2 *vals = nullptr;
   const int *lo = nullptr;
   int w = 0, rows = 0;

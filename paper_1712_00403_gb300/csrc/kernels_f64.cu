@@ -217,9 +217,12 @@ __global__ void __launch_bounds__(256, 4) k_band_df(BandGroupDF g, int nrhs, con
   // With accumulation the T old values of Y are loaded together before the first
   // store, so that their latencies overlap.
   const bool acc = op.accumulate != 0;
+  double *y64 = op.Y64 ? op.Y64 + rhs * op.y_rhs_stride : nullptr;
   auto finish = [&](float sh, float sl, float2 yo, float2 *dst) {
     if (acc) df_add(sh, sl, yo.x, yo.y);
-    *dst = df_norm(sh, sl);
+    const float2 r = df_norm(sh, sl);
+    if (y64) y64[dst - Y] = f64_join(r);
+    else *dst = r;
   };
   const bool swap = op.swap != 0;
   const unsigned d0 = (unsigned)op.d0, d1 = (unsigned)op.d1, d2 = (unsigned)op.d2;
