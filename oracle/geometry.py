@@ -33,6 +33,19 @@ zero mean log over the quadrature points; then tau^k_j = exp(f^{k,j}_j) and
 mu^k_d = exp(mean of f^{k,j}_d over the two j != d). The D_V scaling absorbs
 what the fit misses.
 
+Raviart-Thomas on the identity map with a variable viscosity (the RT push-
+forward by Piola on a non-trivial map is not built): the volume forms above
+with the component-wise RT spaces, plus the Nitsche form sigma of eq. theta
+face by face with nu at the face points (penalty C_pen/h_d on the faces normal
+to e_d). P_D^G for RT: the diagonal entries of C_k^RT = nu |det J| J^{-1}
+(||R_k||^2 I + R_k R_k^T) J^{-T}, R_k = J e_k / det J (eq. Q_RT), fitted as
+above; the weighted K~ of the tangential directions carry the Nitsche bracket
+with tau^k_d(0), tau^k_d(1) (Appendix). Reading: the fit lives on the
+quadrature points as the Appendix says; tau at eta_d = 0, 1 is the fit's own
+direction-d update evaluated on those faces (fit_at), which leaves the
+interior fit unchanged and is exact for separable fields. D_V adds sigma's
+diagonal to diag(A); Q^RT weighs the pressure mass with |det J|^{-1} / nu.
+
 Pins (tests/test_oracle_geometry.py): brute-force element quadrature of the
 symmetric-gradient form and of b vs. the sum-factorized matvec (both maps);
 amplitude 0 with nu = 1 reproduces the cube operator; det J closed form vs.
@@ -46,6 +59,15 @@ Theorem 2 spectral bounds of P_Q^{-1} Q and Theorem 1 bounds of P_V^{-1} A
 (Korn constants 1/2), on both maps. The fit on the mapped domains' own
 fields has no closed form: there it is pinned only through the separable
 and bilinear cases above (the CUDA path runs the same algorithm).
+RT pins (tests/test_oracle_rt_geometry.py): the RT operator with variable nu
+(volume + faces) and its diagonal vs. the dense brute-force quadrature of a +
+sigma and b (a non-separable and a separable field; a planted nu = 1 on the
+faces fails it); on the contrast family (nu depends on eta_1 alone) the
+Kronecker sum of the weighted RT pencils equals the brute-force A_kk and D_V
+= 1 (a planted tau(0) = tau(1) = 1 fails it); nu = 1 reduces P_D^G to P_D;
+C_k^RT vs. the Piola symmetric-gradient form for constant Jacobians and its
+identity-map closed form; fit_at reproduces separable fields on the faces;
+P_D^G-MINRES beats P_D-MINRES on the contrast family.
 """
 import numpy as np
 
@@ -121,13 +143,43 @@ class Grid:
             x, w = splines.gauss_rule(S.pres[d].knots, npts)
             self.pts.append(x)
             self.wts.append(w)
+        self.amp, self.nu_const, self.contrast = amp, nu_const, contrast
         E = np.stack(np.meshgrid(*self.pts, indexing="ij"), axis=-1)
         self.x, self.J, self.det, self.Jinv = geometry(E, amp, geometry_kind)
-        self.nu = np.full(self.det.shape, nu_const) if nu_const is not None else viscosity(self.x, contrast)
+        self.nu = self.nu_of(self.x)
         W = self.wts[0][:, None, None] * self.wts[1][None, :, None] * self.wts[2][None, None, :]
         self.W = W
         # univariate tables at the points: value and derivative of each space
         self.vtab = {}
+
+    @property
+    def identity(self):
+        """True when the map is the identity (sine bump of amplitude 0)."""
+        return self.kind == "sine_bump" and self.amp == 0.0
+
+    def nu_of(self, x):
+        """The viscosity at physical points x (..., 3)."""
+        if self.nu_const is not None:
+            return np.full(x.shape[:-1], float(self.nu_const))
+        return viscosity(x, self.contrast)
+
+    def at(self, E):
+        """Geometry and viscosity at other parametric points E (..., 3), with the
+        attributes J, det, Jinv, nu that the coefficient functions read."""
+        P = _Points()
+        P.x, P.J, P.det, P.Jinv = geometry(E, self.amp, self.kind)
+        P.nu = self.nu_of(P.x)
+        return P
+
+    def face(self, d, t):
+        """Parametric points (tensor grid, extent 1 along direction d) and face
+        weights (product of the Gauss weights of the two other directions) of
+        the face eta_d = t."""
+        axes = [np.array([float(t)]) if e == d else self.pts[e] for e in range(3)]
+        E = np.stack(np.meshgrid(*axes, indexing="ij"), axis=-1)
+        w = [np.ones(1) if e == d else self.wts[e] for e in range(3)]
+        W = w[0][:, None, None] * w[1][None, :, None] * w[2][None, None, :]
+        return E, W
 
     def table(self, space, d, deriv):
         key = (id(space), d, deriv)
@@ -135,6 +187,41 @@ class Grid:
             B, D = splines.basis(space.knots, space.degree, self.pts[d])
             self.vtab[key] = ((D if deriv else B)[:, space.keep]).T.copy()   # (n, npts)
         return self.vtab[key]
+
+
+class _Points:
+    """Geometry and viscosity at a set of parametric points (see Grid.at)."""
+
+
+def tables(G, space3, derivs, face=None):
+    """Per-direction tables (n_d, q_d) of the basis (derivs[d] False) or its
+    derivative; on a face (d, t) the direction-d table is the basis at eta_d = t."""
+    T = []
+    for e in range(3):
+        s = space3[e]
+        if face is not None and face[0] == e:
+            B, D = splines.basis(s.knots, s.degree, np.array([float(face[1])]))
+            T.append(((D if derivs[e] else B)[:, s.keep]).T.copy())
+        else:
+            T.append(G.table(s, e, derivs[e]))
+    return T
+
+
+def eval_tables(T, x):
+    """sum_i x_i prod_d T_d[i_d, q_d], indexed [q1, q2, q3]; x vec-ordered (i1 fastest)."""
+    n = [t.shape[0] for t in T]
+    X = np.asarray(x, float).reshape(n[2], n[1], n[0])
+    Y = np.einsum("cba,ap->cbp", X, T[0])
+    Y = np.einsum("cbp,bq->cpq", Y, T[1])
+    return np.einsum("cpq,cr->pqr", Y, T[2])
+
+
+def test_tables(T, F):
+    """Transpose of eval_tables: y_i = sum_q F[q] prod_d T_d[i_d, q_d] (vec order)."""
+    Y = np.einsum("pqr,cr->pqc", F, T[2])
+    Y = np.einsum("pqc,bq->pbc", Y, T[1])
+    Y = np.einsum("pbc,ap->abc", Y, T[0])
+    return np.transpose(Y, (2, 1, 0)).reshape(-1)
 
 
 def to_points(G, space3, x, derivs):
@@ -240,6 +327,90 @@ def brute_force(S, G):
     return A, B
 
 
+# ---------------------------------------------------------------- RT on the identity map: the Nitsche faces
+
+def _nitsche_constants(S):
+    """C_pen and, per direction d, the h of the penalty C_pen/h on the faces
+    normal to e_d: the Nitsche factor of that direction (the same reading as
+    the Kronecker form's K~_d)."""
+    cp = {s.cpen for row in S.vel for s in row if s.nitsche}
+    assert len(cp) == 1, cp
+    hs = []
+    for d in range(S.dim):
+        hd = {S.vel[k][d].h for k in range(S.dim) if S.vel[k][d].nitsche}
+        assert len(hd) == 1, hd
+        hs.append(hd.pop())
+    return cp.pop(), hs
+
+
+def _require_rt_identity(S, G):
+    if S.disc != "RT":
+        raise ValueError("not a Raviart-Thomas system")
+    if not G.identity:
+        raise ValueError("the RT system is built on the identity map (no Piola push-forward)")
+
+
+def nitsche_matvec(S, G, x):
+    """The velocity blocks of sigma(u, .) (eq. theta) on the six faces of the
+    cube, viscosity nu(x) at the face points, the RT basis e_k B on the identity
+    map. Written from the form: with n the outward normal (-e_d on eta_d = 0,
+    +e_d on eta_d = 1) and v = e_s B_j the test function,
+        2 nu [C_pen/h u.v - ((grad^s u) n).v - ((grad^s v) n).u]
+    (h = the element size along d, the penalty of the direction-d factor K~_d)
+    where ((grad^s v) n).u = (u_s d_n B_j + (u.n) d_s B_j) / 2. Face quadrature:
+    the volume rule's points of the two other directions."""
+    _require_rt_identity(S, G)
+    cpen, h = _nitsche_constants(S)
+    u = S.split(np.asarray(x, float))[:3]
+    ys = [np.zeros(S.block_sizes[k]) for k in range(3)]
+    unit = [[e == b for e in range(3)] for b in range(3)]
+    for d in range(3):
+        for t, sgn in ((0.0, -1.0), (1.0, 1.0)):
+            face = (d, t)
+            E, Wf = G.face(d, t)
+            w2 = 2.0 * G.at(E).nu * Wf
+            val = [eval_tables(tables(G, S.vel[c], [False] * 3, face), u[c]) for c in range(3)]
+            grd = [[eval_tables(tables(G, S.vel[c], unit[b], face), u[c]) for b in range(3)] for c in range(3)]
+            # ((grad^s u) n)_a = (d_d u_a + d_a u_d) sgn / 2
+            sn = [0.5 * sgn * (grd[a][d] + grd[d][a]) for a in range(3)]
+            for s_ in range(3):
+                ys[s_] += test_tables(tables(G, S.vel[s_], [False] * 3, face), w2 * (cpen / h[d] * val[s_] - sn[s_]))
+                ys[s_] += test_tables(tables(G, S.vel[s_], unit[d], face), -0.5 * sgn * w2 * val[s_])
+                ys[s_] += test_tables(tables(G, S.vel[s_], unit[s_], face), -0.5 * sgn * w2 * val[d])
+    return ys
+
+
+def operator(S, G, x):
+    """A x: the volume forms (matvec) and, for RT, the Nitsche form sigma."""
+    y = matvec(S, G, x)
+    if S.disc == "RT":
+        nv = sum(S.block_sizes[:3])
+        y[:nv] += np.concatenate(nitsche_matvec(S, G, x))
+    return y
+
+
+def nitsche_diag(S, G, k):
+    """diag of the sigma part of A_kk: sum over faces of
+    int 2 nu [C_pen/h B_i^2 - 2 ((grad^s e_k B_i) n)_k B_i], with
+    ((grad^s e_k B) n)_k = (d_n B + n_k d_k B) / 2."""
+    _require_rt_identity(S, G)
+    cpen, h = _nitsche_constants(S)
+    out = np.zeros(S.block_sizes[k])
+    sp = S.vel[k]
+    for d in range(3):
+        for t, sgn in ((0.0, -1.0), (1.0, 1.0)):
+            face = (d, t)
+            E, Wf = G.face(d, t)
+            w2 = 2.0 * G.at(E).nu * Wf
+            V = tables(G, sp, [False] * 3, face)
+            D = tables(G, sp, [e == d for e in range(3)], face)
+            sq = [V[e] * V[e] for e in range(3)]
+            mixed_d = [V[e] * (D[e] if e == d else V[e]) for e in range(3)]
+            factor = sgn * (2.0 if d == k else 1.0)        # d_n B + n_k d_k B = sgn (1 + delta_dk) d_d B
+            out += cpen / h[d] * test_tables(sq, w2) - factor * test_tables(mixed_d, w2)
+    return out
+
+
 # ---------------------------------------------------------------- coefficients and separable fit
 
 def c_diag(G, k):
@@ -247,6 +418,20 @@ def c_diag(G, k):
     Ji = G.Jinv
     JJt = np.einsum("...ac,...bc->...ab", Ji, Ji)
     return [G.nu * np.abs(G.det) * (JJt[..., j, j] + Ji[..., j, k] ** 2) for j in range(3)]
+
+
+def c_matrix_rt(J, det, Jinv, nu, k):
+    """C_k^RT = nu |det J| J^{-1} (||R_k||^2 I + R_k R_k^T) J^{-T} with R_k = J e_k / det J (eq. Q_RT)."""
+    R = J[..., :, k] / det[..., None]
+    M = (R * R).sum(-1)[..., None, None] * np.eye(3) + R[..., :, None] * R[..., None, :]
+    C = np.einsum("...ab,...bc,...dc->...ad", Jinv, M, Jinv)
+    return (nu * np.abs(det))[..., None, None] * C
+
+
+def c_diag_rt(G, k):
+    """c^k_jj of C_k^RT (eq. Q_RT), j = 0..2."""
+    C = c_matrix_rt(G.J, G.det, G.Jinv, G.nu, k)
+    return [C[..., j, j] for j in range(3)]
 
 
 def separable_fit(c, sweeps=SWEEPS):
@@ -262,9 +447,25 @@ def separable_fit(c, sweeps=SWEEPS):
     return f
 
 
-def tau_mu(G, k, sweeps=SWEEPS):
-    """tau^k_d and mu^k_d at the quadrature points of direction d (Appendix form)."""
-    cs = c_diag(G, k)
+def fit_at(L_face, f, d):
+    """The direction-d factor of a converged fit log c ~ f_1 + f_2 + f_3 at a
+    point outside the grid (a face eta_d = t): the fit's own update for
+    direction d, the midrange over the face of log c - sum_{e != d} f_e
+    (L_face has extent 1 along d)."""
+    shp = [(-1, 1, 1), (1, -1, 1), (1, 1, -1)]
+    R = L_face - sum(f[e].reshape(shp[e]) for e in range(3) if e != d)
+    return 0.5 * (R.max() + R.min())
+
+
+def tau_mu(G, k, sweeps=SWEEPS, disc="TH"):
+    """tau^k_d and mu^k_d at the quadrature points of direction d (Appendix form);
+    for RT also tau^k_d at eta_d = 0 and 1 (the boundary terms of the weighted
+    K~), returned as a third list of pairs. Reading: the fit is computed on the
+    quadrature points as the Appendix says, and its direction-d factor is
+    carried to the faces by the fit's own update there (fit_at), so that the
+    interior fit is unchanged."""
+    cfun = c_diag_rt if disc == "RT" else c_diag
+    cs = cfun(G, k)
     fits = []
     for j in range(3):
         f = separable_fit(cs[j], sweeps)
@@ -277,19 +478,38 @@ def tau_mu(G, k, sweeps=SWEEPS):
         fits.append(f)
     tau = [np.exp(fits[d][d]) for d in range(3)]
     mu = [np.exp(0.5 * sum(fits[j][d] for j in range(3) if j != d)) for d in range(3)]
-    return tau, mu
+    if disc != "RT":
+        return tau, mu
+    ends = []
+    for d in range(3):
+        pair = []
+        for t in (0.0, 1.0):
+            E, _ = G.face(d, t)
+            L = np.log(cfun(G.at(E), k)[d])
+            pair.append(float(np.exp(fit_at(L, fits[d], d))))
+        ends.append(tuple(pair))
+    return tau, mu, ends
 
 
 def weighted_pencils(S, G, k, sweeps=SWEEPS):
-    """(K^k_d, M^k_d) with weights tau^k_d, mu^k_d given at the quadrature points."""
-    tau, mu = tau_mu(G, k, sweeps)
+    """(K^k_d, M^k_d) with weights tau^k_d, mu^k_d given at the quadrature points;
+    for RT the tangential factors are the weighted K~, M~ of the Appendix, the
+    Nitsche boundary terms scaled by tau^k_d(0) and tau^k_d(1)."""
+    if S.disc == "RT":
+        _require_rt_identity(S, G)
+        tau, mu, ends = tau_mu(G, k, sweeps, "RT")
+    else:
+        tau, mu = tau_mu(G, k, sweeps)
     Ks, Ms = [], []
     for d in range(3):
         sp = S.vel[k][d]
         Tv = G.table(sp, d, False)
         Td = G.table(sp, d, True)
         w = G.wts[d]
-        Ks.append((Td * (w * tau[d])) @ Td.T)
+        K = (Td * (w * tau[d])) @ Td.T
+        if sp.nitsche:
+            K = K - uv.nitsche_boundary(sp, ends[d][0], ends[d][1])
+        Ks.append(K)
         Ms.append((Tv * (w * mu[d])) @ Tv.T)
     return Ks, Ms
 
@@ -318,9 +538,11 @@ def diag_A(S, G, k):
 
 
 def diag_Q(S, G):
-    """[Q]_ii = int nu^{-1} |det J| B_i^2 (eq. weighted-pressure-mass)."""
+    """[Q]_ii = int nu^{-1} g B_i^2 with g = |det J| (TH) or |det J|^{-1} (RT)
+    (eq. weighted-pressure-mass)."""
     T = [G.table(S.pres[d], d, False) ** 2 for d in range(3)]
-    F = G.W * np.abs(G.det) / G.nu
+    g = np.abs(G.det) if S.disc != "RT" else 1.0 / np.abs(G.det)
+    F = G.W * g / G.nu
     Y = np.einsum("pqr,cr->pqc", F, T[2])
     Y = np.einsum("pqc,bq->pbc", Y, T[1])
     Y = np.einsum("pbc,ap->abc", Y, T[0])
@@ -345,7 +567,10 @@ class PDG:
             Ks, Ms = weighted_pencils(S, G, k, sweeps)
             self.pencils.append((Ks, Ms, [1.0, 1.0, 1.0]))
             dP = sum(kron_diag([Ks[e] if e == d else Ms[e] for e in range(3)]) for d in range(3))
-            self.DV.append(diag_A(S, G, k) / dP)
+            dA = diag_A(S, G, k)
+            if S.disc == "RT":
+                dA = dA + nitsche_diag(S, G, k)
+            self.DV.append(dA / dP)
         self.Mp = stokes.pq_factors(S)
         self.DQ = diag_Q(S, G) / kron_diag(self.Mp)
 

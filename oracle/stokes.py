@@ -412,7 +412,9 @@ def brute_force_RT(S, cpen, h, nu=1.0, faces=True):
     the same rule on the face's own directions. Nothing here uses the
     univariate factors, so it pins the Kronecker blocks of A_rs for all r, s
     (the claim that sigma adds only to A_kk included). faces=False leaves
-    sigma out (the volume form alone). Tiny sizes only."""
+    sigma out (the volume form alone). nu is a constant or a function of the
+    points (N, d) -> (N,) (a variable viscosity); h is one mesh size or one per
+    direction (the faces normal to e_d take h[d]). Tiny sizes only."""
     assert S.disc == "RT"
     d = S.dim
     npts = S.p + 2
@@ -427,7 +429,7 @@ def brute_force_RT(S, cpen, h, nu=1.0, faces=True):
             Xf, Wf = _tensor_points(rules, fixed=(e, t))
             nrm = np.zeros(d)
             nrm[e] = sgn
-            face_rules.append((Xf, Wf, nrm))
+            face_rules.append((Xf, Wf, nrm, float(h[e]) if np.ndim(h) else float(h)))
 
     def all_vel(P):
         Vs, Gs = zip(*[_vector_basis(S.vel[k], k, d, P) for k in range(d)])
@@ -435,14 +437,16 @@ def brute_force_RT(S, cpen, h, nu=1.0, faces=True):
         G = np.concatenate(Gs)
         return V, 0.5 * (G + G.transpose(0, 2, 1, 3)), G
 
+    nu_at = nu if callable(nu) else (lambda P: np.full(len(P), float(nu)))
     V, Sg, G = all_vel(X)
-    A = np.einsum("iabp,jabp,p->ij", Sg, Sg, 2.0 * nu * W)
-    for Xf, Wf, nrm in face_rules:
+    A = np.einsum("iabp,jabp,p->ij", Sg, Sg, 2.0 * nu_at(X) * W)
+    for Xf, Wf, nrm, hf in face_rules:
         Vf, Sf, _ = all_vel(Xf)
         Sn = np.einsum("iabp,b->iap", Sf, nrm)                 # (grad^s v) n
-        pen = np.einsum("iap,jap,p->ij", Vf, Vf, Wf)
-        cons = np.einsum("iap,jap,p->ij", Sn, Vf, Wf)          # ((grad^s phi_i) n) . phi_j
-        A += 2.0 * nu * (cpen / h * pen - cons - cons.T)
+        w2 = 2.0 * nu_at(Xf) * Wf
+        pen = np.einsum("iap,jap,p->ij", Vf, Vf, w2)
+        cons = np.einsum("iap,jap,p->ij", Sn, Vf, w2)          # ((grad^s phi_i) n) . phi_j
+        A += cpen / hf * pen - cons - cons.T
     # pressure basis at the volume points (all functions kept)
     pv = []
     for e in range(d):

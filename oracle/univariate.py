@@ -85,11 +85,17 @@ def stiffness(s, weight=None, npts=None, tau0=1.0, tau1=1.0):
     with the boundary values scaled by tau(0), tau(1) in the weighted case (Appendix)."""
     K = mixed(s, 1, s, 1, weight, npts)
     if s.nitsche:
-        B, D = splines.basis(s.knots, s.degree, np.array([0.0, 1.0]))
-        b0, b1 = B[0, s.keep], B[1, s.keep]
-        d0, d1 = D[0, s.keep], D[1, s.keep]
-        bnd = (tau1 * np.outer(d1, b1) - tau0 * np.outer(d0, b0)
-               + tau1 * np.outer(b1, d1) - tau0 * np.outer(b0, d0)
-               - 2.0 * s.cpen / s.h * (tau1 * np.outer(b1, b1) + tau0 * np.outer(b0, b0)))
-        K = K - bnd
+        K = K - nitsche_boundary(s, tau0, tau1)
     return K
+
+
+def nitsche_boundary(s, tau0=1.0, tau1=1.0):
+    """The bracket subtracted from int tau b'b' in K~ (Sec. 5; Appendix for the
+    weights): tau(1) b_l'(1) b_s(1) - tau(0) b_l'(0) b_s(0) + (l <-> s)
+    - 2 C_pen/h (tau(1) b_l(1) b_s(1) + tau(0) b_l(0) b_s(0))."""
+    B, D = splines.basis(s.knots, s.degree, np.array([0.0, 1.0]))
+    b0, b1 = B[0, s.keep], B[1, s.keep]
+    d0, d1 = D[0, s.keep], D[1, s.keep]
+    return (tau1 * np.outer(d1, b1) - tau0 * np.outer(d0, b0)
+            + tau1 * np.outer(b1, d1) - tau0 * np.outer(b0, d0)
+            - 2.0 * s.cpen / s.h * (tau1 * np.outer(b1, b1) + tau0 * np.outer(b0, b0)))
