@@ -60,7 +60,10 @@ enum { FDST_FD_F64 = 0, FDST_FD_TF32X3 = 1, FDST_FD_BF16X6 = 2 };
  * of a thick annulus of Sec. 7 (inner radius 1, outer 2, height 1) in polar form
  * x = (r cos t, r sin t, eta3), r = 1 + eta1, t = pi eta2 / 4. */
 enum { FDST_GEOM_IDENTITY = 0, FDST_GEOM_SINE_BUMP = 1, FDST_GEOM_ANNULUS = 2 };
-enum { FDST_VARIANT_PD = 0, FDST_VARIANT_PD_GEO = 1 };      /* P_D (Sec. 5) or P_D^G (Sec. 6) */
+/* P_D (Sec. 5) or P_D^G (Sec. 6): P_D^G needs a mapped geometry (3D TH) or the
+ * viscosity family on the identity map (3D TH or RT); with a constant viscosity
+ * on the identity map it equals P_D and setup returns FDST_NOT_SUPPORTED. */
+enum { FDST_VARIANT_PD = 0, FDST_VARIANT_PD_GEO = 1 };
 /* Matvec arithmetic: FP64 (DFMA), or double-float (each value an unevaluated
  * sum of two floats, 48-bit significand, error-free FMA products and TwoSum
  * additions on the FP32 units). fdst_solve ends on a true residual computed
@@ -89,9 +92,15 @@ typedef struct {
   int max_rhs;             /* most right-hand sides one call will pass (workspace sizing), >= 1 */
   int matvec_precision;    /* FDST_MV_F64 or FDST_MV_DF64 */
   double geometry_amplitude;  /* sine-bump amplitude a, in (0, 0.25]; <= 0 selects 0.1; ignored by the annulus */
-  double viscosity_contrast;  /* mapped geometry: k >= 1 selects nu(x) = 1 + (k - 1)(1 - cos(2 pi x1)) / 2
-                                 (values in [1, k]); <= 0 selects the map's own field: nu(x) = 1 + 0.5
-                                 sin(2 pi x1) cos(2 pi x2) on the sine bump, nu = 1 on the annulus */
+  double viscosity_contrast;  /* k >= 1 selects nu(x) = 1 + (k - 1)(1 - cos(2 pi x1)) / 2 (values in
+                                 [1, k]); <= 0: on a mapped geometry the map's own field (nu(x) = 1 +
+                                 0.5 sin(2 pi x1) cos(2 pi x2) on the sine bump, nu = 1 on the annulus),
+                                 on the identity map the constant `viscosity`. On the identity map (3D,
+                                 TH or RT) the family depends on eta_1 alone: the operator stays a sum of
+                                 Kronecker products, each A-block term's direction-1 factor weighted by
+                                 nu (the RT Nitsche faces included), and FDST_VARIANT_PD_GEO builds the
+                                 Appendix's weighted pencils for it (RT: K~ with tau(0), tau(1)).
+                                 0 < k < 1 is FDST_INVALID_ARGUMENT; k >= 1 in 2D FDST_NOT_SUPPORTED */
   int matvec_form;         /* mapped geometry: FDST_MATVEC_ASSEMBLED (CSR) or FDST_MATVEC_MATRIX_FREE
                               (no CSR: the operator, its B and B^T parts and diag(A) by sum
                               factorization at the quadrature points, FP64 for the true residual);

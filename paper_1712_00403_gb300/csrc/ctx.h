@@ -43,6 +43,7 @@ struct BandDev {
   int *lo;
   float2 *vals_df;   // the same values split into FP32 pairs (double-float matvec)
   std::vector<double> hvals;   // host copy of vals (rows x w)
+  std::vector<double> hdiag;   // host copy of the diagonal A(i, i), i < min(rows, cols)
 };
 
 // One Kronecker term of the operator: block dst += coef (F2 x F1 x F0) block src.

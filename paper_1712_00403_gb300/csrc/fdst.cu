@@ -416,6 +416,7 @@ static fdst_status band_from_mat(fdst_ctx *h, const Mat &A, int *id) {
   }
   TRY(upload(h, &b.vals_df, vdf));
   b.hvals = vals;
+  for (int i = 0; i < std::min(A.rows, A.cols); ++i) b.hdiag.push_back(A(i, i));
   *id = (int)h->bands.size();
   h->bands.push_back(b);
   return FDST_OK;
@@ -423,15 +424,33 @@ static fdst_status band_from_mat(fdst_ctx *h, const Mat &A, int *id) {
 
 static fdst_status build_matvec(fdst_ctx *h) {
   const int dim = h->dim, p = h->p, npts = p + 2;
-  const double nu = h->desc.viscosity > 0.0 ? h->desc.viscosity : 1.0;
+  // The one-coordinate viscosity family on the identity map: nu(eta_1) multiplies every
+  // integrand of a (and sigma), so each A-block term's direction-1 factor is weighted by
+  // nu at the quadrature points, and its Nitsche boundary values by nu(0), nu(1).
+  const bool nu_field = h->desc.geometry == FDST_GEOM_IDENTITY && h->desc.viscosity_contrast >= 1.0;
+  const double nu = nu_field ? 1.0 : (h->desc.viscosity > 0.0 ? h->desc.viscosity : 1.0);
+  std::vector<double> nu_w;
+  double nu0 = 1.0, nu1 = 1.0;
+  if (nu_field) {
+    std::vector<double> x, w;
+    span_rule(h->pres[0].knots, npts, x, w);
+    for (double e : x) nu_w.push_back(contrast_viscosity(e, h->desc.viscosity_contrast));
+    nu0 = contrast_viscosity(0.0, h->desc.viscosity_contrast);
+    nu1 = contrast_viscosity(1.0, h->desc.viscosity_contrast);
+  }
   std::map<std::string, int> band_ids;
-  // factor key -> band id; builds int_0^1 b_a^(da) b_b^(db) (stiffness with Nitsche when both da=db=1 and same space)
-  auto band_of = [&](const Space1D &sa, int da, const Space1D &sb, int db, int *id) -> fdst_status {
-    std::string key = space_key(sa) + "#" + std::to_string(da) + "#" + space_key(sb) + "#" + std::to_string(db);
+  // factor key -> band id; builds int_0^1 [nu] b_a^(da) b_b^(db) (stiffness with Nitsche when both
+  // da=db=1 and same space); weighted: the nu(eta_1) weight of direction 1
+  auto band_of = [&](const Space1D &sa, int da, const Space1D &sb, int db, bool weighted, int *id) -> fdst_status {
+    std::string key = space_key(sa) + "#" + std::to_string(da) + "#" + space_key(sb) + "#" + std::to_string(db) +
+                      (weighted ? "#nu" : "");
     auto it = band_ids.find(key);
     if (it != band_ids.end()) { *id = it->second; return FDST_OK; }
-    Mat A = (da == 1 && db == 1 && space_key(sa) == space_key(sb)) ? stiffness_matrix(sa, npts)
-                                                                    : mixed_matrix(sa, da, sb, db, npts);
+    static const std::vector<double> none;
+    const std::vector<double> &wt = weighted ? nu_w : none;
+    Mat A = (da == 1 && db == 1 && space_key(sa) == space_key(sb))
+                ? stiffness_matrix(sa, npts, wt, weighted ? nu0 : 1.0, weighted ? nu1 : 1.0)
+                : mixed_matrix(sa, da, sb, db, npts, wt);
     TRY(band_from_mat(h, A, id));
     band_ids[key] = *id;
     return FDST_OK;
@@ -444,7 +463,7 @@ static fdst_status build_matvec(fdst_ctx *h) {
           Term t{r, s, nu * (d == r ? 2.0 : 1.0), {-1, -1, -1}};
           for (int e = 0; e < dim; ++e) {
             const Space1D &sp = h->vel[r][e];
-            TRY(band_of(sp, e == d, sp, e == d, &t.f[e]));
+            TRY(band_of(sp, e == d, sp, e == d, nu_field && e == 0, &t.f[e]));
           }
           terms.push_back(t);
         }
@@ -452,18 +471,18 @@ static fdst_status build_matvec(fdst_ctx *h) {
         // [A_rs]_{ij} = nu int d_s B_i d_r B_j: direction s: (b_i)' b_j, direction r: b_i (b_j)'
         Term t{r, s, nu, {-1, -1, -1}};
         for (int e = 0; e < dim; ++e)
-          TRY(band_of(h->vel[r][e], e == s, h->vel[s][e], e == r, &t.f[e]));
+          TRY(band_of(h->vel[r][e], e == s, h->vel[s][e], e == r, nu_field && e == 0, &t.f[e]));
         terms.push_back(t);
       }
     }
     // B_r^T p: direction r: (b^v)' b^p, others b^v b^p ; coefficient -1
     Term t{r, dim, -1.0, {-1, -1, -1}};
-    for (int e = 0; e < dim; ++e) TRY(band_of(h->vel[r][e], e == r, h->pres[e], 0, &t.f[e]));
+    for (int e = 0; e < dim; ++e) TRY(band_of(h->vel[r][e], e == r, h->pres[e], 0, false, &t.f[e]));
     terms.push_back(t);
   }
   for (int r = 0; r < dim; ++r) {
     Term t{dim, r, -1.0, {-1, -1, -1}};
-    for (int e = 0; e < dim; ++e) TRY(band_of(h->pres[e], 0, h->vel[r][e], e == r, &t.f[e]));
+    for (int e = 0; e < dim; ++e) TRY(band_of(h->pres[e], 0, h->vel[r][e], e == r, false, &t.f[e]));
     terms.push_back(t);
   }
   h->terms = terms;
@@ -1227,8 +1246,20 @@ fdst_status fdst_setup(const fdst_desc *desc, fdst_handle *out) {
     set_error("unknown preconditioner variant");
     return FDST_INVALID_ARGUMENT;
   }
-  if (desc->variant == FDST_VARIANT_PD_GEO && desc->geometry == FDST_GEOM_IDENTITY) {
-    set_error("P_D^G is built for the mapped geometry (on the identity map it equals P_D)");
+  if (desc->geometry == FDST_GEOM_IDENTITY && desc->viscosity_contrast > 0.0) {
+    if (desc->viscosity_contrast < 1.0) {
+      set_error("viscosity_contrast must be >= 1 (or <= 0 for a constant viscosity)");
+      return FDST_INVALID_ARGUMENT;
+    }
+    if (desc->dim != 3) {
+      set_error("the viscosity family on the identity map is built in 3D");
+      return FDST_NOT_SUPPORTED;
+    }
+  }
+  if (desc->variant == FDST_VARIANT_PD_GEO && desc->geometry == FDST_GEOM_IDENTITY &&
+      !(desc->viscosity_contrast >= 1.0)) {
+    set_error("P_D^G on the identity map needs the viscosity family (viscosity_contrast >= 1); "
+              "with a constant viscosity it equals P_D");
     return FDST_NOT_SUPPORTED;
   }
   if (desc->matvec_form != FDST_MATVEC_ASSEMBLED && desc->matvec_form != FDST_MATVEC_MATRIX_FREE) {
@@ -1263,16 +1294,20 @@ fdst_status fdst_setup(const fdst_desc *desc, fdst_handle *out) {
   auto fail = [&](fdst_status s) { fdst_destroy(h.release()); return s; };
   if ((st = build_spaces(hp)) != FDST_OK) return fail(st);
   if (desc->geometry != FDST_GEOM_IDENTITY && (st = build_mapped_pre(hp)) != FDST_OK) return fail(st);
+  if (!hp->mapped && (st = build_matvec(hp)) != FDST_OK) return fail(st);
+  if (desc->geometry == FDST_GEOM_IDENTITY && desc->variant == FDST_VARIANT_PD_GEO &&
+      (st = build_identity_geo(hp)) != FDST_OK)
+    return fail(st);
   if (hp->mapped && desc->matvec_form == FDST_MATVEC_MATRIX_FREE) {
     if ((st = build_matrix_free(hp)) != FDST_OK) return fail(st);
     if (desc->variant == FDST_VARIANT_PD_GEO && (st = mf_velocity_scaling(hp)) != FDST_OK) return fail(st);
   }
   if ((st = build_fd(hp)) != FDST_OK) return fail(st);
-  if (hp->mapped && (st = build_mapped_post(hp)) != FDST_OK) return fail(st);
+  if ((hp->mapped || desc->variant == FDST_VARIANT_PD_GEO) && (st = build_mapped_post(hp)) != FDST_OK)
+    return fail(st);
   if (desc->fd_precision != FDST_FD_F64) {
     if ((st = tc_prepare(hp)) != FDST_OK) return fail(st);
   }
-  if (!hp->mapped && (st = build_matvec(hp)) != FDST_OK) return fail(st);
   const size_t nv = (size_t)hp->n_total * hp->max_rhs;
   if ((st = dalloc(hp, &hp->work[0], nv)) != FDST_OK) return fail(st);
   if ((st = dalloc(hp, &hp->work[1], nv)) != FDST_OK) return fail(st);

@@ -54,6 +54,122 @@ void overlap_ranges(const std::vector<int> &relo, const std::vector<int> &rehi, 
 }
 }  // namespace
 
+// Separable fit of the nine diagonal coefficients c^k_jj of C_k at the
+// quadrature points gp (Appendix: log c ~ f_1 + f_2 + f_3 by Diliberto-Straus
+// midrange sweeps), normalized so that each fit's two non-own factors have
+// zero mean log; tau^k_d = exp(f^{k,d}_d), mu^k_d = exp(mean over j != d of
+// f^{k,j}_d). Fills geo_K, geo_M with the weighted pencils. For a Nitsche
+// (RT tangential) factor the K~ boundary terms take tau^k_d at eta_d = 0 and 1:
+// the fit's own direction-d update evaluated on those faces (the midrange over
+// the face points of log c^k_dd minus the other two factors), which leaves the
+// fit at the quadrature points unchanged.
+fdst_status fit_pencils(fdst_ctx *h, const GeoPoints &gp, int kind, double amp, double contrast, cudaStream_t st) {
+  const int nq = h->p + 2;
+  const int fstride = std::max(gp.nq[0], std::max(gp.nq[1], gp.nq[2]));
+  double *L = nullptr, *f = nullptr;
+  CK(cudaMalloc(&L, sizeof(double) * 9 * gp.Q));
+  if (cudaMalloc(&f, sizeof(double) * 27 * fstride) != cudaSuccess) {
+    cudaFree(L);
+    set_error("cudaMalloc failed for the separable fit");
+    return FDST_OUT_OF_MEMORY;
+  }
+  cudaMemset(f, 0, sizeof(double) * 27 * fstride);
+  launch_logc(gp, L, st);
+  for (int sw = 0; sw < kSweeps; ++sw)
+    for (int d = 0; d < 3; ++d) launch_fit_sweep(L, f, d, gp, fstride, st);
+  std::vector<double> fh((size_t)27 * fstride);
+  cudaError_t e1 = cudaMemcpy(fh.data(), f, sizeof(double) * fh.size(), cudaMemcpyDeviceToHost);
+  cudaFree(L);
+  cudaFree(f);
+  if (e1 != cudaSuccess) {
+    set_error(std::string("separable fit: ") + cudaGetErrorString(e1));
+    return FDST_CUDA_ERROR;
+  }
+  auto F = [&](int k, int j, int d) -> double * { return fh.data() + (size_t)((3 * k + j) * 3 + d) * fstride; };
+  for (int k = 0; k < 3; ++k)
+    for (int j = 0; j < 3; ++j)
+      for (int d = 0; d < 3; ++d) {
+        if (d == j) continue;
+        double m = 0.0;
+        for (int t = 0; t < gp.nq[d]; ++t) m += F(k, j, d)[t];
+        m /= gp.nq[d];
+        for (int t = 0; t < gp.nq[d]; ++t) F(k, j, d)[t] -= m;
+        for (int t = 0; t < gp.nq[j]; ++t) F(k, j, j)[t] += m;
+      }
+  // tau^k_d on the faces eta_d = 0 and 1 (needed by Nitsche factors only)
+  double tau_end[3][3][2];
+  for (int k = 0; k < 3; ++k)
+    for (int d = 0; d < 3; ++d) tau_end[k][d][0] = tau_end[k][d][1] = 1.0;
+  bool any_nitsche = false;
+  for (int k = 0; k < 3; ++k)
+    for (int d = 0; d < 3; ++d) any_nitsche = any_nitsche || h->vel[k][d].nitsche;
+  for (int d = 0; d < 3 && any_nitsche; ++d)
+    for (int side = 0; side < 2; ++side) {
+      GeoPoints fp;
+      for (int e = 0; e < 3; ++e) {
+        fp.nq[e] = e == d ? 1 : gp.nq[e];
+        fp.pts[e] = gp.pts[e];
+        fp.wts[e] = gp.wts[e];
+      }
+      const double t = side;
+      double *tp = nullptr, *buf = nullptr;
+      fp.Q = (int64_t)fp.nq[0] * fp.nq[1] * fp.nq[2];
+      CK(cudaMalloc(&tp, sizeof(double)));
+      if (cudaMalloc(&buf, sizeof(double) * 20 * fp.Q) != cudaSuccess) {
+        cudaFree(tp);
+        set_error("cudaMalloc failed for the face points of the separable fit");
+        return FDST_OUT_OF_MEMORY;
+      }
+      cudaMemcpy(tp, &t, sizeof(double), cudaMemcpyHostToDevice);
+      fp.pts[d] = tp;
+      fp.jinv = buf;
+      fp.det = buf + 9 * fp.Q;
+      fp.nu = buf + 10 * fp.Q;
+      double *Lf = buf + 11 * fp.Q;
+      launch_geo_points(fp, kind, amp, contrast, st);
+      launch_logc(fp, Lf, st);
+      std::vector<double> lh((size_t)9 * fp.Q);
+      cudaError_t e2 = cudaMemcpy(lh.data(), Lf, sizeof(double) * lh.size(), cudaMemcpyDeviceToHost);
+      cudaFree(tp);
+      cudaFree(buf);
+      if (e2 != cudaSuccess) {
+        set_error(std::string("separable fit (faces): ") + cudaGetErrorString(e2));
+        return FDST_CUDA_ERROR;
+      }
+      const int da = d == 0 ? 1 : 0, db = d == 2 ? 1 : 2;
+      for (int k = 0; k < 3; ++k) {
+        const double *Lk = lh.data() + (size_t)(3 * k + d) * fp.Q;
+        double mx = -INFINITY, mn = INFINITY;
+        for (int64_t q = 0; q < fp.Q; ++q) {
+          int qq[3];
+          qq[0] = (int)(q % fp.nq[0]);
+          qq[1] = (int)((q / fp.nq[0]) % fp.nq[1]);
+          qq[2] = (int)(q / ((int64_t)fp.nq[0] * fp.nq[1]));
+          const double r = Lk[q] - F(k, d, da)[qq[da]] - F(k, d, db)[qq[db]];
+          mx = std::max(mx, r);
+          mn = std::min(mn, r);
+        }
+        tau_end[k][d][side] = std::exp(0.5 * (mx + mn));
+      }
+    }
+  h->geo_K.assign(3, std::vector<Mat>(3));
+  h->geo_M.assign(3, std::vector<Mat>(3));
+  for (int k = 0; k < 3; ++k)
+    for (int d = 0; d < 3; ++d) {
+      std::vector<double> tau(gp.nq[d]), mu(gp.nq[d]);
+      for (int t = 0; t < gp.nq[d]; ++t) {
+        tau[t] = std::exp(F(k, d, d)[t]);
+        double s = 0.0;
+        for (int j = 0; j < 3; ++j)
+          if (j != d) s += F(k, j, d)[t];
+        mu[t] = std::exp(0.5 * s);
+      }
+      h->geo_K[k][d] = stiffness_matrix(h->vel[k][d], nq, tau, tau_end[k][d][0], tau_end[k][d][1]);
+      h->geo_M[k][d] = mixed_matrix(h->vel[k][d], 0, h->vel[k][d], 0, nq, mu);
+    }
+  return FDST_OK;
+}
+
 // D_V^{-1/2} of P_D^G from diag(A) (the velocity entries of the block vector):
 // [D_V]_ii = A_ii / (P~_V)_ii with diag(P~_V) the Kronecker sum of the pencils' diagonals.
 void set_velocity_scaling(fdst_ctx *h, const std::vector<double> &diagA) {
@@ -118,55 +234,8 @@ fdst_status build_mapped_pre(fdst_ctx *h) {
   launch_geo_points(gp, h->desc.geometry == FDST_GEOM_ANNULUS ? kGeoAnnulus : kGeoSineBump, amp,
                     h->desc.viscosity_contrast, st);
   h->gp = gp;
-  // ---- separable fit of the 9 diagonal coefficients c^k_jj (log, midrange sweeps)
-  const int fstride = std::max(gp.nq[0], std::max(gp.nq[1], gp.nq[2]));
-  double *L = nullptr, *f = nullptr;
-  CK(cudaMalloc(&L, sizeof(double) * 9 * gp.Q));
-  if (cudaMalloc(&f, sizeof(double) * 27 * fstride) != cudaSuccess) {
-    cudaFree(L);
-    set_error("cudaMalloc failed for the separable fit");
-    return FDST_OUT_OF_MEMORY;
-  }
-  cudaMemset(f, 0, sizeof(double) * 27 * fstride);
-  launch_logc(gp, L, st);
-  for (int sw = 0; sw < kSweeps; ++sw)
-    for (int d = 0; d < 3; ++d) launch_fit_sweep(L, f, d, gp, fstride, st);
-  std::vector<double> fh((size_t)27 * fstride);
-  cudaError_t e1 = cudaMemcpy(fh.data(), f, sizeof(double) * fh.size(), cudaMemcpyDeviceToHost);
-  cudaFree(L);
-  cudaFree(f);
-  if (e1 != cudaSuccess) {
-    set_error(std::string("separable fit: ") + cudaGetErrorString(e1));
-    return FDST_CUDA_ERROR;
-  }
-  // normalize each fit: the two non-own factors get zero mean log, the constant goes to the own one;
-  // tau^k_d = exp(f^{k,d}_d), mu^k_d = exp(mean over j != d of f^{k,j}_d)
-  auto F = [&](int k, int j, int d) -> double * { return fh.data() + (size_t)((3 * k + j) * 3 + d) * fstride; };
-  for (int k = 0; k < 3; ++k)
-    for (int j = 0; j < 3; ++j)
-      for (int d = 0; d < 3; ++d) {
-        if (d == j) continue;
-        double m = 0.0;
-        for (int t = 0; t < gp.nq[d]; ++t) m += F(k, j, d)[t];
-        m /= gp.nq[d];
-        for (int t = 0; t < gp.nq[d]; ++t) F(k, j, d)[t] -= m;
-        for (int t = 0; t < gp.nq[j]; ++t) F(k, j, j)[t] += m;
-      }
-  h->geo_K.assign(3, std::vector<Mat>(3));
-  h->geo_M.assign(3, std::vector<Mat>(3));
-  for (int k = 0; k < 3; ++k)
-    for (int d = 0; d < 3; ++d) {
-      std::vector<double> tau(gp.nq[d]), mu(gp.nq[d]);
-      for (int t = 0; t < gp.nq[d]; ++t) {
-        tau[t] = std::exp(F(k, d, d)[t]);
-        double s = 0.0;
-        for (int j = 0; j < 3; ++j)
-          if (j != d) s += F(k, j, d)[t];
-        mu[t] = std::exp(0.5 * s);
-      }
-      h->geo_K[k][d] = stiffness_matrix(h->vel[k][d], nq, tau);
-      h->geo_M[k][d] = mixed_matrix(h->vel[k][d], 0, h->vel[k][d], 0, nq, mu);
-    }
+  TRY(fit_pencils(h, gp, h->desc.geometry == FDST_GEOM_ANNULUS ? kGeoAnnulus : kGeoSineBump, amp,
+                  h->desc.viscosity_contrast, st));
   // ---- element tables per direction
   MeshTables mt;
   mt.nq = nq;
@@ -313,6 +382,89 @@ fdst_status build_mapped_pre(fdst_ctx *h) {
     }
   }
   CK(cudaStreamSynchronize(st));
+  return FDST_OK;
+}
+
+double contrast_viscosity(double eta1, double k) {
+  const double pi = 3.14159265358979323846;
+  return 1.0 + (k - 1.0) * (1.0 - std::cos(2.0 * pi * eta1)) * 0.5;
+}
+
+// P_D^G on the identity map with the one-coordinate viscosity family (3D, TH or
+// RT): the fit of diag(C_k) at the quadrature points (C_k^RT = C_k^TH = nu (I +
+// e_k e_k^T) on this map, eq. Q_TH / Q_RT), the weighted pencils, and the
+// scalings D_V = diag(A) / diag(P~_V) (diag(A) from the operator's Kronecker
+// terms, the Nitsche terms included) and D_Q = diag(Q) / diag(P_Q), Q the
+// 1/nu-weighted pressure mass (Sec. 6). Needs the operator's terms (build_matvec).
+fdst_status build_identity_geo(fdst_ctx *h) {
+  const int nq = h->p + 2;
+  const double contrast = h->desc.viscosity_contrast;
+  cudaStream_t st = 0;
+  GeoPoints gp;
+  std::vector<std::vector<double>> px(3), pw(3);
+  std::vector<double *> owned;
+  auto release = [&]() {
+    for (double *q : owned) cudaFree(q);
+    owned.clear();
+  };
+  for (int d = 0; d < 3; ++d) {
+    span_rule(h->pres[d].knots, nq, px[d], pw[d]);
+    gp.nq[d] = (int)px[d].size();
+    double *dp = nullptr;
+    if (cudaMalloc(&dp, sizeof(double) * 2 * px[d].size()) != cudaSuccess) {
+      release();
+      set_error("cudaMalloc failed for the quadrature points");
+      return FDST_OUT_OF_MEMORY;
+    }
+    owned.push_back(dp);
+    cudaMemcpy(dp, px[d].data(), sizeof(double) * px[d].size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(dp + px[d].size(), pw[d].data(), sizeof(double) * px[d].size(), cudaMemcpyHostToDevice);
+    gp.pts[d] = dp;
+    gp.wts[d] = dp + px[d].size();
+  }
+  gp.Q = (int64_t)gp.nq[0] * gp.nq[1] * gp.nq[2];
+  double *buf = nullptr;
+  if (cudaMalloc(&buf, sizeof(double) * 11 * gp.Q) != cudaSuccess) {
+    release();
+    set_error("cudaMalloc failed for the geometry at the quadrature points");
+    return FDST_OUT_OF_MEMORY;
+  }
+  owned.push_back(buf);
+  gp.jinv = buf;
+  gp.det = buf + 9 * gp.Q;
+  gp.nu = buf + 10 * gp.Q;
+  // the sine bump with amplitude 0 is the identity map (J = I, det J = 1)
+  launch_geo_points(gp, kGeoSineBump, 0.0, contrast, st);
+  fdst_status s = fit_pencils(h, gp, kGeoSineBump, 0.0, contrast, st);
+  release();
+  TRY(s);
+  // diag(A) of the velocity blocks from the Kronecker terms dst = src = k
+  std::vector<double> diagA(h->n_total, 0.0);
+  for (const Term &t : h->terms) {
+    if (t.dst != t.src || t.dst >= 3) continue;
+    const int k = t.dst;
+    const int n1 = h->shape[k][0], n2 = h->shape[k][1], n3 = h->shape[k][2];
+    const std::vector<double> &d0 = h->bands[t.f[0]].hdiag, &d1 = h->bands[t.f[1]].hdiag, &d2 = h->bands[t.f[2]].hdiag;
+    for (int i3 = 0; i3 < n3; ++i3)
+      for (int i2 = 0; i2 < n2; ++i2)
+        for (int i1 = 0; i1 < n1; ++i1)
+          diagA[h->off[k] + ((size_t)i3 * n2 + i2) * n1 + i1] += t.coef * d0[i1] * d1[i2] * d2[i3];
+  }
+  h->geo_scale.assign(4, std::vector<double>());
+  set_velocity_scaling(h, diagA);
+  // D_Q: Q = M_1^{1/nu} (x) M_2 (x) M_3 on this map, P_Q = M_1 (x) M_2 (x) M_3
+  std::vector<double> x1, w1, inv_nu;
+  span_rule(h->pres[0].knots, nq, x1, w1);
+  for (double e : x1) inv_nu.push_back(1.0 / contrast_viscosity(e, contrast));
+  const Mat Mq = mixed_matrix(h->pres[0], 0, h->pres[0], 0, nq, inv_nu);
+  const Mat M0 = mixed_matrix(h->pres[0], 0, h->pres[0], 0, nq);
+  const int n1 = h->shape[3][0], n2 = h->shape[3][1], n3 = h->shape[3][2];
+  std::vector<double> &sc = h->geo_scale[3];
+  sc.resize((size_t)n1 * n2 * n3);
+  for (size_t li = 0; li < sc.size(); ++li) {
+    const int i1 = (int)(li % n1);
+    sc[li] = 1.0 / std::sqrt(Mq(i1, i1) / M0(i1, i1));
+  }
   return FDST_OK;
 }
 
