@@ -332,9 +332,12 @@ fdst_status fdst_fd_apply_static(int dim, const int n[3], const double *const d_
  * a CUDA graph. The handles must share fd_precision and matvec_precision and
  * use the identity geometry; a handle may belong to one batch at a time and
  * must not be used on its own while the batch solves (the batch uses the
- * handle's workspace). autotune != 0 times the tensor-core pipeline depth and
- * the banded-kernel block size on the batch's own shapes at creation and
- * keeps the fastest (fdst_batch_info reports them).
+ * handle's workspace). autotune != 0 times, on the batch's own shapes at
+ * creation, how each contraction step's tensor-core launch is fed (B streamed
+ * with A at each ring depth that fits, B resident in shared memory, A's TF32
+ * pieces in tensor memory) and the banded-kernel block size, and keeps the
+ * fastest of each (fdst_batch_info, fdst_batch_tuning report them); without it
+ * B is streamed at the deepest ring that fits.
  */
 typedef struct fdst_batch_ctx *fdst_batch;
 fdst_status fdst_batch_create(const fdst_handle *handles, int n, int autotune, fdst_batch *out);
@@ -343,6 +346,17 @@ fdst_status fdst_batch_create(const fdst_handle *handles, int n, int autotune, f
 fdst_status fdst_batch_solve(fdst_batch b, const double *const *d_b, double *const *d_x, double tol, int maxit,
                              fdst_solve_info *info, fdst_stream stream);
 fdst_status fdst_batch_info(fdst_batch b, int *tc_ring, int *band_threads, double *ms_apply, double *ms_matvec);
+/* The autotuner's choice per contraction step: *nsteps = the number of steps;
+ * for the first min(cap, *nsteps) steps modes[i] = 1 (B streamed), 2 (B
+ * resident, A in shared memory) or 3 (B resident, A in tensor memory) and
+ * rings[i] = the ring depth (0 = as deep as fits); both 0 for an FP64 batch.
+ * Arrays are caller-owned host memory of cap entries (cap = 0 queries nsteps). */
+fdst_status fdst_batch_tuning(fdst_batch b, int cap, int *nsteps, int *modes, int *rings);
+/* Sets the feeding mode and ring depth of every contraction step (n = the
+ * number of steps, modes and rings as above, host arrays read during the call).
+ * FDST_NOT_SUPPORTED (nothing changed) when a mode does not fit a step's shapes
+ * or the batch is FP64; FDST_INVALID_ARGUMENT for other values. */
+fdst_status fdst_batch_set_tuning(fdst_batch b, int n, const int *modes, const int *rings);
 fdst_status fdst_batch_destroy(fdst_batch b);
 
 /*

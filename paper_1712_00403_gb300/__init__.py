@@ -30,6 +30,9 @@ STATUS = {0: "OK", 1: "INVALID_ARGUMENT", 2: "NOT_SPD", 3: "OUT_OF_MEMORY", 4: "
           11: "NOT_SUPPORTED", 12: "CANCELLED"}
 
 
+BATCH_MODES = {0: "fp64", 1: "streamed", 2: "resident_b", 3: "resident_b_tmem_a"}
+
+
 class FdstError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{STATUS.get(code, code)}: {msg}")
@@ -65,7 +68,7 @@ class SolveInfo(ctypes.Structure):
 
 ENTRY_POINTS = ["fdst_setup", "fdst_destroy", "fdst_get_sizes", "fdst_apply_prec", "fdst_matvec", "fdst_solve",
                 "fdst_solve_host", "fdst_solve_host_zero", "fdst_apply_prec_host", "fdst_solve_gmres", "fdst_apply_block_prec", "fdst_set_timing", "fdst_get_timing", "fdst_get_kernel_timing", "fdst_convert",
-                "fdst_fd_apply_static", "fdst_batch_create", "fdst_batch_solve", "fdst_batch_info",
+                "fdst_fd_apply_static", "fdst_batch_create", "fdst_batch_solve", "fdst_batch_info", "fdst_batch_tuning", "fdst_batch_set_tuning",
                 "fdst_batch_destroy", "fdst_server_create", "fdst_server_submit", "fdst_server_step",
                 "fdst_server_result", "fdst_server_stats", "fdst_server_cancel", "fdst_server_destroy",
                 "fdst_check_bounded_wait", "fdst_device_error", "fdst_inject_alloc_failure",
@@ -100,6 +103,8 @@ def load_library(path=LIB_PATH):
     lib.fdst_batch_create.argtypes = [ctypes.POINTER(vp), i, i, ctypes.POINTER(vp)]
     lib.fdst_batch_solve.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), d, i, ctypes.POINTER(SolveInfo), vp]
     lib.fdst_batch_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(d), ctypes.POINTER(d)]
+    lib.fdst_batch_tuning.argtypes = [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
+    lib.fdst_batch_set_tuning.argtypes = [vp, i, ctypes.POINTER(i), ctypes.POINTER(i)]
     lib.fdst_batch_destroy.argtypes = [vp]
     lib.fdst_server_create.argtypes = [ctypes.POINTER(ServerOpts), ctypes.POINTER(vp)]
     lib.fdst_server_submit.argtypes = [vp, ctypes.POINTER(Desc), vp, d, ctypes.POINTER(i64)]
@@ -379,7 +384,22 @@ class Batch:
     def info(self):
         r, t, a, m = ctypes.c_int(), ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
         _check(_lib.fdst_batch_info(self._b, ctypes.byref(r), ctypes.byref(t), ctypes.byref(a), ctypes.byref(m)))
-        return dict(tc_ring=r.value, band_threads=t.value, ms_apply=a.value, ms_matvec=m.value)
+        n = ctypes.c_int()
+        _check(_lib.fdst_batch_tuning(self._b, 0, ctypes.byref(n), None, None))
+        modes, rings = (ctypes.c_int * max(1, n.value))(), (ctypes.c_int * max(1, n.value))()
+        _check(_lib.fdst_batch_tuning(self._b, n.value, ctypes.byref(n), modes, rings))
+        return dict(tc_ring=r.value, band_threads=t.value, ms_apply=a.value, ms_matvec=m.value,
+                    step_modes=[BATCH_MODES[modes[k]] for k in range(n.value)], step_rings=list(rings[:n.value]))
+
+    def set_tuning(self, modes, rings):
+        """Feeding mode ("streamed", "resident_b", "resident_b_tmem_a") and ring depth
+        (0 = as deep as fits) of every contraction step."""
+        codes = {v: k for k, v in BATCH_MODES.items()}
+        if len(modes) != len(rings) or any(m not in codes or codes[m] == 0 for m in modes):
+            raise ValueError("modes: one of streamed / resident_b / resident_b_tmem_a per step, rings alike")
+        n = len(modes)
+        cm, cr = (ctypes.c_int * max(1, n))(*[codes[m] for m in modes]), (ctypes.c_int * max(1, n))(*rings)
+        _check(_lib.fdst_batch_set_tuning(self._b, n, cm, cr))
 
     def solve(self, bs, xs, tol=1e-8, maxit=1000, stream=None):
         n = len(self.problems)

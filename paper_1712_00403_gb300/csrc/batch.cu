@@ -9,8 +9,10 @@
 //     a table of per-problem segments.
 // Pointers never change between iterations (in-place Lanczos/direction
 // shifts), so one iteration is captured into a CUDA graph and replayed. An
-// autotuner times the tensor-core ring depth and the banded-kernel block size
-// on the batch's own shapes and keeps the fastest.
+// autotuner times, per contraction step, how the tensor-core kernel is fed (B
+// streamed with A at each ring depth, B resident in shared memory, A's TF32
+// pieces in tensor memory) and the banded-kernel block size on the batch's own
+// shapes and keeps the fastest.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -193,6 +195,9 @@ struct fdst_batch_ctx {
   struct Step {
     void *tab = nullptr;
     int count = 0, maxR = 0, maxN = 0;
+    int bmax = 0;            // largest resident-B image among the step's problems
+    int mode = 1, ring = 0;  // feeding mode (TcGroup::mode; B streamed unless the autotuner picked
+                             // another) and ring depth (0: as many stages as fit)
   };
   std::vector<Step> steps;
   struct Round {
@@ -239,18 +244,29 @@ static dim3 seg_grid(const fdst_batch b) {
   return dim3((unsigned)blocks, (unsigned)b->n);
 }
 
+static TcGroup step_group(fdst_batch b, const fdst_batch_ctx::Step &S, int mode) {
+  TcGroup g;
+  g.split = b->hs[0]->desc.fd_precision == FDST_FD_BF16X6 ? 1 : 0;
+  g.table = static_cast<const TcProb *>(S.tab);
+  g.nprob = S.count;
+  g.maxR = S.maxR;
+  g.maxN = S.maxN;
+  g.bmax = S.bmax;
+  g.mode = mode;
+  g.convert = &S == &b->steps[0];
+  return g;
+}
+
+static fdst_status batch_step_apply(fdst_batch b, const fdst_batch_ctx::Step &S, cudaStream_t st, int mode, int ring) {
+  return launch_gemm_tc(step_group(b, S, mode), 1, nullptr, st, ring);
+}
+
+// ring < 0: each step's own autotuned mode and ring depth.
 static fdst_status batch_apply(fdst_batch b, cudaStream_t st, int ring) {
   for (auto &S : b->steps) {
     if (S.count == 0) continue;
     if (b->tc) {
-      TcGroup g;
-      g.split = b->hs[0]->desc.fd_precision == FDST_FD_BF16X6 ? 1 : 0;
-      g.table = static_cast<const TcProb *>(S.tab);
-      g.nprob = S.count;
-      g.maxR = S.maxR;
-      g.maxN = S.maxN;
-      g.convert = &S == &b->steps[0];
-      TRY(launch_gemm_tc(g, 1, nullptr, st, ring));
+      TRY(ring < 0 ? batch_step_apply(b, S, st, S.mode, S.ring) : batch_step_apply(b, S, st, 1, ring));
     } else {
       GemmGroup g;
       g.table = static_cast<const GemmProb *>(S.tab);
@@ -300,7 +316,7 @@ static fdst_status batch_iterate(fdst_batch b, int maxit, cudaStream_t st) {
   count_launch(4);
   k_bdot<<<dg, 256, 0, st>>>(b->segs, kAz, kZ, 1);
   k_blanczos<<<sg, 256, 0, st>>>(b->segs);
-  TRY(batch_apply(b, st, b->ring));
+  TRY(batch_apply(b, st, -1));
   k_bdot<<<dg, 256, 0, st>>>(b->segs, kV, kZNew, 2);
   k_bscalars<<<tb, 64, 0, st>>>(b->segs, b->n, maxit, b->n_stopped);
   count_launch(2);
@@ -310,7 +326,8 @@ static fdst_status batch_iterate(fdst_batch b, int maxit, cudaStream_t st) {
 }
 
 // Times candidate tensor-core ring depths and banded-kernel block sizes on the
-// batch's own tables and keeps the fastest of each.
+// batch's own tables and keeps the fastest of each: per contraction step the
+// feeding mode of B and A and the ring depth, and the banded block size.
 static fdst_status batch_autotune(fdst_batch b) {
   cudaStream_t st = b->bs;
   for (auto *h : b->hs) {
@@ -332,23 +349,28 @@ static fdst_status batch_autotune(fdst_batch b) {
     return ms / 2.0f;
   };
   if (b->tc) {
-    int maxring = 4;
+    // per contraction step: B streamed with A at each ring depth that fits, B resident
+    // with A in shared memory, B resident with A's TF32 pieces in tensor memory; a
+    // mode that does not fit the step's shapes is skipped
+    double total = 0.0;
+    int ring_min = 4;
     for (auto &S : b->steps) {
       if (S.count == 0) continue;
-      TcGroup g;
-      g.split = b->hs[0]->desc.fd_precision == FDST_FD_BF16X6 ? 1 : 0;
-      g.table = static_cast<const TcProb *>(S.tab);
-      g.nprob = S.count;
-      g.maxR = S.maxR;
-      g.maxN = S.maxN;
-      maxring = std::min(maxring, tc_max_ring(g));
+      const TcGroup g0 = step_group(b, S, 1);
+      float best = 1e30f;
+      auto consider = [&](int mode, int ring) {
+        if (tc_mode_fits(step_group(b, S, mode), ring) != FDST_OK) return;
+        const float ms = timed([&] { batch_step_apply(b, S, st, mode, ring); });
+        if (ms < best) { best = ms; S.mode = mode; S.ring = ring; }
+      };
+      for (int ring = 2; ring <= tc_max_ring(g0); ++ring) consider(1, ring);
+      consider(2, 0);
+      consider(3, 0);
+      total += best;
+      if (S.mode == 1) ring_min = std::min(ring_min, S.ring);
     }
-    float best = 1e30f;
-    for (int ring = 2; ring <= maxring; ++ring) {
-      float ms = timed([&] { batch_apply(b, st, ring); });
-      if (ms < best) { best = ms; b->ring = ring; }
-    }
-    b->ms_apply = best;
+    b->ring = ring_min;
+    b->ms_apply = total;
   } else {
     b->ms_apply = timed([&] { batch_apply(b, st, 0); });
   }
@@ -431,6 +453,7 @@ static fdst_status build_batch(fdst_batch b) {
           P.scale_in = first ? c.scale : nullptr;
           P.scale_out = last ? c.scale : nullptr;
           P.done_flag = h->done;
+          S.bmax = std::max(S.bmax, tc_b_tile_bytes(P.K, P.N, h->desc.fd_precision == FDST_FD_BF16X6 ? 1 : 0));
           tcp.push_back(P);
         } else {
           GemmProb P;
@@ -581,6 +604,7 @@ fdst_status batch_new(const std::vector<fdst_ctx *> &hs, int ring, int threads, 
     delete b;
     return st;
   }
+  for (auto &S : b->steps) S.ring = ring;
   *out = b;
   return FDST_OK;
 }
@@ -646,6 +670,41 @@ fdst_status fdst_batch_info(fdst_batch b, int *ring, int *threads, double *ms_ap
   if (threads) *threads = b->threads;
   if (ms_apply) *ms_apply = b->ms_apply;
   if (ms_matvec) *ms_matvec = b->ms_matvec;
+  return FDST_OK;
+}
+
+fdst_status fdst_batch_tuning(fdst_batch b, int cap, int *nsteps, int *modes, int *rings) {
+  if (!b || !nsteps) { set_error("NULL argument"); return FDST_INVALID_ARGUMENT; }
+  if (cap < 0 || (cap > 0 && (!modes || !rings))) { set_error("cap must be >= 0 with modes and rings given"); return FDST_INVALID_ARGUMENT; }
+  *nsteps = (int)b->steps.size();
+  for (int i = 0; i < *nsteps && i < cap; ++i) {
+    modes[i] = b->tc ? b->steps[i].mode : 0;
+    rings[i] = b->tc ? b->steps[i].ring : 0;
+  }
+  return FDST_OK;
+}
+
+fdst_status fdst_batch_set_tuning(fdst_batch b, int n, const int *modes, const int *rings) {
+  if (!b || !modes || !rings) { set_error("NULL argument"); return FDST_INVALID_ARGUMENT; }
+  if (!b->tc) { set_error("fdst_batch_set_tuning: FP64 batches have no tensor-core launches"); return FDST_NOT_SUPPORTED; }
+  if (n != (int)b->steps.size()) { set_error("fdst_batch_set_tuning: n must equal the number of steps"); return FDST_INVALID_ARGUMENT; }
+  for (int i = 0; i < n; ++i) {
+    if (modes[i] < 1 || modes[i] > 3 || rings[i] < 0) {
+      set_error("fdst_batch_set_tuning: modes in {1, 2, 3}, rings >= 0");
+      return FDST_INVALID_ARGUMENT;
+    }
+    const auto &S = b->steps[i];
+    if (S.count > 0) TRY(tc_mode_fits(step_group(b, S, modes[i]), rings[i]));
+  }
+  for (int i = 0; i < n; ++i) {
+    b->steps[i].mode = modes[i];
+    b->steps[i].ring = rings[i];
+  }
+  if (b->graph) {   // the captured iteration holds the old launches
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->graph_maxit = -1;
+  }
   return FDST_OK;
 }
 

@@ -90,6 +90,13 @@ static int tile_nt(int npad, int t) {
   return rest < kNTMax ? rest : kNTMax;
 }
 
+int tc_b_tile_bytes(int K, int N, int split) {
+  const int kp = tc_kpad(K, split), np = tc_npad(N), bpe = split ? SplitTraits<1>::kBPE : SplitTraits<0>::kBPE;
+  int b = 0;
+  for (int t = 0; t * kNTMax < np; ++t) b = std::max(b, bpe * tile_nt(np, t) * kp);
+  return b;
+}
+
 size_t tc_packed_bytes(int K, int N, int split) { return (split ? 6 : 8) * (size_t)tc_kpad(K, split) * tc_npad(N); }
 
 // Three bf16 pieces of a float by truncation: x = b0 + b1 + b2 up to the last
@@ -948,17 +955,14 @@ int tc_max_ring(const TcGroup &g) {
   return nring > 4 ? 4 : nring;
 }
 
-fdst_status launch_gemm_tc(const TcGroup &g, int nrhs, const int *done, cudaStream_t s, int ring) {
-  if (nrhs > kMaxRhsLaunch) {
-    // the kernel keeps the stop flags of its right-hand sides in shared memory
-    TcGroup h = g;
-    for (int r0 = 0; r0 < nrhs; r0 += kMaxRhsLaunch) {
-      h.rhs0 = g.rhs0 + r0;
-      const fdst_status st = launch_gemm_tc(h, std::min(kMaxRhsLaunch, nrhs - r0), done, s, ring);
-      if (st != FDST_OK) return st;
-    }
-    return FDST_OK;
-  }
+// The launch's shape: column tiles, tensor-memory columns, feeding mode (B
+// streamed or resident, A in shared or tensor memory), ring depth and shared
+// memory. Host-only; FDST_NOT_SUPPORTED when the requested mode does not fit.
+struct TcPlan {
+  int maxR, ntn, nt, ntc, bres, amode, tmem_cols, nring, smem;
+};
+
+static fdst_status tc_plan(const TcGroup &g, int ring, TcPlan &P) {
   int maxR, maxN;
   tc_dims(g, maxR, maxN);
   const int npad = tc_npad(maxN);
@@ -971,12 +975,10 @@ fdst_status launch_gemm_tc(const TcGroup &g, int nrhs, const int *done, cudaStre
   int nring = tc_max_ring(g);
   // resident B when the largest (problem, column tile) image fits beside two A stages
   int bres = 0;
-  if (!g.table) {
-    int bmax = 0;
-    for (int i = 0; i < g.nprob; ++i) {
-      const int kp = tc_kpad(g.p[i].K, g.split), np = tc_npad(g.p[i].N);
-      for (int t = 0; t * kNTMax < np; ++t) bmax = std::max(bmax, bpe * tile_nt(np, t) * kp);
-    }
+  int bmax = g.table ? g.bmax : 0;
+  if (!g.table)
+    for (int i = 0; i < g.nprob; ++i) bmax = std::max(bmax, tc_b_tile_bytes(g.p[i].K, g.p[i].N, g.split));
+  if (bmax > 0 && g.mode != 1) {
     const int nr = std::min(4, (kSmemBudget - 2048 - bmax) / astage);
     if (nr >= 2) {
       bres = (bmax + 1023) & ~1023;
@@ -984,22 +986,65 @@ fdst_status launch_gemm_tc(const TcGroup &g, int nrhs, const int *done, cudaStre
       stage_bytes = astage;
     }
   }
+  if ((g.mode == 2 || g.mode == 3) && bres == 0) {
+    set_error("tensor-core contraction: the resident B operand does not fit in shared memory");
+    return FDST_NOT_SUPPORTED;
+  }
   // split-TF32 with resident B: A's pieces go to tensor memory when both accumulators
   // (32-column multiples) and two 64-column A stages fit in its 512 columns
   int amode = 0, tmem_cols = 2 * ntc;
-  if (bres > 0 && !g.split && 2 * ((nt + 31) & ~31) + 128 <= 512) {
+  if (bres > 0 && !g.split && 2 * ((nt + 31) & ~31) + 128 <= 512 && g.mode != 2) {
     amode = 1;
     ntc = (nt + 31) & ~31;
     tmem_cols = 512;
     stage_bytes = kAHalfBytes;
     nring = std::min(4, (kSmemBudget - 2048 - bres) / kAHalfBytes);
   }
+  if (g.mode == 3 && !amode) {
+    set_error("tensor-core contraction: A in tensor memory needs split-TF32, resident B and N <= 192");
+    return FDST_NOT_SUPPORTED;
+  }
   if (ring > 0 && ring < nring) nring = ring;
   if (nring < 2) {
     set_error("tensor-core contraction: shared memory too small for two stages");
     return FDST_NOT_SUPPORTED;
   }
-  const int smem = nring * stage_bytes + bres + 1024 + 1024;
+  P.maxR = maxR;
+  P.ntn = ntn;
+  P.nt = nt;
+  P.ntc = ntc;
+  P.bres = bres;
+  P.amode = amode;
+  P.tmem_cols = tmem_cols;
+  P.nring = nring;
+  P.smem = nring * stage_bytes + bres + 1024 + 1024;
+  return FDST_OK;
+}
+
+fdst_status tc_mode_fits(const TcGroup &g, int ring) {
+  TcPlan P;
+  return tc_plan(g, ring, P);
+}
+
+fdst_status launch_gemm_tc(const TcGroup &g, int nrhs, const int *done, cudaStream_t s, int ring) {
+  if (nrhs > kMaxRhsLaunch) {
+    // the kernel keeps the stop flags of its right-hand sides in shared memory
+    TcGroup h = g;
+    for (int r0 = 0; r0 < nrhs; r0 += kMaxRhsLaunch) {
+      h.rhs0 = g.rhs0 + r0;
+      const fdst_status st = launch_gemm_tc(h, std::min(kMaxRhsLaunch, nrhs - r0), done, s, ring);
+      if (st != FDST_OK) return st;
+    }
+    return FDST_OK;
+  }
+  TcPlan P;
+  {
+    const fdst_status st = tc_plan(g, ring, P);
+    if (st != FDST_OK) return st;
+  }
+  const int maxR = P.maxR, ntn = P.ntn, nt = P.nt, ntc = P.ntc, bres = P.bres, amode = P.amode;
+  const int tmem_cols = P.tmem_cols, nring = P.nring;
+  const int smem = P.smem;
   static int configured[2] = {0, 0}, nsm = 0;
   static std::mutex init_mutex;
   std::lock_guard<std::mutex> lock(init_mutex);

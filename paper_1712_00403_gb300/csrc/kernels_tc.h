@@ -43,7 +43,16 @@ struct TcGroup {
   int convert = 0;                  // 1: convert A64 into A32 first (problems with A64 set)
   int split = 0;                    // 0: split-TF32 (hi/lo, 3 products); 1: split-BF16 (3 pieces, 6 products)
   int rhs0 = 0;                     // the launch covers right-hand sides rhs0 .. rhs0 + nrhs - 1
+  int bmax = 0;                     // with a table: largest B image of one (problem, column tile) in bytes
+                                    // (tc_b_tile_bytes; 0 = unknown: B is streamed)
+  int mode = 0;                     // how B and A are fed: 0 the launcher's choice (B resident in shared
+                                    // memory when it fits beside two A stages; for split-TF32 A's pieces
+                                    // in tensor memory when they fit too), 1 B streamed with A, 2 B resident
+                                    // with A in shared memory, 3 B resident with A in tensor memory; a mode
+                                    // that does not fit returns FDST_NOT_SUPPORTED
 };
+// Largest B image of one column tile of a K x N factor (the resident-B footprint).
+int tc_b_tile_bytes(int K, int N, int split);
 // Layout of one contraction step of a chain (rows R, contracted size K,
 // out_nv = size of the next contracted index): lda = K rounded up to 8 (TMA
 // pitch), ldv = out_nv rounded up to 8 (the next step's lda), c_cs = output
@@ -71,6 +80,9 @@ fdst_status tc_encode_map(void *map128, const float *A32, int K, int R, int lda,
 fdst_status launch_gemm_tc(const TcGroup &g, int nrhs, const int *done, cudaStream_t s, int ring = 0);
 // number of stages that fit for the widest column tile of g
 int tc_max_ring(const TcGroup &g);
+// FDST_OK when a launch of g with this ring depth (0 = as deep as fits) and g.mode fits
+// (host-only; the launch would return the same status).
+fdst_status tc_mode_fits(const TcGroup &g, int ring);
 
 // Host packing of B (K x N row-major FP64) into the kernel's per-stage
 // shared-memory image (SWIZZLE_32B K-major; TF32 hi/lo or three bf16 pieces
