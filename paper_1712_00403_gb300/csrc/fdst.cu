@@ -8,6 +8,7 @@
 #include <atomic>
 
 #include <algorithm>
+#include <tuple>
 #include <array>
 #include <cmath>
 #include <cstring>
@@ -358,6 +359,21 @@ static fdst_status build_plan(fdst_ctx *h, const std::vector<Term> &terms, std::
   // stage 2 then contracts l1 as the slowest index (mode 2 over (i0, l2, l1)) and
   // writes G in its usual (i0, i1, l2) order by swapping back
   plan_df = plan;
+  // ops of a stage ordered by band width (stable), so that a launch groups ops of one
+  // width (the banded kernel then unrolls its band loop fully); the accumulate flags
+  // follow the new order (the first op into each output of the stage stores)
+  std::stable_sort(plan_df.begin(), plan_df.end(), [&](const PlanOp &a, const PlanOp &b) {
+    if (a.stage != b.stage) return a.stage < b.stage;
+    return h->bands[a.band].w < h->bands[b.band].w;
+  });
+  {
+    std::map<std::tuple<int, int, int>, int> written;
+    for (auto &op : plan_df) {
+      int &wr = written[std::make_tuple(op.stage, op.out_kind, op.out_id)];
+      op.accumulate = wr;
+      wr = 1;
+    }
+  }
   if (dim == 3)
     for (auto &op : plan_df) {
       if (op.stage == 1) {
@@ -816,7 +832,8 @@ static fdst_status run_plan_df(fdst_ctx *h, const PlanView &V, const double *x, 
     BandGroupDF g;
     std::vector<std::pair<int, int>> outs;
     int stage = P[i].stage;
-    while (i < P.size() && P[i].stage == stage && g.nop < kMaxGroup) {
+    const int width = h->bands[P[i].band].w;
+    while (i < P.size() && P[i].stage == stage && g.nop < kMaxGroup && h->bands[P[i].band].w == width) {
       auto o = std::make_pair(P[i].out_kind, P[i].out_id);
       if (std::find(outs.begin(), outs.end(), o) != outs.end()) break;
       outs.push_back(o);

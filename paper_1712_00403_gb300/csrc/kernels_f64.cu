@@ -199,7 +199,9 @@ void launch_band(const BandGroup &g, int nrhs, const int *done, cudaStream_t s) 
 // address plus constant offsets. Work items run row-fastest so that warps in
 // flight share their X windows in L1/L2.
 // At most 256 threads per block and 64 registers per thread (4 blocks of 256 per SM).
-template <int T>
+// W > 0: every op of the launch has band width W (the band loops unroll fully,
+// so the loads take immediate offsets from a few base pointers); W = 0: any width.
+template <int T, int W>
 __global__ void __launch_bounds__(256, 4) k_band_df(BandGroupDF g, int nrhs, const int *done) {
   const int rhs = blockIdx.y;
   if (done && done[rhs]) return;
@@ -257,11 +259,23 @@ __global__ void __launch_bounds__(256, 4) k_band_df(BandGroupDF g, int nrhs, con
 #pragma unroll
       for (int t = 0; t < T; ++t) sh[t] = sl[t] = 0.0f;
       if (L0 + T <= lines) {
-#pragma unroll 2
-        for (int j = 0; j < w; ++j) {
-          const float2 v = vp[j];
+        if constexpr (W > 0) {
+          const float2 *xt[T];
 #pragma unroll
-          for (int t = 0; t < T; ++t) df_fma_acc(v, xp[t * d0 + j], sh[t], sl[t]);
+          for (int t = 0; t < T; ++t) xt[t] = xp + t * d0;
+#pragma unroll
+          for (int j = 0; j < W; ++j) {
+            const float2 v = vp[j];
+#pragma unroll
+            for (int t = 0; t < T; ++t) df_fma_acc(v, xt[t][j], sh[t], sl[t]);
+          }
+        } else {
+#pragma unroll 2
+          for (int j = 0; j < w; ++j) {
+            const float2 v = vp[j];
+#pragma unroll
+            for (int t = 0; t < T; ++t) df_fma_acc(v, xp[t * d0 + j], sh[t], sl[t]);
+          }
         }
         float2 yo[T];
 #pragma unroll
@@ -313,12 +327,22 @@ __global__ void __launch_bounds__(256, 4) k_band_df(BandGroupDF g, int nrhs, con
         // the whole chunk in one outer slab (warp-uniform): offsets 32 t from one base
         const unsigned p0 = c0 - o0 * P + lane;
         const float2 *xp = X + ((size_t)(o0 * din + l) * P + p0);
-#pragma unroll 4
-        for (int j = 0; j < w; ++j) {
-          const float2 v = vp[j];
+        if constexpr (W > 0) {
 #pragma unroll
-          for (int t = 0; t < T; ++t) df_fma_acc(v, xp[32 * t], sh[t], sl[t]);
-          xp += P;
+          for (int j = 0; j < W; ++j) {
+            const float2 v = vp[j];
+#pragma unroll
+            for (int t = 0; t < T; ++t) df_fma_acc(v, xp[32 * t], sh[t], sl[t]);
+            xp += P;
+          }
+        } else {
+#pragma unroll 4
+          for (int j = 0; j < w; ++j) {
+            const float2 v = vp[j];
+#pragma unroll
+            for (int t = 0; t < T; ++t) df_fma_acc(v, xp[32 * t], sh[t], sl[t]);
+            xp += P;
+          }
         }
         unsigned yoff[T];
         if (!swap || op.mode == 1) {
@@ -388,7 +412,22 @@ void launch_band_df(const BandGroupDF &g, int nrhs, const int *done, cudaStream_
   if (blocks < 1) blocks = 1;
   dim3 grid((unsigned)blocks, nrhs, g.nop);
   count_launch(1);
-  k_band_df<T><<<grid, thr, 0, s>>>(g, nrhs, done);
+  // the band width shared by every op of the launch (by value: from the ops; from a
+  // table: as the caller states), dispatched to a fully unrolled instantiation
+  int w = g.w;
+  if (!g.table) {
+    w = g.nop > 0 ? g.op[0].w : 0;
+    for (int i = 1; i < g.nop; ++i)
+      if (g.op[i].w != w) w = 0;
+  }
+  switch (w) {
+#define FDST_BAND_W(WW) \
+    case WW: k_band_df<T, WW><<<grid, thr, 0, s>>>(g, nrhs, done); break;
+    FDST_BAND_W(4) FDST_BAND_W(6) FDST_BAND_W(7) FDST_BAND_W(8) FDST_BAND_W(9) FDST_BAND_W(10)
+    FDST_BAND_W(11) FDST_BAND_W(13) FDST_BAND_W(14)
+#undef FDST_BAND_W
+    default: k_band_df<T, 0><<<grid, thr, 0, s>>>(g, nrhs, done); break;
+  }
 }
 
 // Two entries per thread with 16-byte accesses where the row start allows it
