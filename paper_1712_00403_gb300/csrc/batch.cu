@@ -19,6 +19,7 @@
 #include <cmath>
 #include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "ctx.h"
@@ -204,6 +205,7 @@ struct fdst_batch_ctx {
     void *tab = nullptr;
     int count = 0;
     int64_t maxt = 0;
+    int w = 0;               // band width shared by the round's ops (double-float rounds)
   };
   std::vector<Round> rounds;
   int ring = 0, threads = 256;
@@ -292,6 +294,7 @@ static void batch_matvec(fdst_batch b, cudaStream_t st, int threads) {
       g.nop = R.count;
       g.maxt = R.maxt;
       g.threads = threads;
+      g.w = R.w;
       launch_band_df(g, 1, nullptr, st);
     } else {
       BandGroup g;
@@ -481,14 +484,16 @@ static fdst_status build_batch(fdst_batch b) {
     }
   }
   // ---- matvec rounds: (stage, k-th op on the same output) merged across problems
-  std::map<std::pair<int, int>, std::vector<BandOpDF>> rdf;
-  std::map<std::pair<int, int>, std::vector<BandOp>> rf;
-  std::map<std::pair<int, int>, int64_t> rmax;
+  // keyed by (stage, k-th op on the same output, band width): a double-float launch
+  // then shares one width and runs the kernel's fully unrolled instantiation
+  std::map<std::tuple<int, int, int>, std::vector<BandOpDF>> rdf;
+  std::map<std::tuple<int, int, int>, std::vector<BandOp>> rf;
+  std::map<std::tuple<int, int, int>, int64_t> rmax;
   for (auto *h : b->hs) {
     std::map<std::tuple<int, int, int>, int> seen;   // (stage, out_kind, out_id) -> ops so far
     for (const PlanOp &op : b->df ? h->plan_df : h->plan) {
       const int round = seen[std::make_tuple(op.stage, op.out_kind, op.out_id)]++;
-      const auto key = std::make_pair(op.stage, round);
+      const auto key = std::make_tuple(op.stage, round, b->df ? h->bands[op.band].w : 0);
       const BandDev &bd = h->bands[op.band];
       int od[3] = {op.dims[0], op.dims[1], op.dims[2]};
       od[op.mode] = bd.rows;
@@ -527,6 +532,7 @@ static fdst_status build_batch(fdst_batch b) {
   for (auto &kv : rmax) {
     fdst_batch_ctx::Round R;
     R.maxt = kv.second;
+    R.w = std::get<2>(kv.first);
     if (b->df) {
       auto &v = rdf[kv.first];
       R.count = (int)v.size();
