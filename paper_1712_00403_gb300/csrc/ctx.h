@@ -237,8 +237,9 @@ int resume_action(const MinresState &S, double true_rel, double prev_true, int r
 // threshold becomes the one that corresponds to tol at the restart point.
 // Leaves h->done[j] = 0 for the listed ones and 1 for every other one;
 // hs (host copy of the states) is updated and uploaded.
+// vecs: the (v, v_old, w, w_old) buffers in their current roles (default: the handle's).
 fdst_status minres_restart(fdst_ctx *h, const double *b, double *x, int nrhs, const std::vector<int> &which,
                            const std::vector<double> &true_rel, double tol, std::vector<MinresState> &hs,
-                           cudaStream_t st);
+                           cudaStream_t st, double *const *vecs = nullptr);
 
 }  // namespace fdst

@@ -930,15 +930,17 @@ int resume_action(const MinresState &S, double true_rel, double prev_true, int r
 
 fdst_status minres_restart(fdst_ctx *h, const double *b, double *x, int nrhs, const std::vector<int> &which,
                            const std::vector<double> &true_rel, double tol, std::vector<MinresState> &hs,
-                           cudaStream_t st) {
+                           cudaStream_t st, double *const *vecs) {
   const int64_t n = h->n_total;
+  double *v = vecs ? vecs[0] : h->v, *v_old = vecs ? vecs[1] : h->v_old;
+  double *w = vecs ? vecs[2] : h->w, *w_old = vecs ? vecs[3] : h->w_old;
   std::vector<int> mask(nrhs, 1);
   for (int j : which) mask[j] = 0;
   CK(cudaMemcpyAsync(h->done, mask.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, st));
   TRY(run_matvec(h, x, h->Az, nrhs, h->done, st, true));
-  launch_restart_vectors(b, h->Az, h->v, h->v_old, h->w, h->w_old, n, n, nrhs, h->done, st);
-  TRY(run_apply(h, h->v, h->z, nrhs, h->done, st));
-  launch_dot(h->v, h->z, n, n, nrhs, h->partials, h->counters, h->dots, h->done, st);
+  launch_restart_vectors(b, h->Az, v, v_old, w, w_old, n, n, nrhs, h->done, st);
+  TRY(run_apply(h, v, h->z, nrhs, h->done, st));
+  launch_dot(v, h->z, n, n, nrhs, h->partials, h->counters, h->dots, h->done, st);
   std::vector<double> g(nrhs);
   CK(cudaMemcpyAsync(g.data(), h->dots, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -1716,6 +1718,12 @@ fdst_status fdst_solve(fdst_handle h, const double *d_b, double *d_x, int nrhs, 
   std::vector<MinresState> hs(nrhs);
   std::vector<double> prev_true(nrhs, -1.0);
   std::vector<int> restarts(nrhs, 0), est_iters(nrhs, -1);
+  // The Lanczos and update passes write the new vector over the old one and the
+  // roles of (v, v_old) and (w, w_old) are exchanged by pointer after every
+  // iteration, for every right-hand side at once. A right-hand side that sits
+  // stopped for an odd number of iterations therefore has its pairs in the
+  // opposite roles; before it resumes, its slices are exchanged back.
+  std::vector<int> sync_it(nrhs, 0), sync_iters(nrhs, 0);
   const int check_every = 4;
   int it = 0;
   bool residuals_current = false;
@@ -1737,7 +1745,8 @@ fdst_status fdst_solve(fdst_handle h, const double *d_b, double *d_x, int nrhs, 
     size_t e1 = 0;
     if (h->timing) { mark(); e1 = ev.size() - 1; spans.push_back({0, e0, e1}); }
     launch_dot(h->Az, h->z, n, n, nrhs, h->partials, h->counters, delta, h->done, st);
-    launch_minres_lanczos(h->Az, v, v_old, h->state, delta, n, n, nrhs, h->done, st);
+    launch_minres_lanczos(h->Az, v, v_old, h->state, delta, n, n, nrhs, h->done, st, true);
+    std::swap(v, v_old);
     size_t e2 = 0;
     if (h->timing) { mark(); e2 = ev.size() - 1; spans.push_back({2, e1, e2}); }
     TRY(run_apply(h, v, h->z_new, nrhs, h->done, st));
@@ -1745,7 +1754,9 @@ fdst_status fdst_solve(fdst_handle h, const double *d_b, double *d_x, int nrhs, 
     if (h->timing) { mark(); e3 = ev.size() - 1; spans.push_back({1, e2, e3}); }
     launch_dot(v, h->z_new, n, n, nrhs, h->partials, h->counters, g2, h->done, st);
     launch_minres_scalars(h->state, delta, g2, nrhs, maxit, h->done, h->n_stopped, st);
-    launch_minres_update(w_old, w, d_x, h->z, h->z_new, h->state, n, n, nrhs, h->done, st, dfp ? h->x2 : nullptr);
+    launch_minres_update(w_old, w, d_x, h->z, h->z_new, h->state, n, n, nrhs, h->done, st, dfp ? h->x2 : nullptr,
+                         true);
+    std::swap(w, w_old);
     z_pairs = dfp;
     launch_minres_commit(h->state, h->done, nrhs, st);
     if (h->timing) { mark(); spans.push_back({2, e3, ev.size() - 1}); }
@@ -1780,11 +1791,21 @@ fdst_status fdst_solve(fdst_handle h, const double *d_b, double *d_x, int nrhs, 
         for (int j : resume) {
           hs[j].tau = 0.5 * hs[j].tau * tol / true_rel[j];
           hs[j].stop = 0;
+          const int idle = (it - sync_it[j]) - (hs[j].iters - sync_iters[j]);   // iterations spent stopped
+          if (idle & 1) {
+            launch_swap(v + (size_t)j * n, v_old + (size_t)j * n, n, st);
+            launch_swap(w + (size_t)j * n, w_old + (size_t)j * n, n, st);
+          }
         }
         if (!restart.empty()) {
           for (int j : restart) ++restarts[j];
-          TRY(minres_restart(h, d_b, d_x, nrhs, restart, true_rel, tol, hs, st));
+          double *const vecs[4] = {v, v_old, w, w_old};
+          TRY(minres_restart(h, d_b, d_x, nrhs, restart, true_rel, tol, hs, st, vecs));
           z_pairs = false;   // the restarted right-hand sides have a new z
+        }
+        for (int j = 0; j < nrhs; ++j) {
+          sync_it[j] = it;
+          sync_iters[j] = hs[j].iters;
         }
         std::vector<int> hd(nrhs, 1);
         for (int j : resume) hd[j] = 0;

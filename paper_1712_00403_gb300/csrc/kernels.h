@@ -137,9 +137,12 @@ void launch_axpby(const double *x, double *y, double alpha, double beta, int64_t
 void launch_minres_init(MinresState *st, const double *g, int *done, int nrhs, int *n_stopped, double tol,
                         cudaStream_t s);
 // t = Az - (delta/gamma) v - (gamma/gamma_old) v_old; v_old <- v; v <- t (delta = <Az, z>).
+// rotate: v_old <- t only (v untouched); the caller then exchanges the v and v_old pointers.
 void launch_minres_lanczos(const double *Az, double *v, double *v_old, const MinresState *st,
                            const double *delta, int64_t n, int64_t stride, int nrhs, const int *done,
-                           cudaStream_t s);
+                           cudaStream_t s, bool rotate = false);
+// a[i] <-> b[i], i < n.
+void launch_swap(double *a, double *b, int64_t n, cudaStream_t s);
 
 // scalar QR update from gamma_new^2 = <v_new, z_new> (one thread per right-hand side).
 // The estimate |eta|/eta0 is compared with the per-right-hand-side threshold st.tau.
@@ -147,9 +150,10 @@ void launch_minres_scalars(MinresState *st, const double *delta, const double *g
                            const int *done, int *n_stopped, cudaStream_t s);
 // w_new = (z - a3 w_old - a2 w)/a1; w_old <- w; w <- w_new; x += coef_x w_new; z <- z_new / gamma_new;
 // with z_df set, also z_df <- the double-float split of the new z (the next matvec's input).
+// rotate: w_old <- w_new only (w untouched); the caller then exchanges the w and w_old pointers.
 void launch_minres_update(double *w_old, double *w, double *x, double *z, const double *z_new,
                           MinresState *st, int64_t n, int64_t stride, int nrhs, int *done, cudaStream_t s,
-                          float2 *z_df = nullptr);
+                          float2 *z_df = nullptr, bool rotate = false);
 void launch_minres_commit(MinresState *st, int *done, int nrhs, cudaStream_t s);
 // v = b - Ax, v_old = w = w_old = 0 for the right-hand sides with done[j] == 0.
 void launch_restart_vectors(const double *b, const double *Ax, double *v, double *v_old, double *w, double *w_old,

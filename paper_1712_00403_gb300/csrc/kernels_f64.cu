@@ -666,6 +666,9 @@ __device__ __forceinline__ bool same_phase(const void *a, const void *b) {
   return ((reinterpret_cast<uintptr_t>(a) ^ reinterpret_cast<uintptr_t>(b)) & 15) == 0;
 }
 
+// ROT: the new Lanczos vector is written over v_old and v is left as it is (the
+// caller exchanges the two roles), so the pass writes one vector instead of two.
+template <bool ROT>
 __global__ void k_minres_lanczos(const double *Az, double *v, double *v_old, const MinresState *st,
                                  const double *delta, int64_t n, int64_t stride, const int *done) {
   const int j = blockIdx.y;
@@ -674,40 +677,66 @@ __global__ void k_minres_lanczos(const double *Az, double *v, double *v_old, con
   const double f1 = delta[j] / gamma, f2 = gamma / gamma_old;
   const double *a = Az + j * stride;
   double *vv = v + j * stride, *vo = v_old + j * stride;
-  auto step = [&](double ai, double vi, double voi, double &vo_out, double &vv_out) {
-    const double t = ai - f1 * vi - f2 * voi;
-    vo_out = vi;
-    vv_out = t;
+  // one entry: returns the new Lanczos value t, stores it (and, without ROT, shifts v into v_old)
+  auto one = [&](int64_t i) {
+    const double vi = vv[i], t = a[i] - f1 * vi - f2 * vo[i];
+    if (ROT) {
+      vo[i] = t;
+    } else {
+      vo[i] = vi;
+      vv[i] = t;
+    }
   };
   const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, ts = (int64_t)gridDim.x * blockDim.x;
   if (!(same_phase(a, vv) && same_phase(a, vo))) {
-    for (int64_t i = t0; i < n; i += ts) step(a[i], vv[i], vo[i], vo[i], vv[i]);
+    for (int64_t i = t0; i < n; i += ts) one(i);
     return;
   }
   const int64_t head = (reinterpret_cast<uintptr_t>(a) & 15) && n > 0 ? 1 : 0;
-  if (head && t0 == 0) step(a[0], vv[0], vo[0], vo[0], vv[0]);
+  if (head && t0 == 0) one(0);
   const int64_t pairs = (n - head) >> 1;
   const double2 *a2 = reinterpret_cast<const double2 *>(a + head);
   double2 *v2 = reinterpret_cast<double2 *>(vv + head), *o2 = reinterpret_cast<double2 *>(vo + head);
   for (int64_t i = t0; i < pairs; i += ts) {
     const double2 ai = a2[i], vi = v2[i], oi = o2[i];
-    double2 no, nv;
-    step(ai.x, vi.x, oi.x, no.x, nv.x);
-    step(ai.y, vi.y, oi.y, no.y, nv.y);
-    o2[i] = no;
-    v2[i] = nv;
+    const double2 t = make_double2(ai.x - f1 * vi.x - f2 * oi.x, ai.y - f1 * vi.y - f2 * oi.y);
+    if (ROT) {
+      o2[i] = t;
+    } else {
+      o2[i] = vi;
+      v2[i] = t;
+    }
   }
-  if (((n - head) & 1) && t0 == 0) step(a[n - 1], vv[n - 1], vo[n - 1], vo[n - 1], vv[n - 1]);
+  if (((n - head) & 1) && t0 == 0) one(n - 1);
 }
 
 void launch_minres_lanczos(const double *Az, double *v, double *v_old, const MinresState *st,
                            const double *delta, int64_t n, int64_t stride, int nrhs, const int *done,
-                           cudaStream_t s) {
+                           cudaStream_t s, bool rotate) {
   int64_t blocks = (n + 255) / 256;
   if (blocks > 4096) blocks = 4096;
   if (blocks < 1) blocks = 1;
   count_launch(1);
-  k_minres_lanczos<<<dim3((unsigned)blocks, nrhs), 256, 0, s>>>(Az, v, v_old, st, delta, n, stride, done);
+  if (rotate)
+    k_minres_lanczos<true><<<dim3((unsigned)blocks, nrhs), 256, 0, s>>>(Az, v, v_old, st, delta, n, stride, done);
+  else
+    k_minres_lanczos<false><<<dim3((unsigned)blocks, nrhs), 256, 0, s>>>(Az, v, v_old, st, delta, n, stride, done);
+}
+
+__global__ void k_swap(double *a, double *b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double t = a[i];
+    a[i] = b[i];
+    b[i] = t;
+  }
+}
+
+void launch_swap(double *a, double *b, int64_t n, cudaStream_t s) {
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 2048) blocks = 2048;
+  if (blocks < 1) blocks = 1;
+  count_launch(1);
+  k_swap<<<(unsigned)blocks, 256, 0, s>>>(a, b, n);
 }
 
 // One thread per right-hand side: Givens QR update of the Lanczos tridiagonal
@@ -764,6 +793,9 @@ void launch_minres_scalars(MinresState *st, const double *delta, const double *g
 // z <- z_new / gamma_new (the next normalized Lanczos vector), all in place; with z_df
 // set, also the double-float pairs of the new z (the next banded matvec reads them
 // instead of a separate split pass).
+// ROT: the new direction is written over w_old and w is left as it is (the caller
+// exchanges the two roles), so the pass writes one direction vector instead of two.
+template <bool ROT>
 __global__ void k_minres_update(double *w_old, double *w, double *x, double *z, const double *z_new,
                                 const MinresState *st, int64_t n, int64_t stride, const int *done, float2 *z_df) {
   const int j = blockIdx.y;
@@ -776,8 +808,12 @@ __global__ void k_minres_update(double *w_old, double *w, double *x, double *z, 
   auto step = [&](double wi, double woi, double zi, double xi, double zni, double &wo_out, double &w_out,
                   double &x_out, double &z_out) {
     const double wn = (zi - a3 * woi - a2 * wi) * ia1;
-    wo_out = wi;
-    w_out = wn;
+    if (ROT) {
+      wo_out = wn;
+    } else {
+      wo_out = wi;
+      w_out = wn;
+    }
     x_out = fma(cx, wn, xi);
     z_out = zni * ig;
   };
@@ -805,7 +841,7 @@ __global__ void k_minres_update(double *w_old, double *w, double *x, double *z, 
     step(wi.x, oi.x, zi.x, xi.x, ni.x, no.x, nw.x, nx.x, nz.x);
     step(wi.y, oi.y, zi.y, xi.y, ni.y, no.y, nw.y, nx.y, nz.y);
     o2[i] = no;
-    w2[i] = nw;
+    if (!ROT) w2[i] = nw;
     x2[i] = nx;
     z2[i] = nz;
     if (zd) {
@@ -821,12 +857,17 @@ __global__ void k_minres_update(double *w_old, double *w, double *x, double *z, 
 
 void launch_minres_update(double *w_old, double *w, double *x, double *z, const double *z_new,
                           MinresState *st, int64_t n, int64_t stride, int nrhs, int *done, cudaStream_t s,
-                          float2 *z_df) {
+                          float2 *z_df, bool rotate) {
   int64_t blocks = (n + 255) / 256;
   if (blocks > 4096) blocks = 4096;
   if (blocks < 1) blocks = 1;
   count_launch(1);
-  k_minres_update<<<dim3((unsigned)blocks, nrhs), 256, 0, s>>>(w_old, w, x, z, z_new, st, n, stride, done, z_df);
+  if (rotate)
+    k_minres_update<true><<<dim3((unsigned)blocks, nrhs), 256, 0, s>>>(w_old, w, x, z, z_new, st, n, stride, done,
+                                                                     z_df);
+  else
+    k_minres_update<false><<<dim3((unsigned)blocks, nrhs), 256, 0, s>>>(w_old, w, x, z, z_new, st, n, stride, done,
+                                                                      z_df);
 }
 
 __global__ void k_minres_commit(MinresState *st, int *done, int nrhs) {
