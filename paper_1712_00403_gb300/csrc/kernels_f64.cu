@@ -423,8 +423,10 @@ void launch_band_df(const BandGroupDF &g, int nrhs, const int *done, cudaStream_
   switch (w) {
 #define FDST_BAND_W(WW) \
     case WW: k_band_df<T, WW><<<grid, thr, 0, s>>>(g, nrhs, done); break;
-    FDST_BAND_W(4) FDST_BAND_W(6) FDST_BAND_W(7) FDST_BAND_W(8) FDST_BAND_W(9) FDST_BAND_W(10)
-    FDST_BAND_W(11) FDST_BAND_W(13) FDST_BAND_W(14)
+    // the widths of the banded factors at degrees 1..8 (Kronecker plans and point-basis tables)
+    FDST_BAND_W(2) FDST_BAND_W(3) FDST_BAND_W(4) FDST_BAND_W(5) FDST_BAND_W(6) FDST_BAND_W(7)
+    FDST_BAND_W(8) FDST_BAND_W(9) FDST_BAND_W(10) FDST_BAND_W(11) FDST_BAND_W(12) FDST_BAND_W(13)
+    FDST_BAND_W(14) FDST_BAND_W(15) FDST_BAND_W(16) FDST_BAND_W(17) FDST_BAND_W(19) FDST_BAND_W(20)
 #undef FDST_BAND_W
     default: k_band_df<T, 0><<<grid, thr, 0, s>>>(g, nrhs, done); break;
   }
