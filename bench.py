@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--matrix-free", action="store_true",
                     help="mapped workloads: sum-factorized matvec in the iterations instead of the CSR SpMV")
     ap.add_argument("--no-fp64", action="store_true",
-                    help="skip the plain-FP64 leg (FD apply and matvec in FP64) of single-problem workloads")
+                    help="skip the plain-FP64 leg (FD apply and matvec in FP64; batched: the FP64-FD batch)")
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the plain-FP64 leg")
     ap.add_argument("--serving-nel3-max", type=int, default=96,
                     help="largest elements per direction of the served 3D instances (default: the batched range 16..96)")
@@ -591,6 +591,10 @@ def run_gpu(args):
     xh = torch.zeros(b.numel(), dtype=torch.float64, pin_memory=True)
     bn, xn = bh.numpy(), xh.numpy()
     e2e_steps = max(1, args.steps // 3)
+    if not gm:
+        # untimed warm-up call: the host-pointer entry point allocates its device staging
+        # buffers on first use
+        P.solve_host(bn, xn, tol=1e-8, maxit=args.maxit, stream=stream, zero_guess=True)
     torch.cuda.synchronize()
     rep.barrier()
     t0 = time.perf_counter()
@@ -811,17 +815,18 @@ def run_batched(args):
         return res
 
     tc = timed_batch(fd.FD_TF32X3, args.steps, args.warmup, host_e2e=True)
-    f64 = timed_batch(fd.FD_F64, max(1, args.steps // 3 or 1), max(3, args.warmup // 2))
-    errs = [float(torch.linalg.norm(a - b) / torch.linalg.norm(b)) for a, b in zip(tc["apply_out"], f64["apply_out"])]
+    f64 = None if args.no_fp64 else timed_batch(fd.FD_F64, max(1, args.steps // 3 or 1), max(3, args.warmup // 2))
+    errs = ([float(torch.linalg.norm(a - b) / torch.linalg.norm(b)) for a, b in zip(tc["apply_out"], f64["apply_out"])]
+            if f64 else None)
     n = len(specs)
     value = rep.sum(args.steps * n) / (tc["ms"] / 1e3)
     e2e_value = rep.job_rate(n, tc["e2e_s"])
     it_tc = [i["iterations"] for inf in tc["infos"] for i in inf]
-    it_64 = [i["iterations"] for inf in f64["infos"] for i in inf]
+    it_64 = [i["iterations"] for inf in f64["infos"] for i in inf] if f64 else []
     st_tc = sorted(set(i["status"] for inf in tc["infos"] for i in inf))
     tr_tc = max(i["true_rel_res"] for inf in tc["infos"] for i in inf)
-    tr_64 = max(i["true_rel_res"] for inf in f64["infos"] for i in inf)
-    value64 = rep.sum(len(f64["infos"]) * n) / (f64["ms"] / 1e3)
+    tr_64 = max(i["true_rel_res"] for inf in f64["infos"] for i in inf) if f64 else None
+    value64 = rep.sum(len(f64["infos"]) * n) / (f64["ms"] / 1e3) if f64 else None
     # roofline of the grouped split-TF32 FD apply (one launch chain over all instances, autotuner timing)
     flops_apply = 0.0
     for sp in specs:
@@ -855,10 +860,11 @@ def run_batched(args):
                           float(np.mean(it_tc)), "status": st_tc, "true_rel_res_max": tr_tc,
                           "iterations_estimate_mean": float(np.mean([i["iterations_estimate"] for inf in tc["infos"]
                                                                       for i in inf]))},
-               "fp64_fd": {"solves_per_s": value64, "ms_per_step": f64["ms"] / len(f64["infos"]),
-                           "iterations_mean": float(np.mean(it_64)), "true_rel_res_max": tr_64,
-                           "ms_apply_grouped": f64["info"]["ms_apply"],
-                           "iteration_delta_max": max(abs(a - b) for a, b in zip(it_tc[:n], it_64[:n]))},
+               "fp64_fd": ({"solves_per_s": value64, "ms_per_step": f64["ms"] / len(f64["infos"]),
+                            "iterations_mean": float(np.mean(it_64)), "true_rel_res_max": tr_64,
+                            "ms_apply_grouped": f64["info"]["ms_apply"],
+                            "iteration_delta_max": max(abs(a - b) for a, b in zip(it_tc[:n], it_64[:n]))}
+                           if f64 else None),
                "fd_apply_rel_err_vs_f64": errs,
                "autotune": tc["info"], "setup_s": tc["setup_s"], "autotune_s": tc["tune_s"],
                "roofline": roofline, "cpu_baseline": cpu,

@@ -4,7 +4,10 @@
 //   * FD apply: for each contraction step, one tensor-core (or FP64) launch
 //     whose problem table holds every problem's chains (Algorithm 1 steps 2-4);
 //   * Stokes matvec: the problems' banded-Kronecker plans merged stage by
-//     stage into rounds of ops with distinct outputs (one launch per round);
+//     stage into rounds of ops with distinct outputs and one band width (one
+//     launch per round); in double-float the update writes the FP32 pairs of
+//     the next z and the last product into each result block writes FP64, so
+//     no split or join pass runs;
 //   * MINRES vector updates and inner products: one launch per operation over
 //     a table of per-problem segments.
 // Pointers never change between iterations (in-place Lanczos/direction
@@ -22,6 +25,7 @@
 #include <tuple>
 #include <vector>
 
+#include "batch.h"
 #include "ctx.h"
 #include "fp_bits.cuh"
 
@@ -142,7 +146,8 @@ __global__ void k_bscalars(const BatchSeg *segs, int n, int maxit, int *n_stoppe
   *B.st = S;
 }
 
-__global__ void k_bupdate(const BatchSeg *segs) {
+// with df, also the FP32 pairs of the new z (the next matvec's input) into x2
+__global__ void k_bupdate(const BatchSeg *segs, int df) {
   const BatchSeg &B = segs[blockIdx.y];
   if (*B.done) return;
   const MinresState &S = *B.st;
@@ -155,22 +160,15 @@ __global__ void k_bupdate(const BatchSeg *segs) {
     wo[i] = wi;
     w[i] = wn;
     x[i] = fma(cx, wn, x[i]);
-    z[i] = zn[i] * ig;
+    const double znew = zn[i] * ig;
+    z[i] = znew;
+    if (df) B.x2[i] = f64_split(znew);
   }
 }
 
 __global__ void k_bcommit(const BatchSeg *segs, int n) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j < n && !*segs[j].done && segs[j].st->stop) *segs[j].done = 1;
-}
-
-__global__ void k_bsplit(const BatchSeg *segs, int src) {
-  const BatchSeg &B = segs[blockIdx.y];
-  if (*B.done) return;
-  const double *x = B.vec[src];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < B.n; i += (int64_t)gridDim.x * blockDim.x) {
-    B.x2[i] = f64_split(x[i]);
-  }
 }
 
 __global__ void k_bjoin(const BatchSeg *segs, int dst) {
@@ -190,6 +188,7 @@ struct fdst_batch_ctx {
   std::vector<fdst_ctx *> hs;
   int n = 0;
   bool tc = false, df = false;
+  bool join = false;   // double-float results joined by a pass of their own (else by the last products)
   std::vector<BatchSeg> hsegs;
   BatchSeg *segs = nullptr;
   int *n_stopped = nullptr, *h_n_stopped = nullptr;
@@ -283,10 +282,7 @@ static fdst_status batch_apply(fdst_batch b, cudaStream_t st, int ring) {
 
 static void batch_matvec(fdst_batch b, cudaStream_t st, int threads) {
   const dim3 sg = seg_grid(b);
-  if (b->df) {
-    count_launch(1);
-    k_bsplit<<<sg, 256, 0, st>>>(b->segs, kZ);
-  }
+  // (double-float: x2 holds the pairs of z, written by member_init, the update and restarts)
   for (auto &R : b->rounds) {
     if (b->df) {
       BandGroupDF g;
@@ -305,7 +301,7 @@ static void batch_matvec(fdst_batch b, cudaStream_t st, int threads) {
       launch_band(g, 1, nullptr, st);
     }
   }
-  if (b->df) {
+  if (b->join) {
     count_launch(1);
     k_bjoin<<<sg, 256, 0, st>>>(b->segs, kAz);
   }
@@ -323,7 +319,7 @@ static fdst_status batch_iterate(fdst_batch b, int maxit, cudaStream_t st) {
   k_bdot<<<dg, 256, 0, st>>>(b->segs, kV, kZNew, 2);
   k_bscalars<<<tb, 64, 0, st>>>(b->segs, b->n, maxit, b->n_stopped);
   count_launch(2);
-  k_bupdate<<<sg, 256, 0, st>>>(b->segs);
+  k_bupdate<<<sg, 256, 0, st>>>(b->segs, b->df ? 1 : 0);
   k_bcommit<<<tb, 64, 0, st>>>(b->segs, b->n);
   return FDST_OK;
 }
@@ -489,9 +485,24 @@ static fdst_status build_batch(fdst_batch b) {
   std::map<std::tuple<int, int, int>, std::vector<BandOpDF>> rdf;
   std::map<std::tuple<int, int, int>, std::vector<BandOp>> rf;
   std::map<std::tuple<int, int, int>, int64_t> rmax;
+  // double-float: the last product into each result block writes Az in FP64 itself
+  // (when every problem's plan writes all of its blocks), so no join pass runs
+  bool all_joined = b->df;
+  for (auto *h : b->hs) {
+    std::map<int, int> blocks;
+    for (const PlanOp &op : h->plan_df)
+      if (op.out_kind == 3) blocks[op.out_id] = 1;
+    if ((int)blocks.size() != h->dim + 1) all_joined = false;
+  }
+  b->join = b->df && !all_joined;
   for (auto *h : b->hs) {
     std::map<std::tuple<int, int, int>, int> seen;   // (stage, out_kind, out_id) -> ops so far
-    for (const PlanOp &op : b->df ? h->plan_df : h->plan) {
+    const auto &plan = b->df ? h->plan_df : h->plan;
+    std::map<int, size_t> last;
+    for (size_t k = 0; k < plan.size(); ++k)
+      if (plan[k].out_kind == 3) last[plan[k].out_id] = k;
+    for (size_t opi = 0; opi < plan.size(); ++opi) {
+      const PlanOp &op = plan[opi];
       const int round = seen[std::make_tuple(op.stage, op.out_kind, op.out_id)]++;
       const auto key = std::make_tuple(op.stage, round, b->df ? h->bands[op.band].w : 0);
       const BandDev &bd = h->bands[op.band];
@@ -507,7 +518,10 @@ static fdst_status build_batch(fdst_batch b) {
         if (op.in_kind == 0) o.X = h->x2 + h->off[op.in_id];
         else if (op.in_kind == 1) o.X = reinterpret_cast<const float2 *>(h->t1[op.in_id]);
         else o.X = reinterpret_cast<const float2 *>(h->g[op.in_id]);
-        if (op.out_kind == 3) o.Y = h->y2 + h->off[op.out_id];
+        if (op.out_kind == 3) {
+          o.Y = h->y2 + h->off[op.out_id];
+          if (all_joined && last[op.out_id] == opi) o.Y64 = h->Az + h->off[op.out_id];
+        }
         else if (op.out_kind == 1) o.Y = reinterpret_cast<float2 *>(h->t1[op.out_id]);
         else o.Y = reinterpret_cast<float2 *>(h->g[op.out_id]);
         o.done_flag = h->done;
@@ -579,7 +593,15 @@ fdst_status member_init(fdst_ctx *h, int *n_stopped, double tol, cudaStream_t st
   launch_minres_init(h->state, h->dots, h->done, 1, n_stopped, tol, st);
   launch_scale_by_inv_gamma(h->z, h->state, m, m, 1, h->done, st);
   launch_dot(h->hb, h->hb, m, m, 1, h->partials, h->counters, h->dots + 3, nullptr, st);
+  member_split_z(h, st);
   return FDST_OK;
+}
+
+// Double-float batches read the FP32 pairs of z (x2); the update keeps them current,
+// and this writes them after the member's z was set anew (start, restart).
+void member_split_z(fdst_ctx *h, cudaStream_t st) {
+  if (h->desc.matvec_precision == FDST_MV_DF64 && h->x2)
+    launch_split_df(h->z, h->x2, h->n_total, h->n_total, 1, nullptr, st);
 }
 
 // Enqueues ||b - A x||^2 (FP64 matvec) into dots[0]; the caller syncs and divides by dots[3].
@@ -801,6 +823,7 @@ fdst_status fdst_batch_solve(fdst_batch b, const double *const *d_b, double *con
           } else if (a == kRestart) {
             ++restarts[i];
             TRY(minres_restart(h, h->hb, h->hx, 1, {0}, {true_rel[i]}, tol, one, st));
+            member_split_z(h, st);
             if (!one[0].stop && one[0].status == 0) ++running;
           } else {
             one[0].tau = 0.5 * one[0].tau * tol / true_rel[i];

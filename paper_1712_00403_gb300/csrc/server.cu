@@ -323,6 +323,7 @@ fdst_status fdst_server_step(fdst_server s, double now, int *n_active, int *n_qu
         } else if (a == kRestart) {
           ++r.restarts;
           TRY(minres_restart(r.h, r.h->hb, r.h->hx, 1, {0}, {tr}, s->o.tol, one, st));
+          member_split_z(r.h, st);
           cont = !one[0].stop && one[0].status == 0;
         } else if (a == kStagnated) {
           one[0].status = FDST_STAGNATION;
