@@ -66,6 +66,10 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true",
                     help="skip the plain-FP64 leg (FD apply and matvec in FP64; batched: the FP64-FD batch)")
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the plain-FP64 leg")
+    ap.add_argument("--serving-max-active", type=int, default=16,
+                    help="most requests the server advances together (serving workload)")
+    ap.add_argument("--serving-iters", type=int, default=4,
+                    help="MINRES iterations per scheduler step (serving workload)")
     ap.add_argument("--serving-nel3-max", type=int, default=96,
                     help="largest elements per direction of the served 3D instances (default: the batched range 16..96)")
     ap.add_argument("--no-cpu-baseline", action="store_true",
@@ -896,8 +900,8 @@ def run_serving(args):
             out.append((r, knots, synth.rhs(rep.seed(r["seed"]), sizes)))
         return out
 
-    def serve(reqs, max_active=16, fd_precision=fd.FD_TF32X3, matvec_precision=fd.MV_DF64):
-        server = fd.Server(max_active=max_active, iters_per_step=4, fd_precision=fd_precision,
+    def serve(reqs, max_active=args.serving_max_active, fd_precision=fd.FD_TF32X3, matvec_precision=fd.MV_DF64):
+        server = fd.Server(max_active=max_active, iters_per_step=args.serving_iters, fd_precision=fd_precision,
                            matvec_precision=matvec_precision, tol=1e-8, maxit=args.maxit)
         ids, k = [], 0
         l0 = fd.kernel_launches()
@@ -990,8 +994,9 @@ def run_serving(args):
                "ms_per_step": 1e3 * float(tot[1]) / len(w["rates"]), "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "f64+tf32x3 (matvec df64)", "data": "synthetic",
                "config": {"workload": "serving: " + w_text(args.workload, w),
-                          "server": "max_active 16, 4 MINRES iterations per scheduler step, HBM budget 90% of free, "
-                                    "handles set up on 8 host threads",
+                          "server": "max_active %d, %d MINRES iterations per scheduler step, HBM budget 90%% of "
+                                    "free, handles set up on 8 host threads" % (args.serving_max_active,
+                                                                                args.serving_iters),
                           "timing": "host wall clock from each stream's first arrival to its last completion "
                                     "(latency = completion - arrival, host clock)",
                           "parallelism": rep.parallelism},
