@@ -111,7 +111,7 @@ class ClockSampler:
     def summary(self):
         self.f.flush()
         self.f.seek(0)
-        sm, mx, reasons = [], [], set()
+        sm, mx, pw, reasons = [], [], [], set()
         for line in self.f:
             parts = [x.strip() for x in line.split(",")]
             if len(parts) < 9:
@@ -121,6 +121,10 @@ class ClockSampler:
                 mx.append(float(parts[2]))
             except ValueError:
                 continue
+            try:
+                pw.append(float(parts[3]))
+            except ValueError:
+                pass
             names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
             for n, v in zip(names, parts[5:9]):
                 if v.lower().startswith("active"):
@@ -129,7 +133,8 @@ class ClockSampler:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "sm_min_mhz": min(sm),
+                "power_w_median": statistics.median(pw) if pw else None}
 
 
 # ------------------------------------------------------------------ helpers
@@ -594,27 +599,32 @@ def run_gpu(args):
     bh.copy_(b.cpu())
     xh = torch.zeros(b.numel(), dtype=torch.float64, pin_memory=True)
     bn, xn = bh.numpy(), xh.numpy()
-    e2e_steps = max(1, args.steps // 3)
+    e2e_steps = max(2, args.steps // 3)
     if not gm:
         # untimed warm-up call: the host-pointer entry point allocates its device staging
         # buffers on first use
         P.solve_host(bn, xn, tol=1e-8, maxit=args.maxit, stream=stream, zero_guess=True)
     torch.cuda.synchronize()
     rep.barrier()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        if gm:
-            bd = bh.to(dev, non_blocking=True)
-            xd = torch.zeros_like(bd)
-            solve_dev(bd, xd)
-            xh.copy_(xd, non_blocking=True)
-            torch.cuda.synchronize()
-        else:
-            # x0 = 0 cleared on the device: only b goes in, only the solutions come back
-            P.solve_host(bn, xn, tol=1e-8, maxit=args.maxit, stream=stream, zero_guess=True)
-    e2e_s = time.perf_counter() - t0
+    e2e_each = []
+    with ClockSampler(local) as e2e_clk:
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            t_one = time.perf_counter()
+            if gm:
+                bd = bh.to(dev, non_blocking=True)
+                xd = torch.zeros_like(bd)
+                solve_dev(bd, xd)
+                xh.copy_(xd, non_blocking=True)
+                torch.cuda.synchronize()
+            else:
+                # x0 = 0 cleared on the device: only b goes in, only the solutions come back
+                P.solve_host(bn, xn, tol=1e-8, maxit=args.maxit, stream=stream, zero_guess=True)
+            e2e_each.append(1e3 * (time.perf_counter() - t_one))
+        e2e_s = time.perf_counter() - t0
     e2e = {"value": rep.job_rate(e2e_steps * nrhs, e2e_s), "unit": "solves/s",
            "h2d_bytes_per_step": b.numel() * 8, "d2h_bytes_per_step": b.numel() * 8,
+           "ms_each_step": e2e_each, "clocks": e2e_clk.summary(),
            "entry": "fdst_solve_gmres with torch copies" if gm else "fdst_solve_host_zero (pinned host b in, x out)"}
 
     cpu = None
