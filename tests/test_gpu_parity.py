@@ -142,6 +142,35 @@ def test_multi_rhs_equals_single():
         assert max_rel(X4[j], xj.cpu().numpy()) <= 1e-13
 
 
+def test_staggered_stops_and_resumes_equal_single_solves():
+    """Right-hand sides whose recurrence estimates meet the threshold at different
+    iterations sit stopped for different numbers of iterations (odd and even) while
+    the others run, then resume after the true-residual check. MINRES exchanges the
+    roles of (v, v_old) and (w, w_old) by pointer every iteration, so a stopped one
+    has its slices exchanged back before it resumes: each must equal its own
+    single-right-hand-side solve (split-TF32 FD, double-float matvec)."""
+    import paper_1712_00403_gb300 as fd
+    spec = problem_spec(3, 2, 16)
+    kw = dict(fd_precision=fd.FD_TF32X3, matvec_precision=fd.MV_DF64)
+    P6 = gpu_problem(spec, max_rhs=6, **kw)
+    P1 = gpu_problem(spec, max_rhs=1, **kw)
+    B = np.stack([synth.rhs(900 + j, P6.block_sizes) * 10.0 ** (j - 2) for j in range(6)])
+    b = torch.tensor(B.reshape(-1), device="cuda")
+    x = torch.zeros_like(b)
+    info6 = P6.solve(b, x, tol=1e-8, maxit=500)
+    est = [i["iterations_estimate"] for i in info6]
+    assert max(est) > min(est), est                                    # staggered stops
+    assert all(i["iterations"] > i["iterations_estimate"] for i in info6), info6   # every one resumed
+    X6 = x.cpu().numpy().reshape(6, -1)
+    for j in range(6):
+        bj = torch.tensor(B[j], device="cuda")
+        xj = torch.zeros_like(bj)
+        info1 = P1.solve(bj, xj, tol=1e-8, maxit=500)[0]
+        assert info6[j]["status"] == "OK" and info6[j]["true_rel_res"] <= 1e-8
+        assert info1["iterations"] == info6[j]["iterations"], (j, info1, info6[j])
+        assert max_rel(X6[j], xj.cpu().numpy()) <= 1e-13
+
+
 def test_host_entry_points_match_device():
     spec = problem_spec(2, 2, 8)
     P = gpu_problem(spec)
