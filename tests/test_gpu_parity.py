@@ -33,6 +33,11 @@ CASES = [
     problem_spec(2, 3, (26, 5)),       # n_v = 53 > 48: Householder + implicit-QL eigensolver path
     problem_spec(2, 2, 140),           # n_v = 280: FP64 contraction with K and N above 256
     problem_spec(3, 6, (90, 17, 23)),  # a batched-workload-sized instance: p = 6, n_v = 184 x 38 x 50
+    problem_spec(2, 1, (1, 3)),        # degenerate: one element, p = 1 (one velocity function across it)
+    problem_spec(3, 1, (1, 2, 3)),
+    problem_spec(3, 2, (1, 1, 5)),     # two directions of a single element
+    problem_spec(2, 1, 1, "RT"),       # the smallest Raviart-Thomas system (8 unknowns)
+    problem_spec(3, 1, (1, 2, 2), "RT"),
 ]
 
 

@@ -30,6 +30,8 @@ CASES = [
     problem_spec(2, 2, 6, "RT"),
     problem_spec(2, 2, 140),           # n = 280 > 256: the N tile splits in two, ragged second half
     problem_spec(3, 6, (90, 17, 23)),  # a batched-workload-sized instance: p = 6, n = 184 x 38 x 50
+    problem_spec(3, 1, (1, 2, 3)),     # degenerate: a direction with one function (K = N = 1)
+    problem_spec(2, 5, 1),             # one element at p = 5
 ]
 
 
