@@ -41,7 +41,7 @@ TF32_OVER_BF16 = 1.1 / 2.25    # nominal dense TF32 / BF16 ratio
 # double-float matvec of the 40^3 cube (16 RHS, 1,673,830 entries each), scaled to a workload
 # by its entry count (every launch streams operands proportional to it); k_spmv_df per launch
 # of the 32^3 mapped operator at 4 RHS, the bench's own size.
-MATVEC_TRAFFIC = {"k_band_df": {"bytes": 5.7073e9, "entries": 1_673_830, "nrhs": 16, "launches": 24},
+MATVEC_TRAFFIC = {"k_band_df": {"bytes": 5.6576e9, "entries": 1_673_830, "nrhs": 16, "launches": 24},
                   # captured on the 16^3 mapped cube (168,894,405 nonzeros), scaled by nonzero count
                   "k_spmv_df": {"bytes": 2.0534e9, "nnz": 168_894_405, "nrhs": 4, "launches": 1}}
 

@@ -8,6 +8,7 @@
 
 #include <atomic>
 #include <cmath>
+#include <type_traits>
 
 #include "df_arith.cuh"
 #include "fp_bits.cuh"
@@ -313,9 +314,8 @@ __global__ void __launch_bounds__(256, 4) k_band_df(BandGroupDF g, int nrhs, con
     };
     const unsigned M = outer * P;
     const unsigned mb = (M + 32 * T - 1) / (32 * T);
-    for (unsigned u = warp0; u < mb * rows; u += nwarps) {
-      const unsigned cb = u / rows;
-      const unsigned i = u - cb * rows;
+    // band row i over the 32 T entries of chunk cb
+    auto row_unit = [&](unsigned cb, unsigned i) {
       const unsigned c0 = cb * (32 * T);     // first entry of this warp's chunk
       const unsigned l = op.lo[i];
       const float2 *vp = op.vals + (size_t)i * w;
@@ -392,6 +392,91 @@ __global__ void __launch_bounds__(256, 4) k_band_df(BandGroupDF g, int nrhs, con
 #pragma unroll
         for (int t = 0; t < T; ++t)
           if (ok[t]) finish(sh[t], sl[t], yv[t], Y + yo[t]);
+      }
+    };
+    if constexpr (W > 0) {
+      // Rows in pairs (i, i + 1): when lo[i + 1] = lo[i] + D for D <= 2 and the chunk lies
+      // in one outer slab, the two rows read one window of W + D input rows, so each
+      // loaded X entry feeds both rows' sums (each sum still runs over its own band in
+      // column order, so every output equals the one-row evaluation bit for bit). Other
+      // pairs run row by row. (Pairs in mode 0, where the lanes run over rows, spread a
+      // warp's loads over twice the columns and were slower.)
+      auto pair_unit = [&](auto dc, unsigned cb, unsigned i, unsigned o0) {
+        constexpr int D = decltype(dc)::value;
+        const unsigned c0 = cb * (32 * T);
+        const unsigned p0 = c0 - o0 * P + lane;
+        const float2 *va = op.vals + (size_t)i * W, *vb = va + W;
+        const float2 *xp = X + ((size_t)(o0 * din + (unsigned)op.lo[i]) * P + p0);
+        float ah[T], al[T], bh[T], bl[T];
+#pragma unroll
+        for (int t = 0; t < T; ++t) ah[t] = al[t] = bh[t] = bl[t] = 0.0f;
+#pragma unroll
+        for (int j = 0; j < W + D; ++j) {
+          float2 x[T];
+#pragma unroll
+          for (int t = 0; t < T; ++t) x[t] = xp[32 * t];
+          if (j < W) {
+            const float2 v = va[j];
+#pragma unroll
+            for (int t = 0; t < T; ++t) df_fma_acc(v, x[t], ah[t], al[t]);
+          }
+          if (j >= D) {
+            const float2 v = vb[j - D];
+#pragma unroll
+            for (int t = 0; t < T; ++t) df_fma_acc(v, x[t], bh[t], bl[t]);
+          }
+          xp += P;
+        }
+        // output offsets of both rows: row i + 1 sits one row stride after row i
+        unsigned ya[T];
+        unsigned rstride;
+        if (!swap || op.mode == 1) {
+          const unsigned y0 = out12(o0, p0, i);
+#pragma unroll
+          for (int t = 0; t < T; ++t) ya[t] = y0 + 32 * t;
+          rstride = out12(o0, p0, i + 1) - y0;
+        } else {
+          unsigned c1 = p0 / d0, e0 = p0 - c1 * d0;
+#pragma unroll
+          for (int t = 0; t < T; ++t) {
+            ya[t] = e0 + d0 * (i + rows * c1);
+            e0 += 32;
+            while (e0 >= d0) { e0 -= d0; ++c1; }
+          }
+          rstride = d0;
+        }
+        // the old values of both rows are loaded together before the first store
+        float2 yo[2 * T];
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+          yo[t] = acc ? Y[ya[t]] : make_float2(0.f, 0.f);
+          yo[T + t] = acc ? Y[ya[t] + rstride] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int t = 0; t < T; ++t) finish(ah[t], al[t], yo[t], Y + ya[t]);
+#pragma unroll
+        for (int t = 0; t < T; ++t) finish(bh[t], bl[t], yo[T + t], Y + ya[t] + rstride);
+      };
+      const unsigned npairs = (rows + 1) >> 1;
+      for (unsigned u = warp0; u < mb * npairs; u += nwarps) {
+        const unsigned cb = u / npairs;
+        const unsigned i = 2 * (u - cb * npairs);
+        const unsigned c0 = cb * (32 * T);
+        const unsigned o0 = c0 / P;
+        const bool slab = c0 + 32 * T <= M && c0 + 32 * T <= (o0 + 1) * P;
+        const int D = i + 1 < rows ? op.lo[i + 1] - op.lo[i] : -1;
+        if (slab && D == 0) pair_unit(std::integral_constant<int, 0>{}, cb, i, o0);
+        else if (slab && D == 1) pair_unit(std::integral_constant<int, 1>{}, cb, i, o0);
+        else if (slab && D == 2) pair_unit(std::integral_constant<int, 2>{}, cb, i, o0);
+        else {
+          row_unit(cb, i);
+          if (i + 1 < rows) row_unit(cb, i + 1);
+        }
+      }
+    } else {
+      for (unsigned u = warp0; u < mb * rows; u += nwarps) {
+        const unsigned cb = u / rows;
+        row_unit(cb, u - cb * rows);
       }
     }
   }
