@@ -291,6 +291,7 @@ static void batch_matvec(fdst_batch b, cudaStream_t st, int threads) {
       g.maxt = R.maxt;
       g.threads = threads;
       g.w = R.w;
+      g.row_pairs = 0;   // many small products per launch: one band row per warp
       launch_band_df(g, 1, nullptr, st);
     } else {
       BandGroup g;

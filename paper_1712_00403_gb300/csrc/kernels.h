@@ -90,6 +90,7 @@ struct BandGroupDF {
   int64_t maxt = 0;
   int threads = 128;                // at most 256
   int w = 0;                        // with a table: the band width every op shares (0: mixed or unknown)
+  int row_pairs = 1;                // with a shared width: modes 1/2 take band rows in pairs where they can
 };
 void launch_band_df(const BandGroupDF &g, int nrhs, const int *done, cudaStream_t s);
 // Element-wise conversions: kind 0 double -> float (nearest), 1 double -> FP32 pair,

@@ -202,7 +202,8 @@ void launch_band(const BandGroup &g, int nrhs, const int *done, cudaStream_t s) 
 // At most 256 threads per block and 64 registers per thread (4 blocks of 256 per SM).
 // W > 0: every op of the launch has band width W (the band loops unroll fully,
 // so the loads take immediate offsets from a few base pointers); W = 0: any width.
-template <int T, int W>
+// PAIRS (with W > 0): modes 1/2 take band rows in pairs where they can (below).
+template <int T, int W, bool PAIRS>
 __global__ void __launch_bounds__(256, 4) k_band_df(BandGroupDF g, int nrhs, const int *done) {
   const int rhs = blockIdx.y;
   if (done && done[rhs]) return;
@@ -394,13 +395,15 @@ __global__ void __launch_bounds__(256, 4) k_band_df(BandGroupDF g, int nrhs, con
           if (ok[t]) finish(sh[t], sl[t], yv[t], Y + yo[t]);
       }
     };
-    if constexpr (W > 0) {
+    if constexpr (W > 0 && PAIRS) {
       // Rows in pairs (i, i + 1): when lo[i + 1] = lo[i] + D for D <= 2 and the chunk lies
       // in one outer slab, the two rows read one window of W + D input rows, so each
       // loaded X entry feeds both rows' sums (each sum still runs over its own band in
       // column order, so every output equals the one-row evaluation bit for bit). Other
       // pairs run row by row. (Pairs in mode 0, where the lanes run over rows, spread a
-      // warp's loads over twice the columns and were slower.)
+      // warp's loads over twice the columns and were slower. Launches of many small
+      // products with one right-hand side each, as in a batch, run without pairs:
+      // halving their warps lengthened each launch's tail.)
       auto pair_unit = [&](auto dc, unsigned cb, unsigned i, unsigned o0) {
         constexpr int D = decltype(dc)::value;
         const unsigned c0 = cb * (32 * T);
@@ -506,14 +509,17 @@ void launch_band_df(const BandGroupDF &g, int nrhs, const int *done, cudaStream_
       if (g.op[i].w != w) w = 0;
   }
   switch (w) {
-#define FDST_BAND_W(WW) \
-    case WW: k_band_df<T, WW><<<grid, thr, 0, s>>>(g, nrhs, done); break;
+#define FDST_BAND_W(WW)                                                 \
+    case WW:                                                            \
+      if (g.row_pairs) k_band_df<T, WW, true><<<grid, thr, 0, s>>>(g, nrhs, done);  \
+      else k_band_df<T, WW, false><<<grid, thr, 0, s>>>(g, nrhs, done); \
+      break;
     // the widths of the banded factors at degrees 1..8 (Kronecker plans and point-basis tables)
     FDST_BAND_W(2) FDST_BAND_W(3) FDST_BAND_W(4) FDST_BAND_W(5) FDST_BAND_W(6) FDST_BAND_W(7)
     FDST_BAND_W(8) FDST_BAND_W(9) FDST_BAND_W(10) FDST_BAND_W(11) FDST_BAND_W(12) FDST_BAND_W(13)
     FDST_BAND_W(14) FDST_BAND_W(15) FDST_BAND_W(16) FDST_BAND_W(17) FDST_BAND_W(19) FDST_BAND_W(20)
 #undef FDST_BAND_W
-    default: k_band_df<T, 0><<<grid, thr, 0, s>>>(g, nrhs, done); break;
+    default: k_band_df<T, 0, false><<<grid, thr, 0, s>>>(g, nrhs, done); break;
   }
 }
 
